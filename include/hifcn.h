@@ -1,0 +1,182 @@
+/*
+ * hifcn.h - C ABI of the GB300 HIF-preconditioned Crank-Nicolson solver.
+ *
+ * The library solves one Crank-Nicolson (CN) step of
+ *     u_t = div(a(x) grad u) + r(u)      on (0,1)^d, d = 2 or 3, u = 0 on the boundary
+ * (paper Sec. 1, Eq. 1; scheme Eq. CN / CN2) by conjugate gradient
+ * preconditioned with the recursively preconditioned hierarchical
+ * interpolative factorization (PHIF) of A = I - dt/2 M (Sec. 2.2, Eqs. 2_3 - 3_4,
+ * inverse apply Eq. Ainv; algorithm: Algorithm 1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Grid (Sec. 2): n = 1/h = leaf * 2^L intervals per axis, L >= 1; the N =
+ *    (n-1)^d unknowns sit on the interior nodes x_j = h j, 1 <= j <= n-1.
+ *    Every vector argument is a caller-owned buffer of N doubles in
+ *    lexicographic order, x fastest: index = (j_1-1) + (n-1)(j_2-1)
+ *    [+ (n-1)^2 (j_3-1)].  The coefficient a(x) is given at the (n+1)^d nodes
+ *    including the boundary, same ordering with (n+1) in place of (n-1).
+ *  - "device" pointers are CUDA device (or managed) memory of the current
+ *    device; "host" pointers are ordinary host memory.  The library never
+ *    keeps a caller pointer after a call returns.
+ *  - hif_stream is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *    enqueue their device work on that stream.  Host outputs (iteration
+ *    counts, residuals, sizes) are written before the call returns, which
+ *    therefore synchronizes the stream.
+ *  - Return value: HIF_OK (0) or a negative status code listed below;
+ *    hif_strerror() gives a message.  On error no output is guaranteed except
+ *    where stated.
+ *  - A handle is not thread safe; use one handle per host thread or lock.
+ */
+#ifndef HIFCN_H
+#define HIFCN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HIF_OK 0
+#define HIF_EINVAL (-1)   /* invalid argument: grid not leaf*2^L, NULL pointer, bad sizes   */
+#define HIF_ENOMEM (-2)   /* device allocation failed                                          */
+#define HIF_ENOTSPD (-3)  /* a Cholesky pivot was not positive (matrix not SPD / a(x) <= 0)     */
+#define HIF_ENOCONV (-4)  /* PCG reached cg_maxit; outputs hold the last iterate                */
+#define HIF_ETIMEOUT (-5) /* a bounded device-side wait expired                                 */
+#define HIF_ECUDA (-6)    /* a CUDA runtime call failed                                         */
+#define HIF_EFORMAT (-7)  /* factor blob malformed or of another version                        */
+
+typedef void *hif_stream; /* cudaStream_t */
+
+/* Uniform grid of Sec. 2: dim = 2 or 3, n = leaf * 2^L (L >= 1), leaf >= 2. */
+typedef struct {
+  int dim;
+  int n;
+  int leaf;
+} hif_grid;
+
+/* Storage / arithmetic of the factor blocks used by hif_apply inside PCG.
+ * The factorization itself always runs in FP64; the FP32 mode keeps an
+ * additional FP32 copy and applies F^{-1} in FP32 while CG stays in FP64. */
+typedef enum { HIF_FP64 = 0, HIF_FP32 = 1 } hif_precision;
+
+typedef struct {
+  double eps;          /* relative precision of every interpolative decomposition (Eq. 2_5); 0 = exact */
+  int precision;       /* hif_precision of the apply inside pcg_solve / cn_step                      */
+  int skel_edges_3d;   /* 3D only: also skeletonize edges after faces (Sec. 2.2, 3D paragraph)      */
+  double cg_tol;       /* stop when ||r||_2 <= cg_tol ||b||_2 (relative residual)                     */
+  int cg_maxit;        /* iteration cap                                                                */
+  int true_res_period; /* recompute r = b - A x every this many iterations (0 = never)                 */
+} hif_options;
+
+/* Fills *opt with defaults: eps 1e-6, FP64, skel_edges_3d 1, tol 1e-10, maxit 1000, period 50. */
+void hif_default_options(hif_options *opt);
+
+typedef struct hif_handle hif_handle; /* opaque; owns all factor and work memory on the device */
+
+typedef struct {
+  int64_t N;              /* unknowns                                                     */
+  int dim, n, leaf, levels;
+  int root_size;          /* active DOFs left at the root (size of A_L, Eq. 3_4)          */
+  int64_t factor_entries; /* stored factor values (all levels, both precisions counted once) */
+  int64_t apply_bytes;    /* algorithmic bytes one hif_apply streams in the active precision */
+  int64_t device_bytes;   /* device memory the handle holds                                */
+  int precision;
+  double setup_seconds;   /* wall time of the last hif_setup / import                      */
+} hif_info;
+
+/* ---------------------------------------------------------------------------
+ * hif_setup - factor A = I - dt/2 M on the GPU (Sec. 2.2, Eqs. 2_3 - 3_4).
+ *   grid     host, grid description.
+ *   a_nodes  device, (n+1)^dim FP64 nodal values of a(x) > 0 (read during the call).
+ *   dt       time step, > 0.
+ *   opt      host, options (NULL = defaults).
+ *   out      host, receives the new handle (NULL on error).
+ * M is the 5-point (2D) / 7-point (3D) stencil with face coefficient the mean
+ * of the two nodal values.  Levels are factored with cell elimination, block
+ * Jacobi on every separator entity and skeletonization of every edge (2D) /
+ * face (+ edge, 3D) with all IDs of one sub-step computed from the matrix as
+ * it stood before the sub-step.
+ * Errors: HIF_EINVAL, HIF_ENOMEM, HIF_ENOTSPD, HIF_ECUDA. */
+int hif_setup(const hif_grid *grid, const double *a_nodes, double dt, const hif_options *opt,
+              hif_stream stream, hif_handle **out);
+
+/* ---------------------------------------------------------------------------
+ * hif_import_factor - build a handle from a factor blob instead of factoring.
+ *   blob/bytes  host, the packed interchange format written by
+ *               hif_export_factor ("HIFF" v1, see DESIGN of the format below).
+ *   a_nodes, dt as in hif_setup (the stencil of A is assembled from them).
+ * Format (little endian): "HIFF", int32 version=1, dim, n, leaf, levels,
+ * reserved, int64 N, double eps, double dt; per level: int32 ncells, ngroups;
+ * per cell int32 nI, nB, I[nI], B[nB], double G[nI(nI+1)/2] (G = L^{-1}, L =
+ * chol(A_II), packed lower by rows), double V[nB*nI] (V = A_BI A_II^{-1}, row
+ * major); per group int32 ng, idx[ng], double H[ng*ng] (H = K^T C^T restricted
+ * to the group, row major); root int32 nr, idx[nr], double Gr[nr(nr+1)/2].
+ * Errors: HIF_EINVAL, HIF_EFORMAT, HIF_ENOMEM, HIF_ECUDA. */
+int hif_import_factor(const hif_grid *grid, const void *blob, size_t bytes, double dt,
+                      const double *a_nodes, const hif_options *opt, hif_stream stream,
+                      hif_handle **out);
+
+/* hif_export_factor - write the handle's FP64 factor in the "HIFF" v1 format.
+ * If buf is NULL, *bytes receives the size needed; otherwise *bytes is the
+ * capacity of buf (host) and receives the size written.  Errors: HIF_EINVAL. */
+int hif_export_factor(const hif_handle *h, void *buf, size_t *bytes);
+
+/* ---------------------------------------------------------------------------
+ * hif_apply - y = F^{-1} x = R_0 ... R_{L-1} A_L^{-1} R_{L-1}^T ... R_0^T x (Eq. Ainv).
+ *   x, y  device, N doubles each; may not alias.
+ *   precision  HIF_FP64 or HIF_FP32 (needs a handle set up with FP32).
+ * Errors: HIF_EINVAL, HIF_ECUDA. */
+int hif_apply(hif_handle *h, const double *x, double *y, int precision, hif_stream stream);
+
+/* hif_matvec - y = A x with A = I - dt/2 M (Eq. CN).  x, y device, may not alias. */
+int hif_matvec(hif_handle *h, const double *x, double *y, hif_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * pcg_solve - solve A x = b by PCG with preconditioner F^{-1} (Algorithm 1,
+ * pcg(A, g, F^{-1})): x0 = 0, stop when ||r|| <= cg_tol ||b|| on the recurrence
+ * residual, FP64 vectors and scalars, F^{-1} in the handle's precision.
+ *   b       device, N doubles.
+ *   x       device, N doubles, output (input ignored).
+ *   iters   host, number of x updates (may be NULL).
+ *   relres  host, true residual ||b - A x|| / ||b|| at exit (may be NULL).
+ * Errors: HIF_EINVAL, HIF_ENOCONV (x holds the last iterate), HIF_ECUDA. */
+int pcg_solve(hif_handle *h, const double *b, double *x, int *iters, double *relres,
+              hif_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * cn_step - one Crank-Nicolson step (Eq. CN2, loop body of Algorithm 1):
+ *   u_{k+1} = A^{-1} [ (I + dt/2 M) u_k + dt r_k ]
+ *   u_k   device, N doubles.
+ *   r_k   device, N doubles, or NULL to use the built-in reaction set with
+ *         hif_set_reaction evaluated pointwise at u_k (explicit).
+ *   u_k1  device, N doubles, output; may alias u_k.
+ *   iters host, PCG iterations (may be NULL).
+ * Errors: as pcg_solve. */
+int cn_step(hif_handle *h, const double *u_k, const double *r_k, double *u_k1, int *iters,
+            hif_stream stream);
+
+/* hif_set_reaction - built-in explicit reaction r(u) = k1 u (1 - u/k2) (Eq. nr)
+ * for kind = 1; kind = 0 disables it.  k2 may be +inf (linear reaction).
+ * Errors: HIF_EINVAL. */
+int hif_set_reaction(hif_handle *h, int kind, double k1, double k2);
+
+/* hif_query - sizes and statistics of a handle (host output). */
+int hif_query(const hif_handle *h, hif_info *info);
+
+/* hif_destroy - free the handle and all device memory it holds (NULL is a no-op). */
+int hif_destroy(hif_handle *h);
+
+/* hif_strerror - static message for a status code. */
+const char *hif_strerror(int status);
+
+/* hif_last_error - detail of the last failure on the calling host thread
+ * (the failing CUDA call or the reason a blob was rejected); "" if none. */
+const char *hif_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HIFCN_H */

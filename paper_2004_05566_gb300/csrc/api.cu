@@ -1,0 +1,482 @@
+// C ABI entry points of the hifcn library: handle life cycle, factor
+// import/export in the "HIFF" v1 format, and thin wrappers around the device
+// drivers (stencil.cu, apply.cu, pcg.cu, setup.cu).
+#include "internal.h"
+
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+namespace hifcn {
+
+namespace {
+thread_local std::string g_last_error;
+
+double now_seconds() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+__global__ void k_cast_f32(const double *__restrict__ a, float *__restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+}  // namespace
+
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+
+int dev_alloc(Handle *h, void **ptr, size_t bytes) {
+  *ptr = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_last_error(std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes: " +
+                   cudaGetErrorString(e));
+    *ptr = nullptr;
+    return HIF_ENOMEM;
+  }
+  h->allocations.push_back(*ptr);
+  h->device_bytes += (long long)bytes;
+  return HIF_OK;
+}
+
+int alloc_work(Handle *h) {
+  const long long N = h->N;
+  long long nb = (N + 255) / 256;
+  if (nb > 152 * 8) nb = 152 * 8;
+  if (nb < 1) nb = 1;
+  h->nblocks_vec = (int)nb;
+  HIF_TRY(dev_alloc(h, (void **)&h->r, N * sizeof(double)));
+  HIF_TRY(dev_alloc(h, (void **)&h->p, N * sizeof(double)));
+  HIF_TRY(dev_alloc(h, (void **)&h->q, N * sizeof(double)));
+  HIF_TRY(dev_alloc(h, (void **)&h->z, N * sizeof(double)));
+  HIF_TRY(dev_alloc(h, (void **)&h->g, N * sizeof(double)));
+  HIF_TRY(dev_alloc(h, (void **)&h->partials, 4 * nb * sizeof(double)));
+  HIF_TRY(dev_alloc(h, (void **)&h->scal, 16 * sizeof(double)));
+  HIF_CUDA_TRY(cudaMallocHost((void **)&h->host_scal, 16 * sizeof(double)));
+  return HIF_OK;
+}
+
+// Upload the host-built factor (index pool, descriptors, values) and create
+// the reduced-precision copy when requested.
+int build_device_factor(Handle *h, const std::vector<double> &vals64, cudaStream_t s) {
+  h->nvals = (long long)vals64.size();
+  HIF_TRY(dev_alloc(h, (void **)&h->idx, h->idx_host.size() * sizeof(int)));
+  HIF_TRY(dev_alloc(h, (void **)&h->cptr, h->cptr_host.size() * sizeof(long long)));
+  HIF_TRY(dev_alloc(h, (void **)&h->cslot, h->cslot_host.size() * sizeof(long long)));
+  HIF_TRY(dev_alloc(h, (void **)&h->f64.vals, vals64.size() * sizeof(double)));
+  HIF_CUDA_TRY(cudaMemcpyAsync(h->idx, h->idx_host.data(), h->idx_host.size() * sizeof(int),
+                               cudaMemcpyHostToDevice, s));
+  HIF_CUDA_TRY(cudaMemcpyAsync(h->cptr, h->cptr_host.data(), h->cptr_host.size() * sizeof(long long),
+                               cudaMemcpyHostToDevice, s));
+  HIF_CUDA_TRY(cudaMemcpyAsync(h->cslot, h->cslot_host.data(),
+                               h->cslot_host.size() * sizeof(long long), cudaMemcpyHostToDevice, s));
+  HIF_CUDA_TRY(cudaMemcpyAsync(h->f64.vals, vals64.data(), vals64.size() * sizeof(double),
+                               cudaMemcpyHostToDevice, s));
+  return HIF_OK;
+}
+
+// Upload descriptors of every level, allocate the contribution scratch and
+// the FP32 copy (values already on the device in h->f64.vals).
+int finish_device_factor(Handle *h, cudaStream_t s) {
+  h->lv.assign(h->L, LevelDev{});
+  h->max_contrib = 1;
+  for (int l = 0; l < h->L; ++l) {
+    LevelHost &H = h->lv_host[l];
+    LevelDev &D = h->lv[l];
+    D.ncells = (int)H.cells.size();
+    D.ngroups = (int)H.groups.size();
+    for (auto &c : H.cells) {
+      D.max_nI = std::max(D.max_nI, c.nI);
+      D.max_nB = std::max(D.max_nB, c.nB);
+    }
+    for (auto &g : H.groups) D.max_ng = std::max(D.max_ng, g.n);
+    h->max_contrib = std::max(h->max_contrib, H.contrib_slots);
+    HIF_TRY(dev_alloc(h, (void **)&D.cells, std::max<size_t>(1, H.cells.size()) * sizeof(CellDesc)));
+    HIF_TRY(dev_alloc(h, (void **)&D.groups, std::max<size_t>(1, H.groups.size()) * sizeof(GroupDesc)));
+    if (!H.cells.empty())
+      HIF_CUDA_TRY(cudaMemcpyAsync(D.cells, H.cells.data(), H.cells.size() * sizeof(CellDesc),
+                                   cudaMemcpyHostToDevice, s));
+    if (!H.groups.empty())
+      HIF_CUDA_TRY(cudaMemcpyAsync(D.groups, H.groups.data(), H.groups.size() * sizeof(GroupDesc),
+                                   cudaMemcpyHostToDevice, s));
+  }
+  HIF_TRY(dev_alloc(h, (void **)&h->f64.contrib, h->max_contrib * sizeof(double)));
+  if (h->opt.precision == HIF_FP32) {
+    HIF_TRY(dev_alloc(h, (void **)&h->f32.vals, h->nvals * sizeof(float)));
+    HIF_TRY(dev_alloc(h, (void **)&h->f32.contrib, h->max_contrib * sizeof(float)));
+    HIF_TRY(dev_alloc(h, (void **)&h->f32.work, h->N * sizeof(float)));
+    k_cast_f32<<<1216, 256, 0, s>>>(h->f64.vals, h->f32.vals, h->nvals);
+    HIF_CUDA_TRY(cudaGetLastError());
+    h->has_f32 = true;
+  }
+  HIF_CUDA_TRY(cudaStreamSynchronize(s));
+  return HIF_OK;
+}
+
+// Contribution map of one level: for every DOF of every group, the scratch
+// slots (cell C_off + position in B) that cells write for it, in cell order.
+int build_contrib_map(Handle *h, LevelHost &H) {
+  std::vector<int> gpos(h->N, -1);  // global DOF -> running position over the level's groups
+  std::vector<long long> gstart(H.groups.size() + 1, 0);
+  long long tot = 0;
+  for (size_t g = 0; g < H.groups.size(); ++g) {
+    gstart[g] = tot;
+    const int *gi = h->idx_host.data() + H.groups[g].idx_off;
+    for (int i = 0; i < H.groups[g].n; ++i) {
+      if (gi[i] < 0 || gi[i] >= h->N || gpos[gi[i]] != -1) {
+        set_last_error("group DOF out of range or repeated");
+        return HIF_EFORMAT;
+      }
+      gpos[gi[i]] = (int)(tot + i);
+    }
+    tot += H.groups[g].n;
+  }
+  gstart[H.groups.size()] = tot;
+  std::vector<std::vector<long long>> slots(tot);
+  for (auto &c : H.cells) {
+    const int *B = h->idx_host.data() + c.B_off;
+    for (int b = 0; b < c.nB; ++b) {
+      if (B[b] < 0 || B[b] >= h->N || gpos[B[b]] < 0) {
+        set_last_error("cell boundary DOF is not a DOF of any group of its level");
+        return HIF_EFORMAT;
+      }
+      slots[gpos[B[b]]].push_back(c.C_off + b);
+    }
+  }
+  for (size_t g = 0; g < H.groups.size(); ++g) {
+    H.groups[g].cptr_off = (long long)h->cptr_host.size();
+    for (int i = 0; i < H.groups[g].n; ++i) {
+      h->cptr_host.push_back((long long)h->cslot_host.size());
+      for (long long sl : slots[gstart[g] + i]) h->cslot_host.push_back(sl);
+    }
+    h->cptr_host.push_back((long long)h->cslot_host.size());
+  }
+  return HIF_OK;
+}
+
+int validate(const hif_grid *grid, double dt, const void *a_nodes) {
+  if (!grid || !a_nodes) return HIF_EINVAL;
+  if (grid->dim != 2 && grid->dim != 3) return HIF_EINVAL;
+  if (grid->leaf < 2 || grid->n < 4) return HIF_EINVAL;
+  int L = grid_levels(grid->n, grid->leaf);
+  if (L < 1) return HIF_EINVAL;
+  double N = std::pow((double)(grid->n - 1), grid->dim);
+  if (N >= 2147483647.0) return HIF_EINVAL;
+  if (!(dt > 0.0) || !std::isfinite(dt)) return HIF_EINVAL;
+  return HIF_OK;
+}
+
+int create_handle(const hif_grid *grid, const double *a_nodes, double dt, const hif_options *opt,
+                  cudaStream_t s, Handle **out) {
+  *out = nullptr;
+  HIF_TRY(validate(grid, dt, a_nodes));
+  Handle *h = new Handle();
+  h->grid = *grid;
+  h->L = grid_levels(grid->n, grid->leaf);
+  long long S = grid->n - 1;
+  h->N = grid->dim == 2 ? S * S : S * S * S;
+  h->dt = dt;
+  h->h = 1.0 / grid->n;
+  if (opt) h->opt = *opt;
+  else hif_default_options(&h->opt);
+  if (h->opt.precision != HIF_FP64 && h->opt.precision != HIF_FP32) {
+    delete h;
+    return HIF_EINVAL;
+  }
+  int st = alloc_work(h);
+  if (st == HIF_OK) st = stencil_init(h, a_nodes, s);
+  if (st != HIF_OK) {
+    delete h;
+    return st;
+  }
+  *out = h;
+  return HIF_OK;
+}
+
+struct Reader {
+  const unsigned char *p, *end;
+  template <typename T>
+  bool get(T *dst, size_t count = 1) {
+    size_t b = sizeof(T) * count;
+    if ((size_t)(end - p) < b) return false;
+    std::memcpy(dst, p, b);
+    p += b;
+    return true;
+  }
+};
+
+int import_blob(Handle *h, const void *blob, size_t bytes, cudaStream_t s) {
+  Reader rd{(const unsigned char *)blob, (const unsigned char *)blob + bytes};
+  char magic[4];
+  int hdr[6];
+  long long N;
+  double ed[2];
+  if (!rd.get(magic, 4) || std::memcmp(magic, "HIFF", 4) != 0) return HIF_EFORMAT;
+  if (!rd.get(hdr, 6) || !rd.get(&N) || !rd.get(ed, 2)) return HIF_EFORMAT;
+  if (hdr[0] != 1 || hdr[1] != h->grid.dim || hdr[2] != h->grid.n || hdr[3] != h->grid.leaf ||
+      hdr[4] != h->L || N != h->N) {
+    set_last_error("factor blob header does not match the grid");
+    return HIF_EFORMAT;
+  }
+  std::vector<double> vals;
+  h->lv_host.assign(h->L, LevelHost{});
+  auto get_ints = [&](int n, long long *off) -> bool {
+    *off = (long long)h->idx_host.size();
+    h->idx_host.resize(h->idx_host.size() + n);
+    return rd.get(h->idx_host.data() + *off, n);
+  };
+  auto get_vals = [&](long long n, long long *off) -> bool {
+    *off = (long long)vals.size();
+    vals.resize(vals.size() + n);
+    return rd.get(vals.data() + *off, n);
+  };
+  for (int l = 0; l < h->L; ++l) {
+    int cnt[2];
+    if (!rd.get(cnt, 2) || cnt[0] < 0 || cnt[1] < 0) return HIF_EFORMAT;
+    LevelHost &H = h->lv_host[l];
+    long long slots = 0;
+    for (int c = 0; c < cnt[0]; ++c) {
+      CellDesc d{};
+      int sz[2];
+      if (!rd.get(sz, 2) || sz[0] < 0 || sz[1] < 0) return HIF_EFORMAT;
+      d.nI = sz[0];
+      d.nB = sz[1];
+      if (!get_ints(d.nI, &d.I_off) || !get_ints(d.nB, &d.B_off)) return HIF_EFORMAT;
+      if (!get_vals((long long)d.nI * (d.nI + 1) / 2, &d.G_off)) return HIF_EFORMAT;
+      if (!get_vals((long long)d.nB * d.nI, &d.V_off)) return HIF_EFORMAT;
+      d.C_off = slots;
+      slots += d.nB;
+      H.cells.push_back(d);
+    }
+    H.contrib_slots = slots;
+    for (int g = 0; g < cnt[1]; ++g) {
+      GroupDesc d{};
+      if (!rd.get(&d.n) || d.n <= 0) return HIF_EFORMAT;
+      if (!get_ints(d.n, &d.idx_off)) return HIF_EFORMAT;
+      if (!get_vals((long long)d.n * d.n, &d.H_off)) return HIF_EFORMAT;
+      H.groups.push_back(d);
+    }
+    HIF_TRY(build_contrib_map(h, H));
+  }
+  int nr;
+  if (!rd.get(&nr) || nr < 0) return HIF_EFORMAT;
+  h->root_n = nr;
+  if (!get_ints(nr, &h->root_idx_off)) return HIF_EFORMAT;
+  if (!get_vals((long long)nr * (nr + 1) / 2, &h->root_G_off)) return HIF_EFORMAT;
+  if (rd.p != rd.end) return HIF_EFORMAT;
+  for (int v : h->idx_host)
+    if (v < 0 || v >= h->N) return HIF_EFORMAT;
+  HIF_TRY(build_device_factor(h, vals, s));
+  return finish_device_factor(h, s);
+}
+
+long long apply_bytes(const Handle *h, int elem) {
+  long long vals = 0, idxs = 0, slots = 0;
+  for (const LevelHost &H : h->lv_host) {
+    for (auto &c : H.cells) {
+      vals += (long long)c.nI * (c.nI + 1) / 2 + (long long)c.nB * c.nI;
+      idxs += 2LL * c.nI + c.nB;
+    }
+    for (auto &g : H.groups) {
+      vals += (long long)g.n * g.n;
+      idxs += 2LL * g.n;
+    }
+    slots += H.contrib_slots;
+  }
+  vals += (long long)h->root_n * (h->root_n + 1) / 2;
+  // every factor value and index is read once per sweep (forward and
+  // backward); contributions are written and read once; the vector is read
+  // and written once per sweep.
+  return 2 * vals * elem + 2 * idxs * 4 + 2 * slots * elem + 2 * h->N * elem;
+}
+
+}  // namespace hifcn
+
+using namespace hifcn;
+
+hif_handle::~hif_handle() {
+  for (void *p : allocations) cudaFree(p);
+  if (host_scal) cudaFreeHost(host_scal);
+}
+
+extern "C" {
+
+void hif_default_options(hif_options *opt) {
+  if (!opt) return;
+  opt->eps = 1e-6;
+  opt->precision = HIF_FP64;
+  opt->skel_edges_3d = 1;
+  opt->cg_tol = 1e-10;
+  opt->cg_maxit = 1000;
+  opt->true_res_period = 50;
+}
+
+int hif_setup(const hif_grid *grid, const double *a_nodes, double dt, const hif_options *opt,
+              hif_stream stream, hif_handle **out) {
+  if (!out) return HIF_EINVAL;
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  Handle *h = nullptr;
+  HIF_TRY(create_handle(grid, a_nodes, dt, opt, s, &h));
+  if (!(h->opt.eps >= 0.0)) {
+    delete h;
+    return HIF_EINVAL;
+  }
+  double t0 = now_seconds();
+  int st = gpu_setup(h, a_nodes, s);
+  if (st == HIF_OK) st = finish_device_factor(h, s);
+  if (st != HIF_OK) {
+    delete h;
+    return st;
+  }
+  h->setup_seconds = now_seconds() - t0;
+  *out = h;
+  return HIF_OK;
+}
+
+int hif_import_factor(const hif_grid *grid, const void *blob, size_t bytes, double dt,
+                      const double *a_nodes, const hif_options *opt, hif_stream stream,
+                      hif_handle **out) {
+  if (!out || !blob) return HIF_EINVAL;
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  Handle *h = nullptr;
+  HIF_TRY(create_handle(grid, a_nodes, dt, opt, s, &h));
+  double t0 = now_seconds();
+  int st = import_blob(h, blob, bytes, s);
+  if (st != HIF_OK) {
+    delete h;
+    return st;
+  }
+  h->setup_seconds = now_seconds() - t0;
+  *out = h;
+  return HIF_OK;
+}
+
+int hif_export_factor(const hif_handle *hh, void *buf, size_t *bytes) {
+  if (!hh || !bytes) return HIF_EINVAL;
+  const Handle *h = hh;
+  std::vector<unsigned char> out;
+  auto put = [&](const void *p, size_t n) {
+    const unsigned char *c = (const unsigned char *)p;
+    out.insert(out.end(), c, c + n);
+  };
+  std::vector<double> vals(h->nvals);
+  if (h->nvals) {
+    cudaError_t e = cudaMemcpy(vals.data(), h->f64.vals, h->nvals * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return HIF_ECUDA;
+  }
+  put("HIFF", 4);
+  int hdr[6] = {1, h->grid.dim, h->grid.n, h->grid.leaf, h->L, 0};
+  put(hdr, sizeof(hdr));
+  long long N = h->N;
+  put(&N, 8);
+  double ed[2] = {h->opt.eps, h->dt};
+  put(ed, 16);
+  for (const LevelHost &H : h->lv_host) {
+    int cnt[2] = {(int)H.cells.size(), (int)H.groups.size()};
+    put(cnt, 8);
+    for (auto &c : H.cells) {
+      int sz[2] = {c.nI, c.nB};
+      put(sz, 8);
+      put(h->idx_host.data() + c.I_off, c.nI * 4);
+      put(h->idx_host.data() + c.B_off, c.nB * 4);
+      put(vals.data() + c.G_off, (size_t)c.nI * (c.nI + 1) / 2 * 8);
+      put(vals.data() + c.V_off, (size_t)c.nB * c.nI * 8);
+    }
+    for (auto &g : H.groups) {
+      put(&g.n, 4);
+      put(h->idx_host.data() + g.idx_off, g.n * 4);
+      put(vals.data() + g.H_off, (size_t)g.n * g.n * 8);
+    }
+  }
+  put(&h->root_n, 4);
+  put(h->idx_host.data() + h->root_idx_off, h->root_n * 4);
+  put(vals.data() + h->root_G_off, (size_t)h->root_n * (h->root_n + 1) / 2 * 8);
+  if (!buf) {
+    *bytes = out.size();
+    return HIF_OK;
+  }
+  if (*bytes < out.size()) {
+    *bytes = out.size();
+    return HIF_EINVAL;
+  }
+  std::memcpy(buf, out.data(), out.size());
+  *bytes = out.size();
+  return HIF_OK;
+}
+
+int hif_apply(hif_handle *h, const double *x, double *y, int precision, hif_stream stream) {
+  if (!h || !x || !y || x == y) return HIF_EINVAL;
+  return apply_inverse(h, x, y, precision, (cudaStream_t)stream);
+}
+
+int hif_matvec(hif_handle *h, const double *x, double *y, hif_stream stream) {
+  if (!h || !x || !y || x == y) return HIF_EINVAL;
+  return stencil_matvec(h, x, y, (cudaStream_t)stream);
+}
+
+int pcg_solve(hif_handle *h, const double *b, double *x, int *iters, double *relres,
+              hif_stream stream) {
+  if (!h || !b || !x || b == x) return HIF_EINVAL;
+  return pcg(h, b, x, iters, relres, (cudaStream_t)stream);
+}
+
+int cn_step(hif_handle *h, const double *u_k, const double *r_k, double *u_k1, int *iters,
+            hif_stream stream) {
+  if (!h || !u_k || !u_k1) return HIF_EINVAL;
+  return cn(h, u_k, r_k, u_k1, iters, (cudaStream_t)stream);
+}
+
+int hif_set_reaction(hif_handle *h, int kind, double k1, double k2) {
+  if (!h || (kind != 0 && kind != 1)) return HIF_EINVAL;
+  if (kind == 1 && (k2 == 0.0 || std::isnan(k2) || !std::isfinite(k1))) return HIF_EINVAL;
+  h->react_kind = kind;
+  h->react_k1 = k1;
+  h->react_k2 = k2;
+  return HIF_OK;
+}
+
+int hif_query(const hif_handle *hh, hif_info *info) {
+  if (!hh || !info) return HIF_EINVAL;
+  const Handle *h = hh;
+  info->N = h->N;
+  info->dim = h->grid.dim;
+  info->n = h->grid.n;
+  info->leaf = h->grid.leaf;
+  info->levels = h->L;
+  info->root_size = h->root_n;
+  info->factor_entries = h->nvals;
+  info->apply_bytes = apply_bytes(h, h->has_f32 && h->opt.precision == HIF_FP32 ? 4 : 8);
+  info->device_bytes = h->device_bytes;
+  info->precision = h->opt.precision;
+  info->setup_seconds = h->setup_seconds;
+  return HIF_OK;
+}
+
+int hif_destroy(hif_handle *h) {
+  delete h;
+  return HIF_OK;
+}
+
+const char *hif_strerror(int status) {
+  switch (status) {
+    case HIF_OK: return "ok";
+    case HIF_EINVAL: return "invalid argument";
+    case HIF_ENOMEM: return "device allocation failed";
+    case HIF_ENOTSPD: return "Cholesky pivot not positive (matrix not SPD)";
+    case HIF_ENOCONV: return "PCG did not converge within cg_maxit";
+    case HIF_ETIMEOUT: return "bounded device wait expired";
+    case HIF_ECUDA: return "CUDA runtime error";
+    case HIF_EFORMAT: return "malformed factor blob";
+    default: return "unknown status";
+  }
+}
+
+const char *hif_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,154 @@
+// Internal declarations of the hifcn library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/hifcn.h"
+
+namespace hifcn {
+
+// ----------------------------------------------------------------- error handling
+
+struct Status {
+  int code = HIF_OK;
+};
+
+#define HIF_CUDA_TRY(expr)                                                                \
+  do {                                                                                    \
+    cudaError_t _e = (expr);                                                              \
+    if (_e != cudaSuccess) {                                                              \
+      hifcn::set_last_error(std::string(#expr) + ": " + cudaGetErrorString(_e));          \
+      return HIF_ECUDA;                                                                   \
+    }                                                                                     \
+  } while (0)
+
+#define HIF_TRY(expr)        \
+  do {                       \
+    int _s = (expr);         \
+    if (_s != HIF_OK) return _s; \
+  } while (0)
+
+void set_last_error(const std::string &msg);
+
+// ----------------------------------------------------------------- device layout
+//
+// The factor is stored level by level in the form the inverse apply consumes
+// (Eq. Ainv with R_l = E_l C_l K_l):
+//   cell c      : G = L^{-1} (packed lower, row i at offset i(i+1)/2) and
+//                 V = A_BI A_II^{-1} (nB x nI row major);
+//   group g     : H = K_g^T C_g^T restricted to the group's DOFs (n x n row major);
+//   root        : G_r = L_r^{-1} (packed lower).
+// Index lists are int32 global DOF numbers (lexicographic grid order).
+
+struct CellDesc {
+  int nI, nB;
+  long long I_off;  // into the index pool
+  long long B_off;  // into the index pool
+  long long G_off;  // into the value pool
+  long long V_off;  // into the value pool
+  long long C_off;  // into the contribution scratch (nB slots)
+};
+
+struct GroupDesc {
+  int n, pad;
+  long long idx_off;   // into the index pool
+  long long H_off;     // into the value pool
+  long long cptr_off;  // into the per-DOF contribution CSR row pointer array (n+1 entries)
+};
+
+struct LevelHost {
+  std::vector<CellDesc> cells;
+  std::vector<GroupDesc> groups;
+  long long contrib_slots = 0;  // sum of nB over the level's cells
+};
+
+struct LevelDev {
+  int ncells = 0, ngroups = 0;
+  int max_nI = 0, max_nB = 0, max_ng = 0;
+  CellDesc *cells = nullptr;    // device
+  GroupDesc *groups = nullptr;  // device
+};
+
+template <typename T>
+struct FactorValues {
+  T *vals = nullptr;       // device value pool
+  T *contrib = nullptr;    // device contribution scratch
+  T *work = nullptr;       // device work vector (N) for the reduced-precision apply
+};
+
+}  // namespace hifcn
+
+// The opaque C handle is the library's handle object itself.
+struct hif_handle {
+  hif_grid grid{};
+  int L = 0;
+  long long N = 0;
+  double dt = 0, h = 0;
+  hif_options opt{};
+  int react_kind = 0;
+  double react_k1 = 0, react_k2 = 0;
+  double setup_seconds = 0;
+
+  // stencil coefficients of A = I - dt/2 M: diagonal and the coupling to the
+  // +x, +y, +z neighbour (0 when the neighbour is a boundary node)
+  double *diag = nullptr;
+  double *wx = nullptr, *wy = nullptr, *wz = nullptr;
+
+  // factor
+  std::vector<hifcn::LevelHost> lv_host;
+  std::vector<hifcn::LevelDev> lv;
+  std::vector<int> idx_host;         // index pool (host mirror, for export)
+  std::vector<long long> cptr_host;  // contribution CSR row pointers
+  std::vector<long long> cslot_host; // contribution slots
+  int *idx = nullptr;                // device index pool
+  long long *cptr = nullptr, *cslot = nullptr;
+  long long nvals = 0;               // entries in the value pool
+  long long max_contrib = 0;
+  int root_n = 0;
+  long long root_idx_off = 0, root_G_off = 0;
+  hifcn::FactorValues<double> f64;
+  hifcn::FactorValues<float> f32;
+  bool has_f32 = false;
+
+  // PCG work space (FP64)
+  double *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *g = nullptr;
+  double *partials = nullptr;  // per-block partial sums
+  double *scal = nullptr;      // device scalars (see pcg.cu)
+  double *host_scal = nullptr; // pinned host mirror
+  int nblocks_vec = 0;
+
+  std::vector<void *> allocations;
+  long long device_bytes = 0;
+  ~hif_handle();
+};
+
+namespace hifcn {
+
+using Handle = ::hif_handle;
+
+// allocation helper: records the pointer for release in ~Handle
+int dev_alloc(Handle *h, void **ptr, size_t bytes);
+
+// ----------------------------------------------------------------- kernels/drivers
+
+int stencil_init(Handle *h, const double *a_nodes, cudaStream_t s);
+int stencil_matvec(Handle *h, const double *x, double *y, cudaStream_t s);
+int build_device_factor(Handle *h, const std::vector<double> &vals64, cudaStream_t s);
+int apply_inverse(Handle *h, const double *x, double *y, int precision, cudaStream_t s);
+int pcg(Handle *h, const double *b, double *x, int *iters, double *relres, cudaStream_t s);
+int cn(Handle *h, const double *u, const double *r, double *u1, int *iters, cudaStream_t s);
+int gpu_setup(Handle *h, const double *a_nodes, cudaStream_t s);
+int alloc_work(Handle *h);
+
+inline int grid_levels(int n, int leaf) {
+  int L = 0;
+  while ((long long)leaf << L < n) ++L;
+  return ((long long)leaf << L) == n ? L : -1;
+}
+
+}  // namespace hifcn

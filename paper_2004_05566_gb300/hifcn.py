@@ -1,0 +1,238 @@
+"""Python binding of the hifcn C ABI (``include/hifcn.h``).
+
+Argument marshalling only: every step of the solver runs in the CUDA library
+``_lib/libhifcn.so``.  Vectors are torch CUDA tensors (float64, contiguous,
+N = (n-1)^dim elements in lexicographic order, x fastest); PyTorch provides
+device memory and the current stream.  The functions carry the names of the C
+entry points and raise ``HifError`` on a non-zero status.  There is no CPU
+path: if the library is missing, loading fails loudly.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from ctypes import POINTER, byref, c_double, c_int, c_int64, c_size_t, c_void_p
+
+import torch
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libhifcn.so")
+_lib = None
+
+HIF_OK, HIF_EINVAL, HIF_ENOMEM, HIF_ENOTSPD, HIF_ENOCONV, HIF_ETIMEOUT, HIF_ECUDA, HIF_EFORMAT = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+HIF_FP64, HIF_FP32 = 0, 1
+
+EXPORTED = ("hif_default_options", "hif_setup", "hif_import_factor", "hif_export_factor",
+            "hif_apply", "hif_matvec", "pcg_solve", "cn_step", "hif_set_reaction", "hif_query",
+            "hif_destroy", "hif_strerror", "hif_last_error")
+
+
+class HifGrid(ctypes.Structure):
+    _fields_ = [("dim", c_int), ("n", c_int), ("leaf", c_int)]
+
+
+class HifOptions(ctypes.Structure):
+    _fields_ = [("eps", c_double), ("precision", c_int), ("skel_edges_3d", c_int),
+                ("cg_tol", c_double), ("cg_maxit", c_int), ("true_res_period", c_int)]
+
+
+class HifInfo(ctypes.Structure):
+    _fields_ = [("N", c_int64), ("dim", c_int), ("n", c_int), ("leaf", c_int), ("levels", c_int),
+                ("root_size", c_int), ("factor_entries", c_int64), ("apply_bytes", c_int64),
+                ("device_bytes", c_int64), ("precision", c_int), ("setup_seconds", c_double)]
+
+
+class HifError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        self.status = status
+        detail = lib().hif_last_error().decode() if _lib is not None else ""
+        msg = lib().hif_strerror(status).decode()
+        super().__init__(f"{fn} failed: {msg} ({status}){': ' + detail if detail else ''}")
+
+
+def lib():
+    """Load libhifcn.so (built by ``paper_2004_05566_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"CUDA library {_LIB_PATH} is not built; run __graft_entry__.build()")
+    L = ctypes.CDLL(_LIB_PATH)
+    L.hif_default_options.argtypes = [POINTER(HifOptions)]
+    L.hif_default_options.restype = None
+    L.hif_setup.argtypes = [POINTER(HifGrid), c_void_p, c_double, POINTER(HifOptions), c_void_p,
+                            POINTER(c_void_p)]
+    L.hif_import_factor.argtypes = [POINTER(HifGrid), c_void_p, c_size_t, c_double, c_void_p,
+                                    POINTER(HifOptions), c_void_p, POINTER(c_void_p)]
+    L.hif_export_factor.argtypes = [c_void_p, c_void_p, POINTER(c_size_t)]
+    L.hif_apply.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_void_p]
+    L.hif_matvec.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
+    L.pcg_solve.argtypes = [c_void_p, c_void_p, c_void_p, POINTER(c_int), POINTER(c_double), c_void_p]
+    L.cn_step.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_int), c_void_p]
+    L.hif_set_reaction.argtypes = [c_void_p, c_int, c_double, c_double]
+    L.hif_query.argtypes = [c_void_p, POINTER(HifInfo)]
+    L.hif_destroy.argtypes = [c_void_p]
+    L.hif_strerror.argtypes = [c_int]
+    L.hif_strerror.restype = ctypes.c_char_p
+    L.hif_last_error.argtypes = []
+    L.hif_last_error.restype = ctypes.c_char_p
+    for name in ("hif_setup", "hif_import_factor", "hif_export_factor", "hif_apply", "hif_matvec",
+                 "pcg_solve", "cn_step", "hif_set_reaction", "hif_query", "hif_destroy"):
+        getattr(L, name).restype = c_int
+    _lib = L
+    return L
+
+
+def _check(fn: str, status: int, allow=()):
+    if status != HIF_OK and status not in allow:
+        raise HifError(fn, status)
+    return status
+
+
+def _stream(stream):
+    if stream is None:
+        return c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return c_void_p(stream.cuda_stream)
+    return c_void_p(int(stream))
+
+
+def _vec(t: torch.Tensor, N: int, name: str) -> c_void_p:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+        raise TypeError(f"{name} must be a CUDA float64 tensor")
+    if not t.is_contiguous() or t.numel() != N:
+        raise ValueError(f"{name} must be contiguous with {N} elements")
+    return c_void_p(t.data_ptr())
+
+
+def default_options(**kw) -> HifOptions:
+    o = HifOptions()
+    lib().hif_default_options(byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+class Handle:
+    """Owner of a hif_handle*; frees device memory on close()/garbage collection."""
+
+    def __init__(self, ptr: c_void_p, dim: int, n: int, leaf: int):
+        self._ptr = ptr
+        self.dim, self.n, self.leaf = dim, n, leaf
+        self.N = (n - 1) ** dim
+
+    @property
+    def ptr(self) -> c_void_p:
+        if self._ptr is None:
+            raise RuntimeError("handle destroyed")
+        return self._ptr
+
+    def close(self):
+        if self._ptr is not None and _lib is not None:
+            _lib.hif_destroy(self._ptr)
+        self._ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        return hif_query(self)
+
+
+def _grid(dim, n, leaf) -> HifGrid:
+    return HifGrid(dim, n, leaf)
+
+
+def hif_setup(dim: int, n: int, leaf: int, a_nodes: torch.Tensor, dt: float, opt: HifOptions = None,
+              stream=None) -> Handle:
+    """Factor A = I - dt/2 M on the GPU (Sec. 2.2); a_nodes: (n+1)^dim float64 CUDA tensor."""
+    a = _vec(a_nodes.reshape(-1), (n + 1) ** dim, "a_nodes")
+    out = c_void_p()
+    g = _grid(dim, n, leaf)
+    _check("hif_setup", lib().hif_setup(byref(g), a, c_double(dt), byref(opt) if opt else None,
+                                        _stream(stream), byref(out)))
+    return Handle(out, dim, n, leaf)
+
+
+def hif_import_factor(dim: int, n: int, leaf: int, blob: bytes, dt: float, a_nodes: torch.Tensor,
+                      opt: HifOptions = None, stream=None) -> Handle:
+    a = _vec(a_nodes.reshape(-1), (n + 1) ** dim, "a_nodes")
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    out = c_void_p()
+    g = _grid(dim, n, leaf)
+    _check("hif_import_factor", lib().hif_import_factor(byref(g), buf, c_size_t(len(blob)),
+                                                        c_double(dt), a, byref(opt) if opt else None,
+                                                        _stream(stream), byref(out)))
+    return Handle(out, dim, n, leaf)
+
+
+def hif_export_factor(h: Handle) -> bytes:
+    nb = c_size_t(0)
+    _check("hif_export_factor", lib().hif_export_factor(h.ptr, None, byref(nb)))
+    buf = ctypes.create_string_buffer(nb.value)
+    _check("hif_export_factor", lib().hif_export_factor(h.ptr, buf, byref(nb)))
+    return buf.raw[: nb.value]
+
+
+def hif_apply(h: Handle, x: torch.Tensor, y: torch.Tensor = None, precision: int = HIF_FP64,
+              stream=None) -> torch.Tensor:
+    """y = F^{-1} x (Eq. Ainv)."""
+    if y is None:
+        y = torch.empty_like(x)
+    _check("hif_apply", lib().hif_apply(h.ptr, _vec(x, h.N, "x"), _vec(y, h.N, "y"), precision,
+                                        _stream(stream)))
+    return y
+
+
+def hif_matvec(h: Handle, x: torch.Tensor, y: torch.Tensor = None, stream=None) -> torch.Tensor:
+    """y = A x, A = I - dt/2 M (Eq. CN)."""
+    if y is None:
+        y = torch.empty_like(x)
+    _check("hif_matvec", lib().hif_matvec(h.ptr, _vec(x, h.N, "x"), _vec(y, h.N, "y"),
+                                          _stream(stream)))
+    return y
+
+
+def pcg_solve(h: Handle, b: torch.Tensor, x: torch.Tensor = None, stream=None, allow_noconv=False):
+    """Solve A x = b by F^{-1}-preconditioned CG; returns (x, iters, relres)."""
+    if x is None:
+        x = torch.empty_like(b)
+    it = c_int(0)
+    rr = c_double(0.0)
+    _check("pcg_solve", lib().pcg_solve(h.ptr, _vec(b, h.N, "b"), _vec(x, h.N, "x"), byref(it),
+                                        byref(rr), _stream(stream)),
+           allow=(HIF_ENOCONV,) if allow_noconv else ())
+    return x, it.value, rr.value
+
+
+def cn_step(h: Handle, u: torch.Tensor, r: torch.Tensor = None, out: torch.Tensor = None,
+            stream=None):
+    """One Crank-Nicolson step (Eq. CN2); returns (u_next, iters)."""
+    if out is None:
+        out = torch.empty_like(u)
+    it = c_int(0)
+    rp = _vec(r, h.N, "r") if r is not None else None
+    _check("cn_step", lib().cn_step(h.ptr, _vec(u, h.N, "u"), rp, _vec(out, h.N, "out"), byref(it),
+                                    _stream(stream)))
+    return out, it.value
+
+
+def hif_set_reaction(h: Handle, kind: int, k1: float = 1.0, k2: float = math.inf):
+    _check("hif_set_reaction", lib().hif_set_reaction(h.ptr, kind, c_double(k1), c_double(k2)))
+
+
+def hif_query(h: Handle) -> dict:
+    info = HifInfo()
+    _check("hif_query", lib().hif_query(h.ptr, byref(info)))
+    return {k: getattr(info, k) for k, _ in HifInfo._fields_}
+
+
+def hif_destroy(h: Handle):
+    h.close()

@@ -1,0 +1,61 @@
+"""The C-ABI library loads and exports every entry point declared in include/*.h (CPU)."""
+
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(hdr).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([a-z_][a-z0-9_]*)\s*\(",
+                             src, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2004_05566_gb300.hifcn as H
+    return H.lib()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("hif_setup", "hif_apply", "pcg_solve", "cn_step", "hif_import_factor",
+              "hif_export_factor", "hif_query", "hif_destroy", "hif_strerror"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in sorted(_declared()) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_has_same_names(lib):
+    import paper_2004_05566_gb300.hifcn as H
+    for n in _declared():
+        if n in ("hif_strerror", "hif_last_error", "hif_default_options"):
+            continue
+        assert hasattr(H, n), n
+
+
+def test_host_side_validation_without_gpu(lib):
+    """Argument checks that run before any device call."""
+    import ctypes
+    import paper_2004_05566_gb300.hifcn as H
+    out = ctypes.c_void_p()
+    bad = H.HifGrid(2, 100, 16)  # 100 is not 16 * 2^L
+    assert lib.hif_setup(ctypes.byref(bad), ctypes.c_void_p(1), 1.0, None, None,
+                         ctypes.byref(out)) == H.HIF_EINVAL
+    assert lib.hif_strerror(H.HIF_EINVAL) == b"invalid argument"
+    o = H.default_options()
+    assert abs(o.eps - 1e-6) < 1e-20 and o.true_res_period == 50 and o.cg_maxit == 1000
