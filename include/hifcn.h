@@ -168,6 +168,27 @@ int hif_query(const hif_handle *h, hif_info *info);
 /* hif_destroy - free the handle and all device memory it holds (NULL is a no-op). */
 int hif_destroy(hif_handle *h);
 
+/* ---------------------------------------------------------------------------
+ * Kernel statistics (measurement support; no counterpart in the paper).
+ * hif_stats_enable(h, on): when on != 0 every kernel the handle launches on
+ * the apply path is bracketed by CUDA events on its launch stream and its
+ * algorithmic bytes (factor values and indices read once, vector entries read
+ * and written once) are recorded; hif_stats_read synchronizes, aggregates by
+ * kernel name (e.g. "cell_bwd_l0"), writes up to cap records to out (host),
+ * sets *count to the number of records, and clears the accumulated data. */
+typedef struct {
+  char name[48];
+  int64_t launches;
+  double ms;    /* summed device time of the launches */
+  double bytes; /* summed algorithmic bytes of the launches */
+} hif_kernel_stat;
+
+int hif_stats_enable(hif_handle *h, int on);
+int hif_stats_read(hif_handle *h, hif_kernel_stat *out, int cap, int *count);
+
+/* hif_launch_count - kernels launched by this library in this process so far. */
+int64_t hif_launch_count(void);
+
 /* hif_strerror - static message for a status code. */
 const char *hif_strerror(int status);
 

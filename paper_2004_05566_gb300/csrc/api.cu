@@ -3,10 +3,11 @@
 // drivers (stencil.cu, apply.cu, pcg.cu, setup.cu).
 #include "internal.h"
 
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
-#include <mutex>
+#include <map>
 
 namespace hifcn {
 
@@ -26,6 +27,41 @@ __global__ void k_cast_f32(const double *__restrict__ a, float *__restrict__ b, 
 }  // namespace
 
 void set_last_error(const std::string &msg) { g_last_error = msg; }
+
+static std::atomic<long long> g_launches{0};
+void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+StatScope::StatScope(Handle *hh, const char *name, int level, double by, cudaStream_t st)
+    : h(hh), s(st), bytes(by) {
+  note_launch();
+  if (!h->stats_on) return;
+  std::string nm = std::string(name) + (level >= 0 ? "_l" + std::to_string(level) : "");
+  for (size_t i = 0; i < h->stat_names.size(); ++i)
+    if (h->stat_names[i] == nm) idx = (int)i;
+  if (idx < 0) {
+    idx = (int)h->stat_names.size();
+    h->stat_names.push_back(nm);
+  }
+  auto take = [&]() {
+    cudaEvent_t e = nullptr;
+    if (!h->event_pool.empty()) {
+      e = h->event_pool.back();
+      h->event_pool.pop_back();
+    } else {
+      cudaEventCreate(&e);
+    }
+    return e;
+  };
+  a = take();
+  b = take();
+  cudaEventRecord(a, s);
+}
+
+StatScope::~StatScope() {
+  if (idx < 0) return;
+  cudaEventRecord(b, s);
+  h->stat_pending.push_back({idx, a, b, bytes});
+}
 
 int dev_alloc(Handle *h, void **ptr, size_t bytes) {
   *ptr = nullptr;
@@ -92,8 +128,21 @@ int finish_device_factor(Handle *h, cudaStream_t s) {
     for (auto &c : H.cells) {
       D.max_nI = std::max(D.max_nI, c.nI);
       D.max_nB = std::max(D.max_nB, c.nB);
+      D.vals_cell += (double)c.nI * (c.nI + 1) / 2 + (double)c.nB * c.nI;
+      D.idx_cell_fwd += 4.0 * c.nI;
+      D.idx_cell_bwd += 4.0 * (c.nI + c.nB);
+      D.vec_cell_fwd += 2.0 * c.nI;          // x_I read and written
+      D.vec_cell_bwd += 2.0 * c.nI + c.nB;   // x_I read and written, x_B read
+      D.contrib += c.nB;                     // written by cell_fwd, read by group_fwd
     }
-    for (auto &g : H.groups) D.max_ng = std::max(D.max_ng, g.n);
+    for (auto &g : H.groups) {
+      D.max_ng = std::max(D.max_ng, g.n);
+      D.vals_group += (double)g.n * g.n;
+      D.idx_group += 4.0 * g.n + 8.0 * (g.n + 1);
+      D.idx_group_bwd += 4.0 * g.n;
+      D.vec_group += 2.0 * g.n;
+    }
+    D.cslot_bytes = 8.0 * (double)D.contrib;
     h->max_contrib = std::max(h->max_contrib, H.contrib_slots);
     HIF_TRY(dev_alloc(h, (void **)&D.cells, std::max<size_t>(1, H.cells.size()) * sizeof(CellDesc)));
     HIF_TRY(dev_alloc(h, (void **)&D.groups, std::max<size_t>(1, H.groups.size()) * sizeof(GroupDesc)));
@@ -110,6 +159,7 @@ int finish_device_factor(Handle *h, cudaStream_t s) {
     HIF_TRY(dev_alloc(h, (void **)&h->f32.contrib, h->max_contrib * sizeof(float)));
     HIF_TRY(dev_alloc(h, (void **)&h->f32.work, h->N * sizeof(float)));
     k_cast_f32<<<1216, 256, 0, s>>>(h->f64.vals, h->f32.vals, h->nvals);
+    note_launch();
     HIF_CUDA_TRY(cudaGetLastError());
     h->has_f32 = true;
   }
@@ -299,6 +349,12 @@ long long apply_bytes(const Handle *h, int elem) {
 using namespace hifcn;
 
 hif_handle::~hif_handle() {
+  cudaDeviceSynchronize();
+  for (auto &r : stat_pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : event_pool) cudaEventDestroy(e);
   for (void *p : allocations) cudaFree(p);
   if (host_scal) cudaFreeHost(host_scal);
 }
@@ -478,5 +534,42 @@ const char *hif_strerror(int status) {
 }
 
 const char *hif_last_error(void) { return g_last_error.c_str(); }
+
+int hif_stats_enable(hif_handle *h, int on) {
+  if (!h) return HIF_EINVAL;
+  h->stats_on = on != 0;
+  return HIF_OK;
+}
+
+int hif_stats_read(hif_handle *h, hif_kernel_stat *out, int cap, int *count) {
+  if (!h || !count || (cap > 0 && !out)) return HIF_EINVAL;
+  HIF_CUDA_TRY(cudaDeviceSynchronize());
+  std::vector<hif_kernel_stat> agg(h->stat_names.size());
+  for (size_t i = 0; i < agg.size(); ++i) {
+    std::memset(&agg[i], 0, sizeof(hif_kernel_stat));
+    std::strncpy(agg[i].name, h->stat_names[i].c_str(), sizeof(agg[i].name) - 1);
+  }
+  for (auto &r : h->stat_pending) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    agg[r.name].launches += 1;
+    agg[r.name].ms += ms;
+    agg[r.name].bytes += r.bytes;
+    h->event_pool.push_back(r.a);
+    h->event_pool.push_back(r.b);
+  }
+  h->stat_pending.clear();
+  int n = 0;
+  for (auto &a : agg)
+    if (a.launches > 0) {
+      if (n < cap) out[n] = a;
+      ++n;
+    }
+  *count = n < cap ? n : cap;
+  if (cap == 0) *count = n;
+  return HIF_OK;
+}
+
+int64_t hif_launch_count(void) { return (int64_t)g_launches.load(); }
 
 }  // extern "C"

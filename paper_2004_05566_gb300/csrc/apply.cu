@@ -204,20 +204,26 @@ int apply_levels(Handle *h, const FactorValues<T> &fv, T *x, cudaStream_t s) {
     set_last_error("root block exceeds the shared-memory staging limit");
     return HIF_EINVAL;
   }
+  const double E = sizeof(T);
   for (int l = 0; l < h->L; ++l) {
     const LevelDev &lv = h->lv[l];
     if (lv.ncells) {
       size_t sm = (size_t)lv.max_nI * sizeof(T);
+      StatScope sc(h, "cell_fwd", l, (lv.vals_cell + lv.vec_cell_fwd + lv.contrib) * E + lv.idx_cell_fwd, s);
       k_cell_fwd<T><<<lv.ncells, kCellThreads, sm, s>>>(lv.cells, h->idx, fv.vals, fv.contrib, x);
     }
     if (lv.ngroups) {
       size_t sm = (size_t)lv.max_ng * sizeof(T);
+      StatScope sc(h, "group_fwd", l,
+                   (lv.vals_group + lv.vec_group + lv.contrib) * E + lv.idx_group + lv.cslot_bytes, s);
       k_group_fwd<T><<<lv.ngroups, kGroupThreads, sm, s>>>(lv.groups, h->idx, h->cptr, h->cslot,
                                                            fv.vals, fv.contrib, x);
     }
   }
   if (h->root_n > 0) {
     size_t sm = 2 * (size_t)h->root_n * sizeof(T);
+    const double nr = h->root_n;
+    StatScope sc(h, "root", -1, (nr * (nr + 1) / 2 + 2 * nr) * E + 4 * nr, s);
     k_root<T><<<1, kRootThreads, sm, s>>>(h->root_n, h->idx + h->root_idx_off,
                                           fv.vals + h->root_G_off, x);
   }
@@ -225,10 +231,12 @@ int apply_levels(Handle *h, const FactorValues<T> &fv, T *x, cudaStream_t s) {
     const LevelDev &lv = h->lv[l];
     if (lv.ngroups) {
       size_t sm = (size_t)lv.max_ng * sizeof(T);
+      StatScope sc(h, "group_bwd", l, (lv.vals_group + lv.vec_group) * E + lv.idx_group_bwd, s);
       k_group_bwd<T><<<lv.ngroups, kGroupThreads, sm, s>>>(lv.groups, h->idx, fv.vals, x);
     }
     if (lv.ncells) {
       size_t sm = (size_t)(lv.max_nI + lv.max_nB) * sizeof(T);
+      StatScope sc(h, "cell_bwd", l, (lv.vals_cell + lv.vec_cell_bwd) * E + lv.idx_cell_bwd, s);
       k_cell_bwd<T><<<lv.ncells, kCellThreads, sm, s>>>(lv.cells, h->idx, fv.vals, x);
     }
   }
@@ -252,14 +260,17 @@ int apply_inverse(Handle *h, const double *x, double *y, int precision, cudaStre
   }
   if (precision != HIF_FP32 || !h->has_f32) return HIF_EINVAL;
   k_to_float<<<h->nblocks_vec, 256, 0, s>>>(x, h->f32.work, h->N);
+  note_launch();
   HIF_TRY(apply_inplace_f32(h, h->f32.work, s));
   k_to_double<<<h->nblocks_vec, 256, 0, s>>>(h->f32.work, y, h->N);
+  note_launch();
   HIF_CUDA_TRY(cudaGetLastError());
   return HIF_OK;
 }
 
 int cast_values_f32(Handle *h, cudaStream_t s) {
   k_to_float<<<1216, 256, 0, s>>>(h->f64.vals, h->f32.vals, h->nvals);
+  note_launch();
   HIF_CUDA_TRY(cudaGetLastError());
   return HIF_OK;
 }

@@ -70,6 +70,10 @@ struct LevelHost {
 struct LevelDev {
   int ncells = 0, ngroups = 0;
   int max_nI = 0, max_nB = 0, max_ng = 0;
+  // algorithmic bytes per launch for one-byte-per-value accounting:
+  // values read, indices read (4 B), vector entries read+written, contributions
+  double vals_cell = 0, vals_group = 0, idx_cell_fwd = 0, idx_cell_bwd = 0, idx_group = 0, idx_group_bwd = 0;
+  double vec_cell_fwd = 0, vec_cell_bwd = 0, vec_group = 0, contrib = 0, cslot_bytes = 0;
   CellDesc *cells = nullptr;    // device
   GroupDesc *groups = nullptr;  // device
 };
@@ -124,6 +128,17 @@ struct hif_handle {
 
   std::vector<void *> allocations;
   long long device_bytes = 0;
+
+  // kernel statistics (hif_stats_enable)
+  struct StatRec {
+    int name;
+    cudaEvent_t a, b;
+    double bytes;
+  };
+  bool stats_on = false;
+  std::vector<std::string> stat_names;
+  std::vector<StatRec> stat_pending;
+  std::vector<cudaEvent_t> event_pool;
   ~hif_handle();
 };
 
@@ -133,6 +148,19 @@ using Handle = ::hif_handle;
 
 // allocation helper: records the pointer for release in ~Handle
 int dev_alloc(Handle *h, void **ptr, size_t bytes);
+
+// launch bookkeeping: every kernel launch of the library calls note_launch();
+// with statistics on, StatScope brackets a launch with events.
+void note_launch(int n = 1);
+struct StatScope {
+  Handle *h;
+  int idx = -1;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr, b = nullptr;
+  double bytes;
+  StatScope(Handle *h, const char *name, int level, double bytes, cudaStream_t s);
+  ~StatScope();
+};
 
 // ----------------------------------------------------------------- kernels/drivers
 

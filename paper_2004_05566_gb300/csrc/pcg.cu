@@ -176,7 +176,9 @@ int pcg_impl(Handle *h, const double *b, double *x, TZ *z, int *iters_out, doubl
   };
 
   k_start<TZ><<<nb, NT, 0, s>>>(b, x, h->r, z, N, part);
+  note_launch();
   k_scalar<<<1, 32, 0, s>>>(sc, part, nb, 4, tol2);
+  note_launch();
   HIF_CUDA_TRY(cudaMemcpyAsync(h->host_scal, sc, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
   HIF_CUDA_TRY(cudaStreamSynchronize(s));
   const double bb = h->host_scal[S_BB];
@@ -187,19 +189,27 @@ int pcg_impl(Handle *h, const double *b, double *x, TZ *z, int *iters_out, doubl
   }
   HIF_TRY(precond(z));
   k_dot<TZ><<<nb, NT, 0, s>>>(h->r, z, N, part);
+  note_launch();
   k_scalar<<<1, 32, 0, s>>>(sc, part, nb, 3, tol2);
+  note_launch();
   k_update_p<TZ><<<nb, NT, 0, s>>>(h->p, z, sc, N, 1);
+  note_launch();
   int it = 0;
   bool conv = false;
   const int period = h->opt.true_res_period;
   while (it < h->opt.cg_maxit) {
     k_spmv_dot<<<nb, NT, 0, s>>>(h->p, h->q, st, part);
+    note_launch();
     k_scalar<<<1, 32, 0, s>>>(sc, part, nb, 0, tol2);
+    note_launch();
     k_update_xr<TZ><<<nb, NT, 0, s>>>(x, h->r, h->p, h->q, z, sc, N, part);
+    note_launch();
     ++it;
     if (period > 0 && it % period == 0)
       k_true_residual<TZ><<<nb, NT, 0, s>>>(b, x, h->r, z, st, part);
+      note_launch();
     k_scalar<<<1, 32, 0, s>>>(sc, part, nb, 1, tol2);
+    note_launch();
     HIF_CUDA_TRY(cudaGetLastError());
     HIF_CUDA_TRY(cudaMemcpyAsync(h->host_scal, sc, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
     HIF_CUDA_TRY(cudaStreamSynchronize(s));
@@ -209,13 +219,18 @@ int pcg_impl(Handle *h, const double *b, double *x, TZ *z, int *iters_out, doubl
     }
     HIF_TRY(precond(z));
     k_dot<TZ><<<nb, NT, 0, s>>>(h->r, z, N, part);
+    note_launch();
     k_scalar<<<1, 32, 0, s>>>(sc, part, nb, 2, tol2);
+    note_launch();
     k_update_p<TZ><<<nb, NT, 0, s>>>(h->p, z, sc, N, 0);
+    note_launch();
   }
   if (iters_out) *iters_out = it;
   if (relres_out) {
     k_resid_norm<<<nb, NT, 0, s>>>(b, x, st, part);
+    note_launch();
     k_scalar<<<1, 32, 0, s>>>(sc, part, nb, 1, tol2);
+    note_launch();
     HIF_CUDA_TRY(cudaMemcpyAsync(h->host_scal, sc, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
     HIF_CUDA_TRY(cudaStreamSynchronize(s));
     *relres_out = sqrt(h->host_scal[S_RR] / bb);

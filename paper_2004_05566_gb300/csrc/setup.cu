@@ -1,10 +1,1113 @@
-// GPU factorization (placeholder until the batched setup kernels land).
+// GPU factorization: recursively preconditioned hierarchical interpolative
+// factorization of A = I - dt/2 M (paper Sec. 2.2, Eqs. 2_3 - 3_4), FP64.
+//
+// Storage during the factorization is multifrontal: at level l every cell c
+// owns a dense frontal matrix F_c over its active DOFs (interior I_c first,
+// then the boundary B_c grouped by separator entity), and the current matrix
+// is A_l = sum_c P_c F_c P_c^T; an entry shared by several cells is held by
+// the cell of smallest index.  Per level:
+//   1. assemble: level 0 from the stencil, level l > 0 by extend-add of the
+//      children's surviving boundary blocks (children in fixed order);
+//   2. cell elimination (Eq. 2_3): partial Cholesky of F_c over I_c, giving
+//      L, W^T = A_BI L^{-T} and the Schur complement X_BB = A_BB - W^T W;
+//      the apply operators G = L^{-1} and V = A_BI A_II^{-1} = W^T G are stored;
+//   3. block Jacobi (Eq. jacobi-precond): per separator entity g the diagonal
+//      block sum_c F_c[g,g] is factored, L_g^{-1} rescales rows and columns of
+//      g in every cell, the diagonal blocks become I (held by the owner);
+//   4. skeletonization (Eqs. 2_4 - 2_9): per edge (2D) / face then edge (3D)
+//      the tall block A~_{R,g} is gathered (rows shared by two cells summed),
+//      column-pivoted Householder QR selects the skeleton (keep pivots while
+//      |R_tt| > eps |R_00|), T = R11^{-1} R12, S = I + T^T T = Ls Ls^T,
+//      X = I - T S^{-1} T^T replaces the skeleton diagonal block; the group's
+//      apply operator H = K^T C^T restricted to the group is stored.  All IDs
+//      of one sub-step read the matrix as it was before the sub-step.
+// The root (level L) is a single cell without boundary whose G is L_r^{-1}.
+//
+// The host only plans integer structure (entity membership, offsets, maps);
+// every floating-point operation runs in the kernels below.  Each CTA works
+// on one cell / entity; waits are __syncthreads only (no spin-waits).
 #include "internal.h"
+#include "device_common.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
 
 namespace hifcn {
-int gpu_setup(Handle *h, const double *a_nodes, cudaStream_t s) {
-  (void)h; (void)a_nodes; (void)s;
-  set_last_error("GPU setup not available in this build");
-  return HIF_EINVAL;
+
+int finish_device_factor(Handle *h, cudaStream_t s);
+int build_contrib_map(Handle *h, LevelHost &H);
+
+namespace {
+
+constexpr int NT = 256;
+
+// ------------------------------------------------------------------ device data
+
+struct SCell {
+  int nI, nB;
+  long long F_off;    // frontal matrix (n x n column major, n = nI + nB)
+  long long G_off;    // packed L^{-1} in the level value pool
+  long long V_off;    // V (nB x nI row major) in the level value pool
+  long long S_off;    // nB x nB scratch for the Jacobi rescaling
+  long long dofs_off; // local DOF list (I then B), global indices
+  long long bmap_off; // per B position: (group id, position in group)
+};
+
+struct SGroup {
+  int n;              // DOFs
+  int ncell;          // adjacent cells
+  long long gc_off;   // into gcells: (cell id, offset of g in that cell's B)
+  long long Linv_off; // n x n row major
+  long long D_off;    // n x n scratch
+  long long H_off;    // n x n row major in the level value pool
+};
+
+struct SSkel {        // one skeletonized group of a sub-step
+  int g;              // group id
+  int R;              // rows of A~_{R,g}
+  long long row_off;  // into rowptr (R + 1 entries)
+  long long ws_off;   // workspace (doubles)
+  long long perm_off; // output pivot order (n ints)
+};
+
+struct SExt {         // one child of a parent in the extend-add
+  int child, parent;
+  int m;              // surviving boundary positions of the child
+  long long ent_off;  // into ext entries: (child local index, parent local index)
+};
+
+__device__ __forceinline__ bool owner_axis(int a, int b, int s, int nc, int c) {
+  // cells along one axis containing both coordinates a and b; c must be the smallest
+  int lo_a = (a % s == 0) ? a / s - 1 : a / s, hi_a = a / s;
+  int lo_b = (b % s == 0) ? b / s - 1 : b / s, hi_b = b / s;
+  if (hi_a > nc - 1) hi_a = nc - 1;
+  if (hi_b > nc - 1) hi_b = nc - 1;
+  if (lo_a < 0) lo_a = 0;
+  if (lo_b < 0) lo_b = 0;
+  int lo = lo_a > lo_b ? lo_a : lo_b;
+  return c == lo;
 }
+
+// ---------------------------------------------------------------- level 0: stencil
+
+__global__ void __launch_bounds__(NT) k_assemble_leaf(const SCell *__restrict__ cells,
+                                                      const int *__restrict__ cdofs,
+                                                      const double *__restrict__ diag,
+                                                      const double *__restrict__ wx,
+                                                      const double *__restrict__ wy,
+                                                      const double *__restrict__ wz, int dim,
+                                                      int n, int s, int nc, double *__restrict__ F) {
+  extern __shared__ int boxmap[];  // (s+1)^dim
+  const SCell c = cells[blockIdx.x];
+  const int nn = c.nI + c.nB;
+  double *Fc = F + c.F_off;
+  const int *dofs = cdofs + c.dofs_off;
+  const int cid = blockIdx.x;
+  const int cc[3] = {cid % nc, (cid / nc) % nc, dim == 3 ? cid / (nc * nc) : 0};
+  const int box = s + 1;
+  const int boxn = dim == 3 ? box * box * box : box * box;
+  for (int t = threadIdx.x; t < boxn; t += NT) boxmap[t] = -1;
+  for (long long t = threadIdx.x; t < (long long)nn * nn; t += NT) Fc[t] = 0.0;
+  __syncthreads();
+  const long long S = n - 1;
+  for (int p = threadIdx.x; p < nn; p += NT) {
+    long long d = dofs[p];
+    int j0 = (int)(d % S) + 1 - cc[0] * s, j1 = (int)((d / S) % S) + 1 - cc[1] * s;
+    int j2 = dim == 3 ? (int)(d / (S * S)) + 1 - cc[2] * s : 0;
+    boxmap[j0 + box * j1 + box * box * j2] = p;
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < nn; p += NT) {
+    long long d = dofs[p];
+    int a[3] = {(int)(d % S) + 1, (int)((d / S) % S) + 1, dim == 3 ? (int)(d / (S * S)) + 1 : 0};
+    // diagonal
+    bool own = true;
+    for (int ax = 0; ax < dim; ++ax) own = own && owner_axis(a[ax], a[ax], s, nc, cc[ax]);
+    if (own) Fc[p + (long long)p * nn] = diag[d];
+    for (int ax = 0; ax < dim; ++ax) {
+      for (int sg = -1; sg <= 1; sg += 2) {
+        int b[3] = {a[0], a[1], a[2]};
+        b[ax] += sg;
+        if (b[ax] < 1 || b[ax] > n - 1) continue;
+        int lb[3] = {b[0] - cc[0] * s, b[1] - cc[1] * s, dim == 3 ? b[2] - cc[2] * s : 0};
+        bool in = true;
+        for (int q = 0; q < dim; ++q) in = in && lb[q] >= 0 && lb[q] <= s;
+        if (!in) continue;
+        int qpos = boxmap[lb[0] + box * lb[1] + box * box * lb[2]];
+        if (qpos < 0) continue;
+        bool ow = true;
+        for (int q = 0; q < dim; ++q) ow = ow && owner_axis(a[q], b[q], s, nc, cc[q]);
+        if (!ow) continue;
+        long long e = sg > 0 ? d : d - (ax == 0 ? 1 : ax == 1 ? S : S * S);
+        const double *w = ax == 0 ? wx : ax == 1 ? wy : wz;
+        Fc[p + (long long)qpos * nn] = -w[e];
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------ extend-add (l > 0)
+
+__global__ void __launch_bounds__(NT) k_extend_add(const int *__restrict__ pchild, const SExt *__restrict__ ext,
+                                                   const int2 *__restrict__ ent,
+                                                   const SCell *__restrict__ pcells,
+                                                   const SCell *__restrict__ ccells,
+                                                   const double *__restrict__ Fc,
+                                                   double *__restrict__ Fp) {
+  const SCell P = pcells[blockIdx.x];
+  const int np = P.nI + P.nB;
+  double *FP = Fp + P.F_off;
+  for (long long t = threadIdx.x; t < (long long)np * np; t += NT) FP[t] = 0.0;
+  __syncthreads();
+  for (int e = pchild[blockIdx.x]; e < pchild[blockIdx.x + 1]; ++e) {
+    const SExt x = ext[e];
+    const SCell C = ccells[x.child];
+    const int nc = C.nI + C.nB;
+    const double *FC = Fc + C.F_off;
+    const int2 *en = ent + x.ent_off;
+    const long long mm = (long long)x.m * x.m;
+    for (long long t = threadIdx.x; t < mm; t += NT) {
+      int a = (int)(t % x.m), b = (int)(t / x.m);
+      FP[en[a].y + (long long)en[b].y * np] += FC[en[a].x + (long long)en[b].x * nc];
+    }
+    __syncthreads();
+  }
+}
+
+// -------------------------------------------------------------- cell elimination
+
+__global__ void __launch_bounds__(NT) k_cell_eliminate(const SCell *__restrict__ cells,
+                                                       double *__restrict__ F,
+                                                       double *__restrict__ vals,
+                                                       int *__restrict__ err) {
+  extern __shared__ double sm[];  // col[n], row[nI]
+  const SCell c = cells[blockIdx.x];
+  const int nI = c.nI, nB = c.nB, nn = nI + nB;
+  double *A = F + c.F_off;
+  double *col = sm;
+  double *row = sm + nn;
+  __shared__ double piv;
+  // partial right-looking Cholesky over the first nI columns (lower triangle)
+  for (int k = 0; k < nI; ++k) {
+    if (threadIdx.x == 0) {
+      double d = A[k + (long long)k * nn];
+      if (!(d > 0.0)) {
+        atomicExch(err, 1);
+        d = 1.0;
+      }
+      d = sqrt(d);
+      A[k + (long long)k * nn] = d;
+      piv = d;
+    }
+    __syncthreads();
+    const double inv = 1.0 / piv;
+    for (int i = k + 1 + threadIdx.x; i < nn; i += NT) {
+      double v = A[i + (long long)k * nn] * inv;
+      A[i + (long long)k * nn] = v;
+      col[i] = v;
+    }
+    __syncthreads();
+    const int m = nn - k - 1;
+    const long long mm = (long long)m * m;
+    for (long long t = threadIdx.x; t < mm; t += NT) {
+      int i = k + 1 + (int)(t % m), j = k + 1 + (int)(t / m);
+      if (i >= j) A[i + (long long)j * nn] -= col[i] * col[j];
+    }
+    __syncthreads();
+  }
+  // G = L^{-1}, row by row: G[i][c] = (delta_ic - sum_{k=c}^{i-1} L[i][k] G[k][c]) / L[i][i]
+  double *G = vals + c.G_off;
+  for (int i = 0; i < nI; ++i) {
+    for (int k = threadIdx.x; k <= i; k += NT) row[k] = A[i + (long long)k * nn];
+    __syncthreads();
+    const double dinv = 1.0 / row[i];
+    for (int cc = threadIdx.x; cc <= i; cc += NT) {
+      double acc = (cc == i) ? 1.0 : 0.0;
+      for (int k = cc; k < i; ++k) acc -= row[k] * G[(long long)k * (k + 1) / 2 + cc];
+      G[(long long)i * (i + 1) / 2 + cc] = acc * dinv;
+    }
+    __syncthreads();
+  }
+  // V[b][cc] = sum_{i >= cc} W^T[b][i] G[i][cc], W^T = A[nI + b][i]
+  double *V = vals + c.V_off;
+  const long long nv = (long long)nB * nI;
+  for (long long t = threadIdx.x; t < nv; t += NT) {
+    int b = (int)(t % nB), cc = (int)(t / nB);
+    double acc = 0.0;
+    for (int i = cc; i < nI; ++i) acc += A[nI + b + (long long)i * nn] * G[(long long)i * (i + 1) / 2 + cc];
+    V[(long long)b * nI + cc] = acc;
+  }
+  // symmetrize the Schur complement block (upper <- lower)
+  const long long nbb = (long long)nB * nB;
+  for (long long t = threadIdx.x; t < nbb; t += NT) {
+    int p = (int)(t % nB), q = (int)(t / nB);
+    if (q > p) A[nI + p + (long long)(nI + q) * nn] = A[nI + q + (long long)(nI + p) * nn];
+  }
+}
+
+// ----------------------------------------------------------------- block Jacobi
+
+// In-CTA Cholesky of an n x n row-major SPD block (in place, lower) and its
+// inverse factor written to Li (row major, zero above the diagonal).
+__device__ void cta_chol_inv(double *D, double *Li, int n, int *err) {
+  __shared__ double pv;
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x == 0) {
+      double d = D[(long long)k * n + k];
+      if (!(d > 0.0)) {
+        atomicExch(err, 1);
+        d = 1.0;
+      }
+      pv = sqrt(d);
+      D[(long long)k * n + k] = pv;
+    }
+    __syncthreads();
+    const double inv = 1.0 / pv;
+    for (int i = k + 1 + threadIdx.x; i < n; i += NT) D[(long long)i * n + k] *= inv;
+    __syncthreads();
+    const int m = n - k - 1;
+    for (int t = threadIdx.x; t < m * m; t += NT) {
+      int i = k + 1 + t % m, j = k + 1 + t / m;
+      if (i >= j) D[(long long)i * n + j] -= D[(long long)i * n + k] * D[(long long)j * n + k];
+    }
+    __syncthreads();
+  }
+  // Li = L^{-1}: row by row as in the cell kernel
+  for (int i = 0; i < n; ++i) {
+    const double dinv = 1.0 / D[(long long)i * n + i];
+    for (int cc = threadIdx.x; cc < n; cc += NT) {
+      double acc = 0.0;
+      if (cc <= i) {
+        acc = (cc == i) ? 1.0 : 0.0;
+        for (int k = cc; k < i; ++k) acc -= D[(long long)i * n + k] * Li[(long long)k * n + cc];
+        acc *= dinv;
+      }
+      Li[(long long)i * n + cc] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(NT) k_group_diag(const SGroup *__restrict__ groups,
+                                                   const int2 *__restrict__ gcells,
+                                                   const SCell *__restrict__ cells,
+                                                   const double *__restrict__ F,
+                                                   double *__restrict__ Dscr,
+                                                   double *__restrict__ Linv, int *__restrict__ err) {
+  const SGroup g = groups[blockIdx.x];
+  const int n = g.n;
+  double *D = Dscr + g.D_off;
+  for (int t = threadIdx.x; t < n * n; t += NT) {
+    int a = t / n, b = t % n;
+    double acc = 0.0;
+    for (int q = 0; q < g.ncell; ++q) {
+      int2 cl = gcells[g.gc_off + q];
+      const SCell c = cells[cl.x];
+      const int nn = c.nI + c.nB;
+      acc += F[c.F_off + (c.nI + cl.y + a) + (long long)(c.nI + cl.y + b) * nn];
+    }
+    D[t] = acc;
+  }
+  __syncthreads();
+  cta_chol_inv(D, Linv + g.Linv_off, n, err);
+}
+
+__global__ void __launch_bounds__(NT) k_cell_scale(const SCell *__restrict__ cells,
+                                                   const int2 *__restrict__ bmap,
+                                                   const SGroup *__restrict__ groups,
+                                                   const int2 *__restrict__ gcells,
+                                                   const double *__restrict__ Linv,
+                                                   double *__restrict__ F, double *__restrict__ S) {
+  const SCell c = cells[blockIdx.x];
+  const int nI = c.nI, nB = c.nB, nn = nI + nB;
+  double *A = F + c.F_off;
+  double *Sc = S + c.S_off;
+  const int2 *bm = bmap + c.bmap_off;
+  const long long nbb = (long long)nB * nB;
+  // S = D F_BB (rows of every group scaled by its L^{-1})
+  for (long long t = threadIdx.x; t < nbb; t += NT) {
+    int p = (int)(t % nB), q = (int)(t / nB);
+    int2 gp = bm[p];
+    const SGroup g = groups[gp.x];
+    const int o = p - gp.y;
+    const double *Li = Linv + g.Linv_off + (long long)gp.y * g.n;
+    double acc = 0.0;
+    for (int b = 0; b <= gp.y; ++b) acc += Li[b] * A[nI + o + b + (long long)(nI + q) * nn];
+    Sc[p + (long long)q * nB] = acc;
+  }
+  __syncthreads();
+  // F_BB = S D^T, then the diagonal blocks become I (owner cell) or 0
+  for (long long t = threadIdx.x; t < nbb; t += NT) {
+    int p = (int)(t % nB), q = (int)(t / nB);
+    int2 gp = bm[p], gq = bm[q];
+    double v;
+    if (gp.x == gq.x) {
+      const SGroup g = groups[gp.x];
+      const bool owner = gcells[g.gc_off].x == (int)blockIdx.x;
+      v = (owner && gp.y == gq.y) ? 1.0 : 0.0;
+    } else {
+      const SGroup g = groups[gq.x];
+      const int o = q - gq.y;
+      const double *Li = Linv + g.Linv_off + (long long)gq.y * g.n;
+      double acc = 0.0;
+      for (int b = 0; b <= gq.y; ++b) acc += Sc[p + (long long)(o + b) * nB] * Li[b];
+      v = acc;
+    }
+    A[nI + p + (long long)(nI + q) * nn] = v;
+  }
+}
+
+__global__ void __launch_bounds__(NT) k_group_h_jacobi(const SGroup *__restrict__ groups,
+                                                       const int *__restrict__ list,
+                                                       const double *__restrict__ Linv,
+                                                       double *__restrict__ vals) {
+  const SGroup g = groups[list[blockIdx.x]];
+  const long long nn = (long long)g.n * g.n;
+  for (long long t = threadIdx.x; t < nn; t += NT) vals[g.H_off + t] = Linv[g.Linv_off + t];
+}
+
+// -------------------------------------------------------------- skeletonization
+
+__global__ void __launch_bounds__(NT) k_skel(const SSkel *__restrict__ sk, const SGroup *__restrict__ groups,
+                                             const int2 *__restrict__ gcells,
+                                             const SCell *__restrict__ cells,
+                                             const long long *__restrict__ rowptr,
+                                             const int2 *__restrict__ rowent,
+                                             const double *__restrict__ Linv, double *__restrict__ F,
+                                             double *__restrict__ ws_all, double *__restrict__ vals,
+                                             int *__restrict__ kout, int *__restrict__ perm_all,
+                                             double eps, int *__restrict__ err) {
+  extern __shared__ double smd[];  // nrm[n] | perm (ints) [n]
+  const SSkel S = sk[blockIdx.x];
+  const SGroup g = groups[S.g];
+  const int n = g.n, R = S.R;
+  double *nrm = smd;
+  int *perm = reinterpret_cast<int *>(smd + n);
+  __shared__ int s_k, s_stop, s_p;
+  __shared__ double s_r00, s_alpha, s_vn2;
+  double *M = ws_all + S.ws_off;              // R x n column major
+  double *T = M + (long long)R * n;            // k x nr row major
+  double *Sm = T + (long long)n * n;           // nr x nr row major (Cholesky in place)
+  double *Lsi = Sm + (long long)n * n;         // nr x nr row major
+  double *TSi = Lsi + (long long)n * n;        // k x nr row major
+  double *Kq = TSi + (long long)n * n;         // n x n row major
+  double *vh = Kq + (long long)n * n;          // Householder vector (R)
+
+  // (a) gather A~_{R,g}
+  for (long long t = threadIdx.x; t < (long long)R * n; t += NT) {
+    int r = (int)(t % R), j = (int)(t / R);
+    double acc = 0.0;
+    for (long long e = rowptr[S.row_off + r]; e < rowptr[S.row_off + r + 1]; ++e) {
+      int2 en = rowent[e];  // (slot in the group's cell list, B position of the row DOF)
+      int2 cl = gcells[g.gc_off + en.x];
+      const SCell c = cells[cl.x];
+      const int nn = c.nI + c.nB;
+      acc += F[c.F_off + (c.nI + en.y) + (long long)(c.nI + cl.y + j) * nn];
+    }
+    M[r + (long long)j * R] = acc;
+  }
+  for (int j = threadIdx.x; j < n; j += NT) perm[j] = j;
+  if (threadIdx.x == 0) {
+    s_k = 0;
+    s_stop = 0;
+    s_r00 = 0.0;
+  }
+  __syncthreads();
+
+  // (b) column-pivoted Householder QR, stopped at the first |R_tt| <= eps |R_00|
+  const int tmax = R < n ? R : n;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int t = 0; t < tmax; ++t) {
+    for (int j = t + warp; j < n; j += NT / 32) {
+      double a = 0.0;
+      for (int r = t + lane; r < R; r += 32) {
+        double v = M[r + (long long)j * R];
+        a += v * v;
+      }
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if (lane == 0) nrm[j] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int p = t;
+      double best = nrm[t];
+      for (int j = t + 1; j < n; ++j)
+        if (nrm[j] > best) {
+          best = nrm[j];
+          p = j;
+        }
+      double r = sqrt(best);
+      if (t == 0) s_r00 = r;
+      if (r == 0.0 || r <= eps * s_r00) {
+        s_stop = 1;
+      } else {
+        s_k = t + 1;
+        int tmp = perm[t];
+        perm[t] = perm[p];
+        perm[p] = tmp;
+        s_p = p;
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const int p = s_p;
+    if (p != t)
+      for (int r = threadIdx.x; r < R; r += NT) {
+        double a = M[r + (long long)t * R];
+        M[r + (long long)t * R] = M[r + (long long)p * R];
+        M[r + (long long)p * R] = a;
+      }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double x0 = M[t + (long long)t * R];
+      double r = sqrt(nrm[p]);
+      double alpha = x0 >= 0.0 ? -r : r;
+      double v0 = x0 - alpha;
+      s_vn2 = r * r - x0 * x0 + v0 * v0;
+      s_alpha = alpha;
+      vh[t] = v0;
+    }
+    for (int r = t + 1 + threadIdx.x; r < R; r += NT) vh[r] = M[r + (long long)t * R];
+    __syncthreads();
+    const double sc = s_vn2 > 0.0 ? 2.0 / s_vn2 : 0.0;
+    for (int j = t + 1 + warp; j < n; j += NT / 32) {
+      double w = 0.0;
+      for (int r = t + lane; r < R; r += 32) w += vh[r] * M[r + (long long)j * R];
+      for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+      w *= sc;
+      for (int r = t + lane; r < R; r += 32) M[r + (long long)j * R] -= w * vh[r];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) M[t + (long long)t * R] = s_alpha;
+    __syncthreads();
+  }
+  const int k = s_k, nr = n - k;
+
+  // (c) T = R11^{-1} R12 (back substitution, one column per thread)
+  for (int cc = threadIdx.x; cc < nr; cc += NT) {
+    for (int i = k - 1; i >= 0; --i) {
+      double acc = M[i + (long long)(k + cc) * R];
+      for (int j = i + 1; j < k; ++j) acc -= M[i + (long long)j * R] * T[(long long)j * nr + cc];
+      T[(long long)i * nr + cc] = acc / M[i + (long long)i * R];
+    }
+  }
+  __syncthreads();
+  // (d) S = I + T^T T, Ls = chol(S), Lsi = Ls^{-1}
+  for (int t = threadIdx.x; t < nr * nr; t += NT) {
+    int a = t / nr, b = t % nr;
+    double acc = (a == b) ? 1.0 : 0.0;
+    for (int i = 0; i < k; ++i) acc += T[(long long)i * nr + a] * T[(long long)i * nr + b];
+    Sm[t] = acc;
+  }
+  __syncthreads();
+  cta_chol_inv(Sm, Lsi, nr, err);
+  // (e) TSi = T S^{-1} = T Lsi^T Lsi
+  //     first Kq[0:nr, 0:nr] <- Lsi^T Lsi (= S^{-1}) as scratch in Kq
+  for (int t = threadIdx.x; t < nr * nr; t += NT) {
+    int a = t / nr, b = t % nr;
+    double acc = 0.0;
+    for (int i = (a > b ? a : b); i < nr; ++i) acc += Lsi[(long long)i * nr + a] * Lsi[(long long)i * nr + b];
+    Kq[t] = acc;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < k * nr; t += NT) {
+    int a = t / nr, b = t % nr;
+    double acc = 0.0;
+    for (int i = 0; i < nr; ++i) acc += T[(long long)a * nr + i] * Kq[(long long)i * nr + b];
+    TSi[t] = acc;
+  }
+  __syncthreads();
+  // (f) K^T in (redundant, skeleton) order:
+  //     [[Lsi, -Lsi T^T], [T S^{-1}, X]],  X = I - T S^{-1} T^T
+  for (int t = threadIdx.x; t < n * n; t += NT) {
+    int a = t / n, b = t % n;
+    double v;
+    if (a < nr && b < nr) {
+      v = Lsi[(long long)a * nr + b];
+    } else if (a < nr) {
+      int bb = b - nr;  // -Lsi T^T: sum_i Lsi[a][i] T[bb][i]
+      double acc = 0.0;
+      for (int i = 0; i <= a; ++i) acc += Lsi[(long long)a * nr + i] * T[(long long)bb * nr + i];
+      v = -acc;
+    } else if (b < nr) {
+      v = TSi[(long long)(a - nr) * nr + b];
+    } else {
+      int aa = a - nr, bb = b - nr;
+      double acc = (aa == bb) ? 1.0 : 0.0;
+      for (int i = 0; i < nr; ++i) acc -= TSi[(long long)aa * nr + i] * T[(long long)bb * nr + i];
+      v = acc;
+    }
+    Kq[t] = v;
+  }
+  __syncthreads();
+  // (g) H[q[a]][col] = sum_b Kq[a][b] Linv[q[b]][col]; q = (perm[k..n-1], perm[0..k-1])
+  const double *Li = Linv + g.Linv_off;
+  double *H = vals + g.H_off;
+  for (int t = threadIdx.x; t < n * n; t += NT) {
+    int a = t / n, col = t % n;
+    double acc = 0.0;
+    for (int b = 0; b < n; ++b) {
+      int qb = b < nr ? perm[k + b] : perm[b - nr];
+      acc += Kq[(long long)a * n + b] * Li[(long long)qb * n + col];
+    }
+    int qa = a < nr ? perm[k + a] : perm[a - nr];
+    H[(long long)qa * n + col] = acc;
+  }
+  // (h) X into the owner cell's diagonal block at the skeleton positions
+  {
+    int2 cl = gcells[g.gc_off];
+    const SCell c = cells[cl.x];
+    const int nn = c.nI + c.nB;
+    for (int t = threadIdx.x; t < k * k; t += NT) {
+      int a = t / k, b = t % k;
+      F[c.F_off + (c.nI + cl.y + perm[a]) + (long long)(c.nI + cl.y + perm[b]) * nn] =
+          Kq[(long long)(nr + a) * n + (nr + b)];
+    }
+  }
+  if (threadIdx.x == 0) kout[blockIdx.x] = k;
+  for (int j = threadIdx.x; j < n; j += NT) perm_all[S.perm_off + j] = perm[j];
+}
+
+// ------------------------------------------------------------------ host planning
+
+struct Plan {
+  int l = 0, s = 0, nc = 0, D = 0;
+  int ncells = 0;
+  std::vector<std::vector<int>> cI;      // interior DOFs, ascending
+  std::vector<std::vector<int>> cG;      // boundary groups, ascending id
+  std::vector<int> g_key, g_codim;
+  std::vector<std::vector<int>> g_dofs;  // ascending
+  std::vector<std::vector<int>> g_cells; // adjacent cells, ascending id
+  std::vector<std::vector<int>> cB;      // boundary DOFs in local order
+  std::vector<std::vector<int>> g_boff;  // offset of g inside each adjacent cell's B
+};
+
+void coords_of(long long d, int n, int dim, int c[3]) {
+  const long long S = n - 1;
+  c[0] = (int)(d % S) + 1;
+  c[1] = (int)((d / S) % S) + 1;
+  c[2] = dim == 3 ? (int)(d / (S * S)) + 1 : 0;
+}
+
+Plan make_plan(const std::vector<int> &active, int n, int dim, int leaf, int l) {
+  Plan P;
+  P.l = l;
+  P.s = leaf << l;
+  P.nc = n / P.s;
+  P.D = 2 * P.nc + 1;
+  const int D = P.D, nc = P.nc, s = P.s;
+  const long long nkeys = dim == 3 ? (long long)D * D * D : (long long)D * D;
+  P.ncells = dim == 3 ? nc * nc * nc : nc * nc;
+  P.cI.assign(P.ncells, {});
+  std::vector<int> gid_of_key(nkeys, -1);
+  std::vector<int> key_of_dof(active.size());
+  // pass 1: which keys hold group DOFs
+  for (size_t t = 0; t < active.size(); ++t) {
+    int c[3];
+    coords_of(active[t], n, dim, c);
+    int code[3] = {0, 0, 0};
+    int codim = 0;
+    for (int ax = 0; ax < dim; ++ax) {
+      code[ax] = 2 * (c[ax] / s) + (c[ax] % s != 0);
+      if (code[ax] % 2 == 0) ++codim;
+    }
+    long long key = code[0] + (long long)D * code[1] + (long long)D * D * code[2];
+    if (codim == 0) {
+      int cid = (code[0] - 1) / 2 + nc * ((code[1] - 1) / 2) + (dim == 3 ? nc * nc * ((code[2] - 1) / 2) : 0);
+      P.cI[cid].push_back(active[t]);
+      key_of_dof[t] = -1;
+    } else {
+      gid_of_key[key] = 0;
+      key_of_dof[t] = (int)key;
+    }
+  }
+  // number groups in ascending key order
+  int ng = 0;
+  for (long long key = 0; key < nkeys; ++key)
+    if (gid_of_key[key] >= 0) {
+      gid_of_key[key] = ng++;
+      P.g_key.push_back((int)key);
+    }
+  P.g_dofs.assign(ng, {});
+  P.g_codim.assign(ng, 0);
+  P.g_cells.assign(ng, {});
+  for (size_t t = 0; t < active.size(); ++t)
+    if (key_of_dof[t] >= 0) P.g_dofs[gid_of_key[key_of_dof[t]]].push_back(active[t]);
+  P.cG.assign(P.ncells, {});
+  for (int g = 0; g < ng; ++g) {
+    int key = P.g_key[g];
+    int code[3] = {key % D, (key / D) % D, dim == 3 ? key / (D * D) : 1};
+    int lo[3], hi[3], codim = 0;
+    for (int ax = 0; ax < 3; ++ax) {
+      if (ax >= dim) {
+        lo[ax] = hi[ax] = 0;
+        continue;
+      }
+      if (code[ax] % 2 == 0) {
+        ++codim;
+        lo[ax] = std::max(0, code[ax] / 2 - 1);
+        hi[ax] = std::min(nc - 1, code[ax] / 2);
+      } else {
+        lo[ax] = hi[ax] = (code[ax] - 1) / 2;
+      }
+    }
+    P.g_codim[g] = codim;
+    for (int z = lo[2]; z <= hi[2]; ++z)
+      for (int y = lo[1]; y <= hi[1]; ++y)
+        for (int x = lo[0]; x <= hi[0]; ++x) {
+          int cid = x + nc * y + nc * nc * z;
+          P.g_cells[g].push_back(cid);
+          P.cG[cid].push_back(g);
+        }
+  }
+  P.cB.assign(P.ncells, {});
+  P.g_boff.assign(ng, {});
+  std::vector<int> off_in_cell(ng, 0);
+  for (int c = 0; c < P.ncells; ++c) {
+    int o = 0;
+    for (int g : P.cG[c]) {
+      for (int d : P.g_dofs[g]) P.cB[c].push_back(d);
+      o += (int)P.g_dofs[g].size();
+    }
+  }
+  for (int g = 0; g < ng; ++g)
+    for (int c : P.g_cells[g]) {
+      int o = 0;
+      for (int g2 : P.cG[c]) {
+        if (g2 == g) break;
+        o += (int)P.g_dofs[g2].size();
+      }
+      P.g_boff[g].push_back(o);
+    }
+  return P;
+}
+
+// scoped device buffer list
+struct Scratch {
+  std::vector<void *> ptrs;
+  ~Scratch() {
+    for (void *p : ptrs) cudaFree(p);
+  }
+  template <typename T>
+  int alloc(T **p, size_t count) {
+    *p = nullptr;
+    size_t bytes = std::max<size_t>(16, count * sizeof(T));
+    if (cudaMalloc((void **)p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      set_last_error("setup: cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+      return HIF_ENOMEM;
+    }
+    ptrs.push_back(*p);
+    return HIF_OK;
+  }
+  template <typename T>
+  int upload(T **p, const std::vector<T> &v, cudaStream_t s) {
+    HIF_TRY(alloc(p, v.size()));
+    if (!v.empty())
+      HIF_CUDA_TRY(cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    return HIF_OK;
+  }
+  void release(void *p) {
+    for (auto &q : ptrs)
+      if (q == p) {
+        cudaFree(q);
+        q = nullptr;
+      }
+  }
+};
+
+int check_err(int *derr, cudaStream_t s, const char *what) {
+  int e = 0;
+  HIF_CUDA_TRY(cudaMemcpyAsync(&e, derr, sizeof(int), cudaMemcpyDeviceToHost, s));
+  HIF_CUDA_TRY(cudaStreamSynchronize(s));
+  if (e) {
+    set_last_error(std::string("setup: non-positive pivot in ") + what);
+    return HIF_ENOTSPD;
+  }
+  return HIF_OK;
+}
+
+int set_smem(const void *fn, size_t bytes) {
+  if (bytes > 48 * 1024)
+    HIF_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  return HIF_OK;
+}
+
+}  // namespace
+
+int gpu_setup(Handle *h, const double *a_nodes, cudaStream_t s) {
+  (void)a_nodes;  // the stencil coefficients were assembled from it in stencil_init
+  const int dim = h->grid.dim, n = h->grid.n, leaf = h->grid.leaf, L = h->L;
+  const long long N = h->N;
+  const double eps = h->opt.eps;
+  Scratch keep;  // lives across levels (previous level's frontal matrices)
+  int *derr = nullptr;
+  HIF_TRY(keep.alloc(&derr, 1));
+  HIF_CUDA_TRY(cudaMemsetAsync(derr, 0, sizeof(int), s));
+
+  std::vector<int> active(N);
+  for (long long d = 0; d < N; ++d) active[d] = (int)d;
+  std::vector<char> alive(N, 1);
+
+  h->lv_host.assign(L, LevelHost{});
+  h->idx_host.clear();
+  std::vector<double *> level_vals(L + 1, nullptr);
+  std::vector<long long> level_nvals(L + 1, 0);
+  Plan prev;
+  double *F_prev = nullptr;
+  SCell *dcells_prev = nullptr;
+  std::vector<SCell> cells_prev;
+
+  for (int l = 0; l <= L; ++l) {
+    Scratch lvl;
+    Plan P = make_plan(active, n, dim, leaf, l);
+    const int ncells = P.ncells;
+    const int ng = (int)P.g_dofs.size();
+    if (l == L && (ncells != 1 || ng != 0)) {
+      set_last_error("setup: root level is not a single cell");
+      return HIF_EINVAL;
+    }
+    // ---- cells: offsets
+    std::vector<SCell> cells(ncells);
+    std::vector<int> cdofs;
+    std::vector<int2> bmap;
+    long long foff = 0, voff = 0, soff = 0;
+    for (int c = 0; c < ncells; ++c) {
+      SCell &C = cells[c];
+      C.nI = (int)P.cI[c].size();
+      C.nB = (int)P.cB[c].size();
+      const long long nn = C.nI + C.nB;
+      C.F_off = foff;
+      foff += nn * nn;
+      C.G_off = voff;
+      voff += (long long)C.nI * (C.nI + 1) / 2;
+      C.V_off = voff;
+      voff += (long long)C.nB * C.nI;
+      C.S_off = soff;
+      soff += (long long)C.nB * C.nB;
+      C.dofs_off = (long long)cdofs.size();
+      C.bmap_off = (long long)bmap.size();
+      cdofs.insert(cdofs.end(), P.cI[c].begin(), P.cI[c].end());
+      cdofs.insert(cdofs.end(), P.cB[c].begin(), P.cB[c].end());
+      for (int g : P.cG[c])
+        for (int a = 0; a < (int)P.g_dofs[g].size(); ++a) bmap.push_back(make_int2(g, a));
+    }
+    // ---- groups: offsets
+    std::vector<SGroup> groups(ng);
+    std::vector<int2> gcells;
+    long long loff = 0, hoff = voff;
+    for (int g = 0; g < ng; ++g) {
+      SGroup &G = groups[g];
+      G.n = (int)P.g_dofs[g].size();
+      G.ncell = (int)P.g_cells[g].size();
+      G.gc_off = (long long)gcells.size();
+      for (size_t q = 0; q < P.g_cells[g].size(); ++q)
+        gcells.push_back(make_int2(P.g_cells[g][q], P.g_boff[g][q]));
+      G.Linv_off = loff;
+      G.D_off = loff;
+      loff += (long long)G.n * G.n;
+      G.H_off = hoff;
+      hoff += (long long)G.n * G.n;
+    }
+    level_nvals[l] = hoff;
+    HIF_TRY(keep.alloc(&level_vals[l], hoff));
+    double *vals = level_vals[l];
+
+    double *F = nullptr;
+    SCell *dcells = nullptr;
+    int *dcdofs = nullptr;
+    HIF_TRY(keep.alloc(&F, foff));
+    HIF_TRY(keep.upload(&dcells, cells, s));
+    HIF_TRY(lvl.upload(&dcdofs, cdofs, s));
+
+    // ---- assemble
+    if (l == 0) {
+      const int box = P.s + 1;
+      size_t sm = sizeof(int) * (dim == 3 ? (size_t)box * box * box : (size_t)box * box);
+      HIF_TRY(set_smem((const void *)k_assemble_leaf, sm));
+      k_assemble_leaf<<<ncells, NT, sm, s>>>(dcells, dcdofs, h->diag, h->wx, h->wy, h->wz, dim, n,
+                                             P.s, P.nc, F);
+      note_launch();
+      HIF_CUDA_TRY(cudaGetLastError());
+    } else {
+      // extend-add of the children's surviving boundary entries
+      std::vector<int> pchild(ncells + 1, 0);
+      std::vector<SExt> ext;
+      std::vector<int2> ent;
+      std::vector<int> lpos(N, -1);
+      const int pnc = prev.nc;
+      std::vector<std::vector<int>> kids(ncells);
+      for (int c = 0; c < prev.ncells; ++c) {
+        int x = c % pnc, y = (c / pnc) % pnc, z = dim == 3 ? c / (pnc * pnc) : 0;
+        int pid = x / 2 + P.nc * (y / 2) + (dim == 3 ? P.nc * P.nc * (z / 2) : 0);
+        kids[pid].push_back(c);
+      }
+      for (int pc = 0; pc < ncells; ++pc) {
+        pchild[pc] = (int)ext.size();
+        int pos = 0;
+        for (int d : P.cI[pc]) lpos[d] = pos++;
+        for (int d : P.cB[pc]) lpos[d] = pos++;
+        for (int c : kids[pc]) {
+          SExt x;
+          x.child = c;
+          x.parent = pc;
+          x.ent_off = (long long)ent.size();
+          const int nIc = cells_prev[c].nI;
+          int m = 0;
+          for (int p = 0; p < (int)prev.cB[c].size(); ++p) {
+            int d = prev.cB[c][p];
+            if (!alive[d]) continue;
+            if (lpos[d] < 0) {
+              set_last_error("setup: surviving DOF missing from its parent cell");
+              return HIF_EINVAL;
+            }
+            ent.push_back(make_int2(nIc + p, lpos[d]));
+            ++m;
+          }
+          x.m = m;
+          ext.push_back(x);
+        }
+        for (int d : P.cI[pc]) lpos[d] = -1;
+        for (int d : P.cB[pc]) lpos[d] = -1;
+      }
+      pchild[ncells] = (int)ext.size();
+      int *dpchild = nullptr;
+      SExt *dext = nullptr;
+      int2 *dent = nullptr;
+      HIF_TRY(lvl.upload(&dpchild, pchild, s));
+      HIF_TRY(lvl.upload(&dext, ext, s));
+      HIF_TRY(lvl.upload(&dent, ent, s));
+      k_extend_add<<<ncells, NT, 0, s>>>(dpchild, dext, dent, dcells, dcells_prev, F_prev, F);
+      note_launch();
+      HIF_CUDA_TRY(cudaGetLastError());
+      HIF_CUDA_TRY(cudaStreamSynchronize(s));
+      keep.release(F_prev);
+      keep.release(dcells_prev);
+    }
+
+    // ---- cell elimination
+    {
+      int max_nn = 1, max_nI = 1;
+      for (auto &C : cells) {
+        max_nn = std::max(max_nn, C.nI + C.nB);
+        max_nI = std::max(max_nI, C.nI);
+      }
+      size_t sm = sizeof(double) * (size_t)(max_nn + max_nI);
+      if (sm > 200 * 1024) {
+        set_last_error("setup: frontal matrix too large for the shared-memory column buffer");
+        return HIF_EINVAL;
+      }
+      HIF_TRY(set_smem((const void *)k_cell_eliminate, sm));
+      k_cell_eliminate<<<ncells, NT, sm, s>>>(dcells, F, vals, derr);
+      note_launch();
+      HIF_CUDA_TRY(cudaGetLastError());
+      HIF_TRY(check_err(derr, s, "cell elimination"));
+    }
+
+    // ---- apply descriptors of the cells (index pool) and the root
+    if (l == L) {
+      const SCell &C = cells[0];
+      h->root_n = C.nI;
+      h->root_idx_off = (long long)h->idx_host.size();
+      h->idx_host.insert(h->idx_host.end(), P.cI[0].begin(), P.cI[0].end());
+      h->root_G_off = C.G_off;  // relative to the root pool; shifted below
+      break;
+    }
+    LevelHost &LH = h->lv_host[l];
+    long long slots = 0;
+    for (int c = 0; c < ncells; ++c) {
+      CellDesc d{};
+      d.nI = cells[c].nI;
+      d.nB = cells[c].nB;
+      d.I_off = (long long)h->idx_host.size();
+      h->idx_host.insert(h->idx_host.end(), P.cI[c].begin(), P.cI[c].end());
+      d.B_off = (long long)h->idx_host.size();
+      h->idx_host.insert(h->idx_host.end(), P.cB[c].begin(), P.cB[c].end());
+      d.G_off = cells[c].G_off;
+      d.V_off = cells[c].V_off;
+      d.C_off = slots;
+      slots += d.nB;
+      if (d.nI > 0 || d.nB > 0) LH.cells.push_back(d);
+    }
+    LH.contrib_slots = slots;
+    for (int g = 0; g < ng; ++g) {
+      GroupDesc d{};
+      d.n = groups[g].n;
+      d.idx_off = (long long)h->idx_host.size();
+      h->idx_host.insert(h->idx_host.end(), P.g_dofs[g].begin(), P.g_dofs[g].end());
+      d.H_off = groups[g].H_off;
+      LH.groups.push_back(d);
+    }
+
+    // ---- block Jacobi
+    SGroup *dgroups = nullptr;
+    int2 *dgcells = nullptr, *dbmap = nullptr;
+    double *Linv = nullptr, *Dscr = nullptr, *Sscr = nullptr;
+    HIF_TRY(lvl.upload(&dgroups, groups, s));
+    HIF_TRY(lvl.upload(&dgcells, gcells, s));
+    HIF_TRY(lvl.upload(&dbmap, bmap, s));
+    HIF_TRY(lvl.alloc(&Linv, loff));
+    HIF_TRY(lvl.alloc(&Dscr, loff));
+    HIF_TRY(lvl.alloc(&Sscr, soff));
+    if (ng > 0) {
+      k_group_diag<<<ng, NT, 0, s>>>(dgroups, dgcells, dcells, F, Dscr, Linv, derr);
+      note_launch();
+      HIF_CUDA_TRY(cudaGetLastError());
+      HIF_TRY(check_err(derr, s, "block Jacobi"));
+      k_cell_scale<<<ncells, NT, 0, s>>>(dcells, dbmap, dgroups, dgcells, Linv, F, Sscr);
+      note_launch();
+      HIF_CUDA_TRY(cudaGetLastError());
+    }
+
+    // ---- skeletonization sub-steps
+    std::vector<char> skeletonized(ng, 0);
+    std::vector<int> codims = {1};
+    if (dim == 3 && h->opt.skel_edges_3d) codims.push_back(2);
+    for (int cd : codims) {
+      std::vector<SSkel> sk;
+      std::vector<long long> rowptr;
+      std::vector<int2> rowent;
+      long long wsoff = 0, poff = 0;
+      int max_n = 1;
+      std::vector<int> rowid(N, -1);
+      for (int g = 0; g < ng; ++g) {
+        if (P.g_codim[g] != cd) continue;
+        SSkel x{};
+        x.g = g;
+        x.row_off = (long long)rowptr.size();
+        // rows: boundary DOFs of the adjacent cells except g's own and those
+        // eliminated earlier in this level (redundant DOFs of a previous sub-step)
+        std::vector<int> rows;
+        std::vector<std::vector<int2>> rent;
+        for (size_t q = 0; q < P.g_cells[g].size(); ++q) {
+          int c = P.g_cells[g][q];
+          int p = 0;
+          for (int g2 : P.cG[c]) {
+            for (int a = 0; a < (int)P.g_dofs[g2].size(); ++a, ++p) {
+              if (g2 == g) continue;
+              int d = P.g_dofs[g2][a];
+              if (!alive[d]) continue;
+              if (rowid[d] < 0) {
+                rowid[d] = (int)rows.size();
+                rows.push_back(d);
+                rent.push_back({});
+              }
+              rent[rowid[d]].push_back(make_int2((int)q, p));
+            }
+          }
+        }
+        for (size_t r = 0; r < rows.size(); ++r) {
+          rowptr.push_back((long long)rowent.size());
+          for (auto e : rent[r]) rowent.push_back(e);
+          rowid[rows[r]] = -1;
+        }
+        rowptr.push_back((long long)rowent.size());
+        x.R = (int)rows.size();
+        x.ws_off = wsoff;
+        const long long nG = groups[g].n;
+        wsoff += (long long)x.R * nG + 5 * nG * nG + std::max<long long>(x.R, 1);
+        x.perm_off = poff;
+        poff += nG;
+        max_n = std::max(max_n, (int)nG);
+        sk.push_back(x);
+      }
+      if (sk.empty()) continue;
+      SSkel *dsk = nullptr;
+      long long *drowptr = nullptr;
+      int2 *drowent = nullptr;
+      double *ws = nullptr;
+      int *dk = nullptr, *dperm = nullptr;
+      Scratch sub;
+      HIF_TRY(sub.upload(&dsk, sk, s));
+      HIF_TRY(sub.upload(&drowptr, rowptr, s));
+      HIF_TRY(sub.upload(&drowent, rowent, s));
+      HIF_TRY(sub.alloc(&ws, wsoff));
+      HIF_TRY(sub.alloc(&dk, sk.size()));
+      HIF_TRY(sub.alloc(&dperm, poff));
+      size_t sm = (size_t)max_n * (sizeof(double) + sizeof(int)) + 16;
+      HIF_TRY(set_smem((const void *)k_skel, sm));
+      k_skel<<<(int)sk.size(), NT, sm, s>>>(dsk, dgroups, dgcells, dcells, drowptr, drowent, Linv, F,
+                                            ws, vals, dk, dperm, eps, derr);
+      note_launch();
+      HIF_CUDA_TRY(cudaGetLastError());
+      HIF_TRY(check_err(derr, s, "skeletonization"));
+      std::vector<int> kh(sk.size()), ph(poff);
+      HIF_CUDA_TRY(cudaMemcpyAsync(kh.data(), dk, kh.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
+      HIF_CUDA_TRY(cudaMemcpyAsync(ph.data(), dperm, ph.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
+      HIF_CUDA_TRY(cudaStreamSynchronize(s));
+      for (size_t t = 0; t < sk.size(); ++t) {
+        const int g = sk[t].g;
+        skeletonized[g] = 1;
+        const int nG = groups[g].n;
+        for (int a = kh[t]; a < nG; ++a) alive[P.g_dofs[g][ph[sk[t].perm_off + a]]] = 0;
+      }
+    }
+    // groups that were only rescaled: H = L_g^{-1}
+    {
+      std::vector<int> jl;
+      for (int g = 0; g < ng; ++g)
+        if (!skeletonized[g]) jl.push_back(g);
+      if (!jl.empty()) {
+        int *djl = nullptr;
+        HIF_TRY(lvl.upload(&djl, jl, s));
+        k_group_h_jacobi<<<(int)jl.size(), NT, 0, s>>>(dgroups, djl, Linv, vals);
+        note_launch();
+        HIF_CUDA_TRY(cudaGetLastError());
+      }
+    }
+    HIF_CUDA_TRY(cudaStreamSynchronize(s));
+    // cell interiors are eliminated
+    for (int c = 0; c < ncells; ++c)
+      for (int d : P.cI[c]) alive[d] = 0;
+    std::vector<int> next;
+    next.reserve(active.size());
+    for (int d : active)
+      if (alive[d]) next.push_back(d);
+    active.swap(next);
+    prev = std::move(P);
+    F_prev = F;
+    dcells_prev = dcells;
+    cells_prev = cells;
+  }
+  keep.release(F_prev);
+
+  // ---- concatenate the level value pools and shift the offsets
+  long long total = 0;
+  std::vector<long long> base(L + 1, 0);
+  for (int l = 0; l <= L; ++l) {
+    base[l] = total;
+    total += level_nvals[l];
+  }
+  HIF_TRY(dev_alloc(h, (void **)&h->f64.vals, std::max<long long>(total, 1) * sizeof(double)));
+  for (int l = 0; l <= L; ++l)
+    if (level_nvals[l])
+      HIF_CUDA_TRY(cudaMemcpyAsync(h->f64.vals + base[l], level_vals[l], level_nvals[l] * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, s));
+  h->nvals = total;
+  for (int l = 0; l < L; ++l) {
+    for (auto &c : h->lv_host[l].cells) {
+      c.G_off += base[l];
+      c.V_off += base[l];
+    }
+    for (auto &g : h->lv_host[l].groups) g.H_off += base[l];
+  }
+  h->root_G_off += base[L];
+  h->cptr_host.clear();
+  h->cslot_host.clear();
+  for (int l = 0; l < L; ++l) HIF_TRY(build_contrib_map(h, h->lv_host[l]));
+  HIF_TRY(dev_alloc(h, (void **)&h->idx, h->idx_host.size() * sizeof(int)));
+  HIF_TRY(dev_alloc(h, (void **)&h->cptr, h->cptr_host.size() * sizeof(long long)));
+  HIF_TRY(dev_alloc(h, (void **)&h->cslot, std::max<size_t>(1, h->cslot_host.size()) * sizeof(long long)));
+  HIF_CUDA_TRY(cudaMemcpyAsync(h->idx, h->idx_host.data(), h->idx_host.size() * sizeof(int),
+                               cudaMemcpyHostToDevice, s));
+  HIF_CUDA_TRY(cudaMemcpyAsync(h->cptr, h->cptr_host.data(), h->cptr_host.size() * sizeof(long long),
+                               cudaMemcpyHostToDevice, s));
+  if (!h->cslot_host.empty())
+    HIF_CUDA_TRY(cudaMemcpyAsync(h->cslot, h->cslot_host.data(), h->cslot_host.size() * sizeof(long long),
+                                 cudaMemcpyHostToDevice, s));
+  HIF_CUDA_TRY(cudaStreamSynchronize(s));
+  return HIF_OK;
+}
+
 }  // namespace hifcn

@@ -77,6 +77,7 @@ int stencil_init(Handle *h, const double *a_nodes, cudaStream_t s) {
   int nb = (int)((N + 255) / 256);
   k_stencil_init<<<nb, 256, 0, s>>>(a_nodes, h->diag, h->wx, h->wy, h->wz, h->grid.dim,
                                     h->grid.n, N, c);
+  note_launch();
   HIF_CUDA_TRY(cudaGetLastError());
   return HIF_OK;
 }
@@ -84,6 +85,7 @@ int stencil_init(Handle *h, const double *a_nodes, cudaStream_t s) {
 int stencil_matvec(Handle *h, const double *x, double *y, cudaStream_t s) {
   k_matvec<<<h->nblocks_vec, 256, 0, s>>>(x, y, h->diag, h->wx, h->wy, h->wz, h->grid.dim,
                                           h->grid.n, h->N);
+  note_launch();
   HIF_CUDA_TRY(cudaGetLastError());
   return HIF_OK;
 }
@@ -93,6 +95,7 @@ int cn_rhs(Handle *h, const double *u, const double *r, double *g, cudaStream_t 
   k_cn_rhs<<<h->nblocks_vec, 256, 0, s>>>(u, r, g, h->diag, h->wx, h->wy, h->wz, h->grid.dim,
                                           h->grid.n, h->N, h->dt, h->react_kind, h->react_k1,
                                           inv_k2);
+  note_launch();
   HIF_CUDA_TRY(cudaGetLastError());
   return HIF_OK;
 }

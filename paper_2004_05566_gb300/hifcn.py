@@ -26,7 +26,8 @@ HIF_FP64, HIF_FP32 = 0, 1
 
 EXPORTED = ("hif_default_options", "hif_setup", "hif_import_factor", "hif_export_factor",
             "hif_apply", "hif_matvec", "pcg_solve", "cn_step", "hif_set_reaction", "hif_query",
-            "hif_destroy", "hif_strerror", "hif_last_error")
+            "hif_destroy", "hif_strerror", "hif_last_error", "hif_stats_enable", "hif_stats_read",
+            "hif_launch_count")
 
 
 class HifGrid(ctypes.Structure):
@@ -42,6 +43,11 @@ class HifInfo(ctypes.Structure):
     _fields_ = [("N", c_int64), ("dim", c_int), ("n", c_int), ("leaf", c_int), ("levels", c_int),
                 ("root_size", c_int), ("factor_entries", c_int64), ("apply_bytes", c_int64),
                 ("device_bytes", c_int64), ("precision", c_int), ("setup_seconds", c_double)]
+
+
+class HifKernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", c_int64), ("ms", c_double),
+                ("bytes", c_double)]
 
 
 class HifError(RuntimeError):
@@ -78,8 +84,13 @@ def lib():
     L.hif_strerror.restype = ctypes.c_char_p
     L.hif_last_error.argtypes = []
     L.hif_last_error.restype = ctypes.c_char_p
+    L.hif_stats_enable.argtypes = [c_void_p, c_int]
+    L.hif_stats_read.argtypes = [c_void_p, POINTER(HifKernelStat), c_int, POINTER(c_int)]
+    L.hif_launch_count.argtypes = []
+    L.hif_launch_count.restype = c_int64
     for name in ("hif_setup", "hif_import_factor", "hif_export_factor", "hif_apply", "hif_matvec",
-                 "pcg_solve", "cn_step", "hif_set_reaction", "hif_query", "hif_destroy"):
+                 "pcg_solve", "cn_step", "hif_set_reaction", "hif_query", "hif_destroy",
+                 "hif_stats_enable", "hif_stats_read"):
         getattr(L, name).restype = c_int
     _lib = L
     return L
@@ -236,3 +247,24 @@ def hif_query(h: Handle) -> dict:
 
 def hif_destroy(h: Handle):
     h.close()
+
+
+def hif_stats_enable(h: Handle, on: bool = True):
+    """Bracket every apply-path kernel launch with CUDA events (measurement)."""
+    _check("hif_stats_enable", lib().hif_stats_enable(h.ptr, 1 if on else 0))
+
+
+def hif_stats_read(h: Handle) -> list:
+    """Per-kernel launches, device ms and algorithmic bytes since the last read."""
+    cnt = c_int(0)
+    _check("hif_stats_read", lib().hif_stats_read(h.ptr, None, 0, byref(cnt)))
+    n = max(cnt.value, 1)
+    arr = (HifKernelStat * n)()
+    _check("hif_stats_read", lib().hif_stats_read(h.ptr, arr, n, byref(cnt)))
+    return [dict(name=a.name.decode(), launches=a.launches, ms=a.ms, bytes=a.bytes)
+            for a in arr[: cnt.value]]
+
+
+def hif_launch_count() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(lib().hif_launch_count())
