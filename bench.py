@@ -1,0 +1,489 @@
+#!/usr/bin/env python
+"""Benchmark: Crank-Nicolson steps/s of HIF-preconditioned CG on one GB300.
+
+Workload (the configuration the headline metric is quoted on): 2D Fisher-KPP
+u_t = div(a grad u) + u(1-u) on (0,1)^2, 1023^2 interior grid (N = 1,046,529),
+a = exp(Gaussian random field, correlation length 0.05) with contrast 1e4,
+zero Dirichlet data, dt = 1.0, HIF leaf 16x16 (L = 6), eps = 1e-6, PCG to
+relative residual 1e-10, u0 = Gaussian bump; synthetic, seeded.
+
+One "step" is one full CN step: right-hand side (stencil + explicit reaction)
+and a PCG solve with the HIF inverse applied every iteration.  The headline
+path keeps the factor in FP32 (apply in FP32) with FP64 CG; the plain FP64
+path is timed beside it.  The factorization (hif_setup) runs once before the
+timed region (its time is reported as t_f).  Inputs are resident in HBM when
+the timed region starts; the factor streamed every apply (~1 GB) is larger than
+the 129 MB L2, so no explicit flush is needed.
+
+Launch: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 (torchrun) every rank runs an independent replica (no collective on
+the data path); value = steps of all ranks / max elapsed over ranks.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "CN steps/s at rel-res 1e-10, mixed-prec batched vs FP64 HIF-PCG; p50/p99 latency"
+WORKLOAD = ("fisher2d_1023: 2D Fisher-KPP r=u(1-u), 1023^2 interior (N=1046529), "
+            "a=exp(GRF corr 0.05) contrast 1e4, dt=1.0, leaf 16 (L=6), eps=1e-6, PCG rel-res 1e-10")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--eps", type=float, default=1e-6)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--n", type=int, default=1024,
+                   help="grid intervals per axis (same recipe); 1024 is the benchmark workload, "
+                        "smaller values are for profiling captures only")
+    p.add_argument("--cpu-sample", type=int, default=0, help=argparse.SUPPRESS)
+    p.add_argument("--cpu-sample-steps", type=int, default=0, help=argparse.SUPPRESS)
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------- CPU oracle leg
+
+def oracle_sample(n: int, steps: int, warmup: int, eps: float) -> dict:
+    """Time the oracle (as it stands) on a smaller instance of the same recipe.
+
+    Runs in its own process with BLAS limited to one thread; the setup is not
+    timed.  Returns steps/s measured on the sample and scaled by N to 1023^2.
+    """
+    import numpy as np
+    import workloads as W
+    from oracle import grid, hif, pcg
+
+    m = 16
+    L = int(round(math.log2(n // m)))
+    rng = np.random.default_rng(1)
+    a = W.lognormal_coefficient(W.grf(rng, n, 2, 0.05), 1e4)
+    u = W.gaussian_bump_u0(n, 2)
+    A = grid.assemble_A(a, 1.0)
+    t0 = time.perf_counter()
+    F = hif.factor(A, n, 2, m, eps)
+    t_f = time.perf_counter() - t0
+    del L
+    iters = []
+
+    def step(u):
+        r = grid.reaction(u, 1, 1.0, 1.0)
+        g = grid.cn_rhs(a, u, 1.0, r)
+        x, it, _, _ = pcg.pcg(A, g.ravel(), lambda v: hif.apply_inverse(F, v), tol=1e-10)
+        iters.append(it)
+        return x.reshape(u.shape)
+
+    for _ in range(warmup):
+        u = step(u)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        u = step(u)
+    dt = time.perf_counter() - t0
+    N_s = (n - 1) ** 2
+    N_full = 1023 ** 2
+    sps = steps / dt
+    return {"steps_per_s_sample": sps, "steps_per_s_scaled": sps * N_s / N_full, "seconds": dt,
+            "steps": steps, "n": n, "N_sample": N_s, "t_f": t_f,
+            "iters_per_step": sum(iters[-steps:]) / steps}
+
+
+def run_oracle_subprocess(n: int, steps: int, warmup: int, eps: float) -> dict:
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = "1"
+    env.pop("RANK", None)
+    env.pop("WORLD_SIZE", None)
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample", str(n),
+           "--cpu-sample-steps", str(steps), "--warmup", str(warmup), "--eps", str(eps)]
+    out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+# ------------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------------- helpers
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            with open(p) as f:
+                return json.load(f)
+        except (OSError, ValueError):
+            pass
+    return {}
+
+
+def _find_peak(d: dict, keys) -> float | None:
+    for k in keys:
+        if k in d and isinstance(d[k], (int, float)):
+            return float(d[k])
+    for v in d.values():
+        if isinstance(v, dict):
+            r = _find_peak(v, keys)
+            if r is not None:
+                return r
+    return None
+
+
+def kernel_traffic(name: str) -> float | None:
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current source of the apply kernels (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        src = open(os.path.join(ROOT, "paper_2004_05566_gb300", "csrc", "apply.cu"), "rb").read()
+        if d.get("apply_cu_sha256") != hashlib.sha256(src).hexdigest():
+            return None
+        k = d.get("kernels", {}).get(name)
+        return float(k["dram_bytes_per_launch_full"]) if k else None
+    except (OSError, ValueError, KeyError, TypeError):
+        return None
+
+
+# ----------------------------------------------------------------------- our arm
+
+def run_ours(args, rank: int, world: int, dist) -> dict | None:
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2004_05566_gb300.hifcn as H
+    import workloads as W
+
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = W.config_fisher2d_1023(eps=args.eps, seed=1 + rank)
+    if args.n != 1024:
+        import math as _m
+        L = int(round(_m.log2(args.n // 16)))
+        rng = np.random.default_rng(1 + rank)
+        w = W.Workload(f"fisher2d_{args.n - 1}", 2, args.n, 16, L, 1.0, args.eps,
+                       W.lognormal_coefficient(W.grf(rng, args.n, 2, 0.05), 1e4),
+                       W.gaussian_bump_u0(args.n, 2), (1, 1.0, 1.0))
+    a = torch.from_numpy(w.a_nodes).to(dev)
+    stream = torch.cuda.current_stream()
+
+    def make(precision):
+        opt = H.default_options(eps=w.eps, precision=precision, cg_tol=1e-10)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = H.hif_setup(2, w.n, w.leaf, a, w.dt, opt)
+        torch.cuda.synchronize()
+        tf = time.perf_counter() - t0
+        H.hif_set_reaction(h, 1, 1.0, 1.0)
+        return h, tf
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed_steps(h, K, W_, per_step=True):
+        u = torch.from_numpy(w.u0.ravel().copy()).to(dev)
+        v = torch.empty_like(u)
+        its = []
+        for _ in range(W_):
+            v, it = H.cn_step(h, u, out=v)
+            u, v = v, u
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+        barrier()
+        lc0 = H.hif_launch_count()
+        evs[0].record(stream)
+        for k in range(K):
+            v, it = H.cn_step(h, u, out=v)
+            u, v = v, u
+            its.append(it)
+            if per_step:
+                evs[k + 1].record(stream)
+        if not per_step:
+            evs[K].record(stream)
+        torch.cuda.synchronize()
+        lc1 = H.hif_launch_count()
+        barrier()
+        total = evs[0].elapsed_time(evs[K])
+        lat = [evs[k].elapsed_time(evs[k + 1]) for k in range(K)] if per_step else []
+        return total, lat, its, lc1 - lc0, u
+
+    # ---- mixed precision (headline)
+    h32, tf32 = make(H.HIF_FP32)
+    info32 = H.hif_query(h32)
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_ms, lat, its, launches, _ = timed_steps(h32, args.steps, args.warmup)
+    clk = clocks.stop()
+    # ---- instrumented pass of the same steps: per-kernel device time
+    H.hif_stats_enable(h32, True)
+    t_ms_stats, _, _, _, _ = timed_steps(h32, args.steps, 0, per_step=False)
+    stats = H.hif_stats_read(h32)
+    H.hif_stats_enable(h32, False)
+    # ---- end to end through host buffers (pinned), same metric
+    K_e2e = args.steps
+    uh = torch.from_numpy(w.u0.ravel().copy()).pin_memory()
+    oh = torch.empty_like(uh).pin_memory()
+    ud = torch.empty(w.N, dtype=torch.float64, device=dev)
+    vd = torch.empty_like(ud)
+    for _ in range(args.warmup):
+        ud.copy_(uh, non_blocking=True)
+        H.cn_step(h32, ud, out=vd)
+        oh.copy_(vd, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K_e2e):
+        ud.copy_(uh, non_blocking=True)
+        H.cn_step(h32, ud, out=vd)
+        oh.copy_(vd, non_blocking=True)
+        uh, oh = oh, uh
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    h32.close()
+    # ---- plain FP64 path on the same GPU
+    h64, tf64 = make(H.HIF_FP64)
+    t64_ms, lat64, its64, _, _ = timed_steps(h64, max(1, args.steps // 2), args.warmup)
+    info64 = H.hif_query(h64)
+    h64.close()
+
+    # ---- max over ranks
+    vals = [t_ms, e2e_ms, t64_ms]
+    if dist is not None:
+        tt = torch.tensor(vals, dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        vals = tt.tolist()
+    t_ms, e2e_ms, t64_ms = vals
+    if rank != 0:
+        return None
+
+    K = args.steps
+    value = world * K / (t_ms / 1e3)
+    lat_sorted = sorted(lat)
+
+    def pct(xs, q):
+        if not xs:
+            return None
+        i = min(len(xs) - 1, max(0, int(math.ceil(q / 100.0 * len(xs))) - 1))
+        return xs[i]
+
+    # ---- roofline of the dominant kernel
+    dom = max(stats, key=lambda s: s["ms"]) if stats else None
+    peaks = measured_peaks()
+    peak = _find_peak(peaks, ("hbm_gbs", "hbm_GBs", "copy_gbs"))
+    peak_note = "measured" if peak else "fallback"
+    if not peak:
+        peak = FALLBACK_HBM_GBS
+    roof = None
+    if dom:
+        per_launch_bytes = dom["bytes"] / dom["launches"]
+        per_launch_s = dom["ms"] / dom["launches"] / 1e3
+        achieved = per_launch_bytes / per_launch_s / 1e9
+        roof = {"bound": "hbm", "kernel": dom["name"], "achieved": round(achieved, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": kernel_traffic(dom["name"]),
+                "algorithmic_bytes_per_launch": per_launch_bytes,
+                "avg_launch_us": round(per_launch_s * 1e6, 2), "peak_source": peak_note,
+                "timing": "CUDA events around each launch on its stream, instrumented pass of "
+                          "the same steps"}
+    kt = sorted(stats, key=lambda s: -s["ms"])
+    apply_ms = sum(s["ms"] for s in stats)
+
+    # ---- CPU oracle baseline (rank 0, one GPU only)
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline and args.n == 1024:
+        try:
+            r = run_oracle_subprocess(256, 8, 1, args.eps)
+            cpu = {"value": round(r["steps_per_s_scaled"], 6), "unit": "steps/s", "cores": 1,
+                   "kind": "oracle",
+                   "sample": (f"oracle (Python/NumPy/SciPy FP64, 1 BLAS thread) on the same recipe "
+                              f"at 255^2 (N={r['N_sample']}), {r['steps']} timed CN steps "
+                              f"({r['seconds']:.1f} s, {r['iters_per_step']:.1f} PCG it/step), "
+                              f"setup untimed ({r['t_f']:.1f} s); steps/s scaled by N to 1023^2 "
+                              f"(measured on sample: {r['steps_per_s_sample']:.3f} steps/s)"),
+                   "cpu": cpu_model()}
+        except Exception as exc:  # report, never fake
+            cpu = {"value": None, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                   "sample": f"failed: {str(exc)[:200]}"}
+
+    iters_per_step = sum(its) / len(its)
+    line = {
+        "metric": METRIC,
+        "value": round(value, 3),
+        "unit": "steps/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": round(t_ms / K, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.n == 1024 else f"same recipe at {args.n - 1}^2 (profiling)",
+                   "precision": "factor FP32 (apply FP32), CG FP64",
+                   "global_batch": world, "parallelism": f"replicas x{world}" if world > 1 else "single",
+                   "l2": "inputs larger than L2: the ~1 GB FP32 factor streams every apply"},
+        "latency_ms": {"p50": pct(lat_sorted, 50), "p99": pct(lat_sorted, 99)},
+        "iters_per_step": round(iters_per_step, 3),
+        "cg_iters_per_s": round(world * sum(its) / (t_ms / 1e3), 2),
+        "t_f_s": {"fp32": round(tf32, 3), "fp64": round(tf64, 3)},
+        "fp64_path": {"value": round(world * max(1, K // 2) / (t64_ms / 1e3), 3), "unit": "steps/s",
+                      "ms_per_step": round(t64_ms / max(1, K // 2), 4),
+                      "iters_per_step": round(sum(its64) / len(its64), 3),
+                      "p50_ms": pct(sorted(lat64), 50), "p99_ms": pct(sorted(lat64), 99)},
+        "factor": {"entries": info32["factor_entries"], "apply_bytes_fp32": info32["apply_bytes"],
+                   "apply_bytes_fp64": info64["apply_bytes"], "root": info32["root_size"],
+                   "device_bytes": info32["device_bytes"]},
+        "e2e": {"value": round(world * K_e2e / (e2e_ms / 1e3), 3), "unit": "steps/s",
+                "h2d_bytes_per_step": 8 * w.N, "d2h_bytes_per_step": 8 * w.N,
+                "api": "cn_step via the C ABI, u^k copied from pinned host memory and u^{k+1} read back every step"},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "apply_kernels": [{"name": s["name"], "launches": s["launches"],
+                           "ms": round(s["ms"], 3), "GBps": round(s["bytes"] / (s["ms"] / 1e3) / 1e9, 1)
+                           if s["ms"] > 0 else None} for s in kt[:8]],
+        "apply_share_of_step": round(apply_ms / t_ms_stats, 3) if t_ms_stats else None,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    return line
+
+
+# ----------------------------------------------------------------- reference arm
+
+def run_reference(args) -> dict:
+    """The oracle, as it stands, on the host cores (bounded sample per step)."""
+    n = 256 if args.steps <= 200 else 128
+    r = run_oracle_subprocess(n, args.steps, args.warmup, args.eps)
+    v = r["steps_per_s_scaled"]
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": "steps/s",
+            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": round(v, 6), "unit": "steps/s", "cores": 1, "kind": "oracle",
+                             "sample": (f"each step = one oracle CN step of the same recipe at "
+                                        f"{n - 1}^2 (N={r['N_sample']}); steps/s scaled by N to "
+                                        f"1023^2; measured {r['steps_per_s_sample']:.3f} steps/s on "
+                                        f"the sample, {r['iters_per_step']:.2f} PCG it/step"),
+                             "cpu": cpu_model()},
+            "e2e": {"value": round(v, 6), "unit": "steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = _args()
+    if args.cpu_sample:
+        r = oracle_sample(args.cpu_sample, args.cpu_sample_steps, args.warmup, args.eps)
+        print(json.dumps(r))
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", rank)))
+        tdist.init_process_group("nccl")
+        dist = tdist
+    line = run_ours(args, rank, world, dist)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

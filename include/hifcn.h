@@ -175,7 +175,9 @@ int hif_destroy(hif_handle *h);
  * algorithmic bytes (factor values and indices read once, vector entries read
  * and written once) are recorded; hif_stats_read synchronizes, aggregates by
  * kernel name (e.g. "cell_bwd_l0"), writes up to cap records to out (host),
- * sets *count to the number of records, and clears the accumulated data. */
+ * sets *count to the number of records, and clears the accumulated data.
+ * With cap = 0 (out may be NULL) it only reports the number of records in
+ * *count and keeps the data. */
 typedef struct {
   char name[48];
   int64_t launches;

@@ -544,6 +544,17 @@ int hif_stats_enable(hif_handle *h, int on) {
 int hif_stats_read(hif_handle *h, hif_kernel_stat *out, int cap, int *count) {
   if (!h || !count || (cap > 0 && !out)) return HIF_EINVAL;
   HIF_CUDA_TRY(cudaDeviceSynchronize());
+  if (cap <= 0) {  // size query: number of kernel names with pending records
+    std::vector<char> seen(h->stat_names.size(), 0);
+    int n = 0;
+    for (auto &r : h->stat_pending)
+      if (!seen[r.name]) {
+        seen[r.name] = 1;
+        ++n;
+      }
+    *count = n;
+    return HIF_OK;
+  }
   std::vector<hif_kernel_stat> agg(h->stat_names.size());
   for (size_t i = 0; i < agg.size(); ++i) {
     std::memset(&agg[i], 0, sizeof(hif_kernel_stat));
@@ -566,7 +577,6 @@ int hif_stats_read(hif_handle *h, hif_kernel_stat *out, int cap, int *count) {
       ++n;
     }
   *count = n < cap ? n : cap;
-  if (cap == 0) *count = n;
   return HIF_OK;
 }
 
