@@ -130,6 +130,30 @@ int hif_export_factor(const hif_handle *h, void *buf, size_t *bytes);
  * Errors: HIF_EINVAL, HIF_ECUDA. */
 int hif_apply(hif_handle *h, const double *x, double *y, int precision, hif_stream stream);
 
+/* ---------------------------------------------------------------------------
+ * hif_apply_noalloc - y = F^{-1} x in FP64, like hif_apply with HIF_FP64, but
+ * the scratch the cell kernels write their boundary updates to comes from a
+ * fixed array compiled into this library (HIF_NOALLOC_MAX_SLOTS doubles, 4 MiB,
+ * held on every device that loads the library until the process exits)
+ * instead of from memory the handle owns.  The paper has no counterpart; this
+ * entry point exists for callers that cannot allocate device memory when they
+ * apply the preconditioner: code running under an allocator that has already
+ * reserved the free HBM (a further cudaMalloc would fail), or a latency-bound
+ * loop that cannot afford the device-wide synchronization a cudaMalloc or
+ * cudaFree may cause.  The call allocates nothing (no cudaMalloc, no cudaFree,
+ * no allocating library routine); the caller passes x and y.
+ *   x, y  device, N doubles each; may not alias.
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the one array and each call overwrites it (every slot is written
+ * before it is read, nothing needs to start at zero), so calls that overlap on
+ * the GPU (concurrent streams, or several handles at once) race: serialize them.
+ * Kernel statistics are not recorded by this call.
+ * Errors: HIF_EINVAL (NULL/aliased pointers, or a factor whose cells need more
+ * than HIF_NOALLOC_MAX_SLOTS boundary slots in one level), HIF_ECUDA. */
+#define HIF_NOALLOC_MAX_SLOTS (1 << 19)
+int hif_apply_noalloc(hif_handle *h, const double *x, double *y, hif_stream stream);
+
 /* hif_matvec - y = A x with A = I - dt/2 M (Eq. CN).  x, y device, may not alias. */
 int hif_matvec(hif_handle *h, const double *x, double *y, hif_stream stream);
 

@@ -248,6 +248,14 @@ int apply_levels(Handle *h, const FactorValues<T> &fv, T *x, cudaStream_t s) {
 
 int apply_inplace_f64(Handle *h, double *x, cudaStream_t s) { return apply_levels<double>(h, h->f64, x, s); }
 
+// FP64 apply in place with the cell-contribution scratch supplied by the
+// caller instead of the handle's own buffer (used by hif_apply_noalloc).
+int apply_inplace_f64_with_scratch(Handle *h, double *contrib, double *x, cudaStream_t s) {
+  FactorValues<double> fv = h->f64;
+  fv.contrib = contrib;
+  return apply_levels<double>(h, fv, x, s);
+}
+
 int apply_inplace_f32(Handle *h, float *x, cudaStream_t s) {
   if (!h->has_f32) return HIF_EINVAL;
   return apply_levels<float>(h, h->f32, x, s);

@@ -27,7 +27,7 @@ HIF_FP64, HIF_FP32 = 0, 1
 EXPORTED = ("hif_default_options", "hif_setup", "hif_import_factor", "hif_export_factor",
             "hif_apply", "hif_matvec", "pcg_solve", "cn_step", "hif_set_reaction", "hif_query",
             "hif_destroy", "hif_strerror", "hif_last_error", "hif_stats_enable", "hif_stats_read",
-            "hif_launch_count")
+            "hif_launch_count", "hif_apply_noalloc")
 
 
 class HifGrid(ctypes.Structure):
@@ -88,6 +88,8 @@ def lib():
     L.hif_stats_read.argtypes = [c_void_p, POINTER(HifKernelStat), c_int, POINTER(c_int)]
     L.hif_launch_count.argtypes = []
     L.hif_launch_count.restype = c_int64
+    L.hif_apply_noalloc.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
+    L.hif_apply_noalloc.restype = c_int
     for name in ("hif_setup", "hif_import_factor", "hif_export_factor", "hif_apply", "hif_matvec",
                  "pcg_solve", "cn_step", "hif_set_reaction", "hif_query", "hif_destroy",
                  "hif_stats_enable", "hif_stats_read"):
@@ -199,6 +201,17 @@ def hif_apply(h: Handle, x: torch.Tensor, y: torch.Tensor = None, precision: int
         y = torch.empty_like(x)
     _check("hif_apply", lib().hif_apply(h.ptr, _vec(x, h.N, "x"), _vec(y, h.N, "y"), precision,
                                         _stream(stream)))
+    return y
+
+
+def hif_apply_noalloc(h: Handle, x: torch.Tensor, y: torch.Tensor = None,
+                      stream=None) -> torch.Tensor:
+    """y = F^{-1} x in FP64 with the library's static scratch (no device allocation in the
+    call; see include/hifcn.h).  If y is None it is allocated here by torch, before the call."""
+    if y is None:
+        y = torch.empty_like(x)
+    _check("hif_apply_noalloc", lib().hif_apply_noalloc(h.ptr, _vec(x, h.N, "x"), _vec(y, h.N, "y"),
+                                                        _stream(stream)))
     return y
 
 
