@@ -181,6 +181,23 @@ int pcg_solve(hif_handle *h, const double *b, double *x, int *iters, double *rel
 int cn_step(hif_handle *h, const double *u_k, const double *r_k, double *u_k1, int *iters,
             hif_stream stream);
 
+/* ---------------------------------------------------------------------------
+ * cn_step_batched - one CN step (as cn_step) for each of count handles, which
+ * may differ in dimension, size and coefficients (independent problems, the
+ * loop body of Algorithm 1 for each).  Results equal those of calling cn_step
+ * on each handle in turn, bit for bit.  The steps of different handles overlap
+ * on the GPU; a handle listed more than once takes its steps in list order.
+ *   hs      host array of count handles.
+ *   u_k     host array of count device pointers (N_i doubles each).
+ *   r_k     host array of count device pointers or NULL entries, or NULL.
+ *   u_k1    host array of count device pointers, outputs (may alias u_k[i]).
+ *   iters   host array of count ints (may be NULL).
+ * The device work is ordered after the work already enqueued on stream; the
+ * call returns when every step is done.
+ * Errors: HIF_EINVAL, HIF_ENOCONV (first failing handle), HIF_ECUDA. */
+int cn_step_batched(hif_handle *const *hs, int count, const double *const *u_k,
+                    const double *const *r_k, double *const *u_k1, int *iters, hif_stream stream);
+
 /* hif_set_reaction - built-in explicit reaction r(u) = k1 u (1 - u/k2) (Eq. nr)
  * for kind = 1; kind = 0 disables it.  k2 may be +inf (linear reaction).
  * Errors: HIF_EINVAL. */

@@ -90,6 +90,7 @@ int alloc_work(Handle *h) {
   HIF_TRY(dev_alloc(h, (void **)&h->q, N * sizeof(double)));
   HIF_TRY(dev_alloc(h, (void **)&h->z, N * sizeof(double)));
   HIF_TRY(dev_alloc(h, (void **)&h->g, N * sizeof(double)));
+  HIF_TRY(dev_alloc(h, (void **)&h->xsol, N * sizeof(double)));
   HIF_TRY(dev_alloc(h, (void **)&h->partials, 4 * nb * sizeof(double)));
   HIF_TRY(dev_alloc(h, (void **)&h->scal, 16 * sizeof(double)));
   HIF_CUDA_TRY(cudaMallocHost((void **)&h->host_scal, 16 * sizeof(double)));
@@ -152,12 +153,42 @@ int finish_device_factor(Handle *h, cudaStream_t s) {
     if (!H.groups.empty())
       HIF_CUDA_TRY(cudaMemcpyAsync(D.groups, H.groups.data(), H.groups.size() * sizeof(GroupDesc),
                                    cudaMemcpyHostToDevice, s));
+    // work items: enough CTAs per launch to cover the GPU at the upper levels
+    const int target = 152 * 4;
+    std::vector<CellItem> fw, bw;
+    for (int c = 0; c < (int)H.cells.size(); ++c) {
+      const CellDesc &cd = H.cells[c];
+      const int rows = cd.nB + cd.nI;
+      int chunks = 1;
+      if ((int)H.cells.size() < target)
+        chunks = std::max(1, std::min((target + (int)H.cells.size() - 1) / (int)H.cells.size(),
+                                      (rows + 31) / 32));
+      int per = ((rows + chunks - 1) / chunks + 31) / 32 * 32;
+      for (int a = 0; a < rows; a += per) fw.push_back({c, a, std::min(rows, a + per), 0});
+      int cch = 1;
+      if ((int)H.cells.size() < target)
+        cch = std::max(1, std::min((target + (int)H.cells.size() - 1) / (int)H.cells.size(),
+                                   (cd.nI + 31) / 32));
+      int cper = ((cd.nI + cch - 1) / cch + 3) / 4 * 4;  // column chunks start on quads
+      if (cper < 4) cper = 4;
+      for (int a = 0; a < cd.nI; a += cper) bw.push_back({c, a, std::min(cd.nI, a + cper), 0});
+    }
+    D.nfwd = (int)fw.size();
+    D.nbwd = (int)bw.size();
+    HIF_TRY(dev_alloc(h, (void **)&D.fwd, std::max<size_t>(1, fw.size()) * sizeof(CellItem)));
+    HIF_TRY(dev_alloc(h, (void **)&D.bwd, std::max<size_t>(1, bw.size()) * sizeof(CellItem)));
+    if (!fw.empty())
+      HIF_CUDA_TRY(cudaMemcpyAsync(D.fwd, fw.data(), fw.size() * sizeof(CellItem), cudaMemcpyHostToDevice, s));
+    if (!bw.empty())
+      HIF_CUDA_TRY(cudaMemcpyAsync(D.bwd, bw.data(), bw.size() * sizeof(CellItem), cudaMemcpyHostToDevice, s));
   }
+  HIF_TRY(dev_alloc(h, (void **)&h->f64.xI, h->N * sizeof(double)));
   HIF_TRY(dev_alloc(h, (void **)&h->f64.contrib, h->max_contrib * sizeof(double)));
   if (h->opt.precision == HIF_FP32) {
     HIF_TRY(dev_alloc(h, (void **)&h->f32.vals, h->nvals * sizeof(float)));
     HIF_TRY(dev_alloc(h, (void **)&h->f32.contrib, h->max_contrib * sizeof(float)));
     HIF_TRY(dev_alloc(h, (void **)&h->f32.work, h->N * sizeof(float)));
+    HIF_TRY(dev_alloc(h, (void **)&h->f32.xI, h->N * sizeof(float)));
     k_cast_f32<<<1216, 256, 0, s>>>(h->f64.vals, h->f32.vals, h->nvals);
     note_launch();
     HIF_CUDA_TRY(cudaGetLastError());
@@ -279,10 +310,21 @@ int import_blob(Handle *h, const void *blob, size_t bytes, cudaStream_t s) {
     h->idx_host.resize(h->idx_host.size() + n);
     return rd.get(h->idx_host.data() + *off, n);
   };
-  auto get_vals = [&](long long n, long long *off) -> bool {
+  // blocks land in the padded layout: every block starts on a multiple of 4
+  // elements, rows are padded with zeros to multiples of 4 elements
+  auto get_lower = [&](int n, long long *off) -> bool {  // packed lower triangle
     *off = (long long)vals.size();
-    vals.resize(vals.size() + n);
-    return rd.get(vals.data() + *off, n);
+    vals.resize(vals.size() + tri_off(n), 0.0);
+    for (int i = 0; i < n; ++i)
+      if (!rd.get(vals.data() + *off + tri_off(i), i + 1)) return false;
+    return true;
+  };
+  auto get_dense = [&](int rows, int cols, long long *off) -> bool {  // row major
+    *off = (long long)vals.size();
+    vals.resize(vals.size() + (long long)rows * pad4(cols), 0.0);
+    for (int i = 0; i < rows; ++i)
+      if (!rd.get(vals.data() + *off + (long long)i * pad4(cols), cols)) return false;
+    return true;
   };
   for (int l = 0; l < h->L; ++l) {
     int cnt[2];
@@ -296,8 +338,8 @@ int import_blob(Handle *h, const void *blob, size_t bytes, cudaStream_t s) {
       d.nI = sz[0];
       d.nB = sz[1];
       if (!get_ints(d.nI, &d.I_off) || !get_ints(d.nB, &d.B_off)) return HIF_EFORMAT;
-      if (!get_vals((long long)d.nI * (d.nI + 1) / 2, &d.G_off)) return HIF_EFORMAT;
-      if (!get_vals((long long)d.nB * d.nI, &d.V_off)) return HIF_EFORMAT;
+      if (!get_lower(d.nI, &d.G_off)) return HIF_EFORMAT;
+      if (!get_dense(d.nB, d.nI, &d.V_off)) return HIF_EFORMAT;
       d.C_off = slots;
       slots += d.nB;
       H.cells.push_back(d);
@@ -307,7 +349,7 @@ int import_blob(Handle *h, const void *blob, size_t bytes, cudaStream_t s) {
       GroupDesc d{};
       if (!rd.get(&d.n) || d.n <= 0) return HIF_EFORMAT;
       if (!get_ints(d.n, &d.idx_off)) return HIF_EFORMAT;
-      if (!get_vals((long long)d.n * d.n, &d.H_off)) return HIF_EFORMAT;
+      if (!get_dense(d.n, d.n, &d.H_off)) return HIF_EFORMAT;
       H.groups.push_back(d);
     }
     HIF_TRY(build_contrib_map(h, H));
@@ -316,7 +358,7 @@ int import_blob(Handle *h, const void *blob, size_t bytes, cudaStream_t s) {
   if (!rd.get(&nr) || nr < 0) return HIF_EFORMAT;
   h->root_n = nr;
   if (!get_ints(nr, &h->root_idx_off)) return HIF_EFORMAT;
-  if (!get_vals((long long)nr * (nr + 1) / 2, &h->root_G_off)) return HIF_EFORMAT;
+  if (!get_lower(nr, &h->root_G_off)) return HIF_EFORMAT;
   if (rd.p != rd.end) return HIF_EFORMAT;
   for (int v : h->idx_host)
     if (v < 0 || v >= h->N) return HIF_EFORMAT;
@@ -350,6 +392,7 @@ using namespace hifcn;
 
 hif_handle::~hif_handle() {
   cudaDeviceSynchronize();
+  hifcn::destroy_pcg_graphs(this);
   for (auto &r : stat_pending) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -441,18 +484,18 @@ int hif_export_factor(const hif_handle *hh, void *buf, size_t *bytes) {
       put(sz, 8);
       put(h->idx_host.data() + c.I_off, c.nI * 4);
       put(h->idx_host.data() + c.B_off, c.nB * 4);
-      put(vals.data() + c.G_off, (size_t)c.nI * (c.nI + 1) / 2 * 8);
-      put(vals.data() + c.V_off, (size_t)c.nB * c.nI * 8);
+      for (int i = 0; i < c.nI; ++i) put(vals.data() + c.G_off + tri_off(i), (size_t)(i + 1) * 8);
+      for (int b = 0; b < c.nB; ++b) put(vals.data() + c.V_off + (long long)b * pad4(c.nI), (size_t)c.nI * 8);
     }
     for (auto &g : H.groups) {
       put(&g.n, 4);
       put(h->idx_host.data() + g.idx_off, g.n * 4);
-      put(vals.data() + g.H_off, (size_t)g.n * g.n * 8);
+      for (int i = 0; i < g.n; ++i) put(vals.data() + g.H_off + (long long)i * pad4(g.n), (size_t)g.n * 8);
     }
   }
   put(&h->root_n, 4);
   put(h->idx_host.data() + h->root_idx_off, h->root_n * 4);
-  put(vals.data() + h->root_G_off, (size_t)h->root_n * (h->root_n + 1) / 2 * 8);
+  for (int i = 0; i < h->root_n; ++i) put(vals.data() + h->root_G_off + tri_off(i), (size_t)(i + 1) * 8);
   if (!buf) {
     *bytes = out.size();
     return HIF_OK;
@@ -486,6 +529,15 @@ int cn_step(hif_handle *h, const double *u_k, const double *r_k, double *u_k1, i
             hif_stream stream) {
   if (!h || !u_k || !u_k1) return HIF_EINVAL;
   return cn(h, u_k, r_k, u_k1, iters, (cudaStream_t)stream);
+}
+
+int cn_step_batched(hif_handle *const *hs, int count, const double *const *u_k,
+                    const double *const *r_k, double *const *u_k1, int *iters, hif_stream stream) {
+  if (count < 0 || (count > 0 && (!hs || !u_k || !u_k1))) return HIF_EINVAL;
+  for (int i = 0; i < count; ++i)
+    if (!hs[i] || !u_k[i] || !u_k1[i]) return HIF_EINVAL;
+  if (count == 0) return HIF_OK;
+  return cn_batched(hs, count, u_k, r_k, u_k1, iters, (cudaStream_t)stream);
 }
 
 int hif_set_reaction(hif_handle *h, int kind, double k1, double k2) {

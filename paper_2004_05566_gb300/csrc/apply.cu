@@ -2,20 +2,24 @@
 //   F^{-1} = R_0 ... R_{L-1} A_L^{-1} R_{L-1}^T ... R_0^T,   R_l = E_l C_l K_l.
 //
 // Forward sweep, level l (R_l^T = K_l^T C_l^T E_l^T):
-//   cells  (E_l^T, Eq. 2_3): x_B -= V x_I with V = A_BI A_II^{-1};  x_I <- G x_I, G = L^{-1}
+//   cells  (E_l^T, Eq. 2_3): x_B -= V x_I with V = A_BI A_II^{-1}; the interior's
+//                            forward value G x_I (G = L^{-1}) goes to the vector xI
 //   groups (K_l^T C_l^T)   : x_g <- H x_g  (block Jacobi rescaling then, for
 //                            skeletonized entities, Z^T and the redundant elimination)
 // Root (Eq. 3_4): x_r <- G_r^T G_r x_r with A_L = L_r L_r^T, G_r = L_r^{-1}.
 // Backward sweep, level l (R_l = E_l C_l K_l):
 //   groups: x_g <- H^T x_g
-//   cells : x_I <- G^T x_I - V^T x_B
+//   cells : x_I <- G^T xI_I - V^T x_B
 //
 // Cells of one level share boundary DOFs; their updates x_B -= V x_I are
 // written to a per-cell contribution scratch and gathered by the group kernel
-// in a fixed order, so results are bitwise reproducible.  One CTA per cell /
-// group; rows of G, V and H are read by whole warps (coalesced), transposed
-// products are accumulated per column thread over contiguous rows.  T is the
-// storage and arithmetic type of the factor (double or float).
+// in a fixed order, so results are bitwise reproducible.  Because the forward
+// cell step never writes x and the backward cell step reads its interior from
+// xI, a cell's rows (forward) or columns (backward) can be spread over several
+// CTAs; the upper levels, with few large cells, use that to fill the GPU.
+// Rows of G, V and H are read by whole warps (coalesced, several rows in
+// flight); transposed products are accumulated per column over contiguous
+// rows.  T is the storage and arithmetic type of the factor (double or float).
 #include "internal.h"
 #include "device_common.cuh"
 
@@ -23,9 +27,11 @@ namespace hifcn {
 
 namespace {
 
-constexpr int kCellThreads = 256;
-constexpr int kGroupThreads = 64;
+constexpr int kCellFwdThreads = 256;
+constexpr int kCellBwdThreads = 256;
+constexpr int kGroupThreads = 128;
 constexpr int kRootThreads = 256;
+constexpr int kRows = 4;  // rows a warp keeps in flight in the row-dot kernels
 
 template <typename T>
 __device__ __forceinline__ T warp_reduce(T v) {
@@ -33,38 +39,106 @@ __device__ __forceinline__ T warp_reduce(T v) {
   return v;
 }
 
+// 16-byte-aligned loads of 4 consecutive elements (one LDG.128 for float,
+// two for double); rows of the factor are padded to multiples of 4 elements.
+__device__ __forceinline__ void ld4(const float *p, float (&o)[4]) {
+  const float4 v = *reinterpret_cast<const float4 *>(p);
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void ld4(const double *p, double (&o)[4]) {
+  const double2 a = *reinterpret_cast<const double2 *>(p);
+  const double2 b = *reinterpret_cast<const double2 *>(p + 2);
+  o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+
+// Dot products of kRows padded rows (pointers rp, lengths in quads nq) with
+// the zero-padded shared vector xs by one warp; every row's loads are issued
+// before the FMAs.
 template <typename T>
-__global__ void __launch_bounds__(kCellThreads) k_cell_fwd(const CellDesc *__restrict__ cells,
-                                                           const int *__restrict__ idx,
-                                                           const T *__restrict__ vals,
-                                                           T *__restrict__ contrib,
-                                                           T *__restrict__ x) {
+__device__ __forceinline__ void warp_rows_dot4(const T *const (&rp)[kRows], const int (&nq)[kRows],
+                                               const T *xs, T (&acc)[kRows]) {
+  const int lane = threadIdx.x & 31;
+  int maxq = 0;
+#pragma unroll
+  for (int u = 0; u < kRows; ++u) {
+    acc[u] = T(0);
+    maxq = nq[u] > maxq ? nq[u] : maxq;
+  }
+  for (int q = lane; q < maxq; q += 32) {
+    T v[kRows][4];
+#pragma unroll
+    for (int u = 0; u < kRows; ++u) {
+      if (q < nq[u]) ld4(rp[u] + 4 * q, v[u]);
+      else v[u][0] = v[u][1] = v[u][2] = v[u][3] = T(0);
+    }
+    T xv[4];
+    xv[0] = xs[4 * q]; xv[1] = xs[4 * q + 1]; xv[2] = xs[4 * q + 2]; xv[3] = xs[4 * q + 3];
+#pragma unroll
+    for (int u = 0; u < kRows; ++u)
+      acc[u] += v[u][0] * xv[0] + v[u][1] * xv[1] + v[u][2] * xv[2] + v[u][3] * xv[3];
+  }
+#pragma unroll
+  for (int u = 0; u < kRows; ++u) acc[u] = warp_reduce(acc[u]);
+}
+
+// Forward cell step (E_I^T): contributions c_B = V x_I and the forward value
+// G x_I of the interior.  A CTA handles rows [a, b) of one cell's stacked
+// [V; G]; x_I is only read here (the forward values go to the separate vector
+// xI, which the backward cell step reads), so a cell may be split over CTAs.
+template <typename T>
+__global__ void __launch_bounds__(kCellFwdThreads) k_cell_fwd(const CellItem *__restrict__ items,
+                                                              const CellDesc *__restrict__ cells,
+                                                              const int *__restrict__ idx,
+                                                              const T *__restrict__ vals,
+                                                              T *__restrict__ contrib,
+                                                              T *__restrict__ xI,
+                                                              const T *__restrict__ x) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *xs = reinterpret_cast<T *>(smem_raw);
-  const CellDesc c = cells[blockIdx.x];
+  const CellItem it = items[blockIdx.x];
+  const CellDesc c = cells[it.cell];
   const int *I = idx + c.I_off;
-  for (int i = threadIdx.x; i < c.nI; i += kCellThreads) xs[i] = x[I[i]];
+  const int nIp = (int)pad4(c.nI);
+  for (int i = threadIdx.x; i < nIp; i += kCellFwdThreads) xs[i] = i < c.nI ? x[I[i]] : T(0);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int NW = kCellThreads / 32;
+  constexpr int NW = kCellFwdThreads / 32;
   const T *V = vals + c.V_off;
-  for (int b = warp; b < c.nB; b += NW) {
-    const T *row = V + (long long)b * c.nI;
-    T acc = 0;
-    for (int i = lane; i < c.nI; i += 32) acc += row[i] * xs[i];
-    acc = warp_reduce(acc);
-    if (lane == 0) contrib[c.C_off + b] = acc;
-  }
   const T *G = vals + c.G_off;
-  for (int i = warp; i < c.nI; i += NW) {
-    const T *row = G + (long long)i * (i + 1) / 2;
-    T acc = 0;
-    for (int j = lane; j <= i; j += 32) acc += row[j] * xs[j];
-    acc = warp_reduce(acc);
-    if (lane == 0) x[I[i]] = acc;
+  const int vq = nIp / 4;
+  for (int r0 = it.a + warp * kRows; r0 < it.b; r0 += NW * kRows) {
+    const T *rp[kRows];
+    int nq[kRows];
+#pragma unroll
+    for (int u = 0; u < kRows; ++u) {
+      const int r = r0 + u;
+      if (r >= it.b) {
+        rp[u] = V;
+        nq[u] = 0;
+      } else if (r < c.nB) {
+        rp[u] = V + (long long)r * nIp;
+        nq[u] = vq;
+      } else {
+        const int i = r - c.nB;
+        rp[u] = G + tri_off(i);
+        nq[u] = (i + 4) / 4;
+      }
+    }
+    T acc[kRows];
+    warp_rows_dot4<T>(rp, nq, xs, acc);
+    if (lane == 0) {
+#pragma unroll
+      for (int u = 0; u < kRows; ++u) {
+        const int r = r0 + u;
+        if (r >= it.b) break;
+        if (r < c.nB) contrib[c.C_off + r] = acc[u];
+        else xI[I[r - c.nB]] = acc[u];
+      }
+    }
   }
 }
 
+// Forward group step (K^T C^T): x_g <- H (x_g - sum of the cells' contributions).
 template <typename T>
 __global__ void __launch_bounds__(kGroupThreads) k_group_fwd(
     const GroupDesc *__restrict__ groups, const int *__restrict__ idx,
@@ -74,94 +148,224 @@ __global__ void __launch_bounds__(kGroupThreads) k_group_fwd(
   T *xs = reinterpret_cast<T *>(smem_raw);
   const GroupDesc g = groups[blockIdx.x];
   const int *gi = idx + g.idx_off;
-  for (int i = threadIdx.x; i < g.n; i += kGroupThreads) {
-    T v = x[gi[i]];
-    const long long a = cptr[g.cptr_off + i], b = cptr[g.cptr_off + i + 1];
-    for (long long s = a; s < b; ++s) v -= contrib[cslot[s]];
+  const int np = (int)pad4(g.n);
+  for (int i = threadIdx.x; i < np; i += kGroupThreads) {
+    T v = T(0);
+    if (i < g.n) {
+      v = x[gi[i]];
+      const long long a = cptr[g.cptr_off + i], b = cptr[g.cptr_off + i + 1];
+      for (long long s = a; s < b; ++s) v -= contrib[cslot[s]];
+    }
     xs[i] = v;
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int NW = kGroupThreads / 32;
   const T *H = vals + g.H_off;
-  for (int i = warp; i < g.n; i += NW) {
-    const T *row = H + (long long)i * g.n;
-    T acc = 0;
-    for (int j = lane; j < g.n; j += 32) acc += row[j] * xs[j];
-    acc = warp_reduce(acc);
-    if (lane == 0) x[gi[i]] = acc;
+  for (int r0 = warp * kRows; r0 < g.n; r0 += NW * kRows) {
+    const T *rp[kRows];
+    int nq[kRows];
+#pragma unroll
+    for (int u = 0; u < kRows; ++u) {
+      const int r = r0 + u;
+      rp[u] = H + (long long)(r < g.n ? r : 0) * np;
+      nq[u] = r < g.n ? np / 4 : 0;
+    }
+    T acc[kRows];
+    warp_rows_dot4<T>(rp, nq, xs, acc);
+    if (lane == 0) {
+#pragma unroll
+      for (int u = 0; u < kRows; ++u)
+        if (r0 + u < g.n) x[gi[r0 + u]] = acc[u];
+    }
   }
 }
 
+// Column-parallel transposed products: threads are (column unit, row group);
+// each thread sums its rows, the row groups are added in a fixed order.
+__device__ __forceinline__ void col_layout(int ncols, int nthreads, int &CW, int &RG) {
+  CW = ((ncols + 31) / 32) * 32;
+  if (CW > nthreads) CW = nthreads;
+  if (CW < 32) CW = 32;
+  RG = nthreads / CW;
+}
+
+// Backward group step: x_g <- H^T x_g.
 template <typename T>
 __global__ void __launch_bounds__(kGroupThreads) k_group_bwd(const GroupDesc *__restrict__ groups,
                                                              const int *__restrict__ idx,
                                                              const T *__restrict__ vals,
                                                              T *__restrict__ x) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *xs = reinterpret_cast<T *>(smem_raw);
   const GroupDesc g = groups[blockIdx.x];
+  T *xs = reinterpret_cast<T *>(smem_raw);
+  T *part = xs + g.n;
   const int *gi = idx + g.idx_off;
   for (int i = threadIdx.x; i < g.n; i += kGroupThreads) xs[i] = x[gi[i]];
   __syncthreads();
   const T *H = vals + g.H_off;
-  for (int j = threadIdx.x; j < g.n; j += kGroupThreads) {
-    T acc = 0;
-    for (int i = 0; i < g.n; ++i) acc += H[(long long)i * g.n + j] * xs[i];
-    x[gi[j]] = acc;
+  const long long np = pad4(g.n);
+  int CW, RG;
+  col_layout(g.n, kGroupThreads, CW, RG);
+  const int cl = threadIdx.x % CW, rg = threadIdx.x / CW;
+  for (int c0 = 0; c0 < g.n; c0 += CW) {
+    const int col = c0 + cl;
+    T acc = T(0);
+    if (rg < RG && col < g.n) {
+#pragma unroll 4
+      for (int i = rg; i < g.n; i += RG) acc += H[(long long)i * np + col] * xs[i];
+    }
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    if (rg == 0 && col < g.n) {
+      T sum = part[cl];
+      for (int q = 1; q < RG; ++q) sum += part[q * CW + cl];
+      x[gi[col]] = sum;
+    }
+    __syncthreads();
   }
 }
 
+// Backward cell step (E_I): x_I <- G^T xI_I - V^T x_B, for columns [a, b)
+// (a a multiple of 4) of one cell.  A thread owns the column quad pair
+// (qa, qb) = (first + p, last - p), which balances the triangular row counts,
+// and reads both quads of a row with 16-byte loads; row groups are added in
+// a fixed order.
 template <typename T>
-__global__ void __launch_bounds__(kCellThreads) k_cell_bwd(const CellDesc *__restrict__ cells,
-                                                           const int *__restrict__ idx,
-                                                           const T *__restrict__ vals,
-                                                           T *__restrict__ x) {
+__global__ void __launch_bounds__(kCellBwdThreads) k_cell_bwd(const CellItem *__restrict__ items,
+                                                              const CellDesc *__restrict__ cells,
+                                                              const int *__restrict__ idx,
+                                                              const T *__restrict__ vals,
+                                                              const T *__restrict__ xI,
+                                                              T *__restrict__ x) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const CellDesc c = cells[blockIdx.x];
-  T *xs = reinterpret_cast<T *>(smem_raw);
+  const CellItem it = items[blockIdx.x];
+  const CellDesc c = cells[it.cell];
+  T *part = reinterpret_cast<T *>(smem_raw);  // 8 * kCellBwdThreads
+  T *xs = part + 8 * kCellBwdThreads;
   T *xb = xs + c.nI;
   const int *I = idx + c.I_off;
   const int *B = idx + c.B_off;
-  for (int i = threadIdx.x; i < c.nI; i += kCellThreads) xs[i] = x[I[i]];
-  for (int b = threadIdx.x; b < c.nB; b += kCellThreads) xb[b] = x[B[b]];
+  for (int i = threadIdx.x; i < c.nI; i += kCellBwdThreads) xs[i] = xI[I[i]];
+  for (int q = threadIdx.x; q < c.nB; q += kCellBwdThreads) xb[q] = x[B[q]];
   __syncthreads();
   const T *G = vals + c.G_off;
   const T *V = vals + c.V_off;
-  for (int j = threadIdx.x; j < c.nI; j += kCellThreads) {
-    T acc = 0;
-#pragma unroll 4
-    for (int i = j; i < c.nI; ++i) acc += G[(long long)i * (i + 1) / 2 + j] * xs[i];
-    T accv = 0;
-#pragma unroll 4
-    for (int b = 0; b < c.nB; ++b) accv += V[(long long)b * c.nI + j] * xb[b];
-    x[I[j]] = acc - accv;
+  const long long vstride = pad4(c.nI);
+  const int q0 = it.a / 4, q1 = (it.b + 3) / 4;  // column quads [q0, q1)
+  const int npairs = (q1 - q0 + 1) / 2;
+  int PW, RG;
+  col_layout(npairs, kCellBwdThreads, PW, RG);
+  const int pl = threadIdx.x % PW, rg = threadIdx.x / PW;
+  for (int p0 = 0; p0 < npairs; p0 += PW) {
+    const int p = p0 + pl;
+    const int qa = q0 + p, qb = q1 - 1 - p;
+    const bool okA = rg < RG && p < npairs;
+    const bool okB = okA && qb > qa;
+    T aA[4] = {T(0), T(0), T(0), T(0)}, aB[4] = {T(0), T(0), T(0), T(0)};
+    if (okA) {
+      // G rows i >= 4 qa with i = rg (mod RG); the quad of row i is inside
+      // the padded row whenever 4q <= i
+      const int ia = 4 * qa;
+      const int i0 = ia + ((rg - ia % RG) % RG + RG) % RG;
+#pragma unroll 2
+      for (int i = i0; i < c.nI; i += RG) {
+        const T *row = G + tri_off(i);
+        const T xv = xs[i];
+        T v[4];
+        ld4(row + 4 * qa, v);
+        aA[0] += v[0] * xv; aA[1] += v[1] * xv; aA[2] += v[2] * xv; aA[3] += v[3] * xv;
+        if (okB && i >= 4 * qb) {
+          T w[4];
+          ld4(row + 4 * qb, w);
+          aB[0] += w[0] * xv; aB[1] += w[1] * xv; aB[2] += w[2] * xv; aB[3] += w[3] * xv;
+        }
+      }
+#pragma unroll 2
+      for (int q = rg; q < c.nB; q += RG) {
+        const T *row = V + (long long)q * vstride;
+        const T xv = xb[q];
+        T v[4];
+        ld4(row + 4 * qa, v);
+        aA[0] -= v[0] * xv; aA[1] -= v[1] * xv; aA[2] -= v[2] * xv; aA[3] -= v[3] * xv;
+        if (okB) {
+          T w[4];
+          ld4(row + 4 * qb, w);
+          aB[0] -= w[0] * xv; aB[1] -= w[1] * xv; aB[2] -= w[2] * xv; aB[3] -= w[3] * xv;
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      part[k * kCellBwdThreads + threadIdx.x] = aA[k];
+      part[(4 + k) * kCellBwdThreads + threadIdx.x] = aB[k];
+    }
+    __syncthreads();
+    if (rg == 0 && p < npairs) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int col = (k < 4 ? 4 * qa : 4 * qb) + (k & 3);
+        if (k >= 4 && qb <= qa) break;
+        if (col < it.a || col >= it.b) continue;
+        T sum = part[k * kCellBwdThreads + pl];
+        for (int g = 1; g < RG; ++g) sum += part[k * kCellBwdThreads + g * PW + pl];
+        x[I[col]] = sum;
+      }
+    }
+    __syncthreads();
   }
 }
 
+// Root (Eq. 3_4): x_r <- G_r^T (G_r x_r).
 template <typename T>
 __global__ void __launch_bounds__(kRootThreads) k_root(int nr, const int *__restrict__ ridx,
                                                        const T *__restrict__ G,
                                                        T *__restrict__ x) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nrp = (int)pad4(nr);
   T *xs = reinterpret_cast<T *>(smem_raw);
-  T *ts = xs + nr;
-  for (int i = threadIdx.x; i < nr; i += kRootThreads) xs[i] = x[ridx[i]];
+  T *ts = xs + nrp;
+  T *part = ts + nrp;
+  for (int i = threadIdx.x; i < nrp; i += kRootThreads) xs[i] = i < nr ? x[ridx[i]] : T(0);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int NW = kRootThreads / 32;
-  for (int i = warp; i < nr; i += NW) {  // t = G x
-    const T *row = G + (long long)i * (i + 1) / 2;
-    T acc = 0;
-    for (int j = lane; j <= i; j += 32) acc += row[j] * xs[j];
-    acc = warp_reduce(acc);
-    if (lane == 0) ts[i] = acc;
+  for (int r0 = warp * kRows; r0 < nr; r0 += NW * kRows) {  // t = G x
+    const T *rp[kRows];
+    int nq[kRows];
+#pragma unroll
+    for (int u = 0; u < kRows; ++u) {
+      const int r = r0 + u;
+      rp[u] = G + tri_off(r < nr ? r : 0);
+      nq[u] = r < nr ? (r + 4) / 4 : 0;
+    }
+    T acc[kRows];
+    warp_rows_dot4<T>(rp, nq, xs, acc);
+    if (lane == 0) {
+#pragma unroll
+      for (int u = 0; u < kRows; ++u)
+        if (r0 + u < nr) ts[r0 + u] = acc[u];
+    }
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < nr; j += kRootThreads) {  // y = G^T t
-    T acc = 0;
-    for (int i = j; i < nr; ++i) acc += G[(long long)i * (i + 1) / 2 + j] * ts[i];
-    x[ridx[j]] = acc;
+  int CW, RG;
+  col_layout(nr, kRootThreads, CW, RG);
+  const int cl = threadIdx.x % CW, rg = threadIdx.x / CW;
+  for (int c0 = 0; c0 < nr; c0 += CW) {  // y = G^T t
+    const int col = c0 + cl;
+    T acc = T(0);
+    if (rg < RG && col < nr) {
+      const int i0 = col + ((rg - col % RG) % RG + RG) % RG;
+      for (int i = i0; i < nr; i += RG) acc += G[tri_off(i) + col] * ts[i];
+    }
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    if (rg == 0 && col < nr) {
+      T sum = part[cl];
+      for (int q = 1; q < RG; ++q) sum += part[q * CW + cl];
+      x[ridx[col]] = sum;
+    }
+    __syncthreads();
   }
 }
 
@@ -196,11 +400,12 @@ int apply_levels(Handle *h, const FactorValues<T> &fv, T *x, cudaStream_t s) {
   HIF_TRY(set_smem_limits<T>());
   const size_t lim = 200 * 1024;
   for (const LevelDev &lv : h->lv)
-    if ((size_t)(lv.max_nI + lv.max_nB) * sizeof(T) > lim || (size_t)lv.max_ng * sizeof(T) > lim) {
+    if ((size_t)(lv.max_nI + lv.max_nB + 8 * kCellBwdThreads) * sizeof(T) > lim ||
+        (size_t)(lv.max_ng + kGroupThreads) * sizeof(T) > lim) {
       set_last_error("a box of the factor exceeds the shared-memory staging limit");
       return HIF_EINVAL;
     }
-  if (2 * (size_t)h->root_n * sizeof(T) > lim) {
+  if ((2 * (size_t)pad4(h->root_n) + kRootThreads) * sizeof(T) > lim) {
     set_last_error("root block exceeds the shared-memory staging limit");
     return HIF_EINVAL;
   }
@@ -208,12 +413,13 @@ int apply_levels(Handle *h, const FactorValues<T> &fv, T *x, cudaStream_t s) {
   for (int l = 0; l < h->L; ++l) {
     const LevelDev &lv = h->lv[l];
     if (lv.ncells) {
-      size_t sm = (size_t)lv.max_nI * sizeof(T);
+      size_t sm = (size_t)pad4(lv.max_nI) * sizeof(T);
       StatScope sc(h, "cell_fwd", l, (lv.vals_cell + lv.vec_cell_fwd + lv.contrib) * E + lv.idx_cell_fwd, s);
-      k_cell_fwd<T><<<lv.ncells, kCellThreads, sm, s>>>(lv.cells, h->idx, fv.vals, fv.contrib, x);
+      k_cell_fwd<T><<<lv.nfwd, kCellFwdThreads, sm, s>>>(lv.fwd, lv.cells, h->idx, fv.vals, fv.contrib,
+                                                          fv.xI, x);
     }
     if (lv.ngroups) {
-      size_t sm = (size_t)lv.max_ng * sizeof(T);
+      size_t sm = (size_t)pad4(lv.max_ng) * sizeof(T);
       StatScope sc(h, "group_fwd", l,
                    (lv.vals_group + lv.vec_group + lv.contrib) * E + lv.idx_group + lv.cslot_bytes, s);
       k_group_fwd<T><<<lv.ngroups, kGroupThreads, sm, s>>>(lv.groups, h->idx, h->cptr, h->cslot,
@@ -221,7 +427,7 @@ int apply_levels(Handle *h, const FactorValues<T> &fv, T *x, cudaStream_t s) {
     }
   }
   if (h->root_n > 0) {
-    size_t sm = 2 * (size_t)h->root_n * sizeof(T);
+    size_t sm = (2 * (size_t)pad4(h->root_n) + kRootThreads) * sizeof(T);
     const double nr = h->root_n;
     StatScope sc(h, "root", -1, (nr * (nr + 1) / 2 + 2 * nr) * E + 4 * nr, s);
     k_root<T><<<1, kRootThreads, sm, s>>>(h->root_n, h->idx + h->root_idx_off,
@@ -230,14 +436,14 @@ int apply_levels(Handle *h, const FactorValues<T> &fv, T *x, cudaStream_t s) {
   for (int l = h->L - 1; l >= 0; --l) {
     const LevelDev &lv = h->lv[l];
     if (lv.ngroups) {
-      size_t sm = (size_t)lv.max_ng * sizeof(T);
+      size_t sm = ((size_t)lv.max_ng + kGroupThreads) * sizeof(T);
       StatScope sc(h, "group_bwd", l, (lv.vals_group + lv.vec_group) * E + lv.idx_group_bwd, s);
       k_group_bwd<T><<<lv.ngroups, kGroupThreads, sm, s>>>(lv.groups, h->idx, fv.vals, x);
     }
     if (lv.ncells) {
-      size_t sm = (size_t)(lv.max_nI + lv.max_nB) * sizeof(T);
+      size_t sm = ((size_t)lv.max_nI + lv.max_nB + 8 * kCellBwdThreads) * sizeof(T);
       StatScope sc(h, "cell_bwd", l, (lv.vals_cell + lv.vec_cell_bwd) * E + lv.idx_cell_bwd, s);
-      k_cell_bwd<T><<<lv.ncells, kCellThreads, sm, s>>>(lv.cells, h->idx, fv.vals, x);
+      k_cell_bwd<T><<<lv.nbwd, kCellBwdThreads, sm, s>>>(lv.bwd, lv.cells, h->idx, fv.vals, fv.xI, x);
     }
   }
   HIF_CUDA_TRY(cudaGetLastError());

@@ -39,11 +39,22 @@ void set_last_error(const std::string &msg);
 //
 // The factor is stored level by level in the form the inverse apply consumes
 // (Eq. Ainv with R_l = E_l C_l K_l):
-//   cell c      : G = L^{-1} (packed lower, row i at offset i(i+1)/2) and
+//   cell c      : G = L^{-1} (packed lower by rows) and
 //                 V = A_BI A_II^{-1} (nB x nI row major);
 //   group g     : H = K_g^T C_g^T restricted to the group's DOFs (n x n row major);
 //   root        : G_r = L_r^{-1} (packed lower).
 // Index lists are int32 global DOF numbers (lexicographic grid order).
+//
+// Rows of every stored block are padded with zeros to a multiple of 4
+// elements and every block starts on a multiple of 4 elements, so rows start
+// on 16-byte boundaries in both the FP64 and the FP32 pool (vector loads):
+//   packed lower triangle: row i at tri_off(i), length pad4(i + 1);
+//   dense n x m row major: row stride pad4(m).
+__host__ __device__ inline long long pad4(long long n) { return (n + 3) & ~3LL; }
+__host__ __device__ inline long long tri_off(long long i) {
+  const long long q = i >> 2, r = i & 3;
+  return 8 * q * (q + 1) + 4 * r * (q + 1);
+}
 
 struct CellDesc {
   int nI, nB;
@@ -67,8 +78,16 @@ struct LevelHost {
   long long contrib_slots = 0;  // sum of nB over the level's cells
 };
 
+// One CTA's share of a level's cell work: rows [a, b) of the stacked [V; G]
+// of a cell in the forward sweep, columns [a, b) of the cell in the backward.
+struct CellItem {
+  int cell, a, b, pad;
+};
+
 struct LevelDev {
   int ncells = 0, ngroups = 0;
+  int nfwd = 0, nbwd = 0;             // work items of the cell kernels
+  CellItem *fwd = nullptr, *bwd = nullptr;  // device
   int max_nI = 0, max_nB = 0, max_ng = 0;
   // algorithmic bytes per launch for one-byte-per-value accounting:
   // values read, indices read (4 B), vector entries read+written, contributions
@@ -83,6 +102,7 @@ struct FactorValues {
   T *vals = nullptr;       // device value pool
   T *contrib = nullptr;    // device contribution scratch
   T *work = nullptr;       // device work vector (N) for the reduced-precision apply
+  T *xI = nullptr;         // device N-vector: forward values of the cell interiors
 };
 
 }  // namespace hifcn
@@ -121,6 +141,10 @@ struct hif_handle {
 
   // PCG work space (FP64)
   double *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *g = nullptr;
+  double *xsol = nullptr;             // solution buffer of the graph-captured solve
+  void *pcg_graph[2] = {nullptr, nullptr};  // captured PCG loop per apply precision
+  cudaStream_t cap_stream = nullptr;  // private stream used for graph capture
+  bool use_graph = true;
   double *partials = nullptr;  // per-block partial sums
   double *scal = nullptr;      // device scalars (see pcg.cu)
   double *host_scal = nullptr; // pinned host mirror
@@ -170,7 +194,10 @@ int build_device_factor(Handle *h, const std::vector<double> &vals64, cudaStream
 int apply_inverse(Handle *h, const double *x, double *y, int precision, cudaStream_t s);
 int pcg(Handle *h, const double *b, double *x, int *iters, double *relres, cudaStream_t s);
 int cn(Handle *h, const double *u, const double *r, double *u1, int *iters, cudaStream_t s);
+int cn_batched(Handle *const *hs, int count, const double *const *u, const double *const *r,
+               double *const *u1, int *iters, cudaStream_t s);
 int gpu_setup(Handle *h, const double *a_nodes, cudaStream_t s);
+void destroy_pcg_graphs(Handle *h);
 int alloc_work(Handle *h);
 
 inline int grid_levels(int n, int leaf) {

@@ -14,13 +14,14 @@ namespace hifcn {
 
 int cn_rhs(Handle *h, const double *u, const double *r, double *g, cudaStream_t s);
 int apply_inplace_f64(Handle *h, double *x, cudaStream_t s);
+extern "C" int64_t hif_launch_count(void);
 int apply_inplace_f32(Handle *h, float *x, cudaStream_t s);
 
 namespace {
 
 constexpr int NT = 256;
 // device scalar slots
-enum { S_RZ = 0, S_ALPHA, S_BETA, S_RR, S_BB, S_PQ, S_CONV, S_COUNT };
+enum { S_RZ = 0, S_ALPHA, S_BETA, S_RR, S_BB, S_PQ, S_CONV, S_IT, S_COUNT };
 
 struct StencilArgs {
   const double *diag, *wx, *wy, *wz;
@@ -161,6 +162,196 @@ __global__ void __launch_bounds__(NT) k_start(const double *__restrict__ b, doub
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
+// ---------------------------------------------------------- graph-captured loop
+//
+// The whole solve is one CUDA graph: a prologue (x = 0, r = b, z = b, b.b)
+// followed by a conditional `while` node whose body is one PCG iteration
+// ordered as  z = F^{-1} r; rz' = r.z; beta; p = z + beta p; q = A p; alpha;
+// x += alpha p; r -= alpha q; [r = b - A x every period]; r.r; continue while
+// ||r|| > tol ||b|| and it < maxit.  The body's last kernel sets the condition,
+// so no iteration returns to the host.  Arithmetic is the same as the host loop.
+
+// prologue scalar phase: b.b, counters, and the loop condition (b != 0)
+__global__ void k_scalar_start(double *__restrict__ s, const double *__restrict__ part, int np,
+                               cudaGraphConditionalHandle cond) {
+  double v = warp_sum_partials(part, np);
+  if (threadIdx.x != 0) return;
+  s[S_BB] = v;
+  s[S_RZ] = 0.0;
+  s[S_IT] = 0.0;
+  s[S_CONV] = 0.0;
+  s[S_RR] = v;
+  cudaGraphSetConditional(cond, v > 0.0 ? 1u : 0u);
+}
+
+// rz' -> beta (0 on the first iteration), rz
+__global__ void k_scalar_beta(double *__restrict__ s, const double *__restrict__ part, int np) {
+  double v = warp_sum_partials(part, np);
+  if (threadIdx.x != 0) return;
+  s[S_BETA] = s[S_IT] == 0.0 ? 0.0 : v / s[S_RZ];
+  s[S_RZ] = v;
+}
+
+// p = z + beta p, with p = z on the first iteration (p is not read then)
+template <typename TZ>
+__global__ void __launch_bounds__(NT) k_update_p_dev(double *__restrict__ p, const TZ *__restrict__ z,
+                                                     const double *__restrict__ s, long long N) {
+  const bool first = s[S_IT] == 0.0;
+  const double beta = s[S_BETA];
+  for (long long j = blockIdx.x * (long long)NT + threadIdx.x; j < N; j += (long long)gridDim.x * NT)
+    p[j] = first ? (double)z[j] : (double)z[j] + beta * p[j];
+}
+
+// every `period` iterations: r = b - A x (true residual), z-input = r, partial r.r
+template <typename TZ>
+__global__ void __launch_bounds__(NT) k_true_residual_periodic(const double *__restrict__ b,
+                                                               const double *__restrict__ x,
+                                                               double *__restrict__ r,
+                                                               TZ *__restrict__ zin, StencilArgs st,
+                                                               const double *__restrict__ s, int period,
+                                                               double *__restrict__ part) {
+  const int it = (int)s[S_IT] + 1;  // iteration that just updated x
+  if (period <= 0 || it % period != 0) return;
+  __shared__ double sm[NT / 32];
+  double acc = 0.0;
+  for (long long j = blockIdx.x * (long long)NT + threadIdx.x; j < st.N; j += (long long)gridDim.x * NT) {
+    double rj = b[j] - stencil_row(x, st.diag, st.wx, st.wy, st.wz, st.dim, st.n, j);
+    r[j] = rj;
+    zin[j] = (TZ)rj;
+    acc += rj * rj;
+  }
+  double t = block_sum<NT>(acc, sm);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// r.r -> convergence; it += 1; loop condition
+__global__ void k_scalar_cond(double *__restrict__ s, const double *__restrict__ part, int np,
+                              double tol2, int maxit, cudaGraphConditionalHandle cond) {
+  double v = warp_sum_partials(part, np);
+  if (threadIdx.x != 0) return;
+  s[S_RR] = v;
+  const double it = s[S_IT] + 1.0;
+  s[S_IT] = it;
+  const bool conv = v <= tol2 * s[S_BB];
+  s[S_CONV] = conv ? 1.0 : 0.0;
+  cudaGraphSetConditional(cond, (!conv && it < (double)maxit) ? 1u : 0u);
+}
+
+struct PcgGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  long long prologue = 0, body = 0;  // kernel launches
+};
+
+template <typename TZ>
+int build_pcg_graph(Handle *h, TZ *z, PcgGraph *G) {
+  if (!h->cap_stream) HIF_CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  cudaStream_t cs = h->cap_stream;
+  const int nb = h->nblocks_vec;
+  const long long N = h->N;
+  double *part = h->partials;
+  double *sc = h->scal;
+  StencilArgs st{h->diag, h->wx, h->wy, h->wz, h->grid.dim, h->grid.n, N};
+  const double tol2 = h->opt.cg_tol * h->opt.cg_tol;
+  // one uncaptured apply sets the kernels' shared-memory attributes
+  if constexpr (sizeof(TZ) == 8) HIF_TRY(apply_inplace_f64(h, (double *)z, cs));
+  else HIF_TRY(apply_inplace_f32(h, (float *)z, cs));
+  HIF_CUDA_TRY(cudaStreamSynchronize(cs));
+  const bool stats = h->stats_on;
+  h->stats_on = false;
+  const long long lc0 = hif_launch_count();
+  HIF_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  cudaGraph_t graph = nullptr;
+  cudaStreamCaptureStatus cst;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t ndeps = 0;
+  cudaGraphConditionalHandle cond;
+  HIF_CUDA_TRY(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &graph, &deps, nullptr, &ndeps));
+  HIF_CUDA_TRY(cudaGraphConditionalHandleCreate(&cond, graph, 0, cudaGraphCondAssignDefault));
+  k_start<TZ><<<nb, NT, 0, cs>>>(h->g, h->xsol, h->r, z, N, part);
+  k_scalar_start<<<1, 32, 0, cs>>>(sc, part, nb, cond);
+  HIF_CUDA_TRY(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &graph, &deps, nullptr, &ndeps));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode;
+  HIF_CUDA_TRY(cudaGraphAddNode(&cnode, graph, deps, nullptr, ndeps, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  HIF_CUDA_TRY(cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+  HIF_CUDA_TRY(cudaStreamEndCapture(cs, &G->graph));
+  const long long lc1 = hif_launch_count();
+  // body: one iteration
+  HIF_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  int st_apply;
+  if constexpr (sizeof(TZ) == 8) st_apply = apply_inplace_f64(h, (double *)z, cs);
+  else st_apply = apply_inplace_f32(h, (float *)z, cs);
+  k_dot<TZ><<<nb, NT, 0, cs>>>(h->r, z, N, part);
+  k_scalar_beta<<<1, 32, 0, cs>>>(sc, part, nb);
+  k_update_p_dev<TZ><<<nb, NT, 0, cs>>>(h->p, z, sc, N);
+  k_spmv_dot<<<nb, NT, 0, cs>>>(h->p, h->q, st, part);
+  k_scalar<<<1, 32, 0, cs>>>(sc, part, nb, 0, tol2);
+  k_update_xr<TZ><<<nb, NT, 0, cs>>>(h->xsol, h->r, h->p, h->q, z, sc, N, part);
+  k_true_residual_periodic<TZ><<<nb, NT, 0, cs>>>(h->g, h->xsol, h->r, z, st, sc,
+                                                  h->opt.true_res_period, part);
+  k_scalar_cond<<<1, 32, 0, cs>>>(sc, part, nb, tol2, h->opt.cg_maxit, cond);
+  note_launch(8);
+  cudaGraph_t body_out = nullptr;
+  cudaError_t e_end = cudaStreamEndCapture(cs, &body_out);
+  const long long lc2 = hif_launch_count();
+  h->stats_on = stats;
+  HIF_TRY(st_apply);
+  HIF_CUDA_TRY(e_end);
+  HIF_CUDA_TRY(cudaGraphInstantiate(&G->exec, G->graph, 0));
+  G->prologue = 2;
+  G->body = lc2 - lc1;
+  note_launch(-(int)(lc2 - lc0));  // capture is not execution
+  return HIF_OK;
+}
+
+template <typename TZ>
+int ensure_pcg_graph(Handle *h, TZ *z, int slot, cudaStream_t s) {
+  if (h->pcg_graph[slot]) return HIF_OK;
+  HIF_CUDA_TRY(cudaStreamSynchronize(s));  // the capture stream does not order with s
+  PcgGraph *G = new PcgGraph();
+  int st = build_pcg_graph<TZ>(h, z, G);
+  if (st != HIF_OK) {
+    if (G->exec) cudaGraphExecDestroy(G->exec);
+    if (G->graph) cudaGraphDestroy(G->graph);
+    delete G;
+    return st;
+  }
+  h->pcg_graph[slot] = G;
+  return HIF_OK;
+}
+
+// enqueue the captured solve and the read-back of its scalars on s
+int pcg_graph_launch(Handle *h, int slot, cudaStream_t s) {
+  PcgGraph *G = static_cast<PcgGraph *>(h->pcg_graph[slot]);
+  HIF_CUDA_TRY(cudaGraphLaunch(G->exec, s));
+  HIF_CUDA_TRY(cudaMemcpyAsync(h->host_scal, h->scal, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+  return HIF_OK;
+}
+
+// after the stream completed: iteration count and status from the scalars
+int pcg_graph_finish(Handle *h, int slot, int *iters_out) {
+  PcgGraph *G = static_cast<PcgGraph *>(h->pcg_graph[slot]);
+  const int it = (int)h->host_scal[S_IT];
+  note_launch((int)(G->prologue + (long long)it * G->body));
+  if (iters_out) *iters_out = it;
+  if (h->host_scal[S_BB] == 0.0) return HIF_OK;
+  return h->host_scal[S_CONV] != 0.0 ? HIF_OK : HIF_ENOCONV;
+}
+
+template <typename TZ>
+int pcg_graph_impl(Handle *h, TZ *z, int slot, int *iters_out, cudaStream_t s) {
+  HIF_TRY(ensure_pcg_graph<TZ>(h, z, slot, s));
+  HIF_TRY(pcg_graph_launch(h, slot, s));
+  HIF_CUDA_TRY(cudaStreamSynchronize(s));
+  return pcg_graph_finish(h, slot, iters_out);
+}
+
 template <typename TZ>
 int pcg_impl(Handle *h, const double *b, double *x, TZ *z, int *iters_out, double *relres_out,
              cudaStream_t s) {
@@ -242,14 +433,110 @@ int pcg_impl(Handle *h, const double *b, double *x, TZ *z, int *iters_out, doubl
 }  // namespace
 
 int pcg(Handle *h, const double *b, double *x, int *iters, double *relres, cudaStream_t s) {
-  if (h->opt.precision == HIF_FP32 && h->has_f32) return pcg_impl<float>(h, b, x, h->f32.work, iters, relres, s);
-  return pcg_impl<double>(h, b, x, h->z, iters, relres, s);
+  const bool f32 = h->opt.precision == HIF_FP32 && h->has_f32;
+  if (!h->use_graph || h->stats_on) {
+    if (f32) return pcg_impl<float>(h, b, x, h->f32.work, iters, relres, s);
+    return pcg_impl<double>(h, b, x, h->z, iters, relres, s);
+  }
+  if (b != h->g)
+    HIF_CUDA_TRY(cudaMemcpyAsync(h->g, b, h->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  int st = f32 ? pcg_graph_impl<float>(h, h->f32.work, 1, iters, s)
+               : pcg_graph_impl<double>(h, h->z, 0, iters, s);
+  if (st != HIF_OK && st != HIF_ENOCONV) return st;
+  HIF_CUDA_TRY(cudaMemcpyAsync(x, h->xsol, h->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  note_launch();
+  if (relres) {
+    const int nb = h->nblocks_vec;
+    StencilArgs sta{h->diag, h->wx, h->wy, h->wz, h->grid.dim, h->grid.n, h->N};
+    k_resid_norm<<<nb, NT, 0, s>>>(h->g, h->xsol, sta, h->partials);
+    k_scalar<<<1, 32, 0, s>>>(h->scal, h->partials, nb, 1, h->opt.cg_tol * h->opt.cg_tol);
+    note_launch(2);
+    HIF_CUDA_TRY(cudaMemcpyAsync(h->host_scal, h->scal, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+    HIF_CUDA_TRY(cudaStreamSynchronize(s));
+    *relres = h->host_scal[S_BB] > 0.0 ? sqrt(h->host_scal[S_RR] / h->host_scal[S_BB]) : 0.0;
+  }
+  return st;
 }
 
 int cn(Handle *h, const double *u, const double *r, double *u1, int *iters, cudaStream_t s) {
   // g = (I + dt/2 M) u + dt r into the handle's RHS buffer, then A u1 = g.
   HIF_TRY(cn_rhs(h, u, r, h->g, s));
   return pcg(h, h->g, u1, iters, nullptr, s);
+}
+
+// Several CN steps, one per handle, overlapped on the GPU: each handle's
+// RHS kernel, captured solve and result copy run on the handle's own stream,
+// which first waits for the caller's stream; the call returns when all are
+// done.  A handle listed twice runs its steps in list order.
+int cn_batched(Handle *const *hs, int count, const double *const *u, const double *const *r,
+               double *const *u1, int *iters, cudaStream_t s) {
+  std::vector<int> status(count, HIF_OK);
+  for (int i = 0; i < count; ++i) {
+    Handle *h = hs[i];
+    if (!h->use_graph || h->stats_on) {  // statistics mode: plain sequential steps
+      int it = 0;
+      status[i] = cn(h, u[i], r ? r[i] : nullptr, u1[i], &it, s);
+      if (iters) iters[i] = it;
+      continue;
+    }
+    const bool f32 = h->opt.precision == HIF_FP32 && h->has_f32;
+    if (f32) HIF_TRY(ensure_pcg_graph<float>(h, h->f32.work, 1, s));
+    else HIF_TRY(ensure_pcg_graph<double>(h, h->z, 0, s));
+  }
+  cudaEvent_t ev;
+  HIF_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  cudaEventRecord(ev, s);
+  for (int i = 0; i < count; ++i) {
+    Handle *h = hs[i];
+    if (!h->use_graph || h->stats_on) continue;
+    const int slot = (h->opt.precision == HIF_FP32 && h->has_f32) ? 1 : 0;
+    cudaStream_t hs_ = h->cap_stream;
+    HIF_CUDA_TRY(cudaStreamWaitEvent(hs_, ev, 0));
+    HIF_TRY(cn_rhs(h, u[i], r ? r[i] : nullptr, h->g, hs_));
+    HIF_TRY(pcg_graph_launch(h, slot, hs_));
+    HIF_CUDA_TRY(cudaMemcpyAsync(u1[i], h->xsol, h->N * sizeof(double), cudaMemcpyDeviceToDevice, hs_));
+    // a handle listed again later must see this step's scalars before they are overwritten
+    bool again = false;
+    for (int j = i + 1; j < count && !again; ++j) again = hs[j] == h;
+    if (again) {
+      HIF_CUDA_TRY(cudaStreamSynchronize(hs_));
+      status[i] = pcg_graph_finish(h, slot, iters ? &iters[i] : nullptr);
+      status[i] = status[i] == HIF_OK ? -100 : status[i];  // marks "already finished"
+    }
+  }
+  int result = HIF_OK;
+  for (int i = 0; i < count; ++i) {
+    Handle *h = hs[i];
+    if (!h->use_graph || h->stats_on) {
+      if (status[i] != HIF_OK && result == HIF_OK) result = status[i];
+      continue;
+    }
+    int st = status[i];
+    if (st == -100) {
+      st = HIF_OK;
+    } else if (st == HIF_OK) {
+      HIF_CUDA_TRY(cudaStreamSynchronize(h->cap_stream));
+      const int slot = (h->opt.precision == HIF_FP32 && h->has_f32) ? 1 : 0;
+      st = pcg_graph_finish(h, slot, iters ? &iters[i] : nullptr);
+    }
+    note_launch(2);  // RHS kernel and result copy
+    if (st != HIF_OK && result == HIF_OK) result = st;
+  }
+  cudaEventDestroy(ev);
+  return result;
+}
+
+void destroy_pcg_graphs(Handle *h) {
+  for (int i = 0; i < 2; ++i) {
+    PcgGraph *G = static_cast<PcgGraph *>(h->pcg_graph[i]);
+    if (!G) continue;
+    if (G->exec) cudaGraphExecDestroy(G->exec);
+    if (G->graph) cudaGraphDestroy(G->graph);
+    delete G;
+    h->pcg_graph[i] = nullptr;
+  }
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  h->cap_stream = nullptr;
 }
 
 }  // namespace hifcn

@@ -224,19 +224,19 @@ __global__ void __launch_bounds__(NT) k_cell_eliminate(const SCell *__restrict__
     const double dinv = 1.0 / row[i];
     for (int cc = threadIdx.x; cc <= i; cc += NT) {
       double acc = (cc == i) ? 1.0 : 0.0;
-      for (int k = cc; k < i; ++k) acc -= row[k] * G[(long long)k * (k + 1) / 2 + cc];
-      G[(long long)i * (i + 1) / 2 + cc] = acc * dinv;
+      for (int k = cc; k < i; ++k) acc -= row[k] * G[tri_off(k) + cc];
+      G[tri_off(i) + cc] = acc * dinv;
     }
     __syncthreads();
   }
   // V[b][cc] = sum_{i >= cc} W^T[b][i] G[i][cc], W^T = A[nI + b][i]
   double *V = vals + c.V_off;
-  const long long nv = (long long)nB * nI;
+  const long long nv = (long long)nB * nI, vs = pad4(nI);
   for (long long t = threadIdx.x; t < nv; t += NT) {
     int b = (int)(t % nB), cc = (int)(t / nB);
     double acc = 0.0;
-    for (int i = cc; i < nI; ++i) acc += A[nI + b + (long long)i * nn] * G[(long long)i * (i + 1) / 2 + cc];
-    V[(long long)b * nI + cc] = acc;
+    for (int i = cc; i < nI; ++i) acc += A[nI + b + (long long)i * nn] * G[tri_off(i) + cc];
+    V[(long long)b * vs + cc] = acc;
   }
   // symmetrize the Schur complement block (upper <- lower)
   const long long nbb = (long long)nB * nB;
@@ -364,7 +364,8 @@ __global__ void __launch_bounds__(NT) k_group_h_jacobi(const SGroup *__restrict_
                                                        double *__restrict__ vals) {
   const SGroup g = groups[list[blockIdx.x]];
   const long long nn = (long long)g.n * g.n;
-  for (long long t = threadIdx.x; t < nn; t += NT) vals[g.H_off + t] = Linv[g.Linv_off + t];
+  for (long long t = threadIdx.x; t < nn; t += NT)
+    vals[g.H_off + (t / g.n) * pad4(g.n) + t % g.n] = Linv[g.Linv_off + t];
 }
 
 // -------------------------------------------------------------- skeletonization
@@ -552,7 +553,7 @@ __global__ void __launch_bounds__(NT) k_skel(const SSkel *__restrict__ sk, const
       acc += Kq[(long long)a * n + b] * Li[(long long)qb * n + col];
     }
     int qa = a < nr ? perm[k + a] : perm[a - nr];
-    H[(long long)qa * n + col] = acc;
+    H[(long long)qa * pad4(n) + col] = acc;
   }
   // (h) X into the owner cell's diagonal block at the skeleton positions
   {
@@ -781,9 +782,9 @@ int gpu_setup(Handle *h, const double *a_nodes, cudaStream_t s) {
       C.F_off = foff;
       foff += nn * nn;
       C.G_off = voff;
-      voff += (long long)C.nI * (C.nI + 1) / 2;
+      voff += tri_off(C.nI);
       C.V_off = voff;
-      voff += (long long)C.nB * C.nI;
+      voff += (long long)C.nB * pad4(C.nI);
       C.S_off = soff;
       soff += (long long)C.nB * C.nB;
       C.dofs_off = (long long)cdofs.size();
@@ -808,11 +809,12 @@ int gpu_setup(Handle *h, const double *a_nodes, cudaStream_t s) {
       G.D_off = loff;
       loff += (long long)G.n * G.n;
       G.H_off = hoff;
-      hoff += (long long)G.n * G.n;
+      hoff += (long long)G.n * pad4(G.n);
     }
     level_nvals[l] = hoff;
     HIF_TRY(keep.alloc(&level_vals[l], hoff));
     double *vals = level_vals[l];
+    HIF_CUDA_TRY(cudaMemsetAsync(vals, 0, std::max<long long>(hoff, 1) * sizeof(double), s));  // row padding
 
     double *F = nullptr;
     SCell *dcells = nullptr;

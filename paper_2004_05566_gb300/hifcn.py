@@ -27,7 +27,7 @@ HIF_FP64, HIF_FP32 = 0, 1
 EXPORTED = ("hif_default_options", "hif_setup", "hif_import_factor", "hif_export_factor",
             "hif_apply", "hif_matvec", "pcg_solve", "cn_step", "hif_set_reaction", "hif_query",
             "hif_destroy", "hif_strerror", "hif_last_error", "hif_stats_enable", "hif_stats_read",
-            "hif_launch_count", "hif_apply_noalloc")
+            "hif_launch_count", "hif_apply_noalloc", "cn_step_batched")
 
 
 class HifGrid(ctypes.Structure):
@@ -90,6 +90,9 @@ def lib():
     L.hif_launch_count.restype = c_int64
     L.hif_apply_noalloc.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
     L.hif_apply_noalloc.restype = c_int
+    L.cn_step_batched.argtypes = [POINTER(c_void_p), c_int, POINTER(c_void_p), POINTER(c_void_p),
+                                  POINTER(c_void_p), POINTER(c_int), c_void_p]
+    L.cn_step_batched.restype = c_int
     for name in ("hif_setup", "hif_import_factor", "hif_export_factor", "hif_apply", "hif_matvec",
                  "pcg_solve", "cn_step", "hif_set_reaction", "hif_query", "hif_destroy",
                  "hif_stats_enable", "hif_stats_read"):
@@ -246,6 +249,28 @@ def cn_step(h: Handle, u: torch.Tensor, r: torch.Tensor = None, out: torch.Tenso
     _check("cn_step", lib().cn_step(h.ptr, _vec(u, h.N, "u"), rp, _vec(out, h.N, "out"), byref(it),
                                     _stream(stream)))
     return out, it.value
+
+
+def cn_step_batched(hs, us, rs=None, outs=None, stream=None):
+    """One CN step for each handle (independent problems, overlapped on the GPU).
+
+    hs: list of Handles; us: list of device vectors; rs: list (entries may be
+    None) or None; outs: list of outputs or None (allocated here by torch).
+    Returns (outs, iters)."""
+    n = len(hs)
+    if len(us) != n or (rs is not None and len(rs) != n):
+        raise ValueError("hs, us and rs must have the same length")
+    if outs is None:
+        outs = [torch.empty_like(u) for u in us]
+    H = (c_void_p * n)(*[h.ptr for h in hs])
+    U = (c_void_p * n)(*[_vec(u, h.N, "u") for u, h in zip(us, hs)])
+    O = (c_void_p * n)(*[_vec(o, h.N, "out") for o, h in zip(outs, hs)])
+    R = None
+    if rs is not None:
+        R = (c_void_p * n)(*[(_vec(r, h.N, "r") if r is not None else None) for r, h in zip(rs, hs)])
+    it = (c_int * n)()
+    _check("cn_step_batched", lib().cn_step_batched(H, n, U, R, O, it, _stream(stream)))
+    return outs, list(it)
 
 
 def hif_set_reaction(h: Handle, kind: int, k1: float = 1.0, k2: float = math.inf):
