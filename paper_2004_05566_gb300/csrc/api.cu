@@ -7,6 +7,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <cstdlib>
 #include <map>
 
 namespace hifcn {
@@ -93,6 +94,7 @@ int alloc_work(Handle *h) {
   HIF_TRY(dev_alloc(h, (void **)&h->xsol, N * sizeof(double)));
   HIF_TRY(dev_alloc(h, (void **)&h->partials, 4 * nb * sizeof(double)));
   HIF_TRY(dev_alloc(h, (void **)&h->scal, 16 * sizeof(double)));
+  HIF_CUDA_TRY(cudaMemset(h->scal, 0, 16 * sizeof(double)));  // includes the wait-expiry flag
   HIF_CUDA_TRY(cudaMallocHost((void **)&h->host_scal, 16 * sizeof(double)));
   return HIF_OK;
 }
@@ -175,6 +177,39 @@ int finish_device_factor(Handle *h, cudaStream_t s) {
     }
     D.nfwd = (int)fw.size();
     D.nbwd = (int)bw.size();
+    // chunk tables for the bulk-copy staged kernels: consecutive whole rows of
+    // the cell block [G rows | V rows] of at most kStageBytes bytes
+    for (int e = 0; e < 2; ++e) {
+      const long long cap = kStageBytes / (e == 0 ? 8 : 4);
+      std::vector<int2> of;
+      std::vector<int> tab;
+      for (const CellDesc &cd : H.cells) {
+        const long long vs = pad4(cd.nI);
+        auto roff = [&](int r) { return r < cd.nI ? tri_off(r) : tri_off(cd.nI) + (long long)(r - cd.nI) * vs; };
+        const int nrows = cd.nI + cd.nB;
+        int2 o{(int)tab.size(), 0};
+        tab.push_back(0);
+        int r = 0;
+        bool ok = nrows == 0 || vs <= cap;
+        while (ok && r < nrows) {
+          const long long start = roff(r);
+          int en = r + 1;
+          while (en < nrows && roff(en + 1) - start <= cap) ++en;
+          tab.push_back(en);
+          ++o.y;
+          r = en;
+        }
+        if (!ok) o.y = -1;
+        D.max_chunks = std::max(D.max_chunks, o.y);
+        of.push_back(o);
+      }
+      HIF_TRY(dev_alloc(h, (void **)&D.chunk_of[e], std::max<size_t>(1, of.size()) * sizeof(int2)));
+      HIF_TRY(dev_alloc(h, (void **)&D.chunk_tab[e], std::max<size_t>(1, tab.size()) * sizeof(int)));
+      if (!of.empty())
+        HIF_CUDA_TRY(cudaMemcpyAsync(D.chunk_of[e], of.data(), of.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+      if (!tab.empty())
+        HIF_CUDA_TRY(cudaMemcpyAsync(D.chunk_tab[e], tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    }
     HIF_TRY(dev_alloc(h, (void **)&D.fwd, std::max<size_t>(1, fw.size()) * sizeof(CellItem)));
     HIF_TRY(dev_alloc(h, (void **)&D.bwd, std::max<size_t>(1, bw.size()) * sizeof(CellItem)));
     if (!fw.empty())
@@ -268,6 +303,9 @@ int create_handle(const hif_grid *grid, const double *a_nodes, double dt, const 
     delete h;
     return HIF_EINVAL;
   }
+  // HIFCN_NO_TMA=1 selects the register-streaming leaf kernels (A/B measurement)
+  const char *no_tma = std::getenv("HIFCN_NO_TMA");
+  if (no_tma && no_tma[0] == '1') h->use_tma = false;
   int st = alloc_work(h);
   if (st == HIF_OK) st = stencil_init(h, a_nodes, s);
   if (st != HIF_OK) {

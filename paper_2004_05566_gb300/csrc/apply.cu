@@ -316,6 +316,300 @@ __global__ void __launch_bounds__(kCellBwdThreads) k_cell_bwd(const CellItem *__
   }
 }
 
+// ------------------------------------------------------------ TMA-staged cells
+//
+// For levels where every cell is one work item (the leaf level), a cell's
+// factor block [G rows | V rows] is contiguous and 16-byte aligned, so it is
+// streamed through shared memory with bulk asynchronous copies (TMA engine,
+// cp.async.bulk with completion on an mbarrier).  One producer warp issues
+// the copies of kStages chunks ahead (a chunk is a run of whole rows of at
+// most kStageBytes, from a table built on the host); eight consumer warps
+// compute on the chunk that has landed and release its stage through a
+// second mbarrier.  Every mbarrier wait is bounded: on expiry the kernel
+// records the failure in err and returns.
+
+constexpr int kStages = 4;
+constexpr int kConsumerWarps = 8;
+constexpr int kConsumers = kConsumerWarps * 32;
+constexpr int kTmaThreads = kConsumers + 32;
+constexpr long long kWaitLimit = 1LL << 22;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes,
+                                          unsigned long long *bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// true when the phase with the given parity completed; false after the limit
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+  const unsigned a = smem_u32(bar);
+  for (long long it = 0; it < kWaitLimit; ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void consumers_sync() {
+  asm volatile("bar.sync 1, %0;" ::"r"(kConsumers) : "memory");
+}
+
+// Row r of a cell block in memory order: G rows 0..nI-1, then V rows.
+__device__ __forceinline__ long long cell_row_off(int r, int nI, long long vs) {
+  return r < nI ? tri_off(r) : tri_off(nI) + (long long)(r - nI) * vs;
+}
+
+// Producer: lane 0 of the last warp streams the chunks of one cell.
+template <typename T>
+__device__ __forceinline__ void produce_chunks(const CellDesc &c, const T *vals, const int *cs, int nch,
+                                               unsigned char *stage, unsigned long long *full,
+                                               unsigned long long *empty, double *err) {
+  const long long vs = pad4(c.nI);
+  for (int k = 0; k < nch; ++k) {
+    const int sidx = k % kStages;
+    if (k >= kStages && !mbar_wait(&empty[sidx], (unsigned)(((k / kStages) - 1) & 1))) {
+      err[0] = 1.0;
+      return;
+    }
+    const long long a = cell_row_off(cs[k], c.nI, vs), b = cell_row_off(cs[k + 1], c.nI, vs);
+    bulk_load(stage + (size_t)sidx * kStageBytes, vals + c.G_off + a, (unsigned)((b - a) * sizeof(T)),
+              &full[sidx]);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTmaThreads) k_cell_fwd_tma(const CellDesc *__restrict__ cells,
+                                                              const int2 *__restrict__ chunk_of,
+                                                              const int *__restrict__ chunk_tab,
+                                                              const int *__restrict__ idx,
+                                                              const T *__restrict__ vals,
+                                                              T *__restrict__ contrib,
+                                                              T *__restrict__ xI,
+                                                              const T *__restrict__ x,
+                                                              double *__restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) unsigned long long full[kStages], empty[kStages];
+  unsigned char *stage = smem_raw;
+  T *xs = reinterpret_cast<T *>(smem_raw + (size_t)kStages * kStageBytes);
+  const CellDesc c = cells[blockIdx.x];
+  const int2 co = chunk_of[blockIdx.x];
+  const int *cs = chunk_tab + co.x;
+  const int nch = co.y;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < kStages; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], kConsumerWarps);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (nch < 0) {
+    if (threadIdx.x == 0) err[0] = 1.0;
+    return;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == kConsumerWarps) {
+    if (lane == 0) produce_chunks<T>(c, vals, cs, nch, stage, full, empty, err);
+    return;
+  }
+  const int *I = idx + c.I_off;
+  const int nIp = (int)pad4(c.nI);
+  const long long vs = nIp;
+  for (int i = threadIdx.x; i < nIp; i += kConsumers) xs[i] = i < c.nI ? x[I[i]] : T(0);
+  consumers_sync();
+  for (int k = 0; k < nch; ++k) {
+    const int sidx = k % kStages;
+    if (!mbar_wait(&full[sidx], (unsigned)((k / kStages) & 1))) {
+      if (lane == 0) err[0] = 1.0;
+      return;
+    }
+    const T *base = reinterpret_cast<const T *>(stage + (size_t)sidx * kStageBytes);
+    const int rb = cs[k], re = cs[k + 1];
+    const long long off0 = cell_row_off(rb, c.nI, vs);
+    for (int r0 = rb + warp * kRows; r0 < re; r0 += kConsumerWarps * kRows) {
+      const T *rp[kRows];
+      int nq[kRows];
+#pragma unroll
+      for (int u = 0; u < kRows; ++u) {
+        const int r = r0 + u;
+        if (r < re) {
+          rp[u] = base + (cell_row_off(r, c.nI, vs) - off0);
+          nq[u] = r < c.nI ? (r + 4) / 4 : nIp / 4;
+        } else {
+          rp[u] = base;
+          nq[u] = 0;
+        }
+      }
+      T acc[kRows];
+#pragma unroll
+      for (int u = 0; u < kRows; ++u) acc[u] = T(0);
+      int maxq = 0;
+#pragma unroll
+      for (int u = 0; u < kRows; ++u) maxq = nq[u] > maxq ? nq[u] : maxq;
+      for (int q = lane; q < maxq; q += 32) {
+        T xv[4];
+        ld4(xs + 4 * q, xv);
+#pragma unroll
+        for (int u = 0; u < kRows; ++u) {
+          if (q < nq[u]) {
+            T v[4];
+            ld4(rp[u] + 4 * q, v);
+            acc[u] += v[0] * xv[0] + v[1] * xv[1] + v[2] * xv[2] + v[3] * xv[3];
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kRows; ++u) acc[u] = warp_reduce(acc[u]);
+      if (lane == 0) {
+#pragma unroll
+        for (int u = 0; u < kRows; ++u) {
+          const int r = r0 + u;
+          if (r >= re) break;
+          if (r < c.nI) xI[I[r]] = acc[u];
+          else contrib[c.C_off + (r - c.nI)] = acc[u];
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[sidx]);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTmaThreads) k_cell_bwd_tma(const CellDesc *__restrict__ cells,
+                                                              const int2 *__restrict__ chunk_of,
+                                                              const int *__restrict__ chunk_tab,
+                                                              const int *__restrict__ idx,
+                                                              const T *__restrict__ vals,
+                                                              const T *__restrict__ xI,
+                                                              T *__restrict__ x,
+                                                              double *__restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) unsigned long long full[kStages], empty[kStages];
+  unsigned char *stage = smem_raw;
+  T *part = reinterpret_cast<T *>(smem_raw + (size_t)kStages * kStageBytes);  // 8 * kConsumers
+  T *xs = part + 8 * kConsumers;
+  const CellDesc c = cells[blockIdx.x];
+  T *xb = xs + c.nI;
+  const int2 co = chunk_of[blockIdx.x];
+  const int *cs = chunk_tab + co.x;
+  const int nch = co.y;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < kStages; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], kConsumerWarps);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (nch < 0) {
+    if (threadIdx.x == 0) err[0] = 1.0;
+    return;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == kConsumerWarps) {
+    if (lane == 0) produce_chunks<T>(c, vals, cs, nch, stage, full, empty, err);
+    return;
+  }
+  const int *I = idx + c.I_off;
+  const int *B = idx + c.B_off;
+  const long long vs = pad4(c.nI);
+  for (int i = threadIdx.x; i < c.nI; i += kConsumers) xs[i] = xI[I[i]];
+  for (int q = threadIdx.x; q < c.nB; q += kConsumers) xb[q] = x[B[q]];
+  consumers_sync();
+  const int nq = (int)(vs / 4);
+  const int npairs = (nq + 1) / 2;
+  int PW, RG;
+  col_layout(npairs, kConsumers, PW, RG);
+  const int pl = threadIdx.x % PW, rg = threadIdx.x / PW;
+  const int qa = pl, qb = nq - 1 - pl;
+  const bool okA = rg < RG && pl < npairs;
+  const bool okB = okA && qb > qa;
+  T aA[4] = {T(0), T(0), T(0), T(0)}, aB[4] = {T(0), T(0), T(0), T(0)};
+  for (int k = 0; k < nch; ++k) {
+    const int sidx = k % kStages;
+    if (!mbar_wait(&full[sidx], (unsigned)((k / kStages) & 1))) {
+      if (lane == 0) err[0] = 1.0;
+      return;
+    }
+    const T *base = reinterpret_cast<const T *>(stage + (size_t)sidx * kStageBytes);
+    const int rb = cs[k], re = cs[k + 1];
+    const long long off0 = cell_row_off(rb, c.nI, vs);
+    if (okA) {
+      for (int r = rb + ((rg - rb % RG) % RG + RG) % RG; r < re; r += RG) {
+        const T *row = base + (cell_row_off(r, c.nI, vs) - off0);
+        if (r < c.nI) {
+          const T xv = xs[r];
+          if (4 * qa <= r) {
+            T v[4];
+            ld4(row + 4 * qa, v);
+            aA[0] += v[0] * xv; aA[1] += v[1] * xv; aA[2] += v[2] * xv; aA[3] += v[3] * xv;
+          }
+          if (okB && 4 * qb <= r) {
+            T w[4];
+            ld4(row + 4 * qb, w);
+            aB[0] += w[0] * xv; aB[1] += w[1] * xv; aB[2] += w[2] * xv; aB[3] += w[3] * xv;
+          }
+        } else {
+          const T xv = xb[r - c.nI];
+          T v[4];
+          ld4(row + 4 * qa, v);
+          aA[0] -= v[0] * xv; aA[1] -= v[1] * xv; aA[2] -= v[2] * xv; aA[3] -= v[3] * xv;
+          if (okB) {
+            T w[4];
+            ld4(row + 4 * qb, w);
+            aB[0] -= w[0] * xv; aB[1] -= w[1] * xv; aB[2] -= w[2] * xv; aB[3] -= w[3] * xv;
+          }
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[sidx]);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    part[k * kConsumers + threadIdx.x] = aA[k];
+    part[(4 + k) * kConsumers + threadIdx.x] = aB[k];
+  }
+  consumers_sync();
+  if (rg == 0 && pl < npairs) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (k >= 4 && qb <= qa) break;
+      const int col = (k < 4 ? 4 * qa : 4 * qb) + (k & 3);
+      if (col >= c.nI) continue;
+      T sum = part[k * kConsumers + pl];
+      for (int g = 1; g < RG; ++g) sum += part[k * kConsumers + g * PW + pl];
+      x[I[col]] = sum;
+    }
+  }
+}
+
 // Root (Eq. 3_4): x_r <- G_r^T (G_r x_r).
 template <typename T>
 __global__ void __launch_bounds__(kRootThreads) k_root(int nr, const int *__restrict__ ridx,
@@ -391,8 +685,24 @@ int set_smem_limits() {
   HIF_CUDA_TRY(cudaFuncSetAttribute(k_group_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   HIF_CUDA_TRY(cudaFuncSetAttribute(k_group_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   HIF_CUDA_TRY(cudaFuncSetAttribute(k_root<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  HIF_CUDA_TRY(cudaFuncSetAttribute(k_cell_fwd_tma<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  HIF_CUDA_TRY(cudaFuncSetAttribute(k_cell_bwd_tma<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   done = true;
   return HIF_OK;
+}
+
+// The TMA-staged cell kernels serve levels whose cells are not split over
+// CTAs, whose rows fit one chunk and whose column pairs fit one pass.
+// FP64 applies are bound by the FP64 pipe, not by HBM; they keep the
+// register-streaming kernels, which measured faster there.
+bool use_tma(const Handle *h, const LevelDev &lv, size_t elem) {
+  if (elem != sizeof(float)) return false;
+  if (!h->use_tma || lv.nfwd != lv.ncells || lv.nbwd != lv.ncells || lv.max_chunks < 0) return false;
+  if ((size_t)pad4(lv.max_nI) * elem > (size_t)kStageBytes) return false;
+  if (pad4(lv.max_nI) / 4 > 2 * kConsumers) return false;
+  const size_t bwd_smem = (size_t)kStages * kStageBytes +
+                          ((size_t)lv.max_nI + lv.max_nB + 8 * kConsumers) * elem;
+  return bwd_smem <= 200 * 1024;
 }
 
 template <typename T>
@@ -413,10 +723,18 @@ int apply_levels(Handle *h, const FactorValues<T> &fv, T *x, cudaStream_t s) {
   for (int l = 0; l < h->L; ++l) {
     const LevelDev &lv = h->lv[l];
     if (lv.ncells) {
-      size_t sm = (size_t)pad4(lv.max_nI) * sizeof(T);
       StatScope sc(h, "cell_fwd", l, (lv.vals_cell + lv.vec_cell_fwd + lv.contrib) * E + lv.idx_cell_fwd, s);
-      k_cell_fwd<T><<<lv.nfwd, kCellFwdThreads, sm, s>>>(lv.fwd, lv.cells, h->idx, fv.vals, fv.contrib,
-                                                          fv.xI, x);
+      if (use_tma(h, lv, sizeof(T))) {
+        const int e = sizeof(T) == 8 ? 0 : 1;
+        size_t sm = (size_t)kStages * kStageBytes + (size_t)pad4(lv.max_nI) * sizeof(T);
+        k_cell_fwd_tma<T><<<lv.ncells, kTmaThreads, sm, s>>>(lv.cells, lv.chunk_of[e], lv.chunk_tab[e],
+                                                              h->idx, fv.vals, fv.contrib, fv.xI, x,
+                                                              h->scal + kScalErr);
+      } else {
+        size_t sm = (size_t)pad4(lv.max_nI) * sizeof(T);
+        k_cell_fwd<T><<<lv.nfwd, kCellFwdThreads, sm, s>>>(lv.fwd, lv.cells, h->idx, fv.vals, fv.contrib,
+                                                            fv.xI, x);
+      }
     }
     if (lv.ngroups) {
       size_t sm = (size_t)pad4(lv.max_ng) * sizeof(T);
@@ -441,9 +759,18 @@ int apply_levels(Handle *h, const FactorValues<T> &fv, T *x, cudaStream_t s) {
       k_group_bwd<T><<<lv.ngroups, kGroupThreads, sm, s>>>(lv.groups, h->idx, fv.vals, x);
     }
     if (lv.ncells) {
-      size_t sm = ((size_t)lv.max_nI + lv.max_nB + 8 * kCellBwdThreads) * sizeof(T);
       StatScope sc(h, "cell_bwd", l, (lv.vals_cell + lv.vec_cell_bwd) * E + lv.idx_cell_bwd, s);
-      k_cell_bwd<T><<<lv.nbwd, kCellBwdThreads, sm, s>>>(lv.bwd, lv.cells, h->idx, fv.vals, fv.xI, x);
+      if (use_tma(h, lv, sizeof(T))) {
+        const int e = sizeof(T) == 8 ? 0 : 1;
+        size_t sm = (size_t)kStages * kStageBytes +
+                    ((size_t)lv.max_nI + lv.max_nB + 8 * kConsumers) * sizeof(T);
+        k_cell_bwd_tma<T><<<lv.ncells, kTmaThreads, sm, s>>>(lv.cells, lv.chunk_of[e], lv.chunk_tab[e],
+                                                              h->idx, fv.vals, fv.xI, x,
+                                                              h->scal + kScalErr);
+      } else {
+        size_t sm = ((size_t)lv.max_nI + lv.max_nB + 8 * kCellBwdThreads) * sizeof(T);
+        k_cell_bwd<T><<<lv.nbwd, kCellBwdThreads, sm, s>>>(lv.bwd, lv.cells, h->idx, fv.vals, fv.xI, x);
+      }
     }
   }
   HIF_CUDA_TRY(cudaGetLastError());

@@ -51,6 +51,13 @@ void set_last_error(const std::string &msg);
 //   packed lower triangle: row i at tri_off(i), length pad4(i + 1);
 //   dense n x m row major: row stride pad4(m).
 __host__ __device__ inline long long pad4(long long n) { return (n + 3) & ~3LL; }
+
+// Slot of the handle's device scalar array that kernels set to 1 when a
+// bounded wait expired (reported as HIF_ETIMEOUT by the next solve).
+constexpr int kScalErr = 15;
+
+// Size of one shared-memory stage of the bulk-copy staged cell kernels.
+constexpr int kStageBytes = 16384;
 __host__ __device__ inline long long tri_off(long long i) {
   const long long q = i >> 2, r = i & 3;
   return 8 * q * (q + 1) + 4 * r * (q + 1);
@@ -88,6 +95,12 @@ struct LevelDev {
   int ncells = 0, ngroups = 0;
   int nfwd = 0, nbwd = 0;             // work items of the cell kernels
   CellItem *fwd = nullptr, *bwd = nullptr;  // device
+  // bulk-copy chunk tables of the cells (row boundaries), one per element size:
+  // cell c's chunks are rows [tab[o + k], tab[o + k + 1]) for k < n with
+  // (o, n) = chunk_of[c]
+  int2 *chunk_of[2] = {nullptr, nullptr};  // [0]: FP64, [1]: FP32
+  int *chunk_tab[2] = {nullptr, nullptr};
+  int max_chunks = 0;
   int max_nI = 0, max_nB = 0, max_ng = 0;
   // algorithmic bytes per launch for one-byte-per-value accounting:
   // values read, indices read (4 B), vector entries read+written, contributions
@@ -145,6 +158,7 @@ struct hif_handle {
   void *pcg_graph[2] = {nullptr, nullptr};  // captured PCG loop per apply precision
   cudaStream_t cap_stream = nullptr;  // private stream used for graph capture
   bool use_graph = true;
+  bool use_tma = true;                // bulk-copy staging of the leaf cell blocks
   double *partials = nullptr;  // per-block partial sums
   double *scal = nullptr;      // device scalars (see pcg.cu)
   double *host_scal = nullptr; // pinned host mirror

@@ -237,6 +237,15 @@ __global__ void k_scalar_cond(double *__restrict__ s, const double *__restrict__
   cudaGraphSetConditional(cond, (!conv && it < (double)maxit) ? 1u : 0u);
 }
 
+// A kernel reported an expired bounded wait: clear the flag, report it.
+int take_timeout(Handle *h) {
+  h->host_scal[kScalErr] = 0.0;
+  HIF_CUDA_TRY(cudaMemcpy(h->scal + kScalErr, &h->host_scal[kScalErr], sizeof(double),
+                          cudaMemcpyHostToDevice));
+  set_last_error("a bounded device wait expired in the HIF apply");
+  return HIF_ETIMEOUT;
+}
+
 struct PcgGraph {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -330,7 +339,7 @@ int ensure_pcg_graph(Handle *h, TZ *z, int slot, cudaStream_t s) {
 int pcg_graph_launch(Handle *h, int slot, cudaStream_t s) {
   PcgGraph *G = static_cast<PcgGraph *>(h->pcg_graph[slot]);
   HIF_CUDA_TRY(cudaGraphLaunch(G->exec, s));
-  HIF_CUDA_TRY(cudaMemcpyAsync(h->host_scal, h->scal, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+  HIF_CUDA_TRY(cudaMemcpyAsync(h->host_scal, h->scal, 16 * sizeof(double), cudaMemcpyDeviceToHost, s));
   return HIF_OK;
 }
 
@@ -340,6 +349,7 @@ int pcg_graph_finish(Handle *h, int slot, int *iters_out) {
   const int it = (int)h->host_scal[S_IT];
   note_launch((int)(G->prologue + (long long)it * G->body));
   if (iters_out) *iters_out = it;
+  if (h->host_scal[kScalErr] != 0.0) return take_timeout(h);
   if (h->host_scal[S_BB] == 0.0) return HIF_OK;
   return h->host_scal[S_CONV] != 0.0 ? HIF_OK : HIF_ENOCONV;
 }
@@ -370,7 +380,7 @@ int pcg_impl(Handle *h, const double *b, double *x, TZ *z, int *iters_out, doubl
   note_launch();
   k_scalar<<<1, 32, 0, s>>>(sc, part, nb, 4, tol2);
   note_launch();
-  HIF_CUDA_TRY(cudaMemcpyAsync(h->host_scal, sc, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+  HIF_CUDA_TRY(cudaMemcpyAsync(h->host_scal, sc, 16 * sizeof(double), cudaMemcpyDeviceToHost, s));
   HIF_CUDA_TRY(cudaStreamSynchronize(s));
   const double bb = h->host_scal[S_BB];
   if (bb == 0.0) {
@@ -402,8 +412,9 @@ int pcg_impl(Handle *h, const double *b, double *x, TZ *z, int *iters_out, doubl
     k_scalar<<<1, 32, 0, s>>>(sc, part, nb, 1, tol2);
     note_launch();
     HIF_CUDA_TRY(cudaGetLastError());
-    HIF_CUDA_TRY(cudaMemcpyAsync(h->host_scal, sc, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+    HIF_CUDA_TRY(cudaMemcpyAsync(h->host_scal, sc, 16 * sizeof(double), cudaMemcpyDeviceToHost, s));
     HIF_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h->host_scal[kScalErr] != 0.0) return take_timeout(h);
     if (h->host_scal[S_CONV] != 0.0) {
       conv = true;
       break;
@@ -422,7 +433,7 @@ int pcg_impl(Handle *h, const double *b, double *x, TZ *z, int *iters_out, doubl
     note_launch();
     k_scalar<<<1, 32, 0, s>>>(sc, part, nb, 1, tol2);
     note_launch();
-    HIF_CUDA_TRY(cudaMemcpyAsync(h->host_scal, sc, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+    HIF_CUDA_TRY(cudaMemcpyAsync(h->host_scal, sc, 16 * sizeof(double), cudaMemcpyDeviceToHost, s));
     HIF_CUDA_TRY(cudaStreamSynchronize(s));
     *relres_out = sqrt(h->host_scal[S_RR] / bb);
   }
@@ -451,7 +462,7 @@ int pcg(Handle *h, const double *b, double *x, int *iters, double *relres, cudaS
     k_resid_norm<<<nb, NT, 0, s>>>(h->g, h->xsol, sta, h->partials);
     k_scalar<<<1, 32, 0, s>>>(h->scal, h->partials, nb, 1, h->opt.cg_tol * h->opt.cg_tol);
     note_launch(2);
-    HIF_CUDA_TRY(cudaMemcpyAsync(h->host_scal, h->scal, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+    HIF_CUDA_TRY(cudaMemcpyAsync(h->host_scal, h->scal, 16 * sizeof(double), cudaMemcpyDeviceToHost, s));
     HIF_CUDA_TRY(cudaStreamSynchronize(s));
     *relres = h->host_scal[S_BB] > 0.0 ? sqrt(h->host_scal[S_RR] / h->host_scal[S_BB]) : 0.0;
   }

@@ -173,3 +173,26 @@ def test_full_size_fisher_1023_steps_satisfy_cn(H):
             u = un.reshape(u.shape)
             ut = u1
         h.close()
+
+
+@pytest.mark.slow
+def test_full_size_heat3d_127_steps_satisfy_cn(H):
+    """3D heat 127^3 (leaf 8, eps 1e-4, dt 0.1, face + edge skeletonization,
+    FP32 apply): each GPU step solves the CN system assembled by the oracle."""
+    import torch
+    w = W.config_heat3d_127()
+    A = grid.assemble_A(w.a_nodes, w.dt)
+    h = _setup(H, w, precision=1)
+    info = H.hif_query(h)
+    assert info["levels"] == 4 and info["root_size"] > 0
+    u = w.u0.copy()
+    ut = torch.from_numpy(u.ravel().copy()).cuda()
+    for _ in range(2):
+        u1, it = H.cn_step(h, ut)
+        g = grid.cn_rhs(w.a_nodes, u, w.dt, None).ravel()
+        un = u1.cpu().numpy()
+        assert np.linalg.norm(A @ un - g) <= 1.05e-10 * np.linalg.norm(g)
+        assert 1 <= it <= 12
+        u = un.reshape(u.shape)
+        ut = u1
+    h.close()
