@@ -177,6 +177,18 @@ int finish_device_factor(Handle *h, cudaStream_t s) {
     }
     D.nfwd = (int)fw.size();
     D.nbwd = (int)bw.size();
+    {
+      std::vector<int> sm, lg;
+      for (int g = 0; g < (int)H.groups.size(); ++g) (H.groups[g].n <= 32 ? sm : lg).push_back(g);
+      D.nsmall = (int)sm.size();
+      D.nlarge = (int)lg.size();
+      HIF_TRY(dev_alloc(h, (void **)&D.small_groups, std::max<size_t>(1, sm.size()) * sizeof(int)));
+      HIF_TRY(dev_alloc(h, (void **)&D.large_groups, std::max<size_t>(1, lg.size()) * sizeof(int)));
+      if (!sm.empty())
+        HIF_CUDA_TRY(cudaMemcpyAsync(D.small_groups, sm.data(), sm.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+      if (!lg.empty())
+        HIF_CUDA_TRY(cudaMemcpyAsync(D.large_groups, lg.data(), lg.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    }
     // chunk tables for the bulk-copy staged kernels: consecutive whole rows of
     // the cell block [G rows | V rows] of at most kStageBytes bytes
     for (int e = 0; e < 2; ++e) {

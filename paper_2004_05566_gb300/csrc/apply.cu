@@ -141,12 +141,12 @@ __global__ void __launch_bounds__(kCellFwdThreads) k_cell_fwd(const CellItem *__
 // Forward group step (K^T C^T): x_g <- H (x_g - sum of the cells' contributions).
 template <typename T>
 __global__ void __launch_bounds__(kGroupThreads) k_group_fwd(
-    const GroupDesc *__restrict__ groups, const int *__restrict__ idx,
+    const int *__restrict__ list, const GroupDesc *__restrict__ groups, const int *__restrict__ idx,
     const long long *__restrict__ cptr, const long long *__restrict__ cslot,
     const T *__restrict__ vals, const T *__restrict__ contrib, T *__restrict__ x) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *xs = reinterpret_cast<T *>(smem_raw);
-  const GroupDesc g = groups[blockIdx.x];
+  const GroupDesc g = groups[list[blockIdx.x]];
   const int *gi = idx + g.idx_off;
   const int np = (int)pad4(g.n);
   for (int i = threadIdx.x; i < np; i += kGroupThreads) {
@@ -181,6 +181,65 @@ __global__ void __launch_bounds__(kGroupThreads) k_group_fwd(
   }
 }
 
+// Separator entities with at most 32 DOFs: one warp per entity, eight per CTA.
+constexpr int kSmallWarps = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(kSmallWarps * 32) k_group_fwd_small(
+    const int *__restrict__ list, int count, const GroupDesc *__restrict__ groups,
+    const int *__restrict__ idx, const long long *__restrict__ cptr,
+    const long long *__restrict__ cslot, const T *__restrict__ vals,
+    const T *__restrict__ contrib, T *__restrict__ x) {
+  __shared__ __align__(16) T xs_all[kSmallWarps][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * kSmallWarps + warp;
+  if (t >= count) return;
+  const GroupDesc g = groups[list[t]];
+  const int *gi = idx + g.idx_off;
+  T *xs = xs_all[warp];
+  T v = T(0);
+  if (lane < g.n) {
+    v = x[gi[lane]];
+    const long long a = cptr[g.cptr_off + lane], b = cptr[g.cptr_off + lane + 1];
+    for (long long s = a; s < b; ++s) v -= contrib[cslot[s]];
+  }
+  xs[lane] = v;
+  __syncwarp();
+  if (lane < g.n) {
+    const int np = (int)pad4(g.n);
+    const T *row = vals + g.H_off + (long long)lane * np;
+    T acc = T(0);
+    for (int q = 0; q < np / 4; ++q) {
+      T w[4];
+      ld4(row + 4 * q, w);
+      acc += w[0] * xs[4 * q] + w[1] * xs[4 * q + 1] + w[2] * xs[4 * q + 2] + w[3] * xs[4 * q + 3];
+    }
+    x[gi[lane]] = acc;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSmallWarps * 32) k_group_bwd_small(
+    const int *__restrict__ list, int count, const GroupDesc *__restrict__ groups,
+    const int *__restrict__ idx, const T *__restrict__ vals, T *__restrict__ x) {
+  __shared__ T xs_all[kSmallWarps][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * kSmallWarps + warp;
+  if (t >= count) return;
+  const GroupDesc g = groups[list[t]];
+  const int *gi = idx + g.idx_off;
+  T *xs = xs_all[warp];
+  xs[lane] = lane < g.n ? x[gi[lane]] : T(0);
+  __syncwarp();
+  if (lane < g.n) {
+    const long long np = pad4(g.n);
+    const T *H = vals + g.H_off;
+    T acc = T(0);
+    for (int r = 0; r < g.n; ++r) acc += H[(long long)r * np + lane] * xs[r];
+    x[gi[lane]] = acc;
+  }
+}
+
 // Column-parallel transposed products: threads are (column unit, row group);
 // each thread sums its rows, the row groups are added in a fixed order.
 __device__ __forceinline__ void col_layout(int ncols, int nthreads, int &CW, int &RG) {
@@ -192,12 +251,13 @@ __device__ __forceinline__ void col_layout(int ncols, int nthreads, int &CW, int
 
 // Backward group step: x_g <- H^T x_g.
 template <typename T>
-__global__ void __launch_bounds__(kGroupThreads) k_group_bwd(const GroupDesc *__restrict__ groups,
+__global__ void __launch_bounds__(kGroupThreads) k_group_bwd(const int *__restrict__ list,
+                                                             const GroupDesc *__restrict__ groups,
                                                              const int *__restrict__ idx,
                                                              const T *__restrict__ vals,
                                                              T *__restrict__ x) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const GroupDesc g = groups[blockIdx.x];
+  const GroupDesc g = groups[list[blockIdx.x]];
   T *xs = reinterpret_cast<T *>(smem_raw);
   T *part = xs + g.n;
   const int *gi = idx + g.idx_off;
@@ -740,8 +800,13 @@ int apply_levels(Handle *h, const FactorValues<T> &fv, T *x, cudaStream_t s) {
       size_t sm = (size_t)pad4(lv.max_ng) * sizeof(T);
       StatScope sc(h, "group_fwd", l,
                    (lv.vals_group + lv.vec_group + lv.contrib) * E + lv.idx_group + lv.cslot_bytes, s);
-      k_group_fwd<T><<<lv.ngroups, kGroupThreads, sm, s>>>(lv.groups, h->idx, h->cptr, h->cslot,
-                                                           fv.vals, fv.contrib, x);
+      if (lv.nsmall)
+        k_group_fwd_small<T><<<(lv.nsmall + kSmallWarps - 1) / kSmallWarps, kSmallWarps * 32, 0, s>>>(
+            lv.small_groups, lv.nsmall, lv.groups, h->idx, h->cptr, h->cslot, fv.vals, fv.contrib, x);
+      if (lv.nlarge)
+        k_group_fwd<T><<<lv.nlarge, kGroupThreads, sm, s>>>(lv.large_groups, lv.groups, h->idx, h->cptr,
+                                                            h->cslot, fv.vals, fv.contrib, x);
+      if (lv.nsmall && lv.nlarge) note_launch();
     }
   }
   if (h->root_n > 0) {
@@ -756,7 +821,12 @@ int apply_levels(Handle *h, const FactorValues<T> &fv, T *x, cudaStream_t s) {
     if (lv.ngroups) {
       size_t sm = ((size_t)lv.max_ng + kGroupThreads) * sizeof(T);
       StatScope sc(h, "group_bwd", l, (lv.vals_group + lv.vec_group) * E + lv.idx_group_bwd, s);
-      k_group_bwd<T><<<lv.ngroups, kGroupThreads, sm, s>>>(lv.groups, h->idx, fv.vals, x);
+      if (lv.nsmall)
+        k_group_bwd_small<T><<<(lv.nsmall + kSmallWarps - 1) / kSmallWarps, kSmallWarps * 32, 0, s>>>(
+            lv.small_groups, lv.nsmall, lv.groups, h->idx, fv.vals, x);
+      if (lv.nlarge)
+        k_group_bwd<T><<<lv.nlarge, kGroupThreads, sm, s>>>(lv.large_groups, lv.groups, h->idx, fv.vals, x);
+      if (lv.nsmall && lv.nlarge) note_launch();
     }
     if (lv.ncells) {
       StatScope sc(h, "cell_bwd", l, (lv.vals_cell + lv.vec_cell_bwd) * E + lv.idx_cell_bwd, s);

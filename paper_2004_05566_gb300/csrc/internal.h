@@ -101,6 +101,9 @@ struct LevelDev {
   int2 *chunk_of[2] = {nullptr, nullptr};  // [0]: FP64, [1]: FP32
   int *chunk_tab[2] = {nullptr, nullptr};
   int max_chunks = 0;
+  // separator entities with at most 32 DOFs (one warp each) and the others
+  int nsmall = 0, nlarge = 0;
+  int *small_groups = nullptr, *large_groups = nullptr;
   int max_nI = 0, max_nB = 0, max_ng = 0;
   // algorithmic bytes per launch for one-byte-per-value accounting:
   // values read, indices read (4 B), vector entries read+written, contributions

@@ -12,6 +12,7 @@
 """
 
 import math
+import os
 
 import numpy as np
 import pytest
@@ -176,6 +177,8 @@ def test_full_size_fisher_1023_steps_satisfy_cn(H):
 
 
 @pytest.mark.slow
+@pytest.mark.skipif(os.environ.get("HIFCN_SLOW_3D") != "1",
+                    reason="the FP64 leaf setup at 127^3 takes ~10 minutes; set HIFCN_SLOW_3D=1")
 def test_full_size_heat3d_127_steps_satisfy_cn(H):
     """3D heat 127^3 (leaf 8, eps 1e-4, dt 0.1, face + edge skeletonization,
     FP32 apply): each GPU step solves the CN system assembled by the oracle."""
