@@ -56,6 +56,8 @@ def _args():
     p.add_argument("--batched-count", type=int, default=256,
                    help="problems of the batched workload reported beside the headline (0: skip)")
     p.add_argument("--batched-steps", type=int, default=20)
+    p.add_argument("--serving-ops", type=int, default=16,
+                   help="resident operators of the serving measurement (0: skip)")
     p.add_argument("--cpu-sample", type=int, default=0, help=argparse.SUPPRESS)
     p.add_argument("--cpu-sample-steps", type=int, default=0, help=argparse.SUPPRESS)
     return p.parse_args()
@@ -342,6 +344,11 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
     if args.batched_count > 0:
         batched = run_batched(args, dev, H, W, np, torch)
 
+    # ---- serving: open-loop Poisson step requests over resident operators
+    serving = None
+    if args.serving_ops > 0:
+        serving = run_serving(args, local, W, np)
+
     # ---- max over ranks
     vals = [t_ms, e2e_ms, t64_ms]
     if dist is not None:
@@ -442,8 +449,62 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
         "clocks": clk,
         "cpu_baseline": cpu,
         "batched": batched,
+        "serving": serving,
     }
     return line
+
+
+def run_serving(args, device_index, W, np) -> dict:
+    """Serving: resident 2D reaction-diffusion operators (side log-uniform in
+    255..1023, leaf 16, lognormal a with contrast 1e3, dt in [1e-2, 1], eps 1e-6,
+    FP32 factors); open-loop Poisson arrivals of CN-step requests, the operator
+    of each request drawn uniformly; the server batches concurrent requests
+    (continuous batching).  Reports latency (arrival to result) percentiles
+    and achieved throughput per offered load."""
+    import random
+    import paper_2004_05566_gb300.serve as S
+
+    rng = np.random.default_rng(2000)
+    srv = S.CNServer(hbm_budget_bytes=64 << 30, device=device_index)
+    ids = []
+    for i in range(args.serving_ops):
+        side = math.exp(rng.uniform(math.log(255), math.log(1023)))
+        n, m, L = W.snap_side(side, leafs=(16,))
+        a = W.lognormal_coefficient(W.grf(rng, n, 2, 0.05), 1e3)
+        dt = math.exp(rng.uniform(math.log(1e-2), math.log(1.0)))
+        srv.register(i, S.OperatorSpec(2, n, m, a, dt, 1e-6, W.gaussian_bump_u0(n, 2), (1, 1.0, 1.0)))
+        ids.append(i)
+    t0 = time.perf_counter()
+    for f in [srv.submit(i) for i in ids]:  # admission (factorization) of every operator
+        f.result()
+    t_admit = time.perf_counter() - t0
+    loads = []
+    rnd = random.Random(7)
+    for lam in (100.0, 300.0, 1000.0, 3000.0):
+        nreq = int(min(2.0 * lam, 3000))
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, size=nreq))
+        futs = []
+        start = time.perf_counter()
+        for t_a in arrivals:
+            delay = start + t_a - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            futs.append(srv.submit(rnd.choice(ids)))
+        res = [f.result() for f in futs]
+        end = time.perf_counter()
+        lat = sorted(r.latency_s * 1e3 for r in res)
+        pct = lambda q: lat[min(len(lat) - 1, max(0, int(math.ceil(q / 100 * len(lat))) - 1))]
+        loads.append({"offered_steps_per_s": lam, "requests": nreq,
+                      "achieved_steps_per_s": round(nreq / (end - start), 1),
+                      "p50_ms": round(pct(50), 3), "p99_ms": round(pct(99), 3),
+                      "mean_batch": round(sum(r.batch_size for r in res) / len(res), 2)})
+    sides = sorted(srv._ops[i].spec.n - 1 for i in ids)
+    out = {"operators": len(ids), "sides_min_max": [sides[0], sides[-1]],
+           "admission_s": round(t_admit, 2), "resident_bytes": srv.resident_bytes(),
+           "loads": loads,
+           "scheduler": "step-level continuous batching over cn_step_batched (serve.CNServer)"}
+    srv.close()
+    return out
 
 
 def run_batched(args, dev, H, W, np, torch) -> dict:

@@ -118,6 +118,8 @@ int build_device_factor(Handle *h, const std::vector<double> &vals64, cudaStream
   return HIF_OK;
 }
 
+int make_cell_inverses(Handle *h, cudaStream_t s);
+
 // Upload descriptors of every level, allocate the contribution scratch and
 // the FP32 copy (values already on the device in h->f64.vals).
 int finish_device_factor(Handle *h, cudaStream_t s) {
@@ -132,6 +134,8 @@ int finish_device_factor(Handle *h, cudaStream_t s) {
       D.max_nI = std::max(D.max_nI, c.nI);
       D.max_nB = std::max(D.max_nB, c.nB);
       D.vals_cell += (double)c.nI * (c.nI + 1) / 2 + (double)c.nB * c.nI;
+      D.vals_S += (double)c.nI * (c.nI + 1) / 2;
+      D.vals_V += (double)c.nB * c.nI;
       D.idx_cell_fwd += 4.0 * c.nI;
       D.idx_cell_bwd += 4.0 * (c.nI + c.nB);
       D.vec_cell_fwd += 2.0 * c.nI;          // x_I read and written
@@ -189,20 +193,21 @@ int finish_device_factor(Handle *h, cudaStream_t s) {
       if (!lg.empty())
         HIF_CUDA_TRY(cudaMemcpyAsync(D.large_groups, lg.data(), lg.size() * sizeof(int), cudaMemcpyHostToDevice, s));
     }
-    // chunk tables for the bulk-copy staged kernels: consecutive whole rows of
-    // the cell block [G rows | V rows] of at most kStageBytes bytes
+    // chunk tables for the bulk-copy staged FP32 kernels: consecutive whole
+    // rows of at most kStageBytes; [0] the V rows, [1] the S rows then the V rows
     for (int e = 0; e < 2; ++e) {
-      const long long cap = kStageBytes / (e == 0 ? 8 : 4);
+      const long long cap = kStageBytes / 4;
       std::vector<int2> of;
       std::vector<int> tab;
       for (const CellDesc &cd : H.cells) {
         const long long vs = pad4(cd.nI);
-        auto roff = [&](int r) { return r < cd.nI ? tri_off(r) : tri_off(cd.nI) + (long long)(r - cd.nI) * vs; };
-        const int nrows = cd.nI + cd.nB;
+        const int nt = e == 0 ? 0 : cd.nI;  // triangular rows first
+        auto roff = [&](int r) { return r < nt ? tri_off(r) : tri_off(nt) + (long long)(r - nt) * vs; };
+        const int nrows = nt + cd.nB;
         int2 o{(int)tab.size(), 0};
         tab.push_back(0);
         int r = 0;
-        bool ok = nrows == 0 || vs <= cap;
+        const bool ok = nrows == 0 || vs <= cap;
         while (ok && r < nrows) {
           const long long start = roff(r);
           int en = r + 1;
@@ -212,7 +217,7 @@ int finish_device_factor(Handle *h, cudaStream_t s) {
           r = en;
         }
         if (!ok) o.y = -1;
-        D.max_chunks = std::max(D.max_chunks, o.y);
+        D.max_chunks = o.y < 0 ? -1 : (D.max_chunks < 0 ? -1 : std::max(D.max_chunks, o.y));
         of.push_back(o);
       }
       HIF_TRY(dev_alloc(h, (void **)&D.chunk_of[e], std::max<size_t>(1, of.size()) * sizeof(int2)));
@@ -230,6 +235,7 @@ int finish_device_factor(Handle *h, cudaStream_t s) {
       HIF_CUDA_TRY(cudaMemcpyAsync(D.bwd, bw.data(), bw.size() * sizeof(CellItem), cudaMemcpyHostToDevice, s));
   }
   HIF_TRY(dev_alloc(h, (void **)&h->f64.xI, h->N * sizeof(double)));
+  HIF_TRY(make_cell_inverses(h, s));
   HIF_TRY(dev_alloc(h, (void **)&h->f64.contrib, h->max_contrib * sizeof(double)));
   if (h->opt.precision == HIF_FP32) {
     HIF_TRY(dev_alloc(h, (void **)&h->f32.vals, h->nvals * sizeof(float)));
@@ -389,6 +395,8 @@ int import_blob(Handle *h, const void *blob, size_t bytes, cudaStream_t s) {
       d.nB = sz[1];
       if (!get_ints(d.nI, &d.I_off) || !get_ints(d.nB, &d.B_off)) return HIF_EFORMAT;
       if (!get_lower(d.nI, &d.G_off)) return HIF_EFORMAT;
+      d.S_off = (long long)vals.size();  // S = G^T G, computed on the device
+      vals.resize(vals.size() + tri_off(d.nI), 0.0);
       if (!get_dense(d.nB, d.nI, &d.V_off)) return HIF_EFORMAT;
       d.C_off = slots;
       slots += d.nB;

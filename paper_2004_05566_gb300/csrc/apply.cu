@@ -444,34 +444,62 @@ __device__ __forceinline__ long long cell_row_off(int r, int nI, long long vs) {
   return r < nI ? tri_off(r) : tri_off(nI) + (long long)(r - nI) * vs;
 }
 
-// Producer: lane 0 of the last warp streams the chunks of one cell.
+// Producer: lane 0 of the last warp streams the chunks of a block whose
+// first ntri rows are packed-triangular rows and the rest dense rows of
+// stride vs (chunk k = rows [cs[k], cs[k+1])).
 template <typename T>
-__device__ __forceinline__ void produce_chunks(const CellDesc &c, const T *vals, const int *cs, int nch,
-                                               unsigned char *stage, unsigned long long *full,
-                                               unsigned long long *empty, double *err) {
-  const long long vs = pad4(c.nI);
+__device__ __forceinline__ void produce_rows(const T *block, int ntri, long long vs, const int *cs,
+                                             int nch, unsigned char *stage, unsigned long long *full,
+                                             unsigned long long *empty, double *err) {
   for (int k = 0; k < nch; ++k) {
     const int sidx = k % kStages;
     if (k >= kStages && !mbar_wait(&empty[sidx], (unsigned)(((k / kStages) - 1) & 1))) {
       err[0] = 1.0;
       return;
     }
-    const long long a = cell_row_off(cs[k], c.nI, vs), b = cell_row_off(cs[k + 1], c.nI, vs);
-    bulk_load(stage + (size_t)sidx * kStageBytes, vals + c.G_off + a, (unsigned)((b - a) * sizeof(T)),
+    const long long a = cell_row_off(cs[k], ntri, vs), b = cell_row_off(cs[k + 1], ntri, vs);
+    bulk_load(stage + (size_t)sidx * kStageBytes, block + a, (unsigned)((b - a) * sizeof(T)),
               &full[sidx]);
   }
 }
 
+// ---------------------------------------------------- symmetric inverse of A_II
+//
+// S = A_II^{-1} = L^{-T} L^{-1} = G^T G (packed lower), built once per factor
+// in FP64 from the stored G: S_ij = sum_{k >= i} G_ki G_kj for j <= i.
+__global__ void __launch_bounds__(256) k_make_S(const CellDesc *__restrict__ cells,
+                                                double *__restrict__ vals) {
+  const CellDesc c = cells[blockIdx.x];
+  const double *G = vals + c.G_off;
+  double *S = vals + c.S_off;
+  for (int i = 0; i < c.nI; ++i) {
+    for (int j = threadIdx.x; j <= i; j += 256) {
+      double acc = 0.0;
+      for (int k = i; k < c.nI; ++k) {
+        const double *row = G + tri_off(k);
+        acc += row[i] * row[j];
+      }
+      S[tri_off(i) + j] = acc;
+    }
+  }
+}
+
+// S-form of the leaf cell steps (FP32, TMA-staged).  Algebraically the same
+// operator as the G-form: the forward sweep only sends the boundary updates
+// c_B = V x_I (x_I is left as it is), and the backward sweep forms
+// x_I <- S x_I - V^T x_B with S = A_II^{-1} = G^T G, which equals
+// G^T (G x_I) - V^T x_B.  S is read once instead of G twice.
+
+// forward: contributions c_B = V x_I, streaming the V rows
 template <typename T>
-__global__ void __launch_bounds__(kTmaThreads) k_cell_fwd_tma(const CellDesc *__restrict__ cells,
-                                                              const int2 *__restrict__ chunk_of,
-                                                              const int *__restrict__ chunk_tab,
-                                                              const int *__restrict__ idx,
-                                                              const T *__restrict__ vals,
-                                                              T *__restrict__ contrib,
-                                                              T *__restrict__ xI,
-                                                              const T *__restrict__ x,
-                                                              double *__restrict__ err) {
+__global__ void __launch_bounds__(kTmaThreads) k_cell_fwd_tma_S(const CellDesc *__restrict__ cells,
+                                                                const int2 *__restrict__ chunk_of,
+                                                                const int *__restrict__ chunk_tab,
+                                                                const int *__restrict__ idx,
+                                                                const T *__restrict__ vals,
+                                                                T *__restrict__ contrib,
+                                                                const T *__restrict__ x,
+                                                                double *__restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) unsigned long long full[kStages], empty[kStages];
   unsigned char *stage = smem_raw;
@@ -493,13 +521,13 @@ __global__ void __launch_bounds__(kTmaThreads) k_cell_fwd_tma(const CellDesc *__
     return;
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nIp = (int)pad4(c.nI);
+  const long long vs = nIp;
   if (warp == kConsumerWarps) {
-    if (lane == 0) produce_chunks<T>(c, vals, cs, nch, stage, full, empty, err);
+    if (lane == 0) produce_rows<T>(vals + c.V_off, 0, vs, cs, nch, stage, full, empty, err);
     return;
   }
   const int *I = idx + c.I_off;
-  const int nIp = (int)pad4(c.nI);
-  const long long vs = nIp;
   for (int i = threadIdx.x; i < nIp; i += kConsumers) xs[i] = i < c.nI ? x[I[i]] : T(0);
   consumers_sync();
   for (int k = 0; k < nch; ++k) {
@@ -510,28 +538,19 @@ __global__ void __launch_bounds__(kTmaThreads) k_cell_fwd_tma(const CellDesc *__
     }
     const T *base = reinterpret_cast<const T *>(stage + (size_t)sidx * kStageBytes);
     const int rb = cs[k], re = cs[k + 1];
-    const long long off0 = cell_row_off(rb, c.nI, vs);
     for (int r0 = rb + warp * kRows; r0 < re; r0 += kConsumerWarps * kRows) {
       const T *rp[kRows];
       int nq[kRows];
 #pragma unroll
       for (int u = 0; u < kRows; ++u) {
         const int r = r0 + u;
-        if (r < re) {
-          rp[u] = base + (cell_row_off(r, c.nI, vs) - off0);
-          nq[u] = r < c.nI ? (r + 4) / 4 : nIp / 4;
-        } else {
-          rp[u] = base;
-          nq[u] = 0;
-        }
+        rp[u] = base + (long long)(r < re ? r - rb : 0) * vs;
+        nq[u] = r < re ? nIp / 4 : 0;
       }
       T acc[kRows];
 #pragma unroll
       for (int u = 0; u < kRows; ++u) acc[u] = T(0);
-      int maxq = 0;
-#pragma unroll
-      for (int u = 0; u < kRows; ++u) maxq = nq[u] > maxq ? nq[u] : maxq;
-      for (int q = lane; q < maxq; q += 32) {
+      for (int q = lane; q < nIp / 4; q += 32) {
         T xv[4];
         ld4(xs + 4 * q, xv);
 #pragma unroll
@@ -547,12 +566,8 @@ __global__ void __launch_bounds__(kTmaThreads) k_cell_fwd_tma(const CellDesc *__
       for (int u = 0; u < kRows; ++u) acc[u] = warp_reduce(acc[u]);
       if (lane == 0) {
 #pragma unroll
-        for (int u = 0; u < kRows; ++u) {
-          const int r = r0 + u;
-          if (r >= re) break;
-          if (r < c.nI) xI[I[r]] = acc[u];
-          else contrib[c.C_off + (r - c.nI)] = acc[u];
-        }
+        for (int u = 0; u < kRows; ++u)
+          if (r0 + u < re) contrib[c.C_off + r0 + u] = acc[u];
       }
     }
     __syncwarp();
@@ -560,22 +575,27 @@ __global__ void __launch_bounds__(kTmaThreads) k_cell_fwd_tma(const CellDesc *__
   }
 }
 
+// backward: x_I <- S x_I - V^T x_B, streaming the S rows then the V rows.
+// Warp w handles the rows r = w (mod 8); lane p owns the column quads
+// (p, nq - 1 - p).  An S row r gives its row dot S[r][.] x (warp reduction)
+// and, below the diagonal, the column products S[r][col] x_r (col < r).
 template <typename T>
-__global__ void __launch_bounds__(kTmaThreads) k_cell_bwd_tma(const CellDesc *__restrict__ cells,
-                                                              const int2 *__restrict__ chunk_of,
-                                                              const int *__restrict__ chunk_tab,
-                                                              const int *__restrict__ idx,
-                                                              const T *__restrict__ vals,
-                                                              const T *__restrict__ xI,
-                                                              T *__restrict__ x,
-                                                              double *__restrict__ err) {
+__global__ void __launch_bounds__(kTmaThreads) k_cell_bwd_tma_S(const CellDesc *__restrict__ cells,
+                                                                const int2 *__restrict__ chunk_of,
+                                                                const int *__restrict__ chunk_tab,
+                                                                const int *__restrict__ idx,
+                                                                const T *__restrict__ vals,
+                                                                T *__restrict__ x,
+                                                                double *__restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) unsigned long long full[kStages], empty[kStages];
   unsigned char *stage = smem_raw;
   T *part = reinterpret_cast<T *>(smem_raw + (size_t)kStages * kStageBytes);  // 8 * kConsumers
-  T *xs = part + 8 * kConsumers;
+  T *xs = part + 8 * kConsumers;  // pad4(nI)
   const CellDesc c = cells[blockIdx.x];
-  T *xb = xs + c.nI;
+  const int nIp = (int)pad4(c.nI);
+  T *yrow = xs + nIp;             // nI
+  T *xb = yrow + c.nI;            // nB
   const int2 co = chunk_of[blockIdx.x];
   const int *cs = chunk_tab + co.x;
   const int nch = co.y;
@@ -592,25 +612,24 @@ __global__ void __launch_bounds__(kTmaThreads) k_cell_bwd_tma(const CellDesc *__
     return;
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long vs = nIp;
   if (warp == kConsumerWarps) {
-    if (lane == 0) produce_chunks<T>(c, vals, cs, nch, stage, full, empty, err);
+    if (lane == 0) produce_rows<T>(vals + c.S_off, c.nI, vs, cs, nch, stage, full, empty, err);
     return;
   }
   const int *I = idx + c.I_off;
   const int *B = idx + c.B_off;
-  const long long vs = pad4(c.nI);
-  for (int i = threadIdx.x; i < c.nI; i += kConsumers) xs[i] = xI[I[i]];
+  for (int i = threadIdx.x; i < nIp; i += kConsumers) xs[i] = i < c.nI ? x[I[i]] : T(0);
   for (int q = threadIdx.x; q < c.nB; q += kConsumers) xb[q] = x[B[q]];
   consumers_sync();
-  const int nq = (int)(vs / 4);
-  const int npairs = (nq + 1) / 2;
-  int PW, RG;
-  col_layout(npairs, kConsumers, PW, RG);
-  const int pl = threadIdx.x % PW, rg = threadIdx.x / PW;
-  const int qa = pl, qb = nq - 1 - pl;
-  const bool okA = rg < RG && pl < npairs;
+  const int nq = nIp / 4;
+  const int qa = lane, qb = nq - 1 - lane;  // one warp covers all column pairs (nq <= 64)
+  const bool okA = qa < (nq + 1) / 2;
   const bool okB = okA && qb > qa;
   T aA[4] = {T(0), T(0), T(0), T(0)}, aB[4] = {T(0), T(0), T(0), T(0)};
+  T xa[4] = {T(0), T(0), T(0), T(0)}, xbq[4] = {T(0), T(0), T(0), T(0)};
+  if (okA) ld4(xs + 4 * qa, xa);
+  if (okB) ld4(xs + 4 * qb, xbq);
   for (int k = 0; k < nch; ++k) {
     const int sidx = k % kStages;
     if (!mbar_wait(&full[sidx], (unsigned)((k / kStages) & 1))) {
@@ -620,31 +639,39 @@ __global__ void __launch_bounds__(kTmaThreads) k_cell_bwd_tma(const CellDesc *__
     const T *base = reinterpret_cast<const T *>(stage + (size_t)sidx * kStageBytes);
     const int rb = cs[k], re = cs[k + 1];
     const long long off0 = cell_row_off(rb, c.nI, vs);
-    if (okA) {
-      for (int r = rb + ((rg - rb % RG) % RG + RG) % RG; r < re; r += RG) {
-        const T *row = base + (cell_row_off(r, c.nI, vs) - off0);
-        if (r < c.nI) {
-          const T xv = xs[r];
-          if (4 * qa <= r) {
-            T v[4];
-            ld4(row + 4 * qa, v);
-            aA[0] += v[0] * xv; aA[1] += v[1] * xv; aA[2] += v[2] * xv; aA[3] += v[3] * xv;
-          }
-          if (okB && 4 * qb <= r) {
-            T w[4];
-            ld4(row + 4 * qb, w);
-            aB[0] += w[0] * xv; aB[1] += w[1] * xv; aB[2] += w[2] * xv; aB[3] += w[3] * xv;
-          }
-        } else {
-          const T xv = xb[r - c.nI];
+    for (int r = rb + ((warp - rb % kConsumerWarps) % kConsumerWarps + kConsumerWarps) % kConsumerWarps;
+         r < re; r += kConsumerWarps) {
+      const T *row = base + (cell_row_off(r, c.nI, vs) - off0);
+      if (r < c.nI) {
+        const T xr = xs[r];
+        T dot = T(0);
+        if (okA && 4 * qa <= r) {
+          T v[4];
+          ld4(row + 4 * qa, v);
+          dot += v[0] * xa[0] + v[1] * xa[1] + v[2] * xa[2] + v[3] * xa[3];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) aA[e] += (4 * qa + e < r ? v[e] : T(0)) * xr;
+        }
+        if (okB && 4 * qb <= r) {
+          T w[4];
+          ld4(row + 4 * qb, w);
+          dot += w[0] * xbq[0] + w[1] * xbq[1] + w[2] * xbq[2] + w[3] * xbq[3];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) aB[e] += (4 * qb + e < r ? w[e] : T(0)) * xr;
+        }
+        dot = warp_reduce(dot);
+        if (lane == 0) yrow[r] = dot;
+      } else {
+        const T xv = xb[r - c.nI];
+        if (okA) {
           T v[4];
           ld4(row + 4 * qa, v);
           aA[0] -= v[0] * xv; aA[1] -= v[1] * xv; aA[2] -= v[2] * xv; aA[3] -= v[3] * xv;
-          if (okB) {
-            T w[4];
-            ld4(row + 4 * qb, w);
-            aB[0] -= w[0] * xv; aB[1] -= w[1] * xv; aB[2] -= w[2] * xv; aB[3] -= w[3] * xv;
-          }
+        }
+        if (okB) {
+          T w[4];
+          ld4(row + 4 * qb, w);
+          aB[0] -= w[0] * xv; aB[1] -= w[1] * xv; aB[2] -= w[2] * xv; aB[3] -= w[3] * xv;
         }
       }
     }
@@ -652,19 +679,20 @@ __global__ void __launch_bounds__(kTmaThreads) k_cell_bwd_tma(const CellDesc *__
     if (lane == 0) mbar_arrive(&empty[sidx]);
   }
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    part[k * kConsumers + threadIdx.x] = aA[k];
-    part[(4 + k) * kConsumers + threadIdx.x] = aB[k];
+  for (int e = 0; e < 4; ++e) {
+    part[e * kConsumers + threadIdx.x] = aA[e];
+    part[(4 + e) * kConsumers + threadIdx.x] = aB[e];
   }
   consumers_sync();
-  if (rg == 0 && pl < npairs) {
+  // column sums over the 8 warps plus the row dot of the same index
+  if (warp == 0 && okA) {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      if (k >= 4 && qb <= qa) break;
-      const int col = (k < 4 ? 4 * qa : 4 * qb) + (k & 3);
+    for (int e = 0; e < 8; ++e) {
+      if (e >= 4 && !okB) break;
+      const int col = (e < 4 ? 4 * qa : 4 * qb) + (e & 3);
       if (col >= c.nI) continue;
-      T sum = part[k * kConsumers + pl];
-      for (int g = 1; g < RG; ++g) sum += part[k * kConsumers + g * PW + pl];
+      T sum = yrow[col];
+      for (int w = 0; w < kConsumerWarps; ++w) sum += part[e * kConsumers + w * 32 + lane];
       x[I[col]] = sum;
     }
   }
@@ -745,24 +773,28 @@ int set_smem_limits() {
   HIF_CUDA_TRY(cudaFuncSetAttribute(k_group_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   HIF_CUDA_TRY(cudaFuncSetAttribute(k_group_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   HIF_CUDA_TRY(cudaFuncSetAttribute(k_root<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  HIF_CUDA_TRY(cudaFuncSetAttribute(k_cell_fwd_tma<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  HIF_CUDA_TRY(cudaFuncSetAttribute(k_cell_bwd_tma<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  HIF_CUDA_TRY(cudaFuncSetAttribute(k_cell_fwd_tma_S<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  HIF_CUDA_TRY(cudaFuncSetAttribute(k_cell_bwd_tma_S<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   done = true;
   return HIF_OK;
 }
 
 // The TMA-staged cell kernels serve levels whose cells are not split over
 // CTAs, whose rows fit one chunk and whose column pairs fit one pass.
-// FP64 applies are bound by the FP64 pipe, not by HBM; they keep the
-// register-streaming kernels, which measured faster there.
-bool use_tma(const Handle *h, const LevelDev &lv, size_t elem) {
-  if (elem != sizeof(float)) return false;
-  if (!h->use_tma || lv.nfwd != lv.ncells || lv.nbwd != lv.ncells || lv.max_chunks < 0) return false;
-  if ((size_t)pad4(lv.max_nI) * elem > (size_t)kStageBytes) return false;
-  if (pad4(lv.max_nI) / 4 > 2 * kConsumers) return false;
+// The TMA-staged S-form leaf kernels serve FP32 levels whose cells are not
+// split over CTAs, whose rows fit one stage and whose column pairs fit one
+// warp (nI <= 256).  FP64 applies are bound by the FP64 pipe, not by HBM, and
+// keep the register-streaming G-form kernels.
+bool level_sform(const Handle *h, const LevelDev &lv) {
+  if (!h->use_tma || lv.ncells == 0 || lv.nfwd != lv.ncells || lv.nbwd != lv.ncells) return false;
+  if (lv.max_chunks < 0 || pad4(lv.max_nI) > 256) return false;
   const size_t bwd_smem = (size_t)kStages * kStageBytes +
-                          ((size_t)lv.max_nI + lv.max_nB + 8 * kConsumers) * elem;
+                          ((size_t)8 * kConsumers + 2 * pad4(lv.max_nI) + lv.max_nB) * sizeof(float);
   return bwd_smem <= 200 * 1024;
+}
+
+bool use_tma(const Handle *h, const LevelDev &lv, size_t elem) {
+  return elem == sizeof(float) && level_sform(h, lv);
 }
 
 template <typename T>
@@ -783,13 +815,15 @@ int apply_levels(Handle *h, const FactorValues<T> &fv, T *x, cudaStream_t s) {
   for (int l = 0; l < h->L; ++l) {
     const LevelDev &lv = h->lv[l];
     if (lv.ncells) {
-      StatScope sc(h, "cell_fwd", l, (lv.vals_cell + lv.vec_cell_fwd + lv.contrib) * E + lv.idx_cell_fwd, s);
+      const bool sf = use_tma(h, lv, sizeof(T));
+      StatScope sc(h, "cell_fwd", l,
+                   sf ? (lv.vals_V + lv.vec_cell_fwd / 2 + lv.contrib) * E + lv.idx_cell_fwd
+                      : (lv.vals_cell + lv.vec_cell_fwd + lv.contrib) * E + lv.idx_cell_fwd, s);
       if (use_tma(h, lv, sizeof(T))) {
-        const int e = sizeof(T) == 8 ? 0 : 1;
         size_t sm = (size_t)kStages * kStageBytes + (size_t)pad4(lv.max_nI) * sizeof(T);
-        k_cell_fwd_tma<T><<<lv.ncells, kTmaThreads, sm, s>>>(lv.cells, lv.chunk_of[e], lv.chunk_tab[e],
-                                                              h->idx, fv.vals, fv.contrib, fv.xI, x,
-                                                              h->scal + kScalErr);
+        k_cell_fwd_tma_S<T><<<lv.ncells, kTmaThreads, sm, s>>>(lv.cells, lv.chunk_of[0], lv.chunk_tab[0],
+                                                                h->idx, fv.vals, fv.contrib, x,
+                                                                h->scal + kScalErr);
       } else {
         size_t sm = (size_t)pad4(lv.max_nI) * sizeof(T);
         k_cell_fwd<T><<<lv.nfwd, kCellFwdThreads, sm, s>>>(lv.fwd, lv.cells, h->idx, fv.vals, fv.contrib,
@@ -829,14 +863,15 @@ int apply_levels(Handle *h, const FactorValues<T> &fv, T *x, cudaStream_t s) {
       if (lv.nsmall && lv.nlarge) note_launch();
     }
     if (lv.ncells) {
-      StatScope sc(h, "cell_bwd", l, (lv.vals_cell + lv.vec_cell_bwd) * E + lv.idx_cell_bwd, s);
+      const bool sf = use_tma(h, lv, sizeof(T));
+      StatScope sc(h, "cell_bwd", l,
+                   sf ? (lv.vals_S + lv.vals_V + lv.vec_cell_bwd) * E + lv.idx_cell_bwd
+                      : (lv.vals_cell + lv.vec_cell_bwd) * E + lv.idx_cell_bwd, s);
       if (use_tma(h, lv, sizeof(T))) {
-        const int e = sizeof(T) == 8 ? 0 : 1;
         size_t sm = (size_t)kStages * kStageBytes +
-                    ((size_t)lv.max_nI + lv.max_nB + 8 * kConsumers) * sizeof(T);
-        k_cell_bwd_tma<T><<<lv.ncells, kTmaThreads, sm, s>>>(lv.cells, lv.chunk_of[e], lv.chunk_tab[e],
-                                                              h->idx, fv.vals, fv.xI, x,
-                                                              h->scal + kScalErr);
+                    ((size_t)8 * kConsumers + 2 * pad4(lv.max_nI) + lv.max_nB) * sizeof(T);
+        k_cell_bwd_tma_S<T><<<lv.ncells, kTmaThreads, sm, s>>>(lv.cells, lv.chunk_of[1], lv.chunk_tab[1],
+                                                                h->idx, fv.vals, x, h->scal + kScalErr);
       } else {
         size_t sm = ((size_t)lv.max_nI + lv.max_nB + 8 * kCellBwdThreads) * sizeof(T);
         k_cell_bwd<T><<<lv.nbwd, kCellBwdThreads, sm, s>>>(lv.bwd, lv.cells, h->idx, fv.vals, fv.xI, x);
@@ -857,6 +892,18 @@ int apply_inplace_f64_with_scratch(Handle *h, double *contrib, double *x, cudaSt
   FactorValues<double> fv = h->f64;
   fv.contrib = contrib;
   return apply_levels<double>(h, fv, x, s);
+}
+
+// S = G^T G of the cells of the levels the FP32 S-form kernels will apply.
+int make_cell_inverses(Handle *h, cudaStream_t s) {
+  if (h->opt.precision != HIF_FP32) return HIF_OK;
+  for (const LevelDev &lv : h->lv) {
+    if (!level_sform(h, lv)) continue;
+    k_make_S<<<lv.ncells, 256, 0, s>>>(lv.cells, h->f64.vals);
+    note_launch();
+  }
+  HIF_CUDA_TRY(cudaGetLastError());
+  return HIF_OK;
 }
 
 int apply_inplace_f32(Handle *h, float *x, cudaStream_t s) {

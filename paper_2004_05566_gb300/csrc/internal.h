@@ -70,6 +70,7 @@ struct CellDesc {
   long long G_off;  // into the value pool
   long long V_off;  // into the value pool
   long long C_off;  // into the contribution scratch (nB slots)
+  long long S_off;  // into the value pool: S = A_II^{-1} = G^T G, packed lower
 };
 
 struct GroupDesc {
@@ -95,12 +96,13 @@ struct LevelDev {
   int ncells = 0, ngroups = 0;
   int nfwd = 0, nbwd = 0;             // work items of the cell kernels
   CellItem *fwd = nullptr, *bwd = nullptr;  // device
-  // bulk-copy chunk tables of the cells (row boundaries), one per element size:
-  // cell c's chunks are rows [tab[o + k], tab[o + k + 1]) for k < n with
-  // (o, n) = chunk_of[c]
-  int2 *chunk_of[2] = {nullptr, nullptr};  // [0]: FP64, [1]: FP32
+  // bulk-copy chunk tables of the FP32 cell blocks (row boundaries): cell c's
+  // chunks are rows [tab[o + k], tab[o + k + 1]) for k < n, (o, n) = of[c];
+  // [0]: the V rows, [1]: the S rows followed by the V rows
+  int2 *chunk_of[2] = {nullptr, nullptr};
   int *chunk_tab[2] = {nullptr, nullptr};
   int max_chunks = 0;
+  double vals_S = 0, vals_V = 0;       // algorithmic value counts of the S and V blocks
   // separator entities with at most 32 DOFs (one warp each) and the others
   int nsmall = 0, nlarge = 0;
   int *small_groups = nullptr, *large_groups = nullptr;

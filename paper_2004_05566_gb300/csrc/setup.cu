@@ -49,7 +49,8 @@ struct SCell {
   long long F_off;    // frontal matrix (n x n column major, n = nI + nB)
   long long G_off;    // packed L^{-1} in the level value pool
   long long V_off;    // V (nB x nI row major) in the level value pool
-  long long S_off;    // nB x nB scratch for the Jacobi rescaling
+  long long Sc_off;   // nB x nB scratch for the Jacobi rescaling
+  long long S_off;    // S = A_II^{-1} (packed lower) in the level value pool
   long long dofs_off; // local DOF list (I then B), global indices
   long long bmap_off; // per B position: (group id, position in group)
 };
@@ -322,7 +323,7 @@ __global__ void __launch_bounds__(NT) k_cell_scale(const SCell *__restrict__ cel
   const SCell c = cells[blockIdx.x];
   const int nI = c.nI, nB = c.nB, nn = nI + nB;
   double *A = F + c.F_off;
-  double *Sc = S + c.S_off;
+  double *Sc = S + c.Sc_off;
   const int2 *bm = bmap + c.bmap_off;
   const long long nbb = (long long)nB * nB;
   // S = D F_BB (rows of every group scaled by its L^{-1})
@@ -783,9 +784,11 @@ int gpu_setup(Handle *h, const double *a_nodes, cudaStream_t s) {
       foff += nn * nn;
       C.G_off = voff;
       voff += tri_off(C.nI);
+      C.S_off = voff;  // S = G^T G, filled after the factorization
+      voff += tri_off(C.nI);
       C.V_off = voff;
       voff += (long long)C.nB * pad4(C.nI);
-      C.S_off = soff;
+      C.Sc_off = soff;
       soff += (long long)C.nB * C.nB;
       C.dofs_off = (long long)cdofs.size();
       C.bmap_off = (long long)bmap.size();
@@ -928,6 +931,7 @@ int gpu_setup(Handle *h, const double *a_nodes, cudaStream_t s) {
       h->idx_host.insert(h->idx_host.end(), P.cB[c].begin(), P.cB[c].end());
       d.G_off = cells[c].G_off;
       d.V_off = cells[c].V_off;
+      d.S_off = cells[c].S_off;
       d.C_off = slots;
       slots += d.nB;
       if (d.nI > 0 || d.nB > 0) LH.cells.push_back(d);
@@ -1091,6 +1095,7 @@ int gpu_setup(Handle *h, const double *a_nodes, cudaStream_t s) {
     for (auto &c : h->lv_host[l].cells) {
       c.G_off += base[l];
       c.V_off += base[l];
+      c.S_off += base[l];
     }
     for (auto &g : h->lv_host[l].groups) g.H_off += base[l];
   }

@@ -1,0 +1,248 @@
+"""Continuous-batching service of Crank-Nicolson steps over resident operators.
+
+Each registered operator is one CN problem (grid, coefficient a(x), dt, eps,
+reaction) whose HIF factor and state u live on the GPU while it is resident.
+Clients submit step requests; a scheduler thread repeatedly takes every
+pending request whose operator is not already in the running batch, admits
+the operators it needs (factoring them on the GPU, evicting the least
+recently used idle operators when the HBM budget would be exceeded), and runs
+the whole batch with one ``cn_step_batched`` call, whose steps overlap on the
+device.  Requests that arrive while a batch runs join the next one
+(step-level continuous batching).  Each request completes with the new step
+index, the PCG iteration count and its latency (arrival to result ready).
+
+Determinism: every kernel of the library reduces in a fixed order and the
+factorization is deterministic, so an operator's trajectory is the same
+whether it is stepped alone, in any mix, or after an eviction and re-factor.
+"""
+
+from __future__ import annotations
+
+import collections
+import threading
+import time
+from concurrent.futures import Future
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import hifcn as H
+
+# device bytes per unknown of a resident 2D operator with FP64 + FP32 factors
+# (measured with hif_query on 2D leaf-16 problems); used before the first setup
+_BYTES_PER_DOF_ESTIMATE = {2: 2300, 3: 12000}
+
+
+@dataclass
+class OperatorSpec:
+    dim: int
+    n: int
+    leaf: int
+    a_nodes: np.ndarray
+    dt: float
+    eps: float
+    u0: np.ndarray
+    reaction: tuple = (0, 0.0, 0.0)
+    precision: int = H.HIF_FP32
+
+    @property
+    def N(self) -> int:
+        return (self.n - 1) ** self.dim
+
+
+@dataclass
+class _Resident:
+    handle: H.Handle
+    u: torch.Tensor
+    out: torch.Tensor
+    bytes: int
+    last_used: float = 0.0
+
+
+@dataclass
+class _State:
+    spec: OperatorSpec
+    step: int = 0
+    u_host: np.ndarray | None = None  # state while not resident
+    resident: _Resident | None = None
+    setups: int = 0
+
+
+@dataclass
+class StepResult:
+    op_id: object
+    step: int
+    iters: int
+    latency_s: float
+    batch_size: int
+
+
+@dataclass
+class _Request:
+    op_id: object
+    arrival: float
+    future: Future = field(default_factory=Future)
+
+
+class CNServer:
+    """Step-level continuous batching of CN steps on one GPU (see module doc)."""
+
+    def __init__(self, hbm_budget_bytes: int, device: int = 0, max_batch: int = 256):
+        self.budget = int(hbm_budget_bytes)
+        self.device = torch.device("cuda", device)
+        self.max_batch = max_batch
+        self._ops: dict = {}
+        self._pending: collections.deque = collections.deque()
+        self._cv = threading.Condition()
+        self._stop = False
+        self._resident_bytes = 0
+        self.batches = 0
+        self.evictions = 0
+        self._error: BaseException | None = None
+        self._thread = threading.Thread(target=self._loop, name="cn-server", daemon=True)
+        self._thread.start()
+
+    # -------------------------------------------------------------- client API
+    def register(self, op_id, spec: OperatorSpec) -> None:
+        with self._cv:
+            if op_id in self._ops:
+                raise KeyError(f"operator {op_id!r} already registered")
+            self._ops[op_id] = _State(spec=spec, u_host=np.array(spec.u0, dtype=np.float64).ravel())
+
+    def submit(self, op_id) -> Future:
+        req = _Request(op_id, time.perf_counter())
+        with self._cv:
+            if self._error is not None:
+                raise RuntimeError("server stopped after an error") from self._error
+            if op_id not in self._ops:
+                raise KeyError(op_id)
+            self._pending.append(req)
+            self._cv.notify()
+        return req.future
+
+    def state(self, op_id) -> np.ndarray:
+        """Current u of an operator (host copy; call when its requests are done)."""
+        with self._cv:
+            st = self._ops[op_id]
+            if st.resident is not None:
+                torch.cuda.synchronize(self.device)
+                return st.resident.u.cpu().numpy().copy()
+            return st.u_host.copy()
+
+    def setups(self, op_id) -> int:
+        with self._cv:
+            return self._ops[op_id].setups
+
+    def step_count(self, op_id) -> int:
+        with self._cv:
+            return self._ops[op_id].step
+
+    def resident_bytes(self) -> int:
+        return self._resident_bytes
+
+    def close(self) -> None:
+        with self._cv:
+            self._stop = True
+            self._cv.notify()
+        self._thread.join()
+        for st in self._ops.values():
+            if st.resident is not None:
+                st.resident.handle.close()
+                st.resident = None
+
+    # -------------------------------------------------------------- scheduler
+    def _estimate(self, spec: OperatorSpec) -> int:
+        return _BYTES_PER_DOF_ESTIMATE[spec.dim] * spec.N
+
+    def _evict_one(self, keep: set) -> bool:
+        with self._cv:
+            cands = [(st.resident.last_used, oid) for oid, st in self._ops.items()
+                     if st.resident is not None and oid not in keep]
+        if not cands:
+            return False
+        _, oid = min(cands, key=lambda t: t[0])
+        st = self._ops[oid]
+        torch.cuda.synchronize(self.device)
+        u_host = st.resident.u.cpu().numpy().copy()
+        with self._cv:
+            res, st.resident, st.u_host = st.resident, None, u_host
+            self._resident_bytes -= res.bytes
+            self.evictions += 1
+        res.handle.close()
+        return True
+
+    def _admit(self, oid, keep: set) -> None:
+        st = self._ops[oid]
+        if st.resident is not None:
+            return
+        spec = st.spec
+        need = self._estimate(spec)
+        while self._resident_bytes + need > self.budget:
+            if not self._evict_one(keep):
+                break  # admit anyway when nothing else can be evicted
+        a = torch.from_numpy(spec.a_nodes).to(self.device)
+        opt = H.default_options(eps=spec.eps, precision=spec.precision, cg_tol=1e-10)
+        h = H.hif_setup(spec.dim, spec.n, spec.leaf, a, spec.dt, opt)
+        if spec.reaction[0]:
+            H.hif_set_reaction(h, *spec.reaction)
+        info = H.hif_query(h)
+        u = torch.from_numpy(st.u_host).to(self.device)
+        with self._cv:
+            st.resident = _Resident(h, u, torch.empty_like(u), int(info["device_bytes"]))
+            st.setups += 1
+            self._resident_bytes += st.resident.bytes
+        while self._resident_bytes > self.budget and self._evict_one(keep | {oid}):
+            pass
+
+    def _take_batch(self) -> list:
+        """Pending requests, at most one per operator (the rest stay queued)."""
+        batch, seen, rest = [], set(), collections.deque()
+        while self._pending and len(batch) < self.max_batch:
+            r = self._pending.popleft()
+            if r.op_id in seen:
+                rest.append(r)
+            else:
+                seen.add(r.op_id)
+                batch.append(r)
+        while rest:
+            self._pending.appendleft(rest.pop())
+        return batch
+
+    def _loop(self) -> None:
+        torch.cuda.set_device(self.device)
+        while True:
+            with self._cv:
+                while not self._pending and not self._stop:
+                    self._cv.wait()
+                if self._stop and not self._pending:
+                    return
+                batch = self._take_batch()
+            try:
+                keep = {r.op_id for r in batch}
+                for r in batch:
+                    self._admit(r.op_id, keep)
+                res = [self._ops[r.op_id].resident for r in batch]
+                outs, iters = H.cn_step_batched([x.handle for x in res], [x.u for x in res],
+                                                outs=[x.out for x in res])
+                now = time.perf_counter()
+                done = []
+                with self._cv:
+                    self.batches += 1
+                    for r, x, it in zip(batch, res, iters):
+                        x.u, x.out = x.out, x.u
+                        x.last_used = now
+                        st = self._ops[r.op_id]
+                        st.step += 1
+                        done.append((r, StepResult(r.op_id, st.step, it, now - r.arrival, len(batch))))
+                for r, out in done:
+                    r.future.set_result(out)
+            except BaseException as exc:  # surface to every waiting client
+                with self._cv:
+                    self._error = exc
+                    for r in batch:
+                        if not r.future.done():
+                            r.future.set_exception(exc)
+                    while self._pending:
+                        self._pending.popleft().future.set_exception(exc)
+                return
