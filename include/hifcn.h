@@ -68,9 +68,17 @@ typedef struct {
   double cg_tol;       /* stop when ||r||_2 <= cg_tol ||b||_2 (relative residual)                     */
   int cg_maxit;        /* iteration cap                                                                */
   int true_res_period; /* recompute r = b - A x every this many iterations (0 = never)                 */
+  double theta;        /* time-stepping weight: A = I - theta dt M, right-hand side
+                          u + (1 - theta) dt M u + dt r; 0.5 = Crank-Nicolson (Eq. CN),
+                          1 = backward Euler (Sec. 1); must lie in (0, 1]                           */
+  int x0_mode;         /* 0: PCG starts from x0 = 0 (Algorithm 1 as read); 1: warm start from u_k
+                          (cn_step) or from the input x (pcg_solve)                                   */
+  int solver;          /* 0: PCG (Algorithm 1); 1: direct, x = F^{-1} b without CG (the factor used
+                          as a solver, Sec. 3 Example 1), iterations reported as 0                    */
 } hif_options;
 
-/* Fills *opt with defaults: eps 1e-6, FP64, skel_edges_3d 1, tol 1e-10, maxit 1000, period 50. */
+/* Fills *opt with defaults: eps 1e-6, FP64, skel_edges_3d 1, tol 1e-10, maxit 1000, period 50,
+ * theta 0.5, x0_mode 0, solver 0. */
 void hif_default_options(hif_options *opt);
 
 typedef struct hif_handle hif_handle; /* opaque; owns all factor and work memory on the device */
@@ -159,10 +167,11 @@ int hif_matvec(hif_handle *h, const double *x, double *y, hif_stream stream);
 
 /* ---------------------------------------------------------------------------
  * pcg_solve - solve A x = b by PCG with preconditioner F^{-1} (Algorithm 1,
- * pcg(A, g, F^{-1})): x0 = 0, stop when ||r|| <= cg_tol ||b|| on the recurrence
- * residual, FP64 vectors and scalars, F^{-1} in the handle's precision.
+ * pcg(A, g, F^{-1})): x0 = 0 (or the input x when x0_mode = 1), stop when
+ * ||r|| <= cg_tol ||b|| on the recurrence residual, FP64 vectors and scalars,
+ * F^{-1} in the handle's precision; with solver = 1, x = F^{-1} b directly.
  *   b       device, N doubles.
- *   x       device, N doubles, output (input ignored).
+ *   x       device, N doubles, output (input used only as the warm start).
  *   iters   host, number of x updates (may be NULL).
  *   relres  host, true residual ||b - A x|| / ||b|| at exit (may be NULL).
  * Errors: HIF_EINVAL, HIF_ENOCONV (x holds the last iterate), HIF_ECUDA. */

@@ -113,11 +113,12 @@ def assemble_M(a_nodes: np.ndarray) -> sp.csr_matrix:
     return M * (1.0 / (h * h))
 
 
-def assemble_A(a_nodes: np.ndarray, dt: float) -> sp.csr_matrix:
-    """A = I - dt/2 M (Eq. CN), sparse SPD."""
+def assemble_A(a_nodes: np.ndarray, dt: float, theta: float = 0.5) -> sp.csr_matrix:
+    """A = I - theta dt M, sparse SPD: theta = 1/2 is Crank-Nicolson (Eq. CN),
+    theta = 1 the backward Euler scheme the introduction mentions."""
     M = assemble_M(a_nodes)
     N = M.shape[0]
-    A = sp.identity(N, format="csr") - (0.5 * dt) * M
+    A = sp.identity(N, format="csr") - (theta * dt) * M
     A.sort_indices()
     return A.tocsr()
 
@@ -131,10 +132,13 @@ def reaction(u: np.ndarray, kind: int, k1: float, k2: float) -> np.ndarray:
     raise ValueError(f"unknown reaction kind {kind}")
 
 
-def cn_rhs(a_nodes: np.ndarray, u: np.ndarray, dt: float, r: np.ndarray | None) -> np.ndarray:
-    """g = (I + dt/2 M) u^k + dt r^k (Eq. CN2 / first line of the loop in Algorithm 1)."""
+def cn_rhs(a_nodes: np.ndarray, u: np.ndarray, dt: float, r: np.ndarray | None,
+           theta: float = 0.5) -> np.ndarray:
+    """g = (I + (1 - theta) dt M) u^k + dt r^k: with theta = 1/2 the CN right-hand
+    side (Eq. CN2 / first line of the loop in Algorithm 1), with theta = 1 the
+    backward Euler one, u^k + dt r^k."""
     n = u.shape[0] + 1
-    g = u + 0.5 * dt * apply_M(a_nodes, u, 1.0 / n)
+    g = u + (1.0 - theta) * dt * apply_M(a_nodes, u, 1.0 / n) if theta != 1.0 else np.array(u, dtype=np.float64)
     if r is not None:
         g = g + dt * r
     return g

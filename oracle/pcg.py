@@ -20,14 +20,18 @@ from . import grid
 from . import hif
 
 
-def pcg(A, b: np.ndarray, precond, tol: float = 1e-10, maxit: int = 1000):
-    """Solve A x = b by PCG; returns (x, iters, relres_true, converged)."""
+def pcg(A, b: np.ndarray, precond, tol: float = 1e-10, maxit: int = 1000, x0=None):
+    """Solve A x = b by PCG; returns (x, iters, relres_true, converged).
+
+    x0 = None is the zero initial guess; a given x0 starts from it (warm start)."""
     b = np.asarray(b, dtype=np.float64).ravel()
     nb = float(np.linalg.norm(b))
-    x = np.zeros_like(b)
-    if nb == 0.0:
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64).ravel().copy()
+    if nb == 0.0 and x0 is None:
         return x, 0, 0.0, True
-    r = b.copy()
+    r = b - A @ x if x0 is not None else b.copy()
+    if nb == 0.0 or float(np.linalg.norm(r)) <= tol * nb:
+        return x, 0, (float(np.linalg.norm(r)) / nb if nb else 0.0), True
     z = precond(r)
     p = z.copy()
     rz = float(r @ z)
@@ -53,18 +57,27 @@ def pcg(A, b: np.ndarray, precond, tol: float = 1e-10, maxit: int = 1000):
 
 def cn_solve(a_nodes: np.ndarray, u0: np.ndarray, dt: float, steps: int, leaf: int,
              eps: float, reaction=(0, 0.0, 0.0), tol: float = 1e-10, factor=None,
-             skel_edges_3d: bool = True):
-    """Algorithm 1: returns (u after ``steps`` CN steps, per-step iteration counts, factor)."""
+             skel_edges_3d: bool = True, theta: float = 0.5, warm_start: bool = False,
+             direct: bool = False):
+    """Algorithm 1: returns (u after ``steps`` steps, per-step iteration counts, factor).
+
+    theta = 1/2 is Crank-Nicolson, theta = 1 backward Euler; warm_start starts
+    PCG from u^k instead of 0; direct replaces PCG by u^{k+1} = F^{-1} g (the
+    factor used as a solver, Sec. 3 Example 1), reporting 0 iterations."""
     dim = u0.ndim
     n = u0.shape[0] + 1
-    A = grid.assemble_A(a_nodes, dt)
+    A = grid.assemble_A(a_nodes, dt, theta)
     F = factor if factor is not None else hif.factor(A, n, dim, leaf, eps, skel_edges_3d)
     u = np.array(u0, dtype=np.float64)
     iters = []
     for _ in range(steps):
         r = grid.reaction(u, *reaction) if reaction[0] else None
-        g = grid.cn_rhs(a_nodes, u, dt, r)
-        x, it, _, _ = pcg(A, g.ravel(), lambda v: hif.apply_inverse(F, v), tol=tol)
+        g = grid.cn_rhs(a_nodes, u, dt, r, theta)
+        if direct:
+            x, it = hif.apply_inverse(F, g.ravel()), 0
+        else:
+            x, it, _, _ = pcg(A, g.ravel(), lambda v: hif.apply_inverse(F, v), tol=tol,
+                              x0=u.ravel() if warm_start else None)
         u = x.reshape(u.shape)
         iters.append(it)
     return u, iters, F

@@ -317,7 +317,9 @@ int create_handle(const hif_grid *grid, const double *a_nodes, double dt, const 
   h->h = 1.0 / grid->n;
   if (opt) h->opt = *opt;
   else hif_default_options(&h->opt);
-  if (h->opt.precision != HIF_FP64 && h->opt.precision != HIF_FP32) {
+  if ((h->opt.precision != HIF_FP64 && h->opt.precision != HIF_FP32) || !(h->opt.theta > 0.0) ||
+      !(h->opt.theta <= 1.0) || (h->opt.x0_mode != 0 && h->opt.x0_mode != 1) ||
+      (h->opt.solver != 0 && h->opt.solver != 1) || h->opt.cg_maxit < 0) {
     delete h;
     return HIF_EINVAL;
   }
@@ -470,6 +472,9 @@ void hif_default_options(hif_options *opt) {
   opt->cg_tol = 1e-10;
   opt->cg_maxit = 1000;
   opt->true_res_period = 50;
+  opt->theta = 0.5;
+  opt->x0_mode = 0;
+  opt->solver = 0;
 }
 
 int hif_setup(const hif_grid *grid, const double *a_nodes, double dt, const hif_options *opt,

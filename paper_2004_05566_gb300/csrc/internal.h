@@ -160,7 +160,8 @@ struct hif_handle {
   // PCG work space (FP64)
   double *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *g = nullptr;
   double *xsol = nullptr;             // solution buffer of the graph-captured solve
-  void *pcg_graph[2] = {nullptr, nullptr};  // captured PCG loop per apply precision
+  void *pcg_graph[4] = {nullptr, nullptr, nullptr, nullptr};  // captured PCG loop per
+                                                             // (precision, warm start)
   cudaStream_t cap_stream = nullptr;  // private stream used for graph capture
   bool use_graph = true;
   bool use_tma = true;                // bulk-copy staging of the leaf cell blocks

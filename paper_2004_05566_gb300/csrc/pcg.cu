@@ -252,8 +252,53 @@ struct PcgGraph {
   long long prologue = 0, body = 0;  // kernel launches
 };
 
+// warm start: x given, r = b - A x, z-input = r, partials of r.r and b.b
 template <typename TZ>
-int build_pcg_graph(Handle *h, TZ *z, PcgGraph *G) {
+__global__ void __launch_bounds__(NT) k_start_warm(const double *__restrict__ b,
+                                                   const double *__restrict__ x, double *__restrict__ r,
+                                                   TZ *__restrict__ zin, StencilArgs st,
+                                                   double *__restrict__ part_rr,
+                                                   double *__restrict__ part_bb) {
+  __shared__ double sm[NT / 32];
+  double arr = 0.0, abb = 0.0;
+  for (long long j = blockIdx.x * (long long)NT + threadIdx.x; j < st.N; j += (long long)gridDim.x * NT) {
+    const double bj = b[j];
+    const double rj = bj - stencil_row(x, st.diag, st.wx, st.wy, st.wz, st.dim, st.n, j);
+    r[j] = rj;
+    zin[j] = (TZ)rj;
+    arr += rj * rj;
+    abb += bj * bj;
+  }
+  double t = block_sum<NT>(arr, sm);
+  if (threadIdx.x == 0) part_rr[blockIdx.x] = t;
+  t = block_sum<NT>(abb, sm);
+  if (threadIdx.x == 0) part_bb[blockIdx.x] = t;
+}
+
+// warm-start scalar phase: b.b, r.r, counters; loop condition (graph) when
+// the start is not converged already.  For b = 0 the solution is x = 0, which
+// the warp writes itself (a degenerate case, not worth a separate launch).
+template <bool kGraph>
+__global__ void k_scalar_start_warm(double *__restrict__ s, const double *__restrict__ part_rr,
+                                    const double *__restrict__ part_bb, int np, double tol2,
+                                    double *__restrict__ x, long long N,
+                                    cudaGraphConditionalHandle cond) {
+  const double rr = warp_sum_partials(part_rr, np);
+  const double bb = warp_sum_partials(part_bb, np);
+  if (bb == 0.0)
+    for (long long j = threadIdx.x; j < N; j += 32) x[j] = 0.0;
+  if (threadIdx.x != 0) return;
+  s[S_BB] = bb;
+  s[S_RR] = rr;
+  s[S_RZ] = 0.0;
+  s[S_IT] = 0.0;
+  const bool conv = bb == 0.0 || rr <= tol2 * bb;
+  s[S_CONV] = conv ? 1.0 : 0.0;
+  if constexpr (kGraph) cudaGraphSetConditional(cond, conv ? 0u : 1u);
+}
+
+template <typename TZ>
+int build_pcg_graph(Handle *h, TZ *z, PcgGraph *G, bool warm) {
   if (!h->cap_stream) HIF_CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   cudaStream_t cs = h->cap_stream;
   const int nb = h->nblocks_vec;
@@ -277,8 +322,13 @@ int build_pcg_graph(Handle *h, TZ *z, PcgGraph *G) {
   cudaGraphConditionalHandle cond;
   HIF_CUDA_TRY(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &graph, &deps, nullptr, &ndeps));
   HIF_CUDA_TRY(cudaGraphConditionalHandleCreate(&cond, graph, 0, cudaGraphCondAssignDefault));
-  k_start<TZ><<<nb, NT, 0, cs>>>(h->g, h->xsol, h->r, z, N, part);
-  k_scalar_start<<<1, 32, 0, cs>>>(sc, part, nb, cond);
+  if (warm) {  // x0 = xsol as set by the caller
+    k_start_warm<TZ><<<nb, NT, 0, cs>>>(h->g, h->xsol, h->r, z, st, part, part + nb);
+    k_scalar_start_warm<true><<<1, 32, 0, cs>>>(sc, part, part + nb, nb, tol2, h->xsol, N, cond);
+  } else {
+    k_start<TZ><<<nb, NT, 0, cs>>>(h->g, h->xsol, h->r, z, N, part);
+    k_scalar_start<<<1, 32, 0, cs>>>(sc, part, nb, cond);
+  }
   HIF_CUDA_TRY(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &graph, &deps, nullptr, &ndeps));
   cudaGraphNodeParams cp = {};
   cp.type = cudaGraphNodeTypeConditional;
@@ -324,7 +374,7 @@ int ensure_pcg_graph(Handle *h, TZ *z, int slot, cudaStream_t s) {
   if (h->pcg_graph[slot]) return HIF_OK;
   HIF_CUDA_TRY(cudaStreamSynchronize(s));  // the capture stream does not order with s
   PcgGraph *G = new PcgGraph();
-  int st = build_pcg_graph<TZ>(h, z, G);
+  int st = build_pcg_graph<TZ>(h, z, G, slot >= 2);
   if (st != HIF_OK) {
     if (G->exec) cudaGraphExecDestroy(G->exec);
     if (G->graph) cudaGraphDestroy(G->graph);
@@ -354,6 +404,11 @@ int pcg_graph_finish(Handle *h, int slot, int *iters_out) {
   return h->host_scal[S_CONV] != 0.0 ? HIF_OK : HIF_ENOCONV;
 }
 
+int graph_slot(const Handle *h) {
+  const int p = (h->opt.precision == HIF_FP32 && h->has_f32) ? 1 : 0;
+  return p + (h->opt.x0_mode == 1 ? 2 : 0);
+}
+
 template <typename TZ>
 int pcg_graph_impl(Handle *h, TZ *z, int slot, int *iters_out, cudaStream_t s) {
   HIF_TRY(ensure_pcg_graph<TZ>(h, z, slot, s));
@@ -364,7 +419,7 @@ int pcg_graph_impl(Handle *h, TZ *z, int slot, int *iters_out, cudaStream_t s) {
 
 template <typename TZ>
 int pcg_impl(Handle *h, const double *b, double *x, TZ *z, int *iters_out, double *relres_out,
-             cudaStream_t s) {
+             cudaStream_t s, bool warm = false) {
   const int nb = h->nblocks_vec;
   const long long N = h->N;
   double *part = h->partials;
@@ -376,16 +431,23 @@ int pcg_impl(Handle *h, const double *b, double *x, TZ *z, int *iters_out, doubl
     else return apply_inplace_f32(h, (float *)v, s);
   };
 
-  k_start<TZ><<<nb, NT, 0, s>>>(b, x, h->r, z, N, part);
-  note_launch();
-  k_scalar<<<1, 32, 0, s>>>(sc, part, nb, 4, tol2);
-  note_launch();
+  if (warm) {
+    k_start_warm<TZ><<<nb, NT, 0, s>>>(b, x, h->r, z, st, part, part + nb);
+    k_scalar_start_warm<false><<<1, 32, 0, s>>>(sc, part, part + nb, nb, tol2, x, N, 0);
+  } else {
+    k_start<TZ><<<nb, NT, 0, s>>>(b, x, h->r, z, N, part);
+    k_scalar<<<1, 32, 0, s>>>(sc, part, nb, 4, tol2);
+  }
+  note_launch(2);
   HIF_CUDA_TRY(cudaMemcpyAsync(h->host_scal, sc, 16 * sizeof(double), cudaMemcpyDeviceToHost, s));
   HIF_CUDA_TRY(cudaStreamSynchronize(s));
   const double bb = h->host_scal[S_BB];
-  if (bb == 0.0) {
+  if (bb == 0.0 || (warm && h->host_scal[S_CONV] != 0.0)) {
     if (iters_out) *iters_out = 0;
-    if (relres_out) *relres_out = 0.0;
+    if (relres_out) {
+      HIF_CUDA_TRY(cudaStreamSynchronize(s));
+      *relres_out = bb == 0.0 ? 0.0 : sqrt(h->host_scal[S_RR] / bb);
+    }
     return HIF_OK;
   }
   HIF_TRY(precond(z));
@@ -406,9 +468,10 @@ int pcg_impl(Handle *h, const double *b, double *x, TZ *z, int *iters_out, doubl
     k_update_xr<TZ><<<nb, NT, 0, s>>>(x, h->r, h->p, h->q, z, sc, N, part);
     note_launch();
     ++it;
-    if (period > 0 && it % period == 0)
+    if (period > 0 && it % period == 0) {
       k_true_residual<TZ><<<nb, NT, 0, s>>>(b, x, h->r, z, st, part);
       note_launch();
+    }
     k_scalar<<<1, 32, 0, s>>>(sc, part, nb, 1, tol2);
     note_launch();
     HIF_CUDA_TRY(cudaGetLastError());
@@ -443,25 +506,42 @@ int pcg_impl(Handle *h, const double *b, double *x, TZ *z, int *iters_out, doubl
 
 }  // namespace
 
-int pcg(Handle *h, const double *b, double *x, int *iters, double *relres, cudaStream_t s) {
+// Solve A x = b with b already in h->g (when b == h->g) or given; x0 is the
+// warm start (ignored unless x0_mode = 1); the solution goes to x.
+int solve_core(Handle *h, const double *b, const double *x0, double *x, int *iters, double *relres,
+               cudaStream_t s) {
   const bool f32 = h->opt.precision == HIF_FP32 && h->has_f32;
-  if (!h->use_graph || h->stats_on) {
-    if (f32) return pcg_impl<float>(h, b, x, h->f32.work, iters, relres, s);
-    return pcg_impl<double>(h, b, x, h->z, iters, relres, s);
+  const bool warm = h->opt.x0_mode == 1;
+  int st = HIF_OK;
+  if (h->opt.solver == 1) {  // direct: x = F^{-1} b
+    HIF_TRY(apply_inverse(h, b, x, f32 ? HIF_FP32 : HIF_FP64, s));
+    if (iters) *iters = 0;
+  } else if (!h->use_graph || h->stats_on) {
+    if (warm && x0 != x)
+      HIF_CUDA_TRY(cudaMemcpyAsync(x, x0, h->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (f32) st = pcg_impl<float>(h, b, x, h->f32.work, iters, relres, s, warm);
+    else st = pcg_impl<double>(h, b, x, h->z, iters, relres, s, warm);
+    return st;
+  } else {
+    if (b != h->g)
+      HIF_CUDA_TRY(cudaMemcpyAsync(h->g, b, h->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (warm)
+      HIF_CUDA_TRY(cudaMemcpyAsync(h->xsol, x0, h->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    const int slot = graph_slot(h);
+    st = f32 ? pcg_graph_impl<float>(h, h->f32.work, slot, iters, s)
+             : pcg_graph_impl<double>(h, h->z, slot, iters, s);
+    if (st != HIF_OK && st != HIF_ENOCONV) return st;
+    HIF_CUDA_TRY(cudaMemcpyAsync(x, h->xsol, h->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    note_launch();
   }
-  if (b != h->g)
-    HIF_CUDA_TRY(cudaMemcpyAsync(h->g, b, h->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  int st = f32 ? pcg_graph_impl<float>(h, h->f32.work, 1, iters, s)
-               : pcg_graph_impl<double>(h, h->z, 0, iters, s);
-  if (st != HIF_OK && st != HIF_ENOCONV) return st;
-  HIF_CUDA_TRY(cudaMemcpyAsync(x, h->xsol, h->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  note_launch();
   if (relres) {
     const int nb = h->nblocks_vec;
     StencilArgs sta{h->diag, h->wx, h->wy, h->wz, h->grid.dim, h->grid.n, h->N};
-    k_resid_norm<<<nb, NT, 0, s>>>(h->g, h->xsol, sta, h->partials);
+    k_resid_norm<<<nb, NT, 0, s>>>(b, x, sta, h->partials);
+    k_dot<double><<<nb, NT, 0, s>>>(b, b, h->N, h->partials + nb);
     k_scalar<<<1, 32, 0, s>>>(h->scal, h->partials, nb, 1, h->opt.cg_tol * h->opt.cg_tol);
-    note_launch(2);
+    k_scalar<<<1, 32, 0, s>>>(h->scal, h->partials + nb, nb, 4, 0.0);
+    note_launch(4);
     HIF_CUDA_TRY(cudaMemcpyAsync(h->host_scal, h->scal, 16 * sizeof(double), cudaMemcpyDeviceToHost, s));
     HIF_CUDA_TRY(cudaStreamSynchronize(s));
     *relres = h->host_scal[S_BB] > 0.0 ? sqrt(h->host_scal[S_RR] / h->host_scal[S_BB]) : 0.0;
@@ -469,10 +549,14 @@ int pcg(Handle *h, const double *b, double *x, int *iters, double *relres, cudaS
   return st;
 }
 
+int pcg(Handle *h, const double *b, double *x, int *iters, double *relres, cudaStream_t s) {
+  return solve_core(h, b, x, x, iters, relres, s);
+}
+
 int cn(Handle *h, const double *u, const double *r, double *u1, int *iters, cudaStream_t s) {
-  // g = (I + dt/2 M) u + dt r into the handle's RHS buffer, then A u1 = g.
+  // g = (I + (1 - theta) dt M) u + dt r into the handle's RHS buffer, then A u1 = g.
   HIF_TRY(cn_rhs(h, u, r, h->g, s));
-  return pcg(h, h->g, u1, iters, nullptr, s);
+  return solve_core(h, h->g, u, u1, iters, nullptr, s);
 }
 
 // Several CN steps, one per handle, overlapped on the GPU: each handle's
@@ -482,28 +566,31 @@ int cn(Handle *h, const double *u, const double *r, double *u1, int *iters, cuda
 int cn_batched(Handle *const *hs, int count, const double *const *u, const double *const *r,
                double *const *u1, int *iters, cudaStream_t s) {
   std::vector<int> status(count, HIF_OK);
+  auto sequential = [](const Handle *h) { return !h->use_graph || h->stats_on || h->opt.solver == 1; };
   for (int i = 0; i < count; ++i) {
     Handle *h = hs[i];
-    if (!h->use_graph || h->stats_on) {  // statistics mode: plain sequential steps
+    if (sequential(h)) {  // statistics mode or direct solver: plain steps in order
       int it = 0;
       status[i] = cn(h, u[i], r ? r[i] : nullptr, u1[i], &it, s);
       if (iters) iters[i] = it;
       continue;
     }
-    const bool f32 = h->opt.precision == HIF_FP32 && h->has_f32;
-    if (f32) HIF_TRY(ensure_pcg_graph<float>(h, h->f32.work, 1, s));
-    else HIF_TRY(ensure_pcg_graph<double>(h, h->z, 0, s));
+    const int slot = graph_slot(h);
+    if (slot & 1) HIF_TRY(ensure_pcg_graph<float>(h, h->f32.work, slot, s));
+    else HIF_TRY(ensure_pcg_graph<double>(h, h->z, slot, s));
   }
   cudaEvent_t ev;
   HIF_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
   cudaEventRecord(ev, s);
   for (int i = 0; i < count; ++i) {
     Handle *h = hs[i];
-    if (!h->use_graph || h->stats_on) continue;
-    const int slot = (h->opt.precision == HIF_FP32 && h->has_f32) ? 1 : 0;
+    if (sequential(h)) continue;
+    const int slot = graph_slot(h);
     cudaStream_t hs_ = h->cap_stream;
     HIF_CUDA_TRY(cudaStreamWaitEvent(hs_, ev, 0));
     HIF_TRY(cn_rhs(h, u[i], r ? r[i] : nullptr, h->g, hs_));
+    if (slot >= 2)
+      HIF_CUDA_TRY(cudaMemcpyAsync(h->xsol, u[i], h->N * sizeof(double), cudaMemcpyDeviceToDevice, hs_));
     HIF_TRY(pcg_graph_launch(h, slot, hs_));
     HIF_CUDA_TRY(cudaMemcpyAsync(u1[i], h->xsol, h->N * sizeof(double), cudaMemcpyDeviceToDevice, hs_));
     // a handle listed again later must see this step's scalars before they are overwritten
@@ -518,7 +605,7 @@ int cn_batched(Handle *const *hs, int count, const double *const *u, const doubl
   int result = HIF_OK;
   for (int i = 0; i < count; ++i) {
     Handle *h = hs[i];
-    if (!h->use_graph || h->stats_on) {
+    if (sequential(h)) {
       if (status[i] != HIF_OK && result == HIF_OK) result = status[i];
       continue;
     }
@@ -527,8 +614,7 @@ int cn_batched(Handle *const *hs, int count, const double *const *u, const doubl
       st = HIF_OK;
     } else if (st == HIF_OK) {
       HIF_CUDA_TRY(cudaStreamSynchronize(h->cap_stream));
-      const int slot = (h->opt.precision == HIF_FP32 && h->has_f32) ? 1 : 0;
-      st = pcg_graph_finish(h, slot, iters ? &iters[i] : nullptr);
+      st = pcg_graph_finish(h, graph_slot(h), iters ? &iters[i] : nullptr);
     }
     note_launch(2);  // RHS kernel and result copy
     if (st != HIF_OK && result == HIF_OK) result = st;
@@ -538,7 +624,7 @@ int cn_batched(Handle *const *hs, int count, const double *const *u, const doubl
 }
 
 void destroy_pcg_graphs(Handle *h) {
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < 4; ++i) {
     PcgGraph *G = static_cast<PcgGraph *>(h->pcg_graph[i]);
     if (!G) continue;
     if (G->exec) cudaGraphExecDestroy(G->exec);

@@ -48,17 +48,23 @@ __global__ void k_matvec(const double *__restrict__ x, double *__restrict__ y,
     y[j] = stencil_row(x, diag, wx, wy, wz, dim, n, j);
 }
 
-// g = (I + dt/2 M) u + dt r = 2u - A u + dt r, with r either given or the
-// built-in logistic reaction k1 u (1 - u/k2) (Eq. nr), explicit in time.
+// g = (I + (1 - theta) dt M) u + dt r (Eq. CN2 for theta = 1/2), with r either
+// given or the built-in logistic reaction k1 u (1 - u/k2) (Eq. nr), explicit
+// in time.
+// With A = I - theta dt M:  (I + (1 - theta) dt M) u = u + kappa (u - A u),
+// kappa = (1 - theta) / theta; for theta = 1/2 this is 2u - A u.
 __global__ void k_cn_rhs(const double *__restrict__ u, const double *__restrict__ r,
                          double *__restrict__ g, const double *__restrict__ diag,
                          const double *__restrict__ wx, const double *__restrict__ wy,
                          const double *__restrict__ wz, int dim, int n, long long N, double dt,
-                         int kind, double k1, double inv_k2) {
+                         int kind, double k1, double inv_k2, double kappa) {
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < N;
        j += (long long)gridDim.x * blockDim.x) {
     double uj = u[j];
-    double v = 2.0 * uj - stencil_row(u, diag, wx, wy, wz, dim, n, j);
+    double v;
+    if (kappa == 1.0) v = 2.0 * uj - stencil_row(u, diag, wx, wy, wz, dim, n, j);
+    else if (kappa == 0.0) v = uj;
+    else v = uj + kappa * (uj - stencil_row(u, diag, wx, wy, wz, dim, n, j));
     if (r) v += dt * r[j];
     else if (kind == 1) v += dt * (k1 * uj * (1.0 - uj * inv_k2));
     g[j] = v;
@@ -73,7 +79,7 @@ int stencil_init(Handle *h, const double *a_nodes, cudaStream_t s) {
   HIF_TRY(dev_alloc(h, (void **)&h->wx, N * sizeof(double)));
   HIF_TRY(dev_alloc(h, (void **)&h->wy, N * sizeof(double)));
   if (h->grid.dim == 3) HIF_TRY(dev_alloc(h, (void **)&h->wz, N * sizeof(double)));
-  const double c = 0.5 * h->dt / (h->h * h->h);
+  const double c = h->opt.theta * h->dt / (h->h * h->h);  // A = I - theta dt M
   int nb = (int)((N + 255) / 256);
   k_stencil_init<<<nb, 256, 0, s>>>(a_nodes, h->diag, h->wx, h->wy, h->wz, h->grid.dim,
                                     h->grid.n, N, c);
@@ -92,9 +98,10 @@ int stencil_matvec(Handle *h, const double *x, double *y, cudaStream_t s) {
 
 int cn_rhs(Handle *h, const double *u, const double *r, double *g, cudaStream_t s) {
   double inv_k2 = h->react_k2 == 0.0 ? 0.0 : 1.0 / h->react_k2;
+  const double kappa = (1.0 - h->opt.theta) / h->opt.theta;
   k_cn_rhs<<<h->nblocks_vec, 256, 0, s>>>(u, r, g, h->diag, h->wx, h->wy, h->wz, h->grid.dim,
                                           h->grid.n, h->N, h->dt, h->react_kind, h->react_k1,
-                                          inv_k2);
+                                          inv_k2, kappa);
   note_launch();
   HIF_CUDA_TRY(cudaGetLastError());
   return HIF_OK;

@@ -36,7 +36,8 @@ class HifGrid(ctypes.Structure):
 
 class HifOptions(ctypes.Structure):
     _fields_ = [("eps", c_double), ("precision", c_int), ("skel_edges_3d", c_int),
-                ("cg_tol", c_double), ("cg_maxit", c_int), ("true_res_period", c_int)]
+                ("cg_tol", c_double), ("cg_maxit", c_int), ("true_res_period", c_int),
+                ("theta", c_double), ("x0_mode", c_int), ("solver", c_int)]
 
 
 class HifInfo(ctypes.Structure):
@@ -228,9 +229,12 @@ def hif_matvec(h: Handle, x: torch.Tensor, y: torch.Tensor = None, stream=None) 
 
 
 def pcg_solve(h: Handle, b: torch.Tensor, x: torch.Tensor = None, stream=None, allow_noconv=False):
-    """Solve A x = b by F^{-1}-preconditioned CG; returns (x, iters, relres)."""
+    """Solve A x = b by F^{-1}-preconditioned CG; returns (x, iters, relres).
+
+    With options.x0_mode = 1 the incoming x is the initial guess (zeros when
+    x is None); with options.solver = 1, x = F^{-1} b and iters = 0."""
     if x is None:
-        x = torch.empty_like(b)
+        x = torch.zeros_like(b)
     it = c_int(0)
     rr = c_double(0.0)
     _check("pcg_solve", lib().pcg_solve(h.ptr, _vec(b, h.N, "b"), _vec(x, h.N, "x"), byref(it),

@@ -59,3 +59,11 @@ def test_host_side_validation_without_gpu(lib):
     assert lib.hif_strerror(H.HIF_EINVAL) == b"invalid argument"
     o = H.default_options()
     assert abs(o.eps - 1e-6) < 1e-20 and o.true_res_period == 50 and o.cg_maxit == 1000
+    assert o.theta == 0.5 and o.x0_mode == 0 and o.solver == 0
+    good = H.HifGrid(2, 32, 8)
+    for field, value in (("theta", 0.0), ("theta", 1.5), ("x0_mode", 2), ("solver", -1),
+                         ("cg_maxit", -1)):
+        ob = H.default_options()
+        setattr(ob, field, value)
+        assert lib.hif_setup(ctypes.byref(good), ctypes.c_void_p(1), 1.0, ctypes.byref(ob), None,
+                             ctypes.byref(out)) == H.HIF_EINVAL, field

@@ -167,3 +167,42 @@ def test_cn_config1_full_size_matches_closed_form():
     exact = _dst_closed_form(w.u0, w.dt, w.steps)
     assert np.linalg.norm(u - exact) <= 1e-9 * np.linalg.norm(exact)
     assert max(iters) <= 3
+
+
+def _dst_be(u0, dt, steps):
+    """Exact backward-Euler evolution for a = 1: each DST-I mode is scaled by
+    1 / (1 - dt lam) per step."""
+    import scipy.fft
+    n = u0.shape[0] + 1
+    h = 1.0 / n
+    coef = scipy.fft.dstn(u0, type=1)
+    ks = np.arange(1, n)
+    lam = np.zeros(u0.shape)
+    for ax in range(u0.ndim):
+        s = [1] * u0.ndim
+        s[ax] = n - 1
+        lam = lam - (4.0 / h ** 2) * np.sin(ks * math.pi * h / 2).reshape(s) ** 2
+    return scipy.fft.idstn(coef * (1.0 / (1.0 - dt * lam)) ** steps, type=1)
+
+
+def test_backward_euler_matches_dst_closed_form():
+    n, m, dt, steps = 32, 8, 1e-2, 3
+    u0 = W.sine_modes_u0(n, 2, [(1, 1), (3, 2)], rng=np.random.default_rng(1), noise=0.05)
+    ones = np.ones((n + 1, n + 1))
+    u, iters, _ = pcg.cn_solve(ones, u0, dt, steps, m, 1e-6, tol=1e-12, theta=1.0)
+    exact = _dst_be(u0, dt, steps)
+    assert np.linalg.norm(u - exact) <= 1e-9 * np.linalg.norm(exact)
+
+
+def test_warm_start_and_direct_variants():
+    w = W.small_variable_2d(n=64, m=8, eps=1e-6, contrast=1e3, dt=0.5, corr_len=0.1)
+    cold, it_c, F = pcg.cn_solve(w.a_nodes, w.u0, w.dt, 3, w.leaf, w.eps, (1, 1.0, 1.0), tol=1e-11)
+    warm, it_w, _ = pcg.cn_solve(w.a_nodes, w.u0, w.dt, 3, w.leaf, w.eps, (1, 1.0, 1.0), tol=1e-11,
+                                 factor=F, warm_start=True)
+    direct, it_d, _ = pcg.cn_solve(w.a_nodes, w.u0, w.dt, 3, w.leaf, w.eps, (1, 1.0, 1.0),
+                                   factor=F, direct=True)
+    assert np.linalg.norm(warm - cold) <= 1e-9 * np.linalg.norm(cold)
+    assert sum(it_w) <= sum(it_c)
+    assert it_d == [0, 0, 0]
+    # the direct solve is accurate to the factor's precision (O(eps))
+    assert np.linalg.norm(direct - cold) <= 1e-3 * np.linalg.norm(cold)
