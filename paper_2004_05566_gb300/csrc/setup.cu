@@ -28,10 +28,16 @@
 // on one cell / entity; waits are __syncthreads only (no spin-waits).
 #include "internal.h"
 #include "device_common.cuh"
+#include "dense_batched.cuh"
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
 
 namespace hifcn {
 
@@ -53,6 +59,7 @@ struct SCell {
   long long S_off;    // S = A_II^{-1} (packed lower) in the level value pool
   long long dofs_off; // local DOF list (I then B), global indices
   long long bmap_off; // per B position: (group id, position in group)
+  long long kid_off;  // into the extend-add lists of this level (n + 1 entries)
 };
 
 struct SGroup {
@@ -70,12 +77,6 @@ struct SSkel {        // one skeletonized group of a sub-step
   long long row_off;  // into rowptr (R + 1 entries)
   long long ws_off;   // workspace (doubles)
   long long perm_off; // output pivot order (n ints)
-};
-
-struct SExt {         // one child of a parent in the extend-add
-  int child, parent;
-  int m;              // surviving boundary positions of the child
-  long long ent_off;  // into ext entries: (child local index, parent local index)
 };
 
 __device__ __forceinline__ bool owner_axis(int a, int b, int s, int nc, int c) {
@@ -150,100 +151,47 @@ __global__ void __launch_bounds__(NT) k_assemble_leaf(const SCell *__restrict__ 
 
 // ------------------------------------------------------------ extend-add (l > 0)
 
-__global__ void __launch_bounds__(NT) k_extend_add(const int *__restrict__ pchild, const SExt *__restrict__ ext,
-                                                   const int2 *__restrict__ ent,
-                                                   const SCell *__restrict__ pcells,
+// Parent frontal matrix from its children's Schur complements, as a gather:
+// entry (p, r) of the parent is the sum, over the children holding both DOFs,
+// of the children's entries, taken in increasing child order (deterministic,
+// no atomics).  Per parent position p, kid_ptr/kid_ent list the children that
+// hold it with the child-local index, sorted by child.  grid = (parents, column
+// chunks); entries no child holds are zero.
+__global__ void __launch_bounds__(NT) k_extend_add(const SCell *__restrict__ pcells,
                                                    const SCell *__restrict__ ccells,
+                                                   const long long *__restrict__ kid_ptr,
+                                                   const int2 *__restrict__ kid_ent,
                                                    const double *__restrict__ Fc,
                                                    double *__restrict__ Fp) {
+  __shared__ int2 lr[8];
+  __shared__ int nlr;
   const SCell P = pcells[blockIdx.x];
   const int np = P.nI + P.nB;
+  const long long *ptr = kid_ptr + P.kid_off;
   double *FP = Fp + P.F_off;
-  for (long long t = threadIdx.x; t < (long long)np * np; t += NT) FP[t] = 0.0;
-  __syncthreads();
-  for (int e = pchild[blockIdx.x]; e < pchild[blockIdx.x + 1]; ++e) {
-    const SExt x = ext[e];
-    const SCell C = ccells[x.child];
-    const int nc = C.nI + C.nB;
-    const double *FC = Fc + C.F_off;
-    const int2 *en = ent + x.ent_off;
-    const long long mm = (long long)x.m * x.m;
-    for (long long t = threadIdx.x; t < mm; t += NT) {
-      int a = (int)(t % x.m), b = (int)(t / x.m);
-      FP[en[a].y + (long long)en[b].y * np] += FC[en[a].x + (long long)en[b].x * nc];
-    }
-    __syncthreads();
-  }
-}
-
-// -------------------------------------------------------------- cell elimination
-
-__global__ void __launch_bounds__(NT) k_cell_eliminate(const SCell *__restrict__ cells,
-                                                       double *__restrict__ F,
-                                                       double *__restrict__ vals,
-                                                       int *__restrict__ err) {
-  extern __shared__ double sm[];  // col[n], row[nI]
-  const SCell c = cells[blockIdx.x];
-  const int nI = c.nI, nB = c.nB, nn = nI + nB;
-  double *A = F + c.F_off;
-  double *col = sm;
-  double *row = sm + nn;
-  __shared__ double piv;
-  // partial right-looking Cholesky over the first nI columns (lower triangle)
-  for (int k = 0; k < nI; ++k) {
+  for (int r = blockIdx.y; r < np; r += gridDim.y) {
     if (threadIdx.x == 0) {
-      double d = A[k + (long long)k * nn];
-      if (!(d > 0.0)) {
-        atomicExch(err, 1);
-        d = 1.0;
+      const long long b = ptr[r];
+      nlr = (int)min(ptr[r + 1] - b, 8LL);
+      for (int q = 0; q < nlr; ++q) lr[q] = kid_ent[b + q];
+    }
+    __syncthreads();
+    const int nr = nlr;
+    for (int p = threadIdx.x; p < np; p += NT) {
+      const long long pb = ptr[p], pe = ptr[p + 1];
+      long long a = pb;
+      double acc = 0.0;
+      for (int q = 0; q < nr; ++q) {
+        const int child = lr[q].x;
+        while (a < pe && kid_ent[a].x < child) ++a;
+        if (a < pe && kid_ent[a].x == child) {
+          const SCell C = ccells[child];
+          acc += Fc[C.F_off + kid_ent[a].y + (long long)lr[q].y * (C.nI + C.nB)];
+        }
       }
-      d = sqrt(d);
-      A[k + (long long)k * nn] = d;
-      piv = d;
+      FP[p + (long long)r * np] = acc;
     }
     __syncthreads();
-    const double inv = 1.0 / piv;
-    for (int i = k + 1 + threadIdx.x; i < nn; i += NT) {
-      double v = A[i + (long long)k * nn] * inv;
-      A[i + (long long)k * nn] = v;
-      col[i] = v;
-    }
-    __syncthreads();
-    const int m = nn - k - 1;
-    const long long mm = (long long)m * m;
-    for (long long t = threadIdx.x; t < mm; t += NT) {
-      int i = k + 1 + (int)(t % m), j = k + 1 + (int)(t / m);
-      if (i >= j) A[i + (long long)j * nn] -= col[i] * col[j];
-    }
-    __syncthreads();
-  }
-  // G = L^{-1}, row by row: G[i][c] = (delta_ic - sum_{k=c}^{i-1} L[i][k] G[k][c]) / L[i][i]
-  double *G = vals + c.G_off;
-  for (int i = 0; i < nI; ++i) {
-    for (int k = threadIdx.x; k <= i; k += NT) row[k] = A[i + (long long)k * nn];
-    __syncthreads();
-    const double dinv = 1.0 / row[i];
-    for (int cc = threadIdx.x; cc <= i; cc += NT) {
-      double acc = (cc == i) ? 1.0 : 0.0;
-      for (int k = cc; k < i; ++k) acc -= row[k] * G[tri_off(k) + cc];
-      G[tri_off(i) + cc] = acc * dinv;
-    }
-    __syncthreads();
-  }
-  // V[b][cc] = sum_{i >= cc} W^T[b][i] G[i][cc], W^T = A[nI + b][i]
-  double *V = vals + c.V_off;
-  const long long nv = (long long)nB * nI, vs = pad4(nI);
-  for (long long t = threadIdx.x; t < nv; t += NT) {
-    int b = (int)(t % nB), cc = (int)(t / nB);
-    double acc = 0.0;
-    for (int i = cc; i < nI; ++i) acc += A[nI + b + (long long)i * nn] * G[tri_off(i) + cc];
-    V[(long long)b * vs + cc] = acc;
-  }
-  // symmetrize the Schur complement block (upper <- lower)
-  const long long nbb = (long long)nB * nB;
-  for (long long t = threadIdx.x; t < nbb; t += NT) {
-    int p = (int)(t % nB), q = (int)(t / nB);
-    if (q > p) A[nI + p + (long long)(nI + q) * nn] = A[nI + q + (long long)(nI + p) * nn];
   }
 }
 
@@ -290,46 +238,73 @@ __device__ void cta_chol_inv(double *D, double *Li, int n, int *err) {
   }
 }
 
-__global__ void __launch_bounds__(NT) k_group_diag(const SGroup *__restrict__ groups,
-                                                   const int2 *__restrict__ gcells,
-                                                   const SCell *__restrict__ cells,
-                                                   const double *__restrict__ F,
-                                                   double *__restrict__ Dscr,
-                                                   double *__restrict__ Linv, int *__restrict__ err) {
+// Diagonal block of each separator entity, summed over its adjacent cells'
+// frontal matrices (each cell holds its share), column major n x n at D_off.
+// grid = (groups, chunks).
+__global__ void __launch_bounds__(NT) k_group_gather_D(const SGroup *__restrict__ groups,
+                                                       const int2 *__restrict__ gcells,
+                                                       const SCell *__restrict__ cells,
+                                                       const double *__restrict__ F,
+                                                       double *__restrict__ Dscr) {
   const SGroup g = groups[blockIdx.x];
   const int n = g.n;
   double *D = Dscr + g.D_off;
-  for (int t = threadIdx.x; t < n * n; t += NT) {
-    int a = t / n, b = t % n;
+  for (long long t = blockIdx.y * (long long)NT + threadIdx.x; t < (long long)n * n;
+       t += (long long)gridDim.y * NT) {
+    const int a = (int)(t % n), b = (int)(t / n);
     double acc = 0.0;
     for (int q = 0; q < g.ncell; ++q) {
-      int2 cl = gcells[g.gc_off + q];
+      const int2 cl = gcells[g.gc_off + q];
       const SCell c = cells[cl.x];
       const int nn = c.nI + c.nB;
       acc += F[c.F_off + (c.nI + cl.y + a) + (long long)(c.nI + cl.y + b) * nn];
     }
     D[t] = acc;
   }
-  __syncthreads();
-  cta_chol_inv(D, Linv + g.Linv_off, n, err);
 }
 
-__global__ void __launch_bounds__(NT) k_cell_scale(const SCell *__restrict__ cells,
-                                                   const int2 *__restrict__ bmap,
-                                                   const SGroup *__restrict__ groups,
-                                                   const int2 *__restrict__ gcells,
-                                                   const double *__restrict__ Linv,
-                                                   double *__restrict__ F, double *__restrict__ S) {
+// Dense descriptor of an entity's diagonal block for the batched Cholesky.
+struct JBlock {
+  int nI, nB;
+  long long F_off, G_off, V_off;
+};
+
+// Linv (n x n row major, zero above the diagonal) from the packed inverse
+// factor.  grid = (groups, chunks).
+__global__ void __launch_bounds__(NT) k_unpack_Linv(const SGroup *__restrict__ groups,
+                                                    const JBlock *__restrict__ jb,
+                                                    const double *__restrict__ Gp,
+                                                    double *__restrict__ Linv) {
+  const SGroup g = groups[blockIdx.x];
+  const int n = g.n;
+  const double *G = Gp + jb[blockIdx.x].G_off;
+  double *Li = Linv + g.Linv_off;
+  for (long long t = blockIdx.y * (long long)NT + threadIdx.x; t < (long long)n * n;
+       t += (long long)gridDim.y * NT) {
+    const int i = (int)(t / n), j = (int)(t % n);
+    Li[t] = j <= i ? G[tri_off(i) + j] : 0.0;
+  }
+}
+
+// Block Jacobi on a cell's boundary block, F_BB <- D F_BB D^T with D the
+// block-diagonal of the entities' L^{-1}; the entities' own diagonal blocks
+// become I (owner cell) or 0.  Two passes over (cells, chunks):
+// rows first (Sc = D F_BB), then columns (F_BB = Sc D^T).
+__global__ void __launch_bounds__(NT) k_cell_scale_rows(const SCell *__restrict__ cells,
+                                                        const int2 *__restrict__ bmap,
+                                                        const SGroup *__restrict__ groups,
+                                                        const double *__restrict__ Linv,
+                                                        const double *__restrict__ F,
+                                                        double *__restrict__ S) {
   const SCell c = cells[blockIdx.x];
   const int nI = c.nI, nB = c.nB, nn = nI + nB;
-  double *A = F + c.F_off;
+  const double *A = F + c.F_off;
   double *Sc = S + c.Sc_off;
   const int2 *bm = bmap + c.bmap_off;
   const long long nbb = (long long)nB * nB;
-  // S = D F_BB (rows of every group scaled by its L^{-1})
-  for (long long t = threadIdx.x; t < nbb; t += NT) {
-    int p = (int)(t % nB), q = (int)(t / nB);
-    int2 gp = bm[p];
+  for (long long t = blockIdx.y * (long long)NT + threadIdx.x; t < nbb; t += (long long)gridDim.y * NT) {
+    const int p = (int)(t % nB), q = (int)(t / nB);
+    const int2 gp = bm[p];
     const SGroup g = groups[gp.x];
     const int o = p - gp.y;
     const double *Li = Linv + g.Linv_off + (long long)gp.y * g.n;
@@ -337,11 +312,24 @@ __global__ void __launch_bounds__(NT) k_cell_scale(const SCell *__restrict__ cel
     for (int b = 0; b <= gp.y; ++b) acc += Li[b] * A[nI + o + b + (long long)(nI + q) * nn];
     Sc[p + (long long)q * nB] = acc;
   }
-  __syncthreads();
-  // F_BB = S D^T, then the diagonal blocks become I (owner cell) or 0
-  for (long long t = threadIdx.x; t < nbb; t += NT) {
-    int p = (int)(t % nB), q = (int)(t / nB);
-    int2 gp = bm[p], gq = bm[q];
+}
+
+__global__ void __launch_bounds__(NT) k_cell_scale_cols(const SCell *__restrict__ cells,
+                                                        const int2 *__restrict__ bmap,
+                                                        const SGroup *__restrict__ groups,
+                                                        const int2 *__restrict__ gcells,
+                                                        const double *__restrict__ Linv,
+                                                        double *__restrict__ F,
+                                                        const double *__restrict__ S) {
+  const SCell c = cells[blockIdx.x];
+  const int nI = c.nI, nB = c.nB, nn = nI + nB;
+  double *A = F + c.F_off;
+  const double *Sc = S + c.Sc_off;
+  const int2 *bm = bmap + c.bmap_off;
+  const long long nbb = (long long)nB * nB;
+  for (long long t = blockIdx.y * (long long)NT + threadIdx.x; t < nbb; t += (long long)gridDim.y * NT) {
+    const int p = (int)(t % nB), q = (int)(t / nB);
+    const int2 gp = bm[p], gq = bm[q];
     double v;
     if (gp.x == gq.x) {
       const SGroup g = groups[gp.x];
@@ -738,6 +726,42 @@ int set_smem(const void *fn, size_t bytes) {
 
 }  // namespace
 
+int max_front(const std::vector<SCell> &cells) {
+  int m = 0;
+  for (auto &c : cells) m = std::max(m, c.nI + c.nB);
+  return m;
+}
+
+// Optional per-phase timing of the factorization (HIFCN_SETUP_TIMING=1):
+// events on the setup stream, printed to stderr when the setup ends.
+struct PhaseTimer {
+  bool on = false;
+  cudaStream_t s = nullptr;
+  std::vector<std::pair<std::string, cudaEvent_t>> marks;
+  explicit PhaseTimer(cudaStream_t st) : s(st) {
+    const char *e = getenv("HIFCN_SETUP_TIMING");
+    on = e && e[0] == '1';
+    mark("start");
+  }
+  void mark(const std::string &what) {
+    if (!on) return;
+    cudaEvent_t ev;
+    cudaEventCreate(&ev);
+    cudaEventRecord(ev, s);
+    marks.emplace_back(what, ev);
+  }
+  ~PhaseTimer() {
+    if (!on) return;
+    cudaStreamSynchronize(s);
+    for (size_t i = 1; i < marks.size(); ++i) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, marks[i - 1].second, marks[i].second);
+      fprintf(stderr, "[hif setup] %-28s %10.3f ms\n", marks[i].first.c_str(), ms);
+    }
+    for (auto &m : marks) cudaEventDestroy(m.second);
+  }
+};
+
 int gpu_setup(Handle *h, const double *a_nodes, cudaStream_t s) {
   (void)a_nodes;  // the stencil coefficients were assembled from it in stencil_init
   const int dim = h->grid.dim, n = h->grid.n, leaf = h->grid.leaf, L = h->L;
@@ -748,6 +772,7 @@ int gpu_setup(Handle *h, const double *a_nodes, cudaStream_t s) {
   HIF_TRY(keep.alloc(&derr, 1));
   HIF_CUDA_TRY(cudaMemsetAsync(derr, 0, sizeof(int), s));
 
+  PhaseTimer tm(s);
   std::vector<int> active(N);
   for (long long d = 0; d < N; ++d) active[d] = (int)d;
   std::vector<char> alive(N, 1);
@@ -774,7 +799,7 @@ int gpu_setup(Handle *h, const double *a_nodes, cudaStream_t s) {
     std::vector<SCell> cells(ncells);
     std::vector<int> cdofs;
     std::vector<int2> bmap;
-    long long foff = 0, voff = 0, soff = 0;
+    long long foff = 0, voff = 0, soff = 0, kid_total = 0;
     for (int c = 0; c < ncells; ++c) {
       SCell &C = cells[c];
       C.nI = (int)P.cI[c].size();
@@ -790,6 +815,8 @@ int gpu_setup(Handle *h, const double *a_nodes, cudaStream_t s) {
       voff += (long long)C.nB * pad4(C.nI);
       C.Sc_off = soff;
       soff += (long long)C.nB * C.nB;
+      C.kid_off = kid_total;
+      kid_total += nn + 1;
       C.dofs_off = (long long)cdofs.size();
       C.bmap_off = (long long)bmap.size();
       cdofs.insert(cdofs.end(), P.cI[c].begin(), P.cI[c].end());
@@ -836,10 +863,8 @@ int gpu_setup(Handle *h, const double *a_nodes, cudaStream_t s) {
       note_launch();
       HIF_CUDA_TRY(cudaGetLastError());
     } else {
-      // extend-add of the children's surviving boundary entries
-      std::vector<int> pchild(ncells + 1, 0);
-      std::vector<SExt> ext;
-      std::vector<int2> ent;
+      // extend-add of the children's surviving boundary entries: per parent
+      // position, the children holding it (increasing child order)
       std::vector<int> lpos(N, -1);
       const int pnc = prev.nc;
       std::vector<std::vector<int>> kids(ncells);
@@ -848,67 +873,63 @@ int gpu_setup(Handle *h, const double *a_nodes, cudaStream_t s) {
         int pid = x / 2 + P.nc * (y / 2) + (dim == 3 ? P.nc * P.nc * (z / 2) : 0);
         kids[pid].push_back(c);
       }
-      for (int pc = 0; pc < ncells; ++pc) {
-        pchild[pc] = (int)ext.size();
-        int pos = 0;
-        for (int d : P.cI[pc]) lpos[d] = pos++;
-        for (int d : P.cB[pc]) lpos[d] = pos++;
-        for (int c : kids[pc]) {
-          SExt x;
-          x.child = c;
-          x.parent = pc;
-          x.ent_off = (long long)ent.size();
-          const int nIc = cells_prev[c].nI;
-          int m = 0;
-          for (int p = 0; p < (int)prev.cB[c].size(); ++p) {
-            int d = prev.cB[c][p];
-            if (!alive[d]) continue;
-            if (lpos[d] < 0) {
-              set_last_error("setup: surviving DOF missing from its parent cell");
-              return HIF_EINVAL;
-            }
-            ent.push_back(make_int2(nIc + p, lpos[d]));
-            ++m;
+      std::vector<long long> kid_ptr(kid_total + 1, 0);
+      std::vector<int2> kid_ent;
+      for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) {
+          long long run = 0;
+          for (long long t = 0; t < kid_total; ++t) {
+            const long long cnt = kid_ptr[t];
+            kid_ptr[t] = run;
+            run += cnt;
           }
-          x.m = m;
-          ext.push_back(x);
+          kid_ptr[kid_total] = run;
+          kid_ent.assign(run, make_int2(-1, -1));
         }
-        for (int d : P.cI[pc]) lpos[d] = -1;
-        for (int d : P.cB[pc]) lpos[d] = -1;
+        std::vector<long long> fill;
+        for (int pc = 0; pc < ncells; ++pc) {
+          int pos = 0;
+          for (int d : P.cI[pc]) lpos[d] = pos++;
+          for (int d : P.cB[pc]) lpos[d] = pos++;
+          const long long base = cells[pc].kid_off;
+          if (pass == 1) fill.assign(kid_ptr.begin() + base, kid_ptr.begin() + base + pos);
+          for (int c : kids[pc]) {
+            const int nIc = cells_prev[c].nI;
+            for (int q = 0; q < (int)prev.cB[c].size(); ++q) {
+              const int d = prev.cB[c][q];
+              if (!alive[d]) continue;
+              if (lpos[d] < 0) {
+                set_last_error("setup: surviving DOF missing from its parent cell");
+                return HIF_EINVAL;
+              }
+              if (pass == 0) ++kid_ptr[base + lpos[d]];
+              else kid_ent[fill[lpos[d]]++] = make_int2(c, nIc + q);
+            }
+          }
+          for (int d : P.cI[pc]) lpos[d] = -1;
+          for (int d : P.cB[pc]) lpos[d] = -1;
+        }
       }
-      pchild[ncells] = (int)ext.size();
-      int *dpchild = nullptr;
-      SExt *dext = nullptr;
-      int2 *dent = nullptr;
-      HIF_TRY(lvl.upload(&dpchild, pchild, s));
-      HIF_TRY(lvl.upload(&dext, ext, s));
-      HIF_TRY(lvl.upload(&dent, ent, s));
-      k_extend_add<<<ncells, NT, 0, s>>>(dpchild, dext, dent, dcells, dcells_prev, F_prev, F);
+      long long *dkid_ptr = nullptr;
+      int2 *dkid_ent = nullptr;
+      HIF_TRY(lvl.upload(&dkid_ptr, kid_ptr, s));
+      HIF_TRY(lvl.upload(&dkid_ent, kid_ent, s));
+      int max_np = 1;
+      for (auto &C : cells) max_np = std::max(max_np, C.nI + C.nB);
+      k_extend_add<<<dim3(ncells, std::min(max_np, 4096)), NT, 0, s>>>(dcells, dcells_prev, dkid_ptr,
+                                                                       dkid_ent, F_prev, F);
       note_launch();
       HIF_CUDA_TRY(cudaGetLastError());
       HIF_CUDA_TRY(cudaStreamSynchronize(s));
       keep.release(F_prev);
       keep.release(dcells_prev);
     }
+    tm.mark("l" + std::to_string(l) + " assemble");
 
-    // ---- cell elimination
-    {
-      int max_nn = 1, max_nI = 1;
-      for (auto &C : cells) {
-        max_nn = std::max(max_nn, C.nI + C.nB);
-        max_nI = std::max(max_nI, C.nI);
-      }
-      size_t sm = sizeof(double) * (size_t)(max_nn + max_nI);
-      if (sm > 200 * 1024) {
-        set_last_error("setup: frontal matrix too large for the shared-memory column buffer");
-        return HIF_EINVAL;
-      }
-      HIF_TRY(set_smem((const void *)k_cell_eliminate, sm));
-      k_cell_eliminate<<<ncells, NT, sm, s>>>(dcells, F, vals, derr);
-      note_launch();
-      HIF_CUDA_TRY(cudaGetLastError());
-      HIF_TRY(check_err(derr, s, "cell elimination"));
-    }
+    // ---- cell elimination (blocked, batched over the cells of the level)
+    HIF_TRY(dense::eliminate_cells<SCell>(cells, dcells, F, vals, derr, s));
+    HIF_TRY(check_err(derr, s, "cell elimination"));
+    tm.mark("l" + std::to_string(l) + " cells (nn<=" + std::to_string(max_front(cells)) + ")");
 
     // ---- apply descriptors of the cells (index pool) and the root
     if (l == L) {
@@ -957,13 +978,45 @@ int gpu_setup(Handle *h, const double *a_nodes, cudaStream_t s) {
     HIF_TRY(lvl.alloc(&Dscr, loff));
     HIF_TRY(lvl.alloc(&Sscr, soff));
     if (ng > 0) {
-      k_group_diag<<<ng, NT, 0, s>>>(dgroups, dgcells, dcells, F, Dscr, Linv, derr);
+      int max_gn = 1, max_nB = 1;
+      for (auto &G : groups) max_gn = std::max(max_gn, G.n);
+      for (auto &C : cells) max_nB = std::max(max_nB, C.nB);
+      auto chunks_for = [](long long work) {
+        long long ch = (work + 4LL * NT - 1) / (4LL * NT);
+        return (int)std::max(1LL, std::min(ch, 4096LL));
+      };
+      k_group_gather_D<<<dim3(ng, chunks_for((long long)max_gn * max_gn)), NT, 0, s>>>(
+          dgroups, dgcells, dcells, F, Dscr);
+      note_launch();
+      // Cholesky and inverse factor of every entity's diagonal block, batched
+      std::vector<JBlock> jbl(ng);
+      long long gpk = 0;
+      for (int g = 0; g < ng; ++g) {
+        jbl[g].nI = groups[g].n;
+        jbl[g].nB = 0;
+        jbl[g].F_off = groups[g].D_off;
+        jbl[g].G_off = gpk;
+        jbl[g].V_off = 0;
+        gpk += tri_off(groups[g].n);
+      }
+      JBlock *djbl = nullptr;
+      double *Gpk = nullptr;
+      HIF_TRY(lvl.upload(&djbl, jbl, s));
+      HIF_TRY(lvl.alloc(&Gpk, std::max(gpk, 1LL)));
+      HIF_CUDA_TRY(cudaMemsetAsync(Gpk, 0, std::max(gpk, 1LL) * sizeof(double), s));
+      HIF_TRY(dense::eliminate_cells<JBlock>(jbl, djbl, Dscr, Gpk, derr, s));
+      k_unpack_Linv<<<dim3(ng, chunks_for((long long)max_gn * max_gn)), NT, 0, s>>>(dgroups, djbl, Gpk,
+                                                                                    Linv);
       note_launch();
       HIF_CUDA_TRY(cudaGetLastError());
       HIF_TRY(check_err(derr, s, "block Jacobi"));
-      k_cell_scale<<<ncells, NT, 0, s>>>(dcells, dbmap, dgroups, dgcells, Linv, F, Sscr);
-      note_launch();
+      tm.mark("l" + std::to_string(l) + " jacobi diag");
+      const int sch = chunks_for((long long)max_nB * max_nB);
+      k_cell_scale_rows<<<dim3(ncells, sch), NT, 0, s>>>(dcells, dbmap, dgroups, Linv, F, Sscr);
+      k_cell_scale_cols<<<dim3(ncells, sch), NT, 0, s>>>(dcells, dbmap, dgroups, dgcells, Linv, F, Sscr);
+      note_launch(2);
       HIF_CUDA_TRY(cudaGetLastError());
+      tm.mark("l" + std::to_string(l) + " jacobi scale");
     }
 
     // ---- skeletonization sub-steps
@@ -1038,6 +1091,8 @@ int gpu_setup(Handle *h, const double *a_nodes, cudaStream_t s) {
       note_launch();
       HIF_CUDA_TRY(cudaGetLastError());
       HIF_TRY(check_err(derr, s, "skeletonization"));
+      tm.mark("l" + std::to_string(l) + " skel codim " + std::to_string(cd) + " (n<=" +
+              std::to_string(max_n) + ")");
       std::vector<int> kh(sk.size()), ph(poff);
       HIF_CUDA_TRY(cudaMemcpyAsync(kh.data(), dk, kh.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
       HIF_CUDA_TRY(cudaMemcpyAsync(ph.data(), dperm, ph.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
