@@ -212,6 +212,28 @@ int cn_step_batched(hif_handle *const *hs, int count, const double *const *u_k,
  * Errors: HIF_EINVAL. */
 int hif_set_reaction(hif_handle *h, int kind, double k1, double k2);
 
+/* hif_set_coefficient - replace the coefficient field a(x) of the operator
+ * (the stencil of A = I - theta dt M and of the right-hand side) and keep the
+ * current factor as the preconditioner.  For coefficients that change slowly
+ * in time the factor of an earlier field stays a good preconditioner for a
+ * few steps (Sec. 4, Conclusions); PCG still solves the system of the new
+ * field to cg_tol.
+ *   a_nodes: device, (n+1)^dim FP64 nodal values (as in hif_setup); read
+ *            during the call, not retained.
+ * Synchronizes the stream.  Errors: HIF_EINVAL, HIF_ECUDA. */
+int hif_set_coefficient(hif_handle *h, const double *a_nodes, hif_stream stream);
+
+/* hif_refactor - replace a(x) and factor the new operator in place (same
+ * grid, dt and options): the refactorization "once every few time steps" of
+ * Sec. 4 (Conclusions).  The old factor's device memory is released first and
+ * the handle's captured solve graphs are rebuilt on their next use; the
+ * result equals that of a fresh hif_setup with the new field, bit for bit.
+ * Waits for all work on the device.  On failure (HIF_ENOTSPD, HIF_ENOMEM) the
+ * handle has no factor: hif_apply, pcg_solve and cn_step return HIF_EINVAL
+ * until a later hif_refactor succeeds.
+ * Errors: HIF_EINVAL, HIF_ENOTSPD, HIF_ENOMEM, HIF_ECUDA. */
+int hif_refactor(hif_handle *h, const double *a_nodes, hif_stream stream);
+
 /* hif_query - sizes and statistics of a handle (host output). */
 int hif_query(const hif_handle *h, hif_info *info);
 

@@ -10,6 +10,10 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
   true residual ||b - A x|| / ||b|| at exit.
 * ``cn_solve`` runs Algorithm 1: factor once, then per step the right-hand
   side (I + dt/2 M) u + dt r(u) (Eq. CN2) and one PCG solve with A = I - dt/2 M.
+* ``cn_solve_varying`` is the variant of Sec. 4 (Conclusions) for coefficients
+  that change in time: step k uses a_k in A and in the right-hand side, and
+  the factor is recomputed only every few steps, serving as the
+  preconditioner in between.
 """
 
 from __future__ import annotations
@@ -81,3 +85,26 @@ def cn_solve(a_nodes: np.ndarray, u0: np.ndarray, dt: float, steps: int, leaf: i
         u = x.reshape(u.shape)
         iters.append(it)
     return u, iters, F
+
+
+def cn_solve_varying(a_seq, u0: np.ndarray, dt: float, leaf: int, eps: float,
+                     reaction=(0, 0.0, 0.0), tol: float = 1e-10, refactor_every: int = 1,
+                     theta: float = 0.5, skel_edges_3d: bool = True):
+    """Sec. 4: one step per coefficient field a_seq[k] (nodal arrays); the
+    factor is that of the field at the last multiple of ``refactor_every``.
+    Returns (u, per-step iteration counts)."""
+    dim = u0.ndim
+    n = u0.shape[0] + 1
+    u = np.array(u0, dtype=np.float64)
+    iters = []
+    F = None
+    for k, a in enumerate(a_seq):
+        A = grid.assemble_A(a, dt, theta)
+        if k % refactor_every == 0:
+            F = hif.factor(A, n, dim, leaf, eps, skel_edges_3d)
+        r = grid.reaction(u, *reaction) if reaction[0] else None
+        g = grid.cn_rhs(a, u, dt, r, theta)
+        x, it, _, _ = pcg(A, g.ravel(), lambda v: hif.apply_inverse(F, v), tol=tol)
+        u = x.reshape(u.shape)
+        iters.append(it)
+    return u, iters

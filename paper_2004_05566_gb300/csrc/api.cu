@@ -95,6 +95,8 @@ int alloc_work(Handle *h) {
   HIF_TRY(dev_alloc(h, (void **)&h->partials, 4 * nb * sizeof(double)));
   HIF_TRY(dev_alloc(h, (void **)&h->scal, 16 * sizeof(double)));
   HIF_CUDA_TRY(cudaMemset(h->scal, 0, 16 * sizeof(double)));  // includes the wait-expiry flag
+  HIF_TRY(dev_alloc(h, (void **)&h->tickets, 4 * sizeof(unsigned)));
+  HIF_CUDA_TRY(cudaMemset(h->tickets, 0, 4 * sizeof(unsigned)));
   HIF_CUDA_TRY(cudaMallocHost((void **)&h->host_scal, 16 * sizeof(double)));
   return HIF_OK;
 }
@@ -248,6 +250,7 @@ int finish_device_factor(Handle *h, cudaStream_t s) {
     h->has_f32 = true;
   }
   HIF_CUDA_TRY(cudaStreamSynchronize(s));
+  HIF_TRY(build_upper_plan(h));
   return HIF_OK;
 }
 
@@ -332,8 +335,45 @@ int create_handle(const hif_grid *grid, const double *a_nodes, double dt, const 
     delete h;
     return st;
   }
+  h->factor_alloc_begin = h->allocations.size();
+  h->work_device_bytes = h->device_bytes;
   *out = h;
   return HIF_OK;
+}
+
+// Free the factor's device memory and host mirrors (the work vectors and the
+// stencil stay).
+void release_factor(Handle *h) {
+  destroy_pcg_graphs(h);
+  for (size_t i = h->factor_alloc_begin; i < h->allocations.size(); ++i) cudaFree(h->allocations[i]);
+  h->allocations.resize(h->factor_alloc_begin);
+  h->device_bytes = h->work_device_bytes;
+  h->lv_host.clear();
+  h->lv.clear();
+  h->idx_host.clear();
+  h->cptr_host.clear();
+  h->cslot_host.clear();
+  h->idx = nullptr;
+  h->cptr = h->cslot = nullptr;
+  h->nvals = 0;
+  h->max_contrib = 0;
+  h->root_n = 0;
+  h->root_idx_off = h->root_G_off = 0;
+  h->f64 = FactorValues<double>{};
+  h->f32 = FactorValues<float>{};
+  h->has_f32 = false;
+  h->use_upper = false;
+  h->upper_nphase = 0;
+  h->upper_phases = nullptr;
+  h->upper_levels = nullptr;
+  h->upper_rt = nullptr;
+  h->upper_grid[0] = h->upper_grid[1] = 0;
+  for (auto &r : h->stat_pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  h->stat_pending.clear();
+  h->factor_ok = false;
 }
 
 struct Reader {
@@ -496,6 +536,7 @@ int hif_setup(const hif_grid *grid, const double *a_nodes, double dt, const hif_
     return st;
   }
   h->setup_seconds = now_seconds() - t0;
+  h->factor_ok = true;
   *out = h;
   return HIF_OK;
 }
@@ -515,12 +556,13 @@ int hif_import_factor(const hif_grid *grid, const void *blob, size_t bytes, doub
     return st;
   }
   h->setup_seconds = now_seconds() - t0;
+  h->factor_ok = true;
   *out = h;
   return HIF_OK;
 }
 
 int hif_export_factor(const hif_handle *hh, void *buf, size_t *bytes) {
-  if (!hh || !bytes) return HIF_EINVAL;
+  if (!hh || !bytes || !hh->factor_ok) return HIF_EINVAL;
   const Handle *h = hh;
   std::vector<unsigned char> out;
   auto put = [&](const void *p, size_t n) {
@@ -573,7 +615,7 @@ int hif_export_factor(const hif_handle *hh, void *buf, size_t *bytes) {
 }
 
 int hif_apply(hif_handle *h, const double *x, double *y, int precision, hif_stream stream) {
-  if (!h || !x || !y || x == y) return HIF_EINVAL;
+  if (!h || !x || !y || x == y || !h->factor_ok) return HIF_EINVAL;
   return apply_inverse(h, x, y, precision, (cudaStream_t)stream);
 }
 
@@ -584,13 +626,13 @@ int hif_matvec(hif_handle *h, const double *x, double *y, hif_stream stream) {
 
 int pcg_solve(hif_handle *h, const double *b, double *x, int *iters, double *relres,
               hif_stream stream) {
-  if (!h || !b || !x || b == x) return HIF_EINVAL;
+  if (!h || !b || !x || b == x || !h->factor_ok) return HIF_EINVAL;
   return pcg(h, b, x, iters, relres, (cudaStream_t)stream);
 }
 
 int cn_step(hif_handle *h, const double *u_k, const double *r_k, double *u_k1, int *iters,
             hif_stream stream) {
-  if (!h || !u_k || !u_k1) return HIF_EINVAL;
+  if (!h || !u_k || !u_k1 || !h->factor_ok) return HIF_EINVAL;
   return cn(h, u_k, r_k, u_k1, iters, (cudaStream_t)stream);
 }
 
@@ -598,7 +640,7 @@ int cn_step_batched(hif_handle *const *hs, int count, const double *const *u_k,
                     const double *const *r_k, double *const *u_k1, int *iters, hif_stream stream) {
   if (count < 0 || (count > 0 && (!hs || !u_k || !u_k1))) return HIF_EINVAL;
   for (int i = 0; i < count; ++i)
-    if (!hs[i] || !u_k[i] || !u_k1[i]) return HIF_EINVAL;
+    if (!hs[i] || !u_k[i] || !u_k1[i] || !hs[i]->factor_ok) return HIF_EINVAL;
   if (count == 0) return HIF_OK;
   return cn_batched(hs, count, u_k, r_k, u_k1, iters, (cudaStream_t)stream);
 }
@@ -609,6 +651,33 @@ int hif_set_reaction(hif_handle *h, int kind, double k1, double k2) {
   h->react_kind = kind;
   h->react_k1 = k1;
   h->react_k2 = k2;
+  return HIF_OK;
+}
+
+int hif_set_coefficient(hif_handle *h, const double *a_nodes, hif_stream stream) {
+  if (!h || !a_nodes) return HIF_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  HIF_TRY(stencil_update(h, a_nodes, s));
+  HIF_CUDA_TRY(cudaStreamSynchronize(s));
+  return HIF_OK;
+}
+
+int hif_refactor(hif_handle *h, const double *a_nodes, hif_stream stream) {
+  if (!h || !a_nodes) return HIF_EINVAL;
+  if (!(h->opt.eps >= 0.0)) return HIF_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  HIF_CUDA_TRY(cudaDeviceSynchronize());  // no solve of this handle is in flight
+  release_factor(h);
+  const double t0 = now_seconds();
+  HIF_TRY(stencil_update(h, a_nodes, s));
+  int st = gpu_setup(h, a_nodes, s);
+  if (st == HIF_OK) st = finish_device_factor(h, s);
+  if (st != HIF_OK) {
+    release_factor(h);
+    return st;
+  }
+  h->setup_seconds = now_seconds() - t0;
+  h->factor_ok = true;
   return HIF_OK;
 }
 

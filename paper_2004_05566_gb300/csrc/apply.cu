@@ -23,13 +23,16 @@
 #include "internal.h"
 #include "device_common.cuh"
 
+#include <algorithm>
+#include <cstdlib>
+#include <vector>
+
 namespace hifcn {
 
 namespace {
 
 constexpr int kCellFwdThreads = 256;
 constexpr int kCellBwdThreads = 256;
-constexpr int kGroupThreads = 128;
 constexpr int kRootThreads = 256;
 constexpr int kRows = 4;  // rows a warp keeps in flight in the row-dot kernels
 
@@ -85,24 +88,18 @@ __device__ __forceinline__ void warp_rows_dot4(const T *const (&rp)[kRows], cons
 // G x_I of the interior.  A CTA handles rows [a, b) of one cell's stacked
 // [V; G]; x_I is only read here (the forward values go to the separate vector
 // xI, which the backward cell step reads), so a cell may be split over CTAs.
-template <typename T>
-__global__ void __launch_bounds__(kCellFwdThreads) k_cell_fwd(const CellItem *__restrict__ items,
-                                                              const CellDesc *__restrict__ cells,
-                                                              const int *__restrict__ idx,
-                                                              const T *__restrict__ vals,
-                                                              T *__restrict__ contrib,
-                                                              T *__restrict__ xI,
-                                                              const T *__restrict__ x) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *xs = reinterpret_cast<T *>(smem_raw);
-  const CellItem it = items[blockIdx.x];
+template <typename T, int NT>
+__device__ __forceinline__ void cell_fwd_unit(const CellItem &it, const CellDesc *__restrict__ cells,
+                                              const int *__restrict__ idx, const T *__restrict__ vals,
+                                              T *__restrict__ contrib, T *__restrict__ xI,
+                                              const T *__restrict__ x, T *xs) {
   const CellDesc c = cells[it.cell];
   const int *I = idx + c.I_off;
   const int nIp = (int)pad4(c.nI);
-  for (int i = threadIdx.x; i < nIp; i += kCellFwdThreads) xs[i] = i < c.nI ? x[I[i]] : T(0);
+  for (int i = threadIdx.x; i < nIp; i += NT) xs[i] = i < c.nI ? x[I[i]] : T(0);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int NW = kCellFwdThreads / 32;
+  constexpr int NW = NT / 32;
   const T *V = vals + c.V_off;
   const T *G = vals + c.G_off;
   const int vq = nIp / 4;
@@ -138,18 +135,30 @@ __global__ void __launch_bounds__(kCellFwdThreads) k_cell_fwd(const CellItem *__
   }
 }
 
-// Forward group step (K^T C^T): x_g <- H (x_g - sum of the cells' contributions).
 template <typename T>
-__global__ void __launch_bounds__(kGroupThreads) k_group_fwd(
-    const int *__restrict__ list, const GroupDesc *__restrict__ groups, const int *__restrict__ idx,
-    const long long *__restrict__ cptr, const long long *__restrict__ cslot,
-    const T *__restrict__ vals, const T *__restrict__ contrib, T *__restrict__ x) {
+__global__ void __launch_bounds__(kCellFwdThreads) k_cell_fwd(const CellItem *__restrict__ items,
+                                                              const CellDesc *__restrict__ cells,
+                                                              const int *__restrict__ idx,
+                                                              const T *__restrict__ vals,
+                                                              T *__restrict__ contrib,
+                                                              T *__restrict__ xI,
+                                                              const T *__restrict__ x) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *xs = reinterpret_cast<T *>(smem_raw);
-  const GroupDesc g = groups[list[blockIdx.x]];
+  cell_fwd_unit<T, kCellFwdThreads>(items[blockIdx.x], cells, idx, vals, contrib, xI, x,
+                                    reinterpret_cast<T *>(smem_raw));
+}
+
+// Forward group step (K^T C^T): x_g <- H (x_g - sum of the cells' contributions).
+template <typename T, int NT>
+__device__ __forceinline__ void group_fwd_unit(const GroupDesc &g, const int *__restrict__ idx,
+                                               const long long *__restrict__ cptr,
+                                               const long long *__restrict__ cslot,
+                                               const T *__restrict__ vals,
+                                               const T *__restrict__ contrib, T *__restrict__ x,
+                                               T *xs) {
   const int *gi = idx + g.idx_off;
   const int np = (int)pad4(g.n);
-  for (int i = threadIdx.x; i < np; i += kGroupThreads) {
+  for (int i = threadIdx.x; i < np; i += NT) {
     T v = T(0);
     if (i < g.n) {
       v = x[gi[i]];
@@ -160,7 +169,7 @@ __global__ void __launch_bounds__(kGroupThreads) k_group_fwd(
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int NW = kGroupThreads / 32;
+  constexpr int NW = NT / 32;
   const T *H = vals + g.H_off;
   for (int r0 = warp * kRows; r0 < g.n; r0 += NW * kRows) {
     const T *rp[kRows];
@@ -181,22 +190,20 @@ __global__ void __launch_bounds__(kGroupThreads) k_group_fwd(
   }
 }
 
+
 // Separator entities with at most 32 DOFs: one warp per entity, eight per CTA.
 constexpr int kSmallWarps = 8;
 
+// one warp: entity g with n <= 32; xs is the warp's 32-element buffer
 template <typename T>
-__global__ void __launch_bounds__(kSmallWarps * 32) k_group_fwd_small(
-    const int *__restrict__ list, int count, const GroupDesc *__restrict__ groups,
-    const int *__restrict__ idx, const long long *__restrict__ cptr,
-    const long long *__restrict__ cslot, const T *__restrict__ vals,
-    const T *__restrict__ contrib, T *__restrict__ x) {
-  __shared__ __align__(16) T xs_all[kSmallWarps][32];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int t = blockIdx.x * kSmallWarps + warp;
-  if (t >= count) return;
-  const GroupDesc g = groups[list[t]];
+__device__ __forceinline__ void group_fwd_small_warp(const GroupDesc &g, const int *__restrict__ idx,
+                                                     const long long *__restrict__ cptr,
+                                                     const long long *__restrict__ cslot,
+                                                     const T *__restrict__ vals,
+                                                     const T *__restrict__ contrib,
+                                                     T *__restrict__ x, T *xs) {
+  const int lane = threadIdx.x & 31;
   const int *gi = idx + g.idx_off;
-  T *xs = xs_all[warp];
   T v = T(0);
   if (lane < g.n) {
     v = x[gi[lane]];
@@ -216,19 +223,15 @@ __global__ void __launch_bounds__(kSmallWarps * 32) k_group_fwd_small(
     }
     x[gi[lane]] = acc;
   }
+  __syncwarp();
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kSmallWarps * 32) k_group_bwd_small(
-    const int *__restrict__ list, int count, const GroupDesc *__restrict__ groups,
-    const int *__restrict__ idx, const T *__restrict__ vals, T *__restrict__ x) {
-  __shared__ T xs_all[kSmallWarps][32];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int t = blockIdx.x * kSmallWarps + warp;
-  if (t >= count) return;
-  const GroupDesc g = groups[list[t]];
+__device__ __forceinline__ void group_bwd_small_warp(const GroupDesc &g, const int *__restrict__ idx,
+                                                     const T *__restrict__ vals, T *__restrict__ x,
+                                                     T *xs) {
+  const int lane = threadIdx.x & 31;
   const int *gi = idx + g.idx_off;
-  T *xs = xs_all[warp];
   xs[lane] = lane < g.n ? x[gi[lane]] : T(0);
   __syncwarp();
   if (lane < g.n) {
@@ -238,7 +241,10 @@ __global__ void __launch_bounds__(kSmallWarps * 32) k_group_bwd_small(
     for (int r = 0; r < g.n; ++r) acc += H[(long long)r * np + lane] * xs[r];
     x[gi[lane]] = acc;
   }
+  __syncwarp();
 }
+
+
 
 // Column-parallel transposed products: threads are (column unit, row group);
 // each thread sums its rows, the row groups are added in a fixed order.
@@ -249,24 +255,18 @@ __device__ __forceinline__ void col_layout(int ncols, int nthreads, int &CW, int
   RG = nthreads / CW;
 }
 
-// Backward group step: x_g <- H^T x_g.
-template <typename T>
-__global__ void __launch_bounds__(kGroupThreads) k_group_bwd(const int *__restrict__ list,
-                                                             const GroupDesc *__restrict__ groups,
-                                                             const int *__restrict__ idx,
-                                                             const T *__restrict__ vals,
-                                                             T *__restrict__ x) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const GroupDesc g = groups[list[blockIdx.x]];
-  T *xs = reinterpret_cast<T *>(smem_raw);
+// Backward group step: x_g <- H^T x_g.  xs holds n + NT elements.
+template <typename T, int NT>
+__device__ __forceinline__ void group_bwd_unit(const GroupDesc &g, const int *__restrict__ idx,
+                                               const T *__restrict__ vals, T *__restrict__ x, T *xs) {
   T *part = xs + g.n;
   const int *gi = idx + g.idx_off;
-  for (int i = threadIdx.x; i < g.n; i += kGroupThreads) xs[i] = x[gi[i]];
+  for (int i = threadIdx.x; i < g.n; i += NT) xs[i] = x[gi[i]];
   __syncthreads();
   const T *H = vals + g.H_off;
   const long long np = pad4(g.n);
   int CW, RG;
-  col_layout(g.n, kGroupThreads, CW, RG);
+  col_layout(g.n, NT, CW, RG);
   const int cl = threadIdx.x % CW, rg = threadIdx.x / CW;
   for (int c0 = 0; c0 < g.n; c0 += CW) {
     const int col = c0 + cl;
@@ -286,28 +286,62 @@ __global__ void __launch_bounds__(kGroupThreads) k_group_bwd(const int *__restri
   }
 }
 
+
+// One launch per level and direction for all separator entities: CTA u <
+// nlarge takes large entity u with all its threads; every further CTA takes
+// kSmallWarps entities of at most 32 DOFs, one per warp.
+template <typename T>
+__global__ void __launch_bounds__(kSmallWarps * 32) k_group_fwd_level(
+    const int *__restrict__ large, int nlarge, const int *__restrict__ small, int nsmall,
+    const GroupDesc *__restrict__ groups, const int *__restrict__ idx,
+    const long long *__restrict__ cptr, const long long *__restrict__ cslot,
+    const T *__restrict__ vals, const T *__restrict__ contrib, T *__restrict__ x) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *sm = reinterpret_cast<T *>(smem_raw);
+  const int u = blockIdx.x;
+  if (u < nlarge) {
+    group_fwd_unit<T, kSmallWarps * 32>(groups[large[u]], idx, cptr, cslot, vals, contrib, x, sm);
+    return;
+  }
+  const int warp = threadIdx.x >> 5;
+  const int t = (u - nlarge) * kSmallWarps + warp;
+  if (t < nsmall) group_fwd_small_warp<T>(groups[small[t]], idx, cptr, cslot, vals, contrib, x, sm + 32 * warp);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSmallWarps * 32) k_group_bwd_level(
+    const int *__restrict__ large, int nlarge, const int *__restrict__ small, int nsmall,
+    const GroupDesc *__restrict__ groups, const int *__restrict__ idx, const T *__restrict__ vals,
+    T *__restrict__ x) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *sm = reinterpret_cast<T *>(smem_raw);
+  const int u = blockIdx.x;
+  if (u < nlarge) {
+    group_bwd_unit<T, kSmallWarps * 32>(groups[large[u]], idx, vals, x, sm);
+    return;
+  }
+  const int warp = threadIdx.x >> 5;
+  const int t = (u - nlarge) * kSmallWarps + warp;
+  if (t < nsmall) group_bwd_small_warp<T>(groups[small[t]], idx, vals, x, sm + 32 * warp);
+}
+
 // Backward cell step (E_I): x_I <- G^T xI_I - V^T x_B, for columns [a, b)
 // (a a multiple of 4) of one cell.  A thread owns the column quad pair
 // (qa, qb) = (first + p, last - p), which balances the triangular row counts,
 // and reads both quads of a row with 16-byte loads; row groups are added in
 // a fixed order.
-template <typename T>
-__global__ void __launch_bounds__(kCellBwdThreads) k_cell_bwd(const CellItem *__restrict__ items,
-                                                              const CellDesc *__restrict__ cells,
-                                                              const int *__restrict__ idx,
-                                                              const T *__restrict__ vals,
-                                                              const T *__restrict__ xI,
-                                                              T *__restrict__ x) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const CellItem it = items[blockIdx.x];
+template <typename T, int NT>
+__device__ __forceinline__ void cell_bwd_unit(const CellItem &it, const CellDesc *__restrict__ cells,
+                                              const int *__restrict__ idx, const T *__restrict__ vals,
+                                              const T *__restrict__ xI, T *__restrict__ x, T *smem) {
   const CellDesc c = cells[it.cell];
-  T *part = reinterpret_cast<T *>(smem_raw);  // 8 * kCellBwdThreads
-  T *xs = part + 8 * kCellBwdThreads;
+  T *part = smem;  // 8 * NT
+  T *xs = part + 8 * NT;
   T *xb = xs + c.nI;
   const int *I = idx + c.I_off;
   const int *B = idx + c.B_off;
-  for (int i = threadIdx.x; i < c.nI; i += kCellBwdThreads) xs[i] = xI[I[i]];
-  for (int q = threadIdx.x; q < c.nB; q += kCellBwdThreads) xb[q] = x[B[q]];
+  for (int i = threadIdx.x; i < c.nI; i += NT) xs[i] = xI[I[i]];
+  for (int q = threadIdx.x; q < c.nB; q += NT) xb[q] = x[B[q]];
   __syncthreads();
   const T *G = vals + c.G_off;
   const T *V = vals + c.V_off;
@@ -315,7 +349,7 @@ __global__ void __launch_bounds__(kCellBwdThreads) k_cell_bwd(const CellItem *__
   const int q0 = it.a / 4, q1 = (it.b + 3) / 4;  // column quads [q0, q1)
   const int npairs = (q1 - q0 + 1) / 2;
   int PW, RG;
-  col_layout(npairs, kCellBwdThreads, PW, RG);
+  col_layout(npairs, NT, PW, RG);
   const int pl = threadIdx.x % PW, rg = threadIdx.x / PW;
   for (int p0 = 0; p0 < npairs; p0 += PW) {
     const int p = p0 + pl;
@@ -357,8 +391,8 @@ __global__ void __launch_bounds__(kCellBwdThreads) k_cell_bwd(const CellItem *__
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      part[k * kCellBwdThreads + threadIdx.x] = aA[k];
-      part[(4 + k) * kCellBwdThreads + threadIdx.x] = aB[k];
+      part[k * NT + threadIdx.x] = aA[k];
+      part[(4 + k) * NT + threadIdx.x] = aB[k];
     }
     __syncthreads();
     if (rg == 0 && p < npairs) {
@@ -367,13 +401,25 @@ __global__ void __launch_bounds__(kCellBwdThreads) k_cell_bwd(const CellItem *__
         const int col = (k < 4 ? 4 * qa : 4 * qb) + (k & 3);
         if (k >= 4 && qb <= qa) break;
         if (col < it.a || col >= it.b) continue;
-        T sum = part[k * kCellBwdThreads + pl];
-        for (int g = 1; g < RG; ++g) sum += part[k * kCellBwdThreads + g * PW + pl];
+        T sum = part[k * NT + pl];
+        for (int g = 1; g < RG; ++g) sum += part[k * NT + g * PW + pl];
         x[I[col]] = sum;
       }
     }
     __syncthreads();
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kCellBwdThreads) k_cell_bwd(const CellItem *__restrict__ items,
+                                                              const CellDesc *__restrict__ cells,
+                                                              const int *__restrict__ idx,
+                                                              const T *__restrict__ vals,
+                                                              const T *__restrict__ xI,
+                                                              T *__restrict__ x) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cell_bwd_unit<T, kCellBwdThreads>(items[blockIdx.x], cells, idx, vals, xI, x,
+                                    reinterpret_cast<T *>(smem_raw));
 }
 
 // ------------------------------------------------------------ TMA-staged cells
@@ -391,7 +437,7 @@ __global__ void __launch_bounds__(kCellBwdThreads) k_cell_bwd(const CellItem *__
 constexpr int kStages = 4;
 constexpr int kConsumerWarps = 8;
 constexpr int kConsumers = kConsumerWarps * 32;
-constexpr int kTmaThreads = kConsumers + 32;
+constexpr int kTmaThreads = kConsumers + 64;  // + one copy warp + one gather warp
 constexpr long long kWaitLimit = 1LL << 22;
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
@@ -444,22 +490,87 @@ __device__ __forceinline__ long long cell_row_off(int r, int nI, long long vs) {
   return r < nI ? tri_off(r) : tri_off(nI) + (long long)(r - nI) * vs;
 }
 
-// Producer: lane 0 of the last warp streams the chunks of a block whose
-// first ntri rows are packed-triangular rows and the rest dense rows of
-// stride vs (chunk k = rows [cs[k], cs[k+1])).
+// Copy warp: lane 0 streams, for each cell the CTA owns (cells blockIdx.x,
+// blockIdx.x + gridDim.x, ...), the chunks of the cell's block: its first ntri
+// rows packed-triangular (tri = true: the S rows, then the V rows; tri =
+// false: the V rows only) and dense rows of stride pad4(nI) (chunk j of a cell
+// = rows [cs[j], cs[j+1])).  The chunk's row range goes to meta[stage] before
+// the copy is armed, so the consumers read it from shared memory.  The stage
+// ring runs on across cells: the copies of the next cell are in flight while
+// the consumers finish the current one.
 template <typename T>
-__device__ __forceinline__ void produce_rows(const T *block, int ntri, long long vs, const int *cs,
-                                             int nch, unsigned char *stage, unsigned long long *full,
-                                             unsigned long long *empty, double *err) {
-  for (int k = 0; k < nch; ++k) {
-    const int sidx = k % kStages;
-    if (k >= kStages && !mbar_wait(&empty[sidx], (unsigned)(((k / kStages) - 1) & 1))) {
-      err[0] = 1.0;
+__device__ __forceinline__ void produce_cells(const CellDesc *__restrict__ cells, int ncells,
+                                              const int2 *__restrict__ chunk_of,
+                                              const int *__restrict__ chunk_tab,
+                                              const T *__restrict__ vals, bool tri,
+                                              unsigned char *stage, int2 *meta,
+                                              unsigned long long *full, unsigned long long *empty,
+                                              double *err) {
+  long long k = 0;  // running chunk counter of this CTA
+  for (int ci = blockIdx.x; ci < ncells; ci += gridDim.x) {
+    const CellDesc c = cells[ci];
+    const int2 co = chunk_of[ci];
+    const int *cs = chunk_tab + co.x;
+    const long long vs = pad4(c.nI);
+    const T *block = vals + (tri ? c.S_off : c.V_off);
+    const int ntri = tri ? c.nI : 0;
+    int rb = co.y > 0 ? cs[0] : 0;
+    for (int j = 0; j < co.y; ++j, ++k) {
+      const int re = cs[j + 1];
+      const int sidx = (int)(k % kStages);
+      if (k >= kStages && !mbar_wait(&empty[sidx], (unsigned)(((k / kStages) - 1) & 1))) {
+        err[0] = 1.0;
+        return;
+      }
+      meta[sidx] = make_int2(rb, re);
+      const long long a = cell_row_off(rb, ntri, vs), b = cell_row_off(re, ntri, vs);
+      bulk_load(stage + (size_t)sidx * kStageBytes, block + a, (unsigned)((b - a) * sizeof(T)),
+                &full[sidx]);
+      rb = re;
+    }
+  }
+}
+
+// Per-cell data the gather warp hands to the consumers (double buffered).
+struct CellMeta {
+  CellDesc c;
+  int nch;
+};
+
+// Gather warp: for each cell of the CTA, into buffer b = (cell count) & 1:
+// the cell descriptor and chunk count, x at the interior DOFs (zero padded to
+// pad4(nI)) and, when xb is given, x at the boundary DOFs; every lane arrives
+// on ready[b].  Before refilling a buffer it waits until the consumers freed it.
+template <typename T>
+__device__ __forceinline__ void gather_cells(const CellDesc *__restrict__ cells, int ncells,
+                                             const int2 *__restrict__ chunk_of,
+                                             const int *__restrict__ idx, const T *__restrict__ x,
+                                             CellMeta *cm, T *xs0, long long xs_stride, T *xb0,
+                                             long long xb_stride, unsigned long long *ready,
+                                             unsigned long long *freed, double *err) {
+  const int lane = threadIdx.x & 31;
+  int jc = 0;
+  for (int ci = blockIdx.x; ci < ncells; ci += gridDim.x, ++jc) {
+    const int b = jc & 1;
+    if (jc >= 2 && !mbar_wait(&freed[b], (unsigned)(((jc >> 1) - 1) & 1))) {
+      if (lane == 0) err[0] = 1.0;
       return;
     }
-    const long long a = cell_row_off(cs[k], ntri, vs), b = cell_row_off(cs[k + 1], ntri, vs);
-    bulk_load(stage + (size_t)sidx * kStageBytes, block + a, (unsigned)((b - a) * sizeof(T)),
-              &full[sidx]);
+    const CellDesc c = cells[ci];
+    if (lane == 0) {
+      cm[b].c = c;
+      cm[b].nch = chunk_of[ci].y;
+    }
+    const int nIp = (int)pad4(c.nI);
+    const int *I = idx + c.I_off;
+    T *xs = xs0 + b * xs_stride;
+    for (int i = lane; i < nIp; i += 32) xs[i] = i < c.nI ? x[I[i]] : T(0);
+    if (xb0) {
+      const int *B = idx + c.B_off;
+      T *xb = xb0 + b * xb_stride;
+      for (int q = lane; q < c.nB; q += 32) xb[q] = x[B[q]];
+    }
+    mbar_arrive(&ready[b]);
   }
 }
 
@@ -490,88 +601,108 @@ __global__ void __launch_bounds__(256) k_make_S(const CellDesc *__restrict__ cel
 // x_I <- S x_I - V^T x_B with S = A_II^{-1} = G^T G, which equals
 // G^T (G x_I) - V^T x_B.  S is read once instead of G twice.
 
-// forward: contributions c_B = V x_I, streaming the V rows
+// forward: contributions c_B = V x_I, streaming the V rows.  Persistent: a
+// CTA takes cells blockIdx.x, blockIdx.x + gridDim.x, ...; warp 8 copies the
+// V rows, warp 9 gathers x_I of the next cell, warps 0-7 compute.
 template <typename T>
 __global__ void __launch_bounds__(kTmaThreads) k_cell_fwd_tma_S(const CellDesc *__restrict__ cells,
+                                                                int ncells,
                                                                 const int2 *__restrict__ chunk_of,
                                                                 const int *__restrict__ chunk_tab,
                                                                 const int *__restrict__ idx,
                                                                 const T *__restrict__ vals,
                                                                 T *__restrict__ contrib,
                                                                 const T *__restrict__ x,
-                                                                double *__restrict__ err) {
+                                                                double *__restrict__ err,
+                                                                int max_nI) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(8) unsigned long long full[kStages], empty[kStages];
+  __shared__ __align__(8) unsigned long long full[kStages], empty[kStages], ready[2], freed[2];
+  __shared__ int2 meta[kStages];
+  __shared__ CellMeta cm[2];
   unsigned char *stage = smem_raw;
-  T *xs = reinterpret_cast<T *>(smem_raw + (size_t)kStages * kStageBytes);
-  const CellDesc c = cells[blockIdx.x];
-  const int2 co = chunk_of[blockIdx.x];
-  const int *cs = chunk_tab + co.x;
-  const int nch = co.y;
+  const long long xstride = pad4(max_nI);
+  T *xs0 = reinterpret_cast<T *>(smem_raw + (size_t)kStages * kStageBytes);  // 2 x pad4(max_nI)
   if (threadIdx.x == 0) {
     for (int k = 0; k < kStages; ++k) {
       mbar_init(&full[k], 1);
       mbar_init(&empty[k], kConsumerWarps);
     }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&ready[b], 32);
+      mbar_init(&freed[b], kConsumerWarps);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  if (nch < 0) {
-    if (threadIdx.x == 0) err[0] = 1.0;
-    return;
-  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nIp = (int)pad4(c.nI);
-  const long long vs = nIp;
   if (warp == kConsumerWarps) {
-    if (lane == 0) produce_rows<T>(vals + c.V_off, 0, vs, cs, nch, stage, full, empty, err);
+    if (lane == 0)
+      produce_cells<T>(cells, ncells, chunk_of, chunk_tab, vals, false, stage, meta, full, empty, err);
     return;
   }
-  const int *I = idx + c.I_off;
-  for (int i = threadIdx.x; i < nIp; i += kConsumers) xs[i] = i < c.nI ? x[I[i]] : T(0);
-  consumers_sync();
-  for (int k = 0; k < nch; ++k) {
-    const int sidx = k % kStages;
-    if (!mbar_wait(&full[sidx], (unsigned)((k / kStages) & 1))) {
+  if (warp == kConsumerWarps + 1) {
+    gather_cells<T>(cells, ncells, chunk_of, idx, x, cm, xs0, xstride, nullptr, 0, ready, freed, err);
+    return;
+  }
+  long long k = 0;  // running chunk counter, as in the copy warp
+  int jc = 0;
+  for (int ci = blockIdx.x; ci < ncells; ci += gridDim.x, ++jc) {
+    const int b = jc & 1;
+    if (!mbar_wait(&ready[b], (unsigned)((jc >> 1) & 1))) {
       if (lane == 0) err[0] = 1.0;
       return;
     }
-    const T *base = reinterpret_cast<const T *>(stage + (size_t)sidx * kStageBytes);
-    const int rb = cs[k], re = cs[k + 1];
-    for (int r0 = rb + warp * kRows; r0 < re; r0 += kConsumerWarps * kRows) {
-      const T *rp[kRows];
-      int nq[kRows];
-#pragma unroll
-      for (int u = 0; u < kRows; ++u) {
-        const int r = r0 + u;
-        rp[u] = base + (long long)(r < re ? r - rb : 0) * vs;
-        nq[u] = r < re ? nIp / 4 : 0;
+    const CellDesc c = cm[b].c;
+    const int nch = cm[b].nch;
+    const T *xs = xs0 + b * xstride;
+    const int nIp = (int)pad4(c.nI);
+    const long long vs = nIp;
+    for (int j = 0; j < nch; ++j, ++k) {
+      const int sidx = (int)(k % kStages);
+      if (!mbar_wait(&full[sidx], (unsigned)((k / kStages) & 1))) {
+        if (lane == 0) err[0] = 1.0;
+        return;
       }
-      T acc[kRows];
-#pragma unroll
-      for (int u = 0; u < kRows; ++u) acc[u] = T(0);
-      for (int q = lane; q < nIp / 4; q += 32) {
-        T xv[4];
-        ld4(xs + 4 * q, xv);
+      const T *base = reinterpret_cast<const T *>(stage + (size_t)sidx * kStageBytes);
+      const int2 rr = meta[sidx];
+      const int rb = rr.x, re = rr.y;
+      for (int r0 = rb + warp * kRows; r0 < re; r0 += kConsumerWarps * kRows) {
+        const T *rp[kRows];
+        int nq[kRows];
 #pragma unroll
         for (int u = 0; u < kRows; ++u) {
-          if (q < nq[u]) {
-            T v[4];
-            ld4(rp[u] + 4 * q, v);
-            acc[u] += v[0] * xv[0] + v[1] * xv[1] + v[2] * xv[2] + v[3] * xv[3];
+          const int r = r0 + u;
+          rp[u] = base + (long long)(r < re ? r - rb : 0) * vs;
+          nq[u] = r < re ? nIp / 4 : 0;
+        }
+        T acc[kRows];
+#pragma unroll
+        for (int u = 0; u < kRows; ++u) acc[u] = T(0);
+        for (int q = lane; q < nIp / 4; q += 32) {
+          T xv[4];
+          ld4(xs + 4 * q, xv);
+#pragma unroll
+          for (int u = 0; u < kRows; ++u) {
+            if (q < nq[u]) {
+              T v[4];
+              ld4(rp[u] + 4 * q, v);
+              acc[u] += v[0] * xv[0] + v[1] * xv[1] + v[2] * xv[2] + v[3] * xv[3];
+            }
           }
         }
-      }
 #pragma unroll
-      for (int u = 0; u < kRows; ++u) acc[u] = warp_reduce(acc[u]);
-      if (lane == 0) {
+        for (int u = 0; u < kRows; ++u) acc[u] = warp_reduce(acc[u]);
+        if (lane == 0) {
 #pragma unroll
-        for (int u = 0; u < kRows; ++u)
-          if (r0 + u < re) contrib[c.C_off + r0 + u] = acc[u];
+          for (int u = 0; u < kRows; ++u)
+            if (r0 + u < re) contrib[c.C_off + r0 + u] = acc[u];
+        }
       }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[sidx]);
     }
     __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[sidx]);
+    if (lane == 0) mbar_arrive(&freed[b]);
   }
 }
 
@@ -579,121 +710,141 @@ __global__ void __launch_bounds__(kTmaThreads) k_cell_fwd_tma_S(const CellDesc *
 // Warp w handles the rows r = w (mod 8); lane p owns the column quads
 // (p, nq - 1 - p).  An S row r gives its row dot S[r][.] x (warp reduction)
 // and, below the diagonal, the column products S[r][col] x_r (col < r).
+// Persistent like the forward kernel, with the same copy and gather warps.
 template <typename T>
 __global__ void __launch_bounds__(kTmaThreads) k_cell_bwd_tma_S(const CellDesc *__restrict__ cells,
+                                                                int ncells,
                                                                 const int2 *__restrict__ chunk_of,
                                                                 const int *__restrict__ chunk_tab,
                                                                 const int *__restrict__ idx,
                                                                 const T *__restrict__ vals,
                                                                 T *__restrict__ x,
-                                                                double *__restrict__ err) {
+                                                                double *__restrict__ err,
+                                                                int max_nI, int max_nB) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(8) unsigned long long full[kStages], empty[kStages];
+  __shared__ __align__(8) unsigned long long full[kStages], empty[kStages], ready[2], freed[2];
+  __shared__ int2 meta[kStages];
+  __shared__ CellMeta cm[2];
   unsigned char *stage = smem_raw;
+  const long long xstride = pad4(max_nI), bstride = pad4(max_nB);
   T *part = reinterpret_cast<T *>(smem_raw + (size_t)kStages * kStageBytes);  // 8 * kConsumers
-  T *xs = part + 8 * kConsumers;  // pad4(nI)
-  const CellDesc c = cells[blockIdx.x];
-  const int nIp = (int)pad4(c.nI);
-  T *yrow = xs + nIp;             // nI
-  T *xb = yrow + c.nI;            // nB
-  const int2 co = chunk_of[blockIdx.x];
-  const int *cs = chunk_tab + co.x;
-  const int nch = co.y;
+  T *yrow = part + 8 * kConsumers;   // pad4(max_nI)
+  T *xs0 = yrow + xstride;           // 2 x pad4(max_nI)
+  T *xb0 = xs0 + 2 * xstride;        // 2 x pad4(max_nB)
   if (threadIdx.x == 0) {
     for (int k = 0; k < kStages; ++k) {
       mbar_init(&full[k], 1);
       mbar_init(&empty[k], kConsumerWarps);
     }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&ready[b], 32);
+      mbar_init(&freed[b], kConsumerWarps);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  if (nch < 0) {
-    if (threadIdx.x == 0) err[0] = 1.0;
-    return;
-  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long vs = nIp;
   if (warp == kConsumerWarps) {
-    if (lane == 0) produce_rows<T>(vals + c.S_off, c.nI, vs, cs, nch, stage, full, empty, err);
+    if (lane == 0)
+      produce_cells<T>(cells, ncells, chunk_of, chunk_tab, vals, true, stage, meta, full, empty, err);
     return;
   }
-  const int *I = idx + c.I_off;
-  const int *B = idx + c.B_off;
-  for (int i = threadIdx.x; i < nIp; i += kConsumers) xs[i] = i < c.nI ? x[I[i]] : T(0);
-  for (int q = threadIdx.x; q < c.nB; q += kConsumers) xb[q] = x[B[q]];
-  consumers_sync();
-  const int nq = nIp / 4;
-  const int qa = lane, qb = nq - 1 - lane;  // one warp covers all column pairs (nq <= 64)
-  const bool okA = qa < (nq + 1) / 2;
-  const bool okB = okA && qb > qa;
-  T aA[4] = {T(0), T(0), T(0), T(0)}, aB[4] = {T(0), T(0), T(0), T(0)};
-  T xa[4] = {T(0), T(0), T(0), T(0)}, xbq[4] = {T(0), T(0), T(0), T(0)};
-  if (okA) ld4(xs + 4 * qa, xa);
-  if (okB) ld4(xs + 4 * qb, xbq);
-  for (int k = 0; k < nch; ++k) {
-    const int sidx = k % kStages;
-    if (!mbar_wait(&full[sidx], (unsigned)((k / kStages) & 1))) {
+  if (warp == kConsumerWarps + 1) {
+    gather_cells<T>(cells, ncells, chunk_of, idx, x, cm, xs0, xstride, xb0, bstride, ready, freed, err);
+    return;
+  }
+  long long k = 0;  // running chunk counter, as in the copy warp
+  int jc = 0;
+  for (int ci = blockIdx.x; ci < ncells; ci += gridDim.x, ++jc) {
+    const int b = jc & 1;
+    if (!mbar_wait(&ready[b], (unsigned)((jc >> 1) & 1))) {
       if (lane == 0) err[0] = 1.0;
       return;
     }
-    const T *base = reinterpret_cast<const T *>(stage + (size_t)sidx * kStageBytes);
-    const int rb = cs[k], re = cs[k + 1];
-    const long long off0 = cell_row_off(rb, c.nI, vs);
-    for (int r = rb + ((warp - rb % kConsumerWarps) % kConsumerWarps + kConsumerWarps) % kConsumerWarps;
-         r < re; r += kConsumerWarps) {
-      const T *row = base + (cell_row_off(r, c.nI, vs) - off0);
-      if (r < c.nI) {
-        const T xr = xs[r];
-        T dot = T(0);
-        if (okA && 4 * qa <= r) {
-          T v[4];
-          ld4(row + 4 * qa, v);
-          dot += v[0] * xa[0] + v[1] * xa[1] + v[2] * xa[2] + v[3] * xa[3];
+    const CellDesc c = cm[b].c;
+    const int nch = cm[b].nch;
+    const T *xs = xs0 + b * xstride;
+    const T *xb = xb0 + b * bstride;
+    const int nIp = (int)pad4(c.nI);
+    const long long vs = nIp;
+    consumers_sync();  // yrow and part of the previous cell are no longer read
+    const int nq = nIp / 4;
+    const int qa = lane, qb = nq - 1 - lane;  // one warp covers all column pairs (nq <= 64)
+    const bool okA = qa < (nq + 1) / 2;
+    const bool okB = okA && qb > qa;
+    T aA[4] = {T(0), T(0), T(0), T(0)}, aB[4] = {T(0), T(0), T(0), T(0)};
+    T xa[4] = {T(0), T(0), T(0), T(0)}, xbq[4] = {T(0), T(0), T(0), T(0)};
+    if (okA) ld4(xs + 4 * qa, xa);
+    if (okB) ld4(xs + 4 * qb, xbq);
+    for (int j = 0; j < nch; ++j, ++k) {
+      const int sidx = (int)(k % kStages);
+      if (!mbar_wait(&full[sidx], (unsigned)((k / kStages) & 1))) {
+        if (lane == 0) err[0] = 1.0;
+        return;
+      }
+      const T *base = reinterpret_cast<const T *>(stage + (size_t)sidx * kStageBytes);
+      const int2 rr = meta[sidx];
+      const int rb = rr.x, re = rr.y;
+      const long long off0 = cell_row_off(rb, c.nI, vs);
+      for (int r = rb + ((warp - rb % kConsumerWarps) % kConsumerWarps + kConsumerWarps) % kConsumerWarps;
+           r < re; r += kConsumerWarps) {
+        const T *row = base + (cell_row_off(r, c.nI, vs) - off0);
+        if (r < c.nI) {
+          const T xr = xs[r];
+          T dot = T(0);
+          if (okA && 4 * qa <= r) {
+            T v[4];
+            ld4(row + 4 * qa, v);
+            dot += v[0] * xa[0] + v[1] * xa[1] + v[2] * xa[2] + v[3] * xa[3];
 #pragma unroll
-          for (int e = 0; e < 4; ++e) aA[e] += (4 * qa + e < r ? v[e] : T(0)) * xr;
-        }
-        if (okB && 4 * qb <= r) {
-          T w[4];
-          ld4(row + 4 * qb, w);
-          dot += w[0] * xbq[0] + w[1] * xbq[1] + w[2] * xbq[2] + w[3] * xbq[3];
+            for (int e = 0; e < 4; ++e) aA[e] += (4 * qa + e < r ? v[e] : T(0)) * xr;
+          }
+          if (okB && 4 * qb <= r) {
+            T w[4];
+            ld4(row + 4 * qb, w);
+            dot += w[0] * xbq[0] + w[1] * xbq[1] + w[2] * xbq[2] + w[3] * xbq[3];
 #pragma unroll
-          for (int e = 0; e < 4; ++e) aB[e] += (4 * qb + e < r ? w[e] : T(0)) * xr;
-        }
-        dot = warp_reduce(dot);
-        if (lane == 0) yrow[r] = dot;
-      } else {
-        const T xv = xb[r - c.nI];
-        if (okA) {
-          T v[4];
-          ld4(row + 4 * qa, v);
-          aA[0] -= v[0] * xv; aA[1] -= v[1] * xv; aA[2] -= v[2] * xv; aA[3] -= v[3] * xv;
-        }
-        if (okB) {
-          T w[4];
-          ld4(row + 4 * qb, w);
-          aB[0] -= w[0] * xv; aB[1] -= w[1] * xv; aB[2] -= w[2] * xv; aB[3] -= w[3] * xv;
+            for (int e = 0; e < 4; ++e) aB[e] += (4 * qb + e < r ? w[e] : T(0)) * xr;
+          }
+          dot = warp_reduce(dot);
+          if (lane == 0) yrow[r] = dot;
+        } else {
+          const T xv = xb[r - c.nI];
+          if (okA) {
+            T v[4];
+            ld4(row + 4 * qa, v);
+            aA[0] -= v[0] * xv; aA[1] -= v[1] * xv; aA[2] -= v[2] * xv; aA[3] -= v[3] * xv;
+          }
+          if (okB) {
+            T w[4];
+            ld4(row + 4 * qb, w);
+            aB[0] -= w[0] * xv; aB[1] -= w[1] * xv; aB[2] -= w[2] * xv; aB[3] -= w[3] * xv;
+          }
         }
       }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[sidx]);
     }
     __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[sidx]);
-  }
+    if (lane == 0) mbar_arrive(&freed[b]);  // xs and xb of this buffer are no longer read
 #pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    part[e * kConsumers + threadIdx.x] = aA[e];
-    part[(4 + e) * kConsumers + threadIdx.x] = aB[e];
-  }
-  consumers_sync();
-  // column sums over the 8 warps plus the row dot of the same index
-  if (warp == 0 && okA) {
+    for (int e = 0; e < 4; ++e) {
+      part[e * kConsumers + threadIdx.x] = aA[e];
+      part[(4 + e) * kConsumers + threadIdx.x] = aB[e];
+    }
+    consumers_sync();
+    // column sums over the 8 warps plus the row dot of the same index
+    if (warp == 0 && okA) {
+      const int *I = idx + c.I_off;
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      if (e >= 4 && !okB) break;
-      const int col = (e < 4 ? 4 * qa : 4 * qb) + (e & 3);
-      if (col >= c.nI) continue;
-      T sum = yrow[col];
-      for (int w = 0; w < kConsumerWarps; ++w) sum += part[e * kConsumers + w * 32 + lane];
-      x[I[col]] = sum;
+      for (int e = 0; e < 8; ++e) {
+        if (e >= 4 && !okB) break;
+        const int col = (e < 4 ? 4 * qa : 4 * qb) + (e & 3);
+        if (col >= c.nI) continue;
+        T sum = yrow[col];
+        for (int w = 0; w < kConsumerWarps; ++w) sum += part[e * kConsumers + w * 32 + lane];
+        x[I[col]] = sum;
+      }
     }
   }
 }
@@ -751,6 +902,139 @@ __global__ void __launch_bounds__(kRootThreads) k_root(int nr, const int *__rest
   }
 }
 
+// ------------------------------------------------- fused upper-level sweep
+//
+// The upper levels of the tree hold little data, and as separate launches
+// each step costs a launch and a pipeline ramp while moving a few MB.  One
+// kernel, launched as a single thread-block cluster, runs all of them: the
+// forward steps of the fused levels, the root, and the backward steps, as
+// phases separated by the cluster's hardware barrier (release/acquire at
+// cluster scope, which orders the global-memory writes of one phase before
+// the reads of the next).  In each phase the cluster's CTAs take the phase's
+// work units (cell items, separator entities, root row or column blocks)
+// round robin; a unit is the same code as the corresponding standalone
+// kernel.  The root is split into a row-parallel phase t = G_r x_r (t to a
+// scratch vector) and a column-parallel phase x_r = G_r^T t.
+
+constexpr int kUpperThreads = 512;
+constexpr int kRootBlock = 64;  // rows (phase 1) or columns (phase 2) per root unit
+
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+// root phase 1: t[r] = G_r[r, :] x_r for the rows of unit u
+template <typename T, int NT>
+__device__ __forceinline__ void root_rows_unit(int u, int nr, const int *__restrict__ ridx,
+                                               const T *__restrict__ G, const T *__restrict__ x,
+                                               T *__restrict__ t, T *xs) {
+  const int nrp = (int)pad4(nr);
+  const int r_lo = u * kRootBlock, r_hi = min(nr, r_lo + kRootBlock);
+  const int need = (int)pad4(r_hi);  // row r reads columns <= r
+  for (int i = threadIdx.x; i < need && i < nrp; i += NT) xs[i] = i < nr ? x[ridx[i]] : T(0);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int NW = NT / 32;
+  for (int r0 = r_lo + warp * kRows; r0 < r_hi; r0 += NW * kRows) {
+    const T *rp[kRows];
+    int nq[kRows];
+#pragma unroll
+    for (int k = 0; k < kRows; ++k) {
+      const int r = r0 + k;
+      rp[k] = G + tri_off(r < r_hi ? r : r_lo);
+      nq[k] = r < r_hi ? (r + 4) / 4 : 0;
+    }
+    T acc[kRows];
+    warp_rows_dot4<T>(rp, nq, xs, acc);
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < kRows; ++k)
+        if (r0 + k < r_hi) t[r0 + k] = acc[k];
+    }
+  }
+}
+
+// root phase 2: x_r[col] = sum_{i >= col} G_r[i][col] t[i] for the columns of unit u
+template <typename T, int NT>
+__device__ __forceinline__ void root_cols_unit(int u, int nr, const int *__restrict__ ridx,
+                                               const T *__restrict__ G, const T *__restrict__ t,
+                                               T *__restrict__ x, T *smem) {
+  T *part = smem;        // NT
+  T *ts = smem + NT;     // t[c_lo .. nr)
+  const int c_lo = u * kRootBlock, c_hi = min(nr, c_lo + kRootBlock);
+  for (int i = c_lo + threadIdx.x; i < nr; i += NT) ts[i - c_lo] = t[i];
+  __syncthreads();
+  constexpr int CW = kRootBlock, RG = NT / kRootBlock;
+  const int cl = threadIdx.x % CW, rg = threadIdx.x / CW;
+  const int col = c_lo + cl;
+  T acc = T(0);
+  if (col < c_hi) {
+    const int i0 = col + ((rg - col % RG) % RG + RG) % RG;
+    for (int i = i0; i < nr; i += RG) acc += G[tri_off(i) + col] * ts[i - c_lo];
+  }
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  if (rg == 0 && col < c_hi) {
+    T sum = part[cl];
+    for (int q = 1; q < RG; ++q) sum += part[q * CW + cl];
+    x[ridx[col]] = sum;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kUpperThreads) k_upper_sweep(
+    const UpperPhase *__restrict__ phases, int nphase, const UpperLevel *__restrict__ levels,
+    const int *__restrict__ idx, const long long *__restrict__ cptr,
+    const long long *__restrict__ cslot, const T *__restrict__ vals, T *__restrict__ contrib,
+    T *__restrict__ xI, T *__restrict__ x, int nr, const int *__restrict__ ridx,
+    const T *__restrict__ Gr, T *__restrict__ rt) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *sm = reinterpret_cast<T *>(smem_raw);
+  constexpr int NT = kUpperThreads;
+  constexpr int NW = NT / 32;
+  const int warp = threadIdx.x >> 5;
+  for (int p = 0; p < nphase; ++p) {
+    const UpperPhase P = phases[p];
+    const UpperLevel L = levels[P.level];
+    for (int u = blockIdx.x; u < P.units; u += gridDim.x) {
+      switch (P.type) {
+        case kPhaseCellFwd:
+          cell_fwd_unit<T, NT>(L.fwd[u], L.cells, idx, vals, contrib, xI, x, sm);
+          break;
+        case kPhaseGroupFwd:
+          if (u < L.nlarge) {
+            group_fwd_unit<T, NT>(L.groups[L.large[u]], idx, cptr, cslot, vals, contrib, x, sm);
+          } else {
+            const int t = (u - L.nlarge) * NW + warp;
+            if (t < L.nsmall)
+              group_fwd_small_warp<T>(L.groups[L.small[t]], idx, cptr, cslot, vals, contrib, x,
+                                      sm + 32 * warp);
+          }
+          break;
+        case kPhaseRootRows:
+          root_rows_unit<T, NT>(u, nr, ridx, Gr, x, rt, sm);
+          break;
+        case kPhaseRootCols:
+          root_cols_unit<T, NT>(u, nr, ridx, Gr, rt, x, sm);
+          break;
+        case kPhaseGroupBwd:
+          if (u < L.nlarge) {
+            group_bwd_unit<T, NT>(L.groups[L.large[u]], idx, vals, x, sm);
+          } else {
+            const int t = (u - L.nlarge) * NW + warp;
+            if (t < L.nsmall) group_bwd_small_warp<T>(L.groups[L.small[t]], idx, vals, x, sm + 32 * warp);
+          }
+          break;
+        default:  // kPhaseCellBwd
+          cell_bwd_unit<T, NT>(L.bwd[u], L.cells, idx, vals, xI, x, sm);
+          break;
+      }
+      __syncthreads();  // the unit's shared buffers are reused by the next unit
+    }
+    if (p + 1 < nphase) cluster_barrier();
+  }
+}
+
 __global__ void k_to_float(const double *__restrict__ a, float *__restrict__ b, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
@@ -770,8 +1054,8 @@ int set_smem_limits() {
   const int lim = 200 * 1024;
   HIF_CUDA_TRY(cudaFuncSetAttribute(k_cell_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   HIF_CUDA_TRY(cudaFuncSetAttribute(k_cell_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  HIF_CUDA_TRY(cudaFuncSetAttribute(k_group_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  HIF_CUDA_TRY(cudaFuncSetAttribute(k_group_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  HIF_CUDA_TRY(cudaFuncSetAttribute(k_group_fwd_level<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  HIF_CUDA_TRY(cudaFuncSetAttribute(k_group_bwd_level<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   HIF_CUDA_TRY(cudaFuncSetAttribute(k_root<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   HIF_CUDA_TRY(cudaFuncSetAttribute(k_cell_fwd_tma_S<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   HIF_CUDA_TRY(cudaFuncSetAttribute(k_cell_bwd_tma_S<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
@@ -785,16 +1069,149 @@ int set_smem_limits() {
 // split over CTAs, whose rows fit one stage and whose column pairs fit one
 // warp (nI <= 256).  FP64 applies are bound by the FP64 pipe, not by HBM, and
 // keep the register-streaming G-form kernels.
+// shared-memory elements of the backward S-form kernel beyond the stages:
+// part (8 per consumer), yrow, two x_I buffers, two x_B buffers
+size_t tma_bwd_smem_elems(const LevelDev &lv) {
+  return (size_t)8 * kConsumers + 3 * (size_t)pad4(lv.max_nI) + 2 * (size_t)pad4(lv.max_nB);
+}
+
 bool level_sform(const Handle *h, const LevelDev &lv) {
   if (!h->use_tma || lv.ncells == 0 || lv.nfwd != lv.ncells || lv.nbwd != lv.ncells) return false;
   if (lv.max_chunks < 0 || pad4(lv.max_nI) > 256) return false;
-  const size_t bwd_smem = (size_t)kStages * kStageBytes +
-                          ((size_t)8 * kConsumers + 2 * pad4(lv.max_nI) + lv.max_nB) * sizeof(float);
+  const size_t bwd_smem = (size_t)kStages * kStageBytes + tma_bwd_smem_elems(lv) * sizeof(float);
   return bwd_smem <= 200 * 1024;
 }
 
 bool use_tma(const Handle *h, const LevelDev &lv, size_t elem) {
   return elem == sizeof(float) && level_sform(h, lv);
+}
+
+// Grid of the persistent TMA-staged cell kernels: the CTAs that fit on the
+// GPU at once (HIFCN_TMA_CTAS overrides the CTAs per SM), at most one per cell.
+int tma_grid(const void *fn, size_t smem, int ncells) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kTmaThreads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    occ = 1;
+  }
+  const char *e = std::getenv("HIFCN_TMA_CTAS");
+  if (e && std::atoi(e) > 0) occ = std::min(occ, std::atoi(e));
+  occ = std::max(occ, 1);
+  return std::max(1, std::min(ncells, sms * occ));
+}
+
+// Launches of one level's steps outside the fused sweep.
+template <typename T>
+int launch_cell_fwd(Handle *h, const LevelDev &lv, int l, const FactorValues<T> &fv, T *x,
+                    cudaStream_t s) {
+  if (!lv.ncells) return HIF_OK;
+  const double E = sizeof(T);
+  const bool sf = use_tma(h, lv, sizeof(T));
+  StatScope sc(h, "cell_fwd", l,
+               sf ? (lv.vals_V + lv.vec_cell_fwd / 2 + lv.contrib) * E + lv.idx_cell_fwd
+                  : (lv.vals_cell + lv.vec_cell_fwd + lv.contrib) * E + lv.idx_cell_fwd, s);
+  if (sf) {
+    size_t sm = (size_t)kStages * kStageBytes + 2 * (size_t)pad4(lv.max_nI) * sizeof(T);
+    const int grid = tma_grid((const void *)k_cell_fwd_tma_S<T>, sm, lv.ncells);
+    k_cell_fwd_tma_S<T><<<grid, kTmaThreads, sm, s>>>(lv.cells, lv.ncells, lv.chunk_of[0],
+                                                       lv.chunk_tab[0], h->idx, fv.vals, fv.contrib, x,
+                                                       h->scal + kScalErr, lv.max_nI);
+  } else {
+    size_t sm = (size_t)pad4(lv.max_nI) * sizeof(T);
+    k_cell_fwd<T><<<lv.nfwd, kCellFwdThreads, sm, s>>>(lv.fwd, lv.cells, h->idx, fv.vals, fv.contrib,
+                                                        fv.xI, x);
+  }
+  return HIF_OK;
+}
+
+template <typename T>
+int launch_group_fwd(Handle *h, const LevelDev &lv, int l, const FactorValues<T> &fv, T *x,
+                     cudaStream_t s) {
+  if (!lv.ngroups) return HIF_OK;
+  const double E = sizeof(T);
+  const size_t sm = std::max<size_t>(pad4(lv.max_ng), 32 * kSmallWarps) * sizeof(T);
+  StatScope sc(h, "group_fwd", l,
+               (lv.vals_group + lv.vec_group + lv.contrib) * E + lv.idx_group + lv.cslot_bytes, s);
+  const int grid = lv.nlarge + (lv.nsmall + kSmallWarps - 1) / kSmallWarps;
+  k_group_fwd_level<T><<<grid, kSmallWarps * 32, sm, s>>>(lv.large_groups, lv.nlarge, lv.small_groups,
+                                                          lv.nsmall, lv.groups, h->idx, h->cptr,
+                                                          h->cslot, fv.vals, fv.contrib, x);
+  return HIF_OK;
+}
+
+template <typename T>
+int launch_group_bwd(Handle *h, const LevelDev &lv, int l, const FactorValues<T> &fv, T *x,
+                     cudaStream_t s) {
+  if (!lv.ngroups) return HIF_OK;
+  const double E = sizeof(T);
+  const size_t sm = std::max<size_t>((size_t)lv.max_ng + kSmallWarps * 32, 32 * kSmallWarps) * sizeof(T);
+  StatScope sc(h, "group_bwd", l, (lv.vals_group + lv.vec_group) * E + lv.idx_group_bwd, s);
+  const int grid = lv.nlarge + (lv.nsmall + kSmallWarps - 1) / kSmallWarps;
+  k_group_bwd_level<T><<<grid, kSmallWarps * 32, sm, s>>>(lv.large_groups, lv.nlarge, lv.small_groups,
+                                                          lv.nsmall, lv.groups, h->idx, fv.vals, x);
+  return HIF_OK;
+}
+
+template <typename T>
+int launch_cell_bwd(Handle *h, const LevelDev &lv, int l, const FactorValues<T> &fv, T *x,
+                    cudaStream_t s) {
+  if (!lv.ncells) return HIF_OK;
+  const double E = sizeof(T);
+  const bool sf = use_tma(h, lv, sizeof(T));
+  StatScope sc(h, "cell_bwd", l,
+               sf ? (lv.vals_S + lv.vals_V + lv.vec_cell_bwd) * E + lv.idx_cell_bwd
+                  : (lv.vals_cell + lv.vec_cell_bwd) * E + lv.idx_cell_bwd, s);
+  if (sf) {
+    size_t sm = (size_t)kStages * kStageBytes + tma_bwd_smem_elems(lv) * sizeof(T);
+    const int grid = tma_grid((const void *)k_cell_bwd_tma_S<T>, sm, lv.ncells);
+    k_cell_bwd_tma_S<T><<<grid, kTmaThreads, sm, s>>>(lv.cells, lv.ncells, lv.chunk_of[1],
+                                                       lv.chunk_tab[1], h->idx, fv.vals, x,
+                                                       h->scal + kScalErr, lv.max_nI, lv.max_nB);
+  } else {
+    size_t sm = ((size_t)lv.max_nI + lv.max_nB + 8 * kCellBwdThreads) * sizeof(T);
+    k_cell_bwd<T><<<lv.nbwd, kCellBwdThreads, sm, s>>>(lv.bwd, lv.cells, h->idx, fv.vals, fv.xI, x);
+  }
+  return HIF_OK;
+}
+
+template <typename T>
+int launch_upper(Handle *h, const FactorValues<T> &fv, T *x, cudaStream_t s) {
+  const int pi = sizeof(T) == 8 ? 0 : 1;
+  StatScope sc(h, "upper_sweep", h->upper_lb, h->upper_bytes[pi], s);
+  int nr = h->root_n;
+  const int *ridx = h->idx + h->root_idx_off;
+  const T *Gr = fv.vals + h->root_G_off;
+  T *rt = reinterpret_cast<T *>(h->upper_rt);
+  const UpperPhase *ph = h->upper_phases;
+  int nph = h->upper_nphase;
+  const UpperLevel *lvs = h->upper_levels;
+  const int *idx = h->idx;
+  const long long *cptr = h->cptr, *cslot = h->cslot;
+  const T *vals = fv.vals;
+  T *contrib = fv.contrib, *xI = fv.xI;
+  void *args[] = {(void *)&ph, (void *)&nph, (void *)&lvs, (void *)&idx, (void *)&cptr,
+                  (void *)&cslot, (void *)&vals, (void *)&contrib, (void *)&xI, (void *)&x,
+                  (void *)&nr, (void *)&ridx, (void *)&Gr, (void *)&rt};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(h->upper_grid[pi]);
+  cfg.blockDim = dim3(kUpperThreads);
+  cfg.dynamicSmemBytes = h->upper_smem[pi];
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = h->upper_grid[pi];
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  HIF_CUDA_TRY(cudaLaunchKernelExC(&cfg, (const void *)k_upper_sweep<T>, args));
+  return HIF_OK;
 }
 
 template <typename T>
@@ -803,7 +1220,7 @@ int apply_levels(Handle *h, const FactorValues<T> &fv, T *x, cudaStream_t s) {
   const size_t lim = 200 * 1024;
   for (const LevelDev &lv : h->lv)
     if ((size_t)(lv.max_nI + lv.max_nB + 8 * kCellBwdThreads) * sizeof(T) > lim ||
-        (size_t)(lv.max_ng + kGroupThreads) * sizeof(T) > lim) {
+        (size_t)(lv.max_ng + kSmallWarps * 32) * sizeof(T) > lim) {
       set_last_error("a box of the factor exceeds the shared-memory staging limit");
       return HIF_EINVAL;
     }
@@ -811,77 +1228,165 @@ int apply_levels(Handle *h, const FactorValues<T> &fv, T *x, cudaStream_t s) {
     set_last_error("root block exceeds the shared-memory staging limit");
     return HIF_EINVAL;
   }
-  const double E = sizeof(T);
+  const int pi = sizeof(T) == 8 ? 0 : 1;
+  const bool fused = h->use_upper && h->upper_grid[pi] > 0;
+  const int lb = fused ? h->upper_lb : h->L;  // levels >= lb and the root are fused
   for (int l = 0; l < h->L; ++l) {
-    const LevelDev &lv = h->lv[l];
-    if (lv.ncells) {
-      const bool sf = use_tma(h, lv, sizeof(T));
-      StatScope sc(h, "cell_fwd", l,
-                   sf ? (lv.vals_V + lv.vec_cell_fwd / 2 + lv.contrib) * E + lv.idx_cell_fwd
-                      : (lv.vals_cell + lv.vec_cell_fwd + lv.contrib) * E + lv.idx_cell_fwd, s);
-      if (use_tma(h, lv, sizeof(T))) {
-        size_t sm = (size_t)kStages * kStageBytes + (size_t)pad4(lv.max_nI) * sizeof(T);
-        k_cell_fwd_tma_S<T><<<lv.ncells, kTmaThreads, sm, s>>>(lv.cells, lv.chunk_of[0], lv.chunk_tab[0],
-                                                                h->idx, fv.vals, fv.contrib, x,
-                                                                h->scal + kScalErr);
-      } else {
-        size_t sm = (size_t)pad4(lv.max_nI) * sizeof(T);
-        k_cell_fwd<T><<<lv.nfwd, kCellFwdThreads, sm, s>>>(lv.fwd, lv.cells, h->idx, fv.vals, fv.contrib,
-                                                            fv.xI, x);
-      }
-    }
-    if (lv.ngroups) {
-      size_t sm = (size_t)pad4(lv.max_ng) * sizeof(T);
-      StatScope sc(h, "group_fwd", l,
-                   (lv.vals_group + lv.vec_group + lv.contrib) * E + lv.idx_group + lv.cslot_bytes, s);
-      if (lv.nsmall)
-        k_group_fwd_small<T><<<(lv.nsmall + kSmallWarps - 1) / kSmallWarps, kSmallWarps * 32, 0, s>>>(
-            lv.small_groups, lv.nsmall, lv.groups, h->idx, h->cptr, h->cslot, fv.vals, fv.contrib, x);
-      if (lv.nlarge)
-        k_group_fwd<T><<<lv.nlarge, kGroupThreads, sm, s>>>(lv.large_groups, lv.groups, h->idx, h->cptr,
-                                                            h->cslot, fv.vals, fv.contrib, x);
-      if (lv.nsmall && lv.nlarge) note_launch();
-    }
+    if (fused && l >= lb) break;
+    HIF_TRY(launch_cell_fwd<T>(h, h->lv[l], l, fv, x, s));
+    HIF_TRY(launch_group_fwd<T>(h, h->lv[l], l, fv, x, s));
   }
-  if (h->root_n > 0) {
+  if (fused) {
+    HIF_TRY(launch_upper<T>(h, fv, x, s));
+  } else if (h->root_n > 0) {
     size_t sm = (2 * (size_t)pad4(h->root_n) + kRootThreads) * sizeof(T);
-    const double nr = h->root_n;
+    const double nr = h->root_n, E = sizeof(T);
     StatScope sc(h, "root", -1, (nr * (nr + 1) / 2 + 2 * nr) * E + 4 * nr, s);
     k_root<T><<<1, kRootThreads, sm, s>>>(h->root_n, h->idx + h->root_idx_off,
                                           fv.vals + h->root_G_off, x);
   }
-  for (int l = h->L - 1; l >= 0; --l) {
-    const LevelDev &lv = h->lv[l];
-    if (lv.ngroups) {
-      size_t sm = ((size_t)lv.max_ng + kGroupThreads) * sizeof(T);
-      StatScope sc(h, "group_bwd", l, (lv.vals_group + lv.vec_group) * E + lv.idx_group_bwd, s);
-      if (lv.nsmall)
-        k_group_bwd_small<T><<<(lv.nsmall + kSmallWarps - 1) / kSmallWarps, kSmallWarps * 32, 0, s>>>(
-            lv.small_groups, lv.nsmall, lv.groups, h->idx, fv.vals, x);
-      if (lv.nlarge)
-        k_group_bwd<T><<<lv.nlarge, kGroupThreads, sm, s>>>(lv.large_groups, lv.groups, h->idx, fv.vals, x);
-      if (lv.nsmall && lv.nlarge) note_launch();
-    }
-    if (lv.ncells) {
-      const bool sf = use_tma(h, lv, sizeof(T));
-      StatScope sc(h, "cell_bwd", l,
-                   sf ? (lv.vals_S + lv.vals_V + lv.vec_cell_bwd) * E + lv.idx_cell_bwd
-                      : (lv.vals_cell + lv.vec_cell_bwd) * E + lv.idx_cell_bwd, s);
-      if (use_tma(h, lv, sizeof(T))) {
-        size_t sm = (size_t)kStages * kStageBytes +
-                    ((size_t)8 * kConsumers + 2 * pad4(lv.max_nI) + lv.max_nB) * sizeof(T);
-        k_cell_bwd_tma_S<T><<<lv.ncells, kTmaThreads, sm, s>>>(lv.cells, lv.chunk_of[1], lv.chunk_tab[1],
-                                                                h->idx, fv.vals, x, h->scal + kScalErr);
-      } else {
-        size_t sm = ((size_t)lv.max_nI + lv.max_nB + 8 * kCellBwdThreads) * sizeof(T);
-        k_cell_bwd<T><<<lv.nbwd, kCellBwdThreads, sm, s>>>(lv.bwd, lv.cells, h->idx, fv.vals, fv.xI, x);
-      }
-    }
+  for (int l = (fused ? lb : h->L) - 1; l >= 0; --l) {
+    HIF_TRY(launch_group_bwd<T>(h, h->lv[l], l, fv, x, s));
+    HIF_TRY(launch_cell_bwd<T>(h, h->lv[l], l, fv, x, s));
   }
   HIF_CUDA_TRY(cudaGetLastError());
   return HIF_OK;
 }
 
+// Bytes of one level's steps in the G-form (forward and backward), for the
+// fused sweep's accounting.
+double level_bytes_gform(const LevelDev &lv, double E) {
+  return (2 * lv.vals_cell + lv.vec_cell_fwd + lv.vec_cell_bwd + 2 * lv.contrib) * E +
+         lv.idx_cell_fwd + lv.idx_cell_bwd +
+         (2 * lv.vals_group + 2 * lv.vec_group + lv.contrib) * E + lv.idx_group + lv.idx_group_bwd +
+         lv.cslot_bytes;
+}
+
+// One cluster of 16 CTAs (8 where 16 cannot be scheduled), fewer when the
+// largest phase has fewer units.
+template <typename T>
+int upper_launch_shape(Handle *h, size_t smem, int max_units) {
+  const int pi = sizeof(T) == 8 ? 0 : 1;
+  h->upper_grid[pi] = 0;
+  if (smem > 200 * 1024) return HIF_OK;
+  const void *fn = (const void *)k_upper_sweep<T>;
+  HIF_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  HIF_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  int want = 16;
+  const char *e = std::getenv("HIFCN_UPPER_CTAS");
+  if (e && std::atoi(e) > 0) want = std::min(16, std::atoi(e));
+  for (int c = std::min(want, std::max(1, max_units)); c >= 1; c = c > 8 ? 8 : c - 1) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(c);
+    cfg.blockDim = dim3(kUpperThreads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = c;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      nclusters = 0;
+    }
+    if (nclusters >= 1) {
+      h->upper_grid[pi] = c;
+      h->upper_smem[pi] = smem;
+      return HIF_OK;
+    }
+  }
+  return HIF_OK;
+}
+
+}  // namespace
+
+// Plan of the fused upper-level sweep: which levels it covers (the top levels
+// whose factor data is small, so that a launch per step would cost more than
+// the step), its phases and their work units, and its launch shape per
+// precision.  HIFCN_NO_FUSED=1 keeps one launch per step (A/B measurement).
+int build_upper_plan(Handle *h) {
+  h->use_upper = false;
+  const char *off = std::getenv("HIFCN_NO_FUSED");
+  if (off && off[0] == '1') return HIF_OK;
+  const int L = h->L;
+  // FP32 value bytes of a fused level, in MB: one cluster streams only a few
+  // MB in the time a level's own launch takes, so only the top levels and
+  // the root are fused (HIFCN_FUSE_MB overrides)
+  double fuse_mb = 1.0;
+  const char *fm = std::getenv("HIFCN_FUSE_MB");
+  if (fm && std::atof(fm) >= 0.0) fuse_mb = std::atof(fm);
+  const double kFuseBytes = fuse_mb * 1024 * 1024;
+  int lb = L;
+  while (lb > 0) {
+    const LevelDev &lv = h->lv[lb - 1];
+    if ((lv.vals_cell + lv.vals_group) * 4.0 > kFuseBytes) break;
+    --lb;
+  }
+  std::vector<UpperLevel> ul(L);
+  for (int l = 0; l < L; ++l) {
+    const LevelDev &lv = h->lv[l];
+    ul[l] = UpperLevel{lv.fwd, lv.bwd, lv.cells, lv.groups, lv.small_groups, lv.large_groups,
+                       lv.nfwd, lv.nbwd, lv.nsmall, lv.nlarge};
+  }
+  std::vector<UpperPhase> ph;
+  constexpr int kWarpsU = kUpperThreads / 32;
+  auto group_units = [&](const LevelDev &lv) { return lv.nlarge + (lv.nsmall + kWarpsU - 1) / kWarpsU; };
+  for (int l = lb; l < L; ++l) {
+    const LevelDev &lv = h->lv[l];
+    if (lv.ncells) ph.push_back({kPhaseCellFwd, l, lv.nfwd, 0});
+    if (lv.ngroups) ph.push_back({kPhaseGroupFwd, l, group_units(lv), 0});
+  }
+  const int nr = h->root_n;
+  const int ru = (nr + kRootBlock - 1) / kRootBlock;
+  if (nr > 0) {
+    ph.push_back({kPhaseRootRows, 0, ru, 0});
+    ph.push_back({kPhaseRootCols, 0, ru, 0});
+  }
+  for (int l = L - 1; l >= lb; --l) {
+    const LevelDev &lv = h->lv[l];
+    if (lv.ngroups) ph.push_back({kPhaseGroupBwd, l, group_units(lv), 0});
+    if (lv.ncells) ph.push_back({kPhaseCellBwd, l, lv.nbwd, 0});
+  }
+  if (ph.empty()) return HIF_OK;
+  int max_units = 1;
+  for (auto &p : ph) max_units = std::max(max_units, p.units);
+  // shared memory per precision: the largest unit buffer of any phase
+  size_t need_e = std::max<size_t>(kUpperThreads, kUpperThreads + (size_t)pad4(std::max(nr, 1)));
+  for (auto &p : ph) {
+    const LevelDev &lv = h->lv[p.level];
+    if (p.type == kPhaseCellFwd) need_e = std::max<size_t>(need_e, pad4(lv.max_nI));
+    if (p.type == kPhaseCellBwd)
+      need_e = std::max<size_t>(need_e, (size_t)8 * kUpperThreads + lv.max_nI + lv.max_nB);
+    if (p.type == kPhaseGroupFwd) need_e = std::max<size_t>(need_e, pad4(lv.max_ng));
+    if (p.type == kPhaseGroupBwd) need_e = std::max<size_t>(need_e, (size_t)lv.max_ng + kUpperThreads);
+  }
+  HIF_TRY(upper_launch_shape<double>(h, need_e * sizeof(double), max_units));
+  HIF_TRY(upper_launch_shape<float>(h, need_e * sizeof(float), max_units));
+  if (h->upper_grid[0] == 0 && h->upper_grid[1] == 0) return HIF_OK;
+  for (int pi = 0; pi < 2; ++pi) {
+    const double E = pi == 0 ? 8.0 : 4.0;
+    double b = 0;
+    for (int l = lb; l < L; ++l) b += level_bytes_gform(h->lv[l], E);
+    const double dnr = nr;
+    b += (dnr * (dnr + 1) + 4 * dnr) * E + 8 * dnr;
+    h->upper_bytes[pi] = b;
+  }
+  HIF_TRY(dev_alloc(h, (void **)&h->upper_phases, ph.size() * sizeof(UpperPhase)));
+  HIF_TRY(dev_alloc(h, (void **)&h->upper_levels, std::max<size_t>(1, ul.size()) * sizeof(UpperLevel)));
+  HIF_TRY(dev_alloc(h, &h->upper_rt, std::max(nr, 1) * sizeof(double)));
+  HIF_CUDA_TRY(cudaMemcpy(h->upper_phases, ph.data(), ph.size() * sizeof(UpperPhase), cudaMemcpyHostToDevice));
+  if (!ul.empty())
+    HIF_CUDA_TRY(cudaMemcpy(h->upper_levels, ul.data(), ul.size() * sizeof(UpperLevel), cudaMemcpyHostToDevice));
+  h->upper_nphase = (int)ph.size();
+  h->upper_lb = lb;
+  h->use_upper = true;
+  return HIF_OK;
+}
+
+namespace {
 }  // namespace
 
 int apply_inplace_f64(Handle *h, double *x, cudaStream_t s) { return apply_levels<double>(h, h->f64, x, s); }

@@ -51,7 +51,7 @@ int scratch_for_current_device(double **out) {
 }  // namespace
 
 extern "C" int hif_apply_noalloc(hif_handle *h, const double *x, double *y, hif_stream stream) {
-  if (!h || !x || !y || x == y) return HIF_EINVAL;
+  if (!h || !x || !y || x == y || !h->factor_ok) return HIF_EINVAL;
   if (h->max_contrib > (long long)HIF_NOALLOC_MAX_SLOTS) {
     hifcn::set_last_error("hif_apply_noalloc: the factor needs " + std::to_string(h->max_contrib) +
                           " contribution slots, the static scratch holds " +

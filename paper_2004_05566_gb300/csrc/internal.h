@@ -57,7 +57,7 @@ __host__ __device__ inline long long pad4(long long n) { return (n + 3) & ~3LL; 
 constexpr int kScalErr = 15;
 
 // Size of one shared-memory stage of the bulk-copy staged cell kernels.
-constexpr int kStageBytes = 16384;
+constexpr int kStageBytes = 15872;  // 124 x 128 B: three backward CTAs fit an SM
 __host__ __device__ inline long long tri_off(long long i) {
   const long long q = i >> 2, r = i & 3;
   return 8 * q * (q + 1) + 4 * r * (q + 1);
@@ -115,6 +115,27 @@ struct LevelDev {
   GroupDesc *groups = nullptr;  // device
 };
 
+// Fused upper-level sweep (one cooperative kernel for the small levels and
+// the root): per-level device pointers and the phase program.
+enum UpperPhaseType {
+  kPhaseCellFwd = 0,
+  kPhaseGroupFwd = 1,
+  kPhaseRootRows = 2,
+  kPhaseRootCols = 3,
+  kPhaseGroupBwd = 4,
+  kPhaseCellBwd = 5
+};
+struct UpperLevel {
+  const CellItem *fwd, *bwd;
+  const CellDesc *cells;
+  const GroupDesc *groups;
+  const int *small, *large;
+  int nfwd, nbwd, nsmall, nlarge;
+};
+struct UpperPhase {
+  int type, level, units, pad;
+};
+
 template <typename T>
 struct FactorValues {
   T *vals = nullptr;       // device value pool
@@ -163,15 +184,32 @@ struct hif_handle {
   void *pcg_graph[4] = {nullptr, nullptr, nullptr, nullptr};  // captured PCG loop per
                                                              // (precision, warm start)
   cudaStream_t cap_stream = nullptr;  // private stream used for graph capture
+  // fused upper-level sweep: levels >= upper_lb and the root run in one
+  // kernel launched as a thread-block cluster (see apply.cu)
+  bool use_upper = false;
+  int upper_lb = 0;
+  int upper_nphase = 0;
+  hifcn::UpperPhase *upper_phases = nullptr;  // device
+  hifcn::UpperLevel *upper_levels = nullptr;  // device
+  void *upper_rt = nullptr;                   // device root scratch (root_n doubles)
+  size_t upper_smem[2] = {0, 0};              // dynamic shared memory, FP64 / FP32
+  int upper_grid[2] = {0, 0};                 // CTAs of the cluster, FP64 / FP32
+  double upper_bytes[2] = {0, 0};             // algorithmic bytes per launch, FP64 / FP32
   bool use_graph = true;
   bool use_tma = true;                // bulk-copy staging of the leaf cell blocks
   double *partials = nullptr;  // per-block partial sums
   double *scal = nullptr;      // device scalars (see pcg.cu)
+  unsigned *tickets = nullptr; // last-block counters of the captured loop's kernels (4)
   double *host_scal = nullptr; // pinned host mirror
   int nblocks_vec = 0;
 
   std::vector<void *> allocations;
   long long device_bytes = 0;
+  // allocations [factor_alloc_begin, end) belong to the factor (released by
+  // hif_refactor); work_device_bytes is device_bytes without them
+  size_t factor_alloc_begin = 0;
+  long long work_device_bytes = 0;
+  bool factor_ok = false;  // a factor is present (false after a failed refactor)
 
   // kernel statistics (hif_stats_enable)
   struct StatRec {
@@ -209,9 +247,11 @@ struct StatScope {
 // ----------------------------------------------------------------- kernels/drivers
 
 int stencil_init(Handle *h, const double *a_nodes, cudaStream_t s);
+int stencil_update(Handle *h, const double *a_nodes, cudaStream_t s);
 int stencil_matvec(Handle *h, const double *x, double *y, cudaStream_t s);
 int build_device_factor(Handle *h, const std::vector<double> &vals64, cudaStream_t s);
 int apply_inverse(Handle *h, const double *x, double *y, int precision, cudaStream_t s);
+int build_upper_plan(Handle *h);
 int pcg(Handle *h, const double *b, double *x, int *iters, double *relres, cudaStream_t s);
 int cn(Handle *h, const double *u, const double *r, double *u1, int *iters, cudaStream_t s);
 int cn_batched(Handle *const *hs, int count, const double *const *u, const double *const *r,

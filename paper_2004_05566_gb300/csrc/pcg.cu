@@ -184,13 +184,6 @@ __global__ void k_scalar_start(double *__restrict__ s, const double *__restrict_
   cudaGraphSetConditional(cond, v > 0.0 ? 1u : 0u);
 }
 
-// rz' -> beta (0 on the first iteration), rz
-__global__ void k_scalar_beta(double *__restrict__ s, const double *__restrict__ part, int np) {
-  double v = warp_sum_partials(part, np);
-  if (threadIdx.x != 0) return;
-  s[S_BETA] = s[S_IT] == 0.0 ? 0.0 : v / s[S_RZ];
-  s[S_RZ] = v;
-}
 
 // p = z + beta p, with p = z on the first iteration (p is not read then)
 template <typename TZ>
@@ -202,16 +195,128 @@ __global__ void __launch_bounds__(NT) k_update_p_dev(double *__restrict__ p, con
     p[j] = first ? (double)z[j] : (double)z[j] + beta * p[j];
 }
 
-// every `period` iterations: r = b - A x (true residual), z-input = r, partial r.r
+
+
+// ---- scalar phases folded into the vector kernels of the captured loop.
+// Each block writes its partial sum; the last block to finish (ticket
+// counter) adds all partials in block order, so the scalars are the same as
+// with a separate scalar kernel, and resets the ticket for the next use.
+__device__ __forceinline__ bool last_block(unsigned *ticket) {
+  __shared__ bool am_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) am_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  return am_last;
+}
+
+__device__ __forceinline__ double warp_sum_partials_cg(const double *partials, int np) {
+  const int lane = threadIdx.x & 31;
+  double v = 0.0;
+  for (int i = lane; i < np; i += 32) v += __ldcg(partials + i);
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// rz' = r.z, then (last block) beta = rz'/rz (0 on the first iteration), rz = rz'
+template <typename TB>
+__global__ void __launch_bounds__(NT) k_dot_beta(const double *__restrict__ a, const TB *__restrict__ b,
+                                                 long long N, double *__restrict__ part,
+                                                 double *__restrict__ s, unsigned *__restrict__ ticket) {
+  __shared__ double sm[NT / 32];
+  double acc = 0.0;
+  for (long long j = blockIdx.x * (long long)NT + threadIdx.x; j < N; j += (long long)gridDim.x * NT)
+    acc += a[j] * (double)b[j];
+  double t = block_sum<NT>(acc, sm);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+  if (!last_block(ticket) || threadIdx.x >= 32) return;
+  const double v = warp_sum_partials_cg(part, gridDim.x);
+  if (threadIdx.x == 0) {
+    s[S_BETA] = s[S_IT] == 0.0 ? 0.0 : v / s[S_RZ];
+    s[S_RZ] = v;
+    *ticket = 0u;
+  }
+}
+
+// q = A p, p.q, then (last block) alpha = rz / pq
+__global__ void __launch_bounds__(NT) k_spmv_alpha(const double *__restrict__ p, double *__restrict__ q,
+                                                   StencilArgs st, double *__restrict__ part,
+                                                   double *__restrict__ s, unsigned *__restrict__ ticket) {
+  __shared__ double sm[NT / 32];
+  double acc = 0.0;
+  for (long long j = blockIdx.x * (long long)NT + threadIdx.x; j < st.N; j += (long long)gridDim.x * NT) {
+    double v = stencil_row(p, st.diag, st.wx, st.wy, st.wz, st.dim, st.n, j);
+    q[j] = v;
+    acc += p[j] * v;
+  }
+  double t = block_sum<NT>(acc, sm);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+  if (!last_block(ticket) || threadIdx.x >= 32) return;
+  const double v = warp_sum_partials_cg(part, gridDim.x);
+  if (threadIdx.x == 0) {
+    s[S_PQ] = v;
+    s[S_ALPHA] = s[S_RZ] / v;
+    *ticket = 0u;
+  }
+}
+
+// the end-of-iteration scalar phase: r.r -> convergence; it += 1; loop condition
+__device__ __forceinline__ void finish_iteration(double *s, double rr, double tol2, int maxit,
+                                                 cudaGraphConditionalHandle cond) {
+  s[S_RR] = rr;
+  const double it = s[S_IT] + 1.0;
+  s[S_IT] = it;
+  const bool conv = rr <= tol2 * s[S_BB];
+  s[S_CONV] = conv ? 1.0 : 0.0;
+  cudaGraphSetConditional(cond, (!conv && it < (double)maxit) ? 1u : 0u);
+}
+
+// x += alpha p; r -= alpha q; z-input = r; r.r; then (last block, unless this
+// iteration recomputes the true residual) the end-of-iteration scalar phase
 template <typename TZ>
-__global__ void __launch_bounds__(NT) k_true_residual_periodic(const double *__restrict__ b,
-                                                               const double *__restrict__ x,
-                                                               double *__restrict__ r,
-                                                               TZ *__restrict__ zin, StencilArgs st,
-                                                               const double *__restrict__ s, int period,
-                                                               double *__restrict__ part) {
-  const int it = (int)s[S_IT] + 1;  // iteration that just updated x
-  if (period <= 0 || it % period != 0) return;
+__global__ void __launch_bounds__(NT) k_update_xr_cond(double *__restrict__ x, double *__restrict__ r,
+                                                       const double *__restrict__ p,
+                                                       const double *__restrict__ q,
+                                                       TZ *__restrict__ zin, double *__restrict__ s,
+                                                       long long N, double *__restrict__ part,
+                                                       unsigned *__restrict__ ticket, int period,
+                                                       double tol2, int maxit,
+                                                       cudaGraphConditionalHandle cond) {
+  __shared__ double sm[NT / 32];
+  const double alpha = s[S_ALPHA];
+  const int it1 = (int)s[S_IT] + 1;  // iteration that updates x now
+  double acc = 0.0;
+  for (long long j = blockIdx.x * (long long)NT + threadIdx.x; j < N; j += (long long)gridDim.x * NT) {
+    x[j] += alpha * p[j];
+    double rj = r[j] - alpha * q[j];
+    r[j] = rj;
+    zin[j] = (TZ)rj;
+    acc += rj * rj;
+  }
+  double t = block_sum<NT>(acc, sm);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+  if (period > 0 && it1 % period == 0) return;  // the true-residual kernel finishes the iteration
+  if (!last_block(ticket) || threadIdx.x >= 32) return;
+  const double v = warp_sum_partials_cg(part, gridDim.x);
+  if (threadIdx.x == 0) {
+    *ticket = 0u;
+    finish_iteration(s, v, tol2, maxit, cond);
+  }
+}
+
+// every `period` iterations: r = b - A x, z-input = r, r.r and the
+// end-of-iteration scalar phase (a no-op launch otherwise)
+template <typename TZ>
+__global__ void __launch_bounds__(NT) k_true_residual_cond(const double *__restrict__ b,
+                                                           const double *__restrict__ x,
+                                                           double *__restrict__ r,
+                                                           TZ *__restrict__ zin, StencilArgs st,
+                                                           double *__restrict__ s, int period,
+                                                           double *__restrict__ part,
+                                                           unsigned *__restrict__ ticket, double tol2,
+                                                           int maxit, cudaGraphConditionalHandle cond) {
+  const int it1 = (int)s[S_IT] + 1;
+  if (period <= 0 || it1 % period != 0) return;
   __shared__ double sm[NT / 32];
   double acc = 0.0;
   for (long long j = blockIdx.x * (long long)NT + threadIdx.x; j < st.N; j += (long long)gridDim.x * NT) {
@@ -222,19 +327,12 @@ __global__ void __launch_bounds__(NT) k_true_residual_periodic(const double *__r
   }
   double t = block_sum<NT>(acc, sm);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
-}
-
-// r.r -> convergence; it += 1; loop condition
-__global__ void k_scalar_cond(double *__restrict__ s, const double *__restrict__ part, int np,
-                              double tol2, int maxit, cudaGraphConditionalHandle cond) {
-  double v = warp_sum_partials(part, np);
-  if (threadIdx.x != 0) return;
-  s[S_RR] = v;
-  const double it = s[S_IT] + 1.0;
-  s[S_IT] = it;
-  const bool conv = v <= tol2 * s[S_BB];
-  s[S_CONV] = conv ? 1.0 : 0.0;
-  cudaGraphSetConditional(cond, (!conv && it < (double)maxit) ? 1u : 0u);
+  if (!last_block(ticket) || threadIdx.x >= 32) return;
+  const double v = warp_sum_partials_cg(part, gridDim.x);
+  if (threadIdx.x == 0) {
+    *ticket = 0u;
+    finish_iteration(s, v, tol2, maxit, cond);
+  }
 }
 
 // A kernel reported an expired bounded wait: clear the flag, report it.
@@ -346,16 +444,15 @@ int build_pcg_graph(Handle *h, TZ *z, PcgGraph *G, bool warm) {
   int st_apply;
   if constexpr (sizeof(TZ) == 8) st_apply = apply_inplace_f64(h, (double *)z, cs);
   else st_apply = apply_inplace_f32(h, (float *)z, cs);
-  k_dot<TZ><<<nb, NT, 0, cs>>>(h->r, z, N, part);
-  k_scalar_beta<<<1, 32, 0, cs>>>(sc, part, nb);
+  unsigned *tk = h->tickets;
+  k_dot_beta<TZ><<<nb, NT, 0, cs>>>(h->r, z, N, part, sc, tk);
   k_update_p_dev<TZ><<<nb, NT, 0, cs>>>(h->p, z, sc, N);
-  k_spmv_dot<<<nb, NT, 0, cs>>>(h->p, h->q, st, part);
-  k_scalar<<<1, 32, 0, cs>>>(sc, part, nb, 0, tol2);
-  k_update_xr<TZ><<<nb, NT, 0, cs>>>(h->xsol, h->r, h->p, h->q, z, sc, N, part);
-  k_true_residual_periodic<TZ><<<nb, NT, 0, cs>>>(h->g, h->xsol, h->r, z, st, sc,
-                                                  h->opt.true_res_period, part);
-  k_scalar_cond<<<1, 32, 0, cs>>>(sc, part, nb, tol2, h->opt.cg_maxit, cond);
-  note_launch(8);
+  k_spmv_alpha<<<nb, NT, 0, cs>>>(h->p, h->q, st, part, sc, tk + 1);
+  k_update_xr_cond<TZ><<<nb, NT, 0, cs>>>(h->xsol, h->r, h->p, h->q, z, sc, N, part, tk + 2,
+                                          h->opt.true_res_period, tol2, h->opt.cg_maxit, cond);
+  k_true_residual_cond<TZ><<<nb, NT, 0, cs>>>(h->g, h->xsol, h->r, z, st, sc, h->opt.true_res_period,
+                                              part, tk + 3, tol2, h->opt.cg_maxit, cond);
+  note_launch(5);
   cudaGraph_t body_out = nullptr;
   cudaError_t e_end = cudaStreamEndCapture(cs, &body_out);
   const long long lc2 = hif_launch_count();

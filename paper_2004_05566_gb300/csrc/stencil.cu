@@ -79,6 +79,13 @@ int stencil_init(Handle *h, const double *a_nodes, cudaStream_t s) {
   HIF_TRY(dev_alloc(h, (void **)&h->wx, N * sizeof(double)));
   HIF_TRY(dev_alloc(h, (void **)&h->wy, N * sizeof(double)));
   if (h->grid.dim == 3) HIF_TRY(dev_alloc(h, (void **)&h->wz, N * sizeof(double)));
+  return stencil_update(h, a_nodes, s);
+}
+
+// Re-assemble the stencil of A = I - theta dt M from new nodal coefficients
+// into the handle's existing arrays.
+int stencil_update(Handle *h, const double *a_nodes, cudaStream_t s) {
+  const long long N = h->N;
   const double c = h->opt.theta * h->dt / (h->h * h->h);  // A = I - theta dt M
   int nb = (int)((N + 255) / 256);
   k_stencil_init<<<nb, 256, 0, s>>>(a_nodes, h->diag, h->wx, h->wy, h->wz, h->grid.dim,

@@ -27,7 +27,8 @@ HIF_FP64, HIF_FP32 = 0, 1
 EXPORTED = ("hif_default_options", "hif_setup", "hif_import_factor", "hif_export_factor",
             "hif_apply", "hif_matvec", "pcg_solve", "cn_step", "hif_set_reaction", "hif_query",
             "hif_destroy", "hif_strerror", "hif_last_error", "hif_stats_enable", "hif_stats_read",
-            "hif_launch_count", "hif_apply_noalloc", "cn_step_batched")
+            "hif_launch_count", "hif_apply_noalloc", "cn_step_batched", "hif_set_coefficient",
+            "hif_refactor")
 
 
 class HifGrid(ctypes.Structure):
@@ -94,6 +95,10 @@ def lib():
     L.cn_step_batched.argtypes = [POINTER(c_void_p), c_int, POINTER(c_void_p), POINTER(c_void_p),
                                   POINTER(c_void_p), POINTER(c_int), c_void_p]
     L.cn_step_batched.restype = c_int
+    L.hif_set_coefficient.argtypes = [c_void_p, c_void_p, c_void_p]
+    L.hif_set_coefficient.restype = c_int
+    L.hif_refactor.argtypes = [c_void_p, c_void_p, c_void_p]
+    L.hif_refactor.restype = c_int
     for name in ("hif_setup", "hif_import_factor", "hif_export_factor", "hif_apply", "hif_matvec",
                  "pcg_solve", "cn_step", "hif_set_reaction", "hif_query", "hif_destroy",
                  "hif_stats_enable", "hif_stats_read"):
@@ -275,6 +280,18 @@ def cn_step_batched(hs, us, rs=None, outs=None, stream=None):
     it = (c_int * n)()
     _check("cn_step_batched", lib().cn_step_batched(H, n, U, R, O, it, _stream(stream)))
     return outs, list(it)
+
+
+def hif_set_coefficient(h: Handle, a_nodes: torch.Tensor, stream=None):
+    """Replace a(x); the current factor stays as the preconditioner."""
+    a = _vec(a_nodes.reshape(-1), (h.n + 1) ** h.dim, "a_nodes")
+    _check("hif_set_coefficient", lib().hif_set_coefficient(h.ptr, a, _stream(stream)))
+
+
+def hif_refactor(h: Handle, a_nodes: torch.Tensor, stream=None):
+    """Replace a(x) and factor the new operator in place."""
+    a = _vec(a_nodes.reshape(-1), (h.n + 1) ** h.dim, "a_nodes")
+    _check("hif_refactor", lib().hif_refactor(h.ptr, a, _stream(stream)))
 
 
 def hif_set_reaction(h: Handle, kind: int, k1: float = 1.0, k2: float = math.inf):

@@ -206,3 +206,28 @@ def test_warm_start_and_direct_variants():
     assert it_d == [0, 0, 0]
     # the direct solve is accurate to the factor's precision (O(eps))
     assert np.linalg.norm(direct - cold) <= 1e-3 * np.linalg.norm(cold)
+
+
+def test_time_varying_coefficient_matches_mode_products():
+    """a(x, t_k) = c_k (constant in space): M_k = c_k M_1, so each DST-I mode is
+    multiplied per step by (1 + dt c_k lam / 2) / (1 - dt c_k lam / 2), even
+    with the factor of an earlier c (refactored every 2 steps)."""
+    import scipy.fft
+    n, m, dt = 32, 8, 2e-2
+    cs = [1.0, 1.3, 0.8, 1.6, 1.1]
+    u0 = W.sine_modes_u0(n, 2, [(1, 1), (2, 3), (4, 1)], rng=np.random.default_rng(2), noise=0.05)
+    a_seq = [c * np.ones((n + 1, n + 1)) for c in cs]
+    u, iters = pcg.cn_solve_varying(a_seq, u0, dt, m, 1e-6, tol=1e-12, refactor_every=2)
+    h = 1.0 / n
+    ks = np.arange(1, n)
+    lam1 = -(4.0 / h ** 2) * np.sin(ks * math.pi * h / 2) ** 2
+    lam = lam1[:, None] + lam1[None, :]
+    coef = scipy.fft.dstn(u0, type=1)
+    for c in cs:
+        coef = coef * (1 + dt * c * lam / 2) / (1 - dt * c * lam / 2)
+    exact = scipy.fft.idstn(coef, type=1)
+    assert np.linalg.norm(u - exact) <= 1e-9 * np.linalg.norm(exact)
+    # a stale factor is a worse preconditioner for the steps that reuse it
+    u1, it1 = pcg.cn_solve_varying(a_seq, u0, dt, m, 1e-6, tol=1e-12, refactor_every=1)
+    assert np.linalg.norm(u1 - exact) <= 1e-9 * np.linalg.norm(exact)
+    assert sum(iters) >= sum(it1)
