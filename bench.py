@@ -56,6 +56,8 @@ def _args():
     p.add_argument("--batched-count", type=int, default=256,
                    help="problems of the batched workload reported beside the headline (0: skip)")
     p.add_argument("--batched-steps", type=int, default=20)
+    p.add_argument("--heat3d-steps", type=int, default=50,
+                   help="CN steps of the 3D heat 127^3 measurement reported beside the headline (0: skip)")
     p.add_argument("--serving-ops", type=int, default=16,
                    help="resident operators of the serving measurement (0: skip)")
     p.add_argument("--cpu-sample", type=int, default=0, help=argparse.SUPPRESS)
@@ -212,17 +214,28 @@ def _find_peak(d: dict, keys) -> float | None:
     return None
 
 
+def leaf_kernel_source_hash() -> str:
+    """sha256 of the source of the bulk-copy staged leaf kernels (their section
+    of apply.cu and the stage size in internal.h): the ncu traffic figures stay
+    valid while this is unchanged."""
+    csrc = os.path.join(ROOT, "paper_2004_05566_gb300", "csrc")
+    src = open(os.path.join(csrc, "apply.cu")).read()
+    a = src.index("// ------------------------------------------------------------ TMA-staged cells")
+    b = src.index("// Root (Eq. 3_4)")
+    stage = [l for l in open(os.path.join(csrc, "internal.h")) if "constexpr int kStageBytes" in l]
+    return hashlib.sha256((src[a:b] + "".join(stage)).encode()).hexdigest()
+
+
 def kernel_traffic(name: str) -> float | None:
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current source of the apply kernels (else None)."""
+    the current source of the leaf kernels (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     try:
         with open(p) as f:
             d = json.load(f)
-        src = open(os.path.join(ROOT, "paper_2004_05566_gb300", "csrc", "apply.cu"), "rb").read()
-        if d.get("apply_cu_sha256") != hashlib.sha256(src).hexdigest():
+        if d.get("leaf_kernel_sha256") != leaf_kernel_source_hash():
             return None
         k = d.get("kernels", {}).get(name)
         return float(k["dram_bytes_per_launch_full"]) if k else None
@@ -344,6 +357,11 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
     if args.batched_count > 0:
         batched = run_batched(args, dev, H, W, np, torch)
 
+    # ---- 3D heat 127^3 (leaf 8, eps 1e-4, face + edge skeletonization)
+    heat3d = None
+    if args.heat3d_steps > 0:
+        heat3d = run_heat3d(args, dev, H, W, np, torch)
+
     # ---- serving: open-loop Poisson step requests over resident operators
     serving = None
     if args.serving_ops > 0:
@@ -452,6 +470,7 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
         "clocks": clk,
         "cpu_baseline": cpu,
         "batched": batched,
+        "heat3d": heat3d,
         "serving": serving,
     }
     return line
@@ -508,6 +527,47 @@ def run_serving(args, device_index, W, np) -> dict:
            "scheduler": "step-level continuous batching over cn_step_batched (serve.CNServer)"}
     srv.close()
     return out
+
+
+def run_heat3d(args, dev, H, W, np, torch) -> dict:
+    """3D heat equation on 127^3 (leaf 8, L = 4, eps 1e-4, dt 0.1, lognormal a with
+    contrast 1e3, smooth random u0): GPU setup time, then `heat3d_steps` CN steps
+    with FP32 factors and FP64 CG, timed with CUDA events around the steps."""
+    w = W.config_heat3d_127()
+    a = torch.from_numpy(w.a_nodes).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h = H.hif_setup(3, w.n, w.leaf, a, w.dt,
+                    H.default_options(eps=w.eps, precision=H.HIF_FP32, cg_tol=1e-10))
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    info = H.hif_query(h)
+    u = torch.from_numpy(w.u0.ravel().copy()).to(dev)
+    out = torch.empty_like(u)
+    for _ in range(2):
+        H.cn_step(h, u, out=out)
+        u, out = out, u
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    its = 0
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.heat3d_steps):
+        _, it = H.cn_step(h, u, out=out)
+        its += it
+        u, out = out, u
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    h.close()
+    return {"workload": "heat3d_127: 3D heat, 127^3 interior (N=2048383), lognormal a contrast 1e3, "
+                        "dt=0.1, leaf 8 (L=4), eps=1e-4, face+edge skeletonization, FP32 factor, FP64 CG, "
+                        "PCG rel-res 1e-10",
+            "steps": args.heat3d_steps, "steps_per_s": round(args.heat3d_steps / t, 3),
+            "ms_per_step": round(1e3 * t / args.heat3d_steps, 3),
+            "iters_per_step": round(its / args.heat3d_steps, 3), "setup_s": round(t_setup, 2),
+            "apply_bytes_fp32": info["apply_bytes"], "root": info["root_size"],
+            "device_bytes": info["device_bytes"]}
 
 
 def run_batched(args, dev, H, W, np, torch) -> dict:

@@ -58,8 +58,10 @@ typedef struct {
 
 /* Storage / arithmetic of the factor blocks used by hif_apply inside PCG.
  * The factorization itself always runs in FP64; the FP32 mode keeps an
- * additional FP32 copy and applies F^{-1} in FP32 while CG stays in FP64. */
-typedef enum { HIF_FP64 = 0, HIF_FP32 = 1 } hif_precision;
+ * additional FP32 copy and applies F^{-1} in FP32 while CG stays in FP64.
+ * HIF_FP32_BF16TOP is the FP32 mode with the blocks of the top levels (and the
+ * root) stored in BF16 and applied with FP32 arithmetic (half their bytes). */
+typedef enum { HIF_FP64 = 0, HIF_FP32 = 1, HIF_FP32_BF16TOP = 2 } hif_precision;
 
 typedef struct {
   double eps;          /* relative precision of every interpolative decomposition (Eq. 2_5); 0 = exact */
@@ -75,10 +77,12 @@ typedef struct {
                           (cn_step) or from the input x (pcg_solve)                                   */
   int solver;          /* 0: PCG (Algorithm 1); 1: direct, x = F^{-1} b without CG (the factor used
                           as a solver, Sec. 3 Example 1), iterations reported as 0                    */
+  int bf16_top_levels; /* HIF_FP32_BF16TOP: number of top levels (counted from the root, which is
+                          always included) stored in BF16; 0 selects ceil(L/2)                        */
 } hif_options;
 
 /* Fills *opt with defaults: eps 1e-6, FP64, skel_edges_3d 1, tol 1e-10, maxit 1000, period 50,
- * theta 0.5, x0_mode 0, solver 0. */
+ * theta 0.5, x0_mode 0, solver 0, bf16_top_levels 0. */
 void hif_default_options(hif_options *opt);
 
 typedef struct hif_handle hif_handle; /* opaque; owns all factor and work memory on the device */
@@ -134,7 +138,8 @@ int hif_export_factor(const hif_handle *h, void *buf, size_t *bytes);
 /* ---------------------------------------------------------------------------
  * hif_apply - y = F^{-1} x = R_0 ... R_{L-1} A_L^{-1} R_{L-1}^T ... R_0^T x (Eq. Ainv).
  *   x, y  device, N doubles each; may not alias.
- *   precision  HIF_FP64 or HIF_FP32 (needs a handle set up with FP32).
+ *   precision  HIF_FP64, or HIF_FP32 / HIF_FP32_BF16TOP (needs a handle set up with one of
+ *              these; a BF16TOP handle applies its top levels in BF16 for both).
  * Errors: HIF_EINVAL, HIF_ECUDA. */
 int hif_apply(hif_handle *h, const double *x, double *y, int precision, hif_stream stream);
 

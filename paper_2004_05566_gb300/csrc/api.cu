@@ -121,6 +121,7 @@ int build_device_factor(Handle *h, const std::vector<double> &vals64, cudaStream
 }
 
 int make_cell_inverses(Handle *h, cudaStream_t s);
+int cast_values_bf16(Handle *h, cudaStream_t s);
 
 // Upload descriptors of every level, allocate the contribution scratch and
 // the FP32 copy (values already on the device in h->f64.vals).
@@ -239,7 +240,7 @@ int finish_device_factor(Handle *h, cudaStream_t s) {
   HIF_TRY(dev_alloc(h, (void **)&h->f64.xI, h->N * sizeof(double)));
   HIF_TRY(make_cell_inverses(h, s));
   HIF_TRY(dev_alloc(h, (void **)&h->f64.contrib, h->max_contrib * sizeof(double)));
-  if (h->opt.precision == HIF_FP32) {
+  if (h->opt.precision == HIF_FP32 || h->opt.precision == HIF_FP32_BF16TOP) {
     HIF_TRY(dev_alloc(h, (void **)&h->f32.vals, h->nvals * sizeof(float)));
     HIF_TRY(dev_alloc(h, (void **)&h->f32.contrib, h->max_contrib * sizeof(float)));
     HIF_TRY(dev_alloc(h, (void **)&h->f32.work, h->N * sizeof(float)));
@@ -248,6 +249,14 @@ int finish_device_factor(Handle *h, cudaStream_t s) {
     note_launch();
     HIF_CUDA_TRY(cudaGetLastError());
     h->has_f32 = true;
+  }
+  if (h->opt.precision == HIF_FP32_BF16TOP) {
+    const int top = h->opt.bf16_top_levels > 0 ? std::min(h->opt.bf16_top_levels, h->L)
+                                               : (h->L + 1) / 2;
+    h->bf16_lb = h->L - top;
+    HIF_TRY(dev_alloc(h, &h->bf16_vals, std::max<long long>(h->nvals, 1) * 2));
+    HIF_TRY(cast_values_bf16(h, s));
+    h->has_bf16 = true;
   }
   HIF_CUDA_TRY(cudaStreamSynchronize(s));
   HIF_TRY(build_upper_plan(h));
@@ -320,7 +329,9 @@ int create_handle(const hif_grid *grid, const double *a_nodes, double dt, const 
   h->h = 1.0 / grid->n;
   if (opt) h->opt = *opt;
   else hif_default_options(&h->opt);
-  if ((h->opt.precision != HIF_FP64 && h->opt.precision != HIF_FP32) || !(h->opt.theta > 0.0) ||
+  if ((h->opt.precision != HIF_FP64 && h->opt.precision != HIF_FP32 &&
+       h->opt.precision != HIF_FP32_BF16TOP) ||
+      h->opt.bf16_top_levels < 0 || !(h->opt.theta > 0.0) ||
       !(h->opt.theta <= 1.0) || (h->opt.x0_mode != 0 && h->opt.x0_mode != 1) ||
       (h->opt.solver != 0 && h->opt.solver != 1) || h->opt.cg_maxit < 0) {
     delete h;
@@ -362,6 +373,9 @@ void release_factor(Handle *h) {
   h->f64 = FactorValues<double>{};
   h->f32 = FactorValues<float>{};
   h->has_f32 = false;
+  h->bf16_vals = nullptr;
+  h->has_bf16 = false;
+  h->bf16_lb = 1 << 30;
   h->use_upper = false;
   h->upper_nphase = 0;
   h->upper_phases = nullptr;
@@ -467,8 +481,14 @@ int import_blob(Handle *h, const void *blob, size_t bytes, cudaStream_t s) {
 }
 
 long long apply_bytes(const Handle *h, int elem) {
-  long long vals = 0, idxs = 0, slots = 0;
-  for (const LevelHost &H : h->lv_host) {
+  // every factor value and index is read once per sweep (forward and
+  // backward); contributions are written and read once; the vector is read
+  // and written once per sweep.  BF16 levels hold 2-byte values.
+  long long vbytes = 0, idxs = 0, slots = 0;
+  for (size_t l = 0; l < h->lv_host.size(); ++l) {
+    const LevelHost &H = h->lv_host[l];
+    const int ve = (elem == 4 && h->has_bf16 && (int)l >= h->bf16_lb) ? 2 : elem;
+    long long vals = 0;
     for (auto &c : H.cells) {
       vals += (long long)c.nI * (c.nI + 1) / 2 + (long long)c.nB * c.nI;
       idxs += 2LL * c.nI + c.nB;
@@ -477,13 +497,12 @@ long long apply_bytes(const Handle *h, int elem) {
       vals += (long long)g.n * g.n;
       idxs += 2LL * g.n;
     }
+    vbytes += vals * ve;
     slots += H.contrib_slots;
   }
-  vals += (long long)h->root_n * (h->root_n + 1) / 2;
-  // every factor value and index is read once per sweep (forward and
-  // backward); contributions are written and read once; the vector is read
-  // and written once per sweep.
-  return 2 * vals * elem + 2 * idxs * 4 + 2 * slots * elem + 2 * h->N * elem;
+  const int re = (elem == 4 && h->has_bf16) ? 2 : elem;
+  vbytes += (long long)h->root_n * (h->root_n + 1) / 2 * re;
+  return 2 * vbytes + 2 * idxs * 4 + 2 * slots * elem + 2 * h->N * elem;
 }
 
 }  // namespace hifcn
@@ -515,6 +534,7 @@ void hif_default_options(hif_options *opt) {
   opt->theta = 0.5;
   opt->x0_mode = 0;
   opt->solver = 0;
+  opt->bf16_top_levels = 0;
 }
 
 int hif_setup(const hif_grid *grid, const double *a_nodes, double dt, const hif_options *opt,
@@ -691,7 +711,7 @@ int hif_query(const hif_handle *hh, hif_info *info) {
   info->levels = h->L;
   info->root_size = h->root_n;
   info->factor_entries = h->nvals;
-  info->apply_bytes = apply_bytes(h, h->has_f32 && h->opt.precision == HIF_FP32 ? 4 : 8);
+  info->apply_bytes = apply_bytes(h, reduced_apply(h) ? 4 : 8);
   info->device_bytes = h->device_bytes;
   info->precision = h->opt.precision;
   info->setup_seconds = h->setup_seconds;

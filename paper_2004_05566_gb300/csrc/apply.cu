@@ -23,6 +23,8 @@
 #include "internal.h"
 #include "device_common.cuh"
 
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <cstdlib>
 #include <vector>
@@ -53,12 +55,27 @@ __device__ __forceinline__ void ld4(const double *p, double (&o)[4]) {
   const double2 b = *reinterpret_cast<const double2 *>(p + 2);
   o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
 }
+// BF16 values (the top levels in the HIF_FP32_BF16TOP mode): 4 values in one
+// 8-byte load, widened to FP32 (a BF16 value is the upper half of a float)
+__device__ __forceinline__ void ld4(const __nv_bfloat16 *p, float (&o)[4]) {
+  const uint2 v = *reinterpret_cast<const uint2 *>(p);
+  o[0] = __uint_as_float(v.x << 16);
+  o[1] = __uint_as_float(v.x & 0xffff0000u);
+  o[2] = __uint_as_float(v.y << 16);
+  o[3] = __uint_as_float(v.y & 0xffff0000u);
+}
+
+// one factor value in the arithmetic type T
+template <typename T>
+__device__ __forceinline__ T ldv(const T *p) { return *p; }
+template <typename T>
+__device__ __forceinline__ T ldv(const __nv_bfloat16 *p) { return (T)__bfloat162float(*p); }
 
 // Dot products of kRows padded rows (pointers rp, lengths in quads nq) with
 // the zero-padded shared vector xs by one warp; every row's loads are issued
 // before the FMAs.
-template <typename T>
-__device__ __forceinline__ void warp_rows_dot4(const T *const (&rp)[kRows], const int (&nq)[kRows],
+template <typename T, typename TV = T>
+__device__ __forceinline__ void warp_rows_dot4(const TV *const (&rp)[kRows], const int (&nq)[kRows],
                                                const T *xs, T (&acc)[kRows]) {
   const int lane = threadIdx.x & 31;
   int maxq = 0;
@@ -88,9 +105,9 @@ __device__ __forceinline__ void warp_rows_dot4(const T *const (&rp)[kRows], cons
 // G x_I of the interior.  A CTA handles rows [a, b) of one cell's stacked
 // [V; G]; x_I is only read here (the forward values go to the separate vector
 // xI, which the backward cell step reads), so a cell may be split over CTAs.
-template <typename T, int NT>
+template <typename T, int NT, typename TV = T>
 __device__ __forceinline__ void cell_fwd_unit(const CellItem &it, const CellDesc *__restrict__ cells,
-                                              const int *__restrict__ idx, const T *__restrict__ vals,
+                                              const int *__restrict__ idx, const TV *__restrict__ vals,
                                               T *__restrict__ contrib, T *__restrict__ xI,
                                               const T *__restrict__ x, T *xs) {
   const CellDesc c = cells[it.cell];
@@ -100,11 +117,11 @@ __device__ __forceinline__ void cell_fwd_unit(const CellItem &it, const CellDesc
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int NW = NT / 32;
-  const T *V = vals + c.V_off;
-  const T *G = vals + c.G_off;
+  const TV *V = vals + c.V_off;
+  const TV *G = vals + c.G_off;
   const int vq = nIp / 4;
   for (int r0 = it.a + warp * kRows; r0 < it.b; r0 += NW * kRows) {
-    const T *rp[kRows];
+    const TV *rp[kRows];
     int nq[kRows];
 #pragma unroll
     for (int u = 0; u < kRows; ++u) {
@@ -122,7 +139,7 @@ __device__ __forceinline__ void cell_fwd_unit(const CellItem &it, const CellDesc
       }
     }
     T acc[kRows];
-    warp_rows_dot4<T>(rp, nq, xs, acc);
+    warp_rows_dot4<T, TV>(rp, nq, xs, acc);
     if (lane == 0) {
 #pragma unroll
       for (int u = 0; u < kRows; ++u) {
@@ -135,25 +152,25 @@ __device__ __forceinline__ void cell_fwd_unit(const CellItem &it, const CellDesc
   }
 }
 
-template <typename T>
+template <typename T, typename TV = T>
 __global__ void __launch_bounds__(kCellFwdThreads) k_cell_fwd(const CellItem *__restrict__ items,
                                                               const CellDesc *__restrict__ cells,
                                                               const int *__restrict__ idx,
-                                                              const T *__restrict__ vals,
+                                                              const TV *__restrict__ vals,
                                                               T *__restrict__ contrib,
                                                               T *__restrict__ xI,
                                                               const T *__restrict__ x) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cell_fwd_unit<T, kCellFwdThreads>(items[blockIdx.x], cells, idx, vals, contrib, xI, x,
+  cell_fwd_unit<T, kCellFwdThreads, TV>(items[blockIdx.x], cells, idx, vals, contrib, xI, x,
                                     reinterpret_cast<T *>(smem_raw));
 }
 
 // Forward group step (K^T C^T): x_g <- H (x_g - sum of the cells' contributions).
-template <typename T, int NT>
+template <typename T, int NT, typename TV = T>
 __device__ __forceinline__ void group_fwd_unit(const GroupDesc &g, const int *__restrict__ idx,
                                                const long long *__restrict__ cptr,
                                                const long long *__restrict__ cslot,
-                                               const T *__restrict__ vals,
+                                               const TV *__restrict__ vals,
                                                const T *__restrict__ contrib, T *__restrict__ x,
                                                T *xs) {
   const int *gi = idx + g.idx_off;
@@ -170,9 +187,9 @@ __device__ __forceinline__ void group_fwd_unit(const GroupDesc &g, const int *__
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int NW = NT / 32;
-  const T *H = vals + g.H_off;
+  const TV *H = vals + g.H_off;
   for (int r0 = warp * kRows; r0 < g.n; r0 += NW * kRows) {
-    const T *rp[kRows];
+    const TV *rp[kRows];
     int nq[kRows];
 #pragma unroll
     for (int u = 0; u < kRows; ++u) {
@@ -181,7 +198,7 @@ __device__ __forceinline__ void group_fwd_unit(const GroupDesc &g, const int *__
       nq[u] = r < g.n ? np / 4 : 0;
     }
     T acc[kRows];
-    warp_rows_dot4<T>(rp, nq, xs, acc);
+    warp_rows_dot4<T, TV>(rp, nq, xs, acc);
     if (lane == 0) {
 #pragma unroll
       for (int u = 0; u < kRows; ++u)
@@ -195,11 +212,11 @@ __device__ __forceinline__ void group_fwd_unit(const GroupDesc &g, const int *__
 constexpr int kSmallWarps = 8;
 
 // one warp: entity g with n <= 32; xs is the warp's 32-element buffer
-template <typename T>
+template <typename T, typename TV = T>
 __device__ __forceinline__ void group_fwd_small_warp(const GroupDesc &g, const int *__restrict__ idx,
                                                      const long long *__restrict__ cptr,
                                                      const long long *__restrict__ cslot,
-                                                     const T *__restrict__ vals,
+                                                     const TV *__restrict__ vals,
                                                      const T *__restrict__ contrib,
                                                      T *__restrict__ x, T *xs) {
   const int lane = threadIdx.x & 31;
@@ -214,7 +231,7 @@ __device__ __forceinline__ void group_fwd_small_warp(const GroupDesc &g, const i
   __syncwarp();
   if (lane < g.n) {
     const int np = (int)pad4(g.n);
-    const T *row = vals + g.H_off + (long long)lane * np;
+    const TV *row = vals + g.H_off + (long long)lane * np;
     T acc = T(0);
     for (int q = 0; q < np / 4; ++q) {
       T w[4];
@@ -226,9 +243,9 @@ __device__ __forceinline__ void group_fwd_small_warp(const GroupDesc &g, const i
   __syncwarp();
 }
 
-template <typename T>
+template <typename T, typename TV = T>
 __device__ __forceinline__ void group_bwd_small_warp(const GroupDesc &g, const int *__restrict__ idx,
-                                                     const T *__restrict__ vals, T *__restrict__ x,
+                                                     const TV *__restrict__ vals, T *__restrict__ x,
                                                      T *xs) {
   const int lane = threadIdx.x & 31;
   const int *gi = idx + g.idx_off;
@@ -236,9 +253,9 @@ __device__ __forceinline__ void group_bwd_small_warp(const GroupDesc &g, const i
   __syncwarp();
   if (lane < g.n) {
     const long long np = pad4(g.n);
-    const T *H = vals + g.H_off;
+    const TV *H = vals + g.H_off;
     T acc = T(0);
-    for (int r = 0; r < g.n; ++r) acc += H[(long long)r * np + lane] * xs[r];
+    for (int r = 0; r < g.n; ++r) acc += ldv<T>(H + (long long)r * np + lane) * xs[r];
     x[gi[lane]] = acc;
   }
   __syncwarp();
@@ -256,14 +273,14 @@ __device__ __forceinline__ void col_layout(int ncols, int nthreads, int &CW, int
 }
 
 // Backward group step: x_g <- H^T x_g.  xs holds n + NT elements.
-template <typename T, int NT>
+template <typename T, int NT, typename TV = T>
 __device__ __forceinline__ void group_bwd_unit(const GroupDesc &g, const int *__restrict__ idx,
-                                               const T *__restrict__ vals, T *__restrict__ x, T *xs) {
+                                               const TV *__restrict__ vals, T *__restrict__ x, T *xs) {
   T *part = xs + g.n;
   const int *gi = idx + g.idx_off;
   for (int i = threadIdx.x; i < g.n; i += NT) xs[i] = x[gi[i]];
   __syncthreads();
-  const T *H = vals + g.H_off;
+  const TV *H = vals + g.H_off;
   const long long np = pad4(g.n);
   int CW, RG;
   col_layout(g.n, NT, CW, RG);
@@ -273,7 +290,7 @@ __device__ __forceinline__ void group_bwd_unit(const GroupDesc &g, const int *__
     T acc = T(0);
     if (rg < RG && col < g.n) {
 #pragma unroll 4
-      for (int i = rg; i < g.n; i += RG) acc += H[(long long)i * np + col] * xs[i];
+      for (int i = rg; i < g.n; i += RG) acc += ldv<T>(H + (long long)i * np + col) * xs[i];
     }
     part[threadIdx.x] = acc;
     __syncthreads();
@@ -290,39 +307,40 @@ __device__ __forceinline__ void group_bwd_unit(const GroupDesc &g, const int *__
 // One launch per level and direction for all separator entities: CTA u <
 // nlarge takes large entity u with all its threads; every further CTA takes
 // kSmallWarps entities of at most 32 DOFs, one per warp.
-template <typename T>
+template <typename T, typename TV = T>
 __global__ void __launch_bounds__(kSmallWarps * 32) k_group_fwd_level(
     const int *__restrict__ large, int nlarge, const int *__restrict__ small, int nsmall,
     const GroupDesc *__restrict__ groups, const int *__restrict__ idx,
     const long long *__restrict__ cptr, const long long *__restrict__ cslot,
-    const T *__restrict__ vals, const T *__restrict__ contrib, T *__restrict__ x) {
+    const TV *__restrict__ vals, const T *__restrict__ contrib, T *__restrict__ x) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *sm = reinterpret_cast<T *>(smem_raw);
   const int u = blockIdx.x;
   if (u < nlarge) {
-    group_fwd_unit<T, kSmallWarps * 32>(groups[large[u]], idx, cptr, cslot, vals, contrib, x, sm);
+    group_fwd_unit<T, kSmallWarps * 32, TV>(groups[large[u]], idx, cptr, cslot, vals, contrib, x, sm);
     return;
   }
   const int warp = threadIdx.x >> 5;
   const int t = (u - nlarge) * kSmallWarps + warp;
-  if (t < nsmall) group_fwd_small_warp<T>(groups[small[t]], idx, cptr, cslot, vals, contrib, x, sm + 32 * warp);
+  if (t < nsmall)
+    group_fwd_small_warp<T, TV>(groups[small[t]], idx, cptr, cslot, vals, contrib, x, sm + 32 * warp);
 }
 
-template <typename T>
+template <typename T, typename TV = T>
 __global__ void __launch_bounds__(kSmallWarps * 32) k_group_bwd_level(
     const int *__restrict__ large, int nlarge, const int *__restrict__ small, int nsmall,
-    const GroupDesc *__restrict__ groups, const int *__restrict__ idx, const T *__restrict__ vals,
+    const GroupDesc *__restrict__ groups, const int *__restrict__ idx, const TV *__restrict__ vals,
     T *__restrict__ x) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *sm = reinterpret_cast<T *>(smem_raw);
   const int u = blockIdx.x;
   if (u < nlarge) {
-    group_bwd_unit<T, kSmallWarps * 32>(groups[large[u]], idx, vals, x, sm);
+    group_bwd_unit<T, kSmallWarps * 32, TV>(groups[large[u]], idx, vals, x, sm);
     return;
   }
   const int warp = threadIdx.x >> 5;
   const int t = (u - nlarge) * kSmallWarps + warp;
-  if (t < nsmall) group_bwd_small_warp<T>(groups[small[t]], idx, vals, x, sm + 32 * warp);
+  if (t < nsmall) group_bwd_small_warp<T, TV>(groups[small[t]], idx, vals, x, sm + 32 * warp);
 }
 
 // Backward cell step (E_I): x_I <- G^T xI_I - V^T x_B, for columns [a, b)
@@ -330,9 +348,9 @@ __global__ void __launch_bounds__(kSmallWarps * 32) k_group_bwd_level(
 // (qa, qb) = (first + p, last - p), which balances the triangular row counts,
 // and reads both quads of a row with 16-byte loads; row groups are added in
 // a fixed order.
-template <typename T, int NT>
+template <typename T, int NT, typename TV = T>
 __device__ __forceinline__ void cell_bwd_unit(const CellItem &it, const CellDesc *__restrict__ cells,
-                                              const int *__restrict__ idx, const T *__restrict__ vals,
+                                              const int *__restrict__ idx, const TV *__restrict__ vals,
                                               const T *__restrict__ xI, T *__restrict__ x, T *smem) {
   const CellDesc c = cells[it.cell];
   T *part = smem;  // 8 * NT
@@ -343,8 +361,8 @@ __device__ __forceinline__ void cell_bwd_unit(const CellItem &it, const CellDesc
   for (int i = threadIdx.x; i < c.nI; i += NT) xs[i] = xI[I[i]];
   for (int q = threadIdx.x; q < c.nB; q += NT) xb[q] = x[B[q]];
   __syncthreads();
-  const T *G = vals + c.G_off;
-  const T *V = vals + c.V_off;
+  const TV *G = vals + c.G_off;
+  const TV *V = vals + c.V_off;
   const long long vstride = pad4(c.nI);
   const int q0 = it.a / 4, q1 = (it.b + 3) / 4;  // column quads [q0, q1)
   const int npairs = (q1 - q0 + 1) / 2;
@@ -364,7 +382,7 @@ __device__ __forceinline__ void cell_bwd_unit(const CellItem &it, const CellDesc
       const int i0 = ia + ((rg - ia % RG) % RG + RG) % RG;
 #pragma unroll 2
       for (int i = i0; i < c.nI; i += RG) {
-        const T *row = G + tri_off(i);
+        const TV *row = G + tri_off(i);
         const T xv = xs[i];
         T v[4];
         ld4(row + 4 * qa, v);
@@ -377,7 +395,7 @@ __device__ __forceinline__ void cell_bwd_unit(const CellItem &it, const CellDesc
       }
 #pragma unroll 2
       for (int q = rg; q < c.nB; q += RG) {
-        const T *row = V + (long long)q * vstride;
+        const TV *row = V + (long long)q * vstride;
         const T xv = xb[q];
         T v[4];
         ld4(row + 4 * qa, v);
@@ -410,15 +428,15 @@ __device__ __forceinline__ void cell_bwd_unit(const CellItem &it, const CellDesc
   }
 }
 
-template <typename T>
+template <typename T, typename TV = T>
 __global__ void __launch_bounds__(kCellBwdThreads) k_cell_bwd(const CellItem *__restrict__ items,
                                                               const CellDesc *__restrict__ cells,
                                                               const int *__restrict__ idx,
-                                                              const T *__restrict__ vals,
+                                                              const TV *__restrict__ vals,
                                                               const T *__restrict__ xI,
                                                               T *__restrict__ x) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cell_bwd_unit<T, kCellBwdThreads>(items[blockIdx.x], cells, idx, vals, xI, x,
+  cell_bwd_unit<T, kCellBwdThreads, TV>(items[blockIdx.x], cells, idx, vals, xI, x,
                                     reinterpret_cast<T *>(smem_raw));
 }
 
@@ -850,9 +868,9 @@ __global__ void __launch_bounds__(kTmaThreads) k_cell_bwd_tma_S(const CellDesc *
 }
 
 // Root (Eq. 3_4): x_r <- G_r^T (G_r x_r).
-template <typename T>
+template <typename T, typename TV = T>
 __global__ void __launch_bounds__(kRootThreads) k_root(int nr, const int *__restrict__ ridx,
-                                                       const T *__restrict__ G,
+                                                       const TV *__restrict__ G,
                                                        T *__restrict__ x) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nrp = (int)pad4(nr);
@@ -864,7 +882,7 @@ __global__ void __launch_bounds__(kRootThreads) k_root(int nr, const int *__rest
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int NW = kRootThreads / 32;
   for (int r0 = warp * kRows; r0 < nr; r0 += NW * kRows) {  // t = G x
-    const T *rp[kRows];
+    const TV *rp[kRows];
     int nq[kRows];
 #pragma unroll
     for (int u = 0; u < kRows; ++u) {
@@ -873,7 +891,7 @@ __global__ void __launch_bounds__(kRootThreads) k_root(int nr, const int *__rest
       nq[u] = r < nr ? (r + 4) / 4 : 0;
     }
     T acc[kRows];
-    warp_rows_dot4<T>(rp, nq, xs, acc);
+    warp_rows_dot4<T, TV>(rp, nq, xs, acc);
     if (lane == 0) {
 #pragma unroll
       for (int u = 0; u < kRows; ++u)
@@ -889,7 +907,7 @@ __global__ void __launch_bounds__(kRootThreads) k_root(int nr, const int *__rest
     T acc = T(0);
     if (rg < RG && col < nr) {
       const int i0 = col + ((rg - col % RG) % RG + RG) % RG;
-      for (int i = i0; i < nr; i += RG) acc += G[tri_off(i) + col] * ts[i];
+      for (int i = i0; i < nr; i += RG) acc += ldv<T>(G + tri_off(i) + col) * ts[i];
     }
     part[threadIdx.x] = acc;
     __syncthreads();
@@ -924,9 +942,9 @@ __device__ __forceinline__ void cluster_barrier() {
 }
 
 // root phase 1: t[r] = G_r[r, :] x_r for the rows of unit u
-template <typename T, int NT>
+template <typename T, int NT, typename TV = T>
 __device__ __forceinline__ void root_rows_unit(int u, int nr, const int *__restrict__ ridx,
-                                               const T *__restrict__ G, const T *__restrict__ x,
+                                               const TV *__restrict__ G, const T *__restrict__ x,
                                                T *__restrict__ t, T *xs) {
   const int nrp = (int)pad4(nr);
   const int r_lo = u * kRootBlock, r_hi = min(nr, r_lo + kRootBlock);
@@ -936,7 +954,7 @@ __device__ __forceinline__ void root_rows_unit(int u, int nr, const int *__restr
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int NW = NT / 32;
   for (int r0 = r_lo + warp * kRows; r0 < r_hi; r0 += NW * kRows) {
-    const T *rp[kRows];
+    const TV *rp[kRows];
     int nq[kRows];
 #pragma unroll
     for (int k = 0; k < kRows; ++k) {
@@ -945,7 +963,7 @@ __device__ __forceinline__ void root_rows_unit(int u, int nr, const int *__restr
       nq[k] = r < r_hi ? (r + 4) / 4 : 0;
     }
     T acc[kRows];
-    warp_rows_dot4<T>(rp, nq, xs, acc);
+    warp_rows_dot4<T, TV>(rp, nq, xs, acc);
     if (lane == 0) {
 #pragma unroll
       for (int k = 0; k < kRows; ++k)
@@ -955,9 +973,9 @@ __device__ __forceinline__ void root_rows_unit(int u, int nr, const int *__restr
 }
 
 // root phase 2: x_r[col] = sum_{i >= col} G_r[i][col] t[i] for the columns of unit u
-template <typename T, int NT>
+template <typename T, int NT, typename TV = T>
 __device__ __forceinline__ void root_cols_unit(int u, int nr, const int *__restrict__ ridx,
-                                               const T *__restrict__ G, const T *__restrict__ t,
+                                               const TV *__restrict__ G, const T *__restrict__ t,
                                                T *__restrict__ x, T *smem) {
   T *part = smem;        // NT
   T *ts = smem + NT;     // t[c_lo .. nr)
@@ -970,7 +988,7 @@ __device__ __forceinline__ void root_cols_unit(int u, int nr, const int *__restr
   T acc = T(0);
   if (col < c_hi) {
     const int i0 = col + ((rg - col % RG) % RG + RG) % RG;
-    for (int i = i0; i < nr; i += RG) acc += G[tri_off(i) + col] * ts[i - c_lo];
+    for (int i = i0; i < nr; i += RG) acc += ldv<T>(G + tri_off(i) + col) * ts[i - c_lo];
   }
   part[threadIdx.x] = acc;
   __syncthreads();
@@ -981,13 +999,13 @@ __device__ __forceinline__ void root_cols_unit(int u, int nr, const int *__restr
   }
 }
 
-template <typename T>
+template <typename T, typename TV = T>
 __global__ void __launch_bounds__(kUpperThreads) k_upper_sweep(
     const UpperPhase *__restrict__ phases, int nphase, const UpperLevel *__restrict__ levels,
     const int *__restrict__ idx, const long long *__restrict__ cptr,
-    const long long *__restrict__ cslot, const T *__restrict__ vals, T *__restrict__ contrib,
+    const long long *__restrict__ cslot, const TV *__restrict__ vals, T *__restrict__ contrib,
     T *__restrict__ xI, T *__restrict__ x, int nr, const int *__restrict__ ridx,
-    const T *__restrict__ Gr, T *__restrict__ rt) {
+    const TV *__restrict__ Gr, T *__restrict__ rt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *sm = reinterpret_cast<T *>(smem_raw);
   constexpr int NT = kUpperThreads;
@@ -999,34 +1017,34 @@ __global__ void __launch_bounds__(kUpperThreads) k_upper_sweep(
     for (int u = blockIdx.x; u < P.units; u += gridDim.x) {
       switch (P.type) {
         case kPhaseCellFwd:
-          cell_fwd_unit<T, NT>(L.fwd[u], L.cells, idx, vals, contrib, xI, x, sm);
+          cell_fwd_unit<T, NT, TV>(L.fwd[u], L.cells, idx, vals, contrib, xI, x, sm);
           break;
         case kPhaseGroupFwd:
           if (u < L.nlarge) {
-            group_fwd_unit<T, NT>(L.groups[L.large[u]], idx, cptr, cslot, vals, contrib, x, sm);
+            group_fwd_unit<T, NT, TV>(L.groups[L.large[u]], idx, cptr, cslot, vals, contrib, x, sm);
           } else {
             const int t = (u - L.nlarge) * NW + warp;
             if (t < L.nsmall)
-              group_fwd_small_warp<T>(L.groups[L.small[t]], idx, cptr, cslot, vals, contrib, x,
+              group_fwd_small_warp<T, TV>(L.groups[L.small[t]], idx, cptr, cslot, vals, contrib, x,
                                       sm + 32 * warp);
           }
           break;
         case kPhaseRootRows:
-          root_rows_unit<T, NT>(u, nr, ridx, Gr, x, rt, sm);
+          root_rows_unit<T, NT, TV>(u, nr, ridx, Gr, x, rt, sm);
           break;
         case kPhaseRootCols:
-          root_cols_unit<T, NT>(u, nr, ridx, Gr, rt, x, sm);
+          root_cols_unit<T, NT, TV>(u, nr, ridx, Gr, rt, x, sm);
           break;
         case kPhaseGroupBwd:
           if (u < L.nlarge) {
-            group_bwd_unit<T, NT>(L.groups[L.large[u]], idx, vals, x, sm);
+            group_bwd_unit<T, NT, TV>(L.groups[L.large[u]], idx, vals, x, sm);
           } else {
             const int t = (u - L.nlarge) * NW + warp;
-            if (t < L.nsmall) group_bwd_small_warp<T>(L.groups[L.small[t]], idx, vals, x, sm + 32 * warp);
+            if (t < L.nsmall) group_bwd_small_warp<T, TV>(L.groups[L.small[t]], idx, vals, x, sm + 32 * warp);
           }
           break;
         default:  // kPhaseCellBwd
-          cell_bwd_unit<T, NT>(L.bwd[u], L.cells, idx, vals, xI, x, sm);
+          cell_bwd_unit<T, NT, TV>(L.bwd[u], L.cells, idx, vals, xI, x, sm);
           break;
       }
       __syncthreads();  // the unit's shared buffers are reused by the next unit
@@ -1057,6 +1075,13 @@ int set_smem_limits() {
   HIF_CUDA_TRY(cudaFuncSetAttribute(k_group_fwd_level<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   HIF_CUDA_TRY(cudaFuncSetAttribute(k_group_bwd_level<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   HIF_CUDA_TRY(cudaFuncSetAttribute(k_root<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  if constexpr (sizeof(T) == 4) {
+    HIF_CUDA_TRY(cudaFuncSetAttribute(k_cell_fwd<T, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    HIF_CUDA_TRY(cudaFuncSetAttribute(k_cell_bwd<T, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    HIF_CUDA_TRY(cudaFuncSetAttribute(k_group_fwd_level<T, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    HIF_CUDA_TRY(cudaFuncSetAttribute(k_group_bwd_level<T, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    HIF_CUDA_TRY(cudaFuncSetAttribute(k_root<T, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  }
   HIF_CUDA_TRY(cudaFuncSetAttribute(k_cell_fwd_tma_S<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   HIF_CUDA_TRY(cudaFuncSetAttribute(k_cell_bwd_tma_S<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   done = true;
@@ -1106,16 +1131,35 @@ int tma_grid(const void *fn, size_t smem, int ncells) {
   return std::max(1, std::min(ncells, sms * occ));
 }
 
+using bf16 = __nv_bfloat16;
+
+// true when level l of the FP32 apply reads its values from the BF16 pool
+template <typename T>
+bool bf16_level(const Handle *h, int l) {
+  return sizeof(T) == 4 && h->has_bf16 && l >= h->bf16_lb;
+}
+
 // Launches of one level's steps outside the fused sweep.
 template <typename T>
 int launch_cell_fwd(Handle *h, const LevelDev &lv, int l, const FactorValues<T> &fv, T *x,
                     cudaStream_t s) {
   if (!lv.ncells) return HIF_OK;
   const double E = sizeof(T);
-  const bool sf = use_tma(h, lv, sizeof(T));
+  const bool b16 = bf16_level<T>(h, l);
+  const bool sf = !b16 && use_tma(h, lv, sizeof(T));
   StatScope sc(h, "cell_fwd", l,
                sf ? (lv.vals_V + lv.vec_cell_fwd / 2 + lv.contrib) * E + lv.idx_cell_fwd
-                  : (lv.vals_cell + lv.vec_cell_fwd + lv.contrib) * E + lv.idx_cell_fwd, s);
+                  : lv.vals_cell * (b16 ? 2.0 : E) + (lv.vec_cell_fwd + lv.contrib) * E + lv.idx_cell_fwd,
+               s);
+  if constexpr (sizeof(T) == 4) {
+    if (b16) {
+      size_t sm = (size_t)pad4(lv.max_nI) * sizeof(T);
+      k_cell_fwd<T, bf16><<<lv.nfwd, kCellFwdThreads, sm, s>>>(lv.fwd, lv.cells, h->idx,
+                                                                static_cast<const bf16 *>(h->bf16_vals),
+                                                                fv.contrib, fv.xI, x);
+      return HIF_OK;
+    }
+  }
   if (sf) {
     size_t sm = (size_t)kStages * kStageBytes + 2 * (size_t)pad4(lv.max_nI) * sizeof(T);
     const int grid = tma_grid((const void *)k_cell_fwd_tma_S<T>, sm, lv.ncells);
@@ -1136,9 +1180,20 @@ int launch_group_fwd(Handle *h, const LevelDev &lv, int l, const FactorValues<T>
   if (!lv.ngroups) return HIF_OK;
   const double E = sizeof(T);
   const size_t sm = std::max<size_t>(pad4(lv.max_ng), 32 * kSmallWarps) * sizeof(T);
+  const bool b16 = bf16_level<T>(h, l);
   StatScope sc(h, "group_fwd", l,
-               (lv.vals_group + lv.vec_group + lv.contrib) * E + lv.idx_group + lv.cslot_bytes, s);
+               lv.vals_group * (b16 ? 2.0 : E) + (lv.vec_group + lv.contrib) * E + lv.idx_group +
+                   lv.cslot_bytes,
+               s);
   const int grid = lv.nlarge + (lv.nsmall + kSmallWarps - 1) / kSmallWarps;
+  if constexpr (sizeof(T) == 4) {
+    if (b16) {
+      k_group_fwd_level<T, bf16><<<grid, kSmallWarps * 32, sm, s>>>(
+          lv.large_groups, lv.nlarge, lv.small_groups, lv.nsmall, lv.groups, h->idx, h->cptr, h->cslot,
+          static_cast<const bf16 *>(h->bf16_vals), fv.contrib, x);
+      return HIF_OK;
+    }
+  }
   k_group_fwd_level<T><<<grid, kSmallWarps * 32, sm, s>>>(lv.large_groups, lv.nlarge, lv.small_groups,
                                                           lv.nsmall, lv.groups, h->idx, h->cptr,
                                                           h->cslot, fv.vals, fv.contrib, x);
@@ -1151,8 +1206,17 @@ int launch_group_bwd(Handle *h, const LevelDev &lv, int l, const FactorValues<T>
   if (!lv.ngroups) return HIF_OK;
   const double E = sizeof(T);
   const size_t sm = std::max<size_t>((size_t)lv.max_ng + kSmallWarps * 32, 32 * kSmallWarps) * sizeof(T);
-  StatScope sc(h, "group_bwd", l, (lv.vals_group + lv.vec_group) * E + lv.idx_group_bwd, s);
+  const bool b16 = bf16_level<T>(h, l);
+  StatScope sc(h, "group_bwd", l, lv.vals_group * (b16 ? 2.0 : E) + lv.vec_group * E + lv.idx_group_bwd, s);
   const int grid = lv.nlarge + (lv.nsmall + kSmallWarps - 1) / kSmallWarps;
+  if constexpr (sizeof(T) == 4) {
+    if (b16) {
+      k_group_bwd_level<T, bf16><<<grid, kSmallWarps * 32, sm, s>>>(
+          lv.large_groups, lv.nlarge, lv.small_groups, lv.nsmall, lv.groups, h->idx,
+          static_cast<const bf16 *>(h->bf16_vals), x);
+      return HIF_OK;
+    }
+  }
   k_group_bwd_level<T><<<grid, kSmallWarps * 32, sm, s>>>(lv.large_groups, lv.nlarge, lv.small_groups,
                                                           lv.nsmall, lv.groups, h->idx, fv.vals, x);
   return HIF_OK;
@@ -1163,10 +1227,20 @@ int launch_cell_bwd(Handle *h, const LevelDev &lv, int l, const FactorValues<T> 
                     cudaStream_t s) {
   if (!lv.ncells) return HIF_OK;
   const double E = sizeof(T);
-  const bool sf = use_tma(h, lv, sizeof(T));
+  const bool b16 = bf16_level<T>(h, l);
+  const bool sf = !b16 && use_tma(h, lv, sizeof(T));
   StatScope sc(h, "cell_bwd", l,
                sf ? (lv.vals_S + lv.vals_V + lv.vec_cell_bwd) * E + lv.idx_cell_bwd
-                  : (lv.vals_cell + lv.vec_cell_bwd) * E + lv.idx_cell_bwd, s);
+                  : lv.vals_cell * (b16 ? 2.0 : E) + lv.vec_cell_bwd * E + lv.idx_cell_bwd, s);
+  if constexpr (sizeof(T) == 4) {
+    if (b16) {
+      size_t sm = ((size_t)lv.max_nI + lv.max_nB + 8 * kCellBwdThreads) * sizeof(T);
+      k_cell_bwd<T, bf16><<<lv.nbwd, kCellBwdThreads, sm, s>>>(lv.bwd, lv.cells, h->idx,
+                                                                static_cast<const bf16 *>(h->bf16_vals),
+                                                                fv.xI, x);
+      return HIF_OK;
+    }
+  }
   if (sf) {
     size_t sm = (size_t)kStages * kStageBytes + tma_bwd_smem_elems(lv) * sizeof(T);
     const int grid = tma_grid((const void *)k_cell_bwd_tma_S<T>, sm, lv.ncells);
@@ -1186,14 +1260,17 @@ int launch_upper(Handle *h, const FactorValues<T> &fv, T *x, cudaStream_t s) {
   StatScope sc(h, "upper_sweep", h->upper_lb, h->upper_bytes[pi], s);
   int nr = h->root_n;
   const int *ridx = h->idx + h->root_idx_off;
-  const T *Gr = fv.vals + h->root_G_off;
+  const bool b16 = sizeof(T) == 4 && h->has_bf16;  // the fused levels lie above bf16_lb
+  const void *vp = b16 ? h->bf16_vals : (const void *)fv.vals;
+  const size_t ve = b16 ? 2 : sizeof(T);
+  const void *Gr = static_cast<const char *>(vp) + ve * h->root_G_off;
   T *rt = reinterpret_cast<T *>(h->upper_rt);
   const UpperPhase *ph = h->upper_phases;
   int nph = h->upper_nphase;
   const UpperLevel *lvs = h->upper_levels;
   const int *idx = h->idx;
   const long long *cptr = h->cptr, *cslot = h->cslot;
-  const T *vals = fv.vals;
+  const void *vals = vp;
   T *contrib = fv.contrib, *xI = fv.xI;
   void *args[] = {(void *)&ph, (void *)&nph, (void *)&lvs, (void *)&idx, (void *)&cptr,
                   (void *)&cslot, (void *)&vals, (void *)&contrib, (void *)&xI, (void *)&x,
@@ -1210,7 +1287,10 @@ int launch_upper(Handle *h, const FactorValues<T> &fv, T *x, cudaStream_t s) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  HIF_CUDA_TRY(cudaLaunchKernelExC(&cfg, (const void *)k_upper_sweep<T>, args));
+  const void *fn = (const void *)k_upper_sweep<T>;
+  if constexpr (sizeof(T) == 4)
+    if (b16) fn = (const void *)k_upper_sweep<T, __nv_bfloat16>;
+  HIF_CUDA_TRY(cudaLaunchKernelExC(&cfg, fn, args));
   return HIF_OK;
 }
 
@@ -1241,9 +1321,20 @@ int apply_levels(Handle *h, const FactorValues<T> &fv, T *x, cudaStream_t s) {
   } else if (h->root_n > 0) {
     size_t sm = (2 * (size_t)pad4(h->root_n) + kRootThreads) * sizeof(T);
     const double nr = h->root_n, E = sizeof(T);
-    StatScope sc(h, "root", -1, (nr * (nr + 1) / 2 + 2 * nr) * E + 4 * nr, s);
-    k_root<T><<<1, kRootThreads, sm, s>>>(h->root_n, h->idx + h->root_idx_off,
-                                          fv.vals + h->root_G_off, x);
+    const bool b16 = bf16_level<T>(h, h->L);
+    StatScope sc(h, "root", -1, nr * (nr + 1) / 2 * (b16 ? 2.0 : E) + 2 * nr * E + 4 * nr, s);
+    bool done = false;
+    if constexpr (sizeof(T) == 4) {
+      if (b16) {
+        k_root<T, bf16><<<1, kRootThreads, sm, s>>>(h->root_n, h->idx + h->root_idx_off,
+                                                    static_cast<const bf16 *>(h->bf16_vals) + h->root_G_off,
+                                                    x);
+        done = true;
+      }
+    }
+    if (!done)
+      k_root<T><<<1, kRootThreads, sm, s>>>(h->root_n, h->idx + h->root_idx_off,
+                                            fv.vals + h->root_G_off, x);
   }
   for (int l = (fused ? lb : h->L) - 1; l >= 0; --l) {
     HIF_TRY(launch_group_bwd<T>(h, h->lv[l], l, fv, x, s));
@@ -1254,12 +1345,11 @@ int apply_levels(Handle *h, const FactorValues<T> &fv, T *x, cudaStream_t s) {
 }
 
 // Bytes of one level's steps in the G-form (forward and backward), for the
-// fused sweep's accounting.
-double level_bytes_gform(const LevelDev &lv, double E) {
-  return (2 * lv.vals_cell + lv.vec_cell_fwd + lv.vec_cell_bwd + 2 * lv.contrib) * E +
-         lv.idx_cell_fwd + lv.idx_cell_bwd +
-         (2 * lv.vals_group + 2 * lv.vec_group + lv.contrib) * E + lv.idx_group + lv.idx_group_bwd +
-         lv.cslot_bytes;
+// fused sweep's accounting: E per vector element, EV per factor value.
+double level_bytes_gform(const LevelDev &lv, double E, double EV) {
+  return 2 * (lv.vals_cell + lv.vals_group) * EV +
+         (lv.vec_cell_fwd + lv.vec_cell_bwd + 2 * lv.contrib) * E + lv.idx_cell_fwd + lv.idx_cell_bwd +
+         (2 * lv.vec_group + lv.contrib) * E + lv.idx_group + lv.idx_group_bwd + lv.cslot_bytes;
 }
 
 // One cluster of 16 CTAs (8 where 16 cannot be scheduled), fewer when the
@@ -1272,6 +1362,11 @@ int upper_launch_shape(Handle *h, size_t smem, int max_units) {
   const void *fn = (const void *)k_upper_sweep<T>;
   HIF_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   HIF_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  if constexpr (sizeof(T) == 4) {
+    const void *fb = (const void *)k_upper_sweep<T, __nv_bfloat16>;
+    HIF_CUDA_TRY(cudaFuncSetAttribute(fb, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    HIF_CUDA_TRY(cudaFuncSetAttribute(fb, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  }
   int want = 16;
   const char *e = std::getenv("HIFCN_UPPER_CTAS");
   if (e && std::atoi(e) > 0) want = std::min(16, std::atoi(e));
@@ -1320,7 +1415,8 @@ int build_upper_plan(Handle *h) {
   if (fm && std::atof(fm) >= 0.0) fuse_mb = std::atof(fm);
   const double kFuseBytes = fuse_mb * 1024 * 1024;
   int lb = L;
-  while (lb > 0) {
+  const int lb_min = h->has_bf16 ? std::min(L, h->bf16_lb) : 0;  // one value type per fused sweep
+  while (lb > lb_min) {
     const LevelDev &lv = h->lv[lb - 1];
     if ((lv.vals_cell + lv.vals_group) * 4.0 > kFuseBytes) break;
     --lb;
@@ -1368,10 +1464,11 @@ int build_upper_plan(Handle *h) {
   if (h->upper_grid[0] == 0 && h->upper_grid[1] == 0) return HIF_OK;
   for (int pi = 0; pi < 2; ++pi) {
     const double E = pi == 0 ? 8.0 : 4.0;
+    const double EV = (pi == 1 && h->has_bf16) ? 2.0 : E;
     double b = 0;
-    for (int l = lb; l < L; ++l) b += level_bytes_gform(h->lv[l], E);
+    for (int l = lb; l < L; ++l) b += level_bytes_gform(h->lv[l], E, EV);
     const double dnr = nr;
-    b += (dnr * (dnr + 1) + 4 * dnr) * E + 8 * dnr;
+    b += dnr * (dnr + 1) * EV + 4 * dnr * E + 8 * dnr;
     h->upper_bytes[pi] = b;
   }
   HIF_TRY(dev_alloc(h, (void **)&h->upper_phases, ph.size() * sizeof(UpperPhase)));
@@ -1401,7 +1498,7 @@ int apply_inplace_f64_with_scratch(Handle *h, double *contrib, double *x, cudaSt
 
 // S = G^T G of the cells of the levels the FP32 S-form kernels will apply.
 int make_cell_inverses(Handle *h, cudaStream_t s) {
-  if (h->opt.precision != HIF_FP32) return HIF_OK;
+  if (h->opt.precision != HIF_FP32 && h->opt.precision != HIF_FP32_BF16TOP) return HIF_OK;
   for (const LevelDev &lv : h->lv) {
     if (!level_sform(h, lv)) continue;
     k_make_S<<<lv.ncells, 256, 0, s>>>(lv.cells, h->f64.vals);
@@ -1421,11 +1518,24 @@ int apply_inverse(Handle *h, const double *x, double *y, int precision, cudaStre
     HIF_CUDA_TRY(cudaMemcpyAsync(y, x, h->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
     return apply_inplace_f64(h, y, s);
   }
-  if (precision != HIF_FP32 || !h->has_f32) return HIF_EINVAL;
+  if ((precision != HIF_FP32 && precision != HIF_FP32_BF16TOP) || !h->has_f32) return HIF_EINVAL;
   k_to_float<<<h->nblocks_vec, 256, 0, s>>>(x, h->f32.work, h->N);
   note_launch();
   HIF_TRY(apply_inplace_f32(h, h->f32.work, s));
   k_to_double<<<h->nblocks_vec, 256, 0, s>>>(h->f32.work, y, h->N);
+  note_launch();
+  HIF_CUDA_TRY(cudaGetLastError());
+  return HIF_OK;
+}
+
+__global__ void k_to_bf16(const double *__restrict__ a, __nv_bfloat16 *__restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    b[i] = __double2bfloat16(a[i]);
+}
+
+int cast_values_bf16(Handle *h, cudaStream_t s) {
+  k_to_bf16<<<1216, 256, 0, s>>>(h->f64.vals, static_cast<__nv_bfloat16 *>(h->bf16_vals), h->nvals);
   note_launch();
   HIF_CUDA_TRY(cudaGetLastError());
   return HIF_OK;

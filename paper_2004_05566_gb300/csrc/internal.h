@@ -177,6 +177,11 @@ struct hif_handle {
   hifcn::FactorValues<double> f64;
   hifcn::FactorValues<float> f32;
   bool has_f32 = false;
+  // HIF_FP32_BF16TOP: BF16 copy of the value pool (same element offsets); the
+  // levels >= bf16_lb and the root are applied from it in the FP32 apply
+  void *bf16_vals = nullptr;
+  bool has_bf16 = false;
+  int bf16_lb = 1 << 30;
 
   // PCG work space (FP64)
   double *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *g = nullptr;
@@ -227,6 +232,12 @@ struct hif_handle {
 namespace hifcn {
 
 using Handle = ::hif_handle;
+
+// the handle's solves apply the factor in FP32 (HIF_FP32, or HIF_FP32_BF16TOP
+// with the top levels in BF16)
+inline bool reduced_apply(const Handle *h) {
+  return h->has_f32 && (h->opt.precision == HIF_FP32 || h->opt.precision == HIF_FP32_BF16TOP);
+}
 
 // allocation helper: records the pointer for release in ~Handle
 int dev_alloc(Handle *h, void **ptr, size_t bytes);

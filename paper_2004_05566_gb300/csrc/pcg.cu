@@ -502,7 +502,7 @@ int pcg_graph_finish(Handle *h, int slot, int *iters_out) {
 }
 
 int graph_slot(const Handle *h) {
-  const int p = (h->opt.precision == HIF_FP32 && h->has_f32) ? 1 : 0;
+  const int p = reduced_apply(h) ? 1 : 0;
   return p + (h->opt.x0_mode == 1 ? 2 : 0);
 }
 
@@ -607,7 +607,7 @@ int pcg_impl(Handle *h, const double *b, double *x, TZ *z, int *iters_out, doubl
 // warm start (ignored unless x0_mode = 1); the solution goes to x.
 int solve_core(Handle *h, const double *b, const double *x0, double *x, int *iters, double *relres,
                cudaStream_t s) {
-  const bool f32 = h->opt.precision == HIF_FP32 && h->has_f32;
+  const bool f32 = reduced_apply(h);
   const bool warm = h->opt.x0_mode == 1;
   int st = HIF_OK;
   if (h->opt.solver == 1) {  // direct: x = F^{-1} b

@@ -22,7 +22,7 @@ _lib = None
 
 HIF_OK, HIF_EINVAL, HIF_ENOMEM, HIF_ENOTSPD, HIF_ENOCONV, HIF_ETIMEOUT, HIF_ECUDA, HIF_EFORMAT = (
     0, -1, -2, -3, -4, -5, -6, -7)
-HIF_FP64, HIF_FP32 = 0, 1
+HIF_FP64, HIF_FP32, HIF_FP32_BF16TOP = 0, 1, 2
 
 EXPORTED = ("hif_default_options", "hif_setup", "hif_import_factor", "hif_export_factor",
             "hif_apply", "hif_matvec", "pcg_solve", "cn_step", "hif_set_reaction", "hif_query",
@@ -38,7 +38,8 @@ class HifGrid(ctypes.Structure):
 class HifOptions(ctypes.Structure):
     _fields_ = [("eps", c_double), ("precision", c_int), ("skel_edges_3d", c_int),
                 ("cg_tol", c_double), ("cg_maxit", c_int), ("true_res_period", c_int),
-                ("theta", c_double), ("x0_mode", c_int), ("solver", c_int)]
+                ("theta", c_double), ("x0_mode", c_int), ("solver", c_int),
+                ("bf16_top_levels", c_int)]
 
 
 class HifInfo(ctypes.Structure):
