@@ -126,6 +126,11 @@ int cast_values_bf16(Handle *h, cudaStream_t s);
 // Upload descriptors of every level, allocate the contribution scratch and
 // the FP32 copy (values already on the device in h->f64.vals).
 int finish_device_factor(Handle *h, cudaStream_t s) {
+  // thresholds of the split entity and root launches (HIFCN_SPLIT_DOFS and
+  // HIFCN_ROOT_SPLIT_DOFS override them, for tests of the split paths)
+  int split_dofs = kSplitDofs, root_split = kRootSplitDofs;
+  if (const char *e = std::getenv("HIFCN_SPLIT_DOFS")) split_dofs = std::max(1, std::atoi(e));
+  if (const char *e = std::getenv("HIFCN_ROOT_SPLIT_DOFS")) root_split = std::max(1, std::atoi(e));
   h->lv.assign(h->L, LevelDev{});
   h->max_contrib = 1;
   for (int l = 0; l < h->L; ++l) {
@@ -195,6 +200,28 @@ int finish_device_factor(Handle *h, cudaStream_t s) {
         HIF_CUDA_TRY(cudaMemcpyAsync(D.small_groups, sm.data(), sm.size() * sizeof(int), cudaMemcpyHostToDevice, s));
       if (!lg.empty())
         HIF_CUDA_TRY(cudaMemcpyAsync(D.large_groups, lg.data(), lg.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+      if (D.max_ng > split_dofs && !lg.empty()) {
+        std::vector<long long> off(lg.size());
+        std::vector<int2> rb, cb;
+        long long tot = 0;
+        for (size_t t = 0; t < lg.size(); ++t) {
+          const int n = H.groups[lg[t]].n;
+          off[t] = tot;
+          tot += pad4(n);
+          for (int r = 0; r < n; r += kSplitRows) rb.push_back(make_int2((int)t, r));
+          for (int c = 0; c < n; c += kSplitCols) cb.push_back(make_int2((int)t, c));
+        }
+        D.split = 1;
+        D.gs_total = tot;
+        D.nrblk = (int)rb.size();
+        D.ncblk = (int)cb.size();
+        HIF_TRY(dev_alloc(h, (void **)&D.gs_off, off.size() * sizeof(long long)));
+        HIF_TRY(dev_alloc(h, (void **)&D.rblk, rb.size() * sizeof(int2)));
+        HIF_TRY(dev_alloc(h, (void **)&D.cblk, cb.size() * sizeof(int2)));
+        HIF_CUDA_TRY(cudaMemcpyAsync(D.gs_off, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice, s));
+        HIF_CUDA_TRY(cudaMemcpyAsync(D.rblk, rb.data(), rb.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+        HIF_CUDA_TRY(cudaMemcpyAsync(D.cblk, cb.data(), cb.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+      }
     }
     // chunk tables for the bulk-copy staged FP32 kernels: consecutive whole
     // rows of at most kStageBytes; [0] the V rows, [1] the S rows then the V rows
@@ -238,6 +265,11 @@ int finish_device_factor(Handle *h, cudaStream_t s) {
       HIF_CUDA_TRY(cudaMemcpyAsync(D.bwd, bw.data(), bw.size() * sizeof(CellItem), cudaMemcpyHostToDevice, s));
   }
   HIF_TRY(dev_alloc(h, (void **)&h->f64.xI, h->N * sizeof(double)));
+  long long gs_max = 0;
+  for (const LevelDev &D : h->lv) gs_max = std::max(gs_max, D.gs_total);
+  HIF_TRY(dev_alloc(h, (void **)&h->f64.gs, std::max<long long>(gs_max, 1) * sizeof(double)));
+  if (h->root_n > 0) HIF_TRY(dev_alloc(h, &h->upper_rt, h->root_n * sizeof(double)));
+  h->root_split = h->root_n > root_split;
   HIF_TRY(make_cell_inverses(h, s));
   HIF_TRY(dev_alloc(h, (void **)&h->f64.contrib, h->max_contrib * sizeof(double)));
   if (h->opt.precision == HIF_FP32 || h->opt.precision == HIF_FP32_BF16TOP) {
@@ -245,6 +277,7 @@ int finish_device_factor(Handle *h, cudaStream_t s) {
     HIF_TRY(dev_alloc(h, (void **)&h->f32.contrib, h->max_contrib * sizeof(float)));
     HIF_TRY(dev_alloc(h, (void **)&h->f32.work, h->N * sizeof(float)));
     HIF_TRY(dev_alloc(h, (void **)&h->f32.xI, h->N * sizeof(float)));
+    HIF_TRY(dev_alloc(h, (void **)&h->f32.gs, std::max<long long>(gs_max, 1) * sizeof(float)));
     k_cast_f32<<<1216, 256, 0, s>>>(h->f64.vals, h->f32.vals, h->nvals);
     note_launch();
     HIF_CUDA_TRY(cudaGetLastError());
@@ -381,6 +414,7 @@ void release_factor(Handle *h) {
   h->upper_phases = nullptr;
   h->upper_levels = nullptr;
   h->upper_rt = nullptr;
+  h->root_split = false;
   h->upper_grid[0] = h->upper_grid[1] = 0;
   for (auto &r : h->stat_pending) {
     cudaEventDestroy(r.a);

@@ -343,6 +343,118 @@ __global__ void __launch_bounds__(kSmallWarps * 32) k_group_bwd_level(
   if (t < nsmall) group_bwd_small_warp<T, TV>(groups[small[t]], idx, vals, x, sm + 32 * warp);
 }
 
+// ---- large separator entities, split over many CTAs (levels with entities
+// of more than kSplitDofs DOFs).  The entity input x_g (forward: minus the
+// cells' contributions) is first gathered into the scratch gs, so that the
+// row or column blocks of H can update x in place from any CTA.
+
+// grid = (large entities, chunks)
+template <typename T>
+__global__ void __launch_bounds__(256) k_group_gather(const int *__restrict__ large, int nlarge,
+                                                      const GroupDesc *__restrict__ groups,
+                                                      const int *__restrict__ idx,
+                                                      const long long *__restrict__ cptr,
+                                                      const long long *__restrict__ cslot,
+                                                      const T *__restrict__ contrib,
+                                                      const T *__restrict__ x,
+                                                      const long long *__restrict__ gs_off,
+                                                      T *__restrict__ gs) {
+  const GroupDesc g = groups[large[blockIdx.x]];
+  const int *gi = idx + g.idx_off;
+  T *out = gs + gs_off[blockIdx.x];
+  const int np = (int)pad4(g.n);
+  for (int i = blockIdx.y * 256 + threadIdx.x; i < np; i += gridDim.y * 256) {
+    T v = T(0);
+    if (i < g.n) {
+      v = x[gi[i]];
+      if (contrib) {
+        const long long a = cptr[g.cptr_off + i], b = cptr[g.cptr_off + i + 1];
+        for (long long s = a; s < b; ++s) v -= contrib[cslot[s]];
+      }
+    }
+    out[i] = v;
+  }
+}
+
+// forward, rows [r0, r0 + kSplitRows) of one entity: x_g[r] = H[r, :] gs_g
+template <typename T, typename TV = T>
+__global__ void __launch_bounds__(256) k_group_rows_split(const int2 *__restrict__ rblk,
+                                                          const int *__restrict__ large,
+                                                          const GroupDesc *__restrict__ groups,
+                                                          const int *__restrict__ idx,
+                                                          const TV *__restrict__ vals,
+                                                          const long long *__restrict__ gs_off,
+                                                          const T *__restrict__ gs,
+                                                          T *__restrict__ x) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *xs = reinterpret_cast<T *>(smem_raw);
+  const int2 rb = rblk[blockIdx.x];
+  const GroupDesc g = groups[large[rb.x]];
+  const int np = (int)pad4(g.n);
+  const T *in = gs + gs_off[rb.x];
+  for (int i = threadIdx.x; i < np; i += 256) xs[i] = in[i];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int *gi = idx + g.idx_off;
+  const TV *H = vals + g.H_off;
+  const int r_hi = min(g.n, rb.y + kSplitRows);
+  for (int r0 = rb.y + warp * kRows; r0 < r_hi; r0 += 8 * kRows) {
+    const TV *rp[kRows];
+    int nq[kRows];
+#pragma unroll
+    for (int u = 0; u < kRows; ++u) {
+      const int r = r0 + u;
+      rp[u] = H + (long long)(r < r_hi ? r : rb.y) * np;
+      nq[u] = r < r_hi ? np / 4 : 0;
+    }
+    T acc[kRows];
+    warp_rows_dot4<T, TV>(rp, nq, xs, acc);
+    if (lane == 0) {
+#pragma unroll
+      for (int u = 0; u < kRows; ++u)
+        if (r0 + u < r_hi) x[gi[r0 + u]] = acc[u];
+    }
+  }
+}
+
+// backward, columns [c0, c0 + kSplitCols) of one entity: x_g[c] = sum_i H[i][c] gs_g[i]
+template <typename T, typename TV = T>
+__global__ void __launch_bounds__(256) k_group_cols_split(const int2 *__restrict__ cblk,
+                                                          const int *__restrict__ large,
+                                                          const GroupDesc *__restrict__ groups,
+                                                          const int *__restrict__ idx,
+                                                          const TV *__restrict__ vals,
+                                                          const long long *__restrict__ gs_off,
+                                                          const T *__restrict__ gs,
+                                                          T *__restrict__ x) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *xs = reinterpret_cast<T *>(smem_raw);
+  const int2 cb = cblk[blockIdx.x];
+  const GroupDesc g = groups[large[cb.x]];
+  const int n = g.n;
+  const long long np = pad4(n);
+  T *part = xs + np;  // 256 partial sums
+  const T *in = gs + gs_off[cb.x];
+  for (int i = threadIdx.x; i < n; i += 256) xs[i] = in[i];
+  __syncthreads();
+  constexpr int CW = kSplitCols, RG = 256 / kSplitCols;
+  const int cl = threadIdx.x % CW, rg = threadIdx.x / CW;
+  const int col = cb.y + cl;
+  const TV *H = vals + g.H_off;
+  T acc = T(0);
+  if (col < n) {
+#pragma unroll 4
+    for (int i = rg; i < n; i += RG) acc += ldv<T>(H + (long long)i * np + col) * xs[i];
+  }
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  if (rg == 0 && col < n) {
+    T sum = part[cl];
+    for (int q = 1; q < RG; ++q) sum += part[q * CW + cl];
+    x[idx[g.idx_off + col]] = sum;
+  }
+}
+
 // Backward cell step (E_I): x_I <- G^T xI_I - V^T x_B, for columns [a, b)
 // (a a multiple of 4) of one cell.  A thread owns the column quad pair
 // (qa, qb) = (first + p, last - p), which balances the triangular row counts,
@@ -452,7 +564,7 @@ __global__ void __launch_bounds__(kCellBwdThreads) k_cell_bwd(const CellItem *__
 // second mbarrier.  Every mbarrier wait is bounded: on expiry the kernel
 // records the failure in err and returns.
 
-constexpr int kStages = 4;
+constexpr int kStages = 2;
 constexpr int kConsumerWarps = 8;
 constexpr int kConsumers = kConsumerWarps * 32;
 constexpr int kTmaThreads = kConsumers + 64;  // + one copy warp + one gather warp
@@ -508,33 +620,43 @@ __device__ __forceinline__ long long cell_row_off(int r, int nI, long long vs) {
   return r < nI ? tri_off(r) : tri_off(nI) + (long long)(r - nI) * vs;
 }
 
+// Per-cell data the gather warp hands to the copy warp and the consumers
+// (double buffered): the descriptor and the chunk bounds (row numbers).
+constexpr int kMaxChunks = 64;
+struct CellMeta {
+  CellDesc c;
+  int nch;
+  int cs[kMaxChunks + 1];
+};
+
 // Copy warp: lane 0 streams, for each cell the CTA owns (cells blockIdx.x,
-// blockIdx.x + gridDim.x, ...), the chunks of the cell's block: its first ntri
-// rows packed-triangular (tri = true: the S rows, then the V rows; tri =
-// false: the V rows only) and dense rows of stride pad4(nI) (chunk j of a cell
-// = rows [cs[j], cs[j+1])).  The chunk's row range goes to meta[stage] before
-// the copy is armed, so the consumers read it from shared memory.  The stage
-// ring runs on across cells: the copies of the next cell are in flight while
-// the consumers finish the current one.
+// blockIdx.x + gridDim.x, ...), the cell's block in chunks of whole rows: its
+// first ntri rows packed-triangular (tri = true: the S rows, then the V rows;
+// tri = false: the V rows only) and dense rows of stride pad4(nI).  The cell
+// descriptor and chunk bounds come from the gather warp (ready barrier); each
+// chunk's row range goes to meta[stage] before the copy is armed.  The stage
+// ring runs on across cells.
 template <typename T>
-__device__ __forceinline__ void produce_cells(const CellDesc *__restrict__ cells, int ncells,
-                                              const int2 *__restrict__ chunk_of,
-                                              const int *__restrict__ chunk_tab,
-                                              const T *__restrict__ vals, bool tri,
-                                              unsigned char *stage, int2 *meta,
-                                              unsigned long long *full, unsigned long long *empty,
-                                              double *err) {
+__device__ __forceinline__ void produce_cells(int ncells, const T *__restrict__ vals, bool tri,
+                                              unsigned char *stage, int2 *meta, const CellMeta *cm,
+                                              unsigned long long *ready, unsigned long long *full,
+                                              unsigned long long *empty, double *err) {
   long long k = 0;  // running chunk counter of this CTA
-  for (int ci = blockIdx.x; ci < ncells; ci += gridDim.x) {
-    const CellDesc c = cells[ci];
-    const int2 co = chunk_of[ci];
-    const int *cs = chunk_tab + co.x;
+  int jc = 0;
+  for (int ci = blockIdx.x; ci < ncells; ci += gridDim.x, ++jc) {
+    const int bb = jc & 1;
+    if (!mbar_wait(&ready[bb], (unsigned)((jc >> 1) & 1))) {
+      err[0] = 1.0;
+      return;
+    }
+    const CellDesc c = cm[bb].c;
+    const int nch = cm[bb].nch;
+    const int *cs = cm[bb].cs;
     const long long vs = pad4(c.nI);
     const T *block = vals + (tri ? c.S_off : c.V_off);
     const int ntri = tri ? c.nI : 0;
-    int rb = co.y > 0 ? cs[0] : 0;
-    for (int j = 0; j < co.y; ++j, ++k) {
-      const int re = cs[j + 1];
+    for (int j = 0; j < nch; ++j, ++k) {
+      const int rb = cs[j], re = cs[j + 1];
       const int sidx = (int)(k % kStages);
       if (k >= kStages && !mbar_wait(&empty[sidx], (unsigned)(((k / kStages) - 1) & 1))) {
         err[0] = 1.0;
@@ -544,24 +666,18 @@ __device__ __forceinline__ void produce_cells(const CellDesc *__restrict__ cells
       const long long a = cell_row_off(rb, ntri, vs), b = cell_row_off(re, ntri, vs);
       bulk_load(stage + (size_t)sidx * kStageBytes, block + a, (unsigned)((b - a) * sizeof(T)),
                 &full[sidx]);
-      rb = re;
     }
   }
 }
 
-// Per-cell data the gather warp hands to the consumers (double buffered).
-struct CellMeta {
-  CellDesc c;
-  int nch;
-};
-
 // Gather warp: for each cell of the CTA, into buffer b = (cell count) & 1:
-// the cell descriptor and chunk count, x at the interior DOFs (zero padded to
+// the cell descriptor and chunk bounds, x at the interior DOFs (zero padded to
 // pad4(nI)) and, when xb is given, x at the boundary DOFs; every lane arrives
 // on ready[b].  Before refilling a buffer it waits until the consumers freed it.
 template <typename T>
 __device__ __forceinline__ void gather_cells(const CellDesc *__restrict__ cells, int ncells,
                                              const int2 *__restrict__ chunk_of,
+                                             const int *__restrict__ chunk_tab,
                                              const int *__restrict__ idx, const T *__restrict__ x,
                                              CellMeta *cm, T *xs0, long long xs_stride, T *xb0,
                                              long long xb_stride, unsigned long long *ready,
@@ -575,10 +691,12 @@ __device__ __forceinline__ void gather_cells(const CellDesc *__restrict__ cells,
       return;
     }
     const CellDesc c = cells[ci];
+    const int2 co = chunk_of[ci];
     if (lane == 0) {
       cm[b].c = c;
-      cm[b].nch = chunk_of[ci].y;
+      cm[b].nch = co.y;
     }
+    for (int j = lane; j <= co.y; j += 32) cm[b].cs[j] = chunk_tab[co.x + j];
     const int nIp = (int)pad4(c.nI);
     const int *I = idx + c.I_off;
     T *xs = xs0 + b * xs_stride;
@@ -619,6 +737,29 @@ __global__ void __launch_bounds__(256) k_make_S(const CellDesc *__restrict__ cel
 // x_I <- S x_I - V^T x_B with S = A_II^{-1} = G^T G, which equals
 // G^T (G x_I) - V^T x_B.  S is read once instead of G twice.
 
+// Consumer layout of the S-form kernels.  Row dots (a row of the chunk times
+// x) are split the other way round from the usual warp-per-row form: lane l
+// takes row (first row of the chunk) + l (+32, ...), and warp w the column
+// quads [w*kQuadsPerWarp, (w+1)*kQuadsPerWarp) of every row, so no row needs
+// a cross-lane reduction; each warp leaves one partial per row in shared
+// memory, and the 8 partials of a row are added once per cell, in warp order.
+// Rows have at most 64 quads (nI <= 256), so 8 quads per warp cover them.
+constexpr int kQuadsPerWarp = 8;
+
+// partial dot of `row` (quads [q0, q1)) with the shared vector xs
+template <typename T>
+__device__ __forceinline__ T quad_range_dot(const T *row, const T *xs, int q0, int q1) {
+  T acc = T(0);
+#pragma unroll 4
+  for (int q = q0; q < q1; ++q) {
+    T v[4], xv[4];
+    ld4(row + 4 * q, v);
+    ld4(xs + 4 * q, xv);
+    acc += v[0] * xv[0] + v[1] * xv[1] + v[2] * xv[2] + v[3] * xv[3];
+  }
+  return acc;
+}
+
 // forward: contributions c_B = V x_I, streaming the V rows.  Persistent: a
 // CTA takes cells blockIdx.x, blockIdx.x + gridDim.x, ...; warp 8 copies the
 // V rows, warp 9 gathers x_I of the next cell, warps 0-7 compute.
@@ -632,14 +773,15 @@ __global__ void __launch_bounds__(kTmaThreads) k_cell_fwd_tma_S(const CellDesc *
                                                                 T *__restrict__ contrib,
                                                                 const T *__restrict__ x,
                                                                 double *__restrict__ err,
-                                                                int max_nI) {
+                                                                int max_nI, int max_nB) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) unsigned long long full[kStages], empty[kStages], ready[2], freed[2];
   __shared__ int2 meta[kStages];
   __shared__ CellMeta cm[2];
   unsigned char *stage = smem_raw;
-  const long long xstride = pad4(max_nI);
+  const long long xstride = pad4(max_nI), pstride = pad4(max_nB);
   T *xs0 = reinterpret_cast<T *>(smem_raw + (size_t)kStages * kStageBytes);  // 2 x pad4(max_nI)
+  T *rd = xs0 + 2 * xstride;                                                  // 8 x pad4(max_nB)
   if (threadIdx.x == 0) {
     for (int k = 0; k < kStages; ++k) {
       mbar_init(&full[k], 1);
@@ -655,13 +797,15 @@ __global__ void __launch_bounds__(kTmaThreads) k_cell_fwd_tma_S(const CellDesc *
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == kConsumerWarps) {
     if (lane == 0)
-      produce_cells<T>(cells, ncells, chunk_of, chunk_tab, vals, false, stage, meta, full, empty, err);
+      produce_cells<T>(ncells, vals, false, stage, meta, cm, ready, full, empty, err);
     return;
   }
   if (warp == kConsumerWarps + 1) {
-    gather_cells<T>(cells, ncells, chunk_of, idx, x, cm, xs0, xstride, nullptr, 0, ready, freed, err);
+    gather_cells<T>(cells, ncells, chunk_of, chunk_tab, idx, x, cm, xs0, xstride, nullptr, 0, ready,
+                    freed, err);
     return;
   }
+  const int q0 = warp * kQuadsPerWarp;
   long long k = 0;  // running chunk counter, as in the copy warp
   int jc = 0;
   for (int ci = blockIdx.x; ci < ncells; ci += gridDim.x, ++jc) {
@@ -673,8 +817,10 @@ __global__ void __launch_bounds__(kTmaThreads) k_cell_fwd_tma_S(const CellDesc *
     const CellDesc c = cm[b].c;
     const int nch = cm[b].nch;
     const T *xs = xs0 + b * xstride;
-    const int nIp = (int)pad4(c.nI);
-    const long long vs = nIp;
+    const int nq = (int)pad4(c.nI) / 4;
+    const int q1 = min(nq, q0 + kQuadsPerWarp);
+    const long long vs = 4LL * nq;
+    consumers_sync();  // the previous cell's partials are read
     for (int j = 0; j < nch; ++j, ++k) {
       const int sidx = (int)(k % kStages);
       if (!mbar_wait(&full[sidx], (unsigned)((k / kStages) & 1))) {
@@ -683,52 +829,30 @@ __global__ void __launch_bounds__(kTmaThreads) k_cell_fwd_tma_S(const CellDesc *
       }
       const T *base = reinterpret_cast<const T *>(stage + (size_t)sidx * kStageBytes);
       const int2 rr = meta[sidx];
-      const int rb = rr.x, re = rr.y;
-      for (int r0 = rb + warp * kRows; r0 < re; r0 += kConsumerWarps * kRows) {
-        const T *rp[kRows];
-        int nq[kRows];
-#pragma unroll
-        for (int u = 0; u < kRows; ++u) {
-          const int r = r0 + u;
-          rp[u] = base + (long long)(r < re ? r - rb : 0) * vs;
-          nq[u] = r < re ? nIp / 4 : 0;
-        }
-        T acc[kRows];
-#pragma unroll
-        for (int u = 0; u < kRows; ++u) acc[u] = T(0);
-        for (int q = lane; q < nIp / 4; q += 32) {
-          T xv[4];
-          ld4(xs + 4 * q, xv);
-#pragma unroll
-          for (int u = 0; u < kRows; ++u) {
-            if (q < nq[u]) {
-              T v[4];
-              ld4(rp[u] + 4 * q, v);
-              acc[u] += v[0] * xv[0] + v[1] * xv[1] + v[2] * xv[2] + v[3] * xv[3];
-            }
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < kRows; ++u) acc[u] = warp_reduce(acc[u]);
-        if (lane == 0) {
-#pragma unroll
-          for (int u = 0; u < kRows; ++u)
-            if (r0 + u < re) contrib[c.C_off + r0 + u] = acc[u];
-        }
-      }
+      for (int r = rr.x + lane; r < rr.y; r += 32)
+        rd[warp * pstride + r] = q0 < q1 ? quad_range_dot(base + (long long)(r - rr.x) * vs, xs, q0, q1) : T(0);
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[sidx]);
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&freed[b]);
+    consumers_sync();
+    for (int r = threadIdx.x; r < c.nB; r += kConsumers) {
+      T sum = rd[r];
+#pragma unroll
+      for (int w = 1; w < kConsumerWarps; ++w) sum += rd[w * pstride + r];
+      contrib[c.C_off + r] = sum;
+    }
   }
 }
 
 // backward: x_I <- S x_I - V^T x_B, streaming the S rows then the V rows.
-// Warp w handles the rows r = w (mod 8); lane p owns the column quads
-// (p, nq - 1 - p).  An S row r gives its row dot S[r][.] x (warp reduction)
-// and, below the diagonal, the column products S[r][col] x_r (col < r).
-// Persistent like the forward kernel, with the same copy and gather warps.
+// With S = L + D + L^T stored as its lower triangle by rows: the row dots
+// (L + D) x as in the forward kernel (lane per row, warp per quad range,
+// partials per warp), and the column sums L^T x - V^T x_B by lane-owned
+// column quads (p, nq - 1 - p) over the rows r = w (mod 8) of warp w, with
+// the diagonal masked out; both meet once per cell.  Persistent like the
+// forward kernel, with the same copy and gather warps.
 template <typename T>
 __global__ void __launch_bounds__(kTmaThreads) k_cell_bwd_tma_S(const CellDesc *__restrict__ cells,
                                                                 int ncells,
@@ -746,8 +870,8 @@ __global__ void __launch_bounds__(kTmaThreads) k_cell_bwd_tma_S(const CellDesc *
   unsigned char *stage = smem_raw;
   const long long xstride = pad4(max_nI), bstride = pad4(max_nB);
   T *part = reinterpret_cast<T *>(smem_raw + (size_t)kStages * kStageBytes);  // 8 * kConsumers
-  T *yrow = part + 8 * kConsumers;   // pad4(max_nI)
-  T *xs0 = yrow + xstride;           // 2 x pad4(max_nI)
+  T *rd = part + 8 * kConsumers;     // 8 x pad4(max_nI): row-dot partials
+  T *xs0 = rd + 8 * xstride;         // 2 x pad4(max_nI)
   T *xb0 = xs0 + 2 * xstride;        // 2 x pad4(max_nB)
   if (threadIdx.x == 0) {
     for (int k = 0; k < kStages; ++k) {
@@ -764,13 +888,15 @@ __global__ void __launch_bounds__(kTmaThreads) k_cell_bwd_tma_S(const CellDesc *
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == kConsumerWarps) {
     if (lane == 0)
-      produce_cells<T>(cells, ncells, chunk_of, chunk_tab, vals, true, stage, meta, full, empty, err);
+      produce_cells<T>(ncells, vals, true, stage, meta, cm, ready, full, empty, err);
     return;
   }
   if (warp == kConsumerWarps + 1) {
-    gather_cells<T>(cells, ncells, chunk_of, idx, x, cm, xs0, xstride, xb0, bstride, ready, freed, err);
+    gather_cells<T>(cells, ncells, chunk_of, chunk_tab, idx, x, cm, xs0, xstride, xb0, bstride, ready,
+                    freed, err);
     return;
   }
+  const int q0 = warp * kQuadsPerWarp;
   long long k = 0;  // running chunk counter, as in the copy warp
   int jc = 0;
   for (int ci = blockIdx.x; ci < ncells; ci += gridDim.x, ++jc) {
@@ -785,15 +911,12 @@ __global__ void __launch_bounds__(kTmaThreads) k_cell_bwd_tma_S(const CellDesc *
     const T *xb = xb0 + b * bstride;
     const int nIp = (int)pad4(c.nI);
     const long long vs = nIp;
-    consumers_sync();  // yrow and part of the previous cell are no longer read
+    consumers_sync();  // rd and part of the previous cell are no longer read
     const int nq = nIp / 4;
     const int qa = lane, qb = nq - 1 - lane;  // one warp covers all column pairs (nq <= 64)
     const bool okA = qa < (nq + 1) / 2;
     const bool okB = okA && qb > qa;
     T aA[4] = {T(0), T(0), T(0), T(0)}, aB[4] = {T(0), T(0), T(0), T(0)};
-    T xa[4] = {T(0), T(0), T(0), T(0)}, xbq[4] = {T(0), T(0), T(0), T(0)};
-    if (okA) ld4(xs + 4 * qa, xa);
-    if (okB) ld4(xs + 4 * qb, xbq);
     for (int j = 0; j < nch; ++j, ++k) {
       const int sidx = (int)(k % kStages);
       if (!mbar_wait(&full[sidx], (unsigned)((k / kStages) & 1))) {
@@ -804,28 +927,31 @@ __global__ void __launch_bounds__(kTmaThreads) k_cell_bwd_tma_S(const CellDesc *
       const int2 rr = meta[sidx];
       const int rb = rr.x, re = rr.y;
       const long long off0 = cell_row_off(rb, c.nI, vs);
+      // column sums over the rows r = warp (mod 8)
       for (int r = rb + ((warp - rb % kConsumerWarps) % kConsumerWarps + kConsumerWarps) % kConsumerWarps;
            r < re; r += kConsumerWarps) {
         const T *row = base + (cell_row_off(r, c.nI, vs) - off0);
         if (r < c.nI) {
           const T xr = xs[r];
-          T dot = T(0);
-          if (okA && 4 * qa <= r) {
+          const int qd = r >> 2;  // quad holding the diagonal
+          if (okA && qa <= qd) {
             T v[4];
             ld4(row + 4 * qa, v);
-            dot += v[0] * xa[0] + v[1] * xa[1] + v[2] * xa[2] + v[3] * xa[3];
+            if (qa == qd) {
 #pragma unroll
-            for (int e = 0; e < 4; ++e) aA[e] += (4 * qa + e < r ? v[e] : T(0)) * xr;
+              for (int e = 0; e < 4; ++e) v[e] = (4 * qa + e < r) ? v[e] : T(0);
+            }
+            aA[0] += v[0] * xr; aA[1] += v[1] * xr; aA[2] += v[2] * xr; aA[3] += v[3] * xr;
           }
-          if (okB && 4 * qb <= r) {
+          if (okB && qb <= qd) {
             T w[4];
             ld4(row + 4 * qb, w);
-            dot += w[0] * xbq[0] + w[1] * xbq[1] + w[2] * xbq[2] + w[3] * xbq[3];
+            if (qb == qd) {
 #pragma unroll
-            for (int e = 0; e < 4; ++e) aB[e] += (4 * qb + e < r ? w[e] : T(0)) * xr;
+              for (int e = 0; e < 4; ++e) w[e] = (4 * qb + e < r) ? w[e] : T(0);
+            }
+            aB[0] += w[0] * xr; aB[1] += w[1] * xr; aB[2] += w[2] * xr; aB[3] += w[3] * xr;
           }
-          dot = warp_reduce(dot);
-          if (lane == 0) yrow[r] = dot;
         } else {
           const T xv = xb[r - c.nI];
           if (okA) {
@@ -840,6 +966,13 @@ __global__ void __launch_bounds__(kTmaThreads) k_cell_bwd_tma_S(const CellDesc *
           }
         }
       }
+      // row dots of the S rows of the chunk: lane per row, this warp's quads
+      const int se = min(re, c.nI);
+      for (int r = rb + lane; r < se; r += 32) {
+        const int q1 = min(r / 4 + 1, q0 + kQuadsPerWarp);
+        rd[warp * xstride + r] =
+            q0 < q1 ? quad_range_dot(base + (cell_row_off(r, c.nI, vs) - off0), xs, q0, q1) : T(0);
+      }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[sidx]);
     }
@@ -851,7 +984,7 @@ __global__ void __launch_bounds__(kTmaThreads) k_cell_bwd_tma_S(const CellDesc *
       part[(4 + e) * kConsumers + threadIdx.x] = aB[e];
     }
     consumers_sync();
-    // column sums over the 8 warps plus the row dot of the same index
+    // column sums over the 8 warps plus the row-dot partials of the same index
     if (warp == 0 && okA) {
       const int *I = idx + c.I_off;
 #pragma unroll
@@ -859,7 +992,8 @@ __global__ void __launch_bounds__(kTmaThreads) k_cell_bwd_tma_S(const CellDesc *
         if (e >= 4 && !okB) break;
         const int col = (e < 4 ? 4 * qa : 4 * qb) + (e & 3);
         if (col >= c.nI) continue;
-        T sum = yrow[col];
+        T sum = rd[col];
+        for (int w = 1; w < kConsumerWarps; ++w) sum += rd[w * xstride + col];
         for (int w = 0; w < kConsumerWarps; ++w) sum += part[e * kConsumers + w * 32 + lane];
         x[I[col]] = sum;
       }
@@ -999,6 +1133,24 @@ __device__ __forceinline__ void root_cols_unit(int u, int nr, const int *__restr
   }
 }
 
+// A root above kRootSplitDofs: t = G_r x_r by row blocks, then x_r = G_r^T t
+// by column blocks, each a launch over ceil(n_r / kRootBlock) CTAs.
+template <typename T, typename TV = T>
+__global__ void __launch_bounds__(256) k_root_rows(int nr, const int *__restrict__ ridx,
+                                                   const TV *__restrict__ G, const T *__restrict__ x,
+                                                   T *__restrict__ t) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  root_rows_unit<T, 256, TV>(blockIdx.x, nr, ridx, G, x, t, reinterpret_cast<T *>(smem_raw));
+}
+
+template <typename T, typename TV = T>
+__global__ void __launch_bounds__(256) k_root_cols(int nr, const int *__restrict__ ridx,
+                                                   const TV *__restrict__ G, const T *__restrict__ t,
+                                                   T *__restrict__ x) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  root_cols_unit<T, 256, TV>(blockIdx.x, nr, ridx, G, t, x, reinterpret_cast<T *>(smem_raw));
+}
+
 template <typename T, typename TV = T>
 __global__ void __launch_bounds__(kUpperThreads) k_upper_sweep(
     const UpperPhase *__restrict__ phases, int nphase, const UpperLevel *__restrict__ levels,
@@ -1075,12 +1227,20 @@ int set_smem_limits() {
   HIF_CUDA_TRY(cudaFuncSetAttribute(k_group_fwd_level<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   HIF_CUDA_TRY(cudaFuncSetAttribute(k_group_bwd_level<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   HIF_CUDA_TRY(cudaFuncSetAttribute(k_root<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  HIF_CUDA_TRY(cudaFuncSetAttribute(k_root_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  HIF_CUDA_TRY(cudaFuncSetAttribute(k_root_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  HIF_CUDA_TRY(cudaFuncSetAttribute(k_group_rows_split<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  HIF_CUDA_TRY(cudaFuncSetAttribute(k_group_cols_split<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   if constexpr (sizeof(T) == 4) {
     HIF_CUDA_TRY(cudaFuncSetAttribute(k_cell_fwd<T, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     HIF_CUDA_TRY(cudaFuncSetAttribute(k_cell_bwd<T, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     HIF_CUDA_TRY(cudaFuncSetAttribute(k_group_fwd_level<T, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     HIF_CUDA_TRY(cudaFuncSetAttribute(k_group_bwd_level<T, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     HIF_CUDA_TRY(cudaFuncSetAttribute(k_root<T, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    HIF_CUDA_TRY(cudaFuncSetAttribute(k_root_rows<T, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    HIF_CUDA_TRY(cudaFuncSetAttribute(k_root_cols<T, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    HIF_CUDA_TRY(cudaFuncSetAttribute(k_group_rows_split<T, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    HIF_CUDA_TRY(cudaFuncSetAttribute(k_group_cols_split<T, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   }
   HIF_CUDA_TRY(cudaFuncSetAttribute(k_cell_fwd_tma_S<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   HIF_CUDA_TRY(cudaFuncSetAttribute(k_cell_bwd_tma_S<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
@@ -1094,15 +1254,19 @@ int set_smem_limits() {
 // split over CTAs, whose rows fit one stage and whose column pairs fit one
 // warp (nI <= 256).  FP64 applies are bound by the FP64 pipe, not by HBM, and
 // keep the register-streaming G-form kernels.
-// shared-memory elements of the backward S-form kernel beyond the stages:
-// part (8 per consumer), yrow, two x_I buffers, two x_B buffers
+// shared-memory elements of the S-form kernels beyond the stages: backward:
+// part (8 per consumer), the row-dot partials (8 per row), two x_I and two
+// x_B buffers; forward: two x_I buffers and the row-dot partials
 size_t tma_bwd_smem_elems(const LevelDev &lv) {
-  return (size_t)8 * kConsumers + 3 * (size_t)pad4(lv.max_nI) + 2 * (size_t)pad4(lv.max_nB);
+  return (size_t)8 * kConsumers + 10 * (size_t)pad4(lv.max_nI) + 2 * (size_t)pad4(lv.max_nB);
+}
+size_t tma_fwd_smem_elems(const LevelDev &lv) {
+  return 2 * (size_t)pad4(lv.max_nI) + 8 * (size_t)pad4(lv.max_nB);
 }
 
 bool level_sform(const Handle *h, const LevelDev &lv) {
   if (!h->use_tma || lv.ncells == 0 || lv.nfwd != lv.ncells || lv.nbwd != lv.ncells) return false;
-  if (lv.max_chunks < 0 || pad4(lv.max_nI) > 256) return false;
+  if (lv.max_chunks < 0 || lv.max_chunks > kMaxChunks || pad4(lv.max_nI) > 256) return false;
   const size_t bwd_smem = (size_t)kStages * kStageBytes + tma_bwd_smem_elems(lv) * sizeof(float);
   return bwd_smem <= 200 * 1024;
 }
@@ -1161,11 +1325,11 @@ int launch_cell_fwd(Handle *h, const LevelDev &lv, int l, const FactorValues<T> 
     }
   }
   if (sf) {
-    size_t sm = (size_t)kStages * kStageBytes + 2 * (size_t)pad4(lv.max_nI) * sizeof(T);
+    size_t sm = (size_t)kStages * kStageBytes + tma_fwd_smem_elems(lv) * sizeof(T);
     const int grid = tma_grid((const void *)k_cell_fwd_tma_S<T>, sm, lv.ncells);
-    k_cell_fwd_tma_S<T><<<grid, kTmaThreads, sm, s>>>(lv.cells, lv.ncells, lv.chunk_of[0],
-                                                       lv.chunk_tab[0], h->idx, fv.vals, fv.contrib, x,
-                                                       h->scal + kScalErr, lv.max_nI);
+    k_cell_fwd_tma_S<T><<<grid, kTmaThreads, sm, s>>>(lv.cells, lv.ncells, lv.chunk_of[0], lv.chunk_tab[0],
+                                                       h->idx, fv.vals, fv.contrib, x,
+                                                       h->scal + kScalErr, lv.max_nI, lv.max_nB);
   } else {
     size_t sm = (size_t)pad4(lv.max_nI) * sizeof(T);
     k_cell_fwd<T><<<lv.nfwd, kCellFwdThreads, sm, s>>>(lv.fwd, lv.cells, h->idx, fv.vals, fv.contrib,
@@ -1185,16 +1349,37 @@ int launch_group_fwd(Handle *h, const LevelDev &lv, int l, const FactorValues<T>
                lv.vals_group * (b16 ? 2.0 : E) + (lv.vec_group + lv.contrib) * E + lv.idx_group +
                    lv.cslot_bytes,
                s);
-  const int grid = lv.nlarge + (lv.nsmall + kSmallWarps - 1) / kSmallWarps;
+  if (lv.split) {  // large entities over many CTAs, then the small ones
+    const size_t smx = (size_t)pad4(lv.max_ng) * sizeof(T);
+    k_group_gather<T><<<dim3(lv.nlarge, 4), 256, 0, s>>>(lv.large_groups, lv.nlarge, lv.groups, h->idx,
+                                                         h->cptr, h->cslot, fv.contrib, x, lv.gs_off,
+                                                         fv.gs);
+    bool done = false;
+    if constexpr (sizeof(T) == 4) {
+      if (b16) {
+        k_group_rows_split<T, bf16><<<lv.nrblk, 256, smx, s>>>(lv.rblk, lv.large_groups, lv.groups, h->idx,
+                                                               static_cast<const bf16 *>(h->bf16_vals),
+                                                               lv.gs_off, fv.gs, x);
+        done = true;
+      }
+    }
+    if (!done)
+      k_group_rows_split<T><<<lv.nrblk, 256, smx, s>>>(lv.rblk, lv.large_groups, lv.groups, h->idx, fv.vals,
+                                                       lv.gs_off, fv.gs, x);
+    note_launch(1 + (lv.nsmall ? 1 : 0));
+    if (!lv.nsmall) return HIF_OK;
+  }
+  const int nlg = lv.split ? 0 : lv.nlarge;  // large entities already done when split
+  const int grid = nlg + (lv.nsmall + kSmallWarps - 1) / kSmallWarps;
   if constexpr (sizeof(T) == 4) {
     if (b16) {
       k_group_fwd_level<T, bf16><<<grid, kSmallWarps * 32, sm, s>>>(
-          lv.large_groups, lv.nlarge, lv.small_groups, lv.nsmall, lv.groups, h->idx, h->cptr, h->cslot,
+          lv.large_groups, nlg, lv.small_groups, lv.nsmall, lv.groups, h->idx, h->cptr, h->cslot,
           static_cast<const bf16 *>(h->bf16_vals), fv.contrib, x);
       return HIF_OK;
     }
   }
-  k_group_fwd_level<T><<<grid, kSmallWarps * 32, sm, s>>>(lv.large_groups, lv.nlarge, lv.small_groups,
+  k_group_fwd_level<T><<<grid, kSmallWarps * 32, sm, s>>>(lv.large_groups, nlg, lv.small_groups,
                                                           lv.nsmall, lv.groups, h->idx, h->cptr,
                                                           h->cslot, fv.vals, fv.contrib, x);
   return HIF_OK;
@@ -1208,16 +1393,36 @@ int launch_group_bwd(Handle *h, const LevelDev &lv, int l, const FactorValues<T>
   const size_t sm = std::max<size_t>((size_t)lv.max_ng + kSmallWarps * 32, 32 * kSmallWarps) * sizeof(T);
   const bool b16 = bf16_level<T>(h, l);
   StatScope sc(h, "group_bwd", l, lv.vals_group * (b16 ? 2.0 : E) + lv.vec_group * E + lv.idx_group_bwd, s);
-  const int grid = lv.nlarge + (lv.nsmall + kSmallWarps - 1) / kSmallWarps;
+  if (lv.split) {
+    const size_t smx = ((size_t)pad4(lv.max_ng) + 256) * sizeof(T);
+    k_group_gather<T><<<dim3(lv.nlarge, 4), 256, 0, s>>>(lv.large_groups, lv.nlarge, lv.groups, h->idx,
+                                                         h->cptr, h->cslot, nullptr, x, lv.gs_off, fv.gs);
+    bool done = false;
+    if constexpr (sizeof(T) == 4) {
+      if (b16) {
+        k_group_cols_split<T, bf16><<<lv.ncblk, 256, smx, s>>>(lv.cblk, lv.large_groups, lv.groups, h->idx,
+                                                               static_cast<const bf16 *>(h->bf16_vals),
+                                                               lv.gs_off, fv.gs, x);
+        done = true;
+      }
+    }
+    if (!done)
+      k_group_cols_split<T><<<lv.ncblk, 256, smx, s>>>(lv.cblk, lv.large_groups, lv.groups, h->idx, fv.vals,
+                                                       lv.gs_off, fv.gs, x);
+    note_launch(1 + (lv.nsmall ? 1 : 0));
+    if (!lv.nsmall) return HIF_OK;
+  }
+  const int nlg = lv.split ? 0 : lv.nlarge;
+  const int grid = nlg + (lv.nsmall + kSmallWarps - 1) / kSmallWarps;
   if constexpr (sizeof(T) == 4) {
     if (b16) {
       k_group_bwd_level<T, bf16><<<grid, kSmallWarps * 32, sm, s>>>(
-          lv.large_groups, lv.nlarge, lv.small_groups, lv.nsmall, lv.groups, h->idx,
+          lv.large_groups, nlg, lv.small_groups, lv.nsmall, lv.groups, h->idx,
           static_cast<const bf16 *>(h->bf16_vals), x);
       return HIF_OK;
     }
   }
-  k_group_bwd_level<T><<<grid, kSmallWarps * 32, sm, s>>>(lv.large_groups, lv.nlarge, lv.small_groups,
+  k_group_bwd_level<T><<<grid, kSmallWarps * 32, sm, s>>>(lv.large_groups, nlg, lv.small_groups,
                                                           lv.nsmall, lv.groups, h->idx, fv.vals, x);
   return HIF_OK;
 }
@@ -1244,8 +1449,8 @@ int launch_cell_bwd(Handle *h, const LevelDev &lv, int l, const FactorValues<T> 
   if (sf) {
     size_t sm = (size_t)kStages * kStageBytes + tma_bwd_smem_elems(lv) * sizeof(T);
     const int grid = tma_grid((const void *)k_cell_bwd_tma_S<T>, sm, lv.ncells);
-    k_cell_bwd_tma_S<T><<<grid, kTmaThreads, sm, s>>>(lv.cells, lv.ncells, lv.chunk_of[1],
-                                                       lv.chunk_tab[1], h->idx, fv.vals, x,
+    k_cell_bwd_tma_S<T><<<grid, kTmaThreads, sm, s>>>(lv.cells, lv.ncells, lv.chunk_of[1], lv.chunk_tab[1],
+                                                       h->idx, fv.vals, x,
                                                        h->scal + kScalErr, lv.max_nI, lv.max_nB);
   } else {
     size_t sm = ((size_t)lv.max_nI + lv.max_nB + 8 * kCellBwdThreads) * sizeof(T);
@@ -1319,22 +1524,42 @@ int apply_levels(Handle *h, const FactorValues<T> &fv, T *x, cudaStream_t s) {
   if (fused) {
     HIF_TRY(launch_upper<T>(h, fv, x, s));
   } else if (h->root_n > 0) {
-    size_t sm = (2 * (size_t)pad4(h->root_n) + kRootThreads) * sizeof(T);
     const double nr = h->root_n, E = sizeof(T);
     const bool b16 = bf16_level<T>(h, h->L);
-    StatScope sc(h, "root", -1, nr * (nr + 1) / 2 * (b16 ? 2.0 : E) + 2 * nr * E + 4 * nr, s);
-    bool done = false;
-    if constexpr (sizeof(T) == 4) {
-      if (b16) {
-        k_root<T, bf16><<<1, kRootThreads, sm, s>>>(h->root_n, h->idx + h->root_idx_off,
-                                                    static_cast<const bf16 *>(h->bf16_vals) + h->root_G_off,
-                                                    x);
-        done = true;
+    StatScope sc(h, "root", -1, nr * (nr + 1) * (b16 ? 2.0 : E) + 4 * nr * E + 8 * nr, s);
+    const int *ridx = h->idx + h->root_idx_off;
+    T *rt = reinterpret_cast<T *>(h->upper_rt);
+    if (h->root_split) {  // row blocks, then column blocks, over many CTAs
+      const int units = (h->root_n + kRootBlock - 1) / kRootBlock;
+      const size_t sm1 = (size_t)pad4(h->root_n) * sizeof(T), sm2 = ((size_t)h->root_n + 256) * sizeof(T);
+      bool done = false;
+      if constexpr (sizeof(T) == 4) {
+        if (b16) {
+          const bf16 *G = static_cast<const bf16 *>(h->bf16_vals) + h->root_G_off;
+          k_root_rows<T, bf16><<<units, 256, sm1, s>>>(h->root_n, ridx, G, x, rt);
+          k_root_cols<T, bf16><<<units, 256, sm2, s>>>(h->root_n, ridx, G, rt, x);
+          done = true;
+        }
       }
+      if (!done) {
+        const T *G = fv.vals + h->root_G_off;
+        k_root_rows<T><<<units, 256, sm1, s>>>(h->root_n, ridx, G, x, rt);
+        k_root_cols<T><<<units, 256, sm2, s>>>(h->root_n, ridx, G, rt, x);
+      }
+      note_launch();
+    } else {
+      size_t sm = (2 * (size_t)pad4(h->root_n) + kRootThreads) * sizeof(T);
+      bool done = false;
+      if constexpr (sizeof(T) == 4) {
+        if (b16) {
+          k_root<T, bf16><<<1, kRootThreads, sm, s>>>(h->root_n, ridx,
+                                                      static_cast<const bf16 *>(h->bf16_vals) + h->root_G_off,
+                                                      x);
+          done = true;
+        }
+      }
+      if (!done) k_root<T><<<1, kRootThreads, sm, s>>>(h->root_n, ridx, fv.vals + h->root_G_off, x);
     }
-    if (!done)
-      k_root<T><<<1, kRootThreads, sm, s>>>(h->root_n, h->idx + h->root_idx_off,
-                                            fv.vals + h->root_G_off, x);
   }
   for (int l = (fused ? lb : h->L) - 1; l >= 0; --l) {
     HIF_TRY(launch_group_bwd<T>(h, h->lv[l], l, fv, x, s));
@@ -1406,6 +1631,7 @@ int build_upper_plan(Handle *h) {
   h->use_upper = false;
   const char *off = std::getenv("HIFCN_NO_FUSED");
   if (off && off[0] == '1') return HIF_OK;
+  if (h->root_split) return HIF_OK;  // a large root is spread over the whole GPU
   const int L = h->L;
   // FP32 value bytes of a fused level, in MB: one cluster streams only a few
   // MB in the time a level's own launch takes, so only the top levels and
@@ -1473,7 +1699,6 @@ int build_upper_plan(Handle *h) {
   }
   HIF_TRY(dev_alloc(h, (void **)&h->upper_phases, ph.size() * sizeof(UpperPhase)));
   HIF_TRY(dev_alloc(h, (void **)&h->upper_levels, std::max<size_t>(1, ul.size()) * sizeof(UpperLevel)));
-  HIF_TRY(dev_alloc(h, &h->upper_rt, std::max(nr, 1) * sizeof(double)));
   HIF_CUDA_TRY(cudaMemcpy(h->upper_phases, ph.data(), ph.size() * sizeof(UpperPhase), cudaMemcpyHostToDevice));
   if (!ul.empty())
     HIF_CUDA_TRY(cudaMemcpy(h->upper_levels, ul.data(), ul.size() * sizeof(UpperLevel), cudaMemcpyHostToDevice));

@@ -58,6 +58,13 @@ constexpr int kScalErr = 15;
 
 // Size of one shared-memory stage of the bulk-copy staged cell kernels.
 constexpr int kStageBytes = 15872;  // 124 x 128 B: three backward CTAs fit an SM
+
+// Separator entities above this size are applied split over many CTAs, and
+// roots above kRootSplitDofs by a row-block and a column-block launch.
+constexpr int kSplitDofs = 256;
+constexpr int kRootSplitDofs = 512;
+constexpr int kSplitRows = 32;   // rows of H per CTA (forward)
+constexpr int kSplitCols = 64;   // columns of H per CTA (backward)
 __host__ __device__ inline long long tri_off(long long i) {
   const long long q = i >> 2, r = i & 3;
   return 8 * q * (q + 1) + 4 * r * (q + 1);
@@ -106,6 +113,15 @@ struct LevelDev {
   // separator entities with at most 32 DOFs (one warp each) and the others
   int nsmall = 0, nlarge = 0;
   int *small_groups = nullptr, *large_groups = nullptr;
+  // levels with entities of more than kSplitDofs DOFs apply their large
+  // entities split over many CTAs: the entity inputs are first gathered into
+  // a scratch vector (gs_off per large entity), then row blocks (forward) or
+  // column blocks (backward) of H are spread over CTAs
+  int split = 0;
+  long long *gs_off = nullptr;       // device, per large entity
+  long long gs_total = 0;
+  int2 *rblk = nullptr, *cblk = nullptr;  // device: (large entity, first row / column)
+  int nrblk = 0, ncblk = 0;
   int max_nI = 0, max_nB = 0, max_ng = 0;
   // algorithmic bytes per launch for one-byte-per-value accounting:
   // values read, indices read (4 B), vector entries read+written, contributions
@@ -140,6 +156,7 @@ template <typename T>
 struct FactorValues {
   T *vals = nullptr;       // device value pool
   T *contrib = nullptr;    // device contribution scratch
+  T *gs = nullptr;         // device scratch of the split entity steps (max gs_total)
   T *work = nullptr;       // device work vector (N) for the reduced-precision apply
   T *xI = nullptr;         // device N-vector: forward values of the cell interiors
 };
@@ -197,6 +214,7 @@ struct hif_handle {
   hifcn::UpperPhase *upper_phases = nullptr;  // device
   hifcn::UpperLevel *upper_levels = nullptr;  // device
   void *upper_rt = nullptr;                   // device root scratch (root_n doubles)
+  bool root_split = false;                    // root applied by row- and column-block launches
   size_t upper_smem[2] = {0, 0};              // dynamic shared memory, FP64 / FP32
   int upper_grid[2] = {0, 0};                 // CTAs of the cluster, FP64 / FP32
   double upper_bytes[2] = {0, 0};             // algorithmic bytes per launch, FP64 / FP32
