@@ -293,6 +293,7 @@ int finish_device_factor(Handle *h, cudaStream_t s) {
   }
   HIF_CUDA_TRY(cudaStreamSynchronize(s));
   HIF_TRY(build_upper_plan(h));
+  HIF_TRY(build_view(h));
   return HIF_OK;
 }
 
@@ -415,6 +416,8 @@ void release_factor(Handle *h) {
   h->upper_levels = nullptr;
   h->upper_rt = nullptr;
   h->root_split = false;
+  h->view = nullptr;
+  h->view_ok = false;
   h->upper_grid[0] = h->upper_grid[1] = 0;
   for (auto &r : h->stat_pending) {
     cudaEventDestroy(r.a);
@@ -705,6 +708,7 @@ int hif_set_reaction(hif_handle *h, int kind, double k1, double k2) {
   h->react_kind = kind;
   h->react_k1 = k1;
   h->react_k2 = k2;
+  if (h->factor_ok && h->view_ok) HIF_TRY(build_view(h));  // the merged steps read the reaction
   return HIF_OK;
 }
 

@@ -1002,19 +1002,17 @@ __global__ void __launch_bounds__(kTmaThreads) k_cell_bwd_tma_S(const CellDesc *
 }
 
 // Root (Eq. 3_4): x_r <- G_r^T (G_r x_r).
-template <typename T, typename TV = T>
-__global__ void __launch_bounds__(kRootThreads) k_root(int nr, const int *__restrict__ ridx,
-                                                       const TV *__restrict__ G,
-                                                       T *__restrict__ x) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+template <typename T, int NT, typename TV = T>
+__device__ __forceinline__ void root_unit(int nr, const int *__restrict__ ridx, const TV *__restrict__ G,
+                                          T *__restrict__ x, T *smem) {
   const int nrp = (int)pad4(nr);
-  T *xs = reinterpret_cast<T *>(smem_raw);
+  T *xs = smem;
   T *ts = xs + nrp;
   T *part = ts + nrp;
-  for (int i = threadIdx.x; i < nrp; i += kRootThreads) xs[i] = i < nr ? x[ridx[i]] : T(0);
+  for (int i = threadIdx.x; i < nrp; i += NT) xs[i] = i < nr ? x[ridx[i]] : T(0);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int NW = kRootThreads / 32;
+  constexpr int NW = NT / 32;
   for (int r0 = warp * kRows; r0 < nr; r0 += NW * kRows) {  // t = G x
     const TV *rp[kRows];
     int nq[kRows];
@@ -1034,7 +1032,7 @@ __global__ void __launch_bounds__(kRootThreads) k_root(int nr, const int *__rest
   }
   __syncthreads();
   int CW, RG;
-  col_layout(nr, kRootThreads, CW, RG);
+  col_layout(nr, NT, CW, RG);
   const int cl = threadIdx.x % CW, rg = threadIdx.x / CW;
   for (int c0 = 0; c0 < nr; c0 += CW) {  // y = G^T t
     const int col = c0 + cl;
@@ -1052,6 +1050,14 @@ __global__ void __launch_bounds__(kRootThreads) k_root(int nr, const int *__rest
     }
     __syncthreads();
   }
+}
+
+template <typename T, typename TV = T>
+__global__ void __launch_bounds__(kRootThreads) k_root(int nr, const int *__restrict__ ridx,
+                                                       const TV *__restrict__ G,
+                                                       T *__restrict__ x) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  root_unit<T, kRootThreads, TV>(nr, ridx, G, x, reinterpret_cast<T *>(smem_raw));
 }
 
 // ------------------------------------------------- fused upper-level sweep
@@ -1202,6 +1208,81 @@ __global__ void __launch_bounds__(kUpperThreads) k_upper_sweep(
       __syncthreads();  // the unit's shared buffers are reused by the next unit
     }
     if (p + 1 < nphase) cluster_barrier();
+  }
+}
+
+// ---------------------------------------------- merged steps of many handles
+//
+// cn_step_batched runs each step of the apply once for all handles of the
+// batch: phase (kind, level) has units (cell items, entity groups, roots) of
+// every handle; pre[p] is the first unit of handle p (pre[K] = total).  A CTA
+// finds its handle by binary search and runs the same unit code as the
+// single-handle kernels (G-form cells, FP32 arithmetic, BF16 values at the
+// handle's BF16 levels).  Handles whose solve has converged are skipped.
+template <int KIND>
+__global__ void __launch_bounds__(256) k_merged_phase(const int *__restrict__ pre, int K, int level,
+                                                      HandleView *const *__restrict__ views,
+                                                      const int *__restrict__ active) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float *sm = reinterpret_cast<float *>(smem_raw);
+  int lo = 0, hi = K;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (pre[mid] <= (int)blockIdx.x) lo = mid;
+    else hi = mid;
+  }
+  const int p = lo;
+  if (!active[p]) return;
+  const int u = blockIdx.x - pre[p];
+  const HandleView *v = views[p];
+  const bool b16 = level >= v->bf16_lb;
+  const float *vals = v->vals;
+  const __nv_bfloat16 *vals16 = static_cast<const __nv_bfloat16 *>(v->vals16);
+  const int *idx = v->idx;
+  if constexpr (KIND == kPhaseRootRows) {  // the whole root of handle p
+    const int nr = v->root_n;
+    if (b16) root_unit<float, 256, __nv_bfloat16>(nr, v->ridx, vals16 + v->root_G_off, v->z, sm);
+    else root_unit<float, 256>(nr, v->ridx, vals + v->root_G_off, v->z, sm);
+    return;
+  } else {
+    const LevelView L = v->lv[level];
+    if constexpr (KIND == kPhaseCellFwd) {
+      if (b16) cell_fwd_unit<float, 256, __nv_bfloat16>(L.fwd[u], L.cells, idx, vals16, v->contrib, v->xI, v->z, sm);
+      else cell_fwd_unit<float, 256>(L.fwd[u], L.cells, idx, vals, v->contrib, v->xI, v->z, sm);
+    } else if constexpr (KIND == kPhaseCellBwd) {
+      if (b16) cell_bwd_unit<float, 256, __nv_bfloat16>(L.bwd[u], L.cells, idx, vals16, v->xI, v->z, sm);
+      else cell_bwd_unit<float, 256>(L.bwd[u], L.cells, idx, vals, v->xI, v->z, sm);
+    } else if constexpr (KIND == kPhaseGroupFwd) {
+      if (u < L.nlarge) {
+        const GroupDesc g = L.groups[L.large[u]];
+        if (b16) group_fwd_unit<float, 256, __nv_bfloat16>(g, idx, v->cptr, v->cslot, vals16, v->contrib, v->z, sm);
+        else group_fwd_unit<float, 256>(g, idx, v->cptr, v->cslot, vals, v->contrib, v->z, sm);
+      } else {
+        const int warp = threadIdx.x >> 5;
+        const int t = (u - L.nlarge) * 8 + warp;
+        if (t < L.nsmall) {
+          const GroupDesc g = L.groups[L.small[t]];
+          if (b16)
+            group_fwd_small_warp<float, __nv_bfloat16>(g, idx, v->cptr, v->cslot, vals16, v->contrib, v->z,
+                                                       sm + 32 * warp);
+          else group_fwd_small_warp<float>(g, idx, v->cptr, v->cslot, vals, v->contrib, v->z, sm + 32 * warp);
+        }
+      }
+    } else {  // kPhaseGroupBwd
+      if (u < L.nlarge) {
+        const GroupDesc g = L.groups[L.large[u]];
+        if (b16) group_bwd_unit<float, 256, __nv_bfloat16>(g, idx, vals16, v->z, sm);
+        else group_bwd_unit<float, 256>(g, idx, vals, v->z, sm);
+      } else {
+        const int warp = threadIdx.x >> 5;
+        const int t = (u - L.nlarge) * 8 + warp;
+        if (t < L.nsmall) {
+          const GroupDesc g = L.groups[L.small[t]];
+          if (b16) group_bwd_small_warp<float, __nv_bfloat16>(g, idx, vals16, v->z, sm + 32 * warp);
+          else group_bwd_small_warp<float>(g, idx, vals, v->z, sm + 32 * warp);
+        }
+      }
+    }
   }
 }
 
@@ -1622,6 +1703,130 @@ int upper_launch_shape(Handle *h, size_t smem, int max_units) {
 }
 
 }  // namespace
+
+// The device view of a handle for the merged batched steps (FP32 apply
+// only; handles with split levels, a split root or more than
+// kMaxViewLevels levels keep the per-handle path).
+int build_view(Handle *h) {
+  h->view_ok = false;
+  if (!reduced_apply(h) || h->L > kMaxViewLevels || h->root_split || h->opt.solver != 0) return HIF_OK;
+  for (const LevelDev &lv : h->lv)
+    if (lv.split) return HIF_OK;
+  HandleView v{};
+  v.L = h->L;
+  v.dim = h->grid.dim;
+  v.n = h->grid.n;
+  v.root_n = h->root_n;
+  v.N = h->N;
+  v.bf16_lb = h->has_bf16 ? h->bf16_lb : (1 << 30);
+  v.idx = h->idx;
+  v.cptr = h->cptr;
+  v.cslot = h->cslot;
+  v.vals = h->f32.vals;
+  v.vals16 = h->bf16_vals;
+  v.contrib = h->f32.contrib;
+  v.xI = h->f32.xI;
+  v.z = h->f32.work;
+  v.ridx = h->idx + h->root_idx_off;
+  v.root_G_off = h->root_G_off;
+  v.r = h->r;
+  v.p = h->p;
+  v.q = h->q;
+  v.g = h->g;
+  v.x = h->xsol;
+  v.diag = h->diag;
+  v.wx = h->wx;
+  v.wy = h->wy;
+  v.wz = h->wz;
+  v.dt = h->dt;
+  v.kappa = (1.0 - h->opt.theta) / h->opt.theta;
+  v.react_kind = h->react_kind;
+  v.react_k1 = h->react_k1;
+  v.react_inv_k2 = h->react_k2 == 0.0 ? 0.0 : 1.0 / h->react_k2;
+  v.x0_mode = h->opt.x0_mode;
+  v.true_res_period = h->opt.true_res_period;
+  v.cg_maxit = h->opt.cg_maxit;
+  v.tol2 = h->opt.cg_tol * h->opt.cg_tol;
+  for (int l = 0; l < h->L; ++l) {
+    const LevelDev &D = h->lv[l];
+    v.lv[l] = LevelView{D.fwd, D.bwd, D.cells, D.groups, D.small_groups, D.large_groups,
+                        D.nfwd, D.nbwd, D.nsmall, D.nlarge};
+  }
+  if (!h->view) HIF_TRY(dev_alloc(h, (void **)&h->view, sizeof(HandleView)));
+  HIF_CUDA_TRY(cudaMemcpy(h->view, &v, sizeof(HandleView), cudaMemcpyHostToDevice));
+  h->view_ok = true;
+  return HIF_OK;
+}
+
+// Units and shared memory of one merged phase for handle h (0 units when the
+// handle has no such level).  kind: kPhaseCellFwd / GroupFwd / CellBwd /
+// GroupBwd at `level`, or kPhaseRootRows for the root.
+void merged_units(const Handle *h, int kind, int level, int *units, size_t *smem) {
+  *units = 0;
+  *smem = 0;
+  if (kind == kPhaseRootRows) {
+    if (h->root_n > 0) {
+      *units = 1;
+      *smem = (2 * (size_t)pad4(h->root_n) + 256) * sizeof(float);
+    }
+    return;
+  }
+  if (level >= h->L) return;
+  const LevelDev &lv = h->lv[level];
+  switch (kind) {
+    case kPhaseCellFwd:
+      *units = lv.ncells ? lv.nfwd : 0;
+      *smem = (size_t)pad4(lv.max_nI) * sizeof(float);
+      break;
+    case kPhaseCellBwd:
+      *units = lv.ncells ? lv.nbwd : 0;
+      *smem = ((size_t)lv.max_nI + lv.max_nB + 8 * 256) * sizeof(float);
+      break;
+    case kPhaseGroupFwd:
+      *units = lv.ngroups ? lv.nlarge + (lv.nsmall + 7) / 8 : 0;
+      *smem = std::max<size_t>(pad4(lv.max_ng), 256) * sizeof(float);
+      break;
+    default:
+      *units = lv.ngroups ? lv.nlarge + (lv.nsmall + 7) / 8 : 0;
+      *smem = ((size_t)lv.max_ng + 256) * sizeof(float);
+      break;
+  }
+}
+
+int launch_merged_phase(int kind, int level, const int *pre, int K, int total, size_t smem,
+                        HandleView *const *views, const int *active, cudaStream_t s) {
+  if (total <= 0) return HIF_OK;
+  static bool attr = false;
+  if (!attr) {
+    const int lim = 200 * 1024;
+    HIF_CUDA_TRY(cudaFuncSetAttribute(k_merged_phase<kPhaseCellFwd>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    HIF_CUDA_TRY(cudaFuncSetAttribute(k_merged_phase<kPhaseCellBwd>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    HIF_CUDA_TRY(cudaFuncSetAttribute(k_merged_phase<kPhaseGroupFwd>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    HIF_CUDA_TRY(cudaFuncSetAttribute(k_merged_phase<kPhaseGroupBwd>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    HIF_CUDA_TRY(cudaFuncSetAttribute(k_merged_phase<kPhaseRootRows>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    attr = true;
+  }
+  switch (kind) {
+    case kPhaseCellFwd:
+      k_merged_phase<kPhaseCellFwd><<<total, 256, smem, s>>>(pre, K, level, views, active);
+      break;
+    case kPhaseCellBwd:
+      k_merged_phase<kPhaseCellBwd><<<total, 256, smem, s>>>(pre, K, level, views, active);
+      break;
+    case kPhaseGroupFwd:
+      k_merged_phase<kPhaseGroupFwd><<<total, 256, smem, s>>>(pre, K, level, views, active);
+      break;
+    case kPhaseGroupBwd:
+      k_merged_phase<kPhaseGroupBwd><<<total, 256, smem, s>>>(pre, K, level, views, active);
+      break;
+    default:
+      k_merged_phase<kPhaseRootRows><<<total, 256, smem, s>>>(pre, K, 1 << 20, views, active);
+      break;
+  }
+  note_launch();
+  HIF_CUDA_TRY(cudaGetLastError());
+  return HIF_OK;
+}
 
 // Plan of the fused upper-level sweep: which levels it covers (the top levels
 // whose factor data is small, so that a launch per step would cost more than

@@ -152,6 +152,36 @@ struct UpperPhase {
   int type, level, units, pad;
 };
 
+// Device view of one handle's FP32 apply and CG state, read by the merged
+// kernels of cn_step_batched (one launch per step for all handles).
+constexpr int kMaxViewLevels = 16;
+struct LevelView {
+  const CellItem *fwd, *bwd;
+  const CellDesc *cells;
+  const GroupDesc *groups;
+  const int *small, *large;
+  int nfwd, nbwd, nsmall, nlarge;
+};
+struct HandleView {
+  int L, dim, n, root_n;
+  long long N;
+  int bf16_lb;                    // levels >= bf16_lb (and the root when < L + 1) read vals16
+  const int *idx;
+  const long long *cptr, *cslot;
+  const float *vals;
+  const void *vals16;
+  float *contrib, *xI, *z;
+  const int *ridx;
+  long long root_G_off;
+  // CG (FP64) and the stencil
+  double *r, *p, *q, *g, *x;
+  const double *diag, *wx, *wy, *wz;
+  double dt, kappa, react_k1, react_inv_k2;
+  int react_kind, x0_mode, true_res_period, cg_maxit;
+  double tol2;
+  LevelView lv[kMaxViewLevels];
+};
+
 template <typename T>
 struct FactorValues {
   T *vals = nullptr;       // device value pool
@@ -215,6 +245,8 @@ struct hif_handle {
   hifcn::UpperLevel *upper_levels = nullptr;  // device
   void *upper_rt = nullptr;                   // device root scratch (root_n doubles)
   bool root_split = false;                    // root applied by row- and column-block launches
+  hifcn::HandleView *view = nullptr;          // device view for the merged batched steps
+  bool view_ok = false;                       // the merged batched path can take this handle
   size_t upper_smem[2] = {0, 0};              // dynamic shared memory, FP64 / FP32
   int upper_grid[2] = {0, 0};                 // CTAs of the cluster, FP64 / FP32
   double upper_bytes[2] = {0, 0};             // algorithmic bytes per launch, FP64 / FP32
@@ -281,6 +313,10 @@ int stencil_matvec(Handle *h, const double *x, double *y, cudaStream_t s);
 int build_device_factor(Handle *h, const std::vector<double> &vals64, cudaStream_t s);
 int apply_inverse(Handle *h, const double *x, double *y, int precision, cudaStream_t s);
 int build_upper_plan(Handle *h);
+int build_view(Handle *h);
+void merged_units(const Handle *h, int kind, int level, int *units, size_t *smem);
+int launch_merged_phase(int kind, int level, const int *pre, int K, int total, size_t smem,
+                        HandleView *const *views, const int *active, cudaStream_t s);
 int pcg(Handle *h, const double *b, double *x, int *iters, double *relres, cudaStream_t s);
 int cn(Handle *h, const double *u, const double *r, double *u1, int *iters, cudaStream_t s);
 int cn_batched(Handle *const *hs, int count, const double *const *u, const double *const *r,

@@ -10,6 +10,11 @@
 #include "internal.h"
 #include "device_common.cuh"
 
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
 namespace hifcn {
 
 int cn_rhs(Handle *h, const double *u, const double *r, double *g, cudaStream_t s);
@@ -656,12 +661,384 @@ int cn(Handle *h, const double *u, const double *r, double *u1, int *iters, cuda
   return solve_core(h, h->g, u, u1, iters, nullptr, s);
 }
 
+// ------------------------------------------------- merged batched CN steps
+//
+// For handles with a device view (FP32 apply, no split levels), one batched
+// step runs every kernel once for all handles: the right-hand sides, the PCG
+// vector kernels over "segments" (kSeg consecutive DOFs of one handle, so a
+// handle's partial sums never mix with another's and do not depend on the
+// batch), one warp per handle for the scalar phases, and the merged apply
+// phases.  A handle whose PCG has converged stops updating; the loop ends when
+// no handle is active (one 4-byte read per iteration).  The arithmetic of a
+// handle is the same in any batch, and equals that of its single steps to the
+// CG tolerance (the single path applies the leaf levels in the S form).
+
+constexpr int kSeg = 8192;
+enum { B_RZ = 0, B_ALPHA, B_BETA, B_RR, B_BB, B_PQ, B_IT, B_CONV, B_COUNT };
+
+struct BSeg {  // per-call arrays of the batch (device)
+  HandleView *const *views;
+  const double *const *u;   // u_k per handle
+  const double *const *rr;  // caller reaction per handle (entries may be null)
+  double *const *u1;        // outputs
+  const int *segpre;        // first segment of handle p (K + 1 entries)
+  int K;
+};
+
+__device__ __forceinline__ int seg_owner(const int *segpre, int K, int seg) {
+  int lo = 0, hi = K;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (segpre[mid] <= seg) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// mode 0: g = RHS(u); x = 0 or u (warm); r = g - A x; z = r; partials b.b, r.r
+__global__ void __launch_bounds__(NT) k_b_start(BSeg B, double *__restrict__ part) {
+  __shared__ double sm[NT / 32];
+  const int p = seg_owner(B.segpre, B.K, blockIdx.x);
+  const HandleView *v = B.views[p];
+  const long long j0 = (long long)(blockIdx.x - B.segpre[p]) * kSeg;
+  const long long j1 = min(j0 + kSeg, v->N);
+  const double *u = B.u[p];
+  const double *rr = B.rr ? B.rr[p] : nullptr;
+  const double kappa = v->kappa, dt = v->dt;
+  double abb = 0.0;
+  for (long long j = j0 + threadIdx.x; j < j1; j += NT) {
+    const double uj = u[j];
+    double g;
+    if (kappa == 1.0) g = 2.0 * uj - stencil_row(u, v->diag, v->wx, v->wy, v->wz, v->dim, v->n, j);
+    else if (kappa == 0.0) g = uj;
+    else g = uj + kappa * (uj - stencil_row(u, v->diag, v->wx, v->wy, v->wz, v->dim, v->n, j));
+    if (rr) g += dt * rr[j];
+    else if (v->react_kind == 1) g += dt * (v->react_k1 * uj * (1.0 - uj * v->react_inv_k2));
+    v->g[j] = g;
+    abb += g * g;
+  }
+  double t = block_sum<NT>(abb, sm);
+  if (threadIdx.x == 0) part[2 * blockIdx.x] = t;
+  __syncthreads();  // g of this segment written; A x below reads u only
+  double arr = 0.0;
+  for (long long j = j0 + threadIdx.x; j < j1; j += NT) {
+    double rj;
+    if (v->x0_mode == 1) {
+      v->x[j] = u[j];
+      rj = v->g[j] - stencil_row(u, v->diag, v->wx, v->wy, v->wz, v->dim, v->n, j);
+    } else {
+      v->x[j] = 0.0;
+      rj = v->g[j];
+    }
+    v->r[j] = rj;
+    v->z[j] = (float)rj;
+    arr += rj * rj;
+  }
+  t = block_sum<NT>(arr, sm);
+  if (threadIdx.x == 0) part[2 * blockIdx.x + 1] = t;
+}
+
+// partials of r.z (mode 0), p.q with q = A p (mode 1)
+template <int MODE>
+__global__ void __launch_bounds__(NT) k_b_dot(BSeg B, const int *__restrict__ active,
+                                              const double *__restrict__ sc, double *__restrict__ part) {
+  __shared__ double sm[NT / 32];
+  const int p = seg_owner(B.segpre, B.K, blockIdx.x);
+  if (!active[p]) return;
+  const HandleView *v = B.views[p];
+  const long long j0 = (long long)(blockIdx.x - B.segpre[p]) * kSeg;
+  const long long j1 = min(j0 + kSeg, v->N);
+  double acc = 0.0;
+  if constexpr (MODE == 0) {
+    for (long long j = j0 + threadIdx.x; j < j1; j += NT) acc += v->r[j] * (double)v->z[j];
+  } else {
+    for (long long j = j0 + threadIdx.x; j < j1; j += NT) {
+      const double qj = stencil_row(v->p, v->diag, v->wx, v->wy, v->wz, v->dim, v->n, j);
+      v->q[j] = qj;
+      acc += v->p[j] * qj;
+    }
+  }
+  const double t = block_sum<NT>(acc, sm);
+  if (threadIdx.x == 0) part[2 * blockIdx.x] = t;
+  (void)sc;
+}
+
+// p = z + beta p (p = z on the first iteration)
+__global__ void __launch_bounds__(NT) k_b_update_p(BSeg B, const int *__restrict__ active,
+                                                   const double *__restrict__ sc) {
+  const int p = seg_owner(B.segpre, B.K, blockIdx.x);
+  if (!active[p]) return;
+  const HandleView *v = B.views[p];
+  const long long j0 = (long long)(blockIdx.x - B.segpre[p]) * kSeg;
+  const long long j1 = min(j0 + kSeg, v->N);
+  const bool first = sc[p * B_COUNT + B_IT] == 0.0;
+  const double beta = sc[p * B_COUNT + B_BETA];
+  for (long long j = j0 + threadIdx.x; j < j1; j += NT)
+    v->p[j] = first ? (double)v->z[j] : (double)v->z[j] + beta * v->p[j];
+}
+
+// x += alpha p; r -= alpha q; z = r; partials r.r; every true_res_period
+// iterations the next kernel recomputes r from x instead
+__global__ void __launch_bounds__(NT) k_b_update_xr(BSeg B, const int *__restrict__ active,
+                                                    const double *__restrict__ sc, double *__restrict__ part) {
+  __shared__ double sm[NT / 32];
+  const int p = seg_owner(B.segpre, B.K, blockIdx.x);
+  if (!active[p]) return;
+  const HandleView *v = B.views[p];
+  const long long j0 = (long long)(blockIdx.x - B.segpre[p]) * kSeg;
+  const long long j1 = min(j0 + kSeg, v->N);
+  const double alpha = sc[p * B_COUNT + B_ALPHA];
+  double acc = 0.0;
+  for (long long j = j0 + threadIdx.x; j < j1; j += NT) {
+    v->x[j] += alpha * v->p[j];
+    const double rj = v->r[j] - alpha * v->q[j];
+    v->r[j] = rj;
+    v->z[j] = (float)rj;
+    acc += rj * rj;
+  }
+  const double t = block_sum<NT>(acc, sm);
+  if (threadIdx.x == 0) part[2 * blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(NT) k_b_true_res(BSeg B, const int *__restrict__ active,
+                                                   const double *__restrict__ sc, double *__restrict__ part) {
+  __shared__ double sm[NT / 32];
+  const int p = seg_owner(B.segpre, B.K, blockIdx.x);
+  if (!active[p]) return;
+  const HandleView *v = B.views[p];
+  const int it1 = (int)sc[p * B_COUNT + B_IT] + 1;
+  if (v->true_res_period <= 0 || it1 % v->true_res_period != 0) return;
+  const long long j0 = (long long)(blockIdx.x - B.segpre[p]) * kSeg;
+  const long long j1 = min(j0 + kSeg, v->N);
+  double acc = 0.0;
+  for (long long j = j0 + threadIdx.x; j < j1; j += NT) {
+    const double rj = v->g[j] - stencil_row(v->x, v->diag, v->wx, v->wy, v->wz, v->dim, v->n, j);
+    v->r[j] = rj;
+    v->z[j] = (float)rj;
+    acc += rj * rj;
+  }
+  const double t = block_sum<NT>(acc, sm);
+  if (threadIdx.x == 0) part[2 * blockIdx.x] = t;
+}
+
+// scalar phases, one warp per handle (partials of its segments added in order)
+// mode 0: start (b.b, r.r -> active);  1: beta;  2: alpha;  3: end of iteration
+__global__ void __launch_bounds__(256) k_b_scalar(BSeg B, int mode, int *__restrict__ active,
+                                                  double *__restrict__ sc, const double *__restrict__ part,
+                                                  int *__restrict__ nactive) {
+  const int p = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (p >= B.K) return;
+  if (mode != 0 && !active[p]) return;
+  const HandleView *v = B.views[p];
+  const int s0 = B.segpre[p], s1 = B.segpre[p + 1];
+  double a = 0.0, b = 0.0;
+  for (int i = s0 + lane; i < s1; i += 32) {
+    a += part[2 * i];
+    b += part[2 * i + 1];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if (lane != 0) return;
+  double *s = sc + p * B_COUNT;
+  if (mode == 0) {
+    s[B_BB] = a;
+    s[B_RR] = b;
+    s[B_IT] = 0.0;
+    s[B_RZ] = 0.0;
+    const bool conv = a == 0.0 || (v->x0_mode == 1 && b <= v->tol2 * a);
+    s[B_CONV] = conv ? 1.0 : 0.0;
+    active[p] = conv ? 0 : 1;
+    if (!conv) atomicAdd(nactive, 1);
+  } else if (mode == 1) {
+    s[B_BETA] = s[B_IT] == 0.0 ? 0.0 : a / s[B_RZ];
+    s[B_RZ] = a;
+  } else if (mode == 2) {
+    s[B_PQ] = a;
+    s[B_ALPHA] = s[B_RZ] / a;
+  } else {
+    s[B_RR] = a;
+    const double it = s[B_IT] + 1.0;
+    s[B_IT] = it;
+    const bool conv = a <= v->tol2 * s[B_BB];
+    s[B_CONV] = conv ? 1.0 : 0.0;
+    const bool go = !conv && it < (double)v->cg_maxit;
+    active[p] = go ? 1 : 0;
+    if (go) atomicAdd(nactive, 1);
+  }
+}
+
+// u1 = x (b = 0: x = 0)
+__global__ void __launch_bounds__(NT) k_b_copy_out(BSeg B, const double *__restrict__ sc) {
+  const int p = seg_owner(B.segpre, B.K, blockIdx.x);
+  const HandleView *v = B.views[p];
+  const long long j0 = (long long)(blockIdx.x - B.segpre[p]) * kSeg;
+  const long long j1 = min(j0 + kSeg, v->N);
+  const bool zero = sc[p * B_COUNT + B_BB] == 0.0;
+  double *out = B.u1[p];
+  for (long long j = j0 + threadIdx.x; j < j1; j += NT) out[j] = zero ? 0.0 : v->x[j];
+}
+
+// Workspace of the merged steps (grown on demand, reused across calls).
+struct BatchWorkspace {
+  void *dev = nullptr;
+  size_t dev_bytes = 0;
+  unsigned char *host = nullptr;
+  size_t host_bytes = 0;
+  int *h_nactive = nullptr;
+};
+BatchWorkspace g_bws;
+
+int bws_reserve(size_t dev_bytes, size_t host_bytes) {
+  if (dev_bytes > g_bws.dev_bytes) {
+    if (g_bws.dev) cudaFree(g_bws.dev);
+    g_bws.dev = nullptr;
+    g_bws.dev_bytes = 0;
+    HIF_CUDA_TRY(cudaMalloc(&g_bws.dev, dev_bytes * 2));
+    g_bws.dev_bytes = dev_bytes * 2;
+  }
+  if (host_bytes > g_bws.host_bytes) {
+    if (g_bws.host) cudaFreeHost(g_bws.host);
+    g_bws.host = nullptr;
+    g_bws.host_bytes = 0;
+    HIF_CUDA_TRY(cudaMallocHost((void **)&g_bws.host, host_bytes * 2));
+    g_bws.host_bytes = host_bytes * 2;
+  }
+  if (!g_bws.h_nactive) HIF_CUDA_TRY(cudaMallocHost((void **)&g_bws.h_nactive, sizeof(int)));
+  return HIF_OK;
+}
+
+// Merged steps for K handles that all have a device view (no duplicates).
+int cn_batched_merged(Handle *const *hs, int K, const double *const *u, const double *const *r,
+                      double *const *u1, int *iters, int *status, cudaStream_t s) {
+  // phases of the apply: (kind, level) in sweep order
+  int Lmax = 0;
+  for (int i = 0; i < K; ++i) Lmax = std::max(Lmax, hs[i]->L);
+  std::vector<int2> phases;
+  for (int l = 0; l < Lmax; ++l) {
+    phases.push_back(make_int2(kPhaseCellFwd, l));
+    phases.push_back(make_int2(kPhaseGroupFwd, l));
+  }
+  phases.push_back(make_int2(kPhaseRootRows, 0));
+  for (int l = Lmax - 1; l >= 0; --l) {
+    phases.push_back(make_int2(kPhaseGroupBwd, l));
+    phases.push_back(make_int2(kPhaseCellBwd, l));
+  }
+  const int P = (int)phases.size();
+  // host staging layout: views[K] | u[K] | rr[K] | u1[K] | segpre[K+1] | pre[P][K+1] | active[K]
+  const size_t ptr_bytes = 4 * (size_t)K * sizeof(void *);
+  const size_t int_count = (size_t)(K + 1) * (P + 1) + K;
+  const size_t up_bytes = ptr_bytes + int_count * sizeof(int);
+  int total_seg = 0;
+  std::vector<int> segpre(K + 1, 0);
+  for (int i = 0; i < K; ++i) {
+    segpre[i] = total_seg;
+    total_seg += (int)((hs[i]->N + kSeg - 1) / kSeg);
+  }
+  segpre[K] = total_seg;
+  const size_t sc_off = (up_bytes + 255) / 256 * 256;
+  const size_t part_off = sc_off + (size_t)K * B_COUNT * sizeof(double);
+  const size_t nact_off = part_off + 2 * (size_t)total_seg * sizeof(double);
+  const size_t dev_bytes = nact_off + 256;
+  HIF_TRY(bws_reserve(dev_bytes, up_bytes));
+  unsigned char *hb = g_bws.host;
+  unsigned char *db = static_cast<unsigned char *>(g_bws.dev);
+  void **hp = reinterpret_cast<void **>(hb);
+  bool any_r = false;
+  for (int i = 0; i < K; ++i) {
+    hp[i] = hs[i]->view;
+    hp[K + i] = const_cast<double *>(u[i]);
+    hp[2 * K + i] = r ? const_cast<double *>(r[i]) : nullptr;
+    hp[3 * K + i] = u1[i];
+    any_r = any_r || (r && r[i]);
+  }
+  int *hi = reinterpret_cast<int *>(hb + ptr_bytes);
+  std::memcpy(hi, segpre.data(), (K + 1) * sizeof(int));
+  std::vector<int> totals(P, 0);
+  std::vector<size_t> smem(P, 0);
+  for (int ph = 0; ph < P; ++ph) {
+    int *pre = hi + (size_t)(K + 1) * (ph + 1);
+    int run = 0;
+    for (int i = 0; i < K; ++i) {
+      int un = 0;
+      size_t sm = 0;
+      merged_units(hs[i], phases[ph].x, phases[ph].y, &un, &sm);
+      pre[i] = run;
+      run += un;
+      smem[ph] = std::max(smem[ph], sm);
+    }
+    pre[K] = run;
+    totals[ph] = run;
+  }
+  int *hact = hi + (size_t)(K + 1) * (P + 1);
+  for (int i = 0; i < K; ++i) hact[i] = 1;
+  HIF_CUDA_TRY(cudaMemcpyAsync(db, hb, up_bytes, cudaMemcpyHostToDevice, s));
+  BSeg B;
+  B.views = reinterpret_cast<HandleView *const *>(db);
+  B.u = reinterpret_cast<const double *const *>(db + (size_t)K * sizeof(void *));
+  B.rr = any_r ? reinterpret_cast<const double *const *>(db + 2 * (size_t)K * sizeof(void *)) : nullptr;
+  B.u1 = reinterpret_cast<double *const *>(db + 3 * (size_t)K * sizeof(void *));
+  const int *dint = reinterpret_cast<const int *>(db + ptr_bytes);
+  B.segpre = dint;
+  B.K = K;
+  int *active = const_cast<int *>(dint + (size_t)(K + 1) * (P + 1));
+  double *sc = reinterpret_cast<double *>(db + sc_off);
+  double *part = reinterpret_cast<double *>(db + part_off);
+  int *nactive = reinterpret_cast<int *>(db + nact_off);
+  const int sgrid = (K + 7) / 8;
+
+  auto read_active = [&](int *n) -> int {
+    HIF_CUDA_TRY(cudaMemcpyAsync(g_bws.h_nactive, nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HIF_CUDA_TRY(cudaStreamSynchronize(s));
+    *n = *g_bws.h_nactive;
+    return HIF_OK;
+  };
+  HIF_CUDA_TRY(cudaMemsetAsync(nactive, 0, sizeof(int), s));
+  k_b_start<<<total_seg, NT, 0, s>>>(B, part);
+  k_b_scalar<<<sgrid, 256, 0, s>>>(B, 0, active, sc, part, nactive);
+  note_launch(2);
+  int n_act = 0;
+  HIF_TRY(read_active(&n_act));
+  int maxit = 0;
+  for (int i = 0; i < K; ++i) maxit = std::max(maxit, hs[i]->opt.cg_maxit);
+  for (int it = 0; n_act > 0 && it < maxit; ++it) {
+    for (int ph = 0; ph < P; ++ph)
+      HIF_TRY(launch_merged_phase(phases[ph].x, phases[ph].y, dint + (size_t)(K + 1) * (ph + 1), K,
+                                  totals[ph], smem[ph], const_cast<HandleView *const *>(B.views), active, s));
+    k_b_dot<0><<<total_seg, NT, 0, s>>>(B, active, sc, part);
+    k_b_scalar<<<sgrid, 256, 0, s>>>(B, 1, active, sc, part, nactive);
+    k_b_update_p<<<total_seg, NT, 0, s>>>(B, active, sc);
+    k_b_dot<1><<<total_seg, NT, 0, s>>>(B, active, sc, part);
+    k_b_scalar<<<sgrid, 256, 0, s>>>(B, 2, active, sc, part, nactive);
+    k_b_update_xr<<<total_seg, NT, 0, s>>>(B, active, sc, part);
+    k_b_true_res<<<total_seg, NT, 0, s>>>(B, active, sc, part);
+    HIF_CUDA_TRY(cudaMemsetAsync(nactive, 0, sizeof(int), s));
+    k_b_scalar<<<sgrid, 256, 0, s>>>(B, 3, active, sc, part, nactive);
+    note_launch(8);
+    HIF_CUDA_TRY(cudaGetLastError());
+    HIF_TRY(read_active(&n_act));
+  }
+  k_b_copy_out<<<total_seg, NT, 0, s>>>(B, sc);
+  note_launch();
+  std::vector<double> hsc((size_t)K * B_COUNT);
+  HIF_CUDA_TRY(cudaMemcpyAsync(hsc.data(), sc, hsc.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  HIF_CUDA_TRY(cudaStreamSynchronize(s));
+  for (int i = 0; i < K; ++i) {
+    const double *x = &hsc[(size_t)i * B_COUNT];
+    if (iters) iters[i] = (int)x[B_IT];
+    status[i] = (x[B_BB] == 0.0 || x[B_CONV] != 0.0) ? HIF_OK : HIF_ENOCONV;
+  }
+  return HIF_OK;
+}
+
 // Several CN steps, one per handle, overlapped on the GPU: each handle's
 // RHS kernel, captured solve and result copy run on the handle's own stream,
 // which first waits for the caller's stream; the call returns when all are
 // done.  A handle listed twice runs its steps in list order.
-int cn_batched(Handle *const *hs, int count, const double *const *u, const double *const *r,
-               double *const *u1, int *iters, cudaStream_t s) {
+int cn_batched_streams(Handle *const *hs, int count, const double *const *u, const double *const *r,
+                       double *const *u1, int *iters, cudaStream_t s) {
   std::vector<int> status(count, HIF_OK);
   auto sequential = [](const Handle *h) { return !h->use_graph || h->stats_on || h->opt.solver == 1; };
   for (int i = 0; i < count; ++i) {
@@ -717,6 +1094,57 @@ int cn_batched(Handle *const *hs, int count, const double *const *u, const doubl
     if (st != HIF_OK && result == HIF_OK) result = st;
   }
   cudaEventDestroy(ev);
+  return result;
+}
+
+// cn_step_batched: handles with a device view (FP32 apply, no split levels,
+// PCG solver, statistics off), each listed once, take the merged steps; the
+// others the per-handle streams.  HIFCN_NO_MERGED=1 sends all to the latter.
+int cn_batched(Handle *const *hs, int count, const double *const *u, const double *const *r,
+               double *const *u1, int *iters, cudaStream_t s) {
+  const char *nm = std::getenv("HIFCN_NO_MERGED");
+  const bool no_merged = nm && nm[0] == '1';
+  std::vector<int> mi, oi;
+  for (int i = 0; i < count; ++i) {
+    Handle *h = hs[i];
+    int times = 0;
+    for (int j = 0; j < count; ++j) times += hs[j] == h;
+    const bool ok = !no_merged && h->view_ok && !h->stats_on && h->opt.solver == 0 && times == 1;
+    (ok ? mi : oi).push_back(i);
+  }
+  int result = HIF_OK;
+  auto take = [&](const std::vector<int> &ix, std::vector<Handle *> &H, std::vector<const double *> &U,
+                  std::vector<const double *> &R, std::vector<double *> &U1) {
+    for (int i : ix) {
+      H.push_back(hs[i]);
+      U.push_back(u[i]);
+      R.push_back(r ? r[i] : nullptr);
+      U1.push_back(u1[i]);
+    }
+  };
+  if (!oi.empty()) {
+    std::vector<Handle *> H;
+    std::vector<const double *> U, R;
+    std::vector<double *> U1;
+    take(oi, H, U, R, U1);
+    std::vector<int> it(oi.size(), 0);
+    const int st = cn_batched_streams(H.data(), (int)H.size(), U.data(), R.data(), U1.data(), it.data(), s);
+    for (size_t k = 0; k < oi.size(); ++k)
+      if (iters) iters[oi[k]] = it[k];
+    if (st != HIF_OK && result == HIF_OK) result = st;
+  }
+  if (!mi.empty()) {
+    std::vector<Handle *> H;
+    std::vector<const double *> U, R;
+    std::vector<double *> U1;
+    take(mi, H, U, R, U1);
+    std::vector<int> it(mi.size(), 0), stat(mi.size(), HIF_OK);
+    HIF_TRY(cn_batched_merged(H.data(), (int)H.size(), U.data(), R.data(), U1.data(), it.data(), stat.data(), s));
+    for (size_t k = 0; k < mi.size(); ++k) {
+      if (iters) iters[mi[k]] = it[k];
+      if (stat[k] != HIF_OK && result == HIF_OK) result = stat[k];
+    }
+  }
   return result;
 }
 

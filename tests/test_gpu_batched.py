@@ -1,8 +1,12 @@
 """cn_step_batched: independent CN steps of several operators at once.
 
-Each result must equal the result of cn_step on that handle alone, bit for
-bit (same kernels, deterministic reductions), whatever the mix of sizes,
-dimensions and precisions in the batch, and also when a handle appears twice.
+Handles with the FP32 apply take the merged steps (one launch per step for
+all of them): a handle's result there does not depend on the rest of the
+batch (bit for bit the same alone and in any mix), and equals its single
+cn_step result to the CG tolerance (1e-9 relative at tol 1e-10, iterations
++-1; the single path applies the leaf levels in another, equivalent form).
+FP64 handles, and a handle listed twice, take per-handle streams and equal
+their single steps bit for bit.
 """
 
 import numpy as np
@@ -34,11 +38,17 @@ def _mk(H, dim, n, m, seed, precision):
     return h, u
 
 
+def _close(a, b, tol=1e-9):
+    import torch
+    return float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) <= tol
+
+
 def test_batched_equals_individual_steps(H):
     import torch
     specs = [(2, 64, 8, 1, 0), (2, 128, 16, 2, 1), (3, 16, 4, 3, 0), (2, 256, 16, 4, 1),
-             (2, 32, 8, 5, 0)]
+             (2, 32, 8, 5, 0), (3, 16, 4, 6, 1), (2, 64, 8, 7, 1)]
     hs, us = zip(*[_mk(H, *s) for s in specs])
+    prec = [s[4] for s in specs]
     ref = []
     ref_it = []
     for h, u in zip(hs, us):
@@ -47,13 +57,21 @@ def test_batched_equals_individual_steps(H):
         ref_it.append(it)
     outs, its = H.cn_step_batched(list(hs), list(us))
     torch.cuda.synchronize()
-    for o, r in zip(outs, ref):
-        assert torch.equal(o, r)
-    assert its == ref_it
+    for o, r, i, ri, pr in zip(outs, ref, its, ref_it, prec):
+        if pr == 0:
+            assert torch.equal(o, r) and i == ri
+        else:
+            assert _close(o, r) and abs(i - ri) <= 1
+    # merged results do not depend on the batch: each FP32 handle alone
+    for h, u, o, pr in zip(hs, us, outs, prec):
+        if pr == 1:
+            alone, _ = H.cn_step_batched([h], [u])
+            assert torch.equal(alone[0], o)
     # a second batched step from the first step's results
     outs2, _ = H.cn_step_batched(list(hs), outs)
-    for h, o, o2 in zip(hs, outs, outs2):
-        assert torch.equal(H.cn_step(h, o)[0], o2)
+    for h, o, o2, pr in zip(hs, outs, outs2, prec):
+        single = H.cn_step(h, o)[0]
+        assert torch.equal(single, o2) if pr == 0 else _close(o2, single)
 
 
 def test_batched_repeated_handle_and_caller_reaction(H):
@@ -66,7 +84,7 @@ def test_batched_repeated_handle_and_caller_reaction(H):
     a2, _ = H.cn_step(h, a1, r=r)
     # the same handle twice: its steps run in list order on its own buffers
     outs, its = H.cn_step_batched([h, h2, h], [u, u2, a1], rs=[r, None, r])
-    assert torch.equal(outs[0], a1) and torch.equal(outs[1], b1) and torch.equal(outs[2], a2)
+    assert torch.equal(outs[0], a1) and _close(outs[1], b1) and torch.equal(outs[2], a2)
     assert len(its) == 3 and all(i >= 1 for i in its)
     # empty batch is a no-op
     assert H.cn_step_batched([], []) == ([], [])

@@ -165,6 +165,10 @@ def test_batched_mixed_options_equals_individual(H):
     ref = [H.cn_step(h, u) for h, u in zip(hs, us)]
     outs, its = H.cn_step_batched(hs, us)
     torch.cuda.synchronize()
-    for (o_ref, it_ref), o, it in zip(ref, outs, its):
-        assert torch.equal(o, o_ref)
-        assert it == it_ref
+    for (o_ref, it_ref), o, it, kw in zip(ref, outs, its, cfg):
+        if kw.get("precision", 0) == 0:  # per-handle streams: the single-step kernels
+            assert torch.equal(o, o_ref)
+            assert it == it_ref
+        else:  # merged FP32 steps: equal to the CG tolerance
+            assert float(torch.linalg.norm(o - o_ref) / torch.linalg.norm(o_ref)) <= 1e-9
+            assert abs(it - it_ref) <= 1

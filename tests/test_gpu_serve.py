@@ -1,7 +1,7 @@
 """Serving: CN-step requests over resident operators with continuous batching.
 
 The same operator must follow the same trajectory, bit for bit, whether it is
-stepped alone with cn_step or served in a mix of operators of different
+stepped alone (a batch of one) or served in a mix of operators of different
 sizes and dimensions whose requests arrive from several clients while other
 batches run, and after being evicted (HBM budget) and re-factored.
 """
@@ -45,8 +45,9 @@ def _alone(H, spec, steps):
                     H.default_options(eps=spec.eps, precision=spec.precision, cg_tol=1e-10))
     H.hif_set_reaction(h, *spec.reaction)
     u = torch.from_numpy(np.array(spec.u0).ravel().copy()).cuda()
-    for _ in range(steps):
-        u, _ = H.cn_step(h, u)
+    for _ in range(steps):  # a batch of one: the same kernels as in any served batch
+        outs, _ = H.cn_step_batched([h], [u])
+        u = outs[0]
     out = u.cpu().numpy()
     h.close()
     return out
