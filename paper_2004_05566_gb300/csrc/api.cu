@@ -259,6 +259,19 @@ int finish_device_factor(Handle *h, cudaStream_t s) {
     }
     HIF_TRY(dev_alloc(h, (void **)&D.fwd, std::max<size_t>(1, fw.size()) * sizeof(CellItem)));
     HIF_TRY(dev_alloc(h, (void **)&D.bwd, std::max<size_t>(1, bw.size()) * sizeof(CellItem)));
+    {  // whole cells, for the merged batched steps (the batch fills the GPU)
+      std::vector<CellItem> f1, b1;
+      for (int c = 0; c < (int)H.cells.size(); ++c) {
+        f1.push_back({c, 0, H.cells[c].nB + H.cells[c].nI, 0});
+        b1.push_back({c, 0, H.cells[c].nI, 0});
+      }
+      HIF_TRY(dev_alloc(h, (void **)&D.fwd1, std::max<size_t>(1, f1.size()) * sizeof(CellItem)));
+      HIF_TRY(dev_alloc(h, (void **)&D.bwd1, std::max<size_t>(1, b1.size()) * sizeof(CellItem)));
+      if (!f1.empty()) {
+        HIF_CUDA_TRY(cudaMemcpyAsync(D.fwd1, f1.data(), f1.size() * sizeof(CellItem), cudaMemcpyHostToDevice, s));
+        HIF_CUDA_TRY(cudaMemcpyAsync(D.bwd1, b1.data(), b1.size() * sizeof(CellItem), cudaMemcpyHostToDevice, s));
+      }
+    }
     if (!fw.empty())
       HIF_CUDA_TRY(cudaMemcpyAsync(D.fwd, fw.data(), fw.size() * sizeof(CellItem), cudaMemcpyHostToDevice, s));
     if (!bw.empty())

@@ -1749,8 +1749,8 @@ int build_view(Handle *h) {
   v.tol2 = h->opt.cg_tol * h->opt.cg_tol;
   for (int l = 0; l < h->L; ++l) {
     const LevelDev &D = h->lv[l];
-    v.lv[l] = LevelView{D.fwd, D.bwd, D.cells, D.groups, D.small_groups, D.large_groups,
-                        D.nfwd, D.nbwd, D.nsmall, D.nlarge};
+    v.lv[l] = LevelView{D.fwd1, D.bwd1, D.cells, D.groups, D.small_groups, D.large_groups,
+                        D.ncells, D.ncells, D.nsmall, D.nlarge};
   }
   if (!h->view) HIF_TRY(dev_alloc(h, (void **)&h->view, sizeof(HandleView)));
   HIF_CUDA_TRY(cudaMemcpy(h->view, &v, sizeof(HandleView), cudaMemcpyHostToDevice));
@@ -1775,11 +1775,11 @@ void merged_units(const Handle *h, int kind, int level, int *units, size_t *smem
   const LevelDev &lv = h->lv[level];
   switch (kind) {
     case kPhaseCellFwd:
-      *units = lv.ncells ? lv.nfwd : 0;
+      *units = lv.ncells;
       *smem = (size_t)pad4(lv.max_nI) * sizeof(float);
       break;
     case kPhaseCellBwd:
-      *units = lv.ncells ? lv.nbwd : 0;
+      *units = lv.ncells;
       *smem = ((size_t)lv.max_nI + lv.max_nB + 8 * 256) * sizeof(float);
       break;
     case kPhaseGroupFwd:

@@ -103,6 +103,7 @@ struct LevelDev {
   int ncells = 0, ngroups = 0;
   int nfwd = 0, nbwd = 0;             // work items of the cell kernels
   CellItem *fwd = nullptr, *bwd = nullptr;  // device
+  CellItem *fwd1 = nullptr, *bwd1 = nullptr;  // device: one item per cell (merged batched steps)
   // bulk-copy chunk tables of the FP32 cell blocks (row boundaries): cell c's
   // chunks are rows [tab[o + k], tab[o + k + 1]) for k < n, (o, n) = of[c];
   // [0]: the V rows, [1]: the S rows followed by the V rows
