@@ -227,7 +227,7 @@ def leaf_kernel_source_hash() -> str:
     csrc = os.path.join(ROOT, "paper_2004_05566_gb300", "csrc")
     src = open(os.path.join(csrc, "apply.cu")).read()
     a = src.index("// ------------------------------------------------------------ TMA-staged cells")
-    b = src.index("// Root (Eq. 3_4)")
+    b = src.index("// Root (Eq. 3_4)", a)
     stage = [l for l in open(os.path.join(csrc, "internal.h")) if "constexpr int kStageBytes" in l]
     return hashlib.sha256((src[a:b] + "".join(stage)).encode()).hexdigest()
 
