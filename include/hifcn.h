@@ -242,6 +242,18 @@ int hif_set_coefficient(hif_handle *h, const double *a_nodes, hif_stream stream)
  * Errors: HIF_EINVAL, HIF_ENOTSPD, HIF_ENOMEM, HIF_ECUDA. */
 int hif_refactor(hif_handle *h, const double *a_nodes, hif_stream stream);
 
+/* hif_autotune - choose, by timing on this GPU, how the handle's apply is cut
+ * into CTAs: per level, the number of CTAs its cell work is spread over (a
+ * multiple of the SM count; levels whose cells are no longer cut use the
+ * bulk-copy S-form kernels), and the CTAs per SM of those kernels.  Runs the
+ * apply about 30 times (on the handle's own work vectors) and keeps the
+ * fastest choice for each; the result of the apply is unchanged up to the
+ * rounding order of the cell kernels.  Not part of the paper's method (an
+ * implementation choice of this library).  Call between solves; it waits for
+ * the device and rebuilds the handle's captured solve graphs on next use.
+ * Errors: HIF_EINVAL (no factor), HIF_ENOMEM, HIF_ECUDA. */
+int hif_autotune(hif_handle *h, hif_stream stream);
+
 /* hif_query - sizes and statistics of a handle (host output). */
 int hif_query(const hif_handle *h, hif_info *info);
 

@@ -125,6 +125,39 @@ int cast_values_bf16(Handle *h, cudaStream_t s);
 
 // Upload descriptors of every level, allocate the contribution scratch and
 // the FP32 copy (values already on the device in h->f64.vals).
+// Work items of one level's G-form cell kernels: each cell is cut into row
+// ranges (forward) and column ranges (backward) so that a launch has about
+// `target` CTAs when the level has fewer cells than that.  The arrays of an
+// earlier call stay allocated until the handle is destroyed.
+int build_items(Handle *h, LevelDev &D, const LevelHost &H, int target, cudaStream_t s) {
+  std::vector<CellItem> fw, bw;
+  const int ncell = (int)H.cells.size();
+  for (int c = 0; c < ncell; ++c) {
+    const CellDesc &cd = H.cells[c];
+    const int rows = cd.nB + cd.nI;
+    int chunks = 1;
+    if (ncell < target) chunks = std::max(1, std::min((target + ncell - 1) / ncell, (rows + 31) / 32));
+    int per = ((rows + chunks - 1) / chunks + 31) / 32 * 32;
+    if (per < 32) per = 32;
+    for (int a = 0; a < rows; a += per) fw.push_back({c, a, std::min(rows, a + per), 0});
+    int cch = 1;
+    if (ncell < target) cch = std::max(1, std::min((target + ncell - 1) / ncell, (cd.nI + 31) / 32));
+    int cper = ((cd.nI + cch - 1) / cch + 3) / 4 * 4;  // column chunks start on quads
+    if (cper < 4) cper = 4;
+    for (int a = 0; a < cd.nI; a += cper) bw.push_back({c, a, std::min(cd.nI, a + cper), 0});
+  }
+  D.nfwd = (int)fw.size();
+  D.nbwd = (int)bw.size();
+  D.item_target = target;
+  HIF_TRY(dev_alloc(h, (void **)&D.fwd, std::max<size_t>(1, fw.size()) * sizeof(CellItem)));
+  HIF_TRY(dev_alloc(h, (void **)&D.bwd, std::max<size_t>(1, bw.size()) * sizeof(CellItem)));
+  if (!fw.empty())
+    HIF_CUDA_TRY(cudaMemcpyAsync(D.fwd, fw.data(), fw.size() * sizeof(CellItem), cudaMemcpyHostToDevice, s));
+  if (!bw.empty())
+    HIF_CUDA_TRY(cudaMemcpyAsync(D.bwd, bw.data(), bw.size() * sizeof(CellItem), cudaMemcpyHostToDevice, s));
+  return HIF_OK;
+}
+
 int finish_device_factor(Handle *h, cudaStream_t s) {
   // thresholds of the split entity and root launches (HIFCN_SPLIT_DOFS and
   // HIFCN_ROOT_SPLIT_DOFS override them, for tests of the split paths)
@@ -167,28 +200,7 @@ int finish_device_factor(Handle *h, cudaStream_t s) {
     if (!H.groups.empty())
       HIF_CUDA_TRY(cudaMemcpyAsync(D.groups, H.groups.data(), H.groups.size() * sizeof(GroupDesc),
                                    cudaMemcpyHostToDevice, s));
-    // work items: enough CTAs per launch to cover the GPU at the upper levels
-    const int target = 152 * 4;
-    std::vector<CellItem> fw, bw;
-    for (int c = 0; c < (int)H.cells.size(); ++c) {
-      const CellDesc &cd = H.cells[c];
-      const int rows = cd.nB + cd.nI;
-      int chunks = 1;
-      if ((int)H.cells.size() < target)
-        chunks = std::max(1, std::min((target + (int)H.cells.size() - 1) / (int)H.cells.size(),
-                                      (rows + 31) / 32));
-      int per = ((rows + chunks - 1) / chunks + 31) / 32 * 32;
-      for (int a = 0; a < rows; a += per) fw.push_back({c, a, std::min(rows, a + per), 0});
-      int cch = 1;
-      if ((int)H.cells.size() < target)
-        cch = std::max(1, std::min((target + (int)H.cells.size() - 1) / (int)H.cells.size(),
-                                   (cd.nI + 31) / 32));
-      int cper = ((cd.nI + cch - 1) / cch + 3) / 4 * 4;  // column chunks start on quads
-      if (cper < 4) cper = 4;
-      for (int a = 0; a < cd.nI; a += cper) bw.push_back({c, a, std::min(cd.nI, a + cper), 0});
-    }
-    D.nfwd = (int)fw.size();
-    D.nbwd = (int)bw.size();
+    HIF_TRY(build_items(h, D, H, kDefaultItemTarget, s));
     {
       std::vector<int> sm, lg;
       for (int g = 0; g < (int)H.groups.size(); ++g) (H.groups[g].n <= 32 ? sm : lg).push_back(g);
@@ -257,8 +269,7 @@ int finish_device_factor(Handle *h, cudaStream_t s) {
       if (!tab.empty())
         HIF_CUDA_TRY(cudaMemcpyAsync(D.chunk_tab[e], tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice, s));
     }
-    HIF_TRY(dev_alloc(h, (void **)&D.fwd, std::max<size_t>(1, fw.size()) * sizeof(CellItem)));
-    HIF_TRY(dev_alloc(h, (void **)&D.bwd, std::max<size_t>(1, bw.size()) * sizeof(CellItem)));
+
     {  // whole cells, for the merged batched steps (the batch fills the GPU)
       std::vector<CellItem> f1, b1;
       for (int c = 0; c < (int)H.cells.size(); ++c) {
@@ -272,10 +283,7 @@ int finish_device_factor(Handle *h, cudaStream_t s) {
         HIF_CUDA_TRY(cudaMemcpyAsync(D.bwd1, b1.data(), b1.size() * sizeof(CellItem), cudaMemcpyHostToDevice, s));
       }
     }
-    if (!fw.empty())
-      HIF_CUDA_TRY(cudaMemcpyAsync(D.fwd, fw.data(), fw.size() * sizeof(CellItem), cudaMemcpyHostToDevice, s));
-    if (!bw.empty())
-      HIF_CUDA_TRY(cudaMemcpyAsync(D.bwd, bw.data(), bw.size() * sizeof(CellItem), cudaMemcpyHostToDevice, s));
+
   }
   HIF_TRY(dev_alloc(h, (void **)&h->f64.xI, h->N * sizeof(double)));
   long long gs_max = 0;
@@ -571,6 +579,34 @@ hif_handle::~hif_handle() {
   if (host_scal) cudaFreeHost(host_scal);
 }
 
+namespace hifcn {
+
+// Per launch device time (us) of each apply kernel name over `reps` applies.
+int time_applies(Handle *h, int reps, cudaStream_t s, std::map<std::string, double> *per_launch) {
+  const int prec = reduced_apply(h) ? (h->has_bf16 ? HIF_FP32_BF16TOP : HIF_FP32) : HIF_FP64;
+  for (int r = 0; r < 2; ++r) HIF_TRY(apply_inverse(h, h->g, h->q, prec, s));  // warm-up
+  int cnt = 0;
+  std::vector<hif_kernel_stat> st(256);
+  HIF_TRY(hif_stats_read(h, st.data(), (int)st.size(), &cnt));  // drop the warm-up records
+  for (int r = 0; r < reps; ++r) HIF_TRY(apply_inverse(h, h->g, h->q, prec, s));
+  HIF_TRY(hif_stats_read(h, st.data(), (int)st.size(), &cnt));
+  per_launch->clear();
+  for (int i = 0; i < cnt; ++i) (*per_launch)[st[i].name] = 1e3 * st[i].ms / std::max<double>(1.0, (double)st[i].launches);
+  return HIF_OK;
+}
+
+double level_cell_us(const std::map<std::string, double> &t, int l) {
+  double v = 0.0;
+  for (const char *k : {"cell_fwd_l", "cell_bwd_l"}) {
+    auto it = t.find(std::string(k) + std::to_string(l));
+    if (it != t.end()) v += it->second;
+  }
+  return v;
+}
+
+}  // namespace hifcn
+
+
 extern "C" {
 
 void hif_default_options(hif_options *opt) {
@@ -833,6 +869,70 @@ int hif_stats_read(hif_handle *h, hif_kernel_stat *out, int cap, int *count) {
     }
   *count = n < cap ? n : cap;
   return HIF_OK;
+}
+
+int hif_autotune(hif_handle *h, hif_stream stream) {
+  if (!h || !h->factor_ok) return HIF_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  HIF_CUDA_TRY(cudaGetDevice(&dev));
+  HIF_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const bool stats_was = h->stats_on;
+  h->stats_on = true;
+  const int L = h->L, reps = 5;
+  const std::vector<int> cand = {sms, 2 * sms, 4 * sms, 8 * sms, 16 * sms};
+  std::vector<std::vector<double>> t(L, std::vector<double>(cand.size(), 1e30));
+  std::map<std::string, double> per;
+  int st = HIF_OK;
+  auto set_all = [&](int target) -> int {
+    for (int l = 0; l < L; ++l) HIF_TRY(build_items(h, h->lv[l], h->lv_host[l], target, s));
+    destroy_pcg_graphs(h);
+    return build_upper_plan(h);
+  };
+  // item cut of the G-form levels (and with it, at levels whose cells no
+  // longer split, the S-form kernels): each level takes its fastest target
+  for (size_t c = 0; c < cand.size() && st == HIF_OK; ++c) {
+    st = set_all(cand[c]);
+    if (st == HIF_OK) st = time_applies(h, reps, s, &per);
+    for (int l = 0; l < L && st == HIF_OK; ++l) {
+      const double v = level_cell_us(per, l);
+      if (v > 0.0) t[l][c] = v;
+    }
+  }
+  std::vector<int> best(L, kDefaultItemTarget);
+  for (int l = 0; l < L && st == HIF_OK; ++l) {
+    size_t bi = 0;
+    for (size_t c = 1; c < cand.size(); ++c)
+      if (t[l][c] < t[l][bi]) bi = c;
+    if (t[l][bi] < 1e29) best[l] = cand[bi];
+    st = build_items(h, h->lv[l], h->lv_host[l], best[l], s);
+  }
+  // CTAs per SM of the S-form kernels
+  if (st == HIF_OK) {
+    destroy_pcg_graphs(h);
+    st = build_upper_plan(h);
+  }
+  double tbest = 1e30;
+  int cbest = 0;
+  for (int ctas : {0, 2, 3}) {
+    if (st != HIF_OK) break;
+    h->tma_ctas = ctas;
+    st = time_applies(h, reps, s, &per);
+    double v = 0.0;
+    for (int l = 0; l < L; ++l)
+      if (level_uses_sform(h, l)) v += level_cell_us(per, l);
+    if (v > 0.0 && v < tbest) {
+      tbest = v;
+      cbest = ctas;
+    }
+  }
+  h->tma_ctas = cbest;
+  destroy_pcg_graphs(h);
+  h->stats_on = stats_was;
+  int cnt = 0;
+  hif_kernel_stat drop[1];
+  hif_stats_read(h, drop, 1, &cnt);  // leave no tuning records behind
+  return st;
 }
 
 int64_t hif_launch_count(void) { return (int64_t)g_launches.load(); }

@@ -1345,11 +1345,19 @@ size_t tma_fwd_smem_elems(const LevelDev &lv) {
   return 2 * (size_t)pad4(lv.max_nI) + 8 * (size_t)pad4(lv.max_nB);
 }
 
-bool level_sform(const Handle *h, const LevelDev &lv) {
-  if (!h->use_tma || lv.ncells == 0 || lv.nfwd != lv.ncells || lv.nbwd != lv.ncells) return false;
-  if (lv.max_chunks < 0 || lv.max_chunks > kMaxChunks || pad4(lv.max_nI) > 256) return false;
+// A level whose blocks fit the S-form kernels (rows within a stage, at most
+// kMaxChunks chunks per cell, nI <= 256, shared memory within the limit).
+bool sform_capable(const LevelDev &lv) {
+  if (lv.ncells == 0 || lv.max_chunks < 0 || lv.max_chunks > kMaxChunks || pad4(lv.max_nI) > 256)
+    return false;
   const size_t bwd_smem = (size_t)kStages * kStageBytes + tma_bwd_smem_elems(lv) * sizeof(float);
   return bwd_smem <= 200 * 1024;
+}
+
+// The level is applied by the S-form kernels: capable, S stored, and its
+// cells not cut into several items.
+bool level_sform(const Handle *h, const LevelDev &lv) {
+  return h->use_tma && lv.has_S && lv.nfwd == lv.ncells && lv.nbwd == lv.ncells && sform_capable(lv);
 }
 
 bool use_tma(const Handle *h, const LevelDev &lv, size_t elem) {
@@ -1358,7 +1366,7 @@ bool use_tma(const Handle *h, const LevelDev &lv, size_t elem) {
 
 // Grid of the persistent TMA-staged cell kernels: the CTAs that fit on the
 // GPU at once (HIFCN_TMA_CTAS overrides the CTAs per SM), at most one per cell.
-int tma_grid(const void *fn, size_t smem, int ncells) {
+int tma_grid(const void *fn, size_t smem, int ncells, int ctas_per_sm) {
   static int sms = 0;
   if (sms == 0) {
     int dev = 0;
@@ -1372,6 +1380,7 @@ int tma_grid(const void *fn, size_t smem, int ncells) {
   }
   const char *e = std::getenv("HIFCN_TMA_CTAS");
   if (e && std::atoi(e) > 0) occ = std::min(occ, std::atoi(e));
+  if (ctas_per_sm > 0) occ = std::min(occ, ctas_per_sm);
   occ = std::max(occ, 1);
   return std::max(1, std::min(ncells, sms * occ));
 }
@@ -1407,7 +1416,7 @@ int launch_cell_fwd(Handle *h, const LevelDev &lv, int l, const FactorValues<T> 
   }
   if (sf) {
     size_t sm = (size_t)kStages * kStageBytes + tma_fwd_smem_elems(lv) * sizeof(T);
-    const int grid = tma_grid((const void *)k_cell_fwd_tma_S<T>, sm, lv.ncells);
+    const int grid = tma_grid((const void *)k_cell_fwd_tma_S<T>, sm, lv.ncells, h->tma_ctas);
     k_cell_fwd_tma_S<T><<<grid, kTmaThreads, sm, s>>>(lv.cells, lv.ncells, lv.chunk_of[0], lv.chunk_tab[0],
                                                        h->idx, fv.vals, fv.contrib, x,
                                                        h->scal + kScalErr, lv.max_nI, lv.max_nB);
@@ -1529,7 +1538,7 @@ int launch_cell_bwd(Handle *h, const LevelDev &lv, int l, const FactorValues<T> 
   }
   if (sf) {
     size_t sm = (size_t)kStages * kStageBytes + tma_bwd_smem_elems(lv) * sizeof(T);
-    const int grid = tma_grid((const void *)k_cell_bwd_tma_S<T>, sm, lv.ncells);
+    const int grid = tma_grid((const void *)k_cell_bwd_tma_S<T>, sm, lv.ncells, h->tma_ctas);
     k_cell_bwd_tma_S<T><<<grid, kTmaThreads, sm, s>>>(lv.cells, lv.ncells, lv.chunk_of[1], lv.chunk_tab[1],
                                                        h->idx, fv.vals, x,
                                                        h->scal + kScalErr, lv.max_nI, lv.max_nB);
@@ -1703,6 +1712,10 @@ int upper_launch_shape(Handle *h, size_t smem, int max_units) {
 }
 
 }  // namespace
+
+bool level_uses_sform(const Handle *h, int l) {
+  return h->has_f32 && l >= 0 && l < h->L && use_tma(h, h->lv[l], sizeof(float)) && !bf16_level<float>(h, l);
+}
 
 // The device view of a handle for the merged batched steps (FP32 apply
 // only; handles with split levels, a split root or more than
@@ -1929,10 +1942,11 @@ int apply_inplace_f64_with_scratch(Handle *h, double *contrib, double *x, cudaSt
 // S = G^T G of the cells of the levels the FP32 S-form kernels will apply.
 int make_cell_inverses(Handle *h, cudaStream_t s) {
   if (h->opt.precision != HIF_FP32 && h->opt.precision != HIF_FP32_BF16TOP) return HIF_OK;
-  for (const LevelDev &lv : h->lv) {
-    if (!level_sform(h, lv)) continue;
+  for (LevelDev &lv : h->lv) {
+    if (!h->use_tma || !sform_capable(lv)) continue;
     k_make_S<<<lv.ncells, 256, 0, s>>>(lv.cells, h->f64.vals);
     note_launch();
+    lv.has_S = true;
   }
   HIF_CUDA_TRY(cudaGetLastError());
   return HIF_OK;

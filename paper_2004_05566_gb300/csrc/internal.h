@@ -62,6 +62,9 @@ constexpr int kStageBytes = 15872;  // 124 x 128 B: three backward CTAs fit an S
 // Separator entities above this size are applied split over many CTAs, and
 // roots above kRootSplitDofs by a row-block and a column-block launch.
 constexpr int kSplitDofs = 256;
+// default CTAs per launch the G-form cell items are cut for (hif_autotune
+// picks per level among multiples of the SM count)
+constexpr int kDefaultItemTarget = 152 * 4;
 constexpr int kRootSplitDofs = 512;
 constexpr int kSplitRows = 32;   // rows of H per CTA (forward)
 constexpr int kSplitCols = 64;   // columns of H per CTA (backward)
@@ -104,6 +107,8 @@ struct LevelDev {
   int nfwd = 0, nbwd = 0;             // work items of the cell kernels
   CellItem *fwd = nullptr, *bwd = nullptr;  // device
   CellItem *fwd1 = nullptr, *bwd1 = nullptr;  // device: one item per cell (merged batched steps)
+  int item_target = 0;                // CTAs per launch the items were cut for (see build_items)
+  bool has_S = false;                 // S = A_II^{-1} stored for the cells (S-form possible)
   // bulk-copy chunk tables of the FP32 cell blocks (row boundaries): cell c's
   // chunks are rows [tab[o + k], tab[o + k + 1]) for k < n, (o, n) = of[c];
   // [0]: the V rows, [1]: the S rows followed by the V rows
@@ -246,6 +251,7 @@ struct hif_handle {
   hifcn::UpperLevel *upper_levels = nullptr;  // device
   void *upper_rt = nullptr;                   // device root scratch (root_n doubles)
   bool root_split = false;                    // root applied by row- and column-block launches
+  int tma_ctas = 0;                           // CTAs per SM of the leaf kernels (0: as many as fit)
   hifcn::HandleView *view = nullptr;          // device view for the merged batched steps
   bool view_ok = false;                       // the merged batched path can take this handle
   size_t upper_smem[2] = {0, 0};              // dynamic shared memory, FP64 / FP32
@@ -314,7 +320,9 @@ int stencil_matvec(Handle *h, const double *x, double *y, cudaStream_t s);
 int build_device_factor(Handle *h, const std::vector<double> &vals64, cudaStream_t s);
 int apply_inverse(Handle *h, const double *x, double *y, int precision, cudaStream_t s);
 int build_upper_plan(Handle *h);
+bool level_uses_sform(const Handle *h, int l);
 int build_view(Handle *h);
+int build_items(Handle *h, LevelDev &D, const LevelHost &H, int target, cudaStream_t s);
 void merged_units(const Handle *h, int kind, int level, int *units, size_t *smem);
 int launch_merged_phase(int kind, int level, const int *pre, int K, int total, size_t smem,
                         HandleView *const *views, const int *active, cudaStream_t s);

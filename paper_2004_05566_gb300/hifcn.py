@@ -28,7 +28,7 @@ EXPORTED = ("hif_default_options", "hif_setup", "hif_import_factor", "hif_export
             "hif_apply", "hif_matvec", "pcg_solve", "cn_step", "hif_set_reaction", "hif_query",
             "hif_destroy", "hif_strerror", "hif_last_error", "hif_stats_enable", "hif_stats_read",
             "hif_launch_count", "hif_apply_noalloc", "cn_step_batched", "hif_set_coefficient",
-            "hif_refactor")
+            "hif_refactor", "hif_autotune")
 
 
 class HifGrid(ctypes.Structure):
@@ -100,6 +100,8 @@ def lib():
     L.hif_set_coefficient.restype = c_int
     L.hif_refactor.argtypes = [c_void_p, c_void_p, c_void_p]
     L.hif_refactor.restype = c_int
+    L.hif_autotune.argtypes = [c_void_p, c_void_p]
+    L.hif_autotune.restype = c_int
     for name in ("hif_setup", "hif_import_factor", "hif_export_factor", "hif_apply", "hif_matvec",
                  "pcg_solve", "cn_step", "hif_set_reaction", "hif_query", "hif_destroy",
                  "hif_stats_enable", "hif_stats_read"):
@@ -293,6 +295,11 @@ def hif_refactor(h: Handle, a_nodes: torch.Tensor, stream=None):
     """Replace a(x) and factor the new operator in place."""
     a = _vec(a_nodes.reshape(-1), (h.n + 1) ** h.dim, "a_nodes")
     _check("hif_refactor", lib().hif_refactor(h.ptr, a, _stream(stream)))
+
+
+def hif_autotune(h: Handle, stream=None):
+    """Pick the per-level CTA cut of the apply and the leaf kernels' CTAs per SM by timing."""
+    _check("hif_autotune", lib().hif_autotune(h.ptr, _stream(stream)))
 
 
 def hif_set_reaction(h: Handle, kind: int, k1: float = 1.0, k2: float = math.inf):
