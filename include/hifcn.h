@@ -96,6 +96,8 @@ typedef struct {
   int64_t device_bytes;   /* device memory the handle holds                                */
   int precision;
   double setup_seconds;   /* wall time of the last hif_setup / import                      */
+  int sform_levels;       /* bit l set: the FP32 apply runs level l's cell steps in the
+                             S-form (S = A_II^{-1} streamed by the bulk-copy kernels)       */
 } hif_info;
 
 /* ---------------------------------------------------------------------------

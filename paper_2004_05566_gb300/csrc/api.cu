@@ -200,7 +200,11 @@ int finish_device_factor(Handle *h, cudaStream_t s) {
     if (!H.groups.empty())
       HIF_CUDA_TRY(cudaMemcpyAsync(D.groups, H.groups.data(), H.groups.size() * sizeof(GroupDesc),
                                    cudaMemcpyHostToDevice, s));
-    HIF_TRY(build_items(h, D, H, kDefaultItemTarget, s));
+    // HIFCN_ITEM_TARGET overrides the CTAs per launch the cells are cut for
+    // (1: cells are never cut, so every level that fits runs the S-form kernels)
+    int target = kDefaultItemTarget;
+    if (const char *e = std::getenv("HIFCN_ITEM_TARGET")) target = std::max(1, std::atoi(e));
+    HIF_TRY(build_items(h, D, H, target, s));
     {
       std::vector<int> sm, lg;
       for (int g = 0; g < (int)H.groups.size(); ++g) (H.groups[g].n <= 32 ? sm : lg).push_back(g);
@@ -236,7 +240,8 @@ int finish_device_factor(Handle *h, cudaStream_t s) {
       }
     }
     // chunk tables for the bulk-copy staged FP32 kernels: consecutive whole
-    // rows of at most kStageBytes; [0] the V rows, [1] the S rows then the V rows
+    // rows of at most kStageBytes; [0] the V rows, [1] the S rows then the V
+    // rows (a chunk holds rows of one of the two only)
     for (int e = 0; e < 2; ++e) {
       const long long cap = kStageBytes / 4;
       std::vector<int2> of;
@@ -253,7 +258,7 @@ int finish_device_factor(Handle *h, cudaStream_t s) {
         while (ok && r < nrows) {
           const long long start = roff(r);
           int en = r + 1;
-          while (en < nrows && roff(en + 1) - start <= cap) ++en;
+          while (en < nrows && en != nt && roff(en + 1) - start <= cap) ++en;
           tab.push_back(en);
           ++o.y;
           r = en;
@@ -802,6 +807,10 @@ int hif_query(const hif_handle *hh, hif_info *info) {
   info->device_bytes = h->device_bytes;
   info->precision = h->opt.precision;
   info->setup_seconds = h->setup_seconds;
+  info->sform_levels = 0;
+  const int fused_lb = (h->use_upper && h->upper_grid[1] > 0) ? h->upper_lb : h->L;
+  for (int l = 0; l < std::min(h->L, fused_lb) && l < 31; ++l)
+    if (level_uses_sform(h, l)) info->sform_levels |= 1 << l;
   return HIF_OK;
 }
 

@@ -64,6 +64,9 @@ __device__ __forceinline__ void ld4(const __nv_bfloat16 *p, float (&o)[4]) {
   o[2] = __uint_as_float(v.y << 16);
   o[3] = __uint_as_float(v.y & 0xffff0000u);
 }
+__device__ __forceinline__ void st4(float *p, const float (&v)[4]) {
+  *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
 
 // one factor value in the arithmetic type T
 template <typename T>
@@ -641,7 +644,7 @@ __device__ __forceinline__ void produce_cells(int ncells, const T *__restrict__ 
                                               unsigned char *stage, int2 *meta, const CellMeta *cm,
                                               unsigned long long *ready, unsigned long long *full,
                                               unsigned long long *empty, double *err) {
-  long long k = 0;  // running chunk counter of this CTA
+  int k = 0;  // running chunk counter of this CTA
   int jc = 0;
   for (int ci = blockIdx.x; ci < ncells; ci += gridDim.x, ++jc) {
     const int bb = jc & 1;
@@ -672,39 +675,87 @@ __device__ __forceinline__ void produce_cells(int ncells, const T *__restrict__ 
 
 // Gather warp: for each cell of the CTA, into buffer b = (cell count) & 1:
 // the cell descriptor and chunk bounds, x at the interior DOFs (zero padded to
-// pad4(nI)) and, when xb is given, x at the boundary DOFs; every lane arrives
-// on ready[b].  Before refilling a buffer it waits until the consumers freed it.
+// pad4(nI)), when is0 is given the interior DOF numbers themselves, and when
+// xb0 is given x at the boundary DOFs; every lane arrives on ready[b].
+// Before refilling a buffer it waits until the consumers freed it.
 template <typename T>
 __device__ __forceinline__ void gather_cells(const CellDesc *__restrict__ cells, int ncells,
                                              const int2 *__restrict__ chunk_of,
                                              const int *__restrict__ chunk_tab,
                                              const int *__restrict__ idx, const T *__restrict__ x,
                                              CellMeta *cm, T *xs0, long long xs_stride, T *xb0,
-                                             long long xb_stride, unsigned long long *ready,
+                                             long long xb_stride, int *is0, unsigned long long *ready,
                                              unsigned long long *freed, double *err) {
   const int lane = threadIdx.x & 31;
   int jc = 0;
+  // the next cell's descriptor is loaded while the current one is gathered
+  CellDesc c_next{};
+  int2 co_next{0, 0};
+  if (blockIdx.x < (unsigned)ncells) {
+    c_next = cells[blockIdx.x];
+    co_next = chunk_of[blockIdx.x];
+  }
   for (int ci = blockIdx.x; ci < ncells; ci += gridDim.x, ++jc) {
     const int b = jc & 1;
+    const CellDesc c = c_next;
+    const int2 co = co_next;
+    if (ci + (int)gridDim.x < ncells) {
+      c_next = cells[ci + gridDim.x];
+      co_next = chunk_of[ci + gridDim.x];
+    }
     if (jc >= 2 && !mbar_wait(&freed[b], (unsigned)(((jc >> 1) - 1) & 1))) {
       if (lane == 0) err[0] = 1.0;
       return;
     }
-    const CellDesc c = cells[ci];
-    const int2 co = chunk_of[ci];
     if (lane == 0) {
       cm[b].c = c;
       cm[b].nch = co.y;
     }
     for (int j = lane; j <= co.y; j += 32) cm[b].cs[j] = chunk_tab[co.x + j];
+    // gathers in batches of kG per lane: all index loads, then all value loads
+    constexpr int kG = 4;
     const int nIp = (int)pad4(c.nI);
     const int *I = idx + c.I_off;
     T *xs = xs0 + b * xs_stride;
-    for (int i = lane; i < nIp; i += 32) xs[i] = i < c.nI ? x[I[i]] : T(0);
+    int *is = is0 ? is0 + b * xs_stride : nullptr;
+    for (int base = 0; base < nIp; base += 32 * kG) {
+      int id[kG];
+#pragma unroll
+      for (int k = 0; k < kG; ++k) {
+        const int i = base + 32 * k + lane;
+        id[k] = i < c.nI ? I[i] : -1;
+      }
+      T v[kG];
+#pragma unroll
+      for (int k = 0; k < kG; ++k) v[k] = id[k] >= 0 ? x[id[k]] : T(0);
+#pragma unroll
+      for (int k = 0; k < kG; ++k) {
+        const int i = base + 32 * k + lane;
+        if (i < nIp) {
+          xs[i] = v[k];
+          if (is) is[i] = id[k];
+        }
+      }
+    }
     if (xb0) {
       const int *B = idx + c.B_off;
       T *xb = xb0 + b * xb_stride;
-      for (int q = lane; q < c.nB; q += 32) xb[q] = x[B[q]];
+      for (int base = 0; base < c.nB; base += 32 * kG) {
+        int id[kG];
+#pragma unroll
+        for (int k = 0; k < kG; ++k) {
+          const int q = base + 32 * k + lane;
+          id[k] = q < c.nB ? B[q] : -1;
+        }
+        T v[kG];
+#pragma unroll
+        for (int k = 0; k < kG; ++k) v[k] = id[k] >= 0 ? x[id[k]] : T(0);
+#pragma unroll
+        for (int k = 0; k < kG; ++k) {
+          const int q = base + 32 * k + lane;
+          if (q < c.nB) xb[q] = v[k];
+        }
+      }
     }
     mbar_arrive(&ready[b]);
   }
@@ -712,19 +763,26 @@ __device__ __forceinline__ void gather_cells(const CellDesc *__restrict__ cells,
 
 // ---------------------------------------------------- symmetric inverse of A_II
 //
-// S = A_II^{-1} = L^{-T} L^{-1} = G^T G (packed lower), built once per factor
-// in FP64 from the stored G: S_ij = sum_{k >= i} G_ki G_kj for j <= i.
+// S = A_II^{-1} = L^{-T} L^{-1} = G^T G, built once per factor in FP64 from
+// the stored G: S_ij = sum_{k >= i} G_ki G_kj for j <= i.  Stored as the
+// packed lower triangle with the diagonal halved (S_ii / 2) and the padding
+// of each row's last quad set to zero, the form the backward S-form kernel
+// reads (its row dots and column sums each take half of the diagonal).
 __global__ void __launch_bounds__(256) k_make_S(const CellDesc *__restrict__ cells,
                                                 double *__restrict__ vals) {
   const CellDesc c = cells[blockIdx.x];
   const double *G = vals + c.G_off;
   double *S = vals + c.S_off;
   for (int i = 0; i < c.nI; ++i) {
-    for (int j = threadIdx.x; j <= i; j += 256) {
+    const int jend = 4 * (i >> 2) + 3;
+    for (int j = threadIdx.x; j <= jend; j += 256) {
       double acc = 0.0;
-      for (int k = i; k < c.nI; ++k) {
-        const double *row = G + tri_off(k);
-        acc += row[i] * row[j];
+      if (j <= i) {
+        for (int k = i; k < c.nI; ++k) {
+          const double *row = G + tri_off(k);
+          acc += row[i] * row[j];
+        }
+        if (j == i) acc *= 0.5;
       }
       S[tri_off(i) + j] = acc;
     }
@@ -736,52 +794,77 @@ __global__ void __launch_bounds__(256) k_make_S(const CellDesc *__restrict__ cel
 // c_B = V x_I (x_I is left as it is), and the backward sweep forms
 // x_I <- S x_I - V^T x_B with S = A_II^{-1} = G^T G, which equals
 // G^T (G x_I) - V^T x_B.  S is read once instead of G twice.
+//
+// Consumer layout.  The rows of a staged chunk are taken in pairs; pair p of
+// the CTA's running pair count goes to consumer warp p mod 8, so the warps
+// stay balanced across chunks whatever their row counts.  Within a pair,
+// lane l owns the column quads l and l + 32 (rows have at most 64 quads,
+// nI <= 256) and holds x at those columns in registers for the whole cell.
+// One shared-memory read of a quad feeds both products the backward sweep
+// needs from a stored lower-triangle row of S: the row dot (L + D/2) x and
+// the column sums (L + D/2)^T x; with the diagonal stored halved, their sum
+// is (L + D + L^T) x = S x and no element needs masking.  A pair's two row
+// dots are summed over the warp in one reduce-scatter (5 shuffles).
+constexpr int kPairWarps = kConsumerWarps;
 
-// Consumer layout of the S-form kernels.  Row dots (a row of the chunk times
-// x) are split the other way round from the usual warp-per-row form: lane l
-// takes row (first row of the chunk) + l (+32, ...), and warp w the column
-// quads [w*kQuadsPerWarp, (w+1)*kQuadsPerWarp) of every row, so no row needs
-// a cross-lane reduction; each warp leaves one partial per row in shared
-// memory, and the 8 partials of a row are added once per cell, in warp order.
-// Rows have at most 64 quads (nI <= 256), so 8 quads per warp cover them.
-constexpr int kQuadsPerWarp = 8;
-
-// partial dot of `row` (quads [q0, q1)) with the shared vector xs
+// sum over the 32 lanes of a (lanes 0-15 get it) and of b (lanes 16-31)
 template <typename T>
-__device__ __forceinline__ T quad_range_dot(const T *row, const T *xs, int q0, int q1) {
-  T acc = T(0);
-#pragma unroll 4
-  for (int q = q0; q < q1; ++q) {
-    T v[4], xv[4];
-    ld4(row + 4 * q, v);
-    ld4(xs + 4 * q, xv);
-    acc += v[0] * xv[0] + v[1] * xv[1] + v[2] * xv[2] + v[3] * xv[3];
-  }
-  return acc;
+__device__ __forceinline__ T pair_total(T a, T b, int lane) {
+  const bool hi = (lane & 16) != 0;
+  T keep = hi ? b : a;
+  const T send = hi ? a : b;
+  keep += __shfl_xor_sync(0xffffffffu, send, 16);
+  keep += __shfl_xor_sync(0xffffffffu, keep, 8);
+  keep += __shfl_xor_sync(0xffffffffu, keep, 4);
+  keep += __shfl_xor_sync(0xffffffffu, keep, 2);
+  keep += __shfl_xor_sync(0xffffffffu, keep, 1);
+  return keep;
 }
+
+template <typename T>
+__device__ __forceinline__ T dot4(const T (&v)[4], const T (&x)[4]) {
+  return v[0] * x[0] + v[1] * x[1] + v[2] * x[2] + v[3] * x[3];
+}
+
+template <typename T>
+__device__ __forceinline__ void axpy4(T (&acc)[4], const T (&v)[4], T s) {
+  acc[0] += v[0] * s; acc[1] += v[1] * s; acc[2] += v[2] * s; acc[3] += v[3] * s;
+}
+
+// x at the column quads lane and lane + 32 of a cell with nq quads (zero beyond)
+template <typename T>
+__device__ __forceinline__ void load_xcols(const T *xs, int nq, int lane, T (&xa)[4], T (&xb)[4]) {
+#pragma unroll
+  for (int e = 0; e < 4; ++e) xa[e] = xb[e] = T(0);
+  if (lane < nq) ld4(xs + 4 * lane, xa);
+  if (lane + 32 < nq) ld4(xs + 4 * (lane + 32), xb);
+}
+
+// first pair of a chunk that warp w takes, given the running pair count u (mod 8)
+__device__ __forceinline__ int first_pair(int warp, int u) { return (warp - u) & (kPairWarps - 1); }
 
 // forward: contributions c_B = V x_I, streaming the V rows.  Persistent: a
 // CTA takes cells blockIdx.x, blockIdx.x + gridDim.x, ...; warp 8 copies the
-// V rows, warp 9 gathers x_I of the next cell, warps 0-7 compute.
+// V rows, warp 9 gathers x_I of the next cell, warps 0-7 compute and write
+// each row's total straight to the contribution buffer.
 template <typename T>
-__global__ void __launch_bounds__(kTmaThreads) k_cell_fwd_tma_S(const CellDesc *__restrict__ cells,
-                                                                int ncells,
-                                                                const int2 *__restrict__ chunk_of,
-                                                                const int *__restrict__ chunk_tab,
-                                                                const int *__restrict__ idx,
-                                                                const T *__restrict__ vals,
-                                                                T *__restrict__ contrib,
-                                                                const T *__restrict__ x,
-                                                                double *__restrict__ err,
-                                                                int max_nI, int max_nB) {
+__global__ void __launch_bounds__(kTmaThreads, 4) k_cell_fwd_tma_S(const CellDesc *__restrict__ cells,
+                                                                   int ncells,
+                                                                   const int2 *__restrict__ chunk_of,
+                                                                   const int *__restrict__ chunk_tab,
+                                                                   const int *__restrict__ idx,
+                                                                   const T *__restrict__ vals,
+                                                                   T *__restrict__ contrib,
+                                                                   const T *__restrict__ x,
+                                                                   double *__restrict__ err,
+                                                                   int max_nI, int max_nB) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) unsigned long long full[kStages], empty[kStages], ready[2], freed[2];
   __shared__ int2 meta[kStages];
   __shared__ CellMeta cm[2];
   unsigned char *stage = smem_raw;
-  const long long xstride = pad4(max_nI), pstride = pad4(max_nB);
+  const long long xstride = pad4(max_nI);
   T *xs0 = reinterpret_cast<T *>(smem_raw + (size_t)kStages * kStageBytes);  // 2 x pad4(max_nI)
-  T *rd = xs0 + 2 * xstride;                                                  // 8 x pad4(max_nB)
   if (threadIdx.x == 0) {
     for (int k = 0; k < kStages; ++k) {
       mbar_init(&full[k], 1);
@@ -801,12 +884,12 @@ __global__ void __launch_bounds__(kTmaThreads) k_cell_fwd_tma_S(const CellDesc *
     return;
   }
   if (warp == kConsumerWarps + 1) {
-    gather_cells<T>(cells, ncells, chunk_of, chunk_tab, idx, x, cm, xs0, xstride, nullptr, 0, ready,
-                    freed, err);
+    gather_cells<T>(cells, ncells, chunk_of, chunk_tab, idx, x, cm, xs0, xstride, nullptr, 0, nullptr,
+                    ready, freed, err);
     return;
   }
-  const int q0 = warp * kQuadsPerWarp;
-  long long k = 0;  // running chunk counter, as in the copy warp
+  int k = 0;  // running chunk counter, as in the copy warp
+  int u = 0;        // running pair count (mod 8)
   int jc = 0;
   for (int ci = blockIdx.x; ci < ncells; ci += gridDim.x, ++jc) {
     const int b = jc & 1;
@@ -816,11 +899,11 @@ __global__ void __launch_bounds__(kTmaThreads) k_cell_fwd_tma_S(const CellDesc *
     }
     const CellDesc c = cm[b].c;
     const int nch = cm[b].nch;
-    const T *xs = xs0 + b * xstride;
     const int nq = (int)pad4(c.nI) / 4;
-    const int q1 = min(nq, q0 + kQuadsPerWarp);
-    const long long vs = 4LL * nq;
-    consumers_sync();  // the previous cell's partials are read
+    const int vs = 4 * nq;
+    T xa[4], xb[4];
+    load_xcols(xs0 + b * xstride, nq, lane, xa, xb);
+    T *out = contrib + c.C_off;
     for (int j = 0; j < nch; ++j, ++k) {
       const int sidx = (int)(k % kStages);
       if (!mbar_wait(&full[sidx], (unsigned)((k / kStages) & 1))) {
@@ -829,50 +912,70 @@ __global__ void __launch_bounds__(kTmaThreads) k_cell_fwd_tma_S(const CellDesc *
       }
       const T *base = reinterpret_cast<const T *>(stage + (size_t)sidx * kStageBytes);
       const int2 rr = meta[sidx];
-      for (int r = rr.x + lane; r < rr.y; r += 32)
-        rd[warp * pstride + r] = q0 < q1 ? quad_range_dot(base + (long long)(r - rr.x) * vs, xs, q0, q1) : T(0);
+      const int np = (rr.y - rr.x + 1) >> 1;
+      for (int p = first_pair(warp, u); p < np; p += kPairWarps) {
+        const int r0 = rr.x + 2 * p;
+        const bool has1 = r0 + 1 < rr.y;
+        const T *row0 = base + 2 * p * vs;
+        T p0 = T(0), p1 = T(0);
+        if (lane < nq) {
+          T v[4];
+          ld4(row0 + 4 * lane, v);
+          p0 = dot4(v, xa);
+          if (has1) {
+            ld4(row0 + vs + 4 * lane, v);
+            p1 = dot4(v, xa);
+          }
+        }
+        if (lane + 32 < nq) {
+          T v[4];
+          ld4(row0 + 4 * (lane + 32), v);
+          p0 += dot4(v, xb);
+          if (has1) {
+            ld4(row0 + vs + 4 * (lane + 32), v);
+            p1 += dot4(v, xb);
+          }
+        }
+        const T t = pair_total(p0, p1, lane);
+        if (lane == 0) out[r0] = t;
+        if (lane == 16 && has1) out[r0 + 1] = t;
+      }
+      u = (u + np) & (kPairWarps - 1);
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[sidx]);
     }
     __syncwarp();
-    if (lane == 0) mbar_arrive(&freed[b]);
-    consumers_sync();
-    for (int r = threadIdx.x; r < c.nB; r += kConsumers) {
-      T sum = rd[r];
-#pragma unroll
-      for (int w = 1; w < kConsumerWarps; ++w) sum += rd[w * pstride + r];
-      contrib[c.C_off + r] = sum;
-    }
+    if (lane == 0) mbar_arrive(&freed[b]);  // x_I of this buffer is no longer read
   }
 }
 
-// backward: x_I <- S x_I - V^T x_B, streaming the S rows then the V rows.
-// With S = L + D + L^T stored as its lower triangle by rows: the row dots
-// (L + D) x as in the forward kernel (lane per row, warp per quad range,
-// partials per warp), and the column sums L^T x - V^T x_B by lane-owned
-// column quads (p, nq - 1 - p) over the rows r = w (mod 8) of warp w, with
-// the diagonal masked out; both meet once per cell.  Persistent like the
-// forward kernel, with the same copy and gather warps.
+// backward: x_I <- S x_I - V^T x_B, streaming the S rows (stored lower
+// triangle with the diagonal halved, a chunk never mixes S and V rows) then
+// the V rows.  Per pair of S rows: row dots into rd (one warp owns a row),
+// column sums into the lane-owned accumulators; V rows add -V^T x_B to the
+// same accumulators.  At the end of the cell the 8 warps' column sums and
+// the row dots meet: x[I[i]] = rd[i] + sum_w part_w[i].
 template <typename T>
-__global__ void __launch_bounds__(kTmaThreads) k_cell_bwd_tma_S(const CellDesc *__restrict__ cells,
-                                                                int ncells,
-                                                                const int2 *__restrict__ chunk_of,
-                                                                const int *__restrict__ chunk_tab,
-                                                                const int *__restrict__ idx,
-                                                                const T *__restrict__ vals,
-                                                                T *__restrict__ x,
-                                                                double *__restrict__ err,
-                                                                int max_nI, int max_nB) {
+__global__ void __launch_bounds__(kTmaThreads, 4) k_cell_bwd_tma_S(const CellDesc *__restrict__ cells,
+                                                                   int ncells,
+                                                                   const int2 *__restrict__ chunk_of,
+                                                                   const int *__restrict__ chunk_tab,
+                                                                   const int *__restrict__ idx,
+                                                                   const T *__restrict__ vals,
+                                                                   T *__restrict__ x,
+                                                                   double *__restrict__ err,
+                                                                   int max_nI, int max_nB) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) unsigned long long full[kStages], empty[kStages], ready[2], freed[2];
   __shared__ int2 meta[kStages];
   __shared__ CellMeta cm[2];
   unsigned char *stage = smem_raw;
   const long long xstride = pad4(max_nI), bstride = pad4(max_nB);
-  T *part = reinterpret_cast<T *>(smem_raw + (size_t)kStages * kStageBytes);  // 8 * kConsumers
-  T *rd = part + 8 * kConsumers;     // 8 x pad4(max_nI): row-dot partials
-  T *xs0 = rd + 8 * xstride;         // 2 x pad4(max_nI)
-  T *xb0 = xs0 + 2 * xstride;        // 2 x pad4(max_nB)
+  T *part = reinterpret_cast<T *>(smem_raw + (size_t)kStages * kStageBytes);  // 8 x pad4(max_nI)
+  T *rd = part + kConsumerWarps * xstride;  // pad4(max_nI): row dots
+  T *xs0 = rd + xstride;                    // 2 x pad4(max_nI)
+  T *xb0 = xs0 + 2 * xstride;               // 2 x pad4(max_nB)
+  int *is0 = reinterpret_cast<int *>(xb0 + 2 * bstride);  // 2 x pad4(max_nI): I of the cell
   if (threadIdx.x == 0) {
     for (int k = 0; k < kStages; ++k) {
       mbar_init(&full[k], 1);
@@ -892,12 +995,12 @@ __global__ void __launch_bounds__(kTmaThreads) k_cell_bwd_tma_S(const CellDesc *
     return;
   }
   if (warp == kConsumerWarps + 1) {
-    gather_cells<T>(cells, ncells, chunk_of, chunk_tab, idx, x, cm, xs0, xstride, xb0, bstride, ready,
-                    freed, err);
+    gather_cells<T>(cells, ncells, chunk_of, chunk_tab, idx, x, cm, xs0, xstride, xb0, bstride, is0,
+                    ready, freed, err);
     return;
   }
-  const int q0 = warp * kQuadsPerWarp;
-  long long k = 0;  // running chunk counter, as in the copy warp
+  int k = 0;  // running chunk counter, as in the copy warp
+  int u = 0;        // running pair count (mod 8)
   int jc = 0;
   for (int ci = blockIdx.x; ci < ncells; ci += gridDim.x, ++jc) {
     const int b = jc & 1;
@@ -907,16 +1010,15 @@ __global__ void __launch_bounds__(kTmaThreads) k_cell_bwd_tma_S(const CellDesc *
     }
     const CellDesc c = cm[b].c;
     const int nch = cm[b].nch;
+    const int nI = c.nI;
     const T *xs = xs0 + b * xstride;
-    const T *xb = xb0 + b * bstride;
-    const int nIp = (int)pad4(c.nI);
-    const long long vs = nIp;
+    const T *xbv = xb0 + b * bstride;
+    const int nq = (int)pad4(nI) / 4;
+    const int vs = 4 * nq;
+    T xa[4], xb[4];
+    load_xcols(xs, nq, lane, xa, xb);
+    T ca[4] = {T(0), T(0), T(0), T(0)}, cb[4] = {T(0), T(0), T(0), T(0)};
     consumers_sync();  // rd and part of the previous cell are no longer read
-    const int nq = nIp / 4;
-    const int qa = lane, qb = nq - 1 - lane;  // one warp covers all column pairs (nq <= 64)
-    const bool okA = qa < (nq + 1) / 2;
-    const bool okB = okA && qb > qa;
-    T aA[4] = {T(0), T(0), T(0), T(0)}, aB[4] = {T(0), T(0), T(0), T(0)};
     for (int j = 0; j < nch; ++j, ++k) {
       const int sidx = (int)(k % kStages);
       if (!mbar_wait(&full[sidx], (unsigned)((k / kStages) & 1))) {
@@ -925,79 +1027,90 @@ __global__ void __launch_bounds__(kTmaThreads) k_cell_bwd_tma_S(const CellDesc *
       }
       const T *base = reinterpret_cast<const T *>(stage + (size_t)sidx * kStageBytes);
       const int2 rr = meta[sidx];
-      const int rb = rr.x, re = rr.y;
-      const long long off0 = cell_row_off(rb, c.nI, vs);
-      // column sums over the rows r = warp (mod 8)
-      for (int r = rb + ((warp - rb % kConsumerWarps) % kConsumerWarps + kConsumerWarps) % kConsumerWarps;
-           r < re; r += kConsumerWarps) {
-        const T *row = base + (cell_row_off(r, c.nI, vs) - off0);
-        if (r < c.nI) {
-          const T xr = xs[r];
-          const int qd = r >> 2;  // quad holding the diagonal
-          if (okA && qa <= qd) {
+      const int np = (rr.y - rr.x + 1) >> 1;
+      if (rr.x < nI) {  // rows of S
+        const int off0 = (int)tri_off(rr.x);
+        for (int p = first_pair(warp, u); p < np; p += kPairWarps) {
+          const int r0 = rr.x + 2 * p;
+          const bool has1 = r0 + 1 < rr.y;
+          const int nq0 = (r0 >> 2) + 1, nq1 = has1 ? ((r0 + 1) >> 2) + 1 : 0;
+          const T *row0 = base + ((int)tri_off(r0) - off0);
+          const T *row1 = row0 + 4 * nq0;  // rows of quad row q hold q + 1 quads
+          const T x0 = xs[r0], x1 = xs[r0 + 1];  // x1 is used only when has1
+          T p0 = T(0), p1 = T(0);
+          if (lane < nq0) {
             T v[4];
-            ld4(row + 4 * qa, v);
-            if (qa == qd) {
-#pragma unroll
-              for (int e = 0; e < 4; ++e) v[e] = (4 * qa + e < r) ? v[e] : T(0);
-            }
-            aA[0] += v[0] * xr; aA[1] += v[1] * xr; aA[2] += v[2] * xr; aA[3] += v[3] * xr;
+            ld4(row0 + 4 * lane, v);
+            p0 = dot4(v, xa);
+            axpy4(ca, v, x0);
           }
-          if (okB && qb <= qd) {
-            T w[4];
-            ld4(row + 4 * qb, w);
-            if (qb == qd) {
-#pragma unroll
-              for (int e = 0; e < 4; ++e) w[e] = (4 * qb + e < r) ? w[e] : T(0);
-            }
-            aB[0] += w[0] * xr; aB[1] += w[1] * xr; aB[2] += w[2] * xr; aB[3] += w[3] * xr;
-          }
-        } else {
-          const T xv = xb[r - c.nI];
-          if (okA) {
+          if (lane < nq1) {
             T v[4];
-            ld4(row + 4 * qa, v);
-            aA[0] -= v[0] * xv; aA[1] -= v[1] * xv; aA[2] -= v[2] * xv; aA[3] -= v[3] * xv;
+            ld4(row1 + 4 * lane, v);
+            p1 = dot4(v, xa);
+            axpy4(ca, v, x1);
           }
-          if (okB) {
-            T w[4];
-            ld4(row + 4 * qb, w);
-            aB[0] -= w[0] * xv; aB[1] -= w[1] * xv; aB[2] -= w[2] * xv; aB[3] -= w[3] * xv;
+          if ((has1 ? nq1 : nq0) > 32) {  // nq1 >= nq0 when the pair has two rows
+            if (lane + 32 < nq0) {
+              T v[4];
+              ld4(row0 + 4 * (lane + 32), v);
+              p0 += dot4(v, xb);
+              axpy4(cb, v, x0);
+            }
+            if (lane + 32 < nq1) {
+              T v[4];
+              ld4(row1 + 4 * (lane + 32), v);
+              p1 += dot4(v, xb);
+              axpy4(cb, v, x1);
+            }
+          }
+          const T t = pair_total(p0, p1, lane);
+          if (lane == 0) rd[r0] = t;
+          if (lane == 16 && has1) rd[r0 + 1] = t;
+        }
+      } else {  // rows of V: column sums of -V^T x_B
+        for (int p = first_pair(warp, u); p < np; p += kPairWarps) {
+          const int r0 = rr.x + 2 * p;
+          const bool has1 = r0 + 1 < rr.y;
+          const T *row0 = base + 2 * p * vs;
+          const T y0 = -xbv[r0 - nI], y1 = has1 ? -xbv[r0 + 1 - nI] : T(0);
+          if (lane < nq) {
+            T v[4];
+            ld4(row0 + 4 * lane, v);
+            axpy4(ca, v, y0);
+            if (has1) {
+              ld4(row0 + vs + 4 * lane, v);
+              axpy4(ca, v, y1);
+            }
+          }
+          if (lane + 32 < nq) {
+            T v[4];
+            ld4(row0 + 4 * (lane + 32), v);
+            axpy4(cb, v, y0);
+            if (has1) {
+              ld4(row0 + vs + 4 * (lane + 32), v);
+              axpy4(cb, v, y1);
+            }
           }
         }
       }
-      // row dots of the S rows of the chunk: lane per row, this warp's quads
-      const int se = min(re, c.nI);
-      for (int r = rb + lane; r < se; r += 32) {
-        const int q1 = min(r / 4 + 1, q0 + kQuadsPerWarp);
-        rd[warp * xstride + r] =
-            q0 < q1 ? quad_range_dot(base + (cell_row_off(r, c.nI, vs) - off0), xs, q0, q1) : T(0);
-      }
+      u = (u + np) & (kPairWarps - 1);
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[sidx]);
     }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&freed[b]);  // xs and xb of this buffer are no longer read
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      part[e * kConsumers + threadIdx.x] = aA[e];
-      part[(4 + e) * kConsumers + threadIdx.x] = aB[e];
-    }
+    T *pw = part + warp * xstride;
+    if (lane < nq) st4(pw + 4 * lane, ca);
+    if (lane + 32 < nq) st4(pw + 4 * (lane + 32), cb);
     consumers_sync();
-    // column sums over the 8 warps plus the row-dot partials of the same index
-    if (warp == 0 && okA) {
-      const int *I = idx + c.I_off;
+    const int *is = is0 + b * xstride;
+    for (int i = threadIdx.x; i < nI; i += kConsumers) {
+      T s = rd[i];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        if (e >= 4 && !okB) break;
-        const int col = (e < 4 ? 4 * qa : 4 * qb) + (e & 3);
-        if (col >= c.nI) continue;
-        T sum = rd[col];
-        for (int w = 1; w < kConsumerWarps; ++w) sum += rd[w * xstride + col];
-        for (int w = 0; w < kConsumerWarps; ++w) sum += part[e * kConsumers + w * 32 + lane];
-        x[I[col]] = sum;
-      }
+      for (int w = 0; w < kConsumerWarps; ++w) s += part[w * xstride + i];
+      x[is[i]] = s;
     }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&freed[b]);  // x_I, x_B and I of this buffer are no longer read
   }
 }
 
@@ -1322,9 +1435,9 @@ int set_smem_limits() {
     HIF_CUDA_TRY(cudaFuncSetAttribute(k_root_cols<T, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     HIF_CUDA_TRY(cudaFuncSetAttribute(k_group_rows_split<T, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     HIF_CUDA_TRY(cudaFuncSetAttribute(k_group_cols_split<T, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    HIF_CUDA_TRY(cudaFuncSetAttribute(k_cell_fwd_tma_S<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    HIF_CUDA_TRY(cudaFuncSetAttribute(k_cell_bwd_tma_S<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   }
-  HIF_CUDA_TRY(cudaFuncSetAttribute(k_cell_fwd_tma_S<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  HIF_CUDA_TRY(cudaFuncSetAttribute(k_cell_bwd_tma_S<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   done = true;
   return HIF_OK;
 }
@@ -1335,15 +1448,13 @@ int set_smem_limits() {
 // split over CTAs, whose rows fit one stage and whose column pairs fit one
 // warp (nI <= 256).  FP64 applies are bound by the FP64 pipe, not by HBM, and
 // keep the register-streaming G-form kernels.
-// shared-memory elements of the S-form kernels beyond the stages: backward:
-// part (8 per consumer), the row-dot partials (8 per row), two x_I and two
-// x_B buffers; forward: two x_I buffers and the row-dot partials
+// shared-memory elements (4 bytes each) of the S-form kernels beyond the
+// stages: backward: the 8 warps' column sums, the row dots, two x_I, two x_B
+// and two I buffers; forward: two x_I buffers
 size_t tma_bwd_smem_elems(const LevelDev &lv) {
-  return (size_t)8 * kConsumers + 10 * (size_t)pad4(lv.max_nI) + 2 * (size_t)pad4(lv.max_nB);
+  return 13 * (size_t)pad4(lv.max_nI) + 2 * (size_t)pad4(lv.max_nB);
 }
-size_t tma_fwd_smem_elems(const LevelDev &lv) {
-  return 2 * (size_t)pad4(lv.max_nI) + 8 * (size_t)pad4(lv.max_nB);
-}
+size_t tma_fwd_smem_elems(const LevelDev &lv) { return 2 * (size_t)pad4(lv.max_nI); }
 
 // A level whose blocks fit the S-form kernels (rows within a stage, at most
 // kMaxChunks chunks per cell, nI <= 256, shared memory within the limit).
@@ -1365,7 +1476,8 @@ bool use_tma(const Handle *h, const LevelDev &lv, size_t elem) {
 }
 
 // Grid of the persistent TMA-staged cell kernels: the CTAs that fit on the
-// GPU at once (HIFCN_TMA_CTAS overrides the CTAs per SM), at most one per cell.
+// GPU at once (HIFCN_TMA_CTAS overrides the CTAs per SM), at most one per cell;
+// HIFCN_TMA_GRID caps the total (several cells per CTA on small problems).
 int tma_grid(const void *fn, size_t smem, int ncells, int ctas_per_sm) {
   static int sms = 0;
   if (sms == 0) {
@@ -1382,7 +1494,10 @@ int tma_grid(const void *fn, size_t smem, int ncells, int ctas_per_sm) {
   if (e && std::atoi(e) > 0) occ = std::min(occ, std::atoi(e));
   if (ctas_per_sm > 0) occ = std::min(occ, ctas_per_sm);
   occ = std::max(occ, 1);
-  return std::max(1, std::min(ncells, sms * occ));
+  int grid = std::min(ncells, sms * occ);
+  const char *g = std::getenv("HIFCN_TMA_GRID");
+  if (g && std::atoi(g) > 0) grid = std::min(grid, std::atoi(g));
+  return std::max(1, grid);
 }
 
 using bf16 = __nv_bfloat16;
@@ -1414,13 +1529,17 @@ int launch_cell_fwd(Handle *h, const LevelDev &lv, int l, const FactorValues<T> 
       return HIF_OK;
     }
   }
-  if (sf) {
-    size_t sm = (size_t)kStages * kStageBytes + tma_fwd_smem_elems(lv) * sizeof(T);
-    const int grid = tma_grid((const void *)k_cell_fwd_tma_S<T>, sm, lv.ncells, h->tma_ctas);
-    k_cell_fwd_tma_S<T><<<grid, kTmaThreads, sm, s>>>(lv.cells, lv.ncells, lv.chunk_of[0], lv.chunk_tab[0],
-                                                       h->idx, fv.vals, fv.contrib, x,
-                                                       h->scal + kScalErr, lv.max_nI, lv.max_nB);
-  } else {
+  if constexpr (sizeof(T) == 4) {
+    if (sf) {
+      size_t sm = (size_t)kStages * kStageBytes + tma_fwd_smem_elems(lv) * sizeof(T);
+      const int grid = tma_grid((const void *)k_cell_fwd_tma_S<T>, sm, lv.ncells, h->tma_ctas);
+      k_cell_fwd_tma_S<T><<<grid, kTmaThreads, sm, s>>>(lv.cells, lv.ncells, lv.chunk_of[0],
+                                                         lv.chunk_tab[0], h->idx, fv.vals, fv.contrib, x,
+                                                         h->scal + kScalErr, lv.max_nI, lv.max_nB);
+      return HIF_OK;
+    }
+  }
+  {
     size_t sm = (size_t)pad4(lv.max_nI) * sizeof(T);
     k_cell_fwd<T><<<lv.nfwd, kCellFwdThreads, sm, s>>>(lv.fwd, lv.cells, h->idx, fv.vals, fv.contrib,
                                                         fv.xI, x);
@@ -1536,13 +1655,17 @@ int launch_cell_bwd(Handle *h, const LevelDev &lv, int l, const FactorValues<T> 
       return HIF_OK;
     }
   }
-  if (sf) {
-    size_t sm = (size_t)kStages * kStageBytes + tma_bwd_smem_elems(lv) * sizeof(T);
-    const int grid = tma_grid((const void *)k_cell_bwd_tma_S<T>, sm, lv.ncells, h->tma_ctas);
-    k_cell_bwd_tma_S<T><<<grid, kTmaThreads, sm, s>>>(lv.cells, lv.ncells, lv.chunk_of[1], lv.chunk_tab[1],
-                                                       h->idx, fv.vals, x,
-                                                       h->scal + kScalErr, lv.max_nI, lv.max_nB);
-  } else {
+  if constexpr (sizeof(T) == 4) {
+    if (sf) {
+      size_t sm = (size_t)kStages * kStageBytes + tma_bwd_smem_elems(lv) * sizeof(T);
+      const int grid = tma_grid((const void *)k_cell_bwd_tma_S<T>, sm, lv.ncells, h->tma_ctas);
+      k_cell_bwd_tma_S<T><<<grid, kTmaThreads, sm, s>>>(lv.cells, lv.ncells, lv.chunk_of[1],
+                                                         lv.chunk_tab[1], h->idx, fv.vals, x,
+                                                         h->scal + kScalErr, lv.max_nI, lv.max_nB);
+      return HIF_OK;
+    }
+  }
+  {
     size_t sm = ((size_t)lv.max_nI + lv.max_nB + 8 * kCellBwdThreads) * sizeof(T);
     k_cell_bwd<T><<<lv.nbwd, kCellBwdThreads, sm, s>>>(lv.bwd, lv.cells, h->idx, fv.vals, fv.xI, x);
   }

@@ -45,7 +45,8 @@ class HifOptions(ctypes.Structure):
 class HifInfo(ctypes.Structure):
     _fields_ = [("N", c_int64), ("dim", c_int), ("n", c_int), ("leaf", c_int), ("levels", c_int),
                 ("root_size", c_int), ("factor_entries", c_int64), ("apply_bytes", c_int64),
-                ("device_bytes", c_int64), ("precision", c_int), ("setup_seconds", c_double)]
+                ("device_bytes", c_int64), ("precision", c_int), ("setup_seconds", c_double),
+                ("sform_levels", c_int)]
 
 
 class HifKernelStat(ctypes.Structure):
