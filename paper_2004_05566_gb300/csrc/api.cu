@@ -148,6 +148,8 @@ int build_items(Handle *h, LevelDev &D, const LevelHost &H, int target, cudaStre
   }
   D.nfwd = (int)fw.size();
   D.nbwd = (int)bw.size();
+  D.fwd_host = fw;
+  D.bwd_host = bw;
   D.item_target = target;
   HIF_TRY(dev_alloc(h, (void **)&D.fwd, std::max<size_t>(1, fw.size()) * sizeof(CellItem)));
   HIF_TRY(dev_alloc(h, (void **)&D.bwd, std::max<size_t>(1, bw.size()) * sizeof(CellItem)));
@@ -445,6 +447,14 @@ void release_factor(Handle *h) {
   h->view = nullptr;
   h->view_ok = false;
   h->upper_grid[0] = h->upper_grid[1] = 0;
+  h->use_flow = false;
+  h->flow_nphase = h->flow_units = 0;
+  h->flow_phases = nullptr;
+  h->flow_levels = nullptr;
+  h->flow_dep_ptr = h->flow_dep_idx = nullptr;
+  h->flow_flags = h->flow_ctl = nullptr;
+  h->flow_contrib[0] = h->flow_contrib[1] = nullptr;
+  h->flow_grid[0] = h->flow_grid[1] = 0;
   for (auto &r : h->stat_pending) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);

@@ -31,12 +31,26 @@
 
 namespace hifcn {
 
+// the dependency-driven upper sweep (defined after the level kernels)
+template <typename T>
+int launch_flow(Handle *h, const FactorValues<T> &fv, T *x, cudaStream_t s);
+
 namespace {
 
 constexpr int kCellFwdThreads = 256;
 constexpr int kCellBwdThreads = 256;
 constexpr int kRootThreads = 256;
 constexpr int kRows = 4;  // rows a warp keeps in flight in the row-dot kernels
+
+// Programmatic dependent launch: a kernel of the apply path may be scheduled
+// while the previous kernel on the stream is finishing; it waits here until
+// that kernel's memory operations are complete and visible, then lets the
+// next kernel be scheduled in turn.  Without the launch attribute both are
+// no-ops.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 
 template <typename T>
 __device__ __forceinline__ T warp_reduce(T v) {
@@ -116,7 +130,7 @@ __device__ __forceinline__ void cell_fwd_unit(const CellItem &it, const CellDesc
   const CellDesc c = cells[it.cell];
   const int *I = idx + c.I_off;
   const int nIp = (int)pad4(c.nI);
-  for (int i = threadIdx.x; i < nIp; i += NT) xs[i] = i < c.nI ? x[I[i]] : T(0);
+  for (int i = threadIdx.x; i < nIp; i += NT) xs[i] = i < c.nI ? __ldcg(x + I[i]) : T(0);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int NW = NT / 32;
@@ -163,6 +177,7 @@ __global__ void __launch_bounds__(kCellFwdThreads) k_cell_fwd(const CellItem *__
                                                               T *__restrict__ contrib,
                                                               T *__restrict__ xI,
                                                               const T *__restrict__ x) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cell_fwd_unit<T, kCellFwdThreads, TV>(items[blockIdx.x], cells, idx, vals, contrib, xI, x,
                                     reinterpret_cast<T *>(smem_raw));
@@ -181,9 +196,9 @@ __device__ __forceinline__ void group_fwd_unit(const GroupDesc &g, const int *__
   for (int i = threadIdx.x; i < np; i += NT) {
     T v = T(0);
     if (i < g.n) {
-      v = x[gi[i]];
+      v = __ldcg(x + gi[i]);
       const long long a = cptr[g.cptr_off + i], b = cptr[g.cptr_off + i + 1];
-      for (long long s = a; s < b; ++s) v -= contrib[cslot[s]];
+      for (long long s = a; s < b; ++s) v -= __ldcg(contrib + cslot[s]);
     }
     xs[i] = v;
   }
@@ -226,9 +241,9 @@ __device__ __forceinline__ void group_fwd_small_warp(const GroupDesc &g, const i
   const int *gi = idx + g.idx_off;
   T v = T(0);
   if (lane < g.n) {
-    v = x[gi[lane]];
+    v = __ldcg(x + gi[lane]);
     const long long a = cptr[g.cptr_off + lane], b = cptr[g.cptr_off + lane + 1];
-    for (long long s = a; s < b; ++s) v -= contrib[cslot[s]];
+    for (long long s = a; s < b; ++s) v -= __ldcg(contrib + cslot[s]);
   }
   xs[lane] = v;
   __syncwarp();
@@ -236,6 +251,7 @@ __device__ __forceinline__ void group_fwd_small_warp(const GroupDesc &g, const i
     const int np = (int)pad4(g.n);
     const TV *row = vals + g.H_off + (long long)lane * np;
     T acc = T(0);
+#pragma unroll 8
     for (int q = 0; q < np / 4; ++q) {
       T w[4];
       ld4(row + 4 * q, w);
@@ -252,12 +268,13 @@ __device__ __forceinline__ void group_bwd_small_warp(const GroupDesc &g, const i
                                                      T *xs) {
   const int lane = threadIdx.x & 31;
   const int *gi = idx + g.idx_off;
-  xs[lane] = lane < g.n ? x[gi[lane]] : T(0);
+  xs[lane] = lane < g.n ? __ldcg(x + gi[lane]) : T(0);
   __syncwarp();
   if (lane < g.n) {
     const long long np = pad4(g.n);
     const TV *H = vals + g.H_off;
     T acc = T(0);
+#pragma unroll 8
     for (int r = 0; r < g.n; ++r) acc += ldv<T>(H + (long long)r * np + lane) * xs[r];
     x[gi[lane]] = acc;
   }
@@ -275,32 +292,64 @@ __device__ __forceinline__ void col_layout(int ncols, int nthreads, int &CW, int
   RG = nthreads / CW;
 }
 
-// Backward group step: x_g <- H^T x_g.  xs holds n + NT elements.
+// The same with CW the smallest power of two >= ncols (at most nthreads):
+// narrow items spread their rows over all threads instead of leaving most
+// lanes idle, and the row groups can be added by a tree.
+__device__ __forceinline__ void pow2_layout(int ncols, int nthreads, int &CW, int &RG) {
+  CW = 1;
+  while (CW < ncols && CW < nthreads) CW <<= 1;
+  RG = nthreads / CW;
+}
+
+// part[k * NT + rg * CW + cl] for k < K: after the call, row group 0 holds the
+// sum over all RG row groups (a fixed tree, so results are reproducible).
+// Every thread of the CTA calls it.
+template <typename T, int NT, int K>
+__device__ __forceinline__ void rowgroup_tree(T *part, int CW, int RG) {
+  __syncthreads();
+  for (int s = RG >> 1; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s * CW) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) part[k * NT + threadIdx.x] += part[k * NT + threadIdx.x + s * CW];
+    }
+    __syncthreads();
+  }
+}
+
+// Backward group step: x_g <- H^T x_g.  A thread owns a column quad of H
+// (16-byte loads) and a row group; the row groups are added by a tree.  xs
+// holds pad4(n) + 4 NT elements.
 template <typename T, int NT, typename TV = T>
 __device__ __forceinline__ void group_bwd_unit(const GroupDesc &g, const int *__restrict__ idx,
                                                const TV *__restrict__ vals, T *__restrict__ x, T *xs) {
-  T *part = xs + g.n;
+  const int np = (int)pad4(g.n), nq = np / 4;
+  T *part = xs + np;  // 4 * NT
   const int *gi = idx + g.idx_off;
-  for (int i = threadIdx.x; i < g.n; i += NT) xs[i] = x[gi[i]];
+  for (int i = threadIdx.x; i < g.n; i += NT) xs[i] = __ldcg(x + gi[i]);
   __syncthreads();
   const TV *H = vals + g.H_off;
-  const long long np = pad4(g.n);
   int CW, RG;
-  col_layout(g.n, NT, CW, RG);
+  pow2_layout(nq, NT, CW, RG);
   const int cl = threadIdx.x % CW, rg = threadIdx.x / CW;
-  for (int c0 = 0; c0 < g.n; c0 += CW) {
-    const int col = c0 + cl;
-    T acc = T(0);
-    if (rg < RG && col < g.n) {
+  for (int q0 = 0; q0 < nq; q0 += CW) {
+    const int q = q0 + cl;
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    if (q < nq) {
 #pragma unroll 4
-      for (int i = rg; i < g.n; i += RG) acc += ldv<T>(H + (long long)i * np + col) * xs[i];
+      for (int i = rg; i < g.n; i += RG) {
+        T v[4];
+        ld4(H + (long long)i * np + 4 * q, v);
+        const T xv = xs[i];
+        acc[0] += v[0] * xv; acc[1] += v[1] * xv; acc[2] += v[2] * xv; acc[3] += v[3] * xv;
+      }
     }
-    part[threadIdx.x] = acc;
-    __syncthreads();
-    if (rg == 0 && col < g.n) {
-      T sum = part[cl];
-      for (int q = 1; q < RG; ++q) sum += part[q * CW + cl];
-      x[gi[col]] = sum;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) part[e * NT + threadIdx.x] = acc[e];
+    rowgroup_tree<T, NT, 4>(part, CW, RG);
+    if (rg == 0 && q < nq) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (4 * q + e < g.n) x[gi[4 * q + e]] = part[e * NT + cl];
     }
     __syncthreads();
   }
@@ -316,6 +365,7 @@ __global__ void __launch_bounds__(kSmallWarps * 32) k_group_fwd_level(
     const GroupDesc *__restrict__ groups, const int *__restrict__ idx,
     const long long *__restrict__ cptr, const long long *__restrict__ cslot,
     const TV *__restrict__ vals, const T *__restrict__ contrib, T *__restrict__ x) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *sm = reinterpret_cast<T *>(smem_raw);
   const int u = blockIdx.x;
@@ -334,6 +384,7 @@ __global__ void __launch_bounds__(kSmallWarps * 32) k_group_bwd_level(
     const int *__restrict__ large, int nlarge, const int *__restrict__ small, int nsmall,
     const GroupDesc *__restrict__ groups, const int *__restrict__ idx, const TV *__restrict__ vals,
     T *__restrict__ x) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *sm = reinterpret_cast<T *>(smem_raw);
   const int u = blockIdx.x;
@@ -362,6 +413,7 @@ __global__ void __launch_bounds__(256) k_group_gather(const int *__restrict__ la
                                                       const T *__restrict__ x,
                                                       const long long *__restrict__ gs_off,
                                                       T *__restrict__ gs) {
+  pdl_enter();
   const GroupDesc g = groups[large[blockIdx.x]];
   const int *gi = idx + g.idx_off;
   T *out = gs + gs_off[blockIdx.x];
@@ -389,6 +441,7 @@ __global__ void __launch_bounds__(256) k_group_rows_split(const int2 *__restrict
                                                           const long long *__restrict__ gs_off,
                                                           const T *__restrict__ gs,
                                                           T *__restrict__ x) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *xs = reinterpret_cast<T *>(smem_raw);
   const int2 rb = rblk[blockIdx.x];
@@ -430,6 +483,7 @@ __global__ void __launch_bounds__(256) k_group_cols_split(const int2 *__restrict
                                                           const long long *__restrict__ gs_off,
                                                           const T *__restrict__ gs,
                                                           T *__restrict__ x) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *xs = reinterpret_cast<T *>(smem_raw);
   const int2 cb = cblk[blockIdx.x];
@@ -461,8 +515,9 @@ __global__ void __launch_bounds__(256) k_group_cols_split(const int2 *__restrict
 // Backward cell step (E_I): x_I <- G^T xI_I - V^T x_B, for columns [a, b)
 // (a a multiple of 4) of one cell.  A thread owns the column quad pair
 // (qa, qb) = (first + p, last - p), which balances the triangular row counts,
-// and reads both quads of a row with 16-byte loads; row groups are added in
-// a fixed order.
+// and reads both quads of a row with 16-byte loads.  The pairs take the
+// smallest power-of-two number of threads that covers them, the rest of the
+// CTA splits the rows into groups, and the row groups are added by a tree.
 template <typename T, int NT, typename TV = T>
 __device__ __forceinline__ void cell_bwd_unit(const CellItem &it, const CellDesc *__restrict__ cells,
                                               const int *__restrict__ idx, const TV *__restrict__ vals,
@@ -473,8 +528,8 @@ __device__ __forceinline__ void cell_bwd_unit(const CellItem &it, const CellDesc
   T *xb = xs + c.nI;
   const int *I = idx + c.I_off;
   const int *B = idx + c.B_off;
-  for (int i = threadIdx.x; i < c.nI; i += NT) xs[i] = xI[I[i]];
-  for (int q = threadIdx.x; q < c.nB; q += NT) xb[q] = x[B[q]];
+  for (int i = threadIdx.x; i < c.nI; i += NT) xs[i] = __ldcg(xI + I[i]);
+  for (int q = threadIdx.x; q < c.nB; q += NT) xb[q] = __ldcg(x + B[q]);
   __syncthreads();
   const TV *G = vals + c.G_off;
   const TV *V = vals + c.V_off;
@@ -482,12 +537,12 @@ __device__ __forceinline__ void cell_bwd_unit(const CellItem &it, const CellDesc
   const int q0 = it.a / 4, q1 = (it.b + 3) / 4;  // column quads [q0, q1)
   const int npairs = (q1 - q0 + 1) / 2;
   int PW, RG;
-  col_layout(npairs, NT, PW, RG);
+  pow2_layout(npairs, NT, PW, RG);
   const int pl = threadIdx.x % PW, rg = threadIdx.x / PW;
   for (int p0 = 0; p0 < npairs; p0 += PW) {
     const int p = p0 + pl;
     const int qa = q0 + p, qb = q1 - 1 - p;
-    const bool okA = rg < RG && p < npairs;
+    const bool okA = p < npairs;
     const bool okB = okA && qb > qa;
     T aA[4] = {T(0), T(0), T(0), T(0)}, aB[4] = {T(0), T(0), T(0), T(0)};
     if (okA) {
@@ -495,7 +550,7 @@ __device__ __forceinline__ void cell_bwd_unit(const CellItem &it, const CellDesc
       // the padded row whenever 4q <= i
       const int ia = 4 * qa;
       const int i0 = ia + ((rg - ia % RG) % RG + RG) % RG;
-#pragma unroll 2
+#pragma unroll 4
       for (int i = i0; i < c.nI; i += RG) {
         const TV *row = G + tri_off(i);
         const T xv = xs[i];
@@ -508,7 +563,7 @@ __device__ __forceinline__ void cell_bwd_unit(const CellItem &it, const CellDesc
           aB[0] += w[0] * xv; aB[1] += w[1] * xv; aB[2] += w[2] * xv; aB[3] += w[3] * xv;
         }
       }
-#pragma unroll 2
+#pragma unroll 4
       for (int q = rg; q < c.nB; q += RG) {
         const TV *row = V + (long long)q * vstride;
         const T xv = xb[q];
@@ -527,16 +582,14 @@ __device__ __forceinline__ void cell_bwd_unit(const CellItem &it, const CellDesc
       part[k * NT + threadIdx.x] = aA[k];
       part[(4 + k) * NT + threadIdx.x] = aB[k];
     }
-    __syncthreads();
+    rowgroup_tree<T, NT, 8>(part, PW, RG);
     if (rg == 0 && p < npairs) {
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         const int col = (k < 4 ? 4 * qa : 4 * qb) + (k & 3);
         if (k >= 4 && qb <= qa) break;
         if (col < it.a || col >= it.b) continue;
-        T sum = part[k * NT + pl];
-        for (int g = 1; g < RG; ++g) sum += part[k * NT + g * PW + pl];
-        x[I[col]] = sum;
+        x[I[col]] = part[k * NT + pl];
       }
     }
     __syncthreads();
@@ -550,6 +603,7 @@ __global__ void __launch_bounds__(kCellBwdThreads) k_cell_bwd(const CellItem *__
                                                               const TV *__restrict__ vals,
                                                               const T *__restrict__ xI,
                                                               T *__restrict__ x) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cell_bwd_unit<T, kCellBwdThreads, TV>(items[blockIdx.x], cells, idx, vals, xI, x,
                                     reinterpret_cast<T *>(smem_raw));
@@ -858,6 +912,7 @@ __global__ void __launch_bounds__(kTmaThreads, 4) k_cell_fwd_tma_S(const CellDes
                                                                    const T *__restrict__ x,
                                                                    double *__restrict__ err,
                                                                    int max_nI, int max_nB) {
+  pdl_enter();
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) unsigned long long full[kStages], empty[kStages], ready[2], freed[2];
   __shared__ int2 meta[kStages];
@@ -965,6 +1020,7 @@ __global__ void __launch_bounds__(kTmaThreads, 4) k_cell_bwd_tma_S(const CellDes
                                                                    T *__restrict__ x,
                                                                    double *__restrict__ err,
                                                                    int max_nI, int max_nB) {
+  pdl_enter();
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) unsigned long long full[kStages], empty[kStages], ready[2], freed[2];
   __shared__ int2 meta[kStages];
@@ -1169,6 +1225,7 @@ template <typename T, typename TV = T>
 __global__ void __launch_bounds__(kRootThreads) k_root(int nr, const int *__restrict__ ridx,
                                                        const TV *__restrict__ G,
                                                        T *__restrict__ x) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   root_unit<T, kRootThreads, TV>(nr, ridx, G, x, reinterpret_cast<T *>(smem_raw));
 }
@@ -1202,7 +1259,7 @@ __device__ __forceinline__ void root_rows_unit(int u, int nr, const int *__restr
   const int nrp = (int)pad4(nr);
   const int r_lo = u * kRootBlock, r_hi = min(nr, r_lo + kRootBlock);
   const int need = (int)pad4(r_hi);  // row r reads columns <= r
-  for (int i = threadIdx.x; i < need && i < nrp; i += NT) xs[i] = i < nr ? x[ridx[i]] : T(0);
+  for (int i = threadIdx.x; i < need && i < nrp; i += NT) xs[i] = i < nr ? __ldcg(x + ridx[i]) : T(0);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int NW = NT / 32;
@@ -1233,7 +1290,7 @@ __device__ __forceinline__ void root_cols_unit(int u, int nr, const int *__restr
   T *part = smem;        // NT
   T *ts = smem + NT;     // t[c_lo .. nr)
   const int c_lo = u * kRootBlock, c_hi = min(nr, c_lo + kRootBlock);
-  for (int i = c_lo + threadIdx.x; i < nr; i += NT) ts[i - c_lo] = t[i];
+  for (int i = c_lo + threadIdx.x; i < nr; i += NT) ts[i - c_lo] = __ldcg(t + i);
   __syncthreads();
   constexpr int CW = kRootBlock, RG = NT / kRootBlock;
   const int cl = threadIdx.x % CW, rg = threadIdx.x / CW;
@@ -1258,6 +1315,7 @@ template <typename T, typename TV = T>
 __global__ void __launch_bounds__(256) k_root_rows(int nr, const int *__restrict__ ridx,
                                                    const TV *__restrict__ G, const T *__restrict__ x,
                                                    T *__restrict__ t) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   root_rows_unit<T, 256, TV>(blockIdx.x, nr, ridx, G, x, t, reinterpret_cast<T *>(smem_raw));
 }
@@ -1266,6 +1324,7 @@ template <typename T, typename TV = T>
 __global__ void __launch_bounds__(256) k_root_cols(int nr, const int *__restrict__ ridx,
                                                    const TV *__restrict__ G, const T *__restrict__ t,
                                                    T *__restrict__ x) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   root_cols_unit<T, 256, TV>(blockIdx.x, nr, ridx, G, t, x, reinterpret_cast<T *>(smem_raw));
 }
@@ -1277,6 +1336,7 @@ __global__ void __launch_bounds__(kUpperThreads) k_upper_sweep(
     const long long *__restrict__ cslot, const TV *__restrict__ vals, T *__restrict__ contrib,
     T *__restrict__ xI, T *__restrict__ x, int nr, const int *__restrict__ ridx,
     const TV *__restrict__ Gr, T *__restrict__ rt) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *sm = reinterpret_cast<T *>(smem_raw);
   constexpr int NT = kUpperThreads;
@@ -1321,6 +1381,185 @@ __global__ void __launch_bounds__(kUpperThreads) k_upper_sweep(
       __syncthreads();  // the unit's shared buffers are reused by the next unit
     }
     if (p + 1 < nphase) cluster_barrier();
+  }
+}
+
+// ------------------------------------------ dependency-driven upper sweep
+//
+// The steps of the upper levels move little data each, so as level-by-level
+// launches (or phases behind a barrier) their time is the latency of ~20
+// dependent steps.  Here every work unit of those steps (cell items, entity
+// groups, root row / column blocks) is a node of a dependency graph built on
+// the host from what each unit reads and writes (x, the forward values xI,
+// the contribution slots, the root scratch): a unit depends on the last
+// earlier unit that wrote anything it reads or writes, and on the earlier
+// units that read what it writes.  One persistent kernel runs the graph:
+// each CTA claims the next unit number with an atomic ticket (units are
+// numbered in sweep order, so dependencies always have smaller numbers and
+// are already claimed by running CTAs), waits until the flags of the unit's
+// dependencies show the current epoch, runs the unit with the same code as
+// the level kernels, and publishes its own flag (release after a fence).
+// Flags hold the epoch of the launch that finished them, so nothing is reset
+// between launches; the last CTA to finish resets the tickets and advances
+// the epoch.  Every wait is bounded; on expiry the kernel records the failure
+// in err and marks the launch aborted (ctl[3] = epoch), after which no unit
+// of the launch waits any more, so a failed launch still ends promptly.
+
+constexpr int kFlowThreads = 256;
+constexpr int kFlowWarps = kFlowThreads / 32;
+constexpr long long kFlowWaitLimit = 1LL << 18;  // polls of one flag (a fraction of a second)
+
+__device__ __forceinline__ int ld_acquire_gpu(const int *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_gpu(int *p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Bulk prefetch of bytes [b0, b1) of the allocation at base into L2, in
+// chunks of 8 KB dealt round robin to `nparts` threads (this is `part`);
+// both ends are rounded to 16 bytes inside the range.
+__device__ __forceinline__ void l2_prefetch_range(const void *base, long long b0, long long b1, int part,
+                                                  int nparts) {
+  constexpr long long kChunk = 8192;
+  b0 = (b0 + 15) & ~15LL;
+  b1 &= ~15LL;
+  for (long long c = b0 + (long long)part * kChunk; c < b1; c += (long long)nparts * kChunk) {
+    const unsigned n = (unsigned)min(kChunk, b1 - c);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(static_cast<const char *>(base) + c),
+                 "r"(n)
+                 : "memory");
+  }
+}
+
+template <typename T, typename TV>
+__device__ __forceinline__ void flow_run_unit(int type, const UpperLevel &L, int u,
+                                              const int *__restrict__ idx,
+                                              const long long *__restrict__ cptr,
+                                              const long long *__restrict__ cslot,
+                                              const TV *__restrict__ vals, T *contrib, T *xI, T *x,
+                                              int nr, const int *__restrict__ ridx,
+                                              const TV *__restrict__ Gr, T *rt, T *sm) {
+  constexpr int NT = kFlowThreads, NW = kFlowWarps;
+  const int warp = threadIdx.x >> 5;
+  switch (type) {
+    case kPhaseCellFwd:
+      cell_fwd_unit<T, NT, TV>(L.fwd[u], L.cells, idx, vals, contrib, xI, x, sm);
+      break;
+    case kPhaseGroupFwd:
+      if (u < L.nlarge) {
+        group_fwd_unit<T, NT, TV>(L.groups[L.large[u]], idx, cptr, cslot, vals, contrib, x, sm);
+      } else {
+        const int t = (u - L.nlarge) * NW + warp;
+        if (t < L.nsmall)
+          group_fwd_small_warp<T, TV>(L.groups[L.small[t]], idx, cptr, cslot, vals, contrib, x,
+                                      sm + 32 * warp);
+      }
+      break;
+    case kPhaseRootRows:
+      root_rows_unit<T, NT, TV>(u, nr, ridx, Gr, x, rt, sm);
+      break;
+    case kPhaseRootCols:
+      root_cols_unit<T, NT, TV>(u, nr, ridx, Gr, rt, x, sm);
+      break;
+    case kPhaseGroupBwd:
+      if (u < L.nlarge) {
+        group_bwd_unit<T, NT, TV>(L.groups[L.large[u]], idx, vals, x, sm);
+      } else {
+        const int t = (u - L.nlarge) * NW + warp;
+        if (t < L.nsmall) group_bwd_small_warp<T, TV>(L.groups[L.small[t]], idx, vals, x, sm + 32 * warp);
+      }
+      break;
+    default:  // kPhaseCellBwd
+      cell_bwd_unit<T, NT, TV>(L.bwd[u], L.cells, idx, vals, xI, x, sm);
+      break;
+  }
+}
+
+// ctl[0]: claim ticket, ctl[1]: finished CTAs, ctl[2]: epoch of the last
+// launch, ctl[3]: epoch of the last launch that gave up waiting
+template <typename T>
+__global__ void __launch_bounds__(kFlowThreads) k_flow_sweep(
+    const FlowPhase *__restrict__ phases, int nphase, int total, const UpperLevel *__restrict__ levels,
+    const int *__restrict__ dep_ptr, const int *__restrict__ dep_idx, int *flags, int *ctl,
+    const int *__restrict__ idx, const long long *__restrict__ cptr, const long long *__restrict__ cslot,
+    const T *__restrict__ vals, const __nv_bfloat16 *__restrict__ vals16, T *contrib, T *contrib_flow,
+    T *xI, T *x, int nr, const int *__restrict__ ridx, long long root_G_off, T *rt, double *err,
+    FlowPrefetch pf) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *sm = reinterpret_cast<T *>(smem_raw);
+  __shared__ int s_u, s_epoch;
+  {  // the factor values and indices of the sweep are read from L2 from here on
+    const int part = blockIdx.x * blockDim.x + threadIdx.x, np = gridDim.x * blockDim.x;
+    for (int k = 0; k < 2; ++k) {
+      l2_prefetch_range(vals, pf.v0[k] * (long long)sizeof(T), pf.v1[k] * (long long)sizeof(T), part, np);
+      if (vals16) l2_prefetch_range(vals16, pf.v0[k] * 2, pf.v1[k] * 2, part, np);
+    }
+    l2_prefetch_range(idx, pf.i0 * 4, pf.i1 * 4, part, np);
+    l2_prefetch_range(cptr, pf.c0 * 8, pf.c1 * 8, part, np);
+    l2_prefetch_range(cslot, pf.s0 * 8, pf.s1 * 8, part, np);
+  }
+  if (threadIdx.x == 0) s_epoch = ld_acquire_gpu(ctl + 2) + 1;
+  __syncthreads();
+  const int epoch = s_epoch;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (;;) {
+    if (threadIdx.x == 0) s_u = atomicAdd(ctl, 1);
+    __syncthreads();
+    const int u = s_u;
+    __syncthreads();  // every thread has read s_u before the next claim
+    if (u >= total) break;
+    int p = 0;
+    while (p + 1 < nphase && phases[p + 1].base <= u) ++p;
+    const FlowPhase P = phases[p];
+    if (warp == 0) {
+      for (int d = dep_ptr[u] + lane; d < dep_ptr[u + 1]; d += 32) {
+        const int *f = flags + dep_idx[d];
+        for (long long it = 0; ld_acquire_gpu(f) != epoch; ++it) {
+          if (it >= kFlowWaitLimit) {
+            err[0] = 1.0;
+            atomicExch(ctl + 3, epoch);
+            break;
+          }
+          if (it >= 32) {
+            if (ld_acquire_gpu(ctl + 3) == epoch) break;  // the launch was aborted
+            __nanosleep(64);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    const UpperLevel L = levels[P.level];
+    T *cb = L.cbase < 0 ? contrib : contrib_flow + L.cbase;
+    const int uu = u - P.base;
+    bool done = false;
+    if constexpr (sizeof(T) == 4) {
+      if (P.bf16) {
+        flow_run_unit<T, __nv_bfloat16>(P.type, L, uu, idx, cptr, cslot, vals16, cb, xI, x, nr, ridx,
+                                        vals16 + root_G_off, rt, sm);
+        done = true;
+      }
+    }
+    if (!done)
+      flow_run_unit<T, T>(P.type, L, uu, idx, cptr, cslot, vals, cb, xI, x, nr, ridx, vals + root_G_off, rt,
+                          sm);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      st_release_gpu(flags + u, epoch);
+    }
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(ctl + 1, 1) == (int)gridDim.x - 1) {
+      ctl[0] = 0;
+      ctl[1] = 0;
+      __threadfence();
+      atomicExch(ctl + 2, epoch);
+    }
   }
 }
 
@@ -1400,12 +1639,14 @@ __global__ void __launch_bounds__(256) k_merged_phase(const int *__restrict__ pr
 }
 
 __global__ void k_to_float(const double *__restrict__ a, float *__restrict__ b, long long n) {
+  pdl_enter();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
     b[i] = (float)a[i];
 }
 
 __global__ void k_to_double(const float *__restrict__ a, double *__restrict__ b, long long n) {
+  pdl_enter();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
     b[i] = (double)a[i];
@@ -1502,6 +1743,28 @@ int tma_grid(const void *fn, size_t smem, int ncells, int ctas_per_sm) {
 
 using bf16 = __nv_bfloat16;
 
+// Launch of an apply-path kernel with programmatic dependent launch (the
+// kernels start with pdl_enter); HIFCN_NO_PDL=1 launches them plainly.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                     Args &&...args) {
+  static const bool pdl = [] {
+    const char *e = std::getenv("HIFCN_NO_PDL");
+    return !(e && e[0] == '1');
+  }();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // true when level l of the FP32 apply reads its values from the BF16 pool
 template <typename T>
 bool bf16_level(const Handle *h, int l) {
@@ -1523,9 +1786,9 @@ int launch_cell_fwd(Handle *h, const LevelDev &lv, int l, const FactorValues<T> 
   if constexpr (sizeof(T) == 4) {
     if (b16) {
       size_t sm = (size_t)pad4(lv.max_nI) * sizeof(T);
-      k_cell_fwd<T, bf16><<<lv.nfwd, kCellFwdThreads, sm, s>>>(lv.fwd, lv.cells, h->idx,
+      HIF_CUDA_TRY(launch_k(k_cell_fwd<T, bf16>, lv.nfwd, kCellFwdThreads, sm, s, lv.fwd, lv.cells, h->idx,
                                                                 static_cast<const bf16 *>(h->bf16_vals),
-                                                                fv.contrib, fv.xI, x);
+                                                                fv.contrib, fv.xI, x));
       return HIF_OK;
     }
   }
@@ -1533,16 +1796,16 @@ int launch_cell_fwd(Handle *h, const LevelDev &lv, int l, const FactorValues<T> 
     if (sf) {
       size_t sm = (size_t)kStages * kStageBytes + tma_fwd_smem_elems(lv) * sizeof(T);
       const int grid = tma_grid((const void *)k_cell_fwd_tma_S<T>, sm, lv.ncells, h->tma_ctas);
-      k_cell_fwd_tma_S<T><<<grid, kTmaThreads, sm, s>>>(lv.cells, lv.ncells, lv.chunk_of[0],
+      HIF_CUDA_TRY(launch_k(k_cell_fwd_tma_S<T>, grid, kTmaThreads, sm, s, lv.cells, lv.ncells, lv.chunk_of[0],
                                                          lv.chunk_tab[0], h->idx, fv.vals, fv.contrib, x,
-                                                         h->scal + kScalErr, lv.max_nI, lv.max_nB);
+                                                         h->scal + kScalErr, lv.max_nI, lv.max_nB));
       return HIF_OK;
     }
   }
   {
     size_t sm = (size_t)pad4(lv.max_nI) * sizeof(T);
-    k_cell_fwd<T><<<lv.nfwd, kCellFwdThreads, sm, s>>>(lv.fwd, lv.cells, h->idx, fv.vals, fv.contrib,
-                                                        fv.xI, x);
+    HIF_CUDA_TRY(launch_k(k_cell_fwd<T>, lv.nfwd, kCellFwdThreads, sm, s, lv.fwd, lv.cells, h->idx, fv.vals, fv.contrib,
+                                                        fv.xI, x));
   }
   return HIF_OK;
 }
@@ -1560,21 +1823,21 @@ int launch_group_fwd(Handle *h, const LevelDev &lv, int l, const FactorValues<T>
                s);
   if (lv.split) {  // large entities over many CTAs, then the small ones
     const size_t smx = (size_t)pad4(lv.max_ng) * sizeof(T);
-    k_group_gather<T><<<dim3(lv.nlarge, 4), 256, 0, s>>>(lv.large_groups, lv.nlarge, lv.groups, h->idx,
+    HIF_CUDA_TRY(launch_k(k_group_gather<T>, dim3(lv.nlarge, 4), 256, 0, s, lv.large_groups, lv.nlarge, lv.groups, h->idx,
                                                          h->cptr, h->cslot, fv.contrib, x, lv.gs_off,
-                                                         fv.gs);
+                                                         fv.gs));
     bool done = false;
     if constexpr (sizeof(T) == 4) {
       if (b16) {
-        k_group_rows_split<T, bf16><<<lv.nrblk, 256, smx, s>>>(lv.rblk, lv.large_groups, lv.groups, h->idx,
+        HIF_CUDA_TRY(launch_k(k_group_rows_split<T, bf16>, lv.nrblk, 256, smx, s, lv.rblk, lv.large_groups, lv.groups, h->idx,
                                                                static_cast<const bf16 *>(h->bf16_vals),
-                                                               lv.gs_off, fv.gs, x);
+                                                               lv.gs_off, fv.gs, x));
         done = true;
       }
     }
     if (!done)
-      k_group_rows_split<T><<<lv.nrblk, 256, smx, s>>>(lv.rblk, lv.large_groups, lv.groups, h->idx, fv.vals,
-                                                       lv.gs_off, fv.gs, x);
+      HIF_CUDA_TRY(launch_k(k_group_rows_split<T>, lv.nrblk, 256, smx, s, lv.rblk, lv.large_groups, lv.groups, h->idx, fv.vals,
+                                                       lv.gs_off, fv.gs, x));
     note_launch(1 + (lv.nsmall ? 1 : 0));
     if (!lv.nsmall) return HIF_OK;
   }
@@ -1582,15 +1845,15 @@ int launch_group_fwd(Handle *h, const LevelDev &lv, int l, const FactorValues<T>
   const int grid = nlg + (lv.nsmall + kSmallWarps - 1) / kSmallWarps;
   if constexpr (sizeof(T) == 4) {
     if (b16) {
-      k_group_fwd_level<T, bf16><<<grid, kSmallWarps * 32, sm, s>>>(
+      HIF_CUDA_TRY(launch_k(k_group_fwd_level<T, bf16>, grid, kSmallWarps * 32, sm, s, 
           lv.large_groups, nlg, lv.small_groups, lv.nsmall, lv.groups, h->idx, h->cptr, h->cslot,
-          static_cast<const bf16 *>(h->bf16_vals), fv.contrib, x);
+          static_cast<const bf16 *>(h->bf16_vals), fv.contrib, x));
       return HIF_OK;
     }
   }
-  k_group_fwd_level<T><<<grid, kSmallWarps * 32, sm, s>>>(lv.large_groups, nlg, lv.small_groups,
+  HIF_CUDA_TRY(launch_k(k_group_fwd_level<T>, grid, kSmallWarps * 32, sm, s, lv.large_groups, nlg, lv.small_groups,
                                                           lv.nsmall, lv.groups, h->idx, h->cptr,
-                                                          h->cslot, fv.vals, fv.contrib, x);
+                                                          h->cslot, fv.vals, fv.contrib, x));
   return HIF_OK;
 }
 
@@ -1599,25 +1862,25 @@ int launch_group_bwd(Handle *h, const LevelDev &lv, int l, const FactorValues<T>
                      cudaStream_t s) {
   if (!lv.ngroups) return HIF_OK;
   const double E = sizeof(T);
-  const size_t sm = std::max<size_t>((size_t)lv.max_ng + kSmallWarps * 32, 32 * kSmallWarps) * sizeof(T);
+  const size_t sm = std::max<size_t>((size_t)pad4(lv.max_ng) + 4 * kSmallWarps * 32, 32 * kSmallWarps) * sizeof(T);
   const bool b16 = bf16_level<T>(h, l);
   StatScope sc(h, "group_bwd", l, lv.vals_group * (b16 ? 2.0 : E) + lv.vec_group * E + lv.idx_group_bwd, s);
   if (lv.split) {
     const size_t smx = ((size_t)pad4(lv.max_ng) + 256) * sizeof(T);
-    k_group_gather<T><<<dim3(lv.nlarge, 4), 256, 0, s>>>(lv.large_groups, lv.nlarge, lv.groups, h->idx,
-                                                         h->cptr, h->cslot, nullptr, x, lv.gs_off, fv.gs);
+    HIF_CUDA_TRY(launch_k(k_group_gather<T>, dim3(lv.nlarge, 4), 256, 0, s, lv.large_groups, lv.nlarge, lv.groups, h->idx,
+                                                         h->cptr, h->cslot, nullptr, x, lv.gs_off, fv.gs));
     bool done = false;
     if constexpr (sizeof(T) == 4) {
       if (b16) {
-        k_group_cols_split<T, bf16><<<lv.ncblk, 256, smx, s>>>(lv.cblk, lv.large_groups, lv.groups, h->idx,
+        HIF_CUDA_TRY(launch_k(k_group_cols_split<T, bf16>, lv.ncblk, 256, smx, s, lv.cblk, lv.large_groups, lv.groups, h->idx,
                                                                static_cast<const bf16 *>(h->bf16_vals),
-                                                               lv.gs_off, fv.gs, x);
+                                                               lv.gs_off, fv.gs, x));
         done = true;
       }
     }
     if (!done)
-      k_group_cols_split<T><<<lv.ncblk, 256, smx, s>>>(lv.cblk, lv.large_groups, lv.groups, h->idx, fv.vals,
-                                                       lv.gs_off, fv.gs, x);
+      HIF_CUDA_TRY(launch_k(k_group_cols_split<T>, lv.ncblk, 256, smx, s, lv.cblk, lv.large_groups, lv.groups, h->idx, fv.vals,
+                                                       lv.gs_off, fv.gs, x));
     note_launch(1 + (lv.nsmall ? 1 : 0));
     if (!lv.nsmall) return HIF_OK;
   }
@@ -1625,14 +1888,14 @@ int launch_group_bwd(Handle *h, const LevelDev &lv, int l, const FactorValues<T>
   const int grid = nlg + (lv.nsmall + kSmallWarps - 1) / kSmallWarps;
   if constexpr (sizeof(T) == 4) {
     if (b16) {
-      k_group_bwd_level<T, bf16><<<grid, kSmallWarps * 32, sm, s>>>(
+      HIF_CUDA_TRY(launch_k(k_group_bwd_level<T, bf16>, grid, kSmallWarps * 32, sm, s, 
           lv.large_groups, nlg, lv.small_groups, lv.nsmall, lv.groups, h->idx,
-          static_cast<const bf16 *>(h->bf16_vals), x);
+          static_cast<const bf16 *>(h->bf16_vals), x));
       return HIF_OK;
     }
   }
-  k_group_bwd_level<T><<<grid, kSmallWarps * 32, sm, s>>>(lv.large_groups, nlg, lv.small_groups,
-                                                          lv.nsmall, lv.groups, h->idx, fv.vals, x);
+  HIF_CUDA_TRY(launch_k(k_group_bwd_level<T>, grid, kSmallWarps * 32, sm, s, lv.large_groups, nlg, lv.small_groups,
+                                                          lv.nsmall, lv.groups, h->idx, fv.vals, x));
   return HIF_OK;
 }
 
@@ -1649,9 +1912,9 @@ int launch_cell_bwd(Handle *h, const LevelDev &lv, int l, const FactorValues<T> 
   if constexpr (sizeof(T) == 4) {
     if (b16) {
       size_t sm = ((size_t)lv.max_nI + lv.max_nB + 8 * kCellBwdThreads) * sizeof(T);
-      k_cell_bwd<T, bf16><<<lv.nbwd, kCellBwdThreads, sm, s>>>(lv.bwd, lv.cells, h->idx,
+      HIF_CUDA_TRY(launch_k(k_cell_bwd<T, bf16>, lv.nbwd, kCellBwdThreads, sm, s, lv.bwd, lv.cells, h->idx,
                                                                 static_cast<const bf16 *>(h->bf16_vals),
-                                                                fv.xI, x);
+                                                                fv.xI, x));
       return HIF_OK;
     }
   }
@@ -1659,15 +1922,15 @@ int launch_cell_bwd(Handle *h, const LevelDev &lv, int l, const FactorValues<T> 
     if (sf) {
       size_t sm = (size_t)kStages * kStageBytes + tma_bwd_smem_elems(lv) * sizeof(T);
       const int grid = tma_grid((const void *)k_cell_bwd_tma_S<T>, sm, lv.ncells, h->tma_ctas);
-      k_cell_bwd_tma_S<T><<<grid, kTmaThreads, sm, s>>>(lv.cells, lv.ncells, lv.chunk_of[1],
+      HIF_CUDA_TRY(launch_k(k_cell_bwd_tma_S<T>, grid, kTmaThreads, sm, s, lv.cells, lv.ncells, lv.chunk_of[1],
                                                          lv.chunk_tab[1], h->idx, fv.vals, x,
-                                                         h->scal + kScalErr, lv.max_nI, lv.max_nB);
+                                                         h->scal + kScalErr, lv.max_nI, lv.max_nB));
       return HIF_OK;
     }
   }
   {
     size_t sm = ((size_t)lv.max_nI + lv.max_nB + 8 * kCellBwdThreads) * sizeof(T);
-    k_cell_bwd<T><<<lv.nbwd, kCellBwdThreads, sm, s>>>(lv.bwd, lv.cells, h->idx, fv.vals, fv.xI, x);
+    HIF_CUDA_TRY(launch_k(k_cell_bwd<T>, lv.nbwd, kCellBwdThreads, sm, s, lv.bwd, lv.cells, h->idx, fv.vals, fv.xI, x));
   }
   return HIF_OK;
 }
@@ -1698,13 +1961,16 @@ int launch_upper(Handle *h, const FactorValues<T> &fv, T *x, cudaStream_t s) {
   cfg.blockDim = dim3(kUpperThreads);
   cfg.dynamicSmemBytes = h->upper_smem[pi];
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = h->upper_grid[pi];
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;  // see launch_k
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  const char *no_pdl = std::getenv("HIFCN_NO_PDL");
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = (no_pdl && no_pdl[0] == '1') ? 1 : 2;
   const void *fn = (const void *)k_upper_sweep<T>;
   if constexpr (sizeof(T) == 4)
     if (b16) fn = (const void *)k_upper_sweep<T, __nv_bfloat16>;
@@ -1718,7 +1984,7 @@ int apply_levels(Handle *h, const FactorValues<T> &fv, T *x, cudaStream_t s) {
   const size_t lim = 200 * 1024;
   for (const LevelDev &lv : h->lv)
     if ((size_t)(lv.max_nI + lv.max_nB + 8 * kCellBwdThreads) * sizeof(T) > lim ||
-        (size_t)(lv.max_ng + kSmallWarps * 32) * sizeof(T) > lim) {
+        (size_t)(pad4(lv.max_ng) + 4 * kSmallWarps * 32) * sizeof(T) > lim) {
       set_last_error("a box of the factor exceeds the shared-memory staging limit");
       return HIF_EINVAL;
     }
@@ -1727,14 +1993,19 @@ int apply_levels(Handle *h, const FactorValues<T> &fv, T *x, cudaStream_t s) {
     return HIF_EINVAL;
   }
   const int pi = sizeof(T) == 8 ? 0 : 1;
-  const bool fused = h->use_upper && h->upper_grid[pi] > 0;
-  const int lb = fused ? h->upper_lb : h->L;  // levels >= lb and the root are fused
-  for (int l = 0; l < h->L; ++l) {
-    if (fused && l >= lb) break;
+  // dependency-driven sweep: cells of levels >= flow_lb, entities of levels
+  // >= flow_lb - 1 and the root in one launch
+  const bool flow = h->use_flow && h->flow_grid[pi] > 0;
+  const bool fused = !flow && h->use_upper && h->upper_grid[pi] > 0;
+  const int lb = flow ? h->flow_lb : fused ? h->upper_lb : h->L;  // levels >= lb in one launch
+  for (int l = 0; l < lb; ++l) {
     HIF_TRY(launch_cell_fwd<T>(h, h->lv[l], l, fv, x, s));
+    if (flow && l == lb - 1) break;
     HIF_TRY(launch_group_fwd<T>(h, h->lv[l], l, fv, x, s));
   }
-  if (fused) {
+  if (flow) {
+    HIF_TRY(launch_flow<T>(h, fv, x, s));
+  } else if (fused) {
     HIF_TRY(launch_upper<T>(h, fv, x, s));
   } else if (h->root_n > 0) {
     const double nr = h->root_n, E = sizeof(T);
@@ -1749,15 +2020,15 @@ int apply_levels(Handle *h, const FactorValues<T> &fv, T *x, cudaStream_t s) {
       if constexpr (sizeof(T) == 4) {
         if (b16) {
           const bf16 *G = static_cast<const bf16 *>(h->bf16_vals) + h->root_G_off;
-          k_root_rows<T, bf16><<<units, 256, sm1, s>>>(h->root_n, ridx, G, x, rt);
-          k_root_cols<T, bf16><<<units, 256, sm2, s>>>(h->root_n, ridx, G, rt, x);
+          HIF_CUDA_TRY(launch_k(k_root_rows<T, bf16>, units, 256, sm1, s, h->root_n, ridx, G, x, rt));
+          HIF_CUDA_TRY(launch_k(k_root_cols<T, bf16>, units, 256, sm2, s, h->root_n, ridx, G, rt, x));
           done = true;
         }
       }
       if (!done) {
         const T *G = fv.vals + h->root_G_off;
-        k_root_rows<T><<<units, 256, sm1, s>>>(h->root_n, ridx, G, x, rt);
-        k_root_cols<T><<<units, 256, sm2, s>>>(h->root_n, ridx, G, rt, x);
+        HIF_CUDA_TRY(launch_k(k_root_rows<T>, units, 256, sm1, s, h->root_n, ridx, G, x, rt));
+        HIF_CUDA_TRY(launch_k(k_root_cols<T>, units, 256, sm2, s, h->root_n, ridx, G, rt, x));
       }
       note_launch();
     } else {
@@ -1765,17 +2036,17 @@ int apply_levels(Handle *h, const FactorValues<T> &fv, T *x, cudaStream_t s) {
       bool done = false;
       if constexpr (sizeof(T) == 4) {
         if (b16) {
-          k_root<T, bf16><<<1, kRootThreads, sm, s>>>(h->root_n, ridx,
+          HIF_CUDA_TRY(launch_k(k_root<T, bf16>, 1, kRootThreads, sm, s, h->root_n, ridx,
                                                       static_cast<const bf16 *>(h->bf16_vals) + h->root_G_off,
-                                                      x);
+                                                      x));
           done = true;
         }
       }
-      if (!done) k_root<T><<<1, kRootThreads, sm, s>>>(h->root_n, ridx, fv.vals + h->root_G_off, x);
+      if (!done) HIF_CUDA_TRY(launch_k(k_root<T>, 1, kRootThreads, sm, s, h->root_n, ridx, fv.vals + h->root_G_off, x));
     }
   }
-  for (int l = (fused ? lb : h->L) - 1; l >= 0; --l) {
-    HIF_TRY(launch_group_bwd<T>(h, h->lv[l], l, fv, x, s));
+  for (int l = lb - 1; l >= 0; --l) {
+    if (!(flow && l == lb - 1)) HIF_TRY(launch_group_bwd<T>(h, h->lv[l], l, fv, x, s));
     HIF_TRY(launch_cell_bwd<T>(h, h->lv[l], l, fv, x, s));
   }
   HIF_CUDA_TRY(cudaGetLastError());
@@ -1924,7 +2195,7 @@ void merged_units(const Handle *h, int kind, int level, int *units, size_t *smem
       break;
     default:
       *units = lv.ngroups ? lv.nlarge + (lv.nsmall + 7) / 8 : 0;
-      *smem = ((size_t)lv.max_ng + 256) * sizeof(float);
+      *smem = ((size_t)pad4(lv.max_ng) + 4 * 256) * sizeof(float);
       break;
   }
 }
@@ -1964,12 +2235,315 @@ int launch_merged_phase(int kind, int level, const int *pre, int K, int total, s
   return HIF_OK;
 }
 
+// Plan of the dependency-driven sweep (see k_flow_sweep): the levels it
+// covers (flow_lb is the lowest level >= 1 above every level whose cells
+// run in the S-form and whose entities are split over CTAs), its phases and
+// unit numbering, the dependency lists, the contribution scratch of its
+// levels and its launch shape per precision.  Built when HIFCN_FLOW=1: in a
+// CUDA graph the level-by-level launches measured faster on the benchmark
+// workload (346 against 386 us per FP32 apply at 1023^2).
+int build_flow_plan(Handle *h) {
+  h->use_flow = false;
+  const char *on = std::getenv("HIFCN_FLOW");
+  if (!(on && on[0] == '1')) return HIF_OK;
+  const int L = h->L;
+  if (L < 1) return HIF_OK;
+  int lb = -1;
+  for (int c = L; c >= 1; --c) {
+    bool ok = !h->lv[c - 1].split;
+    for (int l = c; l < L && ok; ++l) ok = !level_uses_sform(h, l) && !h->lv[l].split;
+    if (!ok) break;
+    lb = c;
+  }
+  if (lb < 0) return HIF_OK;
+  const int nr = h->root_n;
+  std::vector<std::vector<int>> small(L), large(L);
+  for (int l = lb - 1; l < L; ++l)
+    for (int g = 0; g < (int)h->lv_host[l].groups.size(); ++g)
+      (h->lv_host[l].groups[g].n <= 32 ? small[l] : large[l]).push_back(g);
+  auto gunits = [&](int l) { return (int)large[l].size() + ((int)small[l].size() + kFlowWarps - 1) / kFlowWarps; };
+  const int ru = (nr + kRootBlock - 1) / kRootBlock;
+  std::vector<FlowPhase> ph;
+  int total = 0;
+  auto add = [&](int type, int level, int units) {
+    if (units <= 0) return;
+    const bool b16 = h->has_bf16 && (type == kPhaseRootRows || type == kPhaseRootCols ? L : level) >= h->bf16_lb;
+    ph.push_back(FlowPhase{type, level, units, total, b16 ? 1 : 0, 0});
+    total += units;
+  };
+  add(kPhaseGroupFwd, lb - 1, gunits(lb - 1));
+  for (int l = lb; l < L; ++l) {
+    add(kPhaseCellFwd, l, h->lv[l].nfwd);
+    add(kPhaseGroupFwd, l, gunits(l));
+  }
+  if (nr > 0) {
+    add(kPhaseRootRows, 0, ru);
+    add(kPhaseRootCols, 0, ru);
+  }
+  for (int l = L - 1; l >= lb; --l) {
+    add(kPhaseGroupBwd, l, gunits(l));
+    add(kPhaseCellBwd, l, h->lv[l].nbwd);
+  }
+  add(kPhaseGroupBwd, lb - 1, gunits(lb - 1));
+  if (total == 0) return HIF_OK;
+
+  // contribution slots of the flow levels: one scratch, a base per level
+  std::vector<long long> cbase(L, -1);
+  long long cflow = 0;
+  for (int l = lb; l < L; ++l) {
+    cbase[l] = cflow;
+    cflow += h->lv_host[l].contrib_slots;
+  }
+  // ids of the data the units touch: x, xI, flow contributions, the shared
+  // contribution scratch (level lb - 1, only read), the root scratch
+  const long long NX = h->N, idXI = NX, idCF = 2 * NX, idCR = idCF + cflow,
+                  idRT = idCR + h->max_contrib, nid = idRT + nr;
+  std::vector<int> last_w(nid, -1), rhead(nid, -1), rnode_u, rnode_next;
+  std::vector<int> dep_ptr(1, 0), dep_idx, deps;
+  std::vector<long long> R, W;
+  const int *idx = h->idx_host.data();
+  auto slot_id = [&](int l, long long slot) { return l >= lb ? idCF + cbase[l] + slot : idCR + slot; };
+  auto group_rw = [&](int l, int g, bool fwd) {
+    const GroupDesc &G = h->lv_host[l].groups[g];
+    for (int i = 0; i < G.n; ++i) {
+      const long long d = idx[G.idx_off + i];
+      R.push_back(d);
+      W.push_back(d);
+      if (fwd)
+        for (long long q = h->cptr_host[G.cptr_off + i]; q < h->cptr_host[G.cptr_off + i + 1]; ++q)
+          R.push_back(slot_id(l, h->cslot_host[q]));
+    }
+  };
+  auto groups_rw = [&](int l, int uu, bool fwd) {
+    const int nl = (int)large[l].size();
+    if (uu < nl) {
+      group_rw(l, large[l][uu], fwd);
+    } else {
+      for (int t = (uu - nl) * kFlowWarps; t < std::min((int)small[l].size(), (uu - nl + 1) * kFlowWarps); ++t)
+        group_rw(l, small[l][t], fwd);
+    }
+  };
+  const int *ridx = idx + h->root_idx_off;
+  for (const FlowPhase &P : ph) {
+    for (int uu = 0; uu < P.units; ++uu) {
+      const int u = P.base + uu;
+      R.clear();
+      W.clear();
+      switch (P.type) {
+        case kPhaseCellFwd: {
+          const CellItem &it = h->lv[P.level].fwd_host[uu];
+          const CellDesc &c = h->lv_host[P.level].cells[it.cell];
+          for (int i = 0; i < c.nI; ++i) R.push_back(idx[c.I_off + i]);
+          for (int r = it.a; r < it.b; ++r)
+            W.push_back(r < c.nB ? slot_id(P.level, c.C_off + r) : idXI + idx[c.I_off + r - c.nB]);
+          break;
+        }
+        case kPhaseGroupFwd:
+          groups_rw(P.level, uu, true);
+          break;
+        case kPhaseRootRows: {
+          const int r_lo = uu * kRootBlock, r_hi = std::min(nr, r_lo + kRootBlock);
+          for (int i = 0; i < std::min<long long>(nr, pad4(r_hi)); ++i) R.push_back(ridx[i]);
+          for (int r = r_lo; r < r_hi; ++r) W.push_back(idRT + r);
+          break;
+        }
+        case kPhaseRootCols: {
+          const int c_lo = uu * kRootBlock, c_hi = std::min(nr, c_lo + kRootBlock);
+          for (int i = c_lo; i < nr; ++i) R.push_back(idRT + i);
+          for (int c = c_lo; c < c_hi; ++c) W.push_back(ridx[c]);
+          break;
+        }
+        case kPhaseGroupBwd:
+          groups_rw(P.level, uu, false);
+          break;
+        default: {  // kPhaseCellBwd
+          const CellItem &it = h->lv[P.level].bwd_host[uu];
+          const CellDesc &c = h->lv_host[P.level].cells[it.cell];
+          for (int i = 0; i < c.nI; ++i) R.push_back(idXI + idx[c.I_off + i]);
+          for (int q = 0; q < c.nB; ++q) R.push_back(idx[c.B_off + q]);
+          for (int col = it.a; col < it.b; ++col) W.push_back(idx[c.I_off + col]);
+          break;
+        }
+      }
+      deps.clear();
+      for (long long d : R)
+        if (last_w[d] >= 0) deps.push_back(last_w[d]);
+      for (long long d : W) {
+        if (last_w[d] >= 0) deps.push_back(last_w[d]);
+        for (int n = rhead[d]; n >= 0; n = rnode_next[n]) deps.push_back(rnode_u[n]);
+      }
+      std::sort(deps.begin(), deps.end());
+      deps.erase(std::unique(deps.begin(), deps.end()), deps.end());
+      dep_idx.insert(dep_idx.end(), deps.begin(), deps.end());
+      dep_ptr.push_back((int)dep_idx.size());
+      for (long long d : R) {
+        if (rhead[d] >= 0 && rnode_u[rhead[d]] == u) continue;
+        rnode_u.push_back(u);
+        rnode_next.push_back(rhead[d]);
+        rhead[d] = (int)rnode_u.size() - 1;
+      }
+      for (long long d : W) {
+        last_w[d] = u;
+        rhead[d] = -1;
+      }
+    }
+  }
+
+  // shared memory of the largest unit, per precision, and the launch shape
+  size_t need_e = 256;
+  for (const FlowPhase &P : ph) {
+    const LevelDev &lv = h->lv[P.level];
+    switch (P.type) {
+      case kPhaseCellFwd: need_e = std::max<size_t>(need_e, pad4(lv.max_nI)); break;
+      case kPhaseGroupFwd: need_e = std::max<size_t>(need_e, pad4(lv.max_ng)); break;
+      case kPhaseRootRows: need_e = std::max<size_t>(need_e, pad4(nr)); break;
+      case kPhaseRootCols: need_e = std::max<size_t>(need_e, (size_t)kFlowThreads + nr); break;
+      case kPhaseGroupBwd:
+        need_e = std::max<size_t>(need_e, (size_t)pad4(lv.max_ng) + 4 * kFlowThreads);
+        break;
+      default:
+        need_e = std::max<size_t>(need_e, (size_t)8 * kFlowThreads + lv.max_nI + lv.max_nB);
+        break;
+    }
+  }
+  int sms = 0, dev = 0;
+  HIF_CUDA_TRY(cudaGetDevice(&dev));
+  HIF_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  for (int pi = 0; pi < 2; ++pi) {
+    const size_t E = pi == 0 ? 8 : 4;
+    const size_t smem = need_e * E;
+    h->flow_grid[pi] = 0;
+    if (smem > 200 * 1024) continue;
+    const void *fn = pi == 0 ? (const void *)k_flow_sweep<double> : (const void *)k_flow_sweep<float>;
+    HIF_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kFlowThreads, smem) != cudaSuccess) {
+      cudaGetLastError();
+      occ = 0;
+    }
+    if (occ < 1) continue;
+    h->flow_grid[pi] = std::max(1, std::min(total, occ * sms));
+    h->flow_smem[pi] = smem;
+    // algorithmic bytes: the flow levels in the G-form, the root, and the
+    // entity steps of level lb - 1
+    const double EV = (pi == 1 && h->has_bf16) ? 2.0 : (double)E;
+    double b = 0;
+    for (int l = lb; l < L; ++l) b += level_bytes_gform(h->lv[l], (double)E, EV);
+    const LevelDev &lg = h->lv[lb - 1];
+    b += 2 * lg.vals_group * EV + (2 * lg.vec_group + lg.contrib) * E + lg.idx_group + lg.idx_group_bwd +
+         lg.cslot_bytes;
+    b += (double)nr * (nr + 1) * EV + 4.0 * nr * E + 8.0 * nr;
+    h->flow_bytes[pi] = b;
+  }
+  if (h->flow_grid[0] == 0 && h->flow_grid[1] == 0) return HIF_OK;
+
+  std::vector<UpperLevel> ul(L);
+  for (int l = 0; l < L; ++l) {
+    const LevelDev &lv = h->lv[l];
+    ul[l] = UpperLevel{lv.fwd, lv.bwd, lv.cells, lv.groups, lv.small_groups, lv.large_groups,
+                       lv.nfwd, lv.nbwd, lv.nsmall, lv.nlarge, cbase[l]};
+  }
+  HIF_TRY(dev_alloc(h, (void **)&h->flow_phases, ph.size() * sizeof(FlowPhase)));
+  HIF_TRY(dev_alloc(h, (void **)&h->flow_levels, ul.size() * sizeof(UpperLevel)));
+  HIF_TRY(dev_alloc(h, (void **)&h->flow_dep_ptr, dep_ptr.size() * sizeof(int)));
+  HIF_TRY(dev_alloc(h, (void **)&h->flow_dep_idx, std::max<size_t>(1, dep_idx.size()) * sizeof(int)));
+  HIF_TRY(dev_alloc(h, (void **)&h->flow_flags, (size_t)total * sizeof(int)));
+  HIF_TRY(dev_alloc(h, (void **)&h->flow_ctl, 4 * sizeof(int)));
+  HIF_TRY(dev_alloc(h, &h->flow_contrib[0], std::max<long long>(1, cflow) * sizeof(double)));
+  if (h->has_f32) HIF_TRY(dev_alloc(h, &h->flow_contrib[1], std::max<long long>(1, cflow) * sizeof(float)));
+  HIF_CUDA_TRY(cudaMemcpy(h->flow_phases, ph.data(), ph.size() * sizeof(FlowPhase), cudaMemcpyHostToDevice));
+  HIF_CUDA_TRY(cudaMemcpy(h->flow_levels, ul.data(), ul.size() * sizeof(UpperLevel), cudaMemcpyHostToDevice));
+  HIF_CUDA_TRY(cudaMemcpy(h->flow_dep_ptr, dep_ptr.data(), dep_ptr.size() * sizeof(int), cudaMemcpyHostToDevice));
+  if (!dep_idx.empty())
+    HIF_CUDA_TRY(cudaMemcpy(h->flow_dep_idx, dep_idx.data(), dep_idx.size() * sizeof(int), cudaMemcpyHostToDevice));
+  HIF_CUDA_TRY(cudaMemset(h->flow_flags, 0, (size_t)total * sizeof(int)));
+  HIF_CUDA_TRY(cudaMemset(h->flow_ctl, 0, 4 * sizeof(int)));
+  // L2 prefetch ranges: the entity blocks of level lb - 1, everything of the
+  // levels >= lb and the root (stored after them), the index and CSR ranges
+  // the units read (HIFCN_FLOW_PREFETCH=0 leaves them out)
+  FlowPrefetch pf{};
+  const char *pfe = std::getenv("HIFCN_FLOW_PREFETCH");
+  if (!(pfe && pfe[0] == '0')) {
+    const long long BIG = 1LL << 62;
+    long long v0a = BIG, v1a = 0, v0b = BIG, i0 = BIG, i1 = 0, c0 = BIG, c1 = 0;
+    for (const GroupDesc &g : h->lv_host[lb - 1].groups) {
+      v0a = std::min(v0a, g.H_off);
+      v1a = std::max(v1a, g.H_off + (long long)g.n * pad4(g.n));
+      i0 = std::min(i0, g.idx_off);
+      i1 = std::max(i1, g.idx_off + g.n);
+      c0 = std::min(c0, g.cptr_off);
+      c1 = std::max(c1, g.cptr_off + g.n + 1);
+    }
+    for (int l = lb; l < L; ++l) {
+      for (const CellDesc &c : h->lv_host[l].cells) {
+        v0b = std::min(v0b, c.G_off);
+        i0 = std::min(i0, std::min(c.I_off, c.B_off));
+        i1 = std::max(i1, std::max(c.I_off + c.nI, c.B_off + c.nB));
+      }
+      for (const GroupDesc &g : h->lv_host[l].groups) {
+        v0b = std::min(v0b, g.H_off);
+        i0 = std::min(i0, g.idx_off);
+        i1 = std::max(i1, g.idx_off + g.n);
+        c0 = std::min(c0, g.cptr_off);
+        c1 = std::max(c1, g.cptr_off + g.n + 1);
+      }
+    }
+    if (nr > 0) {
+      v0b = std::min(v0b, h->root_G_off);
+      i0 = std::min(i0, h->root_idx_off);
+      i1 = std::max(i1, h->root_idx_off + nr);
+    }
+    if (v0a < v1a) {
+      pf.v0[0] = v0a;
+      pf.v1[0] = v1a;
+    }
+    if (v0b < h->nvals) {
+      pf.v0[1] = v0b;
+      pf.v1[1] = h->nvals;
+    }
+    if (i0 < i1) {
+      pf.i0 = i0;
+      pf.i1 = std::min<long long>(i1, (long long)h->idx_host.size());
+    }
+    if (c0 < c1) {
+      pf.c0 = c0;
+      pf.c1 = std::min<long long>(c1, (long long)h->cptr_host.size());
+      pf.s0 = h->cptr_host[pf.c0];
+      pf.s1 = h->cptr_host[pf.c1 - 1];
+    }
+  }
+  h->flow_pf = pf;
+  h->flow_lb = lb;
+  h->flow_nphase = (int)ph.size();
+  h->flow_units = total;
+  h->use_flow = true;
+  return HIF_OK;
+}
+
+template <typename T>
+int launch_flow(Handle *h, const FactorValues<T> &fv, T *x, cudaStream_t s) {
+  const int pi = sizeof(T) == 8 ? 0 : 1;
+  StatScope sc(h, "upper_flow", h->flow_lb, h->flow_bytes[pi], s);
+  const __nv_bfloat16 *v16 = nullptr;
+  if (sizeof(T) == 4 && h->has_bf16) v16 = static_cast<const __nv_bfloat16 *>(h->bf16_vals);
+  k_flow_sweep<T><<<h->flow_grid[pi], kFlowThreads, h->flow_smem[pi], s>>>(
+      h->flow_phases, h->flow_nphase, h->flow_units, h->flow_levels, h->flow_dep_ptr, h->flow_dep_idx,
+      h->flow_flags, h->flow_ctl, h->idx, h->cptr, h->cslot, fv.vals, v16, fv.contrib,
+      static_cast<T *>(h->flow_contrib[pi]), fv.xI, x, h->root_n, h->idx + h->root_idx_off, h->root_G_off,
+      reinterpret_cast<T *>(h->upper_rt), h->scal + kScalErr, h->flow_pf);
+  note_launch();
+  HIF_CUDA_TRY(cudaGetLastError());
+  return HIF_OK;
+}
+
 // Plan of the fused upper-level sweep: which levels it covers (the top levels
 // whose factor data is small, so that a launch per step would cost more than
 // the step), its phases and their work units, and its launch shape per
 // precision.  HIFCN_NO_FUSED=1 keeps one launch per step (A/B measurement).
 int build_upper_plan(Handle *h) {
   h->use_upper = false;
+  HIF_TRY(build_flow_plan(h));
+  if (h->use_flow) return HIF_OK;
   const char *off = std::getenv("HIFCN_NO_FUSED");
   if (off && off[0] == '1') return HIF_OK;
   if (h->root_split) return HIF_OK;  // a large root is spread over the whole GPU
@@ -2024,7 +2598,7 @@ int build_upper_plan(Handle *h) {
     if (p.type == kPhaseCellBwd)
       need_e = std::max<size_t>(need_e, (size_t)8 * kUpperThreads + lv.max_nI + lv.max_nB);
     if (p.type == kPhaseGroupFwd) need_e = std::max<size_t>(need_e, pad4(lv.max_ng));
-    if (p.type == kPhaseGroupBwd) need_e = std::max<size_t>(need_e, (size_t)lv.max_ng + kUpperThreads);
+    if (p.type == kPhaseGroupBwd) need_e = std::max<size_t>(need_e, (size_t)pad4(lv.max_ng) + 4 * kUpperThreads);
   }
   HIF_TRY(upper_launch_shape<double>(h, need_e * sizeof(double), max_units));
   HIF_TRY(upper_launch_shape<float>(h, need_e * sizeof(float), max_units));
@@ -2086,10 +2660,10 @@ int apply_inverse(Handle *h, const double *x, double *y, int precision, cudaStre
     return apply_inplace_f64(h, y, s);
   }
   if ((precision != HIF_FP32 && precision != HIF_FP32_BF16TOP) || !h->has_f32) return HIF_EINVAL;
-  k_to_float<<<h->nblocks_vec, 256, 0, s>>>(x, h->f32.work, h->N);
+  HIF_CUDA_TRY(launch_k(k_to_float, h->nblocks_vec, 256, 0, s, x, h->f32.work, h->N));
   note_launch();
   HIF_TRY(apply_inplace_f32(h, h->f32.work, s));
-  k_to_double<<<h->nblocks_vec, 256, 0, s>>>(h->f32.work, y, h->N);
+  HIF_CUDA_TRY(launch_k(k_to_double, h->nblocks_vec, 256, 0, s, h->f32.work, y, h->N));
   note_launch();
   HIF_CUDA_TRY(cudaGetLastError());
   return HIF_OK;

@@ -106,6 +106,7 @@ struct LevelDev {
   int ncells = 0, ngroups = 0;
   int nfwd = 0, nbwd = 0;             // work items of the cell kernels
   CellItem *fwd = nullptr, *bwd = nullptr;  // device
+  std::vector<CellItem> fwd_host, bwd_host;  // host copies (dependency analysis)
   CellItem *fwd1 = nullptr, *bwd1 = nullptr;  // device: one item per cell (merged batched steps)
   int item_target = 0;                // CTAs per launch the items were cut for (see build_items)
   bool has_S = false;                 // S = A_II^{-1} stored for the cells (S-form possible)
@@ -153,9 +154,23 @@ struct UpperLevel {
   const GroupDesc *groups;
   const int *small, *large;
   int nfwd, nbwd, nsmall, nlarge;
+  long long cbase = -1;  // dependency-driven sweep: offset of the level's contribution
+                         // slots in its own scratch (-1: the shared per-level scratch)
 };
 struct UpperPhase {
   int type, level, units, pad;
+};
+// A phase of the dependency-driven sweep: its units are the global unit
+// numbers [base, base + units); bf16: values from the BF16 pool.
+struct FlowPhase {
+  int type, level, units, base, bf16, pad;
+};
+// Ranges of the static data the dependency-driven sweep reads, prefetched
+// into L2 when it starts: value pool elements [v0[k], v1[k]), index pool
+// entries [i0, i1), contribution CSR pointers [c0, c1) and slots [s0, s1).
+struct FlowPrefetch {
+  long long v0[2], v1[2];
+  long long i0, i1, c0, c1, s0, s1;
 };
 
 // Device view of one handle's FP32 apply and CG state, read by the merged
@@ -254,6 +269,21 @@ struct hif_handle {
   int tma_ctas = 0;                           // CTAs per SM of the leaf kernels (0: as many as fit)
   hifcn::HandleView *view = nullptr;          // device view for the merged batched steps
   bool view_ok = false;                       // the merged batched path can take this handle
+  // dependency-driven sweep (apply.cu): the cell and group steps of levels
+  // >= flow_lb, the root, and the group steps of level flow_lb - 1 run in one
+  // persistent kernel whose work units wait only for the units they depend on
+  bool use_flow = false;
+  int flow_lb = 0, flow_nphase = 0, flow_units = 0;
+  hifcn::FlowPhase *flow_phases = nullptr;           // device
+  hifcn::UpperLevel *flow_levels = nullptr;          // device
+  int *flow_dep_ptr = nullptr, *flow_dep_idx = nullptr;  // device CSR of unit dependencies
+  int *flow_flags = nullptr;                         // device: epoch at which each unit finished
+  int *flow_ctl = nullptr;                           // device: claim ticket, done ticket, epoch
+  void *flow_contrib[2] = {nullptr, nullptr};        // contribution slots of the flow levels
+  int flow_grid[2] = {0, 0};                         // persistent CTAs, FP64 / FP32
+  size_t flow_smem[2] = {0, 0};
+  double flow_bytes[2] = {0, 0};
+  hifcn::FlowPrefetch flow_pf{};                     // L2 prefetch ranges (empty: none)
   size_t upper_smem[2] = {0, 0};              // dynamic shared memory, FP64 / FP32
   int upper_grid[2] = {0, 0};                 // CTAs of the cluster, FP64 / FP32
   double upper_bytes[2] = {0, 0};             // algorithmic bytes per launch, FP64 / FP32
