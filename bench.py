@@ -56,6 +56,8 @@ def _args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--eps", type=float, default=1e-6)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="keep the default launch shapes (profiling runs: the first launches are the timed kind)")
     p.add_argument("--n", type=int, default=1024,
                    help="grid intervals per axis (same recipe); 1024 is the benchmark workload, "
                         "smaller values are for profiling captures only")
@@ -285,7 +287,8 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
         tf = time.perf_counter() - t0
         H.hif_set_reaction(h, 1, 1.0, 1.0)
         t1 = time.perf_counter()
-        H.hif_autotune(h)  # per-level CTA cut of the apply, by timing (outside the timed steps)
+        if not args.no_autotune:
+            H.hif_autotune(h)  # per-level CTA cut of the apply, by timing (outside the timed steps)
         tuning_s[precision] = round(time.perf_counter() - t1, 3)
         return h, tf
 
