@@ -297,7 +297,10 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
             dist.barrier()
         torch.cuda.synchronize()
 
-    def timed_steps(h, K, W_, per_step=True):
+    def timed_steps(h, K, W_, per_step=True, queued=False):
+        """K CN steps after W_ warm-up steps: queued (one cn_steps call, no host
+        synchronization between steps: the throughput of a time loop) or one
+        cn_step call per step (per-step events: the latency of a single call)."""
         u = torch.from_numpy(w.u0.ravel().copy()).to(dev)
         v = torch.empty_like(u)
         its = []
@@ -308,12 +311,16 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
         barrier()
         lc0 = H.hif_launch_count()
         evs[0].record(stream)
-        for k in range(K):
-            v, it = H.cn_step(h, u, out=v)
-            u, v = v, u
-            its.append(it)
-            if per_step:
-                evs[k + 1].record(stream)
+        if queued:
+            its = H.cn_steps(h, u, K)
+            per_step = False
+        else:
+            for k in range(K):
+                v, it = H.cn_step(h, u, out=v)
+                u, v = v, u
+                its.append(it)
+                if per_step:
+                    evs[k + 1].record(stream)
         if not per_step:
             evs[K].record(stream)
         torch.cuda.synchronize()
@@ -328,8 +335,11 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
     info32 = H.hif_query(h32)
     clocks = ClockSampler(local)
     clocks.start()
-    t_ms, lat, its, launches, _ = timed_steps(h32, args.steps, args.warmup)
+    t_ms, _, its, launches, _ = timed_steps(h32, args.steps, args.warmup, queued=True)
     clk = clocks.stop()
+    # ---- per-call latency: one cn_step call per step
+    K_lat = min(args.steps, 300)
+    _, lat, _, _, _ = timed_steps(h32, K_lat, 0, per_step=True)
     # ---- instrumented pass of the same steps: per-kernel device time
     H.hif_stats_enable(h32, True)
     t_ms_stats, _, _, _, _ = timed_steps(h32, args.steps, 0, per_step=False)
@@ -362,7 +372,8 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
     h32.close()
     # ---- plain FP64 path on the same GPU
     h64, tf64 = make(H.HIF_FP64)
-    t64_ms, lat64, its64, _, _ = timed_steps(h64, max(1, args.steps // 2), args.warmup)
+    t64_ms, _, its64, _, _ = timed_steps(h64, max(1, args.steps // 2), args.warmup, queued=True)
+    _, lat64, _, _, _ = timed_steps(h64, min(max(1, args.steps // 2), 300), 0, per_step=True)
     info64 = H.hif_query(h64)
     h64.close()
 
@@ -461,7 +472,10 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
                    "precision": "factor FP32 (apply FP32), CG FP64",
                    "global_batch": world, "parallelism": f"replicas x{world}" if world > 1 else "single",
                    "l2": "inputs larger than L2: the ~1 GB FP32 factor streams every apply"},
-        "latency_ms": {"p50": pct(lat_sorted, 50), "p99": pct(lat_sorted, 99)},
+        "api": "cn_steps: the K timed steps queued in one call (no host synchronization between "
+               "steps; per-step iteration counts read back at the end)",
+        "latency_ms": {"p50": pct(lat_sorted, 50), "p99": pct(lat_sorted, 99),
+                       "api": f"cn_step, one call per step ({len(lat)} steps, per-step CUDA events)"},
         "iters_per_step": round(iters_per_step, 3),
         "cg_iters_per_s": round(world * sum(its) / (t_ms / 1e3), 2),
         "t_f_s": {"fp32": round(tf32, 3), "fp64": round(tf64, 3)},

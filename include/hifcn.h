@@ -198,6 +198,27 @@ int cn_step(hif_handle *h, const double *u_k, const double *r_k, double *u_k1, i
             hif_stream stream);
 
 /* ---------------------------------------------------------------------------
+ * cn_steps - nsteps Crank-Nicolson steps (Eq. CN2, Algorithm 1's time loop)
+ * of one operator, advancing u in place, queued on the stream with no host
+ * synchronization between steps: each step's right-hand side, captured PCG
+ * solve (convergence decided on the device) and result copy follow one
+ * another on the GPU, and the per-step iteration counts and status are read
+ * back once, at the end (the call returns after the last step completed).
+ *   u       device, N doubles, u_0 on entry, u_nsteps on return.
+ *   r_k     device, N doubles used as the source of every step, or NULL for
+ *           the built-in reaction evaluated at each step's u_k.
+ *   nsteps  >= 0.
+ *   iters   host, nsteps ints (may be NULL): PCG iterations of each step.
+ * Errors: HIF_EINVAL (bad arguments, no factor); HIF_ENOCONV if some step did
+ * not reach the tolerance within cg_maxit (u is advanced regardless, as with
+ * cn_step); HIF_ETIMEOUT if a bounded device wait expired; HIF_ECUDA.
+ * With statistics on or the direct solver, the steps are taken one by one.
+ * The handle keeps a small device buffer for the per-step records (grown to
+ * the largest nsteps seen, freed by hif_destroy). Not part of the paper's
+ * method: it is the same sequence of steps as nsteps calls of cn_step. */
+int cn_steps(hif_handle *h, double *u, const double *r_k, int nsteps, int *iters, hif_stream stream);
+
+/* ---------------------------------------------------------------------------
  * cn_step_batched - one CN step (as cn_step) for each of count handles, which
  * may differ in dimension, size and coefficients (independent problems, the
  * loop body of Algorithm 1 for each).  Results equal those of calling cn_step

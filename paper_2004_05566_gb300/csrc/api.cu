@@ -591,6 +591,7 @@ hif_handle::~hif_handle() {
   }
   for (auto e : event_pool) cudaEventDestroy(e);
   for (void *p : allocations) cudaFree(p);
+  if (step_rec) cudaFree(step_rec);
   if (host_scal) cudaFreeHost(host_scal);
 }
 
@@ -755,6 +756,11 @@ int cn_step(hif_handle *h, const double *u_k, const double *r_k, double *u_k1, i
             hif_stream stream) {
   if (!h || !u_k || !u_k1 || !h->factor_ok) return HIF_EINVAL;
   return cn(h, u_k, r_k, u_k1, iters, (cudaStream_t)stream);
+}
+
+int cn_steps(hif_handle *h, double *u, const double *r_k, int nsteps, int *iters, hif_stream stream) {
+  if (!h || !u || nsteps < 0 || !h->factor_ok) return HIF_EINVAL;
+  return cn_multi(h, u, r_k, nsteps, iters, (cudaStream_t)stream);
 }
 
 int cn_step_batched(hif_handle *const *hs, int count, const double *const *u_k,

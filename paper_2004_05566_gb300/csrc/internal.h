@@ -293,6 +293,8 @@ struct hif_handle {
   double *scal = nullptr;      // device scalars (see pcg.cu)
   unsigned *tickets = nullptr; // last-block counters of the captured loop's kernels (4)
   double *host_scal = nullptr; // pinned host mirror
+  double *step_rec = nullptr;  // cn_steps: per-step records (iterations, status), device
+  int step_rec_cap = 0;        // steps step_rec holds (grown on demand, freed with the handle)
   int nblocks_vec = 0;
 
   std::vector<void *> allocations;
@@ -358,6 +360,7 @@ int launch_merged_phase(int kind, int level, const int *pre, int K, int total, s
                         HandleView *const *views, const int *active, cudaStream_t s);
 int pcg(Handle *h, const double *b, double *x, int *iters, double *relres, cudaStream_t s);
 int cn(Handle *h, const double *u, const double *r, double *u1, int *iters, cudaStream_t s);
+int cn_multi(Handle *h, double *u, const double *r, int nsteps, int *iters, cudaStream_t s);
 int cn_batched(Handle *const *hs, int count, const double *const *u, const double *const *r,
                double *const *u1, int *iters, cudaStream_t s);
 int gpu_setup(Handle *h, const double *a_nodes, cudaStream_t s);

@@ -661,6 +661,77 @@ int cn(Handle *h, const double *u, const double *r, double *u1, int *iters, cuda
   return solve_core(h, h->g, u, u1, iters, nullptr, s);
 }
 
+namespace {
+// record of one step of cn_multi: iterations, convergence flag, b.b, error flag
+__global__ void k_step_record(const double *__restrict__ sc, double *__restrict__ rec) {
+  if (threadIdx.x == 0) {
+    rec[0] = sc[S_IT];
+    rec[1] = sc[S_CONV];
+    rec[2] = sc[S_BB];
+    rec[3] = sc[kScalErr];
+  }
+}
+}  // namespace
+
+// nsteps CN steps of u in place, queued on s without host synchronization
+// between them (the captured PCG solve decides convergence on the device);
+// per-step iteration counts and status are recorded on the device and read
+// once at the end.  Configurations without the captured solve (statistics
+// on, direct solver) take the steps one by one.
+int cn_multi(Handle *h, double *u, const double *r, int nsteps, int *iters, cudaStream_t s) {
+  if (nsteps <= 0) return HIF_OK;
+  if (!h->use_graph || h->stats_on || h->opt.solver == 1) {
+    int status = HIF_OK;
+    for (int k = 0; k < nsteps; ++k) {
+      const int st = cn(h, u, r, u, iters ? iters + k : nullptr, s);
+      if (st != HIF_OK && st != HIF_ENOCONV) return st;
+      if (status == HIF_OK) status = st;
+    }
+    return status;
+  }
+  if (nsteps > h->step_rec_cap) {
+    if (h->step_rec) {
+      HIF_CUDA_TRY(cudaStreamSynchronize(s));
+      cudaFree(h->step_rec);
+      h->step_rec = nullptr;
+      h->step_rec_cap = 0;
+    }
+    HIF_CUDA_TRY(cudaMalloc((void **)&h->step_rec, (size_t)nsteps * 4 * sizeof(double)));
+    h->step_rec_cap = nsteps;
+  }
+  const bool f32 = reduced_apply(h);
+  const bool warm = h->opt.x0_mode == 1;
+  const int slot = graph_slot(h);
+  if (f32) HIF_TRY(ensure_pcg_graph<float>(h, h->f32.work, slot, s));
+  else HIF_TRY(ensure_pcg_graph<double>(h, h->z, slot, s));
+  PcgGraph *G = static_cast<PcgGraph *>(h->pcg_graph[slot]);
+  const size_t vb = h->N * sizeof(double);
+  for (int k = 0; k < nsteps; ++k) {
+    HIF_TRY(cn_rhs(h, u, r, h->g, s));
+    if (warm) HIF_CUDA_TRY(cudaMemcpyAsync(h->xsol, u, vb, cudaMemcpyDeviceToDevice, s));
+    HIF_CUDA_TRY(cudaGraphLaunch(G->exec, s));
+    HIF_CUDA_TRY(cudaMemcpyAsync(u, h->xsol, vb, cudaMemcpyDeviceToDevice, s));
+    k_step_record<<<1, 32, 0, s>>>(h->scal, h->step_rec + 4 * (size_t)k);
+    note_launch(2);
+  }
+  HIF_CUDA_TRY(cudaGetLastError());
+  std::vector<double> rec((size_t)nsteps * 4);
+  HIF_CUDA_TRY(cudaMemcpyAsync(rec.data(), h->step_rec, rec.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  HIF_CUDA_TRY(cudaStreamSynchronize(s));
+  int status = HIF_OK;
+  bool timed_out = false;
+  for (int k = 0; k < nsteps; ++k) {
+    const double *q = rec.data() + 4 * (size_t)k;
+    const int it = (int)q[0];
+    note_launch((int)(G->prologue + (long long)it * G->body));
+    if (iters) iters[k] = it;
+    if (q[3] != 0.0) timed_out = true;
+    if (status == HIF_OK && q[2] != 0.0 && q[1] == 0.0) status = HIF_ENOCONV;
+  }
+  if (timed_out) return take_timeout(h);
+  return status;
+}
+
 // ------------------------------------------------- merged batched CN steps
 //
 // For handles with a device view (FP32 apply, no split levels), one batched

@@ -28,7 +28,7 @@ EXPORTED = ("hif_default_options", "hif_setup", "hif_import_factor", "hif_export
             "hif_apply", "hif_matvec", "pcg_solve", "cn_step", "hif_set_reaction", "hif_query",
             "hif_destroy", "hif_strerror", "hif_last_error", "hif_stats_enable", "hif_stats_read",
             "hif_launch_count", "hif_apply_noalloc", "cn_step_batched", "hif_set_coefficient",
-            "hif_refactor", "hif_autotune")
+            "hif_refactor", "hif_autotune", "cn_steps")
 
 
 class HifGrid(ctypes.Structure):
@@ -81,6 +81,7 @@ def lib():
     L.hif_matvec.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
     L.pcg_solve.argtypes = [c_void_p, c_void_p, c_void_p, POINTER(c_int), POINTER(c_double), c_void_p]
     L.cn_step.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_int), c_void_p]
+    L.cn_steps.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p]
     L.hif_set_reaction.argtypes = [c_void_p, c_int, c_double, c_double]
     L.hif_query.argtypes = [c_void_p, POINTER(HifInfo)]
     L.hif_destroy.argtypes = [c_void_p]
@@ -104,7 +105,7 @@ def lib():
     L.hif_autotune.argtypes = [c_void_p, c_void_p]
     L.hif_autotune.restype = c_int
     for name in ("hif_setup", "hif_import_factor", "hif_export_factor", "hif_apply", "hif_matvec",
-                 "pcg_solve", "cn_step", "hif_set_reaction", "hif_query", "hif_destroy",
+                 "pcg_solve", "cn_step", "cn_steps", "hif_set_reaction", "hif_query", "hif_destroy",
                  "hif_stats_enable", "hif_stats_read"):
         getattr(L, name).restype = c_int
     _lib = L
@@ -262,6 +263,15 @@ def cn_step(h: Handle, u: torch.Tensor, r: torch.Tensor = None, out: torch.Tenso
     _check("cn_step", lib().cn_step(h.ptr, _vec(u, h.N, "u"), rp, _vec(out, h.N, "out"), byref(it),
                                     _stream(stream)))
     return out, it.value
+
+
+def cn_steps(h: Handle, u: torch.Tensor, nsteps: int, r: torch.Tensor = None, stream=None) -> list:
+    """nsteps CN steps of u in place, queued without host synchronization
+    between steps; returns the PCG iterations of each step."""
+    its = (c_int * max(nsteps, 1))()
+    rp = _vec(r, h.N, "r") if r is not None else None
+    _check("cn_steps", lib().cn_steps(h.ptr, _vec(u, h.N, "u"), rp, int(nsteps), its, _stream(stream)))
+    return [its[i] for i in range(nsteps)]
 
 
 def cn_step_batched(hs, us, rs=None, outs=None, stream=None):
