@@ -12,18 +12,19 @@ __device__ __forceinline__ double stencil_row(const double *__restrict__ x,
                                               const double *__restrict__ wy,
                                               const double *__restrict__ wz, int dim, int n,
                                               long long j) {
-  const long long S = n - 1;
-  int i1 = (int)(j % S), i2 = (int)((j / S) % S);
-  double y = diag[j] * x[j];
-  if (i1 < n - 2) y -= wx[j] * x[j + 1];
-  if (i1 > 0) y -= wx[j - 1] * x[j - 1];
-  if (i2 < n - 2) y -= wy[j] * x[j + S];
-  if (i2 > 0) y -= wy[j - S] * x[j - S];
+  // 32-bit index arithmetic (grids have fewer than 2^31 unknowns): a 64-bit
+  // division is a long instruction sequence on the GPU
+  const int S = n - 1, jj = (int)j;
+  const int q = jj / S, i1 = jj - q * S, i2 = q % S;
+  double y = diag[jj] * x[jj];
+  if (i1 < S - 1) y -= wx[jj] * x[jj + 1];
+  if (i1 > 0) y -= wx[jj - 1] * x[jj - 1];
+  if (i2 < S - 1) y -= wy[jj] * x[jj + S];
+  if (i2 > 0) y -= wy[jj - S] * x[jj - S];
   if (dim == 3) {
-    const long long S2 = S * S;
-    int i3 = (int)(j / S2);
-    if (i3 < n - 2) y -= wz[j] * x[j + S2];
-    if (i3 > 0) y -= wz[j - S2] * x[j - S2];
+    const int S2 = S * S, i3 = q / S;
+    if (i3 < S - 1) y -= wz[jj] * x[jj + S2];
+    if (i3 > 0) y -= wz[jj - S2] * x[jj - S2];
   }
   return y;
 }

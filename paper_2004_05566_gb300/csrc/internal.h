@@ -253,6 +253,7 @@ struct hif_handle {
 
   // PCG work space (FP64)
   double *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *g = nullptr;
+  double *w = nullptr;                // A z of the current iteration (Chronopoulos-Gear PCG)
   double *xsol = nullptr;             // solution buffer of the graph-captured solve
   void *pcg_graph[4] = {nullptr, nullptr, nullptr, nullptr};  // captured PCG loop per
                                                              // (precision, warm start)

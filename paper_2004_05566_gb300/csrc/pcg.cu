@@ -34,20 +34,6 @@ struct StencilArgs {
   long long N;
 };
 
-// q = A p, partial sums of p.q
-__global__ void __launch_bounds__(NT) k_spmv_dot(const double *__restrict__ p, double *__restrict__ q,
-                                                 StencilArgs st, double *__restrict__ part) {
-  __shared__ double sm[NT / 32];
-  double acc = 0.0;
-  for (long long j = blockIdx.x * (long long)NT + threadIdx.x; j < st.N; j += (long long)gridDim.x * NT) {
-    double v = stencil_row(p, st.diag, st.wx, st.wy, st.wz, st.dim, st.n, j);
-    q[j] = v;
-    acc += p[j] * v;
-  }
-  double t = block_sum<NT>(acc, sm);
-  if (threadIdx.x == 0) part[blockIdx.x] = t;
-}
-
 // partial sums of a.b (b as double or float)
 template <typename TB>
 __global__ void __launch_bounds__(NT) k_dot(const double *__restrict__ a, const TB *__restrict__ b,
@@ -87,54 +73,6 @@ __global__ void k_scalar(double *__restrict__ s, const double *__restrict__ part
   }
 }
 
-// x += alpha p; r -= alpha q; partial r.r; z-input of the preconditioner = r
-template <typename TZ>
-__global__ void __launch_bounds__(NT) k_update_xr(double *__restrict__ x, double *__restrict__ r,
-                                                  const double *__restrict__ p,
-                                                  const double *__restrict__ q, TZ *__restrict__ zin,
-                                                  const double *__restrict__ s, long long N,
-                                                  double *__restrict__ part) {
-  __shared__ double sm[NT / 32];
-  const double alpha = s[S_ALPHA];
-  double acc = 0.0;
-  for (long long j = blockIdx.x * (long long)NT + threadIdx.x; j < N; j += (long long)gridDim.x * NT) {
-    x[j] += alpha * p[j];
-    double rj = r[j] - alpha * q[j];
-    r[j] = rj;
-    zin[j] = (TZ)rj;
-    acc += rj * rj;
-  }
-  double t = block_sum<NT>(acc, sm);
-  if (threadIdx.x == 0) part[blockIdx.x] = t;
-}
-
-// p = z + beta p  (beta = 0 on the first iteration: p = z)
-template <typename TZ>
-__global__ void __launch_bounds__(NT) k_update_p(double *__restrict__ p, const TZ *__restrict__ z,
-                                                 const double *__restrict__ s, long long N, int first) {
-  const double beta = first ? 0.0 : s[S_BETA];
-  for (long long j = blockIdx.x * (long long)NT + threadIdx.x; j < N; j += (long long)gridDim.x * NT)
-    p[j] = (double)z[j] + (first ? 0.0 : beta * p[j]);
-}
-
-// r = b - A x (true residual), z-input = r, partial r.r
-template <typename TZ>
-__global__ void __launch_bounds__(NT) k_true_residual(const double *__restrict__ b,
-                                                      const double *__restrict__ x, double *__restrict__ r,
-                                                      TZ *__restrict__ zin, StencilArgs st,
-                                                      double *__restrict__ part) {
-  __shared__ double sm[NT / 32];
-  double acc = 0.0;
-  for (long long j = blockIdx.x * (long long)NT + threadIdx.x; j < st.N; j += (long long)gridDim.x * NT) {
-    double rj = b[j] - stencil_row(x, st.diag, st.wx, st.wy, st.wz, st.dim, st.n, j);
-    r[j] = rj;
-    zin[j] = (TZ)rj;
-    acc += rj * rj;
-  }
-  double t = block_sum<NT>(acc, sm);
-  if (threadIdx.x == 0) part[blockIdx.x] = t;
-}
-
 // partial sums of |b - A x|^2 (no vector written)
 __global__ void __launch_bounds__(NT) k_resid_norm(const double *__restrict__ b,
                                                    const double *__restrict__ x, StencilArgs st,
@@ -170,13 +108,15 @@ __global__ void __launch_bounds__(NT) k_start(const double *__restrict__ b, doub
 // ---------------------------------------------------------- graph-captured loop
 //
 // The whole solve is one CUDA graph: a prologue (x = 0, r = b, z = b, b.b)
-// followed by a conditional `while` node whose body is one PCG iteration
-// ordered as  z = F^{-1} r; rz' = r.z; beta; p = z + beta p; q = A p; alpha;
-// x += alpha p; r -= alpha q; [r = b - A x every period]; r.r; continue while
-// ||r|| > tol ||b|| and it < maxit.  The body's last kernel sets the condition,
-// so no iteration returns to the host.  Arithmetic is the same as the host loop.
+// followed by a conditional `while` node whose body is one PCG iteration in
+// the Chronopoulos-Gear arrangement (see k_cg_wz): z = F^{-1} r; w = A z with
+// r.z and w.z; beta, alpha; p, q, x, r updates with r.r; [r = b - A x every
+// period]; continue while ||r|| > tol ||b|| and it < maxit.  The body's last
+// kernel sets the condition, so no iteration returns to the host.  The host
+// loop runs the same kernels.
 
 // prologue scalar phase: b.b, counters, and the loop condition (b != 0)
+template <bool kGraph>
 __global__ void k_scalar_start(double *__restrict__ s, const double *__restrict__ part, int np,
                                cudaGraphConditionalHandle cond) {
   double v = warp_sum_partials(part, np);
@@ -184,28 +124,16 @@ __global__ void k_scalar_start(double *__restrict__ s, const double *__restrict_
   s[S_BB] = v;
   s[S_RZ] = 0.0;
   s[S_IT] = 0.0;
-  s[S_CONV] = 0.0;
+  s[S_CONV] = v > 0.0 ? 0.0 : 1.0;
   s[S_RR] = v;
-  cudaGraphSetConditional(cond, v > 0.0 ? 1u : 0u);
+  if constexpr (kGraph) cudaGraphSetConditional(cond, v > 0.0 ? 1u : 0u);
 }
 
 
-// p = z + beta p, with p = z on the first iteration (p is not read then)
-template <typename TZ>
-__global__ void __launch_bounds__(NT) k_update_p_dev(double *__restrict__ p, const TZ *__restrict__ z,
-                                                     const double *__restrict__ s, long long N) {
-  const bool first = s[S_IT] == 0.0;
-  const double beta = s[S_BETA];
-  for (long long j = blockIdx.x * (long long)NT + threadIdx.x; j < N; j += (long long)gridDim.x * NT)
-    p[j] = first ? (double)z[j] : (double)z[j] + beta * p[j];
-}
-
-
-
-// ---- scalar phases folded into the vector kernels of the captured loop.
+// ---- scalar phases folded into the vector kernels of the iteration.
 // Each block writes its partial sum; the last block to finish (ticket
-// counter) adds all partials in block order, so the scalars are the same as
-// with a separate scalar kernel, and resets the ticket for the next use.
+// counter) adds all partials in block order, so the scalars do not depend on
+// which block finished last, and resets the ticket for the next use.
 __device__ __forceinline__ bool last_block(unsigned *ticket) {
   __shared__ bool am_last;
   __threadfence();
@@ -223,49 +151,74 @@ __device__ __forceinline__ double warp_sum_partials_cg(const double *partials, i
   return v;
 }
 
-// rz' = r.z, then (last block) beta = rz'/rz (0 on the first iteration), rz = rz'
-template <typename TB>
-__global__ void __launch_bounds__(NT) k_dot_beta(const double *__restrict__ a, const TB *__restrict__ b,
-                                                 long long N, double *__restrict__ part,
-                                                 double *__restrict__ s, unsigned *__restrict__ ticket) {
+// A z for one row j of the stencil, z of the preconditioner's type (FP32 or
+// FP64) promoted to FP64; 32-bit index arithmetic (N < 2^31).
+template <typename TZ>
+__device__ __forceinline__ double stencil_row_z(const TZ *z, double zj, const StencilArgs &st, int j) {
+  const int S = st.n - 1;
+  const int q = j / S, i1 = j - q * S, i2 = q % S;
+  double y = st.diag[j] * zj;
+  if (i1 < S - 1) y -= st.wx[j] * (double)z[j + 1];
+  if (i1 > 0) y -= st.wx[j - 1] * (double)z[j - 1];
+  if (i2 < S - 1) y -= st.wy[j] * (double)z[j + S];
+  if (i2 > 0) y -= st.wy[j - S] * (double)z[j - S];
+  if (st.dim == 3) {
+    const int S2 = S * S, i3 = q / S;
+    if (i3 < S - 1) y -= st.wz[j] * (double)z[j + S2];
+    if (i3 > 0) y -= st.wz[j - S2] * (double)z[j - S2];
+  }
+  return y;
+}
+
+// PCG in the Chronopoulos-Gear arrangement (the same iterates as the
+// textbook PCG loop in exact arithmetic, one reduction phase fewer):
+//   z = F^{-1} r;  w = A z;  rho = r.z;  mu = w.z
+//   beta = rho / rho_old (0 on the first iteration)
+//   sigma = mu - beta rho / alpha_old (= p.Ap),  alpha = rho / sigma
+//   p = z + beta p;  q = w + beta q (= A p);  x += alpha p;  r -= alpha q
+// using p.Ap = z.Az + 2 beta z.A p_old + beta^2 p_old.A p_old with
+// z.A p_old = -rho / alpha_old (residuals are F-orthogonal) and
+// p_old.A p_old = rho_old / alpha_old.
+//
+// first kernel: w = A z, partials of r.z and w.z; the last block forms
+// beta, sigma and alpha
+template <typename TZ>
+__global__ void __launch_bounds__(NT) k_cg_wz(const double *__restrict__ r, const TZ *__restrict__ z,
+                                              double *__restrict__ w, StencilArgs st,
+                                              double *__restrict__ part, double *__restrict__ s,
+                                              unsigned *__restrict__ ticket) {
   __shared__ double sm[NT / 32];
-  double acc = 0.0;
-  for (long long j = blockIdx.x * (long long)NT + threadIdx.x; j < N; j += (long long)gridDim.x * NT)
-    acc += a[j] * (double)b[j];
-  double t = block_sum<NT>(acc, sm);
+  double arz = 0.0, awz = 0.0;
+  const int N = (int)st.N;
+  for (int j = blockIdx.x * NT + threadIdx.x; j < N; j += gridDim.x * NT) {
+    const double zj = (double)z[j];
+    const double wj = stencil_row_z(z, zj, st, j);
+    w[j] = wj;
+    arz += r[j] * zj;
+    awz += wj * zj;
+  }
+  double t = block_sum<NT>(arz, sm);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
+  t = block_sum<NT>(awz, sm);
+  if (threadIdx.x == 0) part[gridDim.x + blockIdx.x] = t;
   if (!last_block(ticket) || threadIdx.x >= 32) return;
-  const double v = warp_sum_partials_cg(part, gridDim.x);
+  const double rho = warp_sum_partials_cg(part, gridDim.x);
+  const double mu = warp_sum_partials_cg(part + gridDim.x, gridDim.x);
   if (threadIdx.x == 0) {
-    s[S_BETA] = s[S_IT] == 0.0 ? 0.0 : v / s[S_RZ];
-    s[S_RZ] = v;
+    const bool first = s[S_IT] == 0.0;
+    const double beta = first ? 0.0 : rho / s[S_RZ];
+    const double sigma = first ? mu : mu - beta * rho / s[S_ALPHA];
+    s[S_BETA] = beta;
+    s[S_PQ] = sigma;
+    s[S_ALPHA] = rho / sigma;
+    s[S_RZ] = rho;
     *ticket = 0u;
   }
 }
 
-// q = A p, p.q, then (last block) alpha = rz / pq
-__global__ void __launch_bounds__(NT) k_spmv_alpha(const double *__restrict__ p, double *__restrict__ q,
-                                                   StencilArgs st, double *__restrict__ part,
-                                                   double *__restrict__ s, unsigned *__restrict__ ticket) {
-  __shared__ double sm[NT / 32];
-  double acc = 0.0;
-  for (long long j = blockIdx.x * (long long)NT + threadIdx.x; j < st.N; j += (long long)gridDim.x * NT) {
-    double v = stencil_row(p, st.diag, st.wx, st.wy, st.wz, st.dim, st.n, j);
-    q[j] = v;
-    acc += p[j] * v;
-  }
-  double t = block_sum<NT>(acc, sm);
-  if (threadIdx.x == 0) part[blockIdx.x] = t;
-  if (!last_block(ticket) || threadIdx.x >= 32) return;
-  const double v = warp_sum_partials_cg(part, gridDim.x);
-  if (threadIdx.x == 0) {
-    s[S_PQ] = v;
-    s[S_ALPHA] = s[S_RZ] / v;
-    *ticket = 0u;
-  }
-}
-
-// the end-of-iteration scalar phase: r.r -> convergence; it += 1; loop condition
+// the end-of-iteration scalar phase: r.r -> convergence; it += 1; loop
+// condition (inside the captured loop)
+template <bool kGraph>
 __device__ __forceinline__ void finish_iteration(double *s, double rr, double tol2, int maxit,
                                                  cudaGraphConditionalHandle cond) {
   s[S_RR] = rr;
@@ -273,27 +226,36 @@ __device__ __forceinline__ void finish_iteration(double *s, double rr, double to
   s[S_IT] = it;
   const bool conv = rr <= tol2 * s[S_BB];
   s[S_CONV] = conv ? 1.0 : 0.0;
-  cudaGraphSetConditional(cond, (!conv && it < (double)maxit) ? 1u : 0u);
+  if constexpr (kGraph) cudaGraphSetConditional(cond, (!conv && it < (double)maxit) ? 1u : 0u);
 }
 
-// x += alpha p; r -= alpha q; z-input = r; r.r; then (last block, unless this
-// iteration recomputes the true residual) the end-of-iteration scalar phase
-template <typename TZ>
-__global__ void __launch_bounds__(NT) k_update_xr_cond(double *__restrict__ x, double *__restrict__ r,
-                                                       const double *__restrict__ p,
-                                                       const double *__restrict__ q,
-                                                       TZ *__restrict__ zin, double *__restrict__ s,
-                                                       long long N, double *__restrict__ part,
-                                                       unsigned *__restrict__ ticket, int period,
-                                                       double tol2, int maxit,
-                                                       cudaGraphConditionalHandle cond) {
+// second kernel: p = z + beta p, q = w + beta q (p = z, q = w on the first
+// iteration), x += alpha p, r -= alpha q, z-input = r, r.r; then (last block,
+// unless this iteration recomputes the true residual) the end-of-iteration
+// scalar phase.  z and zin are the same buffer: each element is read before
+// it is overwritten, by the same thread.
+template <typename TZ, bool kGraph>
+__global__ void __launch_bounds__(NT) k_cg_update(double *__restrict__ x, double *__restrict__ r,
+                                                  double *__restrict__ p, double *__restrict__ q,
+                                                  const double *__restrict__ w, TZ *zin,
+                                                  double *__restrict__ s, long long N,
+                                                  double *__restrict__ part, unsigned *__restrict__ ticket,
+                                                  int period, double tol2, int maxit,
+                                                  cudaGraphConditionalHandle cond) {
   __shared__ double sm[NT / 32];
-  const double alpha = s[S_ALPHA];
+  const bool first = s[S_IT] == 0.0;
+  const double beta = s[S_BETA], alpha = s[S_ALPHA];
   const int it1 = (int)s[S_IT] + 1;  // iteration that updates x now
   double acc = 0.0;
-  for (long long j = blockIdx.x * (long long)NT + threadIdx.x; j < N; j += (long long)gridDim.x * NT) {
-    x[j] += alpha * p[j];
-    double rj = r[j] - alpha * q[j];
+  const int n = (int)N;
+  for (int j = blockIdx.x * NT + threadIdx.x; j < n; j += gridDim.x * NT) {
+    const double zj = (double)zin[j];
+    const double pj = first ? zj : zj + beta * p[j];
+    const double qj = first ? w[j] : w[j] + beta * q[j];
+    p[j] = pj;
+    q[j] = qj;
+    x[j] += alpha * pj;
+    const double rj = r[j] - alpha * qj;
     r[j] = rj;
     zin[j] = (TZ)rj;
     acc += rj * rj;
@@ -305,13 +267,13 @@ __global__ void __launch_bounds__(NT) k_update_xr_cond(double *__restrict__ x, d
   const double v = warp_sum_partials_cg(part, gridDim.x);
   if (threadIdx.x == 0) {
     *ticket = 0u;
-    finish_iteration(s, v, tol2, maxit, cond);
+    finish_iteration<kGraph>(s, v, tol2, maxit, cond);
   }
 }
 
 // every `period` iterations: r = b - A x, z-input = r, r.r and the
 // end-of-iteration scalar phase (a no-op launch otherwise)
-template <typename TZ>
+template <typename TZ, bool kGraph>
 __global__ void __launch_bounds__(NT) k_true_residual_cond(const double *__restrict__ b,
                                                            const double *__restrict__ x,
                                                            double *__restrict__ r,
@@ -336,7 +298,7 @@ __global__ void __launch_bounds__(NT) k_true_residual_cond(const double *__restr
   const double v = warp_sum_partials_cg(part, gridDim.x);
   if (threadIdx.x == 0) {
     *ticket = 0u;
-    finish_iteration(s, v, tol2, maxit, cond);
+    finish_iteration<kGraph>(s, v, tol2, maxit, cond);
   }
 }
 
@@ -430,7 +392,7 @@ int build_pcg_graph(Handle *h, TZ *z, PcgGraph *G, bool warm) {
     k_scalar_start_warm<true><<<1, 32, 0, cs>>>(sc, part, part + nb, nb, tol2, h->xsol, N, cond);
   } else {
     k_start<TZ><<<nb, NT, 0, cs>>>(h->g, h->xsol, h->r, z, N, part);
-    k_scalar_start<<<1, 32, 0, cs>>>(sc, part, nb, cond);
+    k_scalar_start<true><<<1, 32, 0, cs>>>(sc, part, nb, cond);
   }
   HIF_CUDA_TRY(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &graph, &deps, nullptr, &ndeps));
   cudaGraphNodeParams cp = {};
@@ -450,14 +412,13 @@ int build_pcg_graph(Handle *h, TZ *z, PcgGraph *G, bool warm) {
   if constexpr (sizeof(TZ) == 8) st_apply = apply_inplace_f64(h, (double *)z, cs);
   else st_apply = apply_inplace_f32(h, (float *)z, cs);
   unsigned *tk = h->tickets;
-  k_dot_beta<TZ><<<nb, NT, 0, cs>>>(h->r, z, N, part, sc, tk);
-  k_update_p_dev<TZ><<<nb, NT, 0, cs>>>(h->p, z, sc, N);
-  k_spmv_alpha<<<nb, NT, 0, cs>>>(h->p, h->q, st, part, sc, tk + 1);
-  k_update_xr_cond<TZ><<<nb, NT, 0, cs>>>(h->xsol, h->r, h->p, h->q, z, sc, N, part, tk + 2,
-                                          h->opt.true_res_period, tol2, h->opt.cg_maxit, cond);
-  k_true_residual_cond<TZ><<<nb, NT, 0, cs>>>(h->g, h->xsol, h->r, z, st, sc, h->opt.true_res_period,
-                                              part, tk + 3, tol2, h->opt.cg_maxit, cond);
-  note_launch(5);
+  k_cg_wz<TZ><<<nb, NT, 0, cs>>>(h->r, z, h->w, st, part, sc, tk);
+  k_cg_update<TZ, true><<<nb, NT, 0, cs>>>(h->xsol, h->r, h->p, h->q, h->w, z, sc, N, part, tk + 2,
+                                           h->opt.true_res_period, tol2, h->opt.cg_maxit, cond);
+  k_true_residual_cond<TZ, true><<<nb, NT, 0, cs>>>(h->g, h->xsol, h->r, z, st, sc,
+                                                    h->opt.true_res_period, part, tk + 3, tol2,
+                                                    h->opt.cg_maxit, cond);
+  note_launch(3);
   cudaGraph_t body_out = nullptr;
   cudaError_t e_end = cudaStreamEndCapture(cs, &body_out);
   const long long lc2 = hif_launch_count();
@@ -538,7 +499,7 @@ int pcg_impl(Handle *h, const double *b, double *x, TZ *z, int *iters_out, doubl
     k_scalar_start_warm<false><<<1, 32, 0, s>>>(sc, part, part + nb, nb, tol2, x, N, 0);
   } else {
     k_start<TZ><<<nb, NT, 0, s>>>(b, x, h->r, z, N, part);
-    k_scalar<<<1, 32, 0, s>>>(sc, part, nb, 4, tol2);
+    k_scalar_start<false><<<1, 32, 0, s>>>(sc, part, nb, 0);
   }
   note_launch(2);
   HIF_CUDA_TRY(cudaMemcpyAsync(h->host_scal, sc, 16 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -552,30 +513,21 @@ int pcg_impl(Handle *h, const double *b, double *x, TZ *z, int *iters_out, doubl
     }
     return HIF_OK;
   }
-  HIF_TRY(precond(z));
-  k_dot<TZ><<<nb, NT, 0, s>>>(h->r, z, N, part);
-  note_launch();
-  k_scalar<<<1, 32, 0, s>>>(sc, part, nb, 3, tol2);
-  note_launch();
-  k_update_p<TZ><<<nb, NT, 0, s>>>(h->p, z, sc, N, 1);
-  note_launch();
+  // the iteration of the captured loop, driven from the host (the same
+  // kernels, so the same arithmetic), with a convergence check per iteration
+  unsigned *tk = h->tickets;
   int it = 0;
   bool conv = false;
   const int period = h->opt.true_res_period;
   while (it < h->opt.cg_maxit) {
-    k_spmv_dot<<<nb, NT, 0, s>>>(h->p, h->q, st, part);
-    note_launch();
-    k_scalar<<<1, 32, 0, s>>>(sc, part, nb, 0, tol2);
-    note_launch();
-    k_update_xr<TZ><<<nb, NT, 0, s>>>(x, h->r, h->p, h->q, z, sc, N, part);
-    note_launch();
+    HIF_TRY(precond(z));
+    k_cg_wz<TZ><<<nb, NT, 0, s>>>(h->r, z, h->w, st, part, sc, tk);
+    k_cg_update<TZ, false><<<nb, NT, 0, s>>>(x, h->r, h->p, h->q, h->w, z, sc, N, part, tk + 2, period,
+                                            tol2, h->opt.cg_maxit, 0);
+    k_true_residual_cond<TZ, false><<<nb, NT, 0, s>>>(b, x, h->r, z, st, sc, period, part, tk + 3, tol2,
+                                                     h->opt.cg_maxit, 0);
+    note_launch(3);
     ++it;
-    if (period > 0 && it % period == 0) {
-      k_true_residual<TZ><<<nb, NT, 0, s>>>(b, x, h->r, z, st, part);
-      note_launch();
-    }
-    k_scalar<<<1, 32, 0, s>>>(sc, part, nb, 1, tol2);
-    note_launch();
     HIF_CUDA_TRY(cudaGetLastError());
     HIF_CUDA_TRY(cudaMemcpyAsync(h->host_scal, sc, 16 * sizeof(double), cudaMemcpyDeviceToHost, s));
     HIF_CUDA_TRY(cudaStreamSynchronize(s));
@@ -584,13 +536,6 @@ int pcg_impl(Handle *h, const double *b, double *x, TZ *z, int *iters_out, doubl
       conv = true;
       break;
     }
-    HIF_TRY(precond(z));
-    k_dot<TZ><<<nb, NT, 0, s>>>(h->r, z, N, part);
-    note_launch();
-    k_scalar<<<1, 32, 0, s>>>(sc, part, nb, 2, tol2);
-    note_launch();
-    k_update_p<TZ><<<nb, NT, 0, s>>>(h->p, z, sc, N, 0);
-    note_launch();
   }
   if (iters_out) *iters_out = it;
   if (relres_out) {
