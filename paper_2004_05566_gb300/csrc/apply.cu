@@ -56,6 +56,31 @@ __device__ __forceinline__ void pdl_enter() {
 // FP32 apply in a CUDA graph 393 us with the early trigger, 332 us without).
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// The level kernels split each unit into a prologue that reads only the
+// factor and its index tables (unchanged during an apply) and the part that
+// reads what earlier kernels wrote: with PDL the prologue overlaps the
+// previous kernel.  In the prologue a unit loads its descriptors and index
+// entries and prefetches its factor block into L2.
+template <bool PDL>
+__device__ __forceinline__ void unit_dependency_point() {
+  if constexpr (PDL) pdl_enter();
+}
+
+// bulk L2 prefetch of elements [0, n) of a factor block, in pieces of at
+// most 32 KB, by the calling thread: the start is rounded down to 16 bytes
+// (BF16 blocks start on 8 bytes) and the length to whole 16-byte units, so
+// the range stays inside the block's allocation
+template <typename TV>
+__device__ __forceinline__ void prefetch_block_l2(const TV *p, long long n) {
+  const unsigned long long a = reinterpret_cast<unsigned long long>(p);
+  const char *b = reinterpret_cast<const char *>(a & ~15ULL);
+  const long long bytes = (n * (long long)sizeof(TV) + (long long)(a & 15ULL)) & ~15LL;
+  for (long long o = 0; o < bytes; o += 32768) {
+    const unsigned m = (unsigned)min(32768LL, bytes - o);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(b + o), "r"(m) : "memory");
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_reduce(T v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -126,7 +151,7 @@ __device__ __forceinline__ void warp_rows_dot4(const TV *const (&rp)[kRows], con
 // G x_I of the interior.  A CTA handles rows [a, b) of one cell's stacked
 // [V; G]; x_I is only read here (the forward values go to the separate vector
 // xI, which the backward cell step reads), so a cell may be split over CTAs.
-template <typename T, int NT, typename TV = T>
+template <typename T, int NT, typename TV = T, bool PDL = false>
 __device__ __forceinline__ void cell_fwd_unit(const CellItem &it, const CellDesc *__restrict__ cells,
                                               const int *__restrict__ idx, const TV *__restrict__ vals,
                                               T *__restrict__ contrib, T *__restrict__ xI,
@@ -134,7 +159,18 @@ __device__ __forceinline__ void cell_fwd_unit(const CellItem &it, const CellDesc
   const CellDesc c = cells[it.cell];
   const int *I = idx + c.I_off;
   const int nIp = (int)pad4(c.nI);
-  for (int i = threadIdx.x; i < nIp; i += NT) xs[i] = i < c.nI ? __ldcg(x + I[i]) : T(0);
+  if constexpr (PDL) {
+    if (threadIdx.x == 0) {  // the item's rows of [V; G]
+      const int va = min(it.a, c.nB), vb = min(it.b, c.nB);
+      if (vb > va) prefetch_block_l2(vals + c.V_off + (long long)va * nIp, (long long)(vb - va) * nIp);
+      const int ga = max(it.a - c.nB, 0), gb = max(it.b - c.nB, 0);
+      if (gb > ga) prefetch_block_l2(vals + c.G_off + tri_off(ga), tri_off(gb) - tri_off(ga));
+    }
+  }
+  const int i0 = threadIdx.x;
+  const int id0 = i0 < c.nI ? I[i0] : 0;
+  unit_dependency_point<PDL>();
+  for (int i = i0; i < nIp; i += NT) xs[i] = i < c.nI ? __ldcg(x + (i == i0 ? id0 : I[i])) : T(0);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int NW = NT / 32;
@@ -181,14 +217,13 @@ __global__ void __launch_bounds__(kCellFwdThreads) k_cell_fwd(const CellItem *__
                                                               T *__restrict__ contrib,
                                                               T *__restrict__ xI,
                                                               const T *__restrict__ x) {
-  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cell_fwd_unit<T, kCellFwdThreads, TV>(items[blockIdx.x], cells, idx, vals, contrib, xI, x,
-                                    reinterpret_cast<T *>(smem_raw));
+  cell_fwd_unit<T, kCellFwdThreads, TV, true>(items[blockIdx.x], cells, idx, vals, contrib, xI, x,
+                                          reinterpret_cast<T *>(smem_raw));
 }
 
 // Forward group step (K^T C^T): x_g <- H (x_g - sum of the cells' contributions).
-template <typename T, int NT, typename TV = T>
+template <typename T, int NT, typename TV = T, bool PDL = false>
 __device__ __forceinline__ void group_fwd_unit(const GroupDesc &g, const int *__restrict__ idx,
                                                const long long *__restrict__ cptr,
                                                const long long *__restrict__ cslot,
@@ -197,6 +232,9 @@ __device__ __forceinline__ void group_fwd_unit(const GroupDesc &g, const int *__
                                                T *xs) {
   const int *gi = idx + g.idx_off;
   const int np = (int)pad4(g.n);
+  if constexpr (PDL)
+    if (threadIdx.x == 0) prefetch_block_l2(vals + g.H_off, (long long)g.n * np);
+  unit_dependency_point<PDL>();
   for (int i = threadIdx.x; i < np; i += NT) {
     T v = T(0);
     if (i < g.n) {
@@ -234,7 +272,7 @@ __device__ __forceinline__ void group_fwd_unit(const GroupDesc &g, const int *__
 constexpr int kSmallWarps = 8;
 
 // one warp: entity g with n <= 32; xs is the warp's 32-element buffer
-template <typename T, typename TV = T>
+template <typename T, typename TV = T, bool PDL = false>
 __device__ __forceinline__ void group_fwd_small_warp(const GroupDesc &g, const int *__restrict__ idx,
                                                      const long long *__restrict__ cptr,
                                                      const long long *__restrict__ cslot,
@@ -243,11 +281,29 @@ __device__ __forceinline__ void group_fwd_small_warp(const GroupDesc &g, const i
                                                      T *__restrict__ x, T *xs) {
   const int lane = threadIdx.x & 31;
   const int *gi = idx + g.idx_off;
+  // static part: the DOF, its first contribution slots, the H row in L2
+  constexpr int kSlots = 4;
+  int dof = 0;
+  long long a = 0, b = 0, sl[kSlots];
+  if (lane < g.n) {
+    dof = gi[lane];
+    a = cptr[g.cptr_off + lane];
+    b = cptr[g.cptr_off + lane + 1];
+#pragma unroll
+    for (int k = 0; k < kSlots; ++k) sl[k] = a + k < b ? cslot[a + k] : 0;
+    if constexpr (PDL) {
+      const int np = (int)pad4(g.n);
+      prefetch_block_l2(vals + g.H_off + (long long)lane * np, np);
+    }
+  }
+  unit_dependency_point<PDL>();
   T v = T(0);
   if (lane < g.n) {
-    v = __ldcg(x + gi[lane]);
-    const long long a = cptr[g.cptr_off + lane], b = cptr[g.cptr_off + lane + 1];
-    for (long long s = a; s < b; ++s) v -= __ldcg(contrib + cslot[s]);
+    v = __ldcg(x + dof);
+#pragma unroll
+    for (int k = 0; k < kSlots; ++k)
+      if (a + k < b) v -= __ldcg(contrib + sl[k]);
+    for (long long s = a + kSlots; s < b; ++s) v -= __ldcg(contrib + cslot[s]);
   }
   xs[lane] = v;
   __syncwarp();
@@ -266,13 +322,17 @@ __device__ __forceinline__ void group_fwd_small_warp(const GroupDesc &g, const i
   __syncwarp();
 }
 
-template <typename T, typename TV = T>
+template <typename T, typename TV = T, bool PDL = false>
 __device__ __forceinline__ void group_bwd_small_warp(const GroupDesc &g, const int *__restrict__ idx,
                                                      const TV *__restrict__ vals, T *__restrict__ x,
                                                      T *xs) {
   const int lane = threadIdx.x & 31;
   const int *gi = idx + g.idx_off;
-  xs[lane] = lane < g.n ? __ldcg(x + gi[lane]) : T(0);
+  const int dof = lane < g.n ? gi[lane] : 0;
+  if constexpr (PDL)
+    if (lane < g.n) prefetch_block_l2(vals + g.H_off + (long long)lane * pad4(g.n), pad4(g.n));
+  unit_dependency_point<PDL>();
+  xs[lane] = lane < g.n ? __ldcg(x + dof) : T(0);
   __syncwarp();
   if (lane < g.n) {
     const long long np = pad4(g.n);
@@ -323,12 +383,15 @@ __device__ __forceinline__ void rowgroup_tree(T *part, int CW, int RG) {
 // Backward group step: x_g <- H^T x_g.  A thread owns a column quad of H
 // (16-byte loads) and a row group; the row groups are added by a tree.  xs
 // holds pad4(n) + 4 NT elements.
-template <typename T, int NT, typename TV = T>
+template <typename T, int NT, typename TV = T, bool PDL = false>
 __device__ __forceinline__ void group_bwd_unit(const GroupDesc &g, const int *__restrict__ idx,
                                                const TV *__restrict__ vals, T *__restrict__ x, T *xs) {
   const int np = (int)pad4(g.n), nq = np / 4;
   T *part = xs + np;  // 4 * NT
   const int *gi = idx + g.idx_off;
+  if constexpr (PDL)
+    if (threadIdx.x == 0) prefetch_block_l2(vals + g.H_off, (long long)g.n * np);
+  unit_dependency_point<PDL>();
   for (int i = threadIdx.x; i < g.n; i += NT) xs[i] = __ldcg(x + gi[i]);
   __syncthreads();
   const TV *H = vals + g.H_off;
@@ -369,18 +432,20 @@ __global__ void __launch_bounds__(kSmallWarps * 32) k_group_fwd_level(
     const GroupDesc *__restrict__ groups, const int *__restrict__ idx,
     const long long *__restrict__ cptr, const long long *__restrict__ cslot,
     const TV *__restrict__ vals, const T *__restrict__ contrib, T *__restrict__ x) {
-  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *sm = reinterpret_cast<T *>(smem_raw);
   const int u = blockIdx.x;
   if (u < nlarge) {
-    group_fwd_unit<T, kSmallWarps * 32, TV>(groups[large[u]], idx, cptr, cslot, vals, contrib, x, sm);
+    group_fwd_unit<T, kSmallWarps * 32, TV, true>(groups[large[u]], idx, cptr, cslot, vals, contrib, x, sm);
     return;
   }
   const int warp = threadIdx.x >> 5;
   const int t = (u - nlarge) * kSmallWarps + warp;
   if (t < nsmall)
-    group_fwd_small_warp<T, TV>(groups[small[t]], idx, cptr, cslot, vals, contrib, x, sm + 32 * warp);
+    group_fwd_small_warp<T, TV, true>(groups[small[t]], idx, cptr, cslot, vals, contrib, x,
+                                      sm + 32 * warp);
+  else
+    pdl_enter();  // a warp without an entity
 }
 
 template <typename T, typename TV = T>
@@ -388,17 +453,19 @@ __global__ void __launch_bounds__(kSmallWarps * 32) k_group_bwd_level(
     const int *__restrict__ large, int nlarge, const int *__restrict__ small, int nsmall,
     const GroupDesc *__restrict__ groups, const int *__restrict__ idx, const TV *__restrict__ vals,
     T *__restrict__ x) {
-  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *sm = reinterpret_cast<T *>(smem_raw);
   const int u = blockIdx.x;
   if (u < nlarge) {
-    group_bwd_unit<T, kSmallWarps * 32, TV>(groups[large[u]], idx, vals, x, sm);
+    group_bwd_unit<T, kSmallWarps * 32, TV, true>(groups[large[u]], idx, vals, x, sm);
     return;
   }
   const int warp = threadIdx.x >> 5;
   const int t = (u - nlarge) * kSmallWarps + warp;
-  if (t < nsmall) group_bwd_small_warp<T, TV>(groups[small[t]], idx, vals, x, sm + 32 * warp);
+  if (t < nsmall)
+    group_bwd_small_warp<T, TV, true>(groups[small[t]], idx, vals, x, sm + 32 * warp);
+  else
+    pdl_enter();  // a warp without an entity
 }
 
 // ---- large separator entities, split over many CTAs (levels with entities
@@ -522,7 +589,7 @@ __global__ void __launch_bounds__(256) k_group_cols_split(const int2 *__restrict
 // and reads both quads of a row with 16-byte loads.  The pairs take the
 // smallest power-of-two number of threads that covers them, the rest of the
 // CTA splits the rows into groups, and the row groups are added by a tree.
-template <typename T, int NT, typename TV = T>
+template <typename T, int NT, typename TV = T, bool PDL = false>
 __device__ __forceinline__ void cell_bwd_unit(const CellItem &it, const CellDesc *__restrict__ cells,
                                               const int *__restrict__ idx, const TV *__restrict__ vals,
                                               const T *__restrict__ xI, T *__restrict__ x, T *smem) {
@@ -532,8 +599,18 @@ __device__ __forceinline__ void cell_bwd_unit(const CellItem &it, const CellDesc
   T *xb = xs + c.nI;
   const int *I = idx + c.I_off;
   const int *B = idx + c.B_off;
-  for (int i = threadIdx.x; i < c.nI; i += NT) xs[i] = __ldcg(xI + I[i]);
-  for (int q = threadIdx.x; q < c.nB; q += NT) xb[q] = __ldcg(x + B[q]);
+  if constexpr (PDL) {
+    if (threadIdx.x == 0) {  // G rows from the item's first column on, and V
+      const long long g0 = tri_off(it.a & ~3);
+      prefetch_block_l2(vals + c.G_off + g0, tri_off(c.nI) - g0);
+      prefetch_block_l2(vals + c.V_off, (long long)c.nB * pad4(c.nI));
+    }
+  }
+  const int t0 = threadIdx.x;
+  const int iI = t0 < c.nI ? I[t0] : 0, iB = t0 < c.nB ? B[t0] : 0;
+  unit_dependency_point<PDL>();
+  for (int i = t0; i < c.nI; i += NT) xs[i] = __ldcg(xI + (i == t0 ? iI : I[i]));
+  for (int q = t0; q < c.nB; q += NT) xb[q] = __ldcg(x + (q == t0 ? iB : B[q]));
   __syncthreads();
   const TV *G = vals + c.G_off;
   const TV *V = vals + c.V_off;
@@ -607,10 +684,9 @@ __global__ void __launch_bounds__(kCellBwdThreads) k_cell_bwd(const CellItem *__
                                                               const TV *__restrict__ vals,
                                                               const T *__restrict__ xI,
                                                               T *__restrict__ x) {
-  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cell_bwd_unit<T, kCellBwdThreads, TV>(items[blockIdx.x], cells, idx, vals, xI, x,
-                                    reinterpret_cast<T *>(smem_raw));
+  cell_bwd_unit<T, kCellBwdThreads, TV, true>(items[blockIdx.x], cells, idx, vals, xI, x,
+                                          reinterpret_cast<T *>(smem_raw));
 }
 
 // ------------------------------------------------------------ TMA-staged cells
