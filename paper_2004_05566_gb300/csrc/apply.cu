@@ -815,7 +815,10 @@ __device__ __forceinline__ void produce_cells(int ncells, const T *__restrict__ 
 // Gather warp: for each cell of the CTA, into buffer b = (cell count) & 1:
 // the cell descriptor and chunk bounds, x at the interior DOFs (zero padded to
 // pad4(nI)), when is0 is given the interior DOF numbers themselves, and when
-// xb0 is given x at the boundary DOFs; every lane arrives on ready[b].
+// xb0 is given x at the boundary DOFs; every lane arrives on mready[b] once
+// the descriptor and chunk bounds are in place (only the factor was read:
+// with PDL this happens before the previous kernel has finished) and on
+// ready[b] once x is gathered.
 // Before refilling a buffer it waits until the consumers freed it.
 template <typename T>
 __device__ __forceinline__ void gather_cells(const CellDesc *__restrict__ cells, int ncells,
@@ -824,7 +827,8 @@ __device__ __forceinline__ void gather_cells(const CellDesc *__restrict__ cells,
                                              const int *__restrict__ idx, const T *__restrict__ x,
                                              CellMeta *cm, T *xs0, long long xs_stride, T *xb0,
                                              long long xb_stride, int *is0, unsigned long long *ready,
-                                             unsigned long long *freed, double *err) {
+                                             unsigned long long *mready, unsigned long long *freed,
+                                             double *err) {
   const int lane = threadIdx.x & 31;
   int jc = 0;
   // the next cell's descriptor is loaded while the current one is gathered
@@ -851,6 +855,8 @@ __device__ __forceinline__ void gather_cells(const CellDesc *__restrict__ cells,
       cm[b].nch = co.y;
     }
     for (int j = lane; j <= co.y; j += 32) cm[b].cs[j] = chunk_tab[co.x + j];
+    mbar_arrive(&mready[b]);  // the copy warp may stream the cell's block
+    if (jc == 0) pdl_wait();  // x is written by the previous kernel
     // gathers in batches of kG per lane: all index loads, then all value loads
     constexpr int kG = 4;
     const int nIp = (int)pad4(c.nI);
@@ -997,9 +1003,8 @@ __global__ void __launch_bounds__(kTmaThreads, 4) k_cell_fwd_tma_S(const CellDes
                                                                    const T *__restrict__ x,
                                                                    double *__restrict__ err,
                                                                    int max_nI, int max_nB) {
-  pdl_wait();
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(8) unsigned long long full[kStagesFwd], empty[kStagesFwd], ready[2], freed[2];
+  __shared__ __align__(8) unsigned long long full[kStagesFwd], empty[kStagesFwd], ready[2], mready[2], freed[2];
   __shared__ int2 meta[kStagesFwd];
   __shared__ CellMeta cm[2];
   unsigned char *stage = smem_raw;
@@ -1012,6 +1017,7 @@ __global__ void __launch_bounds__(kTmaThreads, 4) k_cell_fwd_tma_S(const CellDes
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&ready[b], 32);
+      mbar_init(&mready[b], 32);
       mbar_init(&freed[b], kConsumerWarps);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1020,14 +1026,15 @@ __global__ void __launch_bounds__(kTmaThreads, 4) k_cell_fwd_tma_S(const CellDes
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == kConsumerWarps) {
     if (lane == 0)
-      produce_cells<T, kStagesFwd>(ncells, vals, false, stage, meta, cm, ready, full, empty, err);
+      produce_cells<T, kStagesFwd>(ncells, vals, false, stage, meta, cm, mready, full, empty, err);
     return;
   }
   if (warp == kConsumerWarps + 1) {
     gather_cells<T>(cells, ncells, chunk_of, chunk_tab, idx, x, cm, xs0, xstride, nullptr, 0, nullptr,
-                    ready, freed, err);
+                    ready, mready, freed, err);
     return;
   }
+  pdl_wait();  // outputs are written over data the previous kernel reads
   int k = 0;  // running chunk counter, as in the copy warp
   int u = 0;        // running pair count (mod 8)
   int jc = 0;
@@ -1105,9 +1112,8 @@ __global__ void __launch_bounds__(kTmaThreads, 2) k_cell_bwd_tma_S(const CellDes
                                                                    T *__restrict__ x,
                                                                    double *__restrict__ err,
                                                                    int max_nI, int max_nB) {
-  pdl_wait();
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(8) unsigned long long full[kStagesBwd], empty[kStagesBwd], ready[2], freed[2];
+  __shared__ __align__(8) unsigned long long full[kStagesBwd], empty[kStagesBwd], ready[2], mready[2], freed[2];
   __shared__ int2 meta[kStagesBwd];
   __shared__ CellMeta cm[2];
   unsigned char *stage = smem_raw;
@@ -1124,6 +1130,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2) k_cell_bwd_tma_S(const CellDes
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&ready[b], 32);
+      mbar_init(&mready[b], 32);
       mbar_init(&freed[b], kConsumerWarps);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1132,14 +1139,15 @@ __global__ void __launch_bounds__(kTmaThreads, 2) k_cell_bwd_tma_S(const CellDes
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == kConsumerWarps) {
     if (lane == 0)
-      produce_cells<T, kStagesBwd>(ncells, vals, true, stage, meta, cm, ready, full, empty, err);
+      produce_cells<T, kStagesBwd>(ncells, vals, true, stage, meta, cm, mready, full, empty, err);
     return;
   }
   if (warp == kConsumerWarps + 1) {
     gather_cells<T>(cells, ncells, chunk_of, chunk_tab, idx, x, cm, xs0, xstride, xb0, bstride, is0,
-                    ready, freed, err);
+                    ready, mready, freed, err);
     return;
   }
+  pdl_wait();  // outputs are written over data the previous kernel reads
   int k = 0;  // running chunk counter, as in the copy warp
   int u = 0;        // running pair count (mod 8)
   int jc = 0;
@@ -1724,14 +1732,14 @@ __global__ void __launch_bounds__(256) k_merged_phase(const int *__restrict__ pr
 }
 
 __global__ void k_to_float(const double *__restrict__ a, float *__restrict__ b, long long n) {
-  pdl_enter();
+  pdl_wait();  // no early trigger: a successor may read what this kernel writes in its prologue
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
     b[i] = (float)a[i];
 }
 
 __global__ void k_to_double(const float *__restrict__ a, double *__restrict__ b, long long n) {
-  pdl_enter();
+  pdl_wait();  // no early trigger: a successor may read what this kernel writes in its prologue
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
     b[i] = (double)a[i];
