@@ -34,6 +34,42 @@ struct StencilArgs {
   long long N;
 };
 
+// Conversions between the preconditioner's FP32 vectors and the FP64 CG
+// vectors.  On GB300 the conversion instructions run on the FP64 pipe, which
+// retires about one lane operation per clock per SM and already bounds the
+// CG kernels; these do the same conversions exactly with integer operations
+// for normal numbers and zero, and leave the rare other cases (subnormal,
+// infinite, NaN, out-of-range results) to the conversion instruction.
+__device__ __forceinline__ double widen(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  if ((u & 0x7fffffffu) == 0u) return __longlong_as_double((long long)sign);  // +-0
+  if (e == 0u || e == 0xffu) return (double)f;
+  const unsigned long long b = sign | ((unsigned long long)(e + 896u) << 52) |
+                               ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)b);
+}
+__device__ __forceinline__ double widen(double d) { return d; }
+
+// round to nearest even, as __double2float_rn
+__device__ __forceinline__ float narrow_rn(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const int ef = (int)((b >> 52) & 0x7ffu) - 896;  // biased FP32 exponent
+  if (ef <= 0 || ef >= 255) return __double2float_rn(d);
+  const unsigned mf = (unsigned)((b >> 29) & 0x7fffffu);
+  const unsigned rem = (unsigned)(b & 0x1fffffffu);  // the 29 bits dropped
+  unsigned out = ((unsigned)(b >> 32) & 0x80000000u) | ((unsigned)ef << 23) | mf;
+  if (rem > 0x10000000u || (rem == 0x10000000u && (mf & 1u))) out += 1u;  // a carry bumps the exponent
+  return __uint_as_float(out);
+}
+
+template <typename TZ>
+__device__ __forceinline__ TZ to_z(double v) {
+  if constexpr (sizeof(TZ) == 4) return narrow_rn(v);
+  else return v;
+}
+
 // partial sums of a.b (b as double or float)
 template <typename TB>
 __global__ void __launch_bounds__(NT) k_dot(const double *__restrict__ a, const TB *__restrict__ b,
@@ -98,7 +134,7 @@ __global__ void __launch_bounds__(NT) k_start(const double *__restrict__ b, doub
     double bj = b[j];
     x[j] = 0.0;
     r[j] = bj;
-    zin[j] = (TZ)bj;
+    zin[j] = to_z<TZ>(bj);
     acc += bj * bj;
   }
   double t = block_sum<NT>(acc, sm);
@@ -158,14 +194,14 @@ __device__ __forceinline__ double stencil_row_z(const TZ *z, double zj, const St
   const int S = st.n - 1;
   const int q = j / S, i1 = j - q * S, i2 = q % S;
   double y = st.diag[j] * zj;
-  if (i1 < S - 1) y -= st.wx[j] * (double)z[j + 1];
-  if (i1 > 0) y -= st.wx[j - 1] * (double)z[j - 1];
-  if (i2 < S - 1) y -= st.wy[j] * (double)z[j + S];
-  if (i2 > 0) y -= st.wy[j - S] * (double)z[j - S];
+  if (i1 < S - 1) y -= st.wx[j] * widen(z[j + 1]);
+  if (i1 > 0) y -= st.wx[j - 1] * widen(z[j - 1]);
+  if (i2 < S - 1) y -= st.wy[j] * widen(z[j + S]);
+  if (i2 > 0) y -= st.wy[j - S] * widen(z[j - S]);
   if (st.dim == 3) {
     const int S2 = S * S, i3 = q / S;
-    if (i3 < S - 1) y -= st.wz[j] * (double)z[j + S2];
-    if (i3 > 0) y -= st.wz[j - S2] * (double)z[j - S2];
+    if (i3 < S - 1) y -= st.wz[j] * widen(z[j + S2]);
+    if (i3 > 0) y -= st.wz[j - S2] * widen(z[j - S2]);
   }
   return y;
 }
@@ -191,7 +227,7 @@ __global__ void __launch_bounds__(NT) k_cg_wz(const double *__restrict__ r, cons
   double arz = 0.0, awz = 0.0;
   const int N = (int)st.N;
   for (int j = blockIdx.x * NT + threadIdx.x; j < N; j += gridDim.x * NT) {
-    const double zj = (double)z[j];
+    const double zj = widen(z[j]);
     const double wj = stencil_row_z(z, zj, st, j);
     w[j] = wj;
     arz += r[j] * zj;
@@ -249,7 +285,7 @@ __global__ void __launch_bounds__(NT) k_cg_update(double *__restrict__ x, double
   double acc = 0.0;
   const int n = (int)N;
   for (int j = blockIdx.x * NT + threadIdx.x; j < n; j += gridDim.x * NT) {
-    const double zj = (double)zin[j];
+    const double zj = widen(zin[j]);
     const double pj = first ? zj : zj + beta * p[j];
     const double qj = first ? w[j] : w[j] + beta * q[j];
     p[j] = pj;
@@ -257,7 +293,7 @@ __global__ void __launch_bounds__(NT) k_cg_update(double *__restrict__ x, double
     x[j] += alpha * pj;
     const double rj = r[j] - alpha * qj;
     r[j] = rj;
-    zin[j] = (TZ)rj;
+    zin[j] = to_z<TZ>(rj);
     acc += rj * rj;
   }
   double t = block_sum<NT>(acc, sm);
@@ -289,7 +325,7 @@ __global__ void __launch_bounds__(NT) k_true_residual_cond(const double *__restr
   for (long long j = blockIdx.x * (long long)NT + threadIdx.x; j < st.N; j += (long long)gridDim.x * NT) {
     double rj = b[j] - stencil_row(x, st.diag, st.wx, st.wy, st.wz, st.dim, st.n, j);
     r[j] = rj;
-    zin[j] = (TZ)rj;
+    zin[j] = to_z<TZ>(rj);
     acc += rj * rj;
   }
   double t = block_sum<NT>(acc, sm);
@@ -330,7 +366,7 @@ __global__ void __launch_bounds__(NT) k_start_warm(const double *__restrict__ b,
     const double bj = b[j];
     const double rj = bj - stencil_row(x, st.diag, st.wx, st.wy, st.wz, st.dim, st.n, j);
     r[j] = rj;
-    zin[j] = (TZ)rj;
+    zin[j] = to_z<TZ>(rj);
     arr += rj * rj;
     abb += bj * bj;
   }
