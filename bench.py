@@ -35,6 +35,7 @@ import json
 import math
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -156,7 +157,10 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # raw samples (HIFCN_CLOCKS_DIR, else the system temporary directory);
+        # the JSON line carries their summary
+        out_dir = os.environ.get("HIFCN_CLOCKS_DIR", tempfile.gettempdir())
+        self.path = os.path.join(out_dir, f"clocks_rank{gpu_index}.csv")
 
     def start(self):
         try:
