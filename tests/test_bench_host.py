@@ -1,0 +1,77 @@
+"""Host logic of bench.py (no GPU): the reference arm's JSON line, the ncu
+traffic lookup keyed by the leaf-kernel source, peak lookup and the clock
+sampler without nvidia-smi."""
+
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture
+def bench():
+    # imported here, not at collection: bench.py sets process-wide CUDA
+    # environment defaults when it is imported
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    import bench as b
+    return b
+
+
+def test_reference_arm_line(bench):
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--steps", "1", "--warmup", "0"], capture_output=True, text=True,
+                         timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "steps/s"
+    assert d["value"] > 0 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "steps/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+
+
+def test_traffic_follows_leaf_source(bench, tmp_path, monkeypatch):
+    h = bench.leaf_kernel_source_hash()
+    assert len(h) == 64 and h == bench.leaf_kernel_source_hash()
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    doc = {"leaf_kernel_sha256": h,
+           "kernels": {"cell_bwd_l0": {"dram_bytes_per_launch_full": 123456789}}}
+    (prof / "traffic.json").write_text(json.dumps(doc))
+    # the lookup reads profiles/ under ROOT and hashes the sources under ROOT
+    csrc = tmp_path / "paper_2004_05566_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for f in ("apply.cu", "internal.h"):
+        src = os.path.join(ROOT, "paper_2004_05566_gb300", "csrc", f)
+        (csrc / f).write_text(open(src).read())
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.kernel_traffic("cell_bwd_l0") == 123456789.0
+    assert bench.kernel_traffic("cell_fwd_l0") is None
+    # a change inside the leaf-kernel section invalidates the figures
+    a = (csrc / "apply.cu").read_text()
+    marker = "// ------------------------------------------------------------ TMA-staged cells"
+    (csrc / "apply.cu").write_text(a.replace(marker, marker + "\n// edited"))
+    assert bench.kernel_traffic("cell_bwd_l0") is None
+
+
+def test_find_peak_nested(bench):
+    d = {"gpu": {"hbm": {"hbm_gbs": 6793.1}, "bf16_tflops": 1800.0}}
+    assert bench._find_peak(d, ("hbm_gbs",)) == 6793.1
+    assert bench._find_peak(d, ("nothing",)) is None
+
+
+def test_clock_sampler_without_nvidia_smi(bench, tmp_path, monkeypatch):
+    monkeypatch.setenv("HIFCN_CLOCKS_DIR", str(tmp_path))
+    monkeypatch.setenv("PATH", str(tmp_path))  # no nvidia-smi on PATH
+    c = bench.ClockSampler(0)
+    assert c.path.startswith(str(tmp_path))
+    c.start()
+    r = c.stop()
+    assert r["sm_mhz"] is None and r["reasons"] == ["nvidia-smi unavailable"]
