@@ -41,6 +41,10 @@ __all__ = [
     "config_heat3d_127",
     "config_batched",
     "small_variable_2d",
+    "gaussian_bumps_coefficient",
+    "paper_heat2d",
+    "paper_logistic2d",
+    "paper_heat3d",
 ]
 
 
@@ -247,3 +251,31 @@ def paper_heat2d(n: int, leaf: int, eps: float, seed: int = 0) -> Workload:
     u0 = sum(np.exp(-sum((x - c) ** 2 for x in xs) / 0.05) for c in (0.35, 0.65))
     return Workload(f"paper_heat2d_{n - 1}", 2, n, leaf, L, 1.0 / n, eps, a, u0,
                     (0, 0.0, 0.0), steps=100, tol=1e-12)
+
+
+def paper_logistic2d(n: int, leaf: int, eps: float, seed: int = 0) -> Workload:
+    """Paper Example 2 (2D logistic) generator: the coefficient of Example 1,
+    u0 the bump of Eq. 2d_u0 (c = 0.5, sigma^2 = 0.05), k1 = 1, k2 = 10,
+    dt = h as in Example 1."""
+    L = int(round(math.log2(n // leaf)))
+    rng = np.random.default_rng(seed)
+    a = gaussian_bumps_coefficient(rng, n, 2, 100, 0.005, 0.1, 10.0)
+    u0 = gaussian_bump_u0(n, 2)
+    return Workload(f"paper_logistic2d_{n - 1}", 2, n, leaf, L, 1.0 / n, eps, a, u0,
+                    (1, 1.0, 10.0), steps=100, tol=1e-12)
+
+
+def paper_heat3d(n: int, leaf: int, eps: float, seed: int = 0,
+                 logistic: bool = False) -> Workload:
+    """Paper Example 1 in 3D (and Example 2 in 3D with ``logistic``): bumps
+    with sigma_2^2 = 0.005 on [0.05, 20] (1000 of them; 200 for the logistic
+    case), u0 the Gaussian of Eq. 3d_u0 at c = 0.5 with sigma^2 = 0.05 (times
+    (2 pi sigma)^{-3/2} for the logistic case), dt = 0.1 h."""
+    L = int(round(math.log2(n // leaf)))
+    rng = np.random.default_rng(seed)
+    a = gaussian_bumps_coefficient(rng, n, 3, 200 if logistic else 1000, 0.005, 0.05, 20.0)
+    amp = (2.0 * math.pi * math.sqrt(0.05)) ** -1.5 if logistic else 1.0
+    u0 = gaussian_bump_u0(n, 3, amplitude=amp)
+    name = "paper_logistic3d" if logistic else "paper_heat3d"
+    return Workload(f"{name}_{n - 1}", 3, n, leaf, L, 0.1 / n, eps, a, u0,
+                    (1, 1.0, 10.0) if logistic else (0, 0.0, 0.0), steps=100, tol=1e-12)
