@@ -257,6 +257,29 @@ def kernel_traffic(name: str) -> float | None:
 
 # ----------------------------------------------------------------------- our arm
 
+def max_over_ranks(vals, dist, device):
+    """Each timing's maximum over the ranks: the slowest replica sets the job's
+    time.  ``dist`` is torch.distributed (or None on one process)."""
+    if dist is None:
+        return list(vals)
+    import torch
+    tt = torch.tensor(vals, dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return tt.tolist()
+
+
+def job_rate(units_per_rank, t_ms: float, world: int) -> float:
+    """Whole-job rate: every rank processed ``units_per_rank`` units and the
+    job took ``t_ms`` (already the maximum over the ranks)."""
+    return world * units_per_rank / (t_ms / 1e3)
+
+
+def replica_seed(rank: int) -> int:
+    """Seed of rank ``rank``'s coefficient field: every replica solves its own
+    independent problem of the same shape (weak scaling, no data exchange)."""
+    return 1 + rank
+
+
 def run_ours(args, rank: int, world: int, dist) -> dict | None:
     import numpy as np
     import torch
@@ -269,11 +292,11 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
     local = int(os.environ.get("LOCAL_RANK", rank))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = W.config_fisher2d_1023(eps=args.eps, seed=1 + rank)
+    w = W.config_fisher2d_1023(eps=args.eps, seed=replica_seed(rank))
     if args.n != 1024:
         import math as _m
         L = int(round(_m.log2(args.n // 16)))
-        rng = np.random.default_rng(1 + rank)
+        rng = np.random.default_rng(replica_seed(rank))
         w = W.Workload(f"fisher2d_{args.n - 1}", 2, args.n, 16, L, 1.0, args.eps,
                        W.lognormal_coefficient(W.grf(rng, args.n, 2, 0.05), 1e4),
                        W.gaussian_bump_u0(args.n, 2), (1, 1.0, 1.0))
@@ -397,17 +420,12 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
         serving = run_serving(args, local, W, np)
 
     # ---- max over ranks
-    vals = [t_ms, e2e_ms, t64_ms]
-    if dist is not None:
-        tt = torch.tensor(vals, dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        vals = tt.tolist()
-    t_ms, e2e_ms, t64_ms = vals
+    t_ms, e2e_ms, t64_ms = max_over_ranks([t_ms, e2e_ms, t64_ms], dist, dev)
     if rank != 0:
         return None
 
     K = args.steps
-    value = world * K / (t_ms / 1e3)
+    value = job_rate(K, t_ms, world)
     lat_sorted = sorted(lat)
 
     def pct(xs, q):
@@ -481,17 +499,17 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
         "latency_ms": {"p50": pct(lat_sorted, 50), "p99": pct(lat_sorted, 99),
                        "api": f"cn_step, one call per step ({len(lat)} steps, per-step CUDA events)"},
         "iters_per_step": round(iters_per_step, 3),
-        "cg_iters_per_s": round(world * sum(its) / (t_ms / 1e3), 2),
+        "cg_iters_per_s": round(job_rate(sum(its), t_ms, world), 2),
         "t_f_s": {"fp32": round(tf32, 3), "fp64": round(tf64, 3)},
         "autotune_s": {"fp32": tuning_s.get(H.HIF_FP32), "fp64": tuning_s.get(H.HIF_FP64)},
-        "fp64_path": {"value": round(world * max(1, K // 2) / (t64_ms / 1e3), 3), "unit": "steps/s",
+        "fp64_path": {"value": round(job_rate(max(1, K // 2), t64_ms, world), 3), "unit": "steps/s",
                       "ms_per_step": round(t64_ms / max(1, K // 2), 4),
                       "iters_per_step": round(sum(its64) / len(its64), 3),
                       "p50_ms": pct(sorted(lat64), 50), "p99_ms": pct(sorted(lat64), 99)},
         "factor": {"entries": info32["factor_entries"], "apply_bytes_fp32": info32["apply_bytes"],
                    "apply_bytes_fp64": info64["apply_bytes"], "root": info32["root_size"],
                    "device_bytes": info32["device_bytes"]},
-        "e2e": {"value": round(world * K_e2e / (e2e_ms / 1e3), 3), "unit": "steps/s",
+        "e2e": {"value": round(job_rate(K_e2e, e2e_ms, world), 3), "unit": "steps/s",
                 "h2d_bytes_per_step": 8 * w.N, "d2h_bytes_per_step": 8 * w.N,
                 "api": "cn_step via the C ABI, u^k copied from pinned host memory and u^{k+1} read back every step"},
         "gpu_launches": int(launches),
