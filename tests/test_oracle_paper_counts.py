@@ -1,5 +1,5 @@
 """Pin of the whole oracle chain (stencil, PHIF factor, PCG, CN loop) to the
-iteration counts the paper prints.
+iteration counts the paper prints, and of the factor to its printed accuracy.
 
 The four result tables of Sec. 5 give n_i, the mean number of PHIF-PCG
 iterations per CN step at relative residual 1e-12, for the heat and the logistic
@@ -101,3 +101,25 @@ def test_oracle_counts_do_not_grow_with_N():
     a = _mean_iters(W.paper_heat2d(64, 8, 1e-3, seed=0))
     b = _mean_iters(W.paper_heat2d(128, 8, 1e-3, seed=0))
     assert abs(a - b) <= 1.0
+
+
+def test_factor_error_matches_printed():
+    """Sec. 5, Example 1: the paper estimates ||I - A F^{-1}|| = 7.9e-6 at
+    eps = 1e-6 (``golden/paper_factor_error.txt``).  On the same recipe at 63^2
+    the oracle's estimate (the same power iteration) must lie within a factor
+    of 10 of it: the paper's grid is 4000 times larger and the norm grows
+    slowly with N (2.6e-6 at 63^2, 5.6e-6 at 127^2).  A 100-fold looser ID gives
+    3.4e-4, a 100-fold tighter one 2.2e-8, and a missing skeleton diagonal
+    correction gives 3.6."""
+    from oracle import grid, hif
+    from test_oracle_hif import _power_norm_I_minus_AFinv
+    path = os.path.join(os.path.dirname(GOLDEN), "paper_factor_error.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.lstrip().startswith("#")]
+    (ex, dim, eps, side, printed), = rows
+    assert (ex, dim, float(eps), side) == ("heat", "2", 1e-6, "4095")
+    printed = float(printed)
+    w = W.paper_heat2d(64, 8, float(eps), seed=0)
+    A = grid.assemble_A(w.a_nodes, w.dt)
+    F = hif.factor(A, w.n, 2, w.leaf, w.eps)
+    e = _power_norm_I_minus_AFinv(A, F, iters=30)
+    assert printed / 10 <= e <= printed * 10, (e, printed)
