@@ -9,7 +9,9 @@ recently used idle operators when the HBM budget would be exceeded), and runs
 the whole batch with one ``cn_step_batched`` call, whose steps overlap on the
 device.  Requests that arrive while a batch runs join the next one
 (step-level continuous batching).  Each request completes with the new step
-index, the PCG iteration count and its latency (arrival to result ready).
+index, the PCG iteration count and its latency (arrival to result ready).  A
+client may cancel a request's future while it is still queued; the step is then
+not taken.  Once a request joins a batch its future can no longer be cancelled.
 
 Determinism: every kernel of the library reduces in a fixed order and the
 factorization is deterministic, so an operator's trajectory is the same
@@ -88,9 +90,9 @@ class _Request:
 class CNServer:
     """Step-level continuous batching of CN steps on one GPU (see module doc)."""
 
-    def __init__(self, hbm_budget_bytes: int, device: int = 0, max_batch: int = 256):
+    def __init__(self, hbm_budget_bytes: int, device=0, max_batch: int = 256):
         self.budget = int(hbm_budget_bytes)
-        self.device = torch.device("cuda", device)
+        self.device = device if isinstance(device, torch.device) else torch.device("cuda", device)
         self.max_batch = max_batch
         self._ops: dict = {}
         self._pending: collections.deque = collections.deque()
@@ -126,7 +128,7 @@ class CNServer:
         with self._cv:
             st = self._ops[op_id]
             if st.resident is not None:
-                torch.cuda.synchronize(self.device)
+                self._sync()
                 return st.resident.u.cpu().numpy().copy()
             return st.u_host.copy()
 
@@ -152,6 +154,10 @@ class CNServer:
                 st.resident = None
 
     # -------------------------------------------------------------- scheduler
+    def _sync(self) -> None:
+        if self.device.type == "cuda":
+            torch.cuda.synchronize(self.device)
+
     def _estimate(self, spec: OperatorSpec) -> int:
         return _BYTES_PER_DOF_ESTIMATE[spec.dim] * spec.N
 
@@ -163,7 +169,7 @@ class CNServer:
             return False
         _, oid = min(cands, key=lambda t: t[0])
         st = self._ops[oid]
-        torch.cuda.synchronize(self.device)
+        self._sync()
         u_host = st.resident.u.cpu().numpy().copy()
         with self._cv:
             res, st.resident, st.u_host = st.resident, None, u_host
@@ -196,13 +202,16 @@ class CNServer:
             pass
 
     def _take_batch(self) -> list:
-        """Pending requests, at most one per operator (the rest stay queued)."""
+        """Pending requests, at most one per operator (the rest stay queued).
+        Cancelled requests are dropped; the ones taken are marked running."""
         batch, seen, rest = [], set(), collections.deque()
         while self._pending and len(batch) < self.max_batch:
             r = self._pending.popleft()
+            if r.future.cancelled():
+                continue
             if r.op_id in seen:
                 rest.append(r)
-            else:
+            elif r.future.set_running_or_notify_cancel():
                 seen.add(r.op_id)
                 batch.append(r)
         while rest:
@@ -210,7 +219,8 @@ class CNServer:
         return batch
 
     def _loop(self) -> None:
-        torch.cuda.set_device(self.device)
+        if self.device.type == "cuda":
+            torch.cuda.set_device(self.device)
         while True:
             with self._cv:
                 while not self._pending and not self._stop:
@@ -218,6 +228,8 @@ class CNServer:
                 if self._stop and not self._pending:
                     return
                 batch = self._take_batch()
+            if not batch:  # everything taken was cancelled
+                continue
             try:
                 keep = {r.op_id for r in batch}
                 for r in batch:
@@ -244,5 +256,7 @@ class CNServer:
                         if not r.future.done():
                             r.future.set_exception(exc)
                     while self._pending:
-                        self._pending.popleft().future.set_exception(exc)
+                        f = self._pending.popleft().future
+                        if not f.done():  # a cancelled request stays cancelled
+                            f.set_exception(exc)
                 return
