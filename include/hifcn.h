@@ -112,14 +112,18 @@ typedef struct {
  * Jacobi on every separator entity and skeletonization of every edge (2D) /
  * face (+ edge, 3D) with all IDs of one sub-step computed from the matrix as
  * it stood before the sub-step.
- * Errors: HIF_EINVAL, HIF_ENOMEM, HIF_ENOTSPD, HIF_ECUDA. */
+ * Errors: HIF_EINVAL (also for an option out of range: eps or cg_tol negative
+ * or not finite, theta outside (0, 1], an unknown precision, x0_mode, solver or
+ * skel_edges_3d, cg_maxit, true_res_period or bf16_top_levels negative; all of
+ * these are checked before any device memory is taken), HIF_ENOMEM,
+ * HIF_ENOTSPD, HIF_ECUDA. */
 int hif_setup(const hif_grid *grid, const double *a_nodes, double dt, const hif_options *opt,
               hif_stream stream, hif_handle **out);
 
 /* ---------------------------------------------------------------------------
  * hif_import_factor - build a handle from a factor blob instead of factoring.
  *   blob/bytes  host, the packed interchange format written by
- *               hif_export_factor ("HIFF" v1, see DESIGN of the format below).
+ *               hif_export_factor ("HIFF" v1, layout below).
  *   a_nodes, dt as in hif_setup (the stencil of A is assembled from them).
  * Format (little endian): "HIFF", int32 version=1, dim, n, leaf, levels,
  * reserved, int64 N, double eps, double dt; per level: int32 ncells, ngroups;

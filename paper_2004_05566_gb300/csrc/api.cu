@@ -395,11 +395,15 @@ int create_handle(const hif_grid *grid, const double *a_nodes, double dt, const 
   h->h = 1.0 / grid->n;
   if (opt) h->opt = *opt;
   else hif_default_options(&h->opt);
+  // every option is checked here, before any device memory is taken
   if ((h->opt.precision != HIF_FP64 && h->opt.precision != HIF_FP32 &&
        h->opt.precision != HIF_FP32_BF16TOP) ||
       h->opt.bf16_top_levels < 0 || !(h->opt.theta > 0.0) ||
       !(h->opt.theta <= 1.0) || (h->opt.x0_mode != 0 && h->opt.x0_mode != 1) ||
-      (h->opt.solver != 0 && h->opt.solver != 1) || h->opt.cg_maxit < 0) {
+      (h->opt.solver != 0 && h->opt.solver != 1) || h->opt.cg_maxit < 0 ||
+      !(h->opt.eps >= 0.0) || !std::isfinite(h->opt.eps) || !(h->opt.cg_tol >= 0.0) ||
+      !std::isfinite(h->opt.cg_tol) || h->opt.true_res_period < 0 ||
+      (h->opt.skel_edges_3d != 0 && h->opt.skel_edges_3d != 1)) {
     delete h;
     return HIF_EINVAL;
   }
@@ -650,10 +654,6 @@ int hif_setup(const hif_grid *grid, const double *a_nodes, double dt, const hif_
   cudaStream_t s = (cudaStream_t)stream;
   Handle *h = nullptr;
   HIF_TRY(create_handle(grid, a_nodes, dt, opt, s, &h));
-  if (!(h->opt.eps >= 0.0)) {
-    delete h;
-    return HIF_EINVAL;
-  }
   double t0 = now_seconds();
   int st = gpu_setup(h, a_nodes, s);
   if (st == HIF_OK) st = finish_device_factor(h, s);
