@@ -131,6 +131,9 @@ def _vec(t: torch.Tensor, N: int, name: str) -> c_void_p:
         raise TypeError(f"{name} must be a CUDA float64 tensor")
     if not t.is_contiguous() or t.numel() != N:
         raise ValueError(f"{name} must be contiguous with {N} elements")
+    if t.device.index != torch.cuda.current_device():  # the library works on the current device
+        raise ValueError(f"{name} is on {t.device}, the current device is "
+                         f"cuda:{torch.cuda.current_device()}")
     return c_void_p(t.data_ptr())
 
 

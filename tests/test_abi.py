@@ -67,3 +67,16 @@ def test_host_side_validation_without_gpu(lib):
         setattr(ob, field, value)
         assert lib.hif_setup(ctypes.byref(good), ctypes.c_void_p(1), 1.0, ctypes.byref(ob), None,
                              ctypes.byref(out)) == H.HIF_EINVAL, field
+
+
+def test_binding_refuses_host_and_mistyped_tensors():
+    """The binding marshals CUDA float64 tensors only: a host tensor, another
+    dtype or a wrong length is refused before any library call."""
+    import torch
+    import paper_2004_05566_gb300.hifcn as H
+    with pytest.raises(TypeError):
+        H._vec(torch.zeros(9, dtype=torch.float64), 9, "x")
+    with pytest.raises(TypeError):
+        H._vec(torch.zeros(9, dtype=torch.float32), 9, "x")
+    with pytest.raises(TypeError):
+        H._vec([0.0] * 9, 9, "x")
