@@ -8,6 +8,9 @@
   at eps = 1e-6); a sign or index slip in any step breaks one of these.
 * ID: exact on matrices of known low rank, and within eps of the input on
   matrices with decaying spectrum (Eq. 2_5).
+* One level step by step at eps = 0: the Schur complement of the cell
+  elimination, the identity diagonal blocks after block Jacobi and the root
+  against dense linear algebra.
 * PCG with the identity preconditioner reproduces scipy's CG iterates.
 * CN: for a = 1 the oracle matches the exact DST-I mode evolution to the CG
   tolerance, with and without a linear reaction term.
@@ -231,3 +234,39 @@ def test_time_varying_coefficient_matches_mode_products():
     u1, it1 = pcg.cn_solve_varying(a_seq, u0, dt, m, 1e-6, tol=1e-12, refactor_every=1)
     assert np.linalg.norm(u1 - exact) <= 1e-9 * np.linalg.norm(exact)
     assert sum(iters) >= sum(it1)
+
+
+@pytest.mark.parametrize("dim,n,m", [(2, 16, 8), (3, 8, 4)])
+def test_one_level_steps_against_dense_algebra(dim, n, m):
+    """One level (L = 1) at eps = 0, step by step against dense linear algebra.
+
+    * Cell elimination (Eq. 2_3, the cells' updates adding up as in Eq. 3_1):
+      the matrix left on the separators is the dense Schur complement
+      S = A_RR - A_RI A_II^{-1} A_IR over all cell interiors at once.
+    * Block Jacobi (Eq. jacobi-precond): with D = blockdiag(L_g^{-1}),
+      D S D^T has identity diagonal blocks on every entity.
+    * At eps = 0 no DOF is redundant, and the root factor reproduces D S D^T.
+    """
+    A, F = _setup(dim, n, m, 0.0)
+    assert F.levels == 1
+    lvl = F.level_factors[0]
+    Ad = A.toarray()
+    I = np.concatenate([c.I for c in lvl.cells])
+    R = np.setdiff1d(np.arange(A.shape[0]), I)
+    S = Ad[np.ix_(R, R)] - Ad[np.ix_(R, I)] @ np.linalg.solve(Ad[np.ix_(I, I)], Ad[np.ix_(I, R)])
+    pos = {d: k for k, d in enumerate(R)}
+    D = np.zeros_like(S)
+    for j in lvl.jacobi:
+        p = [pos[d] for d in j.I]
+        D[np.ix_(p, p)] = np.linalg.inv(j.L)
+    covered = sorted(pos[d] for j in lvl.jacobi for d in j.I)
+    assert covered == list(range(len(R)))  # every separator DOF in exactly one entity
+    Bm = D @ S @ D.T
+    for j in lvl.jacobi:
+        p = [pos[d] for d in j.I]
+        assert np.allclose(Bm[np.ix_(p, p)], np.eye(len(p)), atol=1e-12)
+    assert all(len(k.rd) == 0 for step in lvl.skel_steps for k in step)
+    r = [pos[d] for d in F.root_idx]
+    assert sorted(r) == list(range(len(R)))
+    AL = F.root_L @ F.root_L.T
+    assert np.allclose(AL, Bm[np.ix_(r, r)], rtol=0, atol=1e-10 * np.abs(Bm).max())
