@@ -463,11 +463,12 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
     cpu = None
     if world == 1 and not args.no_cpu_baseline and args.n == 1024:
         try:
-            r = run_oracle_subprocess(256, 8, 1, args.eps)
+            # 511^2: a quarter of the workload's unknowns, ~10 s of timed oracle steps
+            r = run_oracle_subprocess(512, 8, 1, args.eps)
             cpu = {"value": round(r["steps_per_s_scaled"], 6), "unit": "steps/s", "cores": 1,
                    "kind": "oracle",
                    "sample": (f"oracle (Python/NumPy/SciPy FP64, 1 BLAS thread) on the same recipe "
-                              f"at 255^2 (N={r['N_sample']}), {r['steps']} timed CN steps "
+                              f"at {r['n'] - 1}^2 (N={r['N_sample']}), {r['steps']} timed CN steps "
                               f"({r['seconds']:.1f} s, {r['iters_per_step']:.1f} PCG it/step), "
                               f"setup untimed ({r['t_f']:.1f} s); steps/s scaled by N to 1023^2 "
                               f"(measured on sample: {r['steps_per_s_sample']:.3f} steps/s)"),
