@@ -129,3 +129,37 @@ def test_workload_contrast_and_shapes():
     assert abs(g.mean()) < 1e-12
     n, m, L = W.snap_side(300.0)
     assert n == (1 << L) * m and 8 <= m <= 16 and abs(n - 1 - 300) <= 0.125 * 300
+
+
+def test_paper_recipes_match_the_printed_parameters():
+    """Sec. 5 recipes: coefficient ranges, initial conditions and time steps."""
+    import math
+    w = W.paper_heat2d(64, 8, 1e-3)
+    assert (w.a_nodes.min(), w.a_nodes.max()) == pytest.approx((0.1, 10.0), abs=1e-12)
+    assert w.dt == 1.0 / 64 and w.tol == 1e-12 and w.reaction[0] == 0
+    # the two Gaussians peak at (0.35, 0.35) and (0.65, 0.65): the maximum sits on the
+    # diagonal next to one of them (interior node (i, j) is at y = (i+1)/64, x = (j+1)/64)
+    i, j = divmod(int(np.argmax(w.u0)), 63)
+    x, y = (j + 1) / 64, (i + 1) / 64
+    assert x == y and min(abs(x - 0.35), abs(x - 0.65)) < 1.0 / 64
+    w = W.paper_logistic2d(64, 8, 1e-6)
+    assert w.reaction == (1, 1.0, 10.0) and w.dt == 1.0 / 64
+    assert w.u0.max() <= 2.0 / (3.0 * math.sqrt(2 * math.pi * 0.05)) + 1e-12
+    w = W.paper_heat3d(16, 4, 1e-3)
+    assert (w.a_nodes.min(), w.a_nodes.max()) == pytest.approx((0.05, 20.0), abs=1e-12)
+    assert w.dt == 0.1 / 16 and w.u0.max() <= 1.0
+    w = W.paper_heat3d(16, 4, 1e-3, logistic=True)
+    assert w.reaction == (1, 1.0, 10.0)
+    assert w.u0.max() <= (2 * math.pi * math.sqrt(0.05)) ** -1.5 + 1e-12
+
+
+def test_batched_recipe():
+    ws = W.config_batched(count=12)
+    seen = set()
+    for w in ws:
+        assert w.n == (1 << w.levels) * w.leaf and 8 <= w.leaf <= 16
+        assert 63 * 0.85 <= w.n - 1 <= 511 * 1.15
+        assert 1e-2 <= w.dt <= 1.0 and w.eps == 1e-6 and w.reaction == (1, 1.0, 1.0)
+        assert abs(w.a_nodes.max() / w.a_nodes.min() - 1e3) < 1e-6 * 1e3
+        seen.add(w.a_nodes.tobytes()[:4096])
+    assert len(seen) == len(ws)  # every problem has its own field
