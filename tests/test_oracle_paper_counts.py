@@ -123,3 +123,15 @@ def test_factor_error_matches_printed():
     F = hif.factor(A, w.n, 2, w.leaf, w.eps)
     e = _power_norm_I_minus_AFinv(A, F, iters=30)
     assert printed / 10 <= e <= printed * 10, (e, printed)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("eps", [1e-3, 1e-6])
+def test_oracle_counts_at_the_papers_own_size(eps):
+    """511^2, the smallest 2D heat row of the Sec. 5 table, at its own size: the
+    oracle's mean over three steps (4.67 at eps = 1e-3, 2.33 at 1e-6) must lie
+    within one iteration of the printed mean over 100 steps (4.6 and 2.3)."""
+    w = W.paper_heat2d(512, 8, eps, seed=0)
+    got = _mean_iters(w)
+    printed = [r[4] for r in _load() if r[:4] == ("heat", 2, eps, 511)][0]
+    assert abs(got - printed) <= 1.0, (got, printed)
