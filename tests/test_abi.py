@@ -80,3 +80,38 @@ def test_binding_refuses_host_and_mistyped_tensors():
         H._vec(torch.zeros(9, dtype=torch.float32), 9, "x")
     with pytest.raises(TypeError):
         H._vec([0.0] * 9, 9, "x")
+
+
+def test_product_never_reaches_the_oracle():
+    """No file of the package (Python or CUDA/C++) imports, includes or names
+    the oracle package or the shared input generators."""
+    import ast
+    pkg = os.path.join(ROOT, "paper_2004_05566_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            path = os.path.join(dirpath, f)
+            if f.endswith(".py"):
+                tree = ast.parse(open(path).read(), path)
+                for node in ast.walk(tree):
+                    if isinstance(node, ast.Import):
+                        mods = [a.name for a in node.names]
+                    elif isinstance(node, ast.ImportFrom):
+                        mods = [node.module or ""]
+                    else:
+                        continue
+                    for m in mods:
+                        assert not m.split(".")[0] in ("oracle", "workloads"), (path, m)
+            elif f.endswith((".cu", ".cuh", ".h", ".cpp", ".c")):
+                src = open(path).read()
+                assert "oracle/" not in src and "#include \"oracle" not in src, path
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without the built CUDA library the binding raises: there is no CPU path."""
+    import paper_2004_05566_gb300.hifcn as H
+    monkeypatch.setattr(H, "_lib", None)
+    monkeypatch.setattr(H, "_LIB_PATH", str(tmp_path / "libhifcn.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        H.lib()
+    with pytest.raises(RuntimeError, match="not built"):
+        H.default_options()
