@@ -75,3 +75,24 @@ def test_clock_sampler_without_nvidia_smi(bench, tmp_path, monkeypatch):
     c.start()
     r = c.stop()
     assert r["sm_mhz"] is None and r["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_oracle_only_in_the_baseline_leg():
+    """bench.py imports the oracle only inside the CPU sample (the baseline and
+    reference legs, run in their own process); the timed GPU arm never does."""
+    import ast
+    src = open(os.path.join(ROOT, "bench.py")).read()
+    tree = ast.parse(src)
+    hosts = []
+    for fn in ast.walk(tree):
+        if isinstance(fn, ast.FunctionDef):
+            for node in ast.walk(fn):
+                if isinstance(node, ast.ImportFrom) and (node.module or "").split(".")[0] == "oracle":
+                    hosts.append(fn.name)
+                if isinstance(node, ast.Import) and any(a.name.split(".")[0] == "oracle"
+                                                        for a in node.names):
+                    hosts.append(fn.name)
+    top = [n for n in tree.body if isinstance(n, (ast.Import, ast.ImportFrom))
+           and "oracle" in ast.dump(n)]
+    assert not top
+    assert set(hosts) == {"oracle_sample"}, hosts
