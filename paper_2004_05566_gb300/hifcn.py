@@ -138,6 +138,8 @@ def _vec(t: torch.Tensor, N: int, name: str) -> c_void_p:
 
 
 def default_options(**kw) -> HifOptions:
+    """hif_options with the library's defaults, then the given fields set
+    (eps, precision, cg_tol, cg_maxit, theta, x0_mode, solver, ...)."""
     o = HifOptions()
     lib().hif_default_options(byref(o))
     for k, v in kw.items():
@@ -193,6 +195,8 @@ def hif_setup(dim: int, n: int, leaf: int, a_nodes: torch.Tensor, dt: float, opt
 
 def hif_import_factor(dim: int, n: int, leaf: int, blob: bytes, dt: float, a_nodes: torch.Tensor,
                       opt: HifOptions = None, stream=None) -> Handle:
+    """A handle from a factor blob (the interchange format of hif_export_factor)
+    instead of factoring; a_nodes and dt give the stencil of A."""
     a = _vec(a_nodes.reshape(-1), (n + 1) ** dim, "a_nodes")
     buf = ctypes.create_string_buffer(blob, len(blob))
     out = c_void_p()
@@ -204,6 +208,7 @@ def hif_import_factor(dim: int, n: int, leaf: int, blob: bytes, dt: float, a_nod
 
 
 def hif_export_factor(h: Handle) -> bytes:
+    """The handle's FP64 factor as an interchange blob (checkpoint)."""
     nb = c_size_t(0)
     _check("hif_export_factor", lib().hif_export_factor(h.ptr, None, byref(nb)))
     buf = ctypes.create_string_buffer(nb.value)
@@ -317,16 +322,21 @@ def hif_autotune(h: Handle, stream=None):
 
 
 def hif_set_reaction(h: Handle, kind: int, k1: float = 1.0, k2: float = math.inf):
+    """Explicit reaction of the right-hand side (Eq. nr): kind 1 is
+    k1 u (1 - u/k2) (k2 = inf: linear k1 u), kind 0 none."""
     _check("hif_set_reaction", lib().hif_set_reaction(h.ptr, kind, c_double(k1), c_double(k2)))
 
 
 def hif_query(h: Handle) -> dict:
+    """Sizes of the handle: N, levels, root size, factor entries, apply bytes,
+    device bytes, setup seconds, S-form levels."""
     info = HifInfo()
     _check("hif_query", lib().hif_query(h.ptr, byref(info)))
     return {k: getattr(info, k) for k, _ in HifInfo._fields_}
 
 
 def hif_destroy(h: Handle):
+    """Free the handle's device memory (the same as h.close())."""
     h.close()
 
 
