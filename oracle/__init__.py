@@ -20,7 +20,7 @@ Modules (each function cites the passage of the paper it follows):
 
 Every function is pinned by ``tests/test_oracle_*.py`` (closed forms, exactness
 at eps = 0, invariants).  The iteration counts at eps > 0 are pinned loosely,
-to within 1.5 iterations, against the counts the paper prints for its Sec. 5
+to within 1.5 iterations, against the counts the paper prints for its Sec. 3
 recipes (``tests/golden/paper_iteration_counts.txt``); the paper's draws and
 problem sizes differ from the oracle's, so no tighter pin is possible.
 """

@@ -1,4 +1,4 @@
-"""The GPU factor against the iteration counts printed in Sec. 5.
+"""The GPU factor against the iteration counts printed in Sec. 3.
 
 The FP64 path (GPU factorization, GPU PCG, tolerance 1e-12) runs the
 paper's recipes at 63^2 and 15^3, heat and logistic, at eps = 1e-3 and 1e-6.

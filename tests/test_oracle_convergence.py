@@ -2,7 +2,7 @@
 
 Sec. 2 builds the scheme from second-order differences in space and the
 Crank-Nicolson rule in time, and the paper steps with dt = h.  The error is then
-O(h^2), and Sec. 5 (Example 2, the error plot) reports the error of the
+O(h^2), and Sec. 3 (Example 2, the error plot) reports the error of the
 logistic problem as close to second order asymptotically.  These tests check
 the oracle against the continuous problem, not against its own discrete
 closed form:

@@ -1,12 +1,12 @@
 """Pin of the whole oracle chain (stencil, PHIF factor, PCG, CN loop) to the
 iteration counts the paper prints, and of the factor to its printed accuracy.
 
-The four result tables of Sec. 5 give n_i, the mean number of PHIF-PCG
+The four result tables of Sec. 3 give n_i, the mean number of PHIF-PCG
 iterations per CN step at relative residual 1e-12, for the heat and the logistic
 examples in 2D and 3D at eps = 1e-3 and 1e-6 (``golden/paper_iteration_counts.txt``).
 The paper reports these counts as essentially independent of N; across a
 256-fold range of N its printed means move by at most 1.7 iterations.  The
-oracle runs the same recipes (Sec. 5: Gaussian-bump coefficient fields, the
+oracle runs the same recipes (Sec. 3: Gaussian-bump coefficient fields, the
 printed initial conditions, dt = h in 2D and 0.1 h in 3D) on small grids, and
 its mean count must lie within 1.5 iterations of the count printed for the
 smallest problem, with eps = 1e-6 needing fewer iterations than eps = 1e-3.
@@ -104,7 +104,7 @@ def test_oracle_counts_do_not_grow_with_N():
 
 
 def test_factor_error_matches_printed():
-    """Sec. 5, Example 1: the paper estimates ||I - A F^{-1}|| = 7.9e-6 at
+    """Sec. 3, Example 1: the paper estimates ||I - A F^{-1}|| = 7.9e-6 at
     eps = 1e-6 (``golden/paper_factor_error.txt``).  On the same recipe at 63^2
     the oracle's estimate (the same power iteration) must lie within a factor
     of 10 of it: the paper's grid is 4000 times larger and the norm grows
@@ -128,7 +128,7 @@ def test_factor_error_matches_printed():
 @pytest.mark.slow
 @pytest.mark.parametrize("eps", [1e-3, 1e-6])
 def test_oracle_counts_at_the_papers_own_size(eps):
-    """511^2, the smallest 2D heat row of the Sec. 5 table, at its own size: the
+    """511^2, the smallest 2D heat row of the Sec. 3 table, at its own size: the
     oracle's mean over three steps (4.67 at eps = 1e-3, 2.33 at 1e-6) must lie
     within one iteration of the printed mean over 100 steps (4.6 and 2.3)."""
     w = W.paper_heat2d(512, 8, eps, seed=0)

@@ -132,7 +132,7 @@ def test_workload_contrast_and_shapes():
 
 
 def test_paper_recipes_match_the_printed_parameters():
-    """Sec. 5 recipes: coefficient ranges, initial conditions and time steps."""
+    """Sec. 3 recipes: coefficient ranges, initial conditions and time steps."""
     import math
     w = W.paper_heat2d(64, 8, 1e-3)
     assert (w.a_nodes.min(), w.a_nodes.max()) == pytest.approx((0.1, 10.0), abs=1e-12)
