@@ -314,7 +314,9 @@ int64_t hif_launch_count(void);
 const char *hif_strerror(int status);
 
 /* hif_last_error - detail of the last failure on the calling host thread
- * (the failing CUDA call or the reason a blob was rejected); "" if none. */
+ * (the refused argument or option, e.g. "option out of range: cg_tol", the
+ * failing CUDA call, or the reason a blob was rejected); "" if none.  A
+ * successful call does not clear it. */
 const char *hif_last_error(void);
 
 #ifdef __cplusplus

@@ -370,16 +370,39 @@ int build_contrib_map(Handle *h, LevelHost &H) {
   return HIF_OK;
 }
 
+// HIF_EINVAL with the reason as the thread's last error
+static int invalid(const char *why) {
+  set_last_error(why);
+  return HIF_EINVAL;
+}
+
 int validate(const hif_grid *grid, double dt, const void *a_nodes) {
-  if (!grid || !a_nodes) return HIF_EINVAL;
-  if (grid->dim != 2 && grid->dim != 3) return HIF_EINVAL;
-  if (grid->leaf < 2 || grid->n < 4) return HIF_EINVAL;
+  if (!grid) return invalid("grid is NULL");
+  if (!a_nodes) return invalid("a_nodes is NULL");
+  if (grid->dim != 2 && grid->dim != 3) return invalid("grid: dim must be 2 or 3");
+  if (grid->leaf < 2 || grid->n < 4) return invalid("grid: leaf must be >= 2 and n >= 4");
   int L = grid_levels(grid->n, grid->leaf);
-  if (L < 1) return HIF_EINVAL;
+  if (L < 1) return invalid("grid: n must be leaf * 2^L with L >= 1");
   double N = std::pow((double)(grid->n - 1), grid->dim);
-  if (N >= 2147483647.0) return HIF_EINVAL;
-  if (!(dt > 0.0) || !std::isfinite(dt)) return HIF_EINVAL;
+  if (N >= 2147483647.0) return invalid("grid: (n-1)^dim unknowns must stay below 2^31 - 1");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return invalid("dt must be positive and finite");
   return HIF_OK;
+}
+
+// name of the first option out of range, or nullptr
+static const char *bad_option(const hif_options &o) {
+  if (o.precision != HIF_FP64 && o.precision != HIF_FP32 && o.precision != HIF_FP32_BF16TOP)
+    return "precision";
+  if (o.bf16_top_levels < 0) return "bf16_top_levels";
+  if (!(o.theta > 0.0) || !(o.theta <= 1.0)) return "theta";
+  if (o.x0_mode != 0 && o.x0_mode != 1) return "x0_mode";
+  if (o.solver != 0 && o.solver != 1) return "solver";
+  if (o.cg_maxit < 0) return "cg_maxit";
+  if (!(o.eps >= 0.0) || !std::isfinite(o.eps)) return "eps";
+  if (!(o.cg_tol >= 0.0) || !std::isfinite(o.cg_tol)) return "cg_tol";
+  if (o.true_res_period < 0) return "true_res_period";
+  if (o.skel_edges_3d != 0 && o.skel_edges_3d != 1) return "skel_edges_3d";
+  return nullptr;
 }
 
 int create_handle(const hif_grid *grid, const double *a_nodes, double dt, const hif_options *opt,
@@ -396,15 +419,9 @@ int create_handle(const hif_grid *grid, const double *a_nodes, double dt, const 
   if (opt) h->opt = *opt;
   else hif_default_options(&h->opt);
   // every option is checked here, before any device memory is taken
-  if ((h->opt.precision != HIF_FP64 && h->opt.precision != HIF_FP32 &&
-       h->opt.precision != HIF_FP32_BF16TOP) ||
-      h->opt.bf16_top_levels < 0 || !(h->opt.theta > 0.0) ||
-      !(h->opt.theta <= 1.0) || (h->opt.x0_mode != 0 && h->opt.x0_mode != 1) ||
-      (h->opt.solver != 0 && h->opt.solver != 1) || h->opt.cg_maxit < 0 ||
-      !(h->opt.eps >= 0.0) || !std::isfinite(h->opt.eps) || !(h->opt.cg_tol >= 0.0) ||
-      !std::isfinite(h->opt.cg_tol) || h->opt.true_res_period < 0 ||
-      (h->opt.skel_edges_3d != 0 && h->opt.skel_edges_3d != 1)) {
+  if (const char *bad = bad_option(h->opt)) {
     delete h;
+    set_last_error(std::string("option out of range: ") + bad);
     return HIF_EINVAL;
   }
   // HIFCN_NO_TMA=1 selects the register-streaming leaf kernels (A/B measurement)

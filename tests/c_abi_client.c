@@ -35,6 +35,10 @@ int main(void) {
   hif_info info;
   const int codes[] = {HIF_OK, HIF_EINVAL, HIF_ENOMEM, HIF_ENOTSPD,
                        HIF_ENOCONV, HIF_ETIMEOUT, HIF_ECUDA, HIF_EFORMAT};
+  static const char *const names[14] = {"eps", "eps", "theta", "theta", "precision", "x0_mode",
+                                        "solver", "cg_maxit", "cg_tol", "cg_tol",
+                                        "true_res_period", "skel_edges_3d", "bf16_top_levels",
+                                        "eps"};
   int i, j;
 
   /* defaults */
@@ -51,6 +55,7 @@ int main(void) {
   CHECK(setup_status(&good, NULL, 1.0, NULL) == HIF_EINVAL);
   g = good; g.n = 100; g.leaf = 16;                 /* not leaf * 2^L */
   CHECK(setup_status(&g, a, 1.0, NULL) == HIF_EINVAL);
+  CHECK(strstr(hif_last_error(), "leaf * 2^L") != NULL);
   g = good; g.n = 8; g.leaf = 8;                    /* L = 0 */
   CHECK(setup_status(&g, a, 1.0, NULL) == HIF_EINVAL);
   g = good; g.dim = 4;
@@ -62,6 +67,7 @@ int main(void) {
   CHECK(setup_status(&good, a, 0.0, NULL) == HIF_EINVAL);
   CHECK(setup_status(&good, a, -1.0, NULL) == HIF_EINVAL);
   CHECK(setup_status(&good, a, INFINITY, NULL) == HIF_EINVAL);
+  CHECK(strstr(hif_last_error(), "dt") != NULL);
 
   /* options out of range */
   for (i = 0; i < 14; ++i) {
@@ -83,6 +89,8 @@ int main(void) {
       default: o.eps = INFINITY; break;
     }
     CHECK(setup_status(&good, a, 1.0, &o) == HIF_EINVAL);
+    CHECK(strncmp(hif_last_error(), "option out of range: ", 21) == 0);
+    CHECK(strcmp(hif_last_error() + 21, names[i]) == 0); /* names the option */
   }
 
   /* every handle call refuses a NULL handle without touching the device */
