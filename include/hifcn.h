@@ -162,14 +162,21 @@ int hif_apply(hif_handle *h, const double *x, double *y, int precision, hif_stre
  * cudaFree may cause.  The call allocates nothing (no cudaMalloc, no cudaFree,
  * no allocating library routine); the caller passes x and y.
  *   x, y  device, N doubles each; may not alias.
- * The first call on a device looks up the array's device address with that
- * device current; make that first call before any stream capture.  All calls
+ * Every call looks up the array's device address for the current device (a
+ * host-side lookup).  Under lazy module loading (CUDA's default) device code
+ * and the array are loaded into device memory when first used; hif_setup,
+ * hif_import_factor and hif_refactor therefore look the array up and run the
+ * handle's FP64 apply once (on zeros, with the handle's own scratch), so that
+ * later calls of this entry point for that handle load and allocate nothing.
+ * Set the handle up on the device it is applied on, before memory is reserved
+ * and before any stream capture.  All calls
  * share the one array and each call overwrites it (every slot is written
  * before it is read, nothing needs to start at zero), so calls that overlap on
  * the GPU (concurrent streams, or several handles at once) race: serialize them.
  * Kernel statistics are not recorded by this call.
- * Errors: HIF_EINVAL (NULL/aliased pointers, or a factor whose cells need more
- * than HIF_NOALLOC_MAX_SLOTS boundary slots in one level), HIF_ECUDA. */
+ * Errors: HIF_EINVAL (NULL/aliased pointers, a handle without a factor, or a
+ * factor whose cells need more than HIF_NOALLOC_MAX_SLOTS boundary slots in one
+ * level; hif_last_error names the refused argument), HIF_ECUDA. */
 #define HIF_NOALLOC_MAX_SLOTS (1 << 19)
 int hif_apply_noalloc(hif_handle *h, const double *x, double *y, hif_stream stream);
 

@@ -674,6 +674,7 @@ int hif_setup(const hif_grid *grid, const double *a_nodes, double dt, const hif_
   double t0 = now_seconds();
   int st = gpu_setup(h, a_nodes, s);
   if (st == HIF_OK) st = finish_device_factor(h, s);
+  if (st == HIF_OK) st = noalloc_prepare(h, s);
   if (st != HIF_OK) {
     delete h;
     return st;
@@ -694,6 +695,7 @@ int hif_import_factor(const hif_grid *grid, const void *blob, size_t bytes, doub
   HIF_TRY(create_handle(grid, a_nodes, dt, opt, s, &h));
   double t0 = now_seconds();
   int st = import_blob(h, blob, bytes, s);
+  if (st == HIF_OK) st = noalloc_prepare(h, s);
   if (st != HIF_OK) {
     delete h;
     return st;
@@ -821,6 +823,7 @@ int hif_refactor(hif_handle *h, const double *a_nodes, hif_stream stream) {
   HIF_TRY(stencil_update(h, a_nodes, s));
   int st = gpu_setup(h, a_nodes, s);
   if (st == HIF_OK) st = finish_device_factor(h, s);
+  if (st == HIF_OK) st = noalloc_prepare(h, s);
   if (st != HIF_OK) {
     release_factor(h);
     return st;

@@ -367,6 +367,10 @@ int cn_batched(Handle *const *hs, int count, const double *const *u, const doubl
 int gpu_setup(Handle *h, const double *a_nodes, cudaStream_t s);
 void destroy_pcg_graphs(Handle *h);
 int alloc_work(Handle *h);
+// Loads, with the handle's device current, what hif_apply_noalloc uses (its
+// static scratch and the FP64 apply kernels of the handle), so that its calls
+// allocate nothing under lazy module loading.
+int noalloc_prepare(Handle *h, cudaStream_t s);
 
 inline int grid_levels(int n, int leaf) {
   int L = 0;

@@ -96,6 +96,7 @@ int main(void) {
   /* every handle call refuses a NULL handle without touching the device */
   CHECK(hif_apply(NULL, &x, &y, HIF_FP64, NULL) == HIF_EINVAL);
   CHECK(hif_apply_noalloc(NULL, &x, &y, NULL) == HIF_EINVAL);
+  CHECK(strstr(hif_last_error(), "h is NULL") != NULL);
   CHECK(hif_matvec(NULL, &x, &y, NULL) == HIF_EINVAL);
   CHECK(pcg_solve(NULL, &x, &y, &it, &x, NULL) == HIF_EINVAL);
   CHECK(cn_step(NULL, &x, NULL, &y, &it, NULL) == HIF_EINVAL);
