@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+from parity import rel_err
 from oracle import export, grid, hif, pcg
 
 pytestmark = pytest.mark.gpu
@@ -61,8 +62,8 @@ def _import(H, case, precision=0):
     return H.hif_import_factor(w.dim, w.n, w.leaf, blob, w.dt, a, opt)
 
 
-def _rel(a, b):
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+# normwise and element-by-element relative error (the larger of the two)
+_rel = rel_err
 
 
 @pytest.mark.parametrize("case", CASES, ids=IDS)

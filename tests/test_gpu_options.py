@@ -18,6 +18,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+from parity import rel_err
 from oracle import export, grid, hif, pcg
 
 pytestmark = pytest.mark.gpu
@@ -33,8 +34,8 @@ def H():
     return H
 
 
-def _rel(a, b):
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+# normwise and element-by-element relative error (the larger of the two)
+_rel = rel_err
 
 
 def _work(n=64, m=8, dim=2, eps=1e-6, dt=0.5, seed=21):
