@@ -52,7 +52,7 @@ FALLBACK_HBM_GBS = 6800.0
 def _args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--steps", type=int, default=100)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--eps", type=float, default=1e-6)
@@ -71,23 +71,29 @@ def _args():
                    help="resident operators of the serving measurement (0: skip)")
     p.add_argument("--cpu-sample", type=int, default=0, help=argparse.SUPPRESS)
     p.add_argument("--cpu-sample-steps", type=int, default=0, help=argparse.SUPPRESS)
+    p.add_argument("--cpu-sample-procs", type=int, default=1, help=argparse.SUPPRESS)
+    p.add_argument("--ref-sample-n", type=int, default=0, help=argparse.SUPPRESS)
     return p.parse_args()
 
 
 # ----------------------------------------------------------------- CPU oracle leg
 
-def oracle_sample(n: int, steps: int, warmup: int, eps: float) -> dict:
-    """Time the oracle (as it stands) on a smaller instance of the same recipe.
+def oracle_sample(n: int, steps: int, warmup: int, eps: float, procs: int = 1) -> dict:
+    """Time the oracle (as it stands) on the same recipe at (n-1)^2.
 
-    Runs in its own process with BLAS limited to one thread; the setup is not
-    timed.  Returns steps/s measured on the sample and scaled by N to 1023^2.
+    Runs in its own process (never touches CUDA) with BLAS limited to one
+    thread.  The setup is not timed.  One thread: ``warmup`` steps, then
+    ``steps`` timed steps of the trajectory.  All cores (``procs`` > 1): the
+    process then forks ``procs`` workers that share the factor and each run
+    ``steps`` further steps of the trajectory from the same state, started
+    together; their aggregate steps/s is steps x procs / (last end - first
+    start).  At n = 1024 the sample is the workload itself (no scaling).
     """
     import numpy as np
     import workloads as W
     from oracle import grid, hif, pcg
 
     m = 16
-    L = int(round(math.log2(n // m)))
     rng = np.random.default_rng(1)
     a = W.lognormal_coefficient(W.grf(rng, n, 2, 0.05), 1e4)
     u = W.gaussian_bump_u0(n, 2)
@@ -95,42 +101,78 @@ def oracle_sample(n: int, steps: int, warmup: int, eps: float) -> dict:
     t0 = time.perf_counter()
     F = hif.factor(A, n, 2, m, eps)
     t_f = time.perf_counter() - t0
-    del L
-    iters = []
 
-    def step(u):
+    def step(u, its):
         r = grid.reaction(u, 1, 1.0, 1.0)
         g = grid.cn_rhs(a, u, 1.0, r)
         x, it, _, _ = pcg.pcg(A, g.ravel(), lambda v: hif.apply_inverse(F, v), tol=1e-10)
-        iters.append(it)
+        its.append(it)
         return x.reshape(u.shape)
 
+    its = []
     for _ in range(warmup):
-        u = step(u)
+        u = step(u, its)
+    its = []
     t0 = time.perf_counter()
     for _ in range(steps):
-        u = step(u)
+        u = step(u, its)
     dt = time.perf_counter() - t0
     N_s = (n - 1) ** 2
     N_full = 1023 ** 2
     sps = steps / dt
-    return {"steps_per_s_sample": sps, "steps_per_s_scaled": sps * N_s / N_full, "seconds": dt,
-            "steps": steps, "n": n, "N_sample": N_s, "t_f": t_f,
-            "iters_per_step": sum(iters[-steps:]) / steps}
+    out = {"steps_per_s_sample": sps, "steps_per_s_scaled": sps * N_s / N_full, "seconds": dt,
+           "steps": steps, "warmup": warmup, "n": n, "N_sample": N_s, "t_f": t_f,
+           "iters_per_step": sum(its) / max(1, steps), "cores": 1, "all_cores": None}
+    if procs > 1:
+        import multiprocessing as mp
+        ctx = mp.get_context("fork")  # this process never initialises CUDA
+        bar = ctx.Barrier(procs)
+        q = ctx.Queue()
+        u_start = u
+
+        def worker():
+            bar.wait()
+            w_its = []
+            w0 = time.perf_counter()
+            uu = u_start
+            for _ in range(steps):
+                uu = step(uu, w_its)
+            q.put((w0, time.perf_counter(), sum(w_its)))
+
+        ps = [ctx.Process(target=worker) for _ in range(procs)]
+        for pr in ps:
+            pr.start()
+        res = [q.get() for _ in ps]
+        for pr in ps:
+            pr.join()
+        span = max(r[1] for r in res) - min(r[0] for r in res)
+        agg = procs * steps / span
+        out["all_cores"] = {"steps_per_s_sample": agg, "steps_per_s_scaled": agg * N_s / N_full,
+                            "procs": procs, "seconds": span,
+                            "iters_per_step": sum(r[2] for r in res) / (procs * steps)}
+    return out
 
 
-def run_oracle_subprocess(n: int, steps: int, warmup: int, eps: float) -> dict:
+def run_oracle_subprocess(n: int, steps: int, warmup: int, eps: float, procs: int = 1) -> dict:
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
         env[k] = "1"
     env.pop("RANK", None)
     env.pop("WORLD_SIZE", None)
     cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample", str(n),
-           "--cpu-sample-steps", str(steps), "--warmup", str(warmup), "--eps", str(eps)]
+           "--cpu-sample-steps", str(steps), "--warmup", str(warmup), "--eps", str(eps),
+           "--cpu-sample-procs", str(procs)]
     out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=1800)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
     return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
 
 
 def cpu_model() -> str:
@@ -331,9 +373,12 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
         u = torch.from_numpy(w.u0.ravel().copy()).to(dev)
         v = torch.empty_like(u)
         its = []
-        for _ in range(W_):
-            v, it = H.cn_step(h, u, out=v)
-            u, v = v, u
+        if queued and W_ > 0:
+            H.cn_steps(h, u, W_)  # also sizes the step-record buffer before the timed call
+        else:
+            for _ in range(W_):
+                v, it = H.cn_step(h, u, out=v)
+                u, v = v, u
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
         barrier()
         lc0 = H.hif_launch_count()
@@ -437,42 +482,36 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
     # ---- roofline of the dominant kernel: the factor-streaming cell kernel
     # with the most time (the HBM-bound steps; the upper levels are latency
     # bound and are listed in apply_kernels)
-    cell = [s for s in stats if s["name"].startswith("cell_")]
-    dom = max(cell or stats, key=lambda s: s["ms"]) if stats else None
-    peaks = measured_peaks()
-    peak = _find_peak(peaks, ("hbm_gbs", "hbm_GBs", "copy_gbs"))
-    peak_note = "measured" if peak else "fallback"
-    if not peak:
-        peak = FALLBACK_HBM_GBS
-    roof = None
-    if dom:
-        per_launch_bytes = dom["bytes"] / dom["launches"]
-        per_launch_s = dom["ms"] / dom["launches"] / 1e3
-        achieved = per_launch_bytes / per_launch_s / 1e9
-        roof = {"bound": "hbm", "kernel": dom["name"], "achieved": round(achieved, 1),
-                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": kernel_traffic(dom["name"]),
-                "algorithmic_bytes_per_launch": per_launch_bytes,
-                "avg_launch_us": round(per_launch_s * 1e6, 2), "peak_source": peak_note,
-                "timing": "CUDA events around each launch on its stream, instrumented pass of "
-                          "the same steps"}
+    peak, peak_note = hbm_peak()
+    roof = roofline_of(stats, peak, peak_note)
+    if roof:
+        roof["traffic"] = kernel_traffic(roof["kernel"])
     kt = sorted(stats, key=lambda s: -s["ms"])
     apply_ms = sum(s["ms"] for s in stats)
 
-    # ---- CPU oracle baseline (rank 0, one GPU only)
+    # ---- CPU oracle baseline (rank 0, one GPU only): the workload itself
+    # (1023^2, no scaling), setup untimed, one thread and all host cores
     cpu = None
     if world == 1 and not args.no_cpu_baseline and args.n == 1024:
         try:
-            # 511^2: a quarter of the workload's unknowns, ~10 s of timed oracle steps
-            r = run_oracle_subprocess(512, 8, 1, args.eps)
-            cpu = {"value": round(r["steps_per_s_scaled"], 6), "unit": "steps/s", "cores": 1,
+            procs = host_cores()
+            r = run_oracle_subprocess(1024, 2, 1, args.eps, procs=procs)
+            ac = r.get("all_cores") or {}
+            cpu = {"value": round(r["steps_per_s_sample"], 6), "unit": "steps/s", "cores": 1,
                    "kind": "oracle",
-                   "sample": (f"oracle (Python/NumPy/SciPy FP64, 1 BLAS thread) on the same recipe "
-                              f"at {r['n'] - 1}^2 (N={r['N_sample']}), {r['steps']} timed CN steps "
-                              f"({r['seconds']:.1f} s, {r['iters_per_step']:.1f} PCG it/step), "
-                              f"setup untimed ({r['t_f']:.1f} s); steps/s scaled by N to 1023^2 "
-                              f"(measured on sample: {r['steps_per_s_sample']:.3f} steps/s)"),
-                   "cpu": cpu_model()}
+                   "sample": (f"oracle (Python/NumPy/SciPy FP64, 1 BLAS thread) on the workload "
+                              f"itself, 1023^2 (N={r['N_sample']}), no scaling: setup untimed "
+                              f"({r['t_f']:.1f} s), {r['warmup']} warm-up step, {r['steps']} timed "
+                              f"CN steps ({r['seconds']:.1f} s, {r['iters_per_step']:.2f} PCG it/step)"),
+                   "ms_per_cg_iteration": round(1e3 * r["seconds"] / max(1e-9, r["steps"] * r["iters_per_step"]), 1),
+                   "all_cores": ({"value": round(ac["steps_per_s_sample"], 6), "unit": "steps/s",
+                                  "cores": ac["procs"],
+                                  "sample": (f"{ac['procs']} oracle processes forked after the setup, "
+                                             f"one BLAS thread each, each running {r['steps']} further "
+                                             f"steps of the trajectory; aggregate steps/s over "
+                                             f"{ac['seconds']:.1f} s ({ac['iters_per_step']:.2f} PCG it/step)")}
+                                 if ac else None),
+                   "cpu": cpu_model(), "host_cores": procs}
         except Exception as exc:  # report, never fake
             cpu = {"value": None, "unit": "steps/s", "cores": 1, "kind": "oracle",
                    "sample": f"failed: {str(exc)[:200]}"}
@@ -500,7 +539,11 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
         "latency_ms": {"p50": pct(lat_sorted, 50), "p99": pct(lat_sorted, 99),
                        "api": f"cn_step, one call per step ({len(lat)} steps, per-step CUDA events)"},
         "iters_per_step": round(iters_per_step, 3),
+        "iters_per_step_note": (f"steps {args.warmup + 1}..{args.warmup + K} of the trajectory from u0 "
+                                f"(the early steps after the bump initial condition take more PCG "
+                                f"iterations; steps/s depends on which steps are timed)"),
         "cg_iters_per_s": round(job_rate(sum(its), t_ms, world), 2),
+        "ms_per_cg_iteration": round(t_ms / max(1, sum(its)), 4),
         "t_f_s": {"fp32": round(tf32, 3), "fp64": round(tf64, 3)},
         "autotune_s": {"fp32": tuning_s.get(H.HIF_FP32), "fp64": tuning_s.get(H.HIF_FP64)},
         "fp64_path": {"value": round(job_rate(max(1, K // 2), t64_ms, world), 3), "unit": "steps/s",
@@ -581,45 +624,87 @@ def run_serving(args, device_index, W, np) -> dict:
     return out
 
 
+def roofline_of(stats, peak, peak_note, traffic=None) -> dict | None:
+    """Achieved HBM bandwidth of the factor-streaming cell kernel with the most
+    device time: algorithmic bytes per launch / average launch duration."""
+    cell = [x for x in stats if x["name"].startswith("cell_")]
+    dom = max(cell or stats, key=lambda x: x["ms"]) if stats else None
+    if not dom or dom["launches"] == 0 or dom["ms"] <= 0:
+        return None
+    per_launch_bytes = dom["bytes"] / dom["launches"]
+    per_launch_s = dom["ms"] / dom["launches"] / 1e3
+    achieved = per_launch_bytes / per_launch_s / 1e9
+    return {"bound": "hbm", "kernel": dom["name"], "achieved": round(achieved, 1),
+            "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+            "traffic": traffic, "algorithmic_bytes_per_launch": per_launch_bytes,
+            "avg_launch_us": round(per_launch_s * 1e6, 2), "peak_source": peak_note,
+            "timing": "CUDA events around each launch on its stream, instrumented pass of "
+                      "the same steps"}
+
+
+def hbm_peak() -> tuple:
+    peak = _find_peak(measured_peaks(), ("hbm_gbs", "hbm_GBs", "copy_gbs"))
+    return (peak, "measured") if peak else (FALLBACK_HBM_GBS, "fallback")
+
+
 def run_heat3d(args, dev, H, W, np, torch) -> dict:
     """3D heat equation on 127^3 (leaf 8, L = 4, eps 1e-4, dt 0.1, lognormal a with
-    contrast 1e3, smooth random u0): GPU setup time, then `heat3d_steps` CN steps
-    with FP32 factors and FP64 CG, timed with CUDA events around the steps."""
+    contrast 1e3, smooth random u0, face + edge skeletonization, FP64 CG): GPU
+    setup time, then `heat3d_steps` CN steps queued in one cn_steps call, with
+    the factor in FP32 and the top levels in BF16 (the configuration's
+    precision) and with the factor in FP32 throughout.  Each leg reports the
+    CN-system residual ||A u^{k+1} - g|| / ||g|| of its last step, with
+    g = (I + dt/2 M) u^k = 2 u^k - A u^k (no reaction) evaluated by the
+    library's stencil, and the roofline of its dominant cell kernel."""
     w = W.config_heat3d_127()
     a = torch.from_numpy(w.a_nodes).to(dev)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    h = H.hif_setup(3, w.n, w.leaf, a, w.dt,
-                    H.default_options(eps=w.eps, precision=H.HIF_FP32, cg_tol=1e-10))
-    torch.cuda.synchronize()
-    t_setup = time.perf_counter() - t0
-    info = H.hif_query(h)
-    u = torch.from_numpy(w.u0.ravel().copy()).to(dev)
-    out = torch.empty_like(u)
-    for _ in range(2):
-        H.cn_step(h, u, out=out)
-        u, out = out, u
     stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    its = 0
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(args.heat3d_steps):
-        _, it = H.cn_step(h, u, out=out)
-        its += it
-        u, out = out, u
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t = e0.elapsed_time(e1) / 1e3
-    h.close()
+    peak, peak_note = hbm_peak()
+    legs = {}
+    for name, prec in (("fp32_bf16top", H.HIF_FP32_BF16TOP), ("fp32", H.HIF_FP32)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = H.hif_setup(3, w.n, w.leaf, a, w.dt,
+                        H.default_options(eps=w.eps, precision=prec, cg_tol=1e-10))
+        torch.cuda.synchronize()
+        t_setup = time.perf_counter() - t0
+        info = H.hif_query(h)
+        u = torch.from_numpy(w.u0.ravel().copy()).to(dev)
+        H.cn_steps(h, u, 2)  # warm-up: graph capture, step-record buffer
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        its = H.cn_steps(h, u, args.heat3d_steps - 1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        k_steps = args.heat3d_steps - 1
+        # last step, checked: g = 2 u^k - A u^k, residual of A u^{k+1} = g
+        uk = u.clone()
+        u1, it_last = H.cn_step(h, uk)
+        g = 2.0 * uk - H.hif_matvec(h, uk)
+        res = float((H.hif_matvec(h, u1) - g).norm() / g.norm())
+        # instrumented pass: per-kernel device time of a few steps
+        H.hif_stats_enable(h, True)
+        H.cn_steps(h, u1.clone(), 3)
+        stats = H.hif_stats_read(h)
+        H.hif_stats_enable(h, False)
+        h.close()
+        legs[name] = {"steps": k_steps, "steps_per_s": round(k_steps / t, 3),
+                      "ms_per_step": round(1e3 * t / k_steps, 3),
+                      "iters_per_step": round(sum(its) / k_steps, 3),
+                      "ms_per_cg_iteration": round(1e3 * t / max(1, sum(its)), 4),
+                      "last_step_cn_residual": res, "last_step_iters": it_last,
+                      "setup_s": round(t_setup, 2), "apply_bytes": info["apply_bytes"],
+                      "root": info["root_size"], "device_bytes": info["device_bytes"],
+                      "roofline": roofline_of(stats, peak, peak_note)}
     return {"workload": "heat3d_127: 3D heat, 127^3 interior (N=2048383), lognormal a contrast 1e3, "
-                        "dt=0.1, leaf 8 (L=4), eps=1e-4, face+edge skeletonization, FP32 factor, FP64 CG, "
+                        "dt=0.1, leaf 8 (L=4), eps=1e-4, face+edge skeletonization, FP64 CG, "
                         "PCG rel-res 1e-10",
-            "steps": args.heat3d_steps, "steps_per_s": round(args.heat3d_steps / t, 3),
-            "ms_per_step": round(1e3 * t / args.heat3d_steps, 3),
-            "iters_per_step": round(its / args.heat3d_steps, 3), "setup_s": round(t_setup, 2),
-            "apply_bytes_fp32": info["apply_bytes"], "root": info["root_size"],
-            "device_bytes": info["device_bytes"]}
+            "steps": args.heat3d_steps,
+            "api": "cn_steps (steps queued in one call) after a 2-step warm-up; the last step by "
+                   "cn_step with its residual checked",
+            **legs}
 
 
 def run_batched(args, dev, H, W, np, torch) -> dict:
@@ -686,20 +771,27 @@ def run_batched(args, dev, H, W, np, torch) -> dict:
 # ----------------------------------------------------------------- reference arm
 
 def run_reference(args) -> dict:
-    """The oracle, as it stands, on the host cores (bounded sample per step)."""
-    n = 256 if args.steps <= 200 else 128
-    r = run_oracle_subprocess(n, args.steps, args.warmup, args.eps)
-    v = r["steps_per_s_scaled"]
+    """The oracle, as it stands, on the host cores: K timed CN steps of the
+    workload itself (1023^2, one thread, setup untimed) when K <= 30, else of
+    the same recipe at 255^2 with steps/s scaled by N (so the run stays within
+    minutes).  Warm-up capped at one step (the oracle has no caches to warm)."""
+    full = args.steps <= 30 and args.ref_sample_n in (0, 1024)
+    n = 1024 if full else (args.ref_sample_n or 256)
+    r = run_oracle_subprocess(n, args.steps, min(args.warmup, 1), args.eps)
+    v = r["steps_per_s_sample"] if full else r["steps_per_s_scaled"]
+    sample = (f"each step = one oracle CN step of the workload itself (1023^2, N={r['N_sample']}, "
+              f"no scaling), one thread, setup untimed ({r['t_f']:.1f} s), "
+              f"{r['iters_per_step']:.2f} PCG it/step" if full else
+              f"each step = one oracle CN step of the same recipe at {n - 1}^2 "
+              f"(N={r['N_sample']}); steps/s scaled by N to 1023^2; measured "
+              f"{r['steps_per_s_sample']:.3f} steps/s on the sample, {r['iters_per_step']:.2f} PCG it/step")
     return {"impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": "steps/s",
             "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "ms_per_step": round(1e3 / v, 3),
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD},
+            "config": {"workload": WORKLOAD if full else f"same recipe at {n - 1}^2 (scaled by N)"},
             "cpu_baseline": {"value": round(v, 6), "unit": "steps/s", "cores": 1, "kind": "oracle",
-                             "sample": (f"each step = one oracle CN step of the same recipe at "
-                                        f"{n - 1}^2 (N={r['N_sample']}); steps/s scaled by N to "
-                                        f"1023^2; measured {r['steps_per_s_sample']:.3f} steps/s on "
-                                        f"the sample, {r['iters_per_step']:.2f} PCG it/step"),
-                             "cpu": cpu_model()},
+                             "sample": sample, "cpu": cpu_model()},
             "e2e": {"value": round(v, 6), "unit": "steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
@@ -707,7 +799,8 @@ def run_reference(args) -> dict:
 def main():
     args = _args()
     if args.cpu_sample:
-        r = oracle_sample(args.cpu_sample, args.cpu_sample_steps, args.warmup, args.eps)
+        r = oracle_sample(args.cpu_sample, args.cpu_sample_steps, args.warmup, args.eps,
+                          args.cpu_sample_procs)
         print(json.dumps(r))
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -659,6 +659,8 @@ __global__ void k_step_record(const double *__restrict__ sc, double *__restrict_
 // per-step iteration counts and status are recorded on the device and read
 // once at the end.  Configurations without the captured solve (statistics
 // on, direct solver) take the steps one by one.
+constexpr int kMinStepRecords = 4096;  // 128 KB of step records
+
 int cn_multi(Handle *h, double *u, const double *r, int nsteps, int *iters, cudaStream_t s) {
   if (nsteps <= 0) return HIF_OK;
   if (!h->use_graph || h->stats_on || h->opt.solver == 1) {
@@ -677,8 +679,11 @@ int cn_multi(Handle *h, double *u, const double *r, int nsteps, int *iters, cuda
       h->step_rec = nullptr;
       h->step_rec_cap = 0;
     }
-    HIF_CUDA_TRY(cudaMalloc((void **)&h->step_rec, (size_t)nsteps * 4 * sizeof(double)));
-    h->step_rec_cap = nsteps;
+    // at least kMinStepRecords records, so that a short warm-up call already
+    // sizes the buffer for the longer calls that follow (no cudaMalloc there)
+    const int cap = std::max(nsteps, kMinStepRecords);
+    HIF_CUDA_TRY(cudaMalloc((void **)&h->step_rec, (size_t)cap * 4 * sizeof(double)));
+    h->step_rec_cap = cap;
   }
   const bool f32 = reduced_apply(h);
   const bool warm = h->opt.x0_mode == 1;

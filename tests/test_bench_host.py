@@ -23,9 +23,10 @@ def bench():
 
 
 def test_reference_arm_line(bench):
+    # a 127^2 sample keeps this CPU test short (the default is the 1023^2 workload itself)
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                          "--steps", "1", "--warmup", "0"], capture_output=True, text=True,
-                         timeout=600, cwd=ROOT)
+                          "--steps", "1", "--warmup", "0", "--ref-sample-n", "128"],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [l for l in out.stdout.splitlines() if l.strip()]
     assert len(lines) == 1
@@ -35,6 +36,15 @@ def test_reference_arm_line(bench):
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "steps/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+
+
+def test_oracle_sample_all_cores(bench):
+    """The all-cores leg forks workers after the setup and reports their
+    aggregate rate (small sample: 127^2, one step each, two workers)."""
+    r = bench.run_oracle_subprocess(128, 1, 0, 1e-6, procs=2)
+    assert r["steps"] == 1 and r["steps_per_s_sample"] > 0 and r["iters_per_step"] >= 1
+    ac = r["all_cores"]
+    assert ac["procs"] == 2 and ac["steps_per_s_sample"] > 0 and ac["iters_per_step"] >= 1
 
 
 def test_traffic_follows_leaf_source(bench, tmp_path, monkeypatch):
