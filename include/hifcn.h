@@ -314,6 +314,22 @@ typedef struct {
 int hif_stats_enable(hif_handle *h, int on);
 int hif_stats_read(hif_handle *h, hif_kernel_stat *out, int cap, int *count);
 
+/* ---------------------------------------------------------------------------
+ * hif_inject_flow_stall - failure injection for testing failure detection (no
+ * counterpart in the paper).  Applies only to a handle whose upper levels run
+ * as the dependency-driven sweep (set up with the environment variable
+ * HIFCN_FLOW=1): from the next apply on, work unit `unit` of that sweep runs
+ * but never publishes its completion flag, so every unit that depends on it
+ * waits until its bounded wait of `polls` polls (0: the library's default
+ * limit) expires.  The kernel then records the expiry and ends; the next
+ * pcg_solve / cn_step / cn_steps returns HIF_ETIMEOUT (their results are not
+ * valid) and clears the record.  unit = -1 ends the injection; the handle is
+ * then usable as before.  The GPU is never faulted: the failure is a flag that
+ * nothing sets, the bounded wait turns it into a status.
+ * Errors: HIF_EINVAL (NULL handle, no dependency-driven sweep, unit outside
+ * [-1, units), polls < 0). */
+int hif_inject_flow_stall(hif_handle *h, int unit, long long polls);
+
 /* hif_launch_count - kernels launched by this library in this process so far. */
 int64_t hif_launch_count(void);
 

@@ -833,6 +833,19 @@ int hif_refactor(hif_handle *h, const double *a_nodes, hif_stream stream) {
   return HIF_OK;
 }
 
+int hif_inject_flow_stall(hif_handle *h, int unit, long long polls) {
+  if (!h) return invalid("hif_inject_flow_stall: h is NULL");
+  if (!h->use_flow) return invalid("hif_inject_flow_stall: the handle has no dependency-driven sweep");
+  if (unit < -1 || unit >= h->flow_units)
+    return invalid("hif_inject_flow_stall: unit out of range");
+  if (polls < 0) return invalid("hif_inject_flow_stall: polls < 0");
+  HIF_CUDA_TRY(cudaDeviceSynchronize());  // no solve of this handle is in flight
+  h->flow_withhold = unit;
+  h->flow_wait_limit = polls;
+  destroy_pcg_graphs(h);  // captured solves hold the sweep's launch parameters
+  return HIF_OK;
+}
+
 int hif_query(const hif_handle *hh, hif_info *info) {
   if (!hh || !info) return HIF_EINVAL;
   const Handle *h = hh;

@@ -786,6 +786,17 @@ struct CellMeta {
 // descriptor and chunk bounds come from the gather warp (ready barrier); each
 // chunk's row range goes to meta[stage] before the copy is armed.  The stage
 // ring runs on across cells.
+//
+// Every exit of the copy warp, the normal one and those after an expired
+// wait, first drains the ring: it waits (bounded) for the full barrier of
+// each of the last NS chunks it armed, so no bulk copy still targets the
+// CTA's shared memory when the CTA exits (the consumers may have returned
+// early on a timeout of their own; the CTA ends only when this warp does).
+template <int NS>
+__device__ __forceinline__ void drain_ring(int k, unsigned long long *full) {
+  for (int kk = k > NS ? k - NS : 0; kk < k; ++kk) mbar_wait(&full[kk % NS], (unsigned)((kk / NS) & 1));
+}
+
 template <typename T, int NS>
 __device__ __forceinline__ void produce_cells(int ncells, const T *__restrict__ vals, bool tri,
                                               unsigned char *stage, int2 *meta, const CellMeta *cm,
@@ -797,6 +808,7 @@ __device__ __forceinline__ void produce_cells(int ncells, const T *__restrict__ 
     const int bb = jc & 1;
     if (!mbar_wait(&ready[bb], (unsigned)((jc >> 1) & 1))) {
       err[0] = 1.0;
+      drain_ring<NS>(k, full);
       return;
     }
     const CellDesc c = cm[bb].c;
@@ -810,6 +822,7 @@ __device__ __forceinline__ void produce_cells(int ncells, const T *__restrict__ 
       const int sidx = (int)(k % NS);
       if (k >= NS && !mbar_wait(&empty[sidx], (unsigned)(((k / NS) - 1) & 1))) {
         err[0] = 1.0;
+        drain_ring<NS>(k, full);
         return;
       }
       meta[sidx] = make_int2(rb, re);
@@ -818,6 +831,7 @@ __device__ __forceinline__ void produce_cells(int ncells, const T *__restrict__ 
                 &full[sidx]);
     }
   }
+  drain_ring<NS>(k, full);
 }
 
 // Gather warp: for each cell of the CTA, into buffer b = (cell count) & 1:
@@ -1589,7 +1603,7 @@ __global__ void __launch_bounds__(kFlowThreads) k_flow_sweep(
     const int *__restrict__ idx, const long long *__restrict__ cptr, const long long *__restrict__ cslot,
     const T *__restrict__ vals, const __nv_bfloat16 *__restrict__ vals16, T *contrib, T *contrib_flow,
     T *xI, T *x, int nr, const int *__restrict__ ridx, long long root_G_off, T *rt, double *err,
-    FlowPrefetch pf) {
+    FlowPrefetch pf, int withhold, long long wait_limit) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *sm = reinterpret_cast<T *>(smem_raw);
   __shared__ int s_u, s_epoch;
@@ -1620,7 +1634,7 @@ __global__ void __launch_bounds__(kFlowThreads) k_flow_sweep(
       for (int d = dep_ptr[u] + lane; d < dep_ptr[u + 1]; d += 32) {
         const int *f = flags + dep_idx[d];
         for (long long it = 0; ld_acquire_gpu(f) != epoch; ++it) {
-          if (it >= kFlowWaitLimit) {
+          if (it >= wait_limit) {
             err[0] = 1.0;
             atomicExch(ctl + 3, epoch);
             break;
@@ -1648,7 +1662,7 @@ __global__ void __launch_bounds__(kFlowThreads) k_flow_sweep(
       flow_run_unit<T, T>(P.type, L, uu, idx, cptr, cslot, vals, cb, xI, x, nr, ridx, vals + root_G_off, rt,
                           sm);
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && u != withhold) {  // withhold >= 0 only under failure injection
       __threadfence();
       st_release_gpu(flags + u, epoch);
     }
@@ -2631,7 +2645,8 @@ int launch_flow(Handle *h, const FactorValues<T> &fv, T *x, cudaStream_t s) {
       h->flow_phases, h->flow_nphase, h->flow_units, h->flow_levels, h->flow_dep_ptr, h->flow_dep_idx,
       h->flow_flags, h->flow_ctl, h->idx, h->cptr, h->cslot, fv.vals, v16, fv.contrib,
       static_cast<T *>(h->flow_contrib[pi]), fv.xI, x, h->root_n, h->idx + h->root_idx_off, h->root_G_off,
-      reinterpret_cast<T *>(h->upper_rt), h->scal + kScalErr, h->flow_pf);
+      reinterpret_cast<T *>(h->upper_rt), h->scal + kScalErr, h->flow_pf, h->flow_withhold,
+      h->flow_wait_limit > 0 ? h->flow_wait_limit : kFlowWaitLimit);
   note_launch();
   HIF_CUDA_TRY(cudaGetLastError());
   return HIF_OK;

@@ -285,6 +285,11 @@ struct hif_handle {
   size_t flow_smem[2] = {0, 0};
   double flow_bytes[2] = {0, 0};
   hifcn::FlowPrefetch flow_pf{};                     // L2 prefetch ranges (empty: none)
+  // failure injection (hif_inject_flow_stall): the unit whose completion flag
+  // is never published (-1: none) and the dependency wait limit in polls (0:
+  // the default)
+  int flow_withhold = -1;
+  long long flow_wait_limit = 0;
   size_t upper_smem[2] = {0, 0};              // dynamic shared memory, FP64 / FP32
   int upper_grid[2] = {0, 0};                 // CTAs of the cluster, FP64 / FP32
   double upper_bytes[2] = {0, 0};             // algorithmic bytes per launch, FP64 / FP32

@@ -28,7 +28,7 @@ EXPORTED = ("hif_default_options", "hif_setup", "hif_import_factor", "hif_export
             "hif_apply", "hif_matvec", "pcg_solve", "cn_step", "hif_set_reaction", "hif_query",
             "hif_destroy", "hif_strerror", "hif_last_error", "hif_stats_enable", "hif_stats_read",
             "hif_launch_count", "hif_apply_noalloc", "cn_step_batched", "hif_set_coefficient",
-            "hif_refactor", "hif_autotune", "cn_steps")
+            "hif_refactor", "hif_autotune", "cn_steps", "hif_inject_flow_stall")
 
 
 class HifGrid(ctypes.Structure):
@@ -104,6 +104,8 @@ def lib():
     L.hif_refactor.restype = c_int
     L.hif_autotune.argtypes = [c_void_p, c_void_p]
     L.hif_autotune.restype = c_int
+    L.hif_inject_flow_stall.argtypes = [c_void_p, c_int, ctypes.c_longlong]
+    L.hif_inject_flow_stall.restype = c_int
     for name in ("hif_setup", "hif_import_factor", "hif_export_factor", "hif_apply", "hif_matvec",
                  "pcg_solve", "cn_step", "cn_steps", "hif_set_reaction", "hif_query", "hif_destroy",
                  "hif_stats_enable", "hif_stats_read"):
@@ -319,6 +321,13 @@ def hif_refactor(h: Handle, a_nodes: torch.Tensor, stream=None):
 def hif_autotune(h: Handle, stream=None):
     """Pick the per-level CTA cut of the apply and the leaf kernels' CTAs per SM by timing."""
     _check("hif_autotune", lib().hif_autotune(h.ptr, _stream(stream)))
+
+
+def hif_inject_flow_stall(h: Handle, unit: int, polls: int = 0):
+    """Failure injection (tests): unit `unit` of the dependency-driven sweep never
+    publishes its flag, so its dependents' waits expire after `polls` polls and
+    the next solve returns HIF_ETIMEOUT; unit = -1 ends the injection."""
+    _check("hif_inject_flow_stall", lib().hif_inject_flow_stall(h.ptr, int(unit), int(polls)))
 
 
 def hif_set_reaction(h: Handle, kind: int, k1: float = 1.0, k2: float = math.inf):

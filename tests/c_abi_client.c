@@ -97,6 +97,7 @@ int main(void) {
   CHECK(hif_apply(NULL, &x, &y, HIF_FP64, NULL) == HIF_EINVAL);
   CHECK(hif_apply_noalloc(NULL, &x, &y, NULL) == HIF_EINVAL);
   CHECK(strstr(hif_last_error(), "h is NULL") != NULL);
+  CHECK(hif_inject_flow_stall(NULL, 0, 16) == HIF_EINVAL);
   CHECK(hif_matvec(NULL, &x, &y, NULL) == HIF_EINVAL);
   CHECK(pcg_solve(NULL, &x, &y, &it, &x, NULL) == HIF_EINVAL);
   CHECK(cn_step(NULL, &x, NULL, &y, &it, NULL) == HIF_EINVAL);
