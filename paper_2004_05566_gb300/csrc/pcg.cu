@@ -40,12 +40,17 @@ struct StencilArgs {
 // CG kernels; these do the same conversions exactly with integer operations
 // for normal numbers and zero, and leave the rare other cases (subnormal,
 // infinite, NaN, out-of-range results) to the conversion instruction.
+// The rare cases go through out-of-line calls, so that the hot loops carry a
+// branch around them instead of a predicated conversion on the FP64 pipe.
+__device__ __noinline__ double widen_rare(float f) { return (double)f; }
+__device__ __noinline__ float narrow_rare(double d) { return __double2float_rn(d); }
+
 __device__ __forceinline__ double widen(float f) {
   const unsigned u = __float_as_uint(f);
   const unsigned e = (u >> 23) & 0xffu;
   const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
   if ((u & 0x7fffffffu) == 0u) return __longlong_as_double((long long)sign);  // +-0
-  if (e == 0u || e == 0xffu) return (double)f;
+  if (e == 0u || e == 0xffu) return widen_rare(f);
   const unsigned long long b = sign | ((unsigned long long)(e + 896u) << 52) |
                                ((unsigned long long)(u & 0x7fffffu) << 29);
   return __longlong_as_double((long long)b);
@@ -56,7 +61,8 @@ __device__ __forceinline__ double widen(double d) { return d; }
 __device__ __forceinline__ float narrow_rn(double d) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(d);
   const int ef = (int)((b >> 52) & 0x7ffu) - 896;  // biased FP32 exponent
-  if (ef <= 0 || ef >= 255) return __double2float_rn(d);
+  if ((b << 1) == 0ull) return __uint_as_float((unsigned)(b >> 32));  // +-0
+  if (ef <= 0 || ef >= 255) return narrow_rare(d);
   const unsigned mf = (unsigned)((b >> 29) & 0x7fffffu);
   const unsigned rem = (unsigned)(b & 0x1fffffffu);  // the 29 bits dropped
   unsigned out = ((unsigned)(b >> 32) & 0x80000000u) | ((unsigned)ef << 23) | mf;
@@ -187,23 +193,80 @@ __device__ __forceinline__ double warp_sum_partials_cg(const double *partials, i
   return v;
 }
 
-// A z for one row j of the stencil, z of the preconditioner's type (FP32 or
-// FP64) promoted to FP64; 32-bit index arithmetic (N < 2^31).
-template <typename TZ>
-__device__ __forceinline__ double stencil_row_z(const TZ *z, double zj, const StencilArgs &st, int j) {
-  const int S = st.n - 1;
-  const int q = j / S, i1 = j - q * S, i2 = q % S;
-  double y = st.diag[j] * zj;
-  if (i1 < S - 1) y -= st.wx[j] * widen(z[j + 1]);
-  if (i1 > 0) y -= st.wx[j - 1] * widen(z[j - 1]);
-  if (i2 < S - 1) y -= st.wy[j] * widen(z[j + S]);
-  if (i2 > 0) y -= st.wy[j - S] * widen(z[j - S]);
-  if (st.dim == 3) {
-    const int S2 = S * S, i3 = q / S;
-    if (i3 < S - 1) y -= st.wz[j] * widen(z[j + S2]);
-    if (i3 > 0) y -= st.wz[j - S2] * widen(z[j - S2]);
+// Position (i1, i2, i3) of DOF j = i1 + S (i2 + S i3) on the grid of S = n - 1
+// points per axis, advanced by the grid stride without divisions (a 32-bit
+// division by a runtime value costs a conversion sequence per element).
+struct GridWalk {
+  int i1, i2, i3, d1, d2, d3;
+  __device__ __forceinline__ GridWalk(int j, int stride, int S, bool d3d) {
+    const int q = j / S, qs = stride / S;
+    i1 = j - q * S;
+    d1 = stride - qs * S;
+    if (d3d) {
+      i3 = q / S;
+      i2 = q - i3 * S;
+      d3 = qs / S;
+      d2 = qs - d3 * S;
+    } else {
+      i2 = q;
+      i3 = 0;
+      d2 = qs;
+      d3 = 0;
+    }
   }
-  return y;
+  __device__ __forceinline__ void advance(int S, bool d3d) {
+    i1 += d1;
+    int c = i1 >= S ? 1 : 0;
+    i1 -= c * S;
+    i2 += d2 + c;
+    if (d3d) {
+      c = i2 >= S ? 1 : 0;
+      i2 -= c * S;
+      i3 += d3 + c;
+    }
+  }
+};
+
+// Deterministic block reduction of two doubles per thread in one shuffle
+// tree: after the first exchange lanes 0-15 carry a and lanes 16-31 carry b,
+// so each of the five steps is one FP64 add for both sums; the warps' sums
+// then meet in warp 0 (fixed order).  Result in every lane of warp 0.
+template <int NTB>
+__device__ __forceinline__ double2 block_sum2(double a, double b, double *sm) {
+  constexpr int NW = NTB / 32;
+  static_assert(NW >= 1 && NW <= 16 && (NW & (NW - 1)) == 0, "warps per block: a power of two <= 16");
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const bool hi = (lane & 16) != 0;
+  double keep = hi ? b : a;
+  const double send = hi ? a : b;
+  keep += __shfl_xor_sync(0xffffffffu, send, 16);
+  for (int o = 8; o > 0; o >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o);
+  if ((lane & 15) == 0) sm[(lane >> 4) * NW + w] = keep;
+  __syncthreads();
+  double2 t = make_double2(0.0, 0.0);
+  if (w == 0) {
+    const int k = lane & 15;
+    double v = k < NW ? sm[(lane >> 4) * NW + k] : 0.0;
+    for (int o = NW / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    t.x = __shfl_sync(0xffffffffu, v, 0);
+    t.y = __shfl_sync(0xffffffffu, v, 16);
+  }
+  __syncthreads();
+  return t;
+}
+
+// Sums of the per-block partials pa[0..np) and pb[0..np) by the whole
+// (last) block: thread t adds entries t, t + NT, ... in order, then one
+// block_sum2 (fixed order, so the result does not depend on which block
+// finished last).  pa and pb were written by other blocks: read through L2.
+template <int NTB>
+__device__ __forceinline__ double2 sum_partials2(const double *pa, const double *pb, int np, double *sm) {
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < np; i += NTB) {
+    a += __ldcg(pa + i);
+    if (pb) b += __ldcg(pb + i);
+  }
+  return block_sum2<NTB>(a, b, sm);
 }
 
 // PCG in the Chronopoulos-Gear arrangement (the same iterates as the
@@ -216,6 +279,14 @@ __device__ __forceinline__ double stencil_row_z(const TZ *z, double zj, const St
 // z.A p_old = -rho / alpha_old (residuals are F-orthogonal) and
 // p_old.A p_old = rho_old / alpha_old.
 //
+// On GB300 these kernels are bound by the FP64 pipe (about two FP64
+// operations per clock per SM): per unknown, w = A z takes one multiply and
+// four (3D: six) fused multiply-adds, the two dots two more, and the update
+// kernel five.  Everything else stays off that pipe: positions are walked
+// without divisions, the FP32 <-> FP64 conversions are integer bit
+// operations, both dots share one reduction tree, per-block scalars are read
+// once by one thread.
+//
 // first kernel: w = A z, partials of r.z and w.z; the last block forms
 // beta, sigma and alpha
 template <typename TZ>
@@ -223,24 +294,37 @@ __global__ void __launch_bounds__(NT) k_cg_wz(const double *__restrict__ r, cons
                                               double *__restrict__ w, StencilArgs st,
                                               double *__restrict__ part, double *__restrict__ s,
                                               unsigned *__restrict__ ticket) {
-  __shared__ double sm[NT / 32];
+  __shared__ double sm[2 * (NT / 32)];
   double arz = 0.0, awz = 0.0;
-  const int N = (int)st.N;
-  for (int j = blockIdx.x * NT + threadIdx.x; j < N; j += gridDim.x * NT) {
+  const int N = (int)st.N, S = st.n - 1, S2 = S * S;
+  const int stride = gridDim.x * NT;
+  const bool d3 = st.dim == 3;
+  int j = blockIdx.x * NT + threadIdx.x;
+  GridWalk g(j, stride, S, d3);
+  for (; j < N; j += stride, g.advance(S, d3)) {
     const double zj = widen(z[j]);
-    const double wj = stencil_row_z(z, zj, st, j);
-    w[j] = wj;
+    double y = st.diag[j] * zj;
+    if (g.i1 < S - 1) y -= st.wx[j] * widen(z[j + 1]);
+    if (g.i1 > 0) y -= st.wx[j - 1] * widen(z[j - 1]);
+    if (g.i2 < S - 1) y -= st.wy[j] * widen(z[j + S]);
+    if (g.i2 > 0) y -= st.wy[j - S] * widen(z[j - S]);
+    if (d3) {
+      if (g.i3 < S - 1) y -= st.wz[j] * widen(z[j + S2]);
+      if (g.i3 > 0) y -= st.wz[j - S2] * widen(z[j - S2]);
+    }
+    w[j] = y;
     arz += r[j] * zj;
-    awz += wj * zj;
+    awz += y * zj;
   }
-  double t = block_sum<NT>(arz, sm);
-  if (threadIdx.x == 0) part[blockIdx.x] = t;
-  t = block_sum<NT>(awz, sm);
-  if (threadIdx.x == 0) part[gridDim.x + blockIdx.x] = t;
-  if (!last_block(ticket) || threadIdx.x >= 32) return;
-  const double rho = warp_sum_partials_cg(part, gridDim.x);
-  const double mu = warp_sum_partials_cg(part + gridDim.x, gridDim.x);
+  const double2 t = block_sum2<NT>(arz, awz, sm);
   if (threadIdx.x == 0) {
+    part[blockIdx.x] = t.x;
+    part[gridDim.x + blockIdx.x] = t.y;
+  }
+  if (!last_block(ticket)) return;
+  const double2 tot = sum_partials2<NT>(part, part + gridDim.x, gridDim.x, sm);
+  if (threadIdx.x == 0) {
+    const double rho = tot.x, mu = tot.y;
     const bool first = s[S_IT] == 0.0;
     const double beta = first ? 0.0 : rho / s[S_RZ];
     const double sigma = first ? mu : mu - beta * rho / s[S_ALPHA];
@@ -262,7 +346,9 @@ __device__ __forceinline__ void finish_iteration(double *s, double rr, double to
   s[S_IT] = it;
   const bool conv = rr <= tol2 * s[S_BB];
   s[S_CONV] = conv ? 1.0 : 0.0;
-  if constexpr (kGraph) cudaGraphSetConditional(cond, (!conv && it < (double)maxit) ? 1u : 0u);
+  // a bounded wait of this iteration's apply expired: stop (reported as HIF_ETIMEOUT)
+  const bool failed = s[kScalErr] != 0.0;
+  if constexpr (kGraph) cudaGraphSetConditional(cond, (!conv && !failed && it < (double)maxit) ? 1u : 0u);
 }
 
 // second kernel: p = z + beta p, q = w + beta q (p = z, q = w on the first
@@ -278,10 +364,16 @@ __global__ void __launch_bounds__(NT) k_cg_update(double *__restrict__ x, double
                                                   double *__restrict__ part, unsigned *__restrict__ ticket,
                                                   int period, double tol2, int maxit,
                                                   cudaGraphConditionalHandle cond) {
-  __shared__ double sm[NT / 32];
-  const bool first = s[S_IT] == 0.0;
+  __shared__ double sm[2 * (NT / 32)];
+  __shared__ int s_flags;  // bit 0: first iteration, bit 1: the true residual follows
+  if (threadIdx.x == 0) {
+    const int it1 = (int)s[S_IT] + 1;  // iteration that updates x now
+    s_flags = (it1 == 1 ? 1 : 0) | ((period > 0 && it1 % period == 0) ? 2 : 0);
+  }
+  __syncthreads();
+  const int flags = s_flags;
+  const bool first = (flags & 1) != 0;
   const double beta = s[S_BETA], alpha = s[S_ALPHA];
-  const int it1 = (int)s[S_IT] + 1;  // iteration that updates x now
   double acc = 0.0;
   const int n = (int)N;
   for (int j = blockIdx.x * NT + threadIdx.x; j < n; j += gridDim.x * NT) {
@@ -296,14 +388,14 @@ __global__ void __launch_bounds__(NT) k_cg_update(double *__restrict__ x, double
     zin[j] = to_z<TZ>(rj);
     acc += rj * rj;
   }
-  double t = block_sum<NT>(acc, sm);
-  if (threadIdx.x == 0) part[blockIdx.x] = t;
-  if (period > 0 && it1 % period == 0) return;  // the true-residual kernel finishes the iteration
-  if (!last_block(ticket) || threadIdx.x >= 32) return;
-  const double v = warp_sum_partials_cg(part, gridDim.x);
+  const double2 t = block_sum2<NT>(acc, 0.0, sm);
+  if (threadIdx.x == 0) part[blockIdx.x] = t.x;
+  if (flags & 2) return;  // the true-residual kernel finishes the iteration
+  if (!last_block(ticket)) return;
+  const double2 tot = sum_partials2<NT>(part, nullptr, gridDim.x, sm);
   if (threadIdx.x == 0) {
     *ticket = 0u;
-    finish_iteration<kGraph>(s, v, tol2, maxit, cond);
+    finish_iteration<kGraph>(s, tot.x, tol2, maxit, cond);
   }
 }
 
@@ -692,14 +784,17 @@ int cn_multi(Handle *h, double *u, const double *r, int nsteps, int *iters, cuda
   else HIF_TRY(ensure_pcg_graph<double>(h, h->z, slot, s));
   PcgGraph *G = static_cast<PcgGraph *>(h->pcg_graph[slot]);
   const size_t vb = h->N * sizeof(double);
+  // the iterate stays in the solve's own buffer between steps: step k > 0
+  // forms its right-hand side from xsol (= u^k, also the warm start) before
+  // the solve overwrites it, and u receives the last solution once
   for (int k = 0; k < nsteps; ++k) {
-    HIF_TRY(cn_rhs(h, u, r, h->g, s));
-    if (warm) HIF_CUDA_TRY(cudaMemcpyAsync(h->xsol, u, vb, cudaMemcpyDeviceToDevice, s));
+    HIF_TRY(cn_rhs(h, k == 0 ? u : h->xsol, r, h->g, s));
+    if (warm && k == 0) HIF_CUDA_TRY(cudaMemcpyAsync(h->xsol, u, vb, cudaMemcpyDeviceToDevice, s));
     HIF_CUDA_TRY(cudaGraphLaunch(G->exec, s));
-    HIF_CUDA_TRY(cudaMemcpyAsync(u, h->xsol, vb, cudaMemcpyDeviceToDevice, s));
     k_step_record<<<1, 32, 0, s>>>(h->scal, h->step_rec + 4 * (size_t)k);
     note_launch(2);
   }
+  HIF_CUDA_TRY(cudaMemcpyAsync(u, h->xsol, vb, cudaMemcpyDeviceToDevice, s));
   HIF_CUDA_TRY(cudaGetLastError());
   std::vector<double> rec((size_t)nsteps * 4);
   HIF_CUDA_TRY(cudaMemcpyAsync(rec.data(), h->step_rec, rec.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
