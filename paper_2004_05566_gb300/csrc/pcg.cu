@@ -297,11 +297,11 @@ __global__ void __launch_bounds__(NT) k_cg_wz(const double *__restrict__ r, cons
   __shared__ double sm[2 * (NT / 32)];
   double arz = 0.0, awz = 0.0;
   const int N = (int)st.N, S = st.n - 1, S2 = S * S;
-  const int stride = gridDim.x * NT;
+  const int stride = gridDim.x * NT, stride2 = 2 * stride;
   const bool d3 = st.dim == 3;
-  int j = blockIdx.x * NT + threadIdx.x;
-  GridWalk g(j, stride, S, d3);
-  for (; j < N; j += stride, g.advance(S, d3)) {
+  // two rows per pass (j and j + stride), written as straight-line code so
+  // that the loads of both are in flight together
+  auto row = [&](int j, const GridWalk &g) -> double {
     const double zj = widen(z[j]);
     double y = st.diag[j] * zj;
     if (g.i1 < S - 1) y -= st.wx[j] * widen(z[j + 1]);
@@ -312,9 +312,26 @@ __global__ void __launch_bounds__(NT) k_cg_wz(const double *__restrict__ r, cons
       if (g.i3 < S - 1) y -= st.wz[j] * widen(z[j + S2]);
       if (g.i3 > 0) y -= st.wz[j - S2] * widen(z[j - S2]);
     }
-    w[j] = y;
-    arz += r[j] * zj;
-    awz += y * zj;
+    return y;
+  };
+  int j = blockIdx.x * NT + threadIdx.x;
+  GridWalk g0(j, stride2, S, d3), g1(j + stride, stride2, S, d3);
+  for (; j < N; j += stride2, g0.advance(S, d3), g1.advance(S, d3)) {
+    const int j1 = j + stride;
+    const double z0 = widen(z[j]), r0 = r[j];
+    const double y0 = row(j, g0);
+    double z1 = 0.0, r1 = 0.0, y1 = 0.0;
+    if (j1 < N) {
+      z1 = widen(z[j1]);
+      r1 = r[j1];
+      y1 = row(j1, g1);
+    }
+    w[j] = y0;
+    if (j1 < N) w[j1] = y1;
+    arz += r0 * z0;
+    awz += y0 * z0;
+    arz += r1 * z1;
+    awz += y1 * z1;
   }
   const double2 t = block_sum2<NT>(arz, awz, sm);
   if (threadIdx.x == 0) {
@@ -376,17 +393,42 @@ __global__ void __launch_bounds__(NT) k_cg_update(double *__restrict__ x, double
   const double beta = s[S_BETA], alpha = s[S_ALPHA];
   double acc = 0.0;
   const int n = (int)N;
-  for (int j = blockIdx.x * NT + threadIdx.x; j < n; j += gridDim.x * NT) {
-    const double zj = widen(zin[j]);
-    const double pj = first ? zj : zj + beta * p[j];
-    const double qj = first ? w[j] : w[j] + beta * q[j];
-    p[j] = pj;
-    q[j] = qj;
-    x[j] += alpha * pj;
-    const double rj = r[j] - alpha * qj;
-    r[j] = rj;
-    zin[j] = to_z<TZ>(rj);
-    acc += rj * rj;
+  const int stride = gridDim.x * NT;
+  // two elements per pass (j and j + stride): all loads first, then the updates
+  for (int j = blockIdx.x * NT + threadIdx.x; j < n; j += 2 * stride) {
+    const int j1 = j + stride;
+    const bool h1 = j1 < n;
+    const double z0 = widen(zin[j]), w0 = w[j], r0 = r[j], x0 = x[j];
+    const double p0 = first ? 0.0 : p[j], q0 = first ? 0.0 : q[j];
+    double z1 = 0.0, w1 = 0.0, r1 = 0.0, x1 = 0.0, p1 = 0.0, q1 = 0.0;
+    if (h1) {
+      z1 = widen(zin[j1]);
+      w1 = w[j1];
+      r1 = r[j1];
+      x1 = x[j1];
+      if (!first) {
+        p1 = p[j1];
+        q1 = q[j1];
+      }
+    }
+    const double pj0 = first ? z0 : z0 + beta * p0, qj0 = first ? w0 : w0 + beta * q0;
+    const double rj0 = r0 - alpha * qj0;
+    p[j] = pj0;
+    q[j] = qj0;
+    x[j] = x0 + alpha * pj0;
+    r[j] = rj0;
+    zin[j] = to_z<TZ>(rj0);
+    acc += rj0 * rj0;
+    if (h1) {
+      const double pj1 = first ? z1 : z1 + beta * p1, qj1 = first ? w1 : w1 + beta * q1;
+      const double rj1 = r1 - alpha * qj1;
+      p[j1] = pj1;
+      q[j1] = qj1;
+      x[j1] = x1 + alpha * pj1;
+      r[j1] = rj1;
+      zin[j1] = to_z<TZ>(rj1);
+      acc += rj1 * rj1;
+    }
   }
   const double2 t = block_sum2<NT>(acc, 0.0, sm);
   if (threadIdx.x == 0) part[blockIdx.x] = t.x;
