@@ -67,6 +67,8 @@ def _args():
     p.add_argument("--batched-steps", type=int, default=20)
     p.add_argument("--heat3d-steps", type=int, default=50,
                    help="CN steps of the 3D heat 127^3 measurement reported beside the headline (0: skip)")
+    p.add_argument("--multi-k", type=int, default=16,
+                   help="states of the benchmark operator stepped together by cn_step_multi (0: skip)")
     p.add_argument("--serving-ops", type=int, default=16,
                    help="resident operators of the serving measurement (0: skip)")
     p.add_argument("--cpu-sample", type=int, default=0, help=argparse.SUPPRESS)
@@ -449,6 +451,15 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
     info64 = H.hif_query(h64)
     h64.close()
 
+    # ---- k states of the benchmark operator at once (BF16 top levels on the tensor cores)
+    multi2d = None
+    if args.multi_k > 0:
+        hb, _ = make(H.HIF_FP32_BF16TOP)
+        u_m = torch.from_numpy(w.u0.ravel().copy()).to(dev)
+        H.cn_steps(hb, u_m, args.warmup)
+        multi2d = multi_vs_single(H, torch, hb, u_m, args.multi_k, reps=2)
+        hb.close()
+
     # ---- batched workload: many independent operators, overlapped vs one at a time
     batched = None
     if args.batched_count > 0:
@@ -564,6 +575,7 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
         "apply_share_of_step": round(apply_ms / t_ms_stats, 3) if t_ms_stats else None,
         "clocks": clk,
         "cpu_baseline": cpu,
+        "multi_rhs_2d": multi2d,
         "batched": batched,
         "heat3d": heat3d,
         "serving": serving,
@@ -647,6 +659,46 @@ def hbm_peak() -> tuple:
     return (peak, "measured") if peak else (FALLBACK_HBM_GBS, "fallback")
 
 
+def multi_vs_single(H, torch, h, u, k: int, reps: int = 2) -> dict:
+    """k states of one operator stepped together (cn_step_multi: one
+    multi-column apply per PCG iteration, BF16 top levels on the tensor cores)
+    against the same k steps taken one cn_step at a time on the same handle.
+    States: u scaled by 1 + 0.05 c, c < k; CUDA events around the calls."""
+    stream = torch.cuda.current_stream()
+    U = torch.stack([u * (1.0 + 0.05 * c) for c in range(k)]).contiguous()
+    V = torch.empty_like(U)
+    H.cn_step_multi(h, U, out=V)  # warm-up: work space, graphs of the single path
+    H.cn_step(h, U[0].contiguous())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    its_m = []
+    for _ in range(reps):
+        _, it = H.cn_step_multi(h, U, out=V)
+        its_m += it
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_m = e0.elapsed_time(e1) / 1e3
+    rows = [U[c].contiguous() for c in range(k)]
+    out = torch.empty_like(rows[0])
+    its_s = []
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        for c in range(k):
+            _, it = H.cn_step(h, rows[c], out=out)
+            its_s.append(it)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_s = e0.elapsed_time(e1) / 1e3
+    n = reps * k
+    return {"k": k, "steps": n, "multi_steps_per_s": round(n / t_m, 3),
+            "single_steps_per_s": round(n / t_s, 3), "speedup": round(t_s / t_m, 3),
+            "multi_iters_per_step": round(sum(its_m) / n, 3),
+            "single_iters_per_step": round(sum(its_s) / n, 3),
+            "api": "cn_step_multi (k states, one hif_apply_multi per PCG iteration) vs k cn_step calls"}
+
+
 def run_heat3d(args, dev, H, W, np, torch) -> dict:
     """3D heat equation on 127^3 (leaf 8, L = 4, eps 1e-4, dt 0.1, lognormal a with
     contrast 1e3, smooth random u0, face + edge skeletonization, FP64 CG): GPU
@@ -684,6 +736,7 @@ def run_heat3d(args, dev, H, W, np, torch) -> dict:
         u1, it_last = H.cn_step(h, uk)
         g = 2.0 * uk - H.hif_matvec(h, uk)
         res = float((H.hif_matvec(h, u1) - g).norm() / g.norm())
+        multi = multi_vs_single(H, torch, h, u1, 16, reps=1) if prec == H.HIF_FP32_BF16TOP else None
         # instrumented pass: per-kernel device time of a few steps
         H.hif_stats_enable(h, True)
         H.cn_steps(h, u1.clone(), 3)
@@ -698,6 +751,8 @@ def run_heat3d(args, dev, H, W, np, torch) -> dict:
                       "setup_s": round(t_setup, 2), "apply_bytes": info["apply_bytes"],
                       "root": info["root_size"], "device_bytes": info["device_bytes"],
                       "roofline": roofline_of(stats, peak, peak_note)}
+        if multi:
+            legs[name]["multi_rhs"] = multi
     return {"workload": "heat3d_127: 3D heat, 127^3 interior (N=2048383), lognormal a contrast 1e3, "
                         "dt=0.1, leaf 8 (L=4), eps=1e-4, face+edge skeletonization, FP64 CG, "
                         "PCG rel-res 1e-10",

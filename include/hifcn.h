@@ -180,6 +180,36 @@ int hif_apply(hif_handle *h, const double *x, double *y, int precision, hif_stre
 #define HIF_NOALLOC_MAX_SLOTS (1 << 19)
 int hif_apply_noalloc(hif_handle *h, const double *x, double *y, hif_stream stream);
 
+/* ---------------------------------------------------------------------------
+ * hif_apply_multi - Y = F^{-1} X for k right-hand sides at once (Eq. Ainv),
+ * for handles set up with HIF_FP32_BF16TOP.  X, Y: device, k columns of N
+ * doubles each, column after column (column c at X + c N); may not alias.
+ * 1 <= k <= HIF_MULTI_MAX_COLS.  The levels below the BF16 levels are applied
+ * column by column in FP32 as in hif_apply; the BF16 levels and the root
+ * (Eqs. 2_3, 3_3, 3_4 as stored products G, V, H, G_r) are applied to all k
+ * columns at once as tensor-core products (BF16 factor blocks, each FP32
+ * column split into a high and a low BF16 part, FP32 accumulation), so each
+ * top-level block is read once for the k columns.  The first call for a
+ * handle (and a call with more columns than before) allocates the handle's
+ * multi-column work space.  Errors: HIF_EINVAL (NULL or aliased pointers, no
+ * factor, not a BF16TOP handle, k out of range), HIF_ENOMEM, HIF_ECUDA. */
+#define HIF_MULTI_MAX_COLS 64
+int hif_apply_multi(hif_handle *h, const double *X, double *Y, int k, hif_stream stream);
+
+/* cn_step_multi - one CN step (Eq. CN2, Algorithm 1) for each of k states of
+ * the same operator: U1_c = A^{-1} g(U_c), c < k, for a handle set up with
+ * HIF_FP32_BF16TOP.  U, U1: device, k columns of N doubles (column c at
+ * U + c N); U1 may equal U.  R: device, k columns (the explicit reaction of
+ * each state), or NULL for the handle's built-in reaction.  The k PCG
+ * recurrences (FP64, x0 = 0, the handle's tolerance) run in lockstep, each
+ * with its own scalars, and share one hif_apply_multi per iteration; a
+ * converged column stops updating.  iters: host, k ints, or NULL.  Needs
+ * x0_mode 0 and solver 0.  Synchronizes the stream.  Errors: as
+ * hif_apply_multi, plus HIF_ENOCONV (some column reached cg_maxit; U1 holds
+ * the last iterates) and HIF_ETIMEOUT. */
+int cn_step_multi(hif_handle *h, const double *U, const double *R, double *U1, int k, int *iters,
+                  hif_stream stream);
+
 /* hif_matvec - y = A x with A = I - dt/2 M (Eq. CN).  x, y device, may not alias. */
 int hif_matvec(hif_handle *h, const double *x, double *y, hif_stream stream);
 

@@ -85,8 +85,10 @@ int alloc_work(Handle *h) {
   // blocks of the CG vector kernels: 4 per SM (measured at 1023^2: 839 us per step
   // against 866 us with 8 per SM and 849 us with 2; fewer blocks mean shorter FP64
   // reduction trees, too few leave memory latency uncovered)
+  int bps = 4;
+  if (const char *e = std::getenv("HIFCN_VEC_BPS")) bps = std::max(1, std::min(16, std::atoi(e)));
   long long nb = (N + 255) / 256;
-  if (nb > 152 * 4) nb = 152 * 4;
+  if (nb > 152LL * bps) nb = 152LL * bps;
   if (nb < 1) nb = 1;
   h->nblocks_vec = (int)nb;
   HIF_TRY(dev_alloc(h, (void **)&h->r, N * sizeof(double)));
@@ -443,6 +445,7 @@ int create_handle(const hif_grid *grid, const double *a_nodes, double dt, const 
 // stencil stay).
 void release_factor(Handle *h) {
   destroy_pcg_graphs(h);
+  destroy_multi_state(h);  // its buffers are among the allocations freed below
   for (size_t i = h->factor_alloc_begin; i < h->allocations.size(); ++i) cudaFree(h->allocations[i]);
   h->allocations.resize(h->factor_alloc_begin);
   h->device_bytes = h->work_device_bytes;
@@ -610,6 +613,7 @@ using namespace hifcn;
 hif_handle::~hif_handle() {
   cudaDeviceSynchronize();
   hifcn::destroy_pcg_graphs(this);
+  hifcn::destroy_multi_state(this);
   for (auto &r : stat_pending) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -757,6 +761,22 @@ int hif_export_factor(const hif_handle *hh, void *buf, size_t *bytes) {
   std::memcpy(buf, out.data(), out.size());
   *bytes = out.size();
   return HIF_OK;
+}
+
+int hif_apply_multi(hif_handle *h, const double *X, double *Y, int k, hif_stream stream) {
+  if (!h) return invalid("hif_apply_multi: h is NULL");
+  if (!X || !Y) return invalid("hif_apply_multi: X or Y is NULL");
+  if (X == Y) return invalid("hif_apply_multi: X and Y alias");
+  if (!h->factor_ok) return invalid("hif_apply_multi: the handle holds no factor");
+  return apply_multi(h, X, Y, k, (cudaStream_t)stream);
+}
+
+int cn_step_multi(hif_handle *h, const double *U, const double *R, double *U1, int k, int *iters,
+                  hif_stream stream) {
+  if (!h) return invalid("cn_step_multi: h is NULL");
+  if (!U || !U1) return invalid("cn_step_multi: U or U1 is NULL");
+  if (!h->factor_ok) return invalid("cn_step_multi: the handle holds no factor");
+  return cn_cols(h, U, R, U1, k, iters, (cudaStream_t)stream);
 }
 
 int hif_apply(hif_handle *h, const double *x, double *y, int precision, hif_stream stream) {

@@ -2222,6 +2222,30 @@ int upper_launch_shape(Handle *h, size_t smem, int max_units) {
 
 }  // namespace
 
+// Levels [l0, l1) of the FP32 apply, forward (cells then entities, upward)
+// or backward (entities then cells, downward), with the given contribution
+// scratch and forward-value vector: one column of the multi-column apply.
+int apply_levels_f32_range(Handle *h, float *contrib, float *xI, float *x, int l0, int l1, bool forward,
+                           cudaStream_t s) {
+  HIF_TRY(set_smem_limits<float>());
+  FactorValues<float> fv = h->f32;
+  fv.contrib = contrib;
+  fv.xI = xI;
+  if (forward) {
+    for (int l = l0; l < l1; ++l) {
+      HIF_TRY(launch_cell_fwd<float>(h, h->lv[l], l, fv, x, s));
+      HIF_TRY(launch_group_fwd<float>(h, h->lv[l], l, fv, x, s));
+    }
+  } else {
+    for (int l = l1 - 1; l >= l0; --l) {
+      HIF_TRY(launch_group_bwd<float>(h, h->lv[l], l, fv, x, s));
+      HIF_TRY(launch_cell_bwd<float>(h, h->lv[l], l, fv, x, s));
+    }
+  }
+  HIF_CUDA_TRY(cudaGetLastError());
+  return HIF_OK;
+}
+
 bool level_uses_sform(const Handle *h, int l) {
   return h->has_f32 && l >= 0 && l < h->L && use_tma(h, h->lv[l], sizeof(float)) && !bf16_level<float>(h, l);
 }

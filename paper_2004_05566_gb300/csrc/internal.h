@@ -269,6 +269,7 @@ struct hif_handle {
   bool root_split = false;                    // root applied by row- and column-block launches
   int tma_ctas = 0;                           // CTAs per SM of the leaf kernels (0: as many as fit)
   hifcn::HandleView *view = nullptr;          // device view for the merged batched steps
+  void *multi = nullptr;                      // multi-column apply state (multi.cu), built on first use
   bool view_ok = false;                       // the merged batched path can take this handle
   // dependency-driven sweep (apply.cu): the cell and group steps of levels
   // >= flow_lb, the root, and the group steps of level flow_lb - 1 run in one
@@ -372,6 +373,23 @@ int cn_batched(Handle *const *hs, int count, const double *const *u, const doubl
 int gpu_setup(Handle *h, const double *a_nodes, cudaStream_t s);
 void destroy_pcg_graphs(Handle *h);
 int alloc_work(Handle *h);
+// right-hand sides of one multi-column apply (hif_apply_multi)
+constexpr int kMultiMaxCols = HIF_MULTI_MAX_COLS;
+int apply_multi(Handle *h, const double *X, double *Y, int k, cudaStream_t s);
+int apply_multi_f32(Handle *h, int k, cudaStream_t s);
+void destroy_multi_state(Handle *h);
+int multi_check(Handle *h, int k, const char *fn);
+// per-column CG state of cn_step_multi (column c of a vector at + c N, of the
+// scalars at + 16 c, of the partials at + 4 nb c, of the tickets at + 4 c);
+// z is the FP32 work of the multi-column apply
+struct MultiCG {
+  double *g, *x, *r, *p, *q, *w, *scal, *part;
+  unsigned *tk;
+  float *z;
+  int nb;
+};
+int multi_cg_buffers(Handle *h, int k, MultiCG *out);
+int cn_cols(Handle *h, const double *U, const double *R, double *U1, int k, int *iters, cudaStream_t s);
 // Loads, with the handle's device current, what hif_apply_noalloc uses (its
 // static scratch and the FP64 apply kernels of the handle), so that its calls
 // allocate nothing under lazy module loading.

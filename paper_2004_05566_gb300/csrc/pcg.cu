@@ -776,6 +776,83 @@ int cn(Handle *h, const double *u, const double *r, double *u1, int *iters, cuda
   return solve_core(h, h->g, u, u1, iters, nullptr, s);
 }
 
+// k CN steps of one operator at once (k states, column c of U at U + c N):
+// k independent PCG recurrences in lockstep, each with its own scalars, that
+// share every application of the preconditioner (one multi-column apply per
+// iteration, the BF16 top levels on the tensor cores).  A column that has
+// converged stops updating; the loop ends when none is active.  The vector
+// kernels are those of the single-column solve, launched per active column.
+int cn_cols(Handle *h, const double *U, const double *R, double *U1, int k, int *iters, cudaStream_t s) {
+  HIF_TRY(multi_check(h, k, "cn_step_multi"));
+  if (h->opt.x0_mode != 0 || h->opt.solver != 0) {
+    set_last_error("cn_step_multi: only the PCG solver from x0 = 0 (x0_mode 0, solver 0)");
+    return HIF_EINVAL;
+  }
+  MultiCG C{};
+  HIF_TRY(multi_cg_buffers(h, k, &C));
+  const long long N = h->N;
+  const int nb = C.nb;
+  StencilArgs st{h->diag, h->wx, h->wy, h->wz, h->grid.dim, h->grid.n, N};
+  const double tol2 = h->opt.cg_tol * h->opt.cg_tol;
+  const int period = h->opt.true_res_period;
+  std::vector<double> sc((size_t)16 * k);
+  for (int c = 0; c < k; ++c) {
+    double *g = C.g + c * N;
+    HIF_TRY(cn_rhs(h, U + c * N, R ? R + c * N : nullptr, g, s));
+    k_start<float><<<nb, NT, 0, s>>>(g, C.x + c * N, C.r + c * N, C.z + c * N, N, C.part + 4LL * nb * c);
+    k_scalar_start<false><<<1, 32, 0, s>>>(C.scal + 16 * c, C.part + 4LL * nb * c, nb, 0);
+    note_launch(2);
+  }
+  HIF_CUDA_TRY(cudaGetLastError());
+  HIF_CUDA_TRY(cudaMemcpyAsync(sc.data(), C.scal, sc.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  HIF_CUDA_TRY(cudaStreamSynchronize(s));
+  std::vector<char> active(k);
+  int nactive = 0;
+  for (int c = 0; c < k; ++c) {
+    active[c] = sc[16 * c + S_BB] > 0.0;
+    nactive += active[c];
+    if (iters) iters[c] = 0;
+  }
+  int status = HIF_OK;
+  for (int it = 0; nactive > 0; ++it) {
+    if (it >= h->opt.cg_maxit) {
+      status = HIF_ENOCONV;
+      break;
+    }
+    HIF_TRY(apply_multi_f32(h, k, s));
+    for (int c = 0; c < k; ++c) {
+      if (!active[c]) continue;
+      double *sct = C.scal + 16 * c, *part = C.part + 4LL * nb * c;
+      unsigned *tk = C.tk + 4 * c;
+      float *z = C.z + c * N;
+      k_cg_wz<float><<<nb, NT, 0, s>>>(C.r + c * N, z, C.w + c * N, st, part, sct, tk);
+      k_cg_update<float, false><<<nb, NT, 0, s>>>(C.x + c * N, C.r + c * N, C.p + c * N, C.q + c * N,
+                                                  C.w + c * N, z, sct, N, part, tk + 2, period, tol2,
+                                                  h->opt.cg_maxit, 0);
+      k_true_residual_cond<float, false><<<nb, NT, 0, s>>>(C.g + c * N, C.x + c * N, C.r + c * N, z, st, sct,
+                                                         period, part, tk + 3, tol2, h->opt.cg_maxit, 0);
+      note_launch(3);
+    }
+    HIF_CUDA_TRY(cudaGetLastError());
+    HIF_CUDA_TRY(cudaMemcpyAsync(sc.data(), C.scal, sc.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    HIF_CUDA_TRY(cudaMemcpyAsync(h->host_scal, h->scal, 16 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    HIF_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h->host_scal[kScalErr] != 0.0) return take_timeout(h);
+    for (int c = 0; c < k; ++c) {
+      if (!active[c]) continue;
+      if (iters) iters[c] = (int)sc[16 * c + S_IT];
+      if (sc[16 * c + S_CONV] != 0.0) {
+        active[c] = 0;
+        --nactive;
+      }
+    }
+  }
+  for (int c = 0; c < k; ++c)
+    HIF_CUDA_TRY(cudaMemcpyAsync(U1 + c * N, C.x + c * N, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  HIF_CUDA_TRY(cudaStreamSynchronize(s));
+  return status;
+}
+
 namespace {
 // record of one step of cn_multi: iterations, convergence flag, b.b, error flag
 __global__ void k_step_record(const double *__restrict__ sc, double *__restrict__ rec) {

@@ -28,7 +28,8 @@ EXPORTED = ("hif_default_options", "hif_setup", "hif_import_factor", "hif_export
             "hif_apply", "hif_matvec", "pcg_solve", "cn_step", "hif_set_reaction", "hif_query",
             "hif_destroy", "hif_strerror", "hif_last_error", "hif_stats_enable", "hif_stats_read",
             "hif_launch_count", "hif_apply_noalloc", "cn_step_batched", "hif_set_coefficient",
-            "hif_refactor", "hif_autotune", "cn_steps", "hif_inject_flow_stall")
+            "hif_refactor", "hif_autotune", "cn_steps", "hif_inject_flow_stall",
+            "hif_apply_multi", "cn_step_multi")
 
 
 class HifGrid(ctypes.Structure):
@@ -104,6 +105,10 @@ def lib():
     L.hif_refactor.restype = c_int
     L.hif_autotune.argtypes = [c_void_p, c_void_p]
     L.hif_autotune.restype = c_int
+    L.hif_apply_multi.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_void_p]
+    L.hif_apply_multi.restype = c_int
+    L.cn_step_multi.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p]
+    L.cn_step_multi.restype = c_int
     L.hif_inject_flow_stall.argtypes = [c_void_p, c_int, ctypes.c_longlong]
     L.hif_inject_flow_stall.restype = c_int
     for name in ("hif_setup", "hif_import_factor", "hif_export_factor", "hif_apply", "hif_matvec",
@@ -237,6 +242,43 @@ def hif_apply_noalloc(h: Handle, x: torch.Tensor, y: torch.Tensor = None,
     _check("hif_apply_noalloc", lib().hif_apply_noalloc(h.ptr, _vec(x, h.N, "x"), _vec(y, h.N, "y"),
                                                         _stream(stream)))
     return y
+
+
+HIF_MULTI_MAX_COLS = 64
+
+
+def hif_apply_multi(h: Handle, X: torch.Tensor, Y: torch.Tensor = None, stream=None) -> torch.Tensor:
+    """Y = F^{-1} X for the k columns of X (a (k, N) float64 CUDA tensor, one
+    right-hand side per row, i.e. the columns stored one after another); the
+    BF16 top levels and the root run as tensor-core products for all k at once.
+    Needs a handle set up with HIF_FP32_BF16TOP."""
+    if X.dim() != 2 or X.shape[1] != h.N:
+        raise ValueError(f"X must have shape (k, {h.N})")
+    k = X.shape[0]
+    if Y is None:
+        Y = torch.empty_like(X)
+    _check("hif_apply_multi", lib().hif_apply_multi(h.ptr, _vec(X.reshape(-1), k * h.N, "X"),
+                                                    _vec(Y.reshape(-1), k * h.N, "Y"), int(k),
+                                                    _stream(stream)))
+    return Y
+
+
+def cn_step_multi(h: Handle, U: torch.Tensor, R: torch.Tensor = None, out: torch.Tensor = None,
+                  stream=None):
+    """One CN step for each row of U ((k, N) float64 CUDA tensor: k states of
+    the same operator), the k PCG solves sharing each multi-column apply;
+    returns (U1, iters per state)."""
+    if U.dim() != 2 or U.shape[1] != h.N:
+        raise ValueError(f"U must have shape (k, {h.N})")
+    k = U.shape[0]
+    if out is None:
+        out = torch.empty_like(U)
+    rp = _vec(R.reshape(-1), k * h.N, "R") if R is not None else None
+    its = (c_int * k)()
+    _check("cn_step_multi", lib().cn_step_multi(h.ptr, _vec(U.reshape(-1), k * h.N, "U"), rp,
+                                                _vec(out.reshape(-1), k * h.N, "out"), int(k), its,
+                                                _stream(stream)))
+    return out, [its[i] for i in range(k)]
 
 
 def hif_matvec(h: Handle, x: torch.Tensor, y: torch.Tensor = None, stream=None) -> torch.Tensor:
