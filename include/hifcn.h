@@ -27,6 +27,8 @@
  *    hif_strerror() gives a message.  On error no output is guaranteed except
  *    where stated.
  *  - A handle is not thread safe; use one handle per host thread or lock.
+ *    Calls on disjoint sets of handles may run from several host threads at
+ *    once (each thread has its own work space for cn_step_batched).
  */
 #ifndef HIFCN_H
 #define HIFCN_H
@@ -343,6 +345,31 @@ typedef struct {
 
 int hif_stats_enable(hif_handle *h, int on);
 int hif_stats_read(hif_handle *h, hif_kernel_stat *out, int cap, int *count);
+
+/* ---------------------------------------------------------------------------
+ * Memory of a resident operator (no counterpart in the paper; for serving
+ * many operators under an HBM budget).
+ *
+ * hif_release_fp64 - free the FP64 copy of the factor values (and the FP64
+ * apply's work vectors) of a HIF_FP32 / HIF_FP32_BF16TOP handle, whose solves
+ * use only the reduced-precision copy: about two thirds of the factor's
+ * device memory.  Afterwards hif_apply with HIF_FP64, hif_apply_noalloc and
+ * hif_export_factor refuse (HIF_EINVAL); solves are unchanged, bit for bit.
+ * hif_refactor builds both copies again.  Waits for the device.
+ *
+ * hif_offload - copy the handle's large device allocations (factor values,
+ * indices, work vectors: every allocation of at least 2 MiB) to host memory
+ * and give their device memory back; their device addresses stay reserved.
+ * Until hif_reload the handle refuses solves, applies, refactoring and
+ * coefficient changes (HIF_EINVAL); hif_query reports the device bytes still
+ * held.  hif_reload maps device memory at the same addresses again and copies
+ * the contents back, so the handle (and its captured solve graphs) continues
+ * exactly where it was: later results are bit-identical to those without the
+ * offload.  Both wait for the device.  Needs CUDA virtual memory management
+ * (HIF_EINVAL without it).  Errors: HIF_EINVAL, HIF_ENOMEM, HIF_ECUDA. */
+int hif_release_fp64(hif_handle *h);
+int hif_offload(hif_handle *h);
+int hif_reload(hif_handle *h);
 
 /* ---------------------------------------------------------------------------
  * hif_inject_flow_stall - failure injection for testing failure detection (no

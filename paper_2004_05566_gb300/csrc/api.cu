@@ -64,22 +64,6 @@ StatScope::~StatScope() {
   h->stat_pending.push_back({idx, a, b, bytes});
 }
 
-int dev_alloc(Handle *h, void **ptr, size_t bytes) {
-  *ptr = nullptr;
-  if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(ptr, bytes);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    set_last_error(std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes: " +
-                   cudaGetErrorString(e));
-    *ptr = nullptr;
-    return HIF_ENOMEM;
-  }
-  h->allocations.push_back(*ptr);
-  h->device_bytes += (long long)bytes;
-  return HIF_OK;
-}
-
 int alloc_work(Handle *h) {
   const long long N = h->N;
   // blocks of the CG vector kernels: 4 per SM (measured at 1023^2: 839 us per step
@@ -446,8 +430,9 @@ int create_handle(const hif_grid *grid, const double *a_nodes, double dt, const 
 void release_factor(Handle *h) {
   destroy_pcg_graphs(h);
   destroy_multi_state(h);  // its buffers are among the allocations freed below
-  for (size_t i = h->factor_alloc_begin; i < h->allocations.size(); ++i) cudaFree(h->allocations[i]);
+  for (size_t i = h->factor_alloc_begin; i < h->allocations.size(); ++i) dev_free(h->allocations[i]);
   h->allocations.resize(h->factor_alloc_begin);
+  h->fp64_released = false;
   h->device_bytes = h->work_device_bytes;
   h->lv_host.clear();
   h->lv.clear();
@@ -619,7 +604,7 @@ hif_handle::~hif_handle() {
     cudaEventDestroy(r.b);
   }
   for (auto e : event_pool) cudaEventDestroy(e);
-  for (void *p : allocations) cudaFree(p);
+  for (auto &a : allocations) hifcn::dev_free(a);
   if (step_rec) cudaFree(step_rec);
   if (host_scal) cudaFreeHost(host_scal);
 }
@@ -712,6 +697,7 @@ int hif_import_factor(const hif_grid *grid, const void *blob, size_t bytes, doub
 
 int hif_export_factor(const hif_handle *hh, void *buf, size_t *bytes) {
   if (!hh || !bytes || !hh->factor_ok) return HIF_EINVAL;
+  if (!hh->f64.vals) return invalid("hif_export_factor: the handle's FP64 factor values were released");
   const Handle *h = hh;
   std::vector<unsigned char> out;
   auto put = [&](const void *p, size_t n) {
@@ -827,6 +813,7 @@ int hif_set_reaction(hif_handle *h, int kind, double k1, double k2) {
 
 int hif_set_coefficient(hif_handle *h, const double *a_nodes, hif_stream stream) {
   if (!h || !a_nodes) return HIF_EINVAL;
+  if (h->offloaded) return invalid("hif_set_coefficient: the handle is offloaded (hif_reload first)");
   cudaStream_t s = (cudaStream_t)stream;
   HIF_TRY(stencil_update(h, a_nodes, s));
   HIF_CUDA_TRY(cudaStreamSynchronize(s));
@@ -835,6 +822,7 @@ int hif_set_coefficient(hif_handle *h, const double *a_nodes, hif_stream stream)
 
 int hif_refactor(hif_handle *h, const double *a_nodes, hif_stream stream) {
   if (!h || !a_nodes) return HIF_EINVAL;
+  if (h->offloaded) return invalid("hif_refactor: the handle is offloaded (hif_reload first)");
   if (!(h->opt.eps >= 0.0)) return HIF_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   HIF_CUDA_TRY(cudaDeviceSynchronize());  // no solve of this handle is in flight
@@ -850,6 +838,40 @@ int hif_refactor(hif_handle *h, const double *a_nodes, hif_stream stream) {
   }
   h->setup_seconds = now_seconds() - t0;
   h->factor_ok = true;
+  return HIF_OK;
+}
+
+int hif_release_fp64(hif_handle *h) {
+  if (!h) return invalid("hif_release_fp64: h is NULL");
+  if (!h->factor_ok) return invalid("hif_release_fp64: the handle holds no factor (or is offloaded)");
+  if (!reduced_apply(h)) return invalid("hif_release_fp64: only for HIF_FP32 / HIF_FP32_BF16TOP handles");
+  if (h->fp64_released) return HIF_OK;
+  HIF_CUDA_TRY(cudaDeviceSynchronize());
+  for (void *p : {(void *)h->f64.vals, (void *)h->f64.xI, (void *)h->f64.gs, (void *)h->f64.contrib})
+    if (p) HIF_TRY(dev_free_ptr(h, p));
+  h->f64 = FactorValues<double>{};
+  h->fp64_released = true;
+  return HIF_OK;
+}
+
+int hif_offload(hif_handle *h) {
+  if (!h) return invalid("hif_offload: h is NULL");
+  if (h->offloaded) return HIF_OK;
+  if (!h->factor_ok) return invalid("hif_offload: the handle holds no factor");
+  HIF_TRY(offload_allocations(h));
+  h->offloaded = true;
+  h->factor_ok = false;  // every solve and apply refuses until hif_reload
+  return HIF_OK;
+}
+
+int hif_reload(hif_handle *h) {
+  if (!h) return invalid("hif_reload: h is NULL");
+  if (!h->offloaded) return HIF_OK;
+  const int st = reload_allocations(h);
+  if (st != HIF_OK) return st;
+  h->offloaded = false;
+  h->factor_ok = true;
+  if (h->view_ok) HIF_TRY(build_view(h));  // the reaction may have changed meanwhile
   return HIF_OK;
 }
 

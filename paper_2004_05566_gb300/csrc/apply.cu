@@ -1686,6 +1686,111 @@ __global__ void __launch_bounds__(kFlowThreads) k_flow_sweep(
 // finds its handle by binary search and runs the same unit code as the
 // single-handle kernels (G-form cells, FP32 arithmetic, BF16 values at the
 // handle's BF16 levels).  Handles whose solve has converged are skipped.
+// S-form cell steps of the merged batched path (one CTA of 256 threads per
+// cell, FP32, plain loads; the operator of the bulk-copy kernels): forward
+// c_B = V x_I (x_I left as it is), backward x_I <- S x_I - V^T x_B with S
+// packed lower, diagonal halved.  In the backward, warp w takes rows w, w+8,
+// ...; lane l keeps x at the column quads l and l + 32 and accumulates the
+// column sums there, so one read of a stored quad feeds both the row dot and
+// the column sums; the 8 warps' column sums and the row dots meet at the end
+// in a fixed order (deterministic).  Needs nI <= 256.
+__device__ __forceinline__ float warp_sum_f(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __noinline__ void cell_fwd_S_unit(const CellDesc c, const int *__restrict__ idx,
+                                             const float *__restrict__ vals, float *__restrict__ contrib,
+                                             const float *__restrict__ x, float *sm) {
+  const int nI = c.nI, nq = (int)pad4(nI) / 4;
+  float *xs = sm;
+  for (int i = threadIdx.x; i < 4 * nq; i += 256) xs[i] = i < nI ? x[idx[c.I_off + i]] : 0.f;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float xa[4], xb[4];
+  load_xcols(xs, nq, lane, xa, xb);
+  const float *V = vals + c.V_off;
+  for (int b = warp; b < c.nB; b += 8) {
+    const float *row = V + (long long)b * 4 * nq;
+    float t = 0.f;
+    if (lane < nq) {
+      float v[4];
+      ld4(row + 4 * lane, v);
+      t = dot4(v, xa);
+    }
+    if (lane + 32 < nq) {
+      float v[4];
+      ld4(row + 4 * (lane + 32), v);
+      t += dot4(v, xb);
+    }
+    t = warp_sum_f(t);
+    if (lane == 0) contrib[c.C_off + b] = t;
+  }
+}
+
+__device__ __noinline__ void cell_bwd_S_unit(const CellDesc c, const int *__restrict__ idx,
+                                             const float *__restrict__ vals, float *__restrict__ x, float *sm) {
+  const int nI = c.nI, nB = c.nB, nq = (int)pad4(nI) / 4, np = 4 * nq;
+  float *xs = sm;                    // np
+  float *xbv = xs + np;              // pad4(nB)
+  float *part = xbv + pad4(nB);      // 8 x np column sums
+  float *rd = part + 8 * np;         // np row dots
+  for (int i = threadIdx.x; i < np; i += 256) xs[i] = i < nI ? x[idx[c.I_off + i]] : 0.f;
+  for (int b = threadIdx.x; b < nB; b += 256) xbv[b] = x[idx[c.B_off + b]];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float xa[4], xb[4];
+  load_xcols(xs, nq, lane, xa, xb);
+  float ca[4] = {0.f, 0.f, 0.f, 0.f}, cb[4] = {0.f, 0.f, 0.f, 0.f};
+  const float *S = vals + c.S_off;
+  for (int i = warp; i < nI; i += 8) {
+    const float *row = S + tri_off(i);
+    const int nqi = (i >> 2) + 1;
+    const float xi = xs[i];
+    float t = 0.f;
+    if (lane < nqi) {
+      float v[4];
+      ld4(row + 4 * lane, v);
+      t = dot4(v, xa);
+      axpy4(ca, v, xi);
+    }
+    if (lane + 32 < nqi) {
+      float v[4];
+      ld4(row + 4 * (lane + 32), v);
+      t += dot4(v, xb);
+      axpy4(cb, v, xi);
+    }
+    t = warp_sum_f(t);
+    if (lane == 0) rd[i] = t;
+  }
+  const float *V = vals + c.V_off;
+  for (int b = warp; b < nB; b += 8) {
+    const float *row = V + (long long)b * np;
+    const float y = -xbv[b];
+    if (lane < nq) {
+      float v[4];
+      ld4(row + 4 * lane, v);
+      axpy4(ca, v, y);
+    }
+    if (lane + 32 < nq) {
+      float v[4];
+      ld4(row + 4 * (lane + 32), v);
+      axpy4(cb, v, y);
+    }
+  }
+  float *pw = part + warp * np;
+  if (lane < nq)
+    for (int e = 0; e < 4; ++e) pw[4 * lane + e] = ca[e];
+  if (lane + 32 < nq)
+    for (int e = 0; e < 4; ++e) pw[4 * (lane + 32) + e] = cb[e];
+  __syncthreads();
+  for (int i = threadIdx.x; i < nI; i += 256) {
+    float y = rd[i];
+    for (int w = 0; w < 8; ++w) y += part[w * np + i];
+    x[idx[c.I_off + i]] = y;
+  }
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(256) k_merged_phase(const int *__restrict__ pre, int K, int level,
                                                       HandleView *const *__restrict__ views,
@@ -1714,10 +1819,12 @@ __global__ void __launch_bounds__(256) k_merged_phase(const int *__restrict__ pr
   } else {
     const LevelView L = v->lv[level];
     if constexpr (KIND == kPhaseCellFwd) {
-      if (b16) cell_fwd_unit<float, 256, __nv_bfloat16>(L.fwd[u], L.cells, idx, vals16, v->contrib, v->xI, v->z, sm);
+      if (L.sform) cell_fwd_S_unit(L.cells[L.fwd[u].cell], idx, vals, v->contrib, v->z, sm);
+      else if (b16) cell_fwd_unit<float, 256, __nv_bfloat16>(L.fwd[u], L.cells, idx, vals16, v->contrib, v->xI, v->z, sm);
       else cell_fwd_unit<float, 256>(L.fwd[u], L.cells, idx, vals, v->contrib, v->xI, v->z, sm);
     } else if constexpr (KIND == kPhaseCellBwd) {
-      if (b16) cell_bwd_unit<float, 256, __nv_bfloat16>(L.bwd[u], L.cells, idx, vals16, v->xI, v->z, sm);
+      if (L.sform) cell_bwd_S_unit(L.cells[L.bwd[u].cell], idx, vals, v->z, sm);
+      else if (b16) cell_bwd_unit<float, 256, __nv_bfloat16>(L.bwd[u], L.cells, idx, vals16, v->xI, v->z, sm);
       else cell_bwd_unit<float, 256>(L.bwd[u], L.cells, idx, vals, v->xI, v->z, sm);
     } else if constexpr (KIND == kPhaseGroupFwd) {
       if (u < L.nlarge) {
@@ -2280,6 +2387,7 @@ int build_view(Handle *h) {
   v.q = h->q;
   v.g = h->g;
   v.x = h->xsol;
+  v.w = h->w;
   v.diag = h->diag;
   v.wx = h->wx;
   v.wy = h->wy;
@@ -2296,7 +2404,8 @@ int build_view(Handle *h) {
   for (int l = 0; l < h->L; ++l) {
     const LevelDev &D = h->lv[l];
     v.lv[l] = LevelView{D.fwd1, D.bwd1, D.cells, D.groups, D.small_groups, D.large_groups,
-                        D.ncells, D.ncells, D.nsmall, D.nlarge};
+                        D.ncells, D.ncells, D.nsmall, D.nlarge,
+                        (D.has_S && D.max_nI <= 256 && l < v.bf16_lb) ? 1 : 0};
   }
   if (!h->view) HIF_TRY(dev_alloc(h, (void **)&h->view, sizeof(HandleView)));
   HIF_CUDA_TRY(cudaMemcpy(h->view, &v, sizeof(HandleView), cudaMemcpyHostToDevice));
@@ -2326,7 +2435,8 @@ void merged_units(const Handle *h, int kind, int level, int *units, size_t *smem
       break;
     case kPhaseCellBwd:
       *units = lv.ncells;
-      *smem = ((size_t)lv.max_nI + lv.max_nB + 8 * 256) * sizeof(float);
+      *smem = std::max((size_t)lv.max_nI + lv.max_nB + 8 * 256,
+                       10 * (size_t)pad4(lv.max_nI) + (size_t)pad4(lv.max_nB)) * sizeof(float);
       break;
     case kPhaseGroupFwd:
       *units = lv.ngroups ? lv.nlarge + (lv.nsmall + 7) / 8 : 0;
@@ -2796,6 +2906,10 @@ int apply_inplace_f32(Handle *h, float *x, cudaStream_t s) {
 
 int apply_inverse(Handle *h, const double *x, double *y, int precision, cudaStream_t s) {
   if (precision == HIF_FP64) {
+    if (!h->f64.vals) {
+      set_last_error("hif_apply: the handle's FP64 factor values were released");
+      return HIF_EINVAL;
+    }
     HIF_CUDA_TRY(cudaMemcpyAsync(y, x, h->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
     return apply_inplace_f64(h, y, s);
   }

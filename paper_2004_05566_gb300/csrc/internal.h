@@ -182,6 +182,7 @@ struct LevelView {
   const GroupDesc *groups;
   const int *small, *large;
   int nfwd, nbwd, nsmall, nlarge;
+  int sform;  // cells applied in the S-form (S = A_II^{-1} stored, FP32 values)
 };
 struct HandleView {
   int L, dim, n, root_n;
@@ -195,12 +196,26 @@ struct HandleView {
   const int *ridx;
   long long root_G_off;
   // CG (FP64) and the stencil
-  double *r, *p, *q, *g, *x;
+  double *r, *p, *q, *g, *x, *w;
   const double *diag, *wx, *wy, *wz;
   double dt, kappa, react_k1, react_inv_k2;
   int react_kind, x0_mode, true_res_period, cg_maxit;
   double tol2;
   LevelView lv[kMaxViewLevels];
+};
+
+// One device allocation of a handle (memory.cu).  Allocations of at least
+// kVmmMinBytes are mapped through CUDA virtual memory management: p is a
+// reserved address range, mapped (physical memory present) unless the
+// handle is offloaded, when `host` holds the contents.
+constexpr size_t kVmmMinBytes = 2u << 20;
+struct DevAlloc {
+  void *p = nullptr;
+  size_t bytes = 0, size = 0;   // requested, and reserved / allocated
+  bool vmm = false, mapped = false;
+  int dev = 0;
+  unsigned long long mh = 0;    // physical allocation handle while mapped
+  void *host = nullptr;         // contents while offloaded
 };
 
 template <typename T>
@@ -304,7 +319,9 @@ struct hif_handle {
   int step_rec_cap = 0;        // steps step_rec holds (grown on demand, freed with the handle)
   int nblocks_vec = 0;
 
-  std::vector<void *> allocations;
+  std::vector<hifcn::DevAlloc> allocations;
+  bool offloaded = false;  // hif_offload: large allocations live in host memory
+  bool fp64_released = false;  // hif_release_fp64: no FP64 factor values on the device
   long long device_bytes = 0;
   // allocations [factor_alloc_begin, end) belong to the factor (released by
   // hif_refactor); work_device_bytes is device_bytes without them
@@ -335,8 +352,13 @@ inline bool reduced_apply(const Handle *h) {
   return h->has_f32 && (h->opt.precision == HIF_FP32 || h->opt.precision == HIF_FP32_BF16TOP);
 }
 
-// allocation helper: records the pointer for release in ~Handle
+// allocation helpers (memory.cu): dev_alloc records the allocation for
+// release in ~Handle; dev_free_ptr frees one of them early
 int dev_alloc(Handle *h, void **ptr, size_t bytes);
+void dev_free(DevAlloc &a);
+int dev_free_ptr(Handle *h, void *p);
+int offload_allocations(Handle *h);
+int reload_allocations(Handle *h);
 
 // launch bookkeeping: every kernel launch of the library calls note_launch();
 // with statistics on, StatScope brackets a launch with events.

@@ -1009,68 +1009,6 @@ __global__ void __launch_bounds__(NT) k_b_start(BSeg B, double *__restrict__ par
   if (threadIdx.x == 0) part[2 * blockIdx.x + 1] = t;
 }
 
-// partials of r.z (mode 0), p.q with q = A p (mode 1)
-template <int MODE>
-__global__ void __launch_bounds__(NT) k_b_dot(BSeg B, const int *__restrict__ active,
-                                              const double *__restrict__ sc, double *__restrict__ part) {
-  __shared__ double sm[NT / 32];
-  const int p = seg_owner(B.segpre, B.K, blockIdx.x);
-  if (!active[p]) return;
-  const HandleView *v = B.views[p];
-  const long long j0 = (long long)(blockIdx.x - B.segpre[p]) * kSeg;
-  const long long j1 = min(j0 + kSeg, v->N);
-  double acc = 0.0;
-  if constexpr (MODE == 0) {
-    for (long long j = j0 + threadIdx.x; j < j1; j += NT) acc += v->r[j] * (double)v->z[j];
-  } else {
-    for (long long j = j0 + threadIdx.x; j < j1; j += NT) {
-      const double qj = stencil_row(v->p, v->diag, v->wx, v->wy, v->wz, v->dim, v->n, j);
-      v->q[j] = qj;
-      acc += v->p[j] * qj;
-    }
-  }
-  const double t = block_sum<NT>(acc, sm);
-  if (threadIdx.x == 0) part[2 * blockIdx.x] = t;
-  (void)sc;
-}
-
-// p = z + beta p (p = z on the first iteration)
-__global__ void __launch_bounds__(NT) k_b_update_p(BSeg B, const int *__restrict__ active,
-                                                   const double *__restrict__ sc) {
-  const int p = seg_owner(B.segpre, B.K, blockIdx.x);
-  if (!active[p]) return;
-  const HandleView *v = B.views[p];
-  const long long j0 = (long long)(blockIdx.x - B.segpre[p]) * kSeg;
-  const long long j1 = min(j0 + kSeg, v->N);
-  const bool first = sc[p * B_COUNT + B_IT] == 0.0;
-  const double beta = sc[p * B_COUNT + B_BETA];
-  for (long long j = j0 + threadIdx.x; j < j1; j += NT)
-    v->p[j] = first ? (double)v->z[j] : (double)v->z[j] + beta * v->p[j];
-}
-
-// x += alpha p; r -= alpha q; z = r; partials r.r; every true_res_period
-// iterations the next kernel recomputes r from x instead
-__global__ void __launch_bounds__(NT) k_b_update_xr(BSeg B, const int *__restrict__ active,
-                                                    const double *__restrict__ sc, double *__restrict__ part) {
-  __shared__ double sm[NT / 32];
-  const int p = seg_owner(B.segpre, B.K, blockIdx.x);
-  if (!active[p]) return;
-  const HandleView *v = B.views[p];
-  const long long j0 = (long long)(blockIdx.x - B.segpre[p]) * kSeg;
-  const long long j1 = min(j0 + kSeg, v->N);
-  const double alpha = sc[p * B_COUNT + B_ALPHA];
-  double acc = 0.0;
-  for (long long j = j0 + threadIdx.x; j < j1; j += NT) {
-    v->x[j] += alpha * v->p[j];
-    const double rj = v->r[j] - alpha * v->q[j];
-    v->r[j] = rj;
-    v->z[j] = (float)rj;
-    acc += rj * rj;
-  }
-  const double t = block_sum<NT>(acc, sm);
-  if (threadIdx.x == 0) part[2 * blockIdx.x] = t;
-}
-
 __global__ void __launch_bounds__(NT) k_b_true_res(BSeg B, const int *__restrict__ active,
                                                    const double *__restrict__ sc, double *__restrict__ part) {
   __shared__ double sm[NT / 32];
@@ -1092,8 +1030,78 @@ __global__ void __launch_bounds__(NT) k_b_true_res(BSeg B, const int *__restrict
   if (threadIdx.x == 0) part[2 * blockIdx.x] = t;
 }
 
+// Chronopoulos-Gear iteration of the merged steps (the arrangement of
+// k_cg_wz / k_cg_update, per handle segment): w = A z with partials of r.z
+// and w.z ...
+__global__ void __launch_bounds__(NT) k_b_wz(BSeg B, const int *__restrict__ active, double *__restrict__ part) {
+  __shared__ double sm[2 * (NT / 32)];
+  const int p = seg_owner(B.segpre, B.K, blockIdx.x);
+  if (!active[p]) return;
+  const HandleView *v = B.views[p];
+  const int j0 = (blockIdx.x - B.segpre[p]) * kSeg;
+  const int j1 = (int)min((long long)(j0 + kSeg), v->N);
+  const int S = v->n - 1, S2 = S * S;
+  const bool d3 = v->dim == 3;
+  const float *z = v->z;
+  double arz = 0.0, awz = 0.0;
+  int j = j0 + threadIdx.x;
+  GridWalk g(j, NT, S, d3);
+  for (; j < j1; j += NT, g.advance(S, d3)) {
+    const double zj = widen(z[j]);
+    double y = v->diag[j] * zj;
+    if (g.i1 < S - 1) y -= v->wx[j] * widen(z[j + 1]);
+    if (g.i1 > 0) y -= v->wx[j - 1] * widen(z[j - 1]);
+    if (g.i2 < S - 1) y -= v->wy[j] * widen(z[j + S]);
+    if (g.i2 > 0) y -= v->wy[j - S] * widen(z[j - S]);
+    if (d3) {
+      if (g.i3 < S - 1) y -= v->wz[j] * widen(z[j + S2]);
+      if (g.i3 > 0) y -= v->wz[j - S2] * widen(z[j - S2]);
+    }
+    v->w[j] = y;
+    arz += v->r[j] * zj;
+    awz += y * zj;
+  }
+  const double2 t = block_sum2<NT>(arz, awz, sm);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = t.x;
+    part[2 * blockIdx.x + 1] = t.y;
+  }
+}
+
+// ... then (after the scalar phase: beta, sigma, alpha) p = z + beta p,
+// q = w + beta q, x += alpha p, r -= alpha q, z = r, partials of r.r
+__global__ void __launch_bounds__(NT) k_b_update(BSeg B, const int *__restrict__ active,
+                                                 const double *__restrict__ sc, double *__restrict__ part) {
+  __shared__ double sm[2 * (NT / 32)];
+  const int p = seg_owner(B.segpre, B.K, blockIdx.x);
+  if (!active[p]) return;
+  const HandleView *v = B.views[p];
+  const int j0 = (blockIdx.x - B.segpre[p]) * kSeg;
+  const int j1 = (int)min((long long)(j0 + kSeg), v->N);
+  const double *s = sc + p * B_COUNT;
+  const bool first = s[B_IT] == 0.0;
+  const double beta = s[B_BETA], alpha = s[B_ALPHA];
+  float *z = v->z;
+  double acc = 0.0;
+  for (int j = j0 + threadIdx.x; j < j1; j += NT) {
+    const double zj = widen(z[j]);
+    const double pj = first ? zj : zj + beta * v->p[j];
+    const double qj = first ? v->w[j] : v->w[j] + beta * v->q[j];
+    v->p[j] = pj;
+    v->q[j] = qj;
+    v->x[j] += alpha * pj;
+    const double rj = v->r[j] - alpha * qj;
+    v->r[j] = rj;
+    z[j] = narrow_rn(rj);
+    acc += rj * rj;
+  }
+  const double2 t = block_sum2<NT>(acc, 0.0, sm);
+  if (threadIdx.x == 0) part[2 * blockIdx.x] = t.x;
+}
+
 // scalar phases, one warp per handle (partials of its segments added in order)
-// mode 0: start (b.b, r.r -> active);  1: beta;  2: alpha;  3: end of iteration
+// mode 0: start (b.b, r.r -> active);  1: beta;  2: alpha;  3: end of iteration;
+// 4: beta, sigma = p.Ap and alpha of the Chronopoulos-Gear iteration
 __global__ void __launch_bounds__(256) k_b_scalar(BSeg B, int mode, int *__restrict__ active,
                                                   double *__restrict__ sc, const double *__restrict__ part,
                                                   int *__restrict__ nactive) {
@@ -1129,6 +1137,15 @@ __global__ void __launch_bounds__(256) k_b_scalar(BSeg B, int mode, int *__restr
   } else if (mode == 2) {
     s[B_PQ] = a;
     s[B_ALPHA] = s[B_RZ] / a;
+  } else if (mode == 4) {
+    const bool first = s[B_IT] == 0.0;
+    const double rho = a, mu = b;
+    const double beta = first ? 0.0 : rho / s[B_RZ];
+    const double sigma = first ? mu : mu - beta * rho / s[B_ALPHA];
+    s[B_BETA] = beta;
+    s[B_PQ] = sigma;
+    s[B_ALPHA] = rho / sigma;
+    s[B_RZ] = rho;
   } else {
     s[B_RR] = a;
     const double it = s[B_IT] + 1.0;
@@ -1152,15 +1169,22 @@ __global__ void __launch_bounds__(NT) k_b_copy_out(BSeg B, const double *__restr
   for (long long j = j0 + threadIdx.x; j < j1; j += NT) out[j] = zero ? 0.0 : v->x[j];
 }
 
-// Workspace of the merged steps (grown on demand, reused across calls).
+// Workspace of the merged steps (grown on demand, reused across calls), one
+// per host thread: threads that step disjoint sets of handles at the same
+// time (e.g. the lanes of a serving loop) never share it.
 struct BatchWorkspace {
   void *dev = nullptr;
   size_t dev_bytes = 0;
   unsigned char *host = nullptr;
   size_t host_bytes = 0;
   int *h_nactive = nullptr;
+  ~BatchWorkspace() {
+    if (dev) cudaFree(dev);
+    if (host) cudaFreeHost(host);
+    if (h_nactive) cudaFreeHost(h_nactive);
+  }
 };
-BatchWorkspace g_bws;
+thread_local BatchWorkspace g_bws;
 
 int bws_reserve(size_t dev_bytes, size_t host_bytes) {
   if (dev_bytes > g_bws.dev_bytes) {
@@ -1278,16 +1302,13 @@ int cn_batched_merged(Handle *const *hs, int K, const double *const *u, const do
     for (int ph = 0; ph < P; ++ph)
       HIF_TRY(launch_merged_phase(phases[ph].x, phases[ph].y, dint + (size_t)(K + 1) * (ph + 1), K,
                                   totals[ph], smem[ph], const_cast<HandleView *const *>(B.views), active, s));
-    k_b_dot<0><<<total_seg, NT, 0, s>>>(B, active, sc, part);
-    k_b_scalar<<<sgrid, 256, 0, s>>>(B, 1, active, sc, part, nactive);
-    k_b_update_p<<<total_seg, NT, 0, s>>>(B, active, sc);
-    k_b_dot<1><<<total_seg, NT, 0, s>>>(B, active, sc, part);
-    k_b_scalar<<<sgrid, 256, 0, s>>>(B, 2, active, sc, part, nactive);
-    k_b_update_xr<<<total_seg, NT, 0, s>>>(B, active, sc, part);
+    k_b_wz<<<total_seg, NT, 0, s>>>(B, active, part);
+    k_b_scalar<<<sgrid, 256, 0, s>>>(B, 4, active, sc, part, nactive);
+    k_b_update<<<total_seg, NT, 0, s>>>(B, active, sc, part);
     k_b_true_res<<<total_seg, NT, 0, s>>>(B, active, sc, part);
     HIF_CUDA_TRY(cudaMemsetAsync(nactive, 0, sizeof(int), s));
     k_b_scalar<<<sgrid, 256, 0, s>>>(B, 3, active, sc, part, nactive);
-    note_launch(8);
+    note_launch(5);
     HIF_CUDA_TRY(cudaGetLastError());
     HIF_TRY(read_active(&n_act));
   }

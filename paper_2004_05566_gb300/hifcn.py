@@ -29,7 +29,7 @@ EXPORTED = ("hif_default_options", "hif_setup", "hif_import_factor", "hif_export
             "hif_destroy", "hif_strerror", "hif_last_error", "hif_stats_enable", "hif_stats_read",
             "hif_launch_count", "hif_apply_noalloc", "cn_step_batched", "hif_set_coefficient",
             "hif_refactor", "hif_autotune", "cn_steps", "hif_inject_flow_stall",
-            "hif_apply_multi", "cn_step_multi")
+            "hif_apply_multi", "cn_step_multi", "hif_release_fp64", "hif_offload", "hif_reload")
 
 
 class HifGrid(ctypes.Structure):
@@ -109,6 +109,9 @@ def lib():
     L.hif_apply_multi.restype = c_int
     L.cn_step_multi.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p]
     L.cn_step_multi.restype = c_int
+    for name in ("hif_release_fp64", "hif_offload", "hif_reload"):
+        getattr(L, name).argtypes = [c_void_p]
+        getattr(L, name).restype = c_int
     L.hif_inject_flow_stall.argtypes = [c_void_p, c_int, ctypes.c_longlong]
     L.hif_inject_flow_stall.restype = c_int
     for name in ("hif_setup", "hif_import_factor", "hif_export_factor", "hif_apply", "hif_matvec",
@@ -363,6 +366,21 @@ def hif_refactor(h: Handle, a_nodes: torch.Tensor, stream=None):
 def hif_autotune(h: Handle, stream=None):
     """Pick the per-level CTA cut of the apply and the leaf kernels' CTAs per SM by timing."""
     _check("hif_autotune", lib().hif_autotune(h.ptr, _stream(stream)))
+
+
+def hif_release_fp64(h: Handle):
+    """Free the FP64 factor values of an FP32 / BF16TOP handle (its solves use FP32)."""
+    _check("hif_release_fp64", lib().hif_release_fp64(h.ptr))
+
+
+def hif_offload(h: Handle):
+    """Move the handle's large device allocations to host memory (addresses kept)."""
+    _check("hif_offload", lib().hif_offload(h.ptr))
+
+
+def hif_reload(h: Handle):
+    """Map device memory at the same addresses again and copy the contents back."""
+    _check("hif_reload", lib().hif_reload(h.ptr))
 
 
 def hif_inject_flow_stall(h: Handle, unit: int, polls: int = 0):

@@ -98,6 +98,11 @@ int main(void) {
   CHECK(hif_apply_noalloc(NULL, &x, &y, NULL) == HIF_EINVAL);
   CHECK(strstr(hif_last_error(), "h is NULL") != NULL);
   CHECK(hif_inject_flow_stall(NULL, 0, 16) == HIF_EINVAL);
+  CHECK(hif_release_fp64(NULL) == HIF_EINVAL);
+  CHECK(hif_offload(NULL) == HIF_EINVAL);
+  CHECK(hif_reload(NULL) == HIF_EINVAL);
+  CHECK(hif_apply_multi(NULL, &x, &y, 1, NULL) == HIF_EINVAL);
+  CHECK(cn_step_multi(NULL, &x, NULL, &y, 1, &it, NULL) == HIF_EINVAL);
   CHECK(hif_matvec(NULL, &x, &y, NULL) == HIF_EINVAL);
   CHECK(pcg_solve(NULL, &x, &y, &it, &x, NULL) == HIF_EINVAL);
   CHECK(cn_step(NULL, &x, NULL, &y, &it, NULL) == HIF_EINVAL);

@@ -33,9 +33,13 @@ class _FakeHandle:
 
 
 class _FakeBinding:
+    HIF_FP64 = 0
     HIF_FP32 = 1
 
-    def __init__(self, poison_dt=None):
+    def __init__(self, poison_dt=None, hold_dt=None):
+        self.hold_dt = hold_dt  # steps of operators with this dt wait for hold
+        self.hold = threading.Event()
+        self.held = threading.Event()  # set when such a step waits
         self.setups = 0
         self.live = 0
         self.batch_sizes = []
@@ -60,6 +64,9 @@ class _FakeBinding:
         return {"device_bytes": BYTES}
 
     def cn_step_batched(self, hs, us, outs):
+        if self.hold_dt is not None and any(h.dt == self.hold_dt for h in hs):
+            self.held.set()
+            assert self.hold.wait(30)
         self.entered.set()
         assert self.gate.wait(30)
         assert len({id(h) for h in hs}) == len(hs)  # one request per operator
@@ -79,8 +86,7 @@ def fake(monkeypatch):
     return f
 
 
-def _spec(dt):
-    n = 8
+def _spec(dt, n=8):
     return S.OperatorSpec(dim=2, n=n, leaf=4, a_nodes=np.ones((n + 1, n + 1)), dt=dt, eps=1e-6,
                           u0=np.zeros((n - 1, n - 1)), reaction=(1, 1.0, 10.0), precision=1)
 
@@ -185,3 +191,76 @@ def test_failed_step_reaches_every_waiting_client(fake):
     finally:
         srv.close()
     assert fake.live == 0
+
+
+def test_size_lanes_small_operators_pass_a_held_large_batch(monkeypatch):
+    """Two size lanes: while a step of a large operator is held on the GPU
+    side, requests of small operators are still stepped (their own lane), and
+    every trajectory is the closed form afterwards."""
+    f = _FakeBinding(hold_dt=0.75)
+    monkeypatch.setattr(S, "H", f)
+    srv = _server(10 * BYTES, lanes=[100])  # N <= 100: lane 0 (n = 8: N = 49); n = 16: N = 225
+    srv.register("big", _spec(0.75, n=16))
+    srv.register("s1", _spec(0.5))
+    srv.register("s2", _spec(0.25))
+    try:
+        assert srv.lane_of("big") == 1 and srv.lane_of("s1") == 0
+        fb = srv.submit("big")
+        assert f.held.wait(30)  # the large lane's batch is running (held)
+        small = [srv.submit("s1"), srv.submit("s2"), srv.submit("s1")]
+        res = [r.result(30) for r in small]  # completes while "big" is still held
+        assert not fb.done()
+        assert [r.step for r in res] == [1, 1, 2]
+        f.hold.set()
+        assert fb.result(30).step == 1
+        assert np.all(srv.state("s1") == _expected(0.5, 2))
+        assert np.all(srv.state("big") == _expected(0.75, 1))
+    finally:
+        f.hold.set()
+        srv.close()
+    assert f.live == 0
+
+
+class _OffloadBinding(_FakeBinding):
+    """The fake with hif_offload / hif_reload: an offloaded handle refuses steps."""
+
+    def __init__(self):
+        super().__init__()
+        self.offloads = 0
+
+    def hif_offload(self, h):
+        assert not h.closed and not getattr(h, "off", False)
+        h.off = True
+        self.offloads += 1
+
+    def hif_reload(self, h):
+        assert h.off
+        h.off = False
+
+    def cn_step_batched(self, hs, us, outs):
+        assert not any(getattr(h, "off", False) for h in hs)
+        return super().cn_step_batched(hs, us, outs)
+
+
+def test_eviction_offloads_and_readmission_reloads(monkeypatch):
+    """With offload available, an evicted operator keeps its handle (moved to
+    host memory) and is reloaded instead of factored again; states continue."""
+    f = _OffloadBinding()
+    monkeypatch.setattr(S, "H", f)
+    srv = _server(int(2.5 * BYTES))
+    dts = {"A": 0.5, "B": 0.25, "C": 0.125}
+    for k, dt in dts.items():
+        srv.register(k, _spec(dt))
+    try:
+        for k in ("A", "B", "C", "A", "B"):
+            srv.submit(k).result(30)
+        assert f.offloads >= 2 and srv.evictions == f.offloads
+        assert all(srv.setups(k) == 1 for k in dts)  # never factored twice
+        assert srv.reload_count("A") == 1
+        steps = {"A": 2, "B": 2, "C": 1}
+        for k, dt in dts.items():
+            assert np.all(srv.state(k) == _expected(dt, steps[k])), k
+        assert f.live == 3  # offloaded handles are kept
+    finally:
+        srv.close()
+    assert f.live == 0
