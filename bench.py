@@ -71,6 +71,12 @@ def _args():
                    help="states of the benchmark operator stepped together by cn_step_multi (0: skip)")
     p.add_argument("--serving-ops", type=int, default=16,
                    help="resident operators of the serving measurement (0: skip)")
+    p.add_argument("--serving-full", action="store_true",
+                   help="also serve the full mix: 48 2D (255^2..2047^2) and 16 3D (63^3..127^3) operators "
+                        "under an HBM budget, loads 10..1e4 steps/s (several minutes of setups)")
+    p.add_argument("--serving-budget-gb", type=float, default=100.0)
+    p.add_argument("--serving-seconds", type=float, default=5.0,
+                   help="seconds of arrivals per load point of the full serving mix")
     p.add_argument("--cpu-sample", type=int, default=0, help=argparse.SUPPRESS)
     p.add_argument("--cpu-sample-steps", type=int, default=0, help=argparse.SUPPRESS)
     p.add_argument("--cpu-sample-procs", type=int, default=1, help=argparse.SUPPRESS)
@@ -474,6 +480,7 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
     serving = None
     if args.serving_ops > 0:
         serving = run_serving(args, local, W, np)
+    serving_full = run_serving_full(args, local, W, np) if args.serving_full else None
 
     # ---- max over ranks
     t_ms, e2e_ms, t64_ms = max_over_ranks([t_ms, e2e_ms, t64_ms], dist, dev)
@@ -579,6 +586,7 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
         "batched": batched,
         "heat3d": heat3d,
         "serving": serving,
+        "serving_full": serving_full,
     }
     return line
 
@@ -609,8 +617,8 @@ def run_serving(args, device_index, W, np) -> dict:
     t_admit = time.perf_counter() - t0
     loads = []
     rnd = random.Random(7)
-    for lam in (100.0, 300.0, 1000.0, 3000.0):
-        nreq = int(min(2.0 * lam, 3000))
+    for lam in (10.0, 30.0, 100.0, 300.0, 1000.0, 3000.0, 10000.0):
+        nreq = int(min(max(20.0, 2.0 * lam), 3000))
         arrivals = np.cumsum(rng.exponential(1.0 / lam, size=nreq))
         futs = []
         start = time.perf_counter()
@@ -697,6 +705,82 @@ def multi_vs_single(H, torch, h, u, k: int, reps: int = 2) -> dict:
             "multi_iters_per_step": round(sum(its_m) / n, 3),
             "single_iters_per_step": round(sum(its_s) / n, 3),
             "api": "cn_step_multi (k states, one hif_apply_multi per PCG iteration) vs k cn_step calls"}
+
+
+def _pct(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    return xs[min(len(xs) - 1, max(0, int(math.ceil(q / 100 * len(xs))) - 1))]
+
+
+def run_serving_full(args, device_index, W, np) -> dict:
+    """Serving the full mix (48 2D operators of 255^2..2047^2 and 16 3D of
+    63^3..127^3, FP32 factors with the FP64 copy released, FP64 CG) under an
+    HBM budget smaller than the mix: evicted operators are offloaded to host
+    memory and reloaded.  2D and 3D operators are served in separate lanes
+    (threads and streams), so the 3D steps do not hold back the 2D ones.
+    Open-loop Poisson arrivals at 10 .. 1e4 steps/s, the operator of each
+    request drawn uniformly; latency = arrival to result ready."""
+    import random
+    import paper_2004_05566_gb300.serve as S
+
+    budget = int(args.serving_budget_gb * (1 << 30))
+    srv = S.CNServer(hbm_budget_bytes=budget, device=device_index, lanes=[0])
+    ws = W.config_serving()
+    ids = list(range(len(ws)))
+    for i, w in zip(ids, ws):
+        srv.register(i, S.OperatorSpec(w.dim, w.n, w.leaf, w.a_nodes, w.dt, w.eps, w.u0, w.reaction,
+                                       lane=1 if w.dim == 3 else 0))
+    t0 = time.perf_counter()
+    setup_s = {}
+    for i in ids:  # admission (factorization) of every operator, one at a time
+        t1 = time.perf_counter()
+        srv.submit(i).result()
+        setup_s[i] = time.perf_counter() - t1
+    t_admit = time.perf_counter() - t0
+    rng = np.random.default_rng(2100)
+    rnd = random.Random(11)
+    loads = []
+    for lam in (10.0, 30.0, 100.0, 300.0, 1000.0, 3000.0, 10000.0):
+        nreq = int(min(max(20, lam * args.serving_seconds), 5000))
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, size=nreq))
+        ev0, rl0 = srv.evictions, srv.reloads
+        futs, dims = [], []
+        start = time.perf_counter()
+        for t_a in arrivals:
+            delay = start + t_a - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            oid = rnd.choice(ids)
+            futs.append(srv.submit(oid))
+            dims.append(ws[oid].dim)
+        res = [f.result() for f in futs]
+        end = time.perf_counter()
+        lat = [r.latency_s * 1e3 for r in res]
+        l2 = [x for x, d in zip(lat, dims) if d == 2]
+        l3 = [x for x, d in zip(lat, dims) if d == 3]
+        loads.append({"offered_steps_per_s": lam, "requests": nreq,
+                      "achieved_steps_per_s": round(nreq / (end - start), 1),
+                      "p50_ms": round(_pct(lat, 50), 3), "p99_ms": round(_pct(lat, 99), 3),
+                      "p50_ms_2d": round(_pct(l2, 50), 3) if l2 else None,
+                      "p99_ms_2d": round(_pct(l2, 99), 3) if l2 else None,
+                      "p50_ms_3d": round(_pct(l3, 50), 3) if l3 else None,
+                      "p99_ms_3d": round(_pct(l3, 99), 3) if l3 else None,
+                      "mean_batch": round(sum(r.batch_size for r in res) / len(res), 2),
+                      "evictions": srv.evictions - ev0, "reloads": srv.reloads - rl0})
+    sizes = [(w.dim, w.n - 1) for w in ws]
+    out = {"operators": len(ws), "sizes": {"2d": sorted(s for d, s in sizes if d == 2),
+                                           "3d": sorted(s for d, s in sizes if d == 3)},
+           "hbm_budget_gb": args.serving_budget_gb, "admission_s": round(t_admit, 1),
+           "setup_s_max": round(max(setup_s.values()), 2),
+           "resident_bytes_end": srv.resident_bytes(), "evictions_total": srv.evictions,
+           "reloads_total": srv.reloads, "seconds_per_load": args.serving_seconds, "loads": loads,
+           "scheduler": "two lanes (2D, 3D) of step-level continuous batching over cn_step_batched; "
+                        "eviction offloads the factor to host memory (hif_offload), re-admission "
+                        "reloads it (hif_reload); FP64 factor copy released after the setup"}
+    srv.close()
+    return out
 
 
 def run_heat3d(args, dev, H, W, np, torch) -> dict:

@@ -214,6 +214,33 @@ def config_batched(count: int = 256, seed0: int = 1000, lo: float = 63, hi: floa
     return out
 
 
+def config_serving(count2d: int = 48, count3d: int = 16, seed0: int = 2000):
+    """Serving mix of resident operators: 2D operators with side log-uniform in
+    [255, 2047] (snapped, leaf 16) and 3D operators with side drawn uniformly
+    from {63, 95, 127} (snapped: leaf 8, 12, 8); operator i uses seed
+    seed0 + i.  Lognormal a (GRF corr 0.05, contrast 1e3), dt log-uniform in
+    [1e-2, 1], r = u(1-u), the bump u0; eps 1e-6 in 2D and 1e-4 in 3D (the
+    3D benchmark's tolerance)."""
+    out = []
+    for i in range(count2d + count3d):
+        rng = np.random.default_rng(seed0 + i)
+        if i < count2d:
+            dim = 2
+            side = math.exp(rng.uniform(math.log(255), math.log(2047)))
+            n, m, L = snap_side(side, leafs=(16,))
+            eps = 1e-6
+        else:
+            dim = 3
+            side = float(rng.choice([63, 95, 127]))
+            n, m, L = snap_side(side, leafs=(8, 12))
+            eps = 1e-4
+        a = lognormal_coefficient(grf(rng, n, dim, 0.05), 1e3)
+        dt = math.exp(rng.uniform(math.log(1e-2), math.log(1.0)))
+        out.append(Workload(f"serving_{i}", dim, n, m, L, dt, eps, a, gaussian_bump_u0(n, dim),
+                            (1, 1.0, 1.0), steps=1, meta={"side_drawn": side}))
+    return out
+
+
 def small_variable_2d(n: int = 32, m: int = 8, seed: int = 7, contrast: float = 1e2,
                       dt: float = 1.0, eps: float = 1e-6, dim: int = 2,
                       corr_len: float = 0.1) -> Workload:
