@@ -77,6 +77,9 @@ def _args():
     p.add_argument("--serving-budget-gb", type=float, default=100.0)
     p.add_argument("--serving-seconds", type=float, default=5.0,
                    help="seconds of arrivals per load point of the full serving mix")
+    p.add_argument("--profile-multi", type=int, default=0,
+                   help="profiling run: hif_apply_multi (16 columns, six calls) on a 3D operator with "
+                        "this many grid intervals per axis (leaf 8, BF16 top levels); prints per-kernel times")
     p.add_argument("--cpu-sample", type=int, default=0, help=argparse.SUPPRESS)
     p.add_argument("--cpu-sample-steps", type=int, default=0, help=argparse.SUPPRESS)
     p.add_argument("--cpu-sample-procs", type=int, default=1, help=argparse.SUPPRESS)
@@ -738,12 +741,16 @@ def run_serving_full(args, device_index, W, np) -> dict:
         t1 = time.perf_counter()
         srv.submit(i).result()
         setup_s[i] = time.perf_counter() - t1
+        print(f"serving_full: admitted {i} ({ws[i].dim}D n={ws[i].n} leaf={ws[i].leaf}) in "
+              f"{setup_s[i]:.2f} s, resident {srv.resident_bytes() / 2**30:.1f} GiB, "
+              f"evictions {srv.evictions}", file=sys.stderr, flush=True)
     t_admit = time.perf_counter() - t0
     rng = np.random.default_rng(2100)
     rnd = random.Random(11)
     loads = []
     for lam in (10.0, 30.0, 100.0, 300.0, 1000.0, 3000.0, 10000.0):
         nreq = int(min(max(20, lam * args.serving_seconds), 5000))
+        print(f"serving_full: load {lam} steps/s, {nreq} requests", file=sys.stderr, flush=True)
         arrivals = np.cumsum(rng.exponential(1.0 / lam, size=nreq))
         ev0, rl0 = srv.evictions, srv.reloads
         futs, dims = [], []
@@ -935,8 +942,38 @@ def run_reference(args) -> dict:
                     "d2h_bytes_per_step": 0}}
 
 
+def profile_multi(n: int) -> dict:
+    """hif_apply_multi on a 3D n^3-interval operator (leaf 8, eps 1e-4, lognormal
+    a, HIF_FP32_BF16TOP), 16 columns: three warm-up calls, then three calls with
+    per-kernel statistics (a capture target for ncu on the tensor-core kernel)."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2004_05566_gb300.hifcn as H
+    import workloads as W
+    w = W.small_variable_2d(n=n, m=8, dim=3, eps=1e-4, contrast=1e3, dt=0.1, corr_len=0.05, seed=2)
+    h = H.hif_setup(3, n, 8, torch.from_numpy(w.a_nodes).cuda(), w.dt,
+                    H.default_options(eps=1e-4, precision=H.HIF_FP32_BF16TOP, cg_tol=1e-10))
+    X = torch.from_numpy(np.random.default_rng(0).standard_normal((16, w.N))).cuda()
+    for _ in range(3):
+        H.hif_apply_multi(h, X)
+    torch.cuda.synchronize()
+    H.hif_stats_enable(h, True)
+    for _ in range(3):
+        H.hif_apply_multi(h, X)
+    st = H.hif_stats_read(h)
+    h.close()
+    return {"profile": "hif_apply_multi", "n": n, "k": 16,
+            "kernels_us_per_launch": {s["name"]: round(1e3 * s["ms"] / s["launches"], 1)
+                                      for s in sorted(st, key=lambda s: -s["ms"])}}
+
+
 def main():
     args = _args()
+    if args.profile_multi:
+        print(json.dumps(profile_multi(args.profile_multi)))
+        return
     if args.cpu_sample:
         r = oracle_sample(args.cpu_sample, args.cpu_sample_steps, args.warmup, args.eps,
                           args.cpu_sample_procs)

@@ -51,8 +51,20 @@ constexpr long long kMmaWaitLimit = 1LL << 24;
 
 enum MPhase { kMCellFwd = 0, kMCellBwd, kMGroupFwd, kMGroupBwd, kMRootRows, kMRootCols };
 
+// One CTA's work: rows [r0, r0 + 128) of a box, K chunks [c0, c1).  When a
+// box's K is split over several CTAs (poff >= 0) each writes its partial tile
+// (128 rows of npad floats) to the scratch at poff, and k_box_reduce adds the
+// splits in order; otherwise (poff < 0) the CTA stores the results itself.
 struct MTile {
-  int unit, r0;
+  int unit, r0, c0, c1;
+  long long poff;
+};
+// floats of one partial tile (any k up to kMultiMaxCols)
+constexpr long long kPartTile = (long long)kTM * kMultiMaxCols;
+// a tile whose K was split: nks partial tiles at poff, poff + kPartTile, ...
+struct RTile {
+  int unit, r0, nks, pad;
+  long long poff;
 };
 
 struct MArgs {
@@ -68,6 +80,7 @@ struct MArgs {
   int ncols, npad;          // right-hand sides, and N of the MMA (ncols rounded up to 16)
   float *x, *xI, *contrib, *gs, *rt;
   long long ldx, ldc, ldg, ldr;  // column strides of x / xI, contrib, gs, rt
+  float *part;                   // partial tiles of split boxes
   double *err;
 };
 
@@ -306,7 +319,7 @@ __global__ void __launch_bounds__(kMThreads) k_box_mma(MArgs a, int ph) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s_tmem;
-  const int nch = (bx.K + kKC - 1) / kKC;
+  const int nch = tile.c1 - tile.c0;  // chunks of this CTA (K chunks [c0, c1))
   const uint32_t idesc = mma_idesc(kTM, npad);
   bool ok = true;
   for (int c = 0; c < nch; ++c) {
@@ -314,8 +327,9 @@ __global__ void __launch_bounds__(kMThreads) k_box_mma(MArgs a, int ph) {
     if (c >= 2 && !mbar_wait_bounded(su32(&s_bar[b]), (uint32_t)(((c - 2) >> 1) & 1))) ok = false;
     if (!ok) s_fail = 1;  // benign race: every writer stores 1
     if (ok) {
-      stage_a(a, ph, tile.unit, bx, tile.r0, c * kKC, sA[b]);
-      stage_b(a, ph, tile.unit, bx, c * kKC, sBh[b], sBl[b], lboB);
+      const int k0 = (tile.c0 + c) * kKC;
+      stage_a(a, ph, tile.unit, bx, tile.r0, k0, sA[b]);
+      stage_b(a, ph, tile.unit, bx, k0, sBh[b], sBl[b], lboB);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -363,12 +377,23 @@ __global__ void __launch_bounds__(kMThreads) k_box_mma(MArgs a, int ph) {
           : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
           : "r"(ta));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (tile.poff >= 0) {  // partial tile of a split box
+        float *pt = a.part + tile.poff + (long long)(warp * 32 + lane) * npad + c0;
 #pragma unroll
-      for (int j = 0; j < 8; ++j) store_out(a, ph, tile.unit, bx, row, c0 + j, __uint_as_float(r[j]));
+        for (int j = 0; j < 8; ++j) pt[j] = __uint_as_float(r[j]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) store_out(a, ph, tile.unit, bx, row, c0 + j, __uint_as_float(r[j]));
+      }
     }
   } else if (ok) {  // K = 0: the product is zero
     const int row = tile.r0 + warp * 32 + lane;
-    for (int n = 0; n < a.ncols; ++n) store_out(a, ph, tile.unit, bx, row, n, 0.f);
+    if (tile.poff >= 0) {
+      float *pt = a.part + tile.poff + (long long)(warp * 32 + lane) * npad;
+      for (int n = 0; n < npad; ++n) pt[n] = 0.f;
+    } else {
+      for (int n = 0; n < a.ncols; ++n) store_out(a, ph, tile.unit, bx, row, n, 0.f);
+    }
   } else if (t == 0) {
     a.err[0] = 1.0;
   }
@@ -376,6 +401,19 @@ __global__ void __launch_bounds__(kMThreads) k_box_mma(MArgs a, int ph) {
   __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncol_alloc) : "memory");
+}
+
+// the split boxes: rows of a tile added over its K splits in order, then stored
+__global__ void __launch_bounds__(kTM) k_box_reduce(MArgs a, int ph, const RTile *__restrict__ rt) {
+  const RTile r = rt[blockIdx.x];
+  const Box bx = box_of(a, ph, r.unit);
+  const int row = threadIdx.x;
+  const long long stride = kPartTile;
+  for (int n = 0; n < a.ncols; ++n) {
+    float y = 0.f;
+    for (int k = 0; k < r.nks; ++k) y += a.part[r.poff + k * stride + (long long)row * a.npad + n];
+    store_out(a, ph, r.unit, bx, r.r0 + row, n, y);
+  }
 }
 
 // entity inputs of a level for all columns: gs_c[goff_g + i] = x_c[g_i]
@@ -414,6 +452,16 @@ __global__ void k_cols_to_double(const float *__restrict__ X, double *__restrict
 
 }  // namespace
 
+// The CTAs of one phase (tiles, possibly split along K) and the tiles to
+// reduce afterwards (device arrays).
+struct PhaseWork {
+  MTile *tiles = nullptr;
+  int ntiles = 0;
+  RTile *rtiles = nullptr;
+  int nrtiles = 0;
+  long long part_floats = 0;
+};
+
 // Per-handle state of the multi-column apply (built on first use).
 struct MultiState {
   int cap = 0;  // columns the buffers hold
@@ -424,12 +472,13 @@ struct MultiState {
   double *scal = nullptr, *part = nullptr;
   unsigned *tk = nullptr;
   long long ldc = 0, ldg = 0, ldr = 0;
-  // per top level: tiles of the four phases, per-entity gs offsets
-  std::vector<MTile *> t_cf, t_cb, t_gf, t_gb;
-  std::vector<int> n_cf, n_cb, n_gf, n_gb;
+  // per top level: the work of the cell forward, cell backward and entity
+  // phases (the entity forward and backward share theirs), per-entity gs
+  // offsets; the root's (rows and columns share it)
+  std::vector<PhaseWork> cf, cb, grp;
   std::vector<long long *> goff;
-  MTile *t_root = nullptr;
-  int n_root = 0;
+  PhaseWork root;
+  float *tpart = nullptr;  // partial tiles of split boxes (largest phase)
 };
 
 void destroy_multi_state(Handle *h) {
@@ -440,11 +489,49 @@ void destroy_multi_state(Handle *h) {
 
 namespace {
 
-int upload_tiles(Handle *h, const std::vector<MTile> &v, MTile **out) {
+template <typename T>
+int upload_vec(Handle *h, const std::vector<T> &v, T **out) {
   *out = nullptr;
   if (v.empty()) return HIF_OK;
-  HIF_TRY(dev_alloc(h, (void **)out, v.size() * sizeof(MTile)));
-  HIF_CUDA_TRY(cudaMemcpy(*out, v.data(), v.size() * sizeof(MTile), cudaMemcpyHostToDevice));
+  HIF_TRY(dev_alloc(h, (void **)out, v.size() * sizeof(T)));
+  HIF_CUDA_TRY(cudaMemcpy(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return HIF_OK;
+}
+
+// CTAs of a phase whose boxes have (m, K) = sizes[u]: every 128-row tile; a
+// phase with few tiles splits K so that about kTargetCtas CTAs run (at least
+// 4 chunks per split), the splits of a tile adding up in k_box_reduce.
+int build_phase(Handle *h, const std::vector<int2> &sizes, PhaseWork *w) {
+  constexpr int kTargetCtas = 3 * 152;
+  long long T = 0;
+  for (const int2 &mk : sizes) T += (mk.x + kTM - 1) / kTM;
+  const int ks = (int)std::max<long long>(1, std::min<long long>(16, (kTargetCtas + T - 1) / std::max<long long>(T, 1)));
+  std::vector<MTile> tiles;
+  std::vector<RTile> rts;
+  long long poff = 0;
+  for (int u = 0; u < (int)sizes.size(); ++u) {
+    const int m = sizes[u].x, K = sizes[u].y;
+    const int nch = (K + kKC - 1) / kKC;
+    int nks = std::max(1, std::min(ks, nch / 4));
+    const int cps = nks > 1 ? (nch + nks - 1) / nks : nch;
+    nks = nks > 1 ? (nch + cps - 1) / cps : 1;
+    for (int r = 0; r < m; r += kTM) {
+      if (nks == 1) {
+        tiles.push_back({u, r, 0, nch, -1});
+        continue;
+      }
+      rts.push_back({u, r, nks, 0, poff});
+      for (int k = 0; k < nks; ++k) {
+        tiles.push_back({u, r, k * cps, std::min(nch, (k + 1) * cps), poff});
+        poff += kPartTile;
+      }
+    }
+  }
+  HIF_TRY(upload_vec(h, tiles, &w->tiles));
+  HIF_TRY(upload_vec(h, rts, &w->rtiles));
+  w->ntiles = (int)tiles.size();
+  w->nrtiles = (int)rts.size();
+  w->part_floats = poff;
   return HIF_OK;
 }
 
@@ -456,46 +543,36 @@ int build_multi_state(Handle *h, int k) {
     M = new MultiState();
     h->multi = M;
     const int L = h->L, lb = std::min(h->bf16_lb, L);
-    M->t_cf.assign(L, nullptr);
-    M->t_cb.assign(L, nullptr);
-    M->t_gf.assign(L, nullptr);
-    M->t_gb.assign(L, nullptr);
-    M->n_cf.assign(L, 0);
-    M->n_cb.assign(L, 0);
-    M->n_gf.assign(L, 0);
-    M->n_gb.assign(L, 0);
+    M->cf.assign(L, PhaseWork{});
+    M->cb.assign(L, PhaseWork{});
+    M->grp.assign(L, PhaseWork{});
     M->goff.assign(L, nullptr);
-    long long gsz = 0;
+    long long gsz = 0, part = 0;
     for (int l = lb; l < L; ++l) {
       const LevelHost &H = h->lv_host[l];
-      std::vector<MTile> cf, cb, gt;
-      for (int c = 0; c < (int)H.cells.size(); ++c) {
-        const CellDesc &d = H.cells[c];
-        for (int r = 0; r < d.nI + d.nB; r += kTM) cf.push_back({c, r});
-        for (int r = 0; r < d.nI; r += kTM) cb.push_back({c, r});
+      std::vector<int2> cf, cb, gr;
+      for (const CellDesc &d : H.cells) {
+        cf.push_back(make_int2(d.nI + d.nB, d.nI));
+        cb.push_back(make_int2(d.nI, d.nI + d.nB));
       }
       std::vector<long long> off(std::max<size_t>(1, H.groups.size()), 0);
       long long o = 0;
       for (int g = 0; g < (int)H.groups.size(); ++g) {
         off[g] = o;
         o += pad4(H.groups[g].n);
-        for (int r = 0; r < H.groups[g].n; r += kTM) gt.push_back({g, r});
+        gr.push_back(make_int2(H.groups[g].n, H.groups[g].n));
       }
       gsz = std::max(gsz, o);
-      HIF_TRY(upload_tiles(h, cf, &M->t_cf[l]));
-      HIF_TRY(upload_tiles(h, cb, &M->t_cb[l]));
-      HIF_TRY(upload_tiles(h, gt, &M->t_gf[l]));
-      M->t_gb[l] = M->t_gf[l];
-      M->n_cf[l] = (int)cf.size();
-      M->n_cb[l] = (int)cb.size();
-      M->n_gf[l] = M->n_gb[l] = (int)gt.size();
+      HIF_TRY(build_phase(h, cf, &M->cf[l]));
+      HIF_TRY(build_phase(h, cb, &M->cb[l]));
+      HIF_TRY(build_phase(h, gr, &M->grp[l]));
+      part = std::max({part, M->cf[l].part_floats, M->cb[l].part_floats, M->grp[l].part_floats});
       HIF_TRY(dev_alloc(h, (void **)&M->goff[l], off.size() * sizeof(long long)));
       HIF_CUDA_TRY(cudaMemcpy(M->goff[l], off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice));
     }
-    std::vector<MTile> rt;
-    for (int r = 0; r < h->root_n; r += kTM) rt.push_back({0, r});
-    HIF_TRY(upload_tiles(h, rt, &M->t_root));
-    M->n_root = (int)rt.size();
+    if (h->root_n > 0) HIF_TRY(build_phase(h, {make_int2(h->root_n, h->root_n)}, &M->root));
+    part = std::max(part, M->root.part_floats);
+    HIF_TRY(dev_alloc(h, (void **)&M->tpart, (size_t)std::max<long long>(part, 4) * sizeof(float)));
     M->ldg = std::max<long long>(gsz, 4);
   }
   M->ldc = std::max<long long>(h->max_contrib, 4);
@@ -510,12 +587,12 @@ int build_multi_state(Handle *h, int k) {
   return HIF_OK;
 }
 
-int launch_mma(Handle *h, MultiState *M, int ph, int level, const MTile *tiles, int ntiles, int k,
-               cudaStream_t s) {
-  if (ntiles <= 0) return HIF_OK;
+int launch_mma(Handle *h, MultiState *M, int ph, int level, const PhaseWork &w, int k, cudaStream_t s) {
+  if (w.ntiles <= 0) return HIF_OK;
   const LevelDev *lv = level >= 0 ? &h->lv[level] : nullptr;
   MArgs a{};
-  a.tiles = tiles;
+  a.tiles = w.tiles;
+  a.part = M->tpart;
   a.cells = lv ? lv->cells : nullptr;
   a.groups = lv ? lv->groups : nullptr;
   a.idx = h->idx;
@@ -542,8 +619,12 @@ int launch_mma(Handle *h, MultiState *M, int ph, int level, const MTile *tiles, 
                   : ph == kMGroupFwd ? "mma_group_fwd" : ph == kMGroupBwd ? "mma_group_bwd"
                   : ph == kMRootRows ? "mma_root_rows" : "mma_root_cols",
                level, 0.0, s);
-  k_box_mma<<<ntiles, kMThreads, sm, s>>>(a, ph);
+  k_box_mma<<<w.ntiles, kMThreads, sm, s>>>(a, ph);
   note_launch();
+  if (w.nrtiles > 0) {
+    k_box_reduce<<<w.nrtiles, kTM, 0, s>>>(a, ph, w.rtiles);
+    note_launch();
+  }
   HIF_CUDA_TRY(cudaGetLastError());
   return HIF_OK;
 }
@@ -600,18 +681,18 @@ int apply_multi_f32(Handle *h, int k, cudaStream_t s) {
   for (int c = 0; c < k; ++c)
     HIF_TRY(apply_levels_f32_range(h, h->f32.contrib, M->xI + c * N, M->x + c * N, 0, lb, true, s));
   for (int l = lb; l < L; ++l) {
-    HIF_TRY(launch_mma(h, M, kMCellFwd, l, M->t_cf[l], M->n_cf[l], k, s));
+    HIF_TRY(launch_mma(h, M, kMCellFwd, l, M->cf[l], k, s));
     HIF_TRY(launch_gather(h, M, l, true, k, s));
-    HIF_TRY(launch_mma(h, M, kMGroupFwd, l, M->t_gf[l], M->n_gf[l], k, s));
+    HIF_TRY(launch_mma(h, M, kMGroupFwd, l, M->grp[l], k, s));
   }
   if (h->root_n > 0) {
-    HIF_TRY(launch_mma(h, M, kMRootRows, -1, M->t_root, M->n_root, k, s));
-    HIF_TRY(launch_mma(h, M, kMRootCols, -1, M->t_root, M->n_root, k, s));
+    HIF_TRY(launch_mma(h, M, kMRootRows, -1, M->root, k, s));
+    HIF_TRY(launch_mma(h, M, kMRootCols, -1, M->root, k, s));
   }
   for (int l = L - 1; l >= lb; --l) {
     HIF_TRY(launch_gather(h, M, l, false, k, s));
-    HIF_TRY(launch_mma(h, M, kMGroupBwd, l, M->t_gb[l], M->n_gb[l], k, s));
-    HIF_TRY(launch_mma(h, M, kMCellBwd, l, M->t_cb[l], M->n_cb[l], k, s));
+    HIF_TRY(launch_mma(h, M, kMGroupBwd, l, M->grp[l], k, s));
+    HIF_TRY(launch_mma(h, M, kMCellBwd, l, M->cb[l], k, s));
   }
   for (int c = 0; c < k; ++c)
     HIF_TRY(apply_levels_f32_range(h, h->f32.contrib, M->xI + c * N, M->x + c * N, 0, lb, false, s));

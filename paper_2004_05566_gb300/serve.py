@@ -236,6 +236,7 @@ class CNServer:
             self._resident_bytes -= res.bytes
             self.evictions += 1
             self._busy.discard(oid)
+            self._cv.notify_all()  # a lane may be waiting for this operator
         return True
 
     def _admit(self, oid, keep: set) -> None:
@@ -276,14 +277,15 @@ class CNServer:
     def _take_batch(self, lane: int) -> list:
         """Pending requests of a lane, at most one per operator (the rest stay
         queued).  Cancelled requests are dropped; the ones taken are marked
-        running and their operators busy."""
+        running and their operators busy.  An operator that is busy (being
+        evicted by another lane) keeps its requests queued."""
         pend = self._pending[lane]
         batch, seen, rest = [], set(), collections.deque()
         while pend and len(batch) < self.max_batch:
             r = pend.popleft()
             if r.future.cancelled():
                 continue
-            if r.op_id in seen:
+            if r.op_id in seen or r.op_id in self._busy:
                 rest.append(r)
             elif r.future.set_running_or_notify_cancel():
                 seen.add(r.op_id)
@@ -322,6 +324,8 @@ class CNServer:
                 if self._stop and not pend:
                     return
                 batch = self._take_batch(lane)
+                if not batch and pend:  # only operators that another lane is evicting
+                    self._cv.wait(0.001)
             if not batch:  # everything taken was cancelled
                 continue
             try:

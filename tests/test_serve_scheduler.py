@@ -264,3 +264,40 @@ def test_eviction_offloads_and_readmission_reloads(monkeypatch):
     finally:
         srv.close()
     assert f.live == 0
+
+
+class _SlowOffloadBinding(_OffloadBinding):
+    """Offload takes a while, so another lane's request for the operator being
+    evicted arrives while the eviction runs."""
+
+    def __init__(self):
+        super().__init__()
+        self.offloading = threading.Event()
+
+    def hif_offload(self, h):
+        self.offloading.set()
+        import time
+        time.sleep(0.3)
+        super().hif_offload(h)
+
+
+def test_lane_waits_for_an_eviction_by_another_lane(monkeypatch):
+    """Lane 1's admission evicts lane 0's idle operator; a request for that
+    operator arriving during the eviction waits for it to finish and then
+    reloads the operator (it is never stepped half-evicted)."""
+    f = _SlowOffloadBinding()
+    monkeypatch.setattr(S, "H", f)
+    srv = _server(int(1.5 * BYTES), lanes=[100])
+    srv.register("small", _spec(0.5))          # lane 0
+    srv.register("big", _spec(0.75, n=16))     # lane 1
+    try:
+        assert srv.submit("small").result(30).step == 1
+        fb = srv.submit("big")                 # admission evicts "small" (slowly)
+        assert f.offloading.wait(30)
+        fs = srv.submit("small")               # arrives during the eviction
+        assert fb.result(30).step == 1
+        assert fs.result(30).step == 2         # stepped after the eviction, reloaded
+        assert srv.reload_count("small") == 1
+        assert np.all(srv.state("small") == _expected(0.5, 2))
+    finally:
+        srv.close()
