@@ -51,3 +51,49 @@ def test_gpu_counts_match_printed(H, ex, dim):
         printed = _printed_smallest(ex, dim, eps)
         assert abs(got[eps] - printed) <= WINDOW, (ex, dim, eps, got[eps], printed)
     assert got[1e-6] < got[1e-3]
+
+
+def _printed_at(ex, dim, eps, side):
+    from test_oracle_paper_counts import _load
+    rows = [r for r in _load() if r[:4] == (ex, dim, eps, side)]
+    assert len(rows) == 1
+    return rows[0][4]
+
+
+TABLE_STEPS = 10
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("side", [1023, 2047, 4095])
+@pytest.mark.parametrize("ex", ["heat", "logistic"])
+def test_gpu_counts_at_table_sizes(H, ex, side):
+    """The table sizes themselves (2D, leaf 16, FP64 factor and CG, tolerance
+    1e-12, the paper's recipes): the mean count over the first 10 steps lies
+    within 1.5 of the count printed for that size, eps = 1e-6 below 1e-3."""
+    import workloads as W
+    n = side + 1
+    gen = W.paper_heat2d if ex == "heat" else W.paper_logistic2d
+    got = {}
+    for eps in (1e-3, 1e-6):
+        w = gen(n, 16, eps, seed=0)
+        w.steps = TABLE_STEPS
+        got[eps] = _gpu_mean_iters_n(H, w, TABLE_STEPS)
+        printed = _printed_at(ex, 2, eps, side)
+        print(f"{ex} {side}^2 eps {eps:g}: GPU mean {got[eps]:.2f}, printed {printed}")
+        assert abs(got[eps] - printed) <= WINDOW, (ex, side, eps, got[eps], printed)
+    assert got[1e-6] < got[1e-3]
+
+
+def _gpu_mean_iters_n(H, w, steps):
+    import torch
+    a = torch.from_numpy(w.a_nodes).cuda()
+    opt = H.default_options(eps=w.eps, precision=0, cg_tol=w.tol)
+    h = H.hif_setup(w.dim, w.n, w.leaf, a, w.dt, opt)
+    kind, k1, k2 = w.reaction
+    if kind:
+        H.hif_set_reaction(h, kind, k1, k2)
+    u = torch.from_numpy(w.u0.ravel().copy()).cuda()
+    its = H.cn_steps(h, u, steps)
+    assert np.isfinite(u.cpu().numpy()).all()
+    h.close()
+    return float(np.mean(its))
