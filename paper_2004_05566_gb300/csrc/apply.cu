@@ -2789,13 +2789,15 @@ int launch_flow(Handle *h, const FactorValues<T> &fv, T *x, cudaStream_t s) {
 // Plan of the fused upper-level sweep: which levels it covers (the top levels
 // whose factor data is small, so that a launch per step would cost more than
 // the step), its phases and their work units, and its launch shape per
-// precision.  HIFCN_NO_FUSED=1 keeps one launch per step (A/B measurement).
+// precision.  Built only with HIFCN_FUSED=1: with the prologues of the level
+// kernels, one launch per step measured faster (2D 1023^2: 0.374 against
+// 0.382 ms per CG iteration).
 int build_upper_plan(Handle *h) {
   h->use_upper = false;
   HIF_TRY(build_flow_plan(h));
   if (h->use_flow) return HIF_OK;
-  const char *off = std::getenv("HIFCN_NO_FUSED");
-  if (off && off[0] == '1') return HIF_OK;
+  const char *on = std::getenv("HIFCN_FUSED");
+  if (!(on && on[0] == '1')) return HIF_OK;
   if (h->root_split) return HIF_OK;  // a large root is spread over the whole GPU
   const int L = h->L;
   // FP32 value bytes of a fused level, in MB: one cluster streams only a few

@@ -44,7 +44,8 @@ using bf16 = __nv_bfloat16;
 
 constexpr int kTM = 128;      // rows of a tile (M of the MMA)
 constexpr int kKC = 64;       // K of a staged chunk (4 MMAs of K = 16)
-constexpr int kMThreads = 128;
+constexpr int kMThreads = 256;   // 8 warps stage; warp w reads TMEM lanes 32 (w % 4)..
+constexpr int kMStages = 3;      // staged chunks in flight
 constexpr uint32_t kSbo = 128;               // bytes between core matrices along M / N
 constexpr uint32_t kLboA = 16 * 128 + 16;    // bytes between core matrices along K (A), padded
 constexpr long long kMmaWaitLimit = 1LL << 24;
@@ -282,16 +283,16 @@ __device__ __forceinline__ void store_out(const MArgs &a, int ph, int unit, cons
   }
 }
 
-// Dynamic shared memory: 2 x A chunk, 2 x (X_hi, X_lo) chunk.
+// Dynamic shared memory: kMStages x (A chunk, X_hi chunk, X_lo chunk).
 __host__ __device__ constexpr size_t a_chunk_bytes() { return (size_t)(kKC / 8) * kLboA; }
 __host__ __device__ inline uint32_t b_lbo(int npad) { return (uint32_t)(npad / 8) * kSbo; }
 __host__ __device__ inline size_t b_chunk_bytes(int npad) { return (size_t)(kKC / 8) * b_lbo(npad); }
-inline size_t mma_smem_bytes(int npad) { return 2 * a_chunk_bytes() + 4 * b_chunk_bytes(npad); }
+inline size_t mma_smem_bytes(int npad) { return kMStages * (a_chunk_bytes() + 2 * b_chunk_bytes(npad)); }
 
-__global__ void __launch_bounds__(kMThreads) k_box_mma(MArgs a, int ph) {
+__global__ void __launch_bounds__(kMThreads, 2) k_box_mma(MArgs a, int ph) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ uint32_t s_tmem;
-  __shared__ __align__(8) unsigned long long s_bar[2];
+  __shared__ __align__(8) unsigned long long s_bar[kMStages];
   __shared__ int s_fail;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const MTile tile = a.tiles[blockIdx.x];
@@ -299,10 +300,7 @@ __global__ void __launch_bounds__(kMThreads) k_box_mma(MArgs a, int ph) {
   const int npad = a.npad;
   const uint32_t ncol_alloc = npad <= 32 ? 32u : (npad <= 64 ? 64u : 128u);
   const uint32_t lboB = b_lbo(npad);
-  unsigned char *sA[2] = {smem, smem + a_chunk_bytes()};
-  unsigned char *sB = smem + 2 * a_chunk_bytes();
-  unsigned char *sBh[2] = {sB, sB + 2 * b_chunk_bytes(npad)};
-  unsigned char *sBl[2] = {sB + b_chunk_bytes(npad), sB + 3 * b_chunk_bytes(npad)};
+  const size_t stage_bytes = a_chunk_bytes() + 2 * b_chunk_bytes(npad);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&s_tmem)),
                  "r"(ncol_alloc)
@@ -310,8 +308,8 @@ __global__ void __launch_bounds__(kMThreads) k_box_mma(MArgs a, int ph) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (t == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&s_bar[0])) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&s_bar[1])) : "memory");
+    for (int b = 0; b < kMStages; ++b)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&s_bar[b])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_fail = 0;
   }
@@ -323,13 +321,18 @@ __global__ void __launch_bounds__(kMThreads) k_box_mma(MArgs a, int ph) {
   const uint32_t idesc = mma_idesc(kTM, npad);
   bool ok = true;
   for (int c = 0; c < nch; ++c) {
-    const int b = c & 1;
-    if (c >= 2 && !mbar_wait_bounded(su32(&s_bar[b]), (uint32_t)(((c - 2) >> 1) & 1))) ok = false;
+    const int b = c % kMStages;
+    unsigned char *sA = smem + b * stage_bytes;
+    unsigned char *sBh = sA + a_chunk_bytes(), *sBl = sBh + b_chunk_bytes(npad);
+    // the products of chunk c - kMStages read this stage: wait for their commit
+    if (c >= kMStages &&
+        !mbar_wait_bounded(su32(&s_bar[b]), (uint32_t)(((c - kMStages) / kMStages) & 1)))
+      ok = false;
     if (!ok) s_fail = 1;  // benign race: every writer stores 1
     if (ok) {
       const int k0 = (tile.c0 + c) * kKC;
-      stage_a(a, ph, tile.unit, bx, tile.r0, k0, sA[b]);
-      stage_b(a, ph, tile.unit, bx, k0, sBh[b], sBl[b], lboB);
+      stage_a(a, ph, tile.unit, bx, tile.r0, k0, sA);
+      stage_b(a, ph, tile.unit, bx, k0, sBh, sBl, lboB);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -340,7 +343,7 @@ __global__ void __launch_bounds__(kMThreads) k_box_mma(MArgs a, int ph) {
       break;
     }
     if (t == 0) {
-      const uint32_t a0 = su32(sA[b]), h0 = su32(sBh[b]), l0 = su32(sBl[b]);
+      const uint32_t a0 = su32(sA), h0 = su32(sBh), l0 = su32(sBl);
 #pragma unroll
       for (int ks = 0; ks < kKC / 16; ++ks) {
         const uint64_t ad = smem_desc(a0 + (uint32_t)ks * 2 * kLboA, kLboA, kSbo);
@@ -364,21 +367,24 @@ __global__ void __launch_bounds__(kMThreads) k_box_mma(MArgs a, int ph) {
     }
   }
   // the last commit covers every product issued before it
-  if (ok && nch > 0 && !mbar_wait_bounded(su32(&s_bar[(nch - 1) & 1]), (uint32_t)(((nch - 1) >> 1) & 1)))
+  if (ok && nch > 0 &&
+      !mbar_wait_bounded(su32(&s_bar[(nch - 1) % kMStages]), (uint32_t)(((nch - 1) / kMStages) & 1)))
     ok = false;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  // epilogue: warp w reads lanes 32 (w % 4) + lane, columns of half w / 4
+  const int quarter = warp & 3, half = warp >> 2, hcols = npad / 2;
   if (ok && nch > 0) {
-    const int row = tile.r0 + warp * 32 + lane;
-    for (int c0 = 0; c0 < npad; c0 += 8) {
+    const int row = tile.r0 + quarter * 32 + lane;
+    for (int c0 = half * hcols; c0 < (half + 1) * hcols; c0 += 8) {
       uint32_t r[8];
-      const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
           : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
           : "r"(ta));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       if (tile.poff >= 0) {  // partial tile of a split box
-        float *pt = a.part + tile.poff + (long long)(warp * 32 + lane) * npad + c0;
+        float *pt = a.part + tile.poff + (long long)(quarter * 32 + lane) * npad + c0;
 #pragma unroll
         for (int j = 0; j < 8; ++j) pt[j] = __uint_as_float(r[j]);
       } else {
@@ -386,10 +392,10 @@ __global__ void __launch_bounds__(kMThreads) k_box_mma(MArgs a, int ph) {
         for (int j = 0; j < 8; ++j) store_out(a, ph, tile.unit, bx, row, c0 + j, __uint_as_float(r[j]));
       }
     }
-  } else if (ok) {  // K = 0: the product is zero
-    const int row = tile.r0 + warp * 32 + lane;
+  } else if (ok && half == 0) {  // K = 0: the product is zero
+    const int row = tile.r0 + quarter * 32 + lane;
     if (tile.poff >= 0) {
-      float *pt = a.part + tile.poff + (long long)(warp * 32 + lane) * npad;
+      float *pt = a.part + tile.poff + (long long)(quarter * 32 + lane) * npad;
       for (int n = 0; n < npad; ++n) pt[n] = 0.f;
     } else {
       for (int n = 0; n < a.ncols; ++n) store_out(a, ph, tile.unit, bx, row, n, 0.f);

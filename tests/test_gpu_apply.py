@@ -102,6 +102,20 @@ def test_apply_fp32_matches_oracle(H, case):
     assert _rel(y, hif.apply_inverse(F, x)) <= 1e-5
 
 
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-5)], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_apply_fused_upper_sweep_matches_oracle(H, case, precision, tol, monkeypatch):
+    """HIFCN_FUSED=1: the top levels and the root in one thread-block-cluster
+    kernel (opt-in; one launch per step is the default)."""
+    import torch
+    monkeypatch.setenv("HIFCN_FUSED", "1")
+    w, A, F, blob = _problem(case)
+    h = _import(H, case, precision=precision)
+    x = np.random.default_rng(3).standard_normal(F.N)
+    y = H.hif_apply(h, torch.from_numpy(x).cuda(), precision=precision).cpu().numpy()
+    assert _rel(y, hif.apply_inverse(F, x)) <= tol
+
+
 @pytest.mark.parametrize("case", CASES, ids=IDS)
 def test_pcg_matches_oracle(H, case):
     import torch
