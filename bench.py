@@ -67,6 +67,11 @@ def _args():
     p.add_argument("--batched-steps", type=int, default=20)
     p.add_argument("--heat3d-steps", type=int, default=50,
                    help="CN steps of the 3D heat 127^3 measurement reported beside the headline (0: skip)")
+    p.add_argument("--heat3d-large", type=int, default=0,
+                   help="CN steps of the paper's 3D logistic recipe at 255^3 (FP32 factor; setup takes "
+                        "minutes; 0: skip)")
+    p.add_argument("--heat3d-large-eps", type=float, default=1e-3)
+    p.add_argument("--heat3d-large-side", type=int, default=255)
     p.add_argument("--multi-k", type=int, default=16,
                    help="states of the benchmark operator stepped together by cn_step_multi (0: skip)")
     p.add_argument("--serving-ops", type=int, default=16,
@@ -486,6 +491,10 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
     if args.heat3d_steps > 0:
         heat3d = run_heat3d(args, dev, H, W, np, torch)
 
+    heat3d_large = None
+    if args.heat3d_large > 0:
+        heat3d_large = run_heat3d_large(args, dev, H, W, np, torch)
+
     # ---- serving: open-loop Poisson step requests over resident operators
     serving = None
     if args.serving_ops > 0:
@@ -595,6 +604,7 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
         "multi_rhs_2d": multi2d,
         "batched": batched,
         "heat3d": heat3d,
+        "heat3d_large": heat3d_large,
         "serving": serving,
         "serving_full": serving_full,
     }
@@ -858,6 +868,62 @@ def run_heat3d(args, dev, H, W, np, torch) -> dict:
             "api": "cn_steps (steps queued in one call) after a 2-step warm-up; the last step by "
                    "cn_step with its residual checked",
             **legs}
+
+
+def run_heat3d_large(args, dev, H, W, np, torch) -> dict:
+    """The paper's 3D logistic recipe (Sec. 3, Example 2 in 3D: 200 bumps on
+    [0.05, 20], the scaled Gaussian u0, k1 = 1, k2 = 10, dt = 0.1 h) at 255^3
+    (leaf 8, L = 5) with the factor in FP32 and PCG to the paper's tolerance
+    1e-12: setup time and memory, then `heat3d_large` CN steps one call each,
+    with their iteration counts (the tables print n_i = 6 at eps 1e-3 and 3 at
+    1e-6) and the CN-system residual of every step, ||A u^{k+1} - g|| / ||g||
+    with g = 2 u^k - A u^k + dt k1 u^k (1 - u^k / k2) from the library's
+    stencil."""
+    side = args.heat3d_large_side
+    w = W.paper_heat3d(side + 1, 8, args.heat3d_large_eps, seed=0, logistic=True)
+    a = torch.from_numpy(w.a_nodes).to(dev)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    t0 = time.perf_counter()
+    h = H.hif_setup(3, w.n, w.leaf, a, w.dt,
+                    H.default_options(eps=w.eps, precision=H.HIF_FP32, cg_tol=w.tol))
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    del a
+    info = H.hif_query(h)
+    print(f"[bench] {side}^3 setup {t_setup:.1f} s: {info}", file=sys.stderr, flush=True)
+    _, k1, k2 = w.reaction
+    H.hif_set_reaction(h, 1, k1, k2)
+    u = torch.from_numpy(w.u0.ravel().copy()).to(dev)
+    its, res, ms = [], [], []
+    for _ in range(args.heat3d_large):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        u1, it = H.cn_step(h, u)
+        torch.cuda.synchronize()
+        ms.append(1e3 * (time.perf_counter() - t1))
+        g = 2.0 * u - H.hif_matvec(h, u) + w.dt * k1 * u * (1.0 - u / k2)
+        res.append(float((H.hif_matvec(h, u1) - g).norm() / g.norm()))
+        its.append(it)
+        u = u1
+        print(f"[bench] {side}^3 step {len(its)}: {it} iterations, residual {res[-1]:.3g}, "
+              f"{ms[-1]:.1f} ms", file=sys.stderr, flush=True)
+    fp64_kept = True
+    try:
+        H.hif_apply(h, u, precision=H.HIF_FP64)
+    except H.HifError:
+        fp64_kept = False
+    h.close()
+    return {"workload": f"paper 3D logistic recipe, {side}^3 interior (N={w.N}), leaf 8 (L={w.levels}), "
+                        f"eps={w.eps:g}, face+edge skeletonization, FP32 factor, FP64 CG, PCG rel-res "
+                        f"{w.tol:g}",
+            "setup_s": round(t_setup, 1), "root": info["root_size"],
+            "factor_entries": info["factor_entries"], "device_bytes": info["device_bytes"],
+            "device_free_before_setup": free0, "fp64_factor_kept": fp64_kept,
+            "apply_bytes": info["apply_bytes"], "iters": its,
+            "mean_iters": round(float(np.mean(its)), 2) if its else None,
+            "printed_n_i": {1e-3: 6, 1e-6: 3}.get(w.eps),
+            "cn_residuals": res, "ms_per_step": [round(x, 1) for x in ms]}
 
 
 def run_batched(args, dev, H, W, np, torch) -> dict:

@@ -282,33 +282,42 @@ int finish_device_factor(Handle *h, cudaStream_t s) {
     }
 
   }
-  HIF_TRY(dev_alloc(h, (void **)&h->f64.xI, h->N * sizeof(double)));
+  // a streaming setup left no FP64 values: the FP64 apply buffers are not needed
+  const bool lean = h->lean_setup;
   long long gs_max = 0;
   for (const LevelDev &D : h->lv) gs_max = std::max(gs_max, D.gs_total);
-  HIF_TRY(dev_alloc(h, (void **)&h->f64.gs, std::max<long long>(gs_max, 1) * sizeof(double)));
+  if (!lean) {
+    HIF_TRY(dev_alloc(h, (void **)&h->f64.xI, h->N * sizeof(double)));
+    HIF_TRY(dev_alloc(h, (void **)&h->f64.gs, std::max<long long>(gs_max, 1) * sizeof(double)));
+  }
   if (h->root_n > 0) HIF_TRY(dev_alloc(h, &h->upper_rt, h->root_n * sizeof(double)));
   h->root_split = h->root_n > root_split;
   HIF_TRY(make_cell_inverses(h, s));
-  HIF_TRY(dev_alloc(h, (void **)&h->f64.contrib, h->max_contrib * sizeof(double)));
+  if (!lean) HIF_TRY(dev_alloc(h, (void **)&h->f64.contrib, h->max_contrib * sizeof(double)));
   if (h->opt.precision == HIF_FP32 || h->opt.precision == HIF_FP32_BF16TOP) {
-    HIF_TRY(dev_alloc(h, (void **)&h->f32.vals, h->nvals * sizeof(float)));
+    if (!lean) HIF_TRY(dev_alloc(h, (void **)&h->f32.vals, h->nvals * sizeof(float)));
     HIF_TRY(dev_alloc(h, (void **)&h->f32.contrib, h->max_contrib * sizeof(float)));
     HIF_TRY(dev_alloc(h, (void **)&h->f32.work, h->N * sizeof(float)));
     HIF_TRY(dev_alloc(h, (void **)&h->f32.xI, h->N * sizeof(float)));
     HIF_TRY(dev_alloc(h, (void **)&h->f32.gs, std::max<long long>(gs_max, 1) * sizeof(float)));
-    k_cast_f32<<<1216, 256, 0, s>>>(h->f64.vals, h->f32.vals, h->nvals);
-    note_launch();
-    HIF_CUDA_TRY(cudaGetLastError());
+    if (!lean) {
+      k_cast_f32<<<1216, 256, 0, s>>>(h->f64.vals, h->f32.vals, h->nvals);
+      note_launch();
+      HIF_CUDA_TRY(cudaGetLastError());
+    }
     h->has_f32 = true;
   }
   if (h->opt.precision == HIF_FP32_BF16TOP) {
     const int top = h->opt.bf16_top_levels > 0 ? std::min(h->opt.bf16_top_levels, h->L)
                                                : (h->L + 1) / 2;
     h->bf16_lb = h->L - top;
-    HIF_TRY(dev_alloc(h, &h->bf16_vals, std::max<long long>(h->nvals, 1) * 2));
-    HIF_TRY(cast_values_bf16(h, s));
+    if (!lean) {
+      HIF_TRY(dev_alloc(h, &h->bf16_vals, std::max<long long>(h->nvals, 1) * 2));
+      HIF_TRY(cast_values_bf16(h, s));
+    }
     h->has_bf16 = true;
   }
+  h->fp64_released = lean;
   HIF_CUDA_TRY(cudaStreamSynchronize(s));
   HIF_TRY(build_upper_plan(h));
   HIF_TRY(build_view(h));
@@ -486,6 +495,11 @@ struct Reader {
     p += b;
     return true;
   }
+  bool skip(size_t b) {
+    if ((size_t)(end - p) < b) return false;
+    p += b;
+    return true;
+  }
 };
 
 int import_blob(Handle *h, const void *blob, size_t bytes, cudaStream_t s) {
@@ -528,6 +542,21 @@ int import_blob(Handle *h, const void *blob, size_t bytes, cudaStream_t s) {
     int cnt[2];
     if (!rd.get(cnt, 2) || cnt[0] < 0 || cnt[1] < 0) return HIF_EFORMAT;
     LevelHost &H = h->lv_host[l];
+    // room for S only where the S-form apply can take the level: look ahead
+    // at the level's cell sizes
+    bool want_S = false;
+    {
+      Reader la = rd;
+      int max_nI = 0;
+      for (int c = 0; c < cnt[0]; ++c) {
+        int sz[2];
+        if (!la.get(sz, 2) || sz[0] < 0 || sz[1] < 0) return HIF_EFORMAT;
+        max_nI = std::max(max_nI, sz[0]);
+        const size_t nI = (size_t)sz[0], nB = (size_t)sz[1];
+        if (!la.skip(4 * (nI + nB) + 8 * (nI * (nI + 1) / 2 + nB * nI))) return HIF_EFORMAT;
+      }
+      want_S = pad4(max_nI) <= kSformMaxNI;
+    }
     long long slots = 0;
     for (int c = 0; c < cnt[0]; ++c) {
       CellDesc d{};
@@ -537,8 +566,11 @@ int import_blob(Handle *h, const void *blob, size_t bytes, cudaStream_t s) {
       d.nB = sz[1];
       if (!get_ints(d.nI, &d.I_off) || !get_ints(d.nB, &d.B_off)) return HIF_EFORMAT;
       if (!get_lower(d.nI, &d.G_off)) return HIF_EFORMAT;
-      d.S_off = (long long)vals.size();  // S = G^T G, computed on the device
-      vals.resize(vals.size() + tri_off(d.nI), 0.0);
+      d.S_off = -1;
+      if (want_S) {  // S = G^T G, computed on the device; V follows it
+        d.S_off = (long long)vals.size();
+        vals.resize(vals.size() + tri_off(d.nI), 0.0);
+      }
       if (!get_dense(d.nB, d.nI, &d.V_off)) return HIF_EFORMAT;
       d.C_off = slots;
       slots += d.nB;

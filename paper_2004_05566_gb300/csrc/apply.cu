@@ -1922,7 +1922,7 @@ size_t tma_fwd_smem_elems(const LevelDev &lv) { return 2 * (size_t)pad4(lv.max_n
 // A level whose blocks fit the S-form kernels (rows within a stage, at most
 // kMaxChunks chunks per cell, nI <= 256, shared memory within the limit).
 bool sform_capable(const LevelDev &lv) {
-  if (lv.ncells == 0 || lv.max_chunks < 0 || lv.max_chunks > kMaxChunks || pad4(lv.max_nI) > 256)
+  if (lv.ncells == 0 || lv.max_chunks < 0 || lv.max_chunks > kMaxChunks || pad4(lv.max_nI) > kSformMaxNI)
     return false;
   const size_t bwd_smem = (size_t)kStagesBwd * kStageBytes + tma_bwd_smem_elems(lv) * sizeof(float);
   return bwd_smem <= 200 * 1024;
@@ -2891,10 +2891,16 @@ int apply_inplace_f64_with_scratch(Handle *h, double *contrib, double *x, cudaSt
 // S = G^T G of the cells of the levels the FP32 S-form kernels will apply.
 int make_cell_inverses(Handle *h, cudaStream_t s) {
   if (h->opt.precision != HIF_FP32 && h->opt.precision != HIF_FP32_BF16TOP) return HIF_OK;
-  for (LevelDev &lv : h->lv) {
+  for (size_t l = 0; l < h->lv.size(); ++l) {
+    LevelDev &lv = h->lv[l];
     if (!h->use_tma || !sform_capable(lv)) continue;
-    k_make_S<<<lv.ncells, 256, 0, s>>>(lv.cells, h->f64.vals);
-    note_launch();
+    bool stored = true;  // every cell of the level has room for S
+    for (const CellDesc &c : h->lv_host[l].cells) stored = stored && c.S_off >= 0;
+    if (!stored) continue;
+    if (!h->lean_setup) {  // a streaming setup formed S before dropping the FP64 values
+      k_make_S<<<lv.ncells, 256, 0, s>>>(lv.cells, h->f64.vals);
+      note_launch();
+    }
     lv.has_S = true;
   }
   HIF_CUDA_TRY(cudaGetLastError());
@@ -2933,6 +2939,31 @@ __global__ void k_to_bf16(const double *__restrict__ a, __nv_bfloat16 *__restric
 
 int cast_values_bf16(Handle *h, cudaStream_t s) {
   k_to_bf16<<<1216, 256, 0, s>>>(h->f64.vals, static_cast<__nv_bfloat16 *>(h->bf16_vals), h->nvals);
+  note_launch();
+  HIF_CUDA_TRY(cudaGetLastError());
+  return HIF_OK;
+}
+
+// Reduced-precision copies of n FP64 factor values (either output may be
+// null), rounded as the handle-wide casts round them.
+int cast_pool(const double *a, float *f32, void *b16, long long n, cudaStream_t s) {
+  if (n <= 0) return HIF_OK;
+  if (f32) {
+    k_to_float<<<1216, 256, 0, s>>>(a, f32, n);
+    note_launch();
+  }
+  if (b16) {
+    k_to_bf16<<<1216, 256, 0, s>>>(a, static_cast<__nv_bfloat16 *>(b16), n);
+    note_launch();
+  }
+  HIF_CUDA_TRY(cudaGetLastError());
+  return HIF_OK;
+}
+
+// S = G^T G of the given cells (offsets into vals), FP64.
+int make_S_cells(const CellDesc *dcells, int ncells, double *vals, cudaStream_t s) {
+  if (ncells <= 0) return HIF_OK;
+  k_make_S<<<ncells, 256, 0, s>>>(dcells, vals);
   note_launch();
   HIF_CUDA_TRY(cudaGetLastError());
   return HIF_OK;

@@ -24,12 +24,15 @@
 
 #include "internal.h"
 
+#include <algorithm>
+
 namespace hifcn {
 namespace dense {
 
 constexpr int kPanel = 32;   // panel width of the blocked Cholesky and G blocks
 constexpr int kTile = 64;    // tile edge of the trailing update and of V
 constexpr int kThreads = 256;
+constexpr int kMaxGridY = 65535;  // the launch limit of grid.y
 
 __host__ __device__ inline int ceil_div(long long a, int b) { return (int)((a + b - 1) / b); }
 
@@ -132,11 +135,11 @@ __global__ void __launch_bounds__(kThreads) k_chol_syrk(const Cell *__restrict__
   const int jb = min(kPanel, c.nI - j0);
   const int j1 = j0 + jb;
   const int t = ceil_div(nn - j1, kTile);
-  if ((int)blockIdx.y >= t * (t + 1) / 2) return;
-  int ti, tj;
-  tri_tile(blockIdx.y, ti, tj);
-  const int r0 = j1 + ti * kTile, c0 = j1 + tj * kTile;
   double *A = F + c.F_off;
+  for (int y = blockIdx.y; y < t * (t + 1) / 2; y += gridDim.y) {  // grid.y may be capped
+  int ti, tj;
+  tri_tile(y, ti, tj);
+  const int r0 = j1 + ti * kTile, c0 = j1 + tj * kTile;
   for (int e = threadIdx.x; e < kPanel * kTile; e += kThreads) {
     const int r = e % kTile, k = e / kTile;
     const int ia = r0 + r, ib = c0 + r;
@@ -169,6 +172,8 @@ __global__ void __launch_bounds__(kThreads) k_chol_syrk(const Cell *__restrict__
       const int i = r0 + tr + 16 * u;
       if (i < nn && i >= j) A[i + (long long)j * nn] -= acc[u][v];
     }
+  }
+  __syncthreads();  // As/Bs are refilled for the next tile
   }
 }
 
@@ -286,8 +291,8 @@ __global__ void __launch_bounds__(kThreads) k_form_V(const Cell *__restrict__ ce
   __shared__ double Gs[kPanel][kTile];  // [k][j]
   const Cell c = cells[blockIdx.x];
   const int tb = ceil_div(c.nB, kTile), tjn = ceil_div(c.nI, kTile);
-  if ((int)blockIdx.y >= tb * tjn) return;
-  const int b0 = (blockIdx.y % tb) * kTile, jc0 = (blockIdx.y / tb) * kTile;
+  for (int y = blockIdx.y; y < tb * tjn; y += gridDim.y) {  // grid.y may be capped
+  const int b0 = (y % tb) * kTile, jc0 = (y / tb) * kTile;
   const int nn = c.nI + c.nB;
   const double *A = F + c.F_off;
   const double *G = vals + c.G_off;
@@ -328,6 +333,7 @@ __global__ void __launch_bounds__(kThreads) k_form_V(const Cell *__restrict__ ce
       const int j = jc0 + tc + 16 * v;
       if (j < c.nI) V[(long long)b * vs + j] = acc[u][v];
     }
+  }
   }
 }
 
@@ -370,7 +376,7 @@ int eliminate_cells(const std::vector<Cell> &cells_h, const Cell *cells_d, doubl
     }
     const int t = ceil_div(rest > 0 ? rest : 0, kTile);
     if (t > 0) {
-      k_chol_syrk<Cell><<<dim3(ncells, t * (t + 1) / 2), kThreads, 0, s>>>(cells_d, F, j0);
+      k_chol_syrk<Cell><<<dim3(ncells, std::min(t * (t + 1) / 2, kMaxGridY)), kThreads, 0, s>>>(cells_d, F, j0);
       note_launch();
     }
   }
@@ -385,7 +391,7 @@ int eliminate_cells(const std::vector<Cell> &cells_h, const Cell *cells_d, doubl
   }
   if (max_nB > 0 && max_nI > 0) {
     const int tiles = ceil_div(max_nB, kTile) * ceil_div(max_nI, kTile);
-    k_form_V<Cell><<<dim3(ncells, tiles), kThreads, 0, s>>>(cells_d, F, vals);
+    k_form_V<Cell><<<dim3(ncells, std::min(tiles, kMaxGridY)), kThreads, 0, s>>>(cells_d, F, vals);
     note_launch();
   }
   if (max_nB > 0) {

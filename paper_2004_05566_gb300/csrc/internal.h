@@ -59,6 +59,11 @@ constexpr int kScalErr = 15;
 // Size of one shared-memory stage of the bulk-copy staged cell kernels.
 constexpr int kStageBytes = 15872;  // 124 x 128 B: three backward CTAs fit an SM
 
+// Largest padded interior size of a cell the S-form cell kernels take; S =
+// A_II^{-1} is only stored on levels whose cells all stay within it (other
+// cells have S_off = -1).
+constexpr int kSformMaxNI = 256;
+
 // Separator entities above this size are applied split over many CTAs, and
 // roots above kRootSplitDofs by a row-block and a column-block launch.
 constexpr int kSplitDofs = 256;
@@ -322,6 +327,10 @@ struct hif_handle {
   std::vector<hifcn::DevAlloc> allocations;
   bool offloaded = false;  // hif_offload: large allocations live in host memory
   bool fp64_released = false;  // hif_release_fp64: no FP64 factor values on the device
+  // the setup streamed each level's values into the reduced-precision pools
+  // (S formed first) and dropped the FP64 values: the handle is as after
+  // hif_release_fp64 from the start
+  bool lean_setup = false;
   long long device_bytes = 0;
   // allocations [factor_alloc_begin, end) belong to the factor (released by
   // hif_refactor); work_device_bytes is device_bytes without them

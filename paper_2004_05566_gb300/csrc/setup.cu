@@ -10,7 +10,13 @@
 //      children's surviving boundary blocks (children in fixed order);
 //   2. cell elimination (Eq. 2_3): partial Cholesky of F_c over I_c, giving
 //      L, W^T = A_BI L^{-T} and the Schur complement X_BB = A_BB - W^T W;
-//      the apply operators G = L^{-1} and V = A_BI A_II^{-1} = W^T G are stored;
+//      the apply operators G = L^{-1} and V = A_BI A_II^{-1} = W^T G are stored
+//      (and S = A_II^{-1} on levels the S-form apply can take).  Steps 1 and 2
+//      run over chunks of consecutive cells through one reusable front buffer
+//      sized from the free device memory; only X_BB of every cell is kept, in
+//      the level's boundary store, which steps 3 and 4 work on and the next
+//      level assembles from.  Each cell's arithmetic is the same whatever the
+//      chunking, so the factor does not depend on it;
 //   3. block Jacobi (Eq. jacobi-precond): per separator entity g the diagonal
 //      block sum_c F_c[g,g] is factored, L_g^{-1} rescales rows and columns of
 //      g in every cell, the diagonal blocks become I (held by the owner);
@@ -43,6 +49,8 @@ namespace hifcn {
 
 int finish_device_factor(Handle *h, cudaStream_t s);
 int build_contrib_map(Handle *h, LevelHost &H);
+int cast_pool(const double *a, float *f32, void *b16, long long n, cudaStream_t s);
+int make_S_cells(const CellDesc *dcells, int ncells, double *vals, cudaStream_t s);
 
 namespace {
 
@@ -60,6 +68,7 @@ struct SCell {
   long long dofs_off; // local DOF list (I then B), global indices
   long long bmap_off; // per B position: (group id, position in group)
   long long kid_off;  // into the extend-add lists of this level (n + 1 entries)
+  long long Fb_off;   // Schur complement X_BB (nB x nB column major) in the boundary store
 };
 
 struct SGroup {
@@ -99,13 +108,14 @@ __global__ void __launch_bounds__(NT) k_assemble_leaf(const SCell *__restrict__ 
                                                       const double *__restrict__ wx,
                                                       const double *__restrict__ wy,
                                                       const double *__restrict__ wz, int dim,
-                                                      int n, int s, int nc, double *__restrict__ F) {
+                                                      int n, int s, int nc, int cell0,
+                                                      double *__restrict__ F) {
   extern __shared__ int boxmap[];  // (s+1)^dim
   const SCell c = cells[blockIdx.x];
   const int nn = c.nI + c.nB;
   double *Fc = F + c.F_off;
   const int *dofs = cdofs + c.dofs_off;
-  const int cid = blockIdx.x;
+  const int cid = cell0 + blockIdx.x;
   const int cc[3] = {cid % nc, (cid / nc) % nc, dim == 3 ? cid / (nc * nc) : 0};
   const int box = s + 1;
   const int boxn = dim == 3 ? box * box * box : box * box;
@@ -192,6 +202,22 @@ __global__ void __launch_bounds__(NT) k_extend_add(const SCell *__restrict__ pce
       FP[p + (long long)r * np] = acc;
     }
     __syncthreads();
+  }
+}
+
+// Copy each eliminated cell's Schur complement (the boundary block of its
+// front, already symmetric) into the boundary store.  grid = (cells, chunks).
+__global__ void __launch_bounds__(NT) k_extract_bb(const SCell *__restrict__ cells,
+                                                   const double *__restrict__ F,
+                                                   double *__restrict__ Fb) {
+  const SCell c = cells[blockIdx.x];
+  const int nn = c.nI + c.nB;
+  const long long nbb = (long long)c.nB * c.nB;
+  const double *A = F + c.F_off;
+  double *B = Fb + c.Fb_off;
+  for (long long t = blockIdx.y * (long long)NT + threadIdx.x; t < nbb; t += (long long)gridDim.y * NT) {
+    const int p = (int)(t % c.nB), q = (int)(t / c.nB);
+    B[t] = A[c.nI + p + (long long)(c.nI + q) * nn];
   }
 }
 
@@ -290,16 +316,16 @@ __global__ void __launch_bounds__(NT) k_unpack_Linv(const SGroup *__restrict__ g
 // block-diagonal of the entities' L^{-1}; the entities' own diagonal blocks
 // become I (owner cell) or 0.  Two passes over (cells, chunks):
 // rows first (Sc = D F_BB), then columns (F_BB = Sc D^T).
-__global__ void __launch_bounds__(NT) k_cell_scale_rows(const SCell *__restrict__ cells,
+__global__ void __launch_bounds__(NT) k_cell_scale_rows(const SCell *__restrict__ cells, int cell0,
                                                         const int2 *__restrict__ bmap,
                                                         const SGroup *__restrict__ groups,
                                                         const double *__restrict__ Linv,
                                                         const double *__restrict__ F,
-                                                        double *__restrict__ S) {
-  const SCell c = cells[blockIdx.x];
+                                                        double *__restrict__ S, long long sc_base) {
+  const SCell c = cells[cell0 + blockIdx.x];
   const int nI = c.nI, nB = c.nB, nn = nI + nB;
   const double *A = F + c.F_off;
-  double *Sc = S + c.Sc_off;
+  double *Sc = S + (c.Sc_off - sc_base);
   const int2 *bm = bmap + c.bmap_off;
   const long long nbb = (long long)nB * nB;
   for (long long t = blockIdx.y * (long long)NT + threadIdx.x; t < nbb; t += (long long)gridDim.y * NT) {
@@ -314,17 +340,18 @@ __global__ void __launch_bounds__(NT) k_cell_scale_rows(const SCell *__restrict_
   }
 }
 
-__global__ void __launch_bounds__(NT) k_cell_scale_cols(const SCell *__restrict__ cells,
+__global__ void __launch_bounds__(NT) k_cell_scale_cols(const SCell *__restrict__ cells, int cell0,
                                                         const int2 *__restrict__ bmap,
                                                         const SGroup *__restrict__ groups,
                                                         const int2 *__restrict__ gcells,
                                                         const double *__restrict__ Linv,
                                                         double *__restrict__ F,
-                                                        const double *__restrict__ S) {
-  const SCell c = cells[blockIdx.x];
+                                                        const double *__restrict__ S, long long sc_base) {
+  const int cid = cell0 + (int)blockIdx.x;
+  const SCell c = cells[cid];
   const int nI = c.nI, nB = c.nB, nn = nI + nB;
   double *A = F + c.F_off;
-  const double *Sc = S + c.Sc_off;
+  const double *Sc = S + (c.Sc_off - sc_base);
   const int2 *bm = bmap + c.bmap_off;
   const long long nbb = (long long)nB * nB;
   for (long long t = blockIdx.y * (long long)NT + threadIdx.x; t < nbb; t += (long long)gridDim.y * NT) {
@@ -333,7 +360,7 @@ __global__ void __launch_bounds__(NT) k_cell_scale_cols(const SCell *__restrict_
     double v;
     if (gp.x == gq.x) {
       const SGroup g = groups[gp.x];
-      const bool owner = gcells[g.gc_off].x == (int)blockIdx.x;
+      const bool owner = gcells[g.gc_off].x == cid;
       v = (owner && gp.y == gq.y) ? 1.0 : 0.0;
     } else {
       const SGroup g = groups[gq.x];
@@ -718,6 +745,19 @@ int check_err(int *derr, cudaStream_t s, const char *what) {
   return HIF_OK;
 }
 
+// Bytes one scratch buffer of a setup phase may take: the environment
+// variable when it is set (tests force small chunks with it), else a fraction
+// of the device memory free at the time.
+long long setup_budget(const char *env, double frac) {
+  if (const char *e = std::getenv(env)) return std::max(1LL, std::atoll(e));
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    return 1LL << 30;
+  }
+  return std::max(256LL << 20, (long long)((double)fr * frac));
+}
+
 int set_smem(const void *fn, size_t bytes) {
   if (bytes > 48 * 1024)
     HIF_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
@@ -781,12 +821,54 @@ int gpu_setup(Handle *h, const double *a_nodes, cudaStream_t s) {
   h->idx_host.clear();
   std::vector<double *> level_vals(L + 1, nullptr);
   std::vector<long long> level_nvals(L + 1, 0);
+  // Reduced-precision handles can stream: each finished level's FP64 values
+  // become their FP32 (and BF16) copies, S formed first, and are dropped.  The
+  // setup streams when device memory runs short (below a fifth free at the
+  // start of a level, or too little left for the handle-wide copies at the
+  // end); HIFCN_LEAN_SETUP=1 forces it, =0 forbids it.  The values are the
+  // same either way; a streamed handle holds no FP64 factor.
+  const bool reduced = h->opt.precision == HIF_FP32 || h->opt.precision == HIF_FP32_BF16TOP;
+  const bool want_b16 = h->opt.precision == HIF_FP32_BF16TOP;
+  const char *lean_env = std::getenv("HIFCN_LEAN_SETUP");
+  const int lean_mode = !reduced ? 0 : !lean_env ? -1 : (lean_env[0] == '1' ? 1 : 0);  // -1: by memory
+  h->lean_setup = false;
+  bool lean = false;
+  std::vector<float *> level_f32(L + 1, nullptr);
+  std::vector<unsigned short *> level_b16(L + 1, nullptr);
+  auto stream_level = [&](int k) -> int {
+    if (!level_vals[k]) return HIF_OK;
+    if (k < L && !h->lv_host[k].cells.empty() && h->lv_host[k].cells[0].S_off >= 0) {
+      Scratch tmp;
+      CellDesc *dc = nullptr;
+      HIF_TRY(tmp.upload(&dc, h->lv_host[k].cells, s));
+      HIF_TRY(make_S_cells(dc, (int)h->lv_host[k].cells.size(), level_vals[k], s));
+      HIF_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    HIF_TRY(keep.alloc(&level_f32[k], level_nvals[k]));
+    if (want_b16) HIF_TRY(keep.alloc(&level_b16[k], level_nvals[k]));
+    HIF_TRY(cast_pool(level_vals[k], level_f32[k], level_b16[k], level_nvals[k], s));
+    HIF_CUDA_TRY(cudaStreamSynchronize(s));
+    keep.release(level_vals[k]);
+    level_vals[k] = nullptr;
+    return HIF_OK;
+  };
+  auto go_lean = [&](int upto) -> int {  // levels below `upto` are finished
+    lean = true;
+    for (int k = 0; k < upto; ++k) HIF_TRY(stream_level(k));
+    return HIF_OK;
+  };
+
   Plan prev;
-  double *F_prev = nullptr;
-  SCell *dcells_prev = nullptr;
-  std::vector<SCell> cells_prev;
+  double *Fb_prev = nullptr;       // previous level's boundary store
+  SCell *dbcells_prev = nullptr;   // its descriptors (nI = 0, F_off = Fb_off)
 
   for (int l = 0; l <= L; ++l) {
+    if (!lean && lean_mode == 1) HIF_TRY(go_lean(l));
+    if (!lean && lean_mode == -1) {
+      size_t fr = 0, tot = 0;
+      if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && fr < tot / 5) HIF_TRY(go_lean(l));
+      cudaGetLastError();
+    }
     Scratch lvl;
     Plan P = make_plan(active, n, dim, leaf, l);
     const int ncells = P.ncells;
@@ -795,22 +877,31 @@ int gpu_setup(Handle *h, const double *a_nodes, cudaStream_t s) {
       set_last_error("setup: root level is not a single cell");
       return HIF_EINVAL;
     }
+    // S = A_II^{-1} is only stored on levels whose cells fit the S-form apply
+    int level_max_nI = 0;
+    for (int c = 0; c < ncells; ++c) level_max_nI = std::max(level_max_nI, (int)P.cI[c].size());
+    const bool want_S = l < L && pad4(level_max_nI) <= kSformMaxNI;
     // ---- cells: offsets
     std::vector<SCell> cells(ncells);
     std::vector<int> cdofs;
     std::vector<int2> bmap;
-    long long foff = 0, voff = 0, soff = 0, kid_total = 0;
+    long long foff = 0, fboff = 0, voff = 0, soff = 0, kid_total = 0;
     for (int c = 0; c < ncells; ++c) {
       SCell &C = cells[c];
       C.nI = (int)P.cI[c].size();
       C.nB = (int)P.cB[c].size();
       const long long nn = C.nI + C.nB;
-      C.F_off = foff;
+      C.F_off = 0;  // set per front chunk
       foff += nn * nn;
+      C.Fb_off = fboff;
+      fboff += (long long)C.nB * C.nB;
       C.G_off = voff;
       voff += tri_off(C.nI);
-      C.S_off = voff;  // S = G^T G, filled after the factorization
-      voff += tri_off(C.nI);
+      C.S_off = -1;
+      if (want_S) {
+        C.S_off = voff;  // S = G^T G, filled after the factorization
+        voff += tri_off(C.nI);
+      }
       C.V_off = voff;
       voff += (long long)C.nB * pad4(C.nI);
       C.Sc_off = soff;
@@ -846,25 +937,17 @@ int gpu_setup(Handle *h, const double *a_nodes, cudaStream_t s) {
     double *vals = level_vals[l];
     HIF_CUDA_TRY(cudaMemsetAsync(vals, 0, std::max<long long>(hoff, 1) * sizeof(double), s));  // row padding
 
-    double *F = nullptr;
-    SCell *dcells = nullptr;
+    // boundary store of this level: every cell's Schur complement X_BB
+    double *Fb = nullptr;
+    HIF_TRY(keep.alloc(&Fb, fboff));
     int *dcdofs = nullptr;
-    HIF_TRY(keep.alloc(&F, foff));
-    HIF_TRY(keep.upload(&dcells, cells, s));
     HIF_TRY(lvl.upload(&dcdofs, cdofs, s));
 
-    // ---- assemble
-    if (l == 0) {
-      const int box = P.s + 1;
-      size_t sm = sizeof(int) * (dim == 3 ? (size_t)box * box * box : (size_t)box * box);
-      HIF_TRY(set_smem((const void *)k_assemble_leaf, sm));
-      k_assemble_leaf<<<ncells, NT, sm, s>>>(dcells, dcdofs, h->diag, h->wx, h->wy, h->wz, dim, n,
-                                             P.s, P.nc, F);
-      note_launch();
-      HIF_CUDA_TRY(cudaGetLastError());
-    } else {
-      // extend-add of the children's surviving boundary entries: per parent
-      // position, the children holding it (increasing child order)
+    // ---- extend-add lists (l > 0): per parent position, the children holding
+    // it with the position in the child's boundary store, increasing child order
+    long long *dkid_ptr = nullptr;
+    int2 *dkid_ent = nullptr;
+    if (l > 0) {
       std::vector<int> lpos(N, -1);
       const int pnc = prev.nc;
       std::vector<std::vector<int>> kids(ncells);
@@ -894,7 +977,6 @@ int gpu_setup(Handle *h, const double *a_nodes, cudaStream_t s) {
           const long long base = cells[pc].kid_off;
           if (pass == 1) fill.assign(kid_ptr.begin() + base, kid_ptr.begin() + base + pos);
           for (int c : kids[pc]) {
-            const int nIc = cells_prev[c].nI;
             for (int q = 0; q < (int)prev.cB[c].size(); ++q) {
               const int d = prev.cB[c][q];
               if (!alive[d]) continue;
@@ -903,33 +985,76 @@ int gpu_setup(Handle *h, const double *a_nodes, cudaStream_t s) {
                 return HIF_EINVAL;
               }
               if (pass == 0) ++kid_ptr[base + lpos[d]];
-              else kid_ent[fill[lpos[d]]++] = make_int2(c, nIc + q);
+              else kid_ent[fill[lpos[d]]++] = make_int2(c, q);
             }
           }
           for (int d : P.cI[pc]) lpos[d] = -1;
           for (int d : P.cB[pc]) lpos[d] = -1;
         }
       }
-      long long *dkid_ptr = nullptr;
-      int2 *dkid_ent = nullptr;
       HIF_TRY(lvl.upload(&dkid_ptr, kid_ptr, s));
       HIF_TRY(lvl.upload(&dkid_ent, kid_ent, s));
-      int max_np = 1;
-      for (auto &C : cells) max_np = std::max(max_np, C.nI + C.nB);
-      k_extend_add<<<dim3(ncells, std::min(max_np, 4096)), NT, 0, s>>>(dcells, dcells_prev, dkid_ptr,
-                                                                       dkid_ent, F_prev, F);
+    }
+
+    // ---- fronts in chunks of consecutive cells through one reusable buffer:
+    // assemble (level 0 from the stencil, above by extend-add of the children's
+    // Schur complements), eliminate the interiors, keep X_BB
+    std::vector<int> fchunk = {0};
+    {
+      const long long front_cap = setup_budget("HIFCN_SETUP_FRONT_BYTES", 0.6);
+      long long run = 0, maxrun = 0, cap = std::max(front_cap / (long long)sizeof(double), 1LL);
+      for (int c = 0; c < ncells; ++c) {
+        const long long nn = cells[c].nI + cells[c].nB;
+        if (run > 0 && run + nn * nn > cap) {
+          fchunk.push_back(c);
+          run = 0;
+        }
+        cells[c].F_off = run;
+        run += nn * nn;
+        maxrun = std::max(maxrun, run);
+      }
+      fchunk.push_back(ncells);
+      foff = maxrun;
+    }
+    double *Fc = nullptr;
+    SCell *dcells = nullptr;
+    HIF_TRY(lvl.alloc(&Fc, foff));
+    HIF_TRY(lvl.upload(&dcells, cells, s));
+    int max_np = 1;
+    for (auto &C : cells) max_np = std::max(max_np, C.nI + C.nB);
+    for (size_t k = 0; k + 1 < fchunk.size(); ++k) {
+      const int c0 = fchunk[k], nck = fchunk[k + 1] - c0;
+      if (l == 0) {
+        const int box = P.s + 1;
+        size_t sm = sizeof(int) * (dim == 3 ? (size_t)box * box * box : (size_t)box * box);
+        HIF_TRY(set_smem((const void *)k_assemble_leaf, sm));
+        k_assemble_leaf<<<nck, NT, sm, s>>>(dcells + c0, dcdofs, h->diag, h->wx, h->wy, h->wz, dim, n,
+                                            P.s, P.nc, c0, Fc);
+      } else {
+        k_extend_add<<<dim3(nck, std::min(max_np, 4096)), NT, 0, s>>>(dcells + c0, dbcells_prev, dkid_ptr,
+                                                                      dkid_ent, Fb_prev, Fc);
+      }
       note_launch();
       HIF_CUDA_TRY(cudaGetLastError());
-      HIF_CUDA_TRY(cudaStreamSynchronize(s));
-      keep.release(F_prev);
-      keep.release(dcells_prev);
+      const std::vector<SCell> part(cells.begin() + c0, cells.begin() + c0 + nck);
+      HIF_TRY(dense::eliminate_cells<SCell>(part, dcells + c0, Fc, vals, derr, s));
+      int max_nB = 1;
+      for (auto &C : part) max_nB = std::max(max_nB, C.nB);
+      const long long nbb = (long long)max_nB * max_nB;
+      const int ch = (int)std::max(1LL, std::min((nbb + 4LL * NT - 1) / (4LL * NT), 4096LL));
+      k_extract_bb<<<dim3(nck, ch), NT, 0, s>>>(dcells + c0, Fc, Fb);
+      note_launch();
+      HIF_CUDA_TRY(cudaGetLastError());
     }
-    tm.mark("l" + std::to_string(l) + " assemble");
-
-    // ---- cell elimination (blocked, batched over the cells of the level)
-    HIF_TRY(dense::eliminate_cells<SCell>(cells, dcells, F, vals, derr, s));
     HIF_TRY(check_err(derr, s, "cell elimination"));
-    tm.mark("l" + std::to_string(l) + " cells (nn<=" + std::to_string(max_front(cells)) + ")");
+    lvl.release(Fc);
+    keep.release(Fb_prev);
+    keep.release(dbcells_prev);
+    Fb_prev = nullptr;
+    dbcells_prev = nullptr;
+    tm.mark("l" + std::to_string(l) + " fronts (" + std::to_string(ncells) + " cells in " +
+            std::to_string(fchunk.size() - 1) + " chunks, nn<=" + std::to_string(max_np) + "; level pool " +
+            std::to_string(hoff) + ")");
 
     // ---- apply descriptors of the cells (index pool) and the root
     if (l == L) {
@@ -938,6 +1063,7 @@ int gpu_setup(Handle *h, const double *a_nodes, cudaStream_t s) {
       h->root_idx_off = (long long)h->idx_host.size();
       h->idx_host.insert(h->idx_host.end(), P.cI[0].begin(), P.cI[0].end());
       h->root_G_off = C.G_off;  // relative to the root pool; shifted below
+      keep.release(Fb);
       break;
     }
     LevelHost &LH = h->lv_host[l];
@@ -967,26 +1093,33 @@ int gpu_setup(Handle *h, const double *a_nodes, cudaStream_t s) {
       LH.groups.push_back(d);
     }
 
+    // from here on the cells are their boundary blocks in the store
+    std::vector<SCell> bcells = cells;
+    for (SCell &C : bcells) {
+      C.nI = 0;
+      C.F_off = C.Fb_off;
+    }
+    SCell *dbcells = nullptr;
+    HIF_TRY(keep.upload(&dbcells, bcells, s));
+
     // ---- block Jacobi
     SGroup *dgroups = nullptr;
     int2 *dgcells = nullptr, *dbmap = nullptr;
-    double *Linv = nullptr, *Dscr = nullptr, *Sscr = nullptr;
+    double *Linv = nullptr, *Dscr = nullptr;
     HIF_TRY(lvl.upload(&dgroups, groups, s));
     HIF_TRY(lvl.upload(&dgcells, gcells, s));
     HIF_TRY(lvl.upload(&dbmap, bmap, s));
     HIF_TRY(lvl.alloc(&Linv, loff));
     HIF_TRY(lvl.alloc(&Dscr, loff));
-    HIF_TRY(lvl.alloc(&Sscr, soff));
     if (ng > 0) {
-      int max_gn = 1, max_nB = 1;
+      int max_gn = 1;
       for (auto &G : groups) max_gn = std::max(max_gn, G.n);
-      for (auto &C : cells) max_nB = std::max(max_nB, C.nB);
       auto chunks_for = [](long long work) {
         long long ch = (work + 4LL * NT - 1) / (4LL * NT);
         return (int)std::max(1LL, std::min(ch, 4096LL));
       };
       k_group_gather_D<<<dim3(ng, chunks_for((long long)max_gn * max_gn)), NT, 0, s>>>(
-          dgroups, dgcells, dcells, F, Dscr);
+          dgroups, dgcells, dbcells, Fb, Dscr);
       note_launch();
       // Cholesky and inverse factor of every entity's diagonal block, batched
       std::vector<JBlock> jbl(ng);
@@ -1010,24 +1143,54 @@ int gpu_setup(Handle *h, const double *a_nodes, cudaStream_t s) {
       note_launch();
       HIF_CUDA_TRY(cudaGetLastError());
       HIF_TRY(check_err(derr, s, "block Jacobi"));
+      lvl.release(Gpk);
+      lvl.release(Dscr);
       tm.mark("l" + std::to_string(l) + " jacobi diag");
-      const int sch = chunks_for((long long)max_nB * max_nB);
-      k_cell_scale_rows<<<dim3(ncells, sch), NT, 0, s>>>(dcells, dbmap, dgroups, Linv, F, Sscr);
-      k_cell_scale_cols<<<dim3(ncells, sch), NT, 0, s>>>(dcells, dbmap, dgroups, dgcells, Linv, F, Sscr);
-      note_launch(2);
-      HIF_CUDA_TRY(cudaGetLastError());
-      tm.mark("l" + std::to_string(l) + " jacobi scale");
+      // F_BB <- D F_BB D^T, cells in chunks whose row-scaled copies fit the scratch
+      const long long scap = std::max(setup_budget("HIFCN_SETUP_SCRATCH_BYTES", 0.5) /
+                                          (long long)sizeof(double), 1LL);
+      std::vector<int> sch_at = {0};
+      long long run = 0, maxrun = 0;
+      for (int c = 0; c < ncells; ++c) {
+        const long long nbb = (long long)cells[c].nB * cells[c].nB;
+        if (run > 0 && run + nbb > scap) {
+          sch_at.push_back(c);
+          run = 0;
+        }
+        run += nbb;
+        maxrun = std::max(maxrun, run);
+      }
+      sch_at.push_back(ncells);
+      double *Sscr = nullptr;
+      HIF_TRY(lvl.alloc(&Sscr, maxrun));
+      for (size_t k = 0; k + 1 < sch_at.size(); ++k) {
+        const int c0 = sch_at[k], nck = sch_at[k + 1] - c0;
+        int max_nB = 1;
+        for (int c = c0; c < c0 + nck; ++c) max_nB = std::max(max_nB, cells[c].nB);
+        const int sch = chunks_for((long long)max_nB * max_nB);
+        const long long base = cells[c0].Sc_off;
+        k_cell_scale_rows<<<dim3(nck, sch), NT, 0, s>>>(dbcells, c0, dbmap, dgroups, Linv, Fb, Sscr, base);
+        k_cell_scale_cols<<<dim3(nck, sch), NT, 0, s>>>(dbcells, c0, dbmap, dgroups, dgcells, Linv, Fb, Sscr,
+                                                        base);
+        note_launch(2);
+        HIF_CUDA_TRY(cudaGetLastError());
+      }
+      lvl.release(Sscr);
+      tm.mark("l" + std::to_string(l) + " jacobi scale (" + std::to_string(sch_at.size() - 1) + " chunks)");
     }
 
     // ---- skeletonization sub-steps
     std::vector<char> skeletonized(ng, 0);
     std::vector<int> codims = {1};
     if (dim == 3 && h->opt.skel_edges_3d) codims.push_back(2);
+    const long long wcap = std::max(setup_budget("HIFCN_SETUP_SCRATCH_BYTES", 0.5) /
+                                        (long long)sizeof(double), 1LL);
     for (int cd : codims) {
       std::vector<SSkel> sk;
       std::vector<long long> rowptr;
       std::vector<int2> rowent;
-      long long wsoff = 0, poff = 0;
+      std::vector<int> ws_at = {0};  // groups in launches whose workspaces fit the scratch
+      long long wsoff = 0, wsmax = 0, poff = 0;
       int max_n = 1;
       std::vector<int> rowid(N, -1);
       for (int g = 0; g < ng; ++g) {
@@ -1063,15 +1226,22 @@ int gpu_setup(Handle *h, const double *a_nodes, cudaStream_t s) {
         }
         rowptr.push_back((long long)rowent.size());
         x.R = (int)rows.size();
-        x.ws_off = wsoff;
         const long long nG = groups[g].n;
-        wsoff += (long long)x.R * nG + 5 * nG * nG + std::max<long long>(x.R, 1);
+        const long long need = (long long)x.R * nG + 5 * nG * nG + std::max<long long>(x.R, 1);
+        if (wsoff > 0 && wsoff + need > wcap) {
+          ws_at.push_back((int)sk.size());
+          wsoff = 0;
+        }
+        x.ws_off = wsoff;
+        wsoff += need;
+        wsmax = std::max(wsmax, wsoff);
         x.perm_off = poff;
         poff += nG;
         max_n = std::max(max_n, (int)nG);
         sk.push_back(x);
       }
       if (sk.empty()) continue;
+      ws_at.push_back((int)sk.size());
       SSkel *dsk = nullptr;
       long long *drowptr = nullptr;
       int2 *drowent = nullptr;
@@ -1081,18 +1251,21 @@ int gpu_setup(Handle *h, const double *a_nodes, cudaStream_t s) {
       HIF_TRY(sub.upload(&dsk, sk, s));
       HIF_TRY(sub.upload(&drowptr, rowptr, s));
       HIF_TRY(sub.upload(&drowent, rowent, s));
-      HIF_TRY(sub.alloc(&ws, wsoff));
+      HIF_TRY(sub.alloc(&ws, wsmax));
       HIF_TRY(sub.alloc(&dk, sk.size()));
       HIF_TRY(sub.alloc(&dperm, poff));
       size_t sm = (size_t)max_n * (sizeof(double) + sizeof(int)) + 16;
       HIF_TRY(set_smem((const void *)k_skel, sm));
-      k_skel<<<(int)sk.size(), NT, sm, s>>>(dsk, dgroups, dgcells, dcells, drowptr, drowent, Linv, F,
-                                            ws, vals, dk, dperm, eps, derr);
-      note_launch();
-      HIF_CUDA_TRY(cudaGetLastError());
+      for (size_t k = 0; k + 1 < ws_at.size(); ++k) {
+        const int t0 = ws_at[k], nt = ws_at[k + 1] - t0;
+        k_skel<<<nt, NT, sm, s>>>(dsk + t0, dgroups, dgcells, dbcells, drowptr, drowent, Linv, Fb, ws, vals,
+                                  dk + t0, dperm, eps, derr);
+        note_launch();
+        HIF_CUDA_TRY(cudaGetLastError());
+      }
       HIF_TRY(check_err(derr, s, "skeletonization"));
       tm.mark("l" + std::to_string(l) + " skel codim " + std::to_string(cd) + " (n<=" +
-              std::to_string(max_n) + ")");
+              std::to_string(max_n) + ", " + std::to_string(ws_at.size() - 1) + " launches)");
       std::vector<int> kh(sk.size()), ph(poff);
       HIF_CUDA_TRY(cudaMemcpyAsync(kh.data(), dk, kh.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
       HIF_CUDA_TRY(cudaMemcpyAsync(ph.data(), dperm, ph.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1127,11 +1300,12 @@ int gpu_setup(Handle *h, const double *a_nodes, cudaStream_t s) {
       if (alive[d]) next.push_back(d);
     active.swap(next);
     prev = std::move(P);
-    F_prev = F;
-    dcells_prev = dcells;
-    cells_prev = cells;
+    Fb_prev = Fb;
+    dbcells_prev = dbcells;
+    if (lean) HIF_TRY(stream_level(l));
   }
-  keep.release(F_prev);
+  keep.release(Fb_prev);
+  keep.release(dbcells_prev);
 
   // ---- concatenate the level value pools and shift the offsets
   long long total = 0;
@@ -1140,17 +1314,42 @@ int gpu_setup(Handle *h, const double *a_nodes, cudaStream_t s) {
     base[l] = total;
     total += level_nvals[l];
   }
-  HIF_TRY(dev_alloc(h, (void **)&h->f64.vals, std::max<long long>(total, 1) * sizeof(double)));
-  for (int l = 0; l <= L; ++l)
-    if (level_nvals[l])
-      HIF_CUDA_TRY(cudaMemcpyAsync(h->f64.vals + base[l], level_vals[l], level_nvals[l] * sizeof(double),
-                                   cudaMemcpyDeviceToDevice, s));
+  if (!lean && lean_mode == -1) {  // room for the FP64 pool and the handle-wide casts?
+    size_t fr = 0, tot = 0;
+    const double need = (double)total * (8 + 4 + (want_b16 ? 2 : 0)) + 32.0 * (double)N + (1u << 30);
+    if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && (double)fr < need) lean = true;
+    cudaGetLastError();
+  }
+  if (lean) {
+    HIF_TRY(go_lean(L + 1));
+    HIF_TRY(dev_alloc(h, (void **)&h->f32.vals, std::max<long long>(total, 1) * sizeof(float)));
+    if (want_b16) HIF_TRY(dev_alloc(h, &h->bf16_vals, std::max<long long>(total, 1) * 2));
+    for (int l = 0; l <= L; ++l) {
+      if (level_nvals[l]) {
+        HIF_CUDA_TRY(cudaMemcpyAsync(h->f32.vals + base[l], level_f32[l], level_nvals[l] * sizeof(float),
+                                     cudaMemcpyDeviceToDevice, s));
+        if (want_b16)
+          HIF_CUDA_TRY(cudaMemcpyAsync(static_cast<unsigned short *>(h->bf16_vals) + base[l], level_b16[l],
+                                       level_nvals[l] * 2, cudaMemcpyDeviceToDevice, s));
+      }
+      HIF_CUDA_TRY(cudaStreamSynchronize(s));
+      keep.release(level_f32[l]);
+      keep.release(level_b16[l]);
+    }
+    h->lean_setup = true;
+  } else {
+    HIF_TRY(dev_alloc(h, (void **)&h->f64.vals, std::max<long long>(total, 1) * sizeof(double)));
+    for (int l = 0; l <= L; ++l)
+      if (level_nvals[l])
+        HIF_CUDA_TRY(cudaMemcpyAsync(h->f64.vals + base[l], level_vals[l], level_nvals[l] * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, s));
+  }
   h->nvals = total;
   for (int l = 0; l < L; ++l) {
     for (auto &c : h->lv_host[l].cells) {
       c.G_off += base[l];
       c.V_off += base[l];
-      c.S_off += base[l];
+      if (c.S_off >= 0) c.S_off += base[l];
     }
     for (auto &g : h->lv_host[l].groups) g.H_off += base[l];
   }

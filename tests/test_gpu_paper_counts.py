@@ -97,3 +97,20 @@ def _gpu_mean_iters_n(H, w, steps):
     assert np.isfinite(u.cpu().numpy()).all()
     h.close()
     return float(np.mean(its))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("ex", ["heat", "logistic"])
+def test_gpu_counts_at_table_sizes_3d(H, ex):
+    """The 3D tables' middle size, 127^3 (leaf 8, FP64 factor and CG, tolerance
+    1e-12, the paper's 3D recipes): the mean count over the first 10 steps lies
+    within 1.5 of the count printed for 127^3, eps = 1e-6 below 1e-3."""
+    import workloads as W
+    got = {}
+    for eps in (1e-3, 1e-6):
+        w = W.paper_heat3d(128, 8, eps, seed=0, logistic=(ex == "logistic"))
+        got[eps] = _gpu_mean_iters_n(H, w, TABLE_STEPS)
+        printed = _printed_at(ex, 3, eps, 127)
+        print(f"{ex} 127^3 eps {eps:g}: GPU mean {got[eps]:.2f}, printed {printed}")
+        assert abs(got[eps] - printed) <= WINDOW, (ex, eps, got[eps], printed)
+    assert got[1e-6] < got[1e-3]

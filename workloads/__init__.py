@@ -257,12 +257,15 @@ def gaussian_bumps_coefficient(rng: np.random.Generator, n: int, dim: int, count
                                sigma2: float, lo: float, hi: float) -> np.ndarray:
     """Sum of ``count`` Gaussian bumps at uniform random centres, mapped affinely
     onto [lo, hi] (paper Eqs. 2d_coeff / 3d_coeff; min -> lo, max -> hi)."""
-    xs = node_coords(n, dim)
     centres = rng.uniform(0.0, 1.0, size=(count, dim))
-    s = np.zeros((n + 1,) * dim)
-    for c in centres:
-        r2 = sum((xs[ax] - c[ax]) ** 2 for ax in range(dim))
-        s = s + np.exp(-r2 / sigma2)
+    t = np.arange(n + 1, dtype=np.float64) / n
+    # each bump is a product of one Gaussian per axis: E[ax][c, i] at coordinate t_i
+    E = [np.exp(-((t[None, :] - centres[:, ax, None]) ** 2) / sigma2) for ax in range(dim)]
+    if dim == 2:
+        s = E[1].T @ E[0]  # s[y, x] = sum_c E_y[c, y] E_x[c, x]
+    else:
+        zy = (E[2][:, :, None] * E[1][:, None, :]).reshape(count, -1)
+        s = (zy.T @ E[0]).reshape((n + 1,) * 3)
     smin, smax = float(s.min()), float(s.max())
     return lo + (s - smin) * ((hi - lo) / (smax - smin))
 
