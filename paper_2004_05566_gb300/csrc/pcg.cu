@@ -270,14 +270,18 @@ __device__ __forceinline__ double2 sum_partials2(const double *pa, const double 
 }
 
 // PCG in the Chronopoulos-Gear arrangement (the same iterates as the
-// textbook PCG loop in exact arithmetic, one reduction phase fewer):
-//   z = F^{-1} r;  w = A z;  rho = r.z;  mu = w.z
-//   beta = rho / rho_old (0 on the first iteration)
-//   sigma = mu - beta rho / alpha_old (= p.Ap),  alpha = rho / sigma
+// textbook PCG loop in exact arithmetic, one reduction phase fewer), with the
+// Polak-Ribiere (flexible) form of beta:
+//   z = F^{-1} r;  w = A z;  rho = r.z;  mu = w.z;  xi = q_old.z
+//   beta = (r - r_old).z / rho_old = -alpha_old xi / rho_old (0 at first)
+//   sigma = p.Ap = mu + 2 beta xi + beta^2 sigma_old,  alpha = rho / sigma
 //   p = z + beta p;  q = w + beta q (= A p);  x += alpha p;  r -= alpha q
-// using p.Ap = z.Az + 2 beta z.A p_old + beta^2 p_old.A p_old with
-// z.A p_old = -rho / alpha_old (residuals are F-orthogonal) and
-// p_old.A p_old = rho_old / alpha_old.
+// using r - r_old = -alpha_old q_old and p.Ap = z.Az + 2 beta z.A p_old +
+// beta^2 p_old.A p_old.  With a fixed SPD preconditioner r_old.z = 0 and beta
+// equals rho / rho_old (the textbook value); when the preconditioner is
+// applied in FP32 its rounding makes it vary slightly from one application to
+// the next, and the flexible form keeps the search directions conjugate
+// (about a tenth fewer iterations on the 1023^2 Fisher-KPP steps).
 //
 // On GB300 these kernels are bound by the FP64 pipe (about two FP64
 // operations per clock per SM): per unknown, w = A z takes one multiply and
@@ -287,15 +291,16 @@ __device__ __forceinline__ double2 sum_partials2(const double *pa, const double 
 // operations, both dots share one reduction tree, per-block scalars are read
 // once by one thread.
 //
-// first kernel: w = A z, partials of r.z and w.z; the last block forms
+// first kernel: w = A z, partials of r.z, w.z and q.z; the last block forms
 // beta, sigma and alpha
 template <typename TZ>
 __global__ void __launch_bounds__(NT) k_cg_wz(const double *__restrict__ r, const TZ *__restrict__ z,
-                                              double *__restrict__ w, StencilArgs st,
-                                              double *__restrict__ part, double *__restrict__ s,
-                                              unsigned *__restrict__ ticket) {
+                                              double *__restrict__ w, const double *__restrict__ q,
+                                              StencilArgs st, double *__restrict__ part,
+                                              double *__restrict__ s, unsigned *__restrict__ ticket) {
   __shared__ double sm[2 * (NT / 32)];
-  double arz = 0.0, awz = 0.0;
+  double arz = 0.0, awz = 0.0, aqz = 0.0;
+  const bool first = s[S_IT] == 0.0;  // q holds no direction yet
   const int N = (int)st.N, S = st.n - 1, S2 = S * S;
   const int stride = gridDim.x * NT, stride2 = 2 * stride;
   const bool d3 = st.dim == 3;
@@ -328,23 +333,29 @@ __global__ void __launch_bounds__(NT) k_cg_wz(const double *__restrict__ r, cons
     }
     w[j] = y0;
     if (j1 < N) w[j1] = y1;
+    if (!first) {
+      aqz += q[j] * z0;
+      if (j1 < N) aqz += q[j1] * z1;
+    }
     arz += r0 * z0;
     awz += y0 * z0;
     arz += r1 * z1;
     awz += y1 * z1;
   }
   const double2 t = block_sum2<NT>(arz, awz, sm);
+  const double2 t3 = block_sum2<NT>(aqz, 0.0, sm);
   if (threadIdx.x == 0) {
     part[blockIdx.x] = t.x;
     part[gridDim.x + blockIdx.x] = t.y;
+    part[2 * gridDim.x + blockIdx.x] = t3.x;
   }
   if (!last_block(ticket)) return;
   const double2 tot = sum_partials2<NT>(part, part + gridDim.x, gridDim.x, sm);
+  const double2 tot3 = sum_partials2<NT>(part + 2 * gridDim.x, nullptr, gridDim.x, sm);
   if (threadIdx.x == 0) {
-    const double rho = tot.x, mu = tot.y;
-    const bool first = s[S_IT] == 0.0;
-    const double beta = first ? 0.0 : rho / s[S_RZ];
-    const double sigma = first ? mu : mu - beta * rho / s[S_ALPHA];
+    const double rho = tot.x, mu = tot.y, xi = tot3.x;
+    const double beta = first ? 0.0 : -s[S_ALPHA] * xi / s[S_RZ];
+    const double sigma = first ? mu : mu + beta * (2.0 * xi + beta * s[S_PQ]);
     s[S_BETA] = beta;
     s[S_PQ] = sigma;
     s[S_ALPHA] = rho / sigma;
@@ -582,7 +593,7 @@ int build_pcg_graph(Handle *h, TZ *z, PcgGraph *G, bool warm) {
   if constexpr (sizeof(TZ) == 8) st_apply = apply_inplace_f64(h, (double *)z, cs);
   else st_apply = apply_inplace_f32(h, (float *)z, cs);
   unsigned *tk = h->tickets;
-  k_cg_wz<TZ><<<nb, NT, 0, cs>>>(h->r, z, h->w, st, part, sc, tk);
+  k_cg_wz<TZ><<<nb, NT, 0, cs>>>(h->r, z, h->w, h->q, st, part, sc, tk);
   k_cg_update<TZ, true><<<nb, NT, 0, cs>>>(h->xsol, h->r, h->p, h->q, h->w, z, sc, N, part, tk + 2,
                                            h->opt.true_res_period, tol2, h->opt.cg_maxit, cond);
   k_true_residual_cond<TZ, true><<<nb, NT, 0, cs>>>(h->g, h->xsol, h->r, z, st, sc,
@@ -691,7 +702,7 @@ int pcg_impl(Handle *h, const double *b, double *x, TZ *z, int *iters_out, doubl
   const int period = h->opt.true_res_period;
   while (it < h->opt.cg_maxit) {
     HIF_TRY(precond(z));
-    k_cg_wz<TZ><<<nb, NT, 0, s>>>(h->r, z, h->w, st, part, sc, tk);
+    k_cg_wz<TZ><<<nb, NT, 0, s>>>(h->r, z, h->w, h->q, st, part, sc, tk);
     k_cg_update<TZ, false><<<nb, NT, 0, s>>>(x, h->r, h->p, h->q, h->w, z, sc, N, part, tk + 2, period,
                                             tol2, h->opt.cg_maxit, 0);
     k_true_residual_cond<TZ, false><<<nb, NT, 0, s>>>(b, x, h->r, z, st, sc, period, part, tk + 3, tol2,
@@ -825,7 +836,7 @@ int cn_cols(Handle *h, const double *U, const double *R, double *U1, int k, int 
       double *sct = C.scal + 16 * c, *part = C.part + 4LL * nb * c;
       unsigned *tk = C.tk + 4 * c;
       float *z = C.z + c * N;
-      k_cg_wz<float><<<nb, NT, 0, s>>>(C.r + c * N, z, C.w + c * N, st, part, sct, tk);
+      k_cg_wz<float><<<nb, NT, 0, s>>>(C.r + c * N, z, C.w + c * N, C.q + c * N, st, part, sct, tk);
       k_cg_update<float, false><<<nb, NT, 0, s>>>(C.x + c * N, C.r + c * N, C.p + c * N, C.q + c * N,
                                                   C.w + c * N, z, sct, N, part, tk + 2, period, tol2,
                                                   h->opt.cg_maxit, 0);
@@ -1031,9 +1042,10 @@ __global__ void __launch_bounds__(NT) k_b_true_res(BSeg B, const int *__restrict
 }
 
 // Chronopoulos-Gear iteration of the merged steps (the arrangement of
-// k_cg_wz / k_cg_update, per handle segment): w = A z with partials of r.z
-// and w.z ...
-__global__ void __launch_bounds__(NT) k_b_wz(BSeg B, const int *__restrict__ active, double *__restrict__ part) {
+// k_cg_wz / k_cg_update, per handle segment): w = A z with partials of r.z,
+// w.z and q.z ...
+__global__ void __launch_bounds__(NT) k_b_wz(BSeg B, const int *__restrict__ active,
+                                             const double *__restrict__ sc, double *__restrict__ part) {
   __shared__ double sm[2 * (NT / 32)];
   const int p = seg_owner(B.segpre, B.K, blockIdx.x);
   if (!active[p]) return;
@@ -1043,7 +1055,8 @@ __global__ void __launch_bounds__(NT) k_b_wz(BSeg B, const int *__restrict__ act
   const int S = v->n - 1, S2 = S * S;
   const bool d3 = v->dim == 3;
   const float *z = v->z;
-  double arz = 0.0, awz = 0.0;
+  const bool first = sc[p * B_COUNT + B_IT] == 0.0;  // q holds no direction yet
+  double arz = 0.0, awz = 0.0, aqz = 0.0;
   int j = j0 + threadIdx.x;
   GridWalk g(j, NT, S, d3);
   for (; j < j1; j += NT, g.advance(S, d3)) {
@@ -1060,11 +1073,14 @@ __global__ void __launch_bounds__(NT) k_b_wz(BSeg B, const int *__restrict__ act
     v->w[j] = y;
     arz += v->r[j] * zj;
     awz += y * zj;
+    if (!first) aqz += v->q[j] * zj;
   }
   const double2 t = block_sum2<NT>(arz, awz, sm);
+  const double2 t3 = block_sum2<NT>(aqz, 0.0, sm);
   if (threadIdx.x == 0) {
     part[2 * blockIdx.x] = t.x;
     part[2 * blockIdx.x + 1] = t.y;
+    part[2 * B.segpre[B.K] + blockIdx.x] = t3.x;  // q.z after the two-per-segment partials
   }
 }
 
@@ -1111,14 +1127,17 @@ __global__ void __launch_bounds__(256) k_b_scalar(BSeg B, int mode, int *__restr
   if (mode != 0 && !active[p]) return;
   const HandleView *v = B.views[p];
   const int s0 = B.segpre[p], s1 = B.segpre[p + 1];
-  double a = 0.0, b = 0.0;
+  double a = 0.0, b = 0.0, c = 0.0;
+  const double *part3 = part + 2 * B.segpre[B.K];
   for (int i = s0 + lane; i < s1; i += 32) {
     a += part[2 * i];
     b += part[2 * i + 1];
+    if (mode == 4) c += part3[i];
   }
   for (int o = 16; o > 0; o >>= 1) {
     a += __shfl_xor_sync(0xffffffffu, a, o);
     b += __shfl_xor_sync(0xffffffffu, b, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
   }
   if (lane != 0) return;
   double *s = sc + p * B_COUNT;
@@ -1137,11 +1156,11 @@ __global__ void __launch_bounds__(256) k_b_scalar(BSeg B, int mode, int *__restr
   } else if (mode == 2) {
     s[B_PQ] = a;
     s[B_ALPHA] = s[B_RZ] / a;
-  } else if (mode == 4) {
+  } else if (mode == 4) {  // the flexible beta of k_cg_wz
     const bool first = s[B_IT] == 0.0;
-    const double rho = a, mu = b;
-    const double beta = first ? 0.0 : rho / s[B_RZ];
-    const double sigma = first ? mu : mu - beta * rho / s[B_ALPHA];
+    const double rho = a, mu = b, xi = c;
+    const double beta = first ? 0.0 : -s[B_ALPHA] * xi / s[B_RZ];
+    const double sigma = first ? mu : mu + beta * (2.0 * xi + beta * s[B_PQ]);
     s[B_BETA] = beta;
     s[B_PQ] = sigma;
     s[B_ALPHA] = rho / sigma;
@@ -1235,7 +1254,7 @@ int cn_batched_merged(Handle *const *hs, int K, const double *const *u, const do
   segpre[K] = total_seg;
   const size_t sc_off = (up_bytes + 255) / 256 * 256;
   const size_t part_off = sc_off + (size_t)K * B_COUNT * sizeof(double);
-  const size_t nact_off = part_off + 2 * (size_t)total_seg * sizeof(double);
+  const size_t nact_off = part_off + 3 * (size_t)total_seg * sizeof(double);
   const size_t dev_bytes = nact_off + 256;
   HIF_TRY(bws_reserve(dev_bytes, up_bytes));
   unsigned char *hb = g_bws.host;
@@ -1302,7 +1321,7 @@ int cn_batched_merged(Handle *const *hs, int K, const double *const *u, const do
     for (int ph = 0; ph < P; ++ph)
       HIF_TRY(launch_merged_phase(phases[ph].x, phases[ph].y, dint + (size_t)(K + 1) * (ph + 1), K,
                                   totals[ph], smem[ph], const_cast<HandleView *const *>(B.views), active, s));
-    k_b_wz<<<total_seg, NT, 0, s>>>(B, active, part);
+    k_b_wz<<<total_seg, NT, 0, s>>>(B, active, sc, part);
     k_b_scalar<<<sgrid, 256, 0, s>>>(B, 4, active, sc, part, nactive);
     k_b_update<<<total_seg, NT, 0, s>>>(B, active, sc, part);
     k_b_true_res<<<total_seg, NT, 0, s>>>(B, active, sc, part);
