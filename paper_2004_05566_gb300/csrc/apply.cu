@@ -1010,6 +1010,25 @@ __device__ __forceinline__ void load_xcols(const T *xs, int nq, int lane, T (&xa
 // first pair of a chunk that warp w takes, given the running pair count u (mod 8)
 __device__ __forceinline__ int first_pair(int warp, int u) { return (warp - u) & (kPairWarps - 1); }
 
+// Compensated FP32 summation for the leaf backward step.  The _rn
+// intrinsics keep the compiler from fusing the additions into FMAs, which
+// would break the error-free transformations.
+// Kahan's summation: c carries the negated rounding error of the running sum
+// a (the sum is a - c).
+__device__ __forceinline__ void kahan_acc(float &a, float &c, float p) {
+  const float y = __fsub_rn(p, c);
+  const float t = __fadd_rn(a, y);
+  c = __fsub_rn(__fsub_rn(t, a), y);
+  a = t;
+}
+// Knuth's two-sum: hi + p = t + e exactly; hi <- t, lo += e.
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float p) {
+  const float t = __fadd_rn(hi, p);
+  const float z = __fsub_rn(t, hi);
+  lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(t, z)), __fsub_rn(p, z)));
+  hi = t;
+}
+
 // forward: contributions c_B = V x_I, streaming the V rows.  Persistent: a
 // CTA takes cells blockIdx.x, blockIdx.x + gridDim.x, ...; warp 8 copies the
 // V rows, warp 9 gathers x_I of the next cell, warps 0-7 compute and write
@@ -1124,8 +1143,18 @@ __global__ void __launch_bounds__(kTmaThreads, 4) k_cell_fwd_tma_S(const CellDes
 // column sums into the lane-owned accumulators; V rows add -V^T x_B to the
 // same accumulators.  At the end of the cell the 8 warps' column sums and
 // the row dots meet: x[I[i]] = rd[i] + sum_w part_w[i].
-template <typename T>
-__global__ void __launch_bounds__(kTmaThreads, 2) k_cell_bwd_tma_S(const CellDesc *__restrict__ cells,
+//
+// Accuracy (kComp).  With a large time step the result is dominated by
+// -V^T x_B, the extension of the boundary values into the cell (S x_I is a
+// small correction), and it feeds CG through A, which magnifies rough
+// errors: plain FP32 sums of the V rows cost the 1023^2 Fisher-KPP steps 0.3
+// PCG iterations (2.35 instead of the 2.05 of exact accumulation).  So the V
+// rows' products are added in pairs by Kahan's compensated summation, each
+// warp rounds its compensated sums once, and the row dots and the warps' sums
+// are combined by two-sum: the same 2.05 iterations as FP64 accumulation for
+// about 6% more kernel time (3 CTAs per SM still fit in 64 registers).
+template <typename T, bool kComp = true>
+__global__ void __launch_bounds__(kTmaThreads, kComp ? 3 : 2) k_cell_bwd_tma_S(const CellDesc *__restrict__ cells,
                                                                    int ncells,
                                                                    const int2 *__restrict__ chunk_of,
                                                                    const int *__restrict__ chunk_tab,
@@ -1189,6 +1218,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2) k_cell_bwd_tma_S(const CellDes
     T xa[4], xb[4];
     load_xcols(xs, nq, lane, xa, xb);
     T ca[4] = {T(0), T(0), T(0), T(0)}, cb[4] = {T(0), T(0), T(0), T(0)};
+    T la[4] = {T(0), T(0), T(0), T(0)}, lb[4] = {T(0), T(0), T(0), T(0)};  // Kahan terms (kComp)
     consumers_sync();  // rd and part of the previous cell are no longer read
     for (int j = 0; j < nch; ++j, ++k) {
       const int sidx = (int)(k % kStagesBwd);
@@ -1245,22 +1275,39 @@ __global__ void __launch_bounds__(kTmaThreads, 2) k_cell_bwd_tma_S(const CellDes
           const bool has1 = r0 + 1 < rr.y;
           const T *row0 = base + 2 * p * vs;
           const T y0 = -xbv[r0 - nI], y1 = has1 ? -xbv[r0 + 1 - nI] : T(0);
-          if (lane < nq) {
-            T v[4];
-            ld4(row0 + 4 * lane, v);
-            axpy4(ca, v, y0);
-            if (has1) {
-              ld4(row0 + vs + 4 * lane, v);
-              axpy4(ca, v, y1);
+          if constexpr (kComp) {  // the pair's two products summed, then added by Kahan's summation
+            if (lane < nq) {
+              T v[4], w[4] = {T(0), T(0), T(0), T(0)};
+              ld4(row0 + 4 * lane, v);
+              if (has1) ld4(row0 + vs + 4 * lane, w);
+#pragma unroll
+              for (int e = 0; e < 4; ++e) kahan_acc(ca[e], la[e], __fmaf_rn(w[e], y1, __fmul_rn(v[e], y0)));
             }
-          }
-          if (lane + 32 < nq) {
-            T v[4];
-            ld4(row0 + 4 * (lane + 32), v);
-            axpy4(cb, v, y0);
-            if (has1) {
-              ld4(row0 + vs + 4 * (lane + 32), v);
-              axpy4(cb, v, y1);
+            if (lane + 32 < nq) {
+              T v[4], w[4] = {T(0), T(0), T(0), T(0)};
+              ld4(row0 + 4 * (lane + 32), v);
+              if (has1) ld4(row0 + vs + 4 * (lane + 32), w);
+#pragma unroll
+              for (int e = 0; e < 4; ++e) kahan_acc(cb[e], lb[e], __fmaf_rn(w[e], y1, __fmul_rn(v[e], y0)));
+            }
+          } else {
+            if (lane < nq) {
+              T v[4];
+              ld4(row0 + 4 * lane, v);
+              axpy4(ca, v, y0);
+              if (has1) {
+                ld4(row0 + vs + 4 * lane, v);
+                axpy4(ca, v, y1);
+              }
+            }
+            if (lane + 32 < nq) {
+              T v[4];
+              ld4(row0 + 4 * (lane + 32), v);
+              axpy4(cb, v, y0);
+              if (has1) {
+                ld4(row0 + vs + 4 * (lane + 32), v);
+                axpy4(cb, v, y1);
+              }
             }
           }
         }
@@ -1270,14 +1317,28 @@ __global__ void __launch_bounds__(kTmaThreads, 2) k_cell_bwd_tma_S(const CellDes
       if (lane == 0) mbar_arrive(&empty[sidx]);
     }
     T *pw = part + warp * xstride;
+    if constexpr (kComp) {  // each warp's compensated column sums, rounded once
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        ca[e] = __fsub_rn(ca[e], la[e]);
+        cb[e] = __fsub_rn(cb[e], lb[e]);
+      }
+    }
     if (lane < nq) st4(pw + 4 * lane, ca);
     if (lane + 32 < nq) st4(pw + 4 * (lane + 32), cb);
     consumers_sync();
     const int *is = is0 + b * xstride;
     for (int i = threadIdx.x; i < nI; i += kConsumers) {
       T s = rd[i];
+      if constexpr (kComp) {  // the row dot and the warps' sums, by two-sum
+        T lo = T(0);
 #pragma unroll
-      for (int w = 0; w < kConsumerWarps; ++w) s += part[w * xstride + i];
+        for (int w = 0; w < kConsumerWarps; ++w) two_sum_acc(s, lo, part[w * xstride + i]);
+        s = __fadd_rn(s, lo);
+      } else {
+#pragma unroll
+        for (int w = 0; w < kConsumerWarps; ++w) s += part[w * xstride + i];
+      }
       x[is[i]] = s;
     }
     __syncwarp();
@@ -1899,7 +1960,8 @@ int set_smem_limits() {
     HIF_CUDA_TRY(cudaFuncSetAttribute(k_group_rows_split<T, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     HIF_CUDA_TRY(cudaFuncSetAttribute(k_group_cols_split<T, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     HIF_CUDA_TRY(cudaFuncSetAttribute(k_cell_fwd_tma_S<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-    HIF_CUDA_TRY(cudaFuncSetAttribute(k_cell_bwd_tma_S<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    HIF_CUDA_TRY(cudaFuncSetAttribute(k_cell_bwd_tma_S<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    HIF_CUDA_TRY(cudaFuncSetAttribute(k_cell_bwd_tma_S<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   }
   done = true;
   return HIF_OK;
@@ -2142,11 +2204,13 @@ int launch_cell_bwd(Handle *h, const LevelDev &lv, int l, const FactorValues<T> 
   }
   if constexpr (sizeof(T) == 4) {
     if (sf) {
+      // compensated accumulation of -V^T x_B (HIFCN_LEAF_COMP=0: plain FP32 sums, for measurements)
+      static const bool comp = !(std::getenv("HIFCN_LEAF_COMP") && std::getenv("HIFCN_LEAF_COMP")[0] == '0');
+      auto kern = comp ? k_cell_bwd_tma_S<T, true> : k_cell_bwd_tma_S<T, false>;
       size_t sm = (size_t)kStagesBwd * kStageBytes + tma_bwd_smem_elems(lv) * sizeof(T);
-      const int grid = tma_grid((const void *)k_cell_bwd_tma_S<T>, sm, lv.ncells, h->tma_ctas);
-      HIF_CUDA_TRY(launch_k(k_cell_bwd_tma_S<T>, grid, kTmaThreads, sm, s, lv.cells, lv.ncells, lv.chunk_of[1],
-                                                         lv.chunk_tab[1], h->idx, fv.vals, x,
-                                                         h->scal + kScalErr, lv.max_nI, lv.max_nB));
+      const int grid = tma_grid((const void *)kern, sm, lv.ncells, h->tma_ctas);
+      HIF_CUDA_TRY(launch_k(kern, grid, kTmaThreads, sm, s, lv.cells, lv.ncells, lv.chunk_of[1], lv.chunk_tab[1],
+                            h->idx, fv.vals, x, h->scal + kScalErr, lv.max_nI, lv.max_nB));
       return HIF_OK;
     }
   }
