@@ -112,6 +112,7 @@ int build_device_factor(Handle *h, const std::vector<double> &vals64, cudaStream
 
 int make_cell_inverses(Handle *h, cudaStream_t s);
 int cast_values_bf16(Handle *h, cudaStream_t s);
+int make_root_dense(Handle *h, cudaStream_t s);
 
 // Upload descriptors of every level, allocate the contribution scratch and
 // the FP32 copy (values already on the device in h->f64.vals).
@@ -318,6 +319,7 @@ int finish_device_factor(Handle *h, cudaStream_t s) {
     h->has_bf16 = true;
   }
   h->fp64_released = lean;
+  HIF_TRY(make_root_dense(h, s));
   HIF_CUDA_TRY(cudaStreamSynchronize(s));
   HIF_TRY(build_upper_plan(h));
   HIF_TRY(build_view(h));
@@ -466,6 +468,9 @@ void release_factor(Handle *h) {
   h->upper_levels = nullptr;
   h->upper_rt = nullptr;
   h->root_split = false;
+  h->root_S = nullptr;
+  h->root_S_ld = 0;
+  h->lean_setup = false;
   h->view = nullptr;
   h->view_ok = false;
   h->upper_grid[0] = h->upper_grid[1] = 0;

@@ -1406,6 +1406,54 @@ __global__ void __launch_bounds__(kRootThreads) k_root(int nr, const int *__rest
   root_unit<T, kRootThreads, TV>(nr, ridx, G, x, reinterpret_cast<T *>(smem_raw));
 }
 
+// Small roots, FP32 apply: x_r <- S_r x_r with S_r = G_r^T G_r stored as a
+// full symmetric matrix (rows of ld floats, zero padding): one pass of row
+// dots instead of the two dependent triangular passes of root_unit, whose
+// column pass is a long serial chain per thread for a root of ~100 DOFs.
+__global__ void __launch_bounds__(kRootThreads) k_root_dense(int nr, const int *__restrict__ ridx,
+                                                             const float *__restrict__ S, int ld,
+                                                             float *__restrict__ x) {
+  pdl_enter();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float *xs = reinterpret_cast<float *>(smem_raw);
+  for (int i = threadIdx.x; i < ld; i += kRootThreads) xs[i] = i < nr ? x[ridx[i]] : 0.f;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int NW = kRootThreads / 32;
+  for (int r0 = warp * kRows; r0 < nr; r0 += NW * kRows) {
+    const float *rp[kRows];
+    int nq[kRows];
+#pragma unroll
+    for (int u = 0; u < kRows; ++u) {
+      const int r = r0 + u;
+      rp[u] = S + (long long)(r < nr ? r : 0) * ld;
+      nq[u] = r < nr ? ld / 4 : 0;
+    }
+    float acc[kRows];
+    warp_rows_dot4<float, float>(rp, nq, xs, acc);
+    if (lane == 0) {
+#pragma unroll
+      for (int u = 0; u < kRows; ++u)
+        if (r0 + u < nr) x[ridx[r0 + u]] = acc[u];
+    }
+  }
+}
+
+// S_r = G_r^T G_r from the packed FP32 G_r, accumulated in FP64 and rounded
+// once: S[i][j] = sum_{k >= max(i, j)} G[k][i] G[k][j].  grid = rows.
+__global__ void __launch_bounds__(256) k_make_root_S(const float *__restrict__ G, int nr, int ld,
+                                                     float *__restrict__ S) {
+  const int i = blockIdx.x;
+  for (int j = threadIdx.x; j < ld; j += 256) {
+    double acc = 0.0;
+    if (j < nr)
+      for (int k = i > j ? i : j; k < nr; ++k)
+        acc += (double)G[tri_off(k) + i] * (double)G[tri_off(k) + j];
+    S[(long long)i * ld + j] = (float)acc;
+  }
+}
+
+
 // ------------------------------------------------- fused upper-level sweep
 //
 // The upper levels of the tree hold little data, and as separate launches
@@ -2296,10 +2344,19 @@ int apply_levels(Handle *h, const FactorValues<T> &fv, T *x, cudaStream_t s) {
   } else if (h->root_n > 0) {
     const double nr = h->root_n, E = sizeof(T);
     const bool b16 = bf16_level<T>(h, h->L);
-    StatScope sc(h, "root", -1, nr * (nr + 1) * (b16 ? 2.0 : E) + 4 * nr * E + 8 * nr, s);
+    const bool dense = sizeof(T) == 4 && !b16 && h->root_S;
+    StatScope sc(h, "root", -1,
+                 dense ? nr * h->root_S_ld * E + 2 * nr * E + 4 * nr
+                       : nr * (nr + 1) * (b16 ? 2.0 : E) + 4 * nr * E + 8 * nr, s);
     const int *ridx = h->idx + h->root_idx_off;
     T *rt = reinterpret_cast<T *>(h->upper_rt);
-    if (h->root_split) {  // row blocks, then column blocks, over many CTAs
+    if (dense) {
+      if constexpr (sizeof(T) == 4) {
+        const size_t sm = (size_t)h->root_S_ld * sizeof(float);
+        HIF_CUDA_TRY(launch_k(k_root_dense, 1, kRootThreads, sm, s, h->root_n, ridx, h->root_S, h->root_S_ld, x));
+        note_launch();
+      }
+    } else if (h->root_split) {  // row blocks, then column blocks, over many CTAs
       const int units = (h->root_n + kRootBlock - 1) / kRootBlock;
       const size_t sm1 = (size_t)pad4(h->root_n) * sizeof(T), sm2 = ((size_t)h->root_n + 256) * sizeof(T);
       bool done = false;
@@ -2953,6 +3010,17 @@ int apply_inplace_f64_with_scratch(Handle *h, double *contrib, double *x, cudaSt
 }
 
 // S = G^T G of the cells of the levels the FP32 S-form kernels will apply.
+// the full symmetric root of small FP32 roots (k_root_dense)
+int make_root_dense(Handle *h, cudaStream_t s) {
+  if (!h->has_f32 || h->has_bf16 || h->root_n <= 0 || h->root_n > kRootDenseMax) return HIF_OK;
+  h->root_S_ld = (int)pad4(h->root_n);
+  HIF_TRY(dev_alloc(h, (void **)&h->root_S, (size_t)h->root_n * h->root_S_ld * sizeof(float)));
+  k_make_root_S<<<h->root_n, 256, 0, s>>>(h->f32.vals + h->root_G_off, h->root_n, h->root_S_ld, h->root_S);
+  note_launch();
+  HIF_CUDA_TRY(cudaGetLastError());
+  return HIF_OK;
+}
+
 int make_cell_inverses(Handle *h, cudaStream_t s) {
   if (h->opt.precision != HIF_FP32 && h->opt.precision != HIF_FP32_BF16TOP) return HIF_OK;
   for (size_t l = 0; l < h->lv.size(); ++l) {

@@ -64,6 +64,9 @@ constexpr int kStageBytes = 15872;  // 124 x 128 B: three backward CTAs fit an S
 // cells have S_off = -1).
 constexpr int kSformMaxNI = 256;
 
+// FP32 roots up to this size are applied as a full symmetric matrix.
+constexpr int kRootDenseMax = 512;
+
 // Separator entities above this size are applied split over many CTAs, and
 // roots above kRootSplitDofs by a row-block and a column-block launch.
 constexpr int kSplitDofs = 256;
@@ -287,6 +290,10 @@ struct hif_handle {
   hifcn::UpperLevel *upper_levels = nullptr;  // device
   void *upper_rt = nullptr;                   // device root scratch (root_n doubles)
   bool root_split = false;                    // root applied by row- and column-block launches
+  // small FP32 roots: A_L^{-1} = G_r^T G_r as a full symmetric matrix (FP32,
+  // rows padded to root_S_ld), applied by one pass of row dots
+  float *root_S = nullptr;
+  int root_S_ld = 0;
   int tma_ctas = 0;                           // CTAs per SM of the leaf kernels (0: as many as fit)
   hifcn::HandleView *view = nullptr;          // device view for the merged batched steps
   void *multi = nullptr;                      // multi-column apply state (multi.cu), built on first use
