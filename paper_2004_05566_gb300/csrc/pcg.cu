@@ -26,7 +26,36 @@ namespace {
 
 constexpr int NT = 256;
 // device scalar slots
-enum { S_RZ = 0, S_ALPHA, S_BETA, S_RR, S_BB, S_PQ, S_CONV, S_IT, S_COUNT };
+// S_TRUE: set by the update kernel of an iteration whose residual is recomputed
+// (every true_res_period-th); the recomputing kernel finishes that iteration
+enum { S_RZ = 0, S_ALPHA, S_BETA, S_RR, S_BB, S_PQ, S_CONV, S_IT, S_TRUE, S_COUNT };
+
+// Programmatic dependent launch of the iteration's vector kernels: each is
+// launched early and waits here for the previous kernel's results, then lets
+// the next one be scheduled (no-ops without the launch attribute).
+__device__ __forceinline__ void cg_pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_cg(void (*kernel)(KArgs...), int grid, int block, cudaStream_t s, Args &&...args) {
+  static const bool pdl = [] {
+    const char *e = std::getenv("HIFCN_NO_PDL");
+    return !(e && e[0] == '1');
+  }();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 struct StencilArgs {
   const double *diag, *wx, *wy, *wz;
@@ -166,6 +195,7 @@ __global__ void k_scalar_start(double *__restrict__ s, const double *__restrict_
   s[S_BB] = v;
   s[S_RZ] = 0.0;
   s[S_IT] = 0.0;
+  s[S_TRUE] = 0.0;
   s[S_CONV] = v > 0.0 ? 0.0 : 1.0;
   s[S_RR] = v;
   if constexpr (kGraph) cudaGraphSetConditional(cond, v > 0.0 ? 1u : 0u);
@@ -299,6 +329,7 @@ __global__ void __launch_bounds__(NT) k_cg_wz(const double *__restrict__ r, cons
                                               StencilArgs st, double *__restrict__ part,
                                               double *__restrict__ s, unsigned *__restrict__ ticket) {
   __shared__ double sm[2 * (NT / 32)];
+  cg_pdl_enter();
   double arz = 0.0, awz = 0.0, aqz = 0.0;
   const bool first = s[S_IT] == 0.0;  // q holds no direction yet
   const int N = (int)st.N, S = st.n - 1, S2 = S * S;
@@ -394,9 +425,11 @@ __global__ void __launch_bounds__(NT) k_cg_update(double *__restrict__ x, double
                                                   cudaGraphConditionalHandle cond) {
   __shared__ double sm[2 * (NT / 32)];
   __shared__ int s_flags;  // bit 0: first iteration, bit 1: the true residual follows
+  cg_pdl_enter();
   if (threadIdx.x == 0) {
     const int it1 = (int)s[S_IT] + 1;  // iteration that updates x now
     s_flags = (it1 == 1 ? 1 : 0) | ((period > 0 && it1 % period == 0) ? 2 : 0);
+    if (s_flags & 2) s[S_TRUE] = 1.0;  // (every block writes the same value)
   }
   __syncthreads();
   const int flags = s_flags;
@@ -463,8 +496,12 @@ __global__ void __launch_bounds__(NT) k_true_residual_cond(const double *__restr
                                                            double *__restrict__ part,
                                                            unsigned *__restrict__ ticket, double tol2,
                                                            int maxit, cudaGraphConditionalHandle cond) {
-  const int it1 = (int)s[S_IT] + 1;
-  if (period <= 0 || it1 % period != 0) return;
+  // only after an update kernel that left the iteration to this one (its
+  // count is not advanced yet); every block reads the flag before the last
+  // block clears it
+  (void)period;
+  cg_pdl_enter();
+  if (s[S_TRUE] == 0.0) return;
   __shared__ double sm[NT / 32];
   double acc = 0.0;
   for (long long j = blockIdx.x * (long long)NT + threadIdx.x; j < st.N; j += (long long)gridDim.x * NT) {
@@ -479,6 +516,7 @@ __global__ void __launch_bounds__(NT) k_true_residual_cond(const double *__restr
   const double v = warp_sum_partials_cg(part, gridDim.x);
   if (threadIdx.x == 0) {
     *ticket = 0u;
+    s[S_TRUE] = 0.0;
     finish_iteration<kGraph>(s, v, tol2, maxit, cond);
   }
 }
@@ -538,6 +576,7 @@ __global__ void k_scalar_start_warm(double *__restrict__ s, const double *__rest
   s[S_RR] = rr;
   s[S_RZ] = 0.0;
   s[S_IT] = 0.0;
+  s[S_TRUE] = 0.0;
   const bool conv = bb == 0.0 || rr <= tol2 * bb;
   s[S_CONV] = conv ? 1.0 : 0.0;
   if constexpr (kGraph) cudaGraphSetConditional(cond, conv ? 0u : 1u);
@@ -593,12 +632,13 @@ int build_pcg_graph(Handle *h, TZ *z, PcgGraph *G, bool warm) {
   if constexpr (sizeof(TZ) == 8) st_apply = apply_inplace_f64(h, (double *)z, cs);
   else st_apply = apply_inplace_f32(h, (float *)z, cs);
   unsigned *tk = h->tickets;
-  k_cg_wz<TZ><<<nb, NT, 0, cs>>>(h->r, z, h->w, h->q, st, part, sc, tk);
-  k_cg_update<TZ, true><<<nb, NT, 0, cs>>>(h->xsol, h->r, h->p, h->q, h->w, z, sc, N, part, tk + 2,
-                                           h->opt.true_res_period, tol2, h->opt.cg_maxit, cond);
-  k_true_residual_cond<TZ, true><<<nb, NT, 0, cs>>>(h->g, h->xsol, h->r, z, st, sc,
-                                                    h->opt.true_res_period, part, tk + 3, tol2,
-                                                    h->opt.cg_maxit, cond);
+  HIF_CUDA_TRY(launch_cg(k_cg_wz<TZ>, nb, NT, cs, (const double *)h->r, (const TZ *)z, h->w,
+                         (const double *)h->q, st, part, sc, tk));
+  HIF_CUDA_TRY(launch_cg(k_cg_update<TZ, true>, nb, NT, cs, h->xsol, h->r, h->p, h->q, (const double *)h->w, z,
+                         sc, N, part, tk + 2, h->opt.true_res_period, tol2, h->opt.cg_maxit, cond));
+  HIF_CUDA_TRY(launch_cg(k_true_residual_cond<TZ, true>, nb, NT, cs, (const double *)h->g,
+                         (const double *)h->xsol, h->r, z, st, sc, h->opt.true_res_period, part, tk + 3, tol2,
+                         h->opt.cg_maxit, cond));
   note_launch(3);
   cudaGraph_t body_out = nullptr;
   cudaError_t e_end = cudaStreamEndCapture(cs, &body_out);

@@ -185,3 +185,25 @@ def test_zero_rhs_and_bad_arguments(H):
         H.hif_import_factor(w.dim, w.n, w.leaf, blob[:-8], w.dt,
                             torch.from_numpy(w.a_nodes).cuda())
 
+
+
+@pytest.mark.parametrize("period", [0, 2, 3, 7])
+def test_true_residual_period_keeps_the_count(H, period):
+    """The recurrence residual replaced by b - A x every `period` iterations:
+    a loose factor (eps = 0.2, about 10 PCG iterations) takes the oracle's
+    iteration count within one whatever the period, and each iteration is
+    counted once (the recomputation finishes the iteration it belongs to)."""
+    import torch
+    case = (2, 64, 8, 0.2, 1e4, 1.0)
+    w, A, F, blob = _problem(case)
+    a = torch.from_numpy(w.a_nodes).cuda()
+    opt = H.default_options(eps=w.eps, precision=0, cg_tol=1e-10, true_res_period=period)
+    h = H.hif_import_factor(w.dim, w.n, w.leaf, blob, w.dt, a, opt)
+    b = np.random.default_rng(9).standard_normal(F.N)
+    x, it, relres = H.pcg_solve(h, torch.from_numpy(b).cuda())
+    xr, itr, rr, conv = pcg.pcg(A, b, lambda v: hif.apply_inverse(F, v), tol=1e-10)
+    assert itr >= 6, itr
+    assert abs(it - itr) <= 1, (period, it, itr)
+    assert relres <= 1e-10 * 1.01
+    assert _rel(x.cpu().numpy(), xr) <= 1e-9
+    h.close()
