@@ -330,6 +330,7 @@ struct hif_handle {
   double *step_rec = nullptr;  // cn_steps: per-step records (iterations, status), device
   int step_rec_cap = 0;        // steps step_rec holds (grown on demand, freed with the handle)
   int nblocks_vec = 0;
+  int nblocks_cg = 0;  // blocks of the two pipelined PCG vector kernels (<= nblocks_vec)
 
   std::vector<hifcn::DevAlloc> allocations;
   bool offloaded = false;  // hif_offload: large allocations live in host memory

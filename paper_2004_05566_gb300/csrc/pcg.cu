@@ -299,6 +299,31 @@ __device__ __forceinline__ double2 sum_partials2(const double *pa, const double 
   return block_sum2<NTB>(a, b, sm);
 }
 
+// Block reduction of V values per thread through shared memory: every
+// thread stores its values, then warp v adds the NTB entries of value v
+// (lane l takes entries l, l + 32, ... in order) and finishes with a shuffle
+// tree.  The block total of value v is in lane 0 of warp v.  About a quarter
+// of the FP64 additions of per-warp shuffle trees, in a fixed order.  sm holds
+// V * NTB doubles.
+template <int NTB, int V>
+__device__ __forceinline__ double block_sum_smem(const double (&a)[V], double *sm) {
+  static_assert(V <= NTB / 32, "one warp per value");
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int v = 0; v < V; ++v) sm[v * NTB + threadIdx.x] = a[v];
+  __syncthreads();
+  double t = 0.0;
+  if (w < V) {
+    const double *p = sm + w * NTB;
+    t = p[lane];
+#pragma unroll
+    for (int k = 1; k < NTB / 32; ++k) t += p[lane + 32 * k];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  __syncthreads();
+  return t;
+}
+
 // PCG in the Chronopoulos-Gear arrangement (the same iterates as the
 // textbook PCG loop in exact arithmetic, one reduction phase fewer), with the
 // Polak-Ribiere (flexible) form of beta:
@@ -313,73 +338,110 @@ __device__ __forceinline__ double2 sum_partials2(const double *pa, const double 
 // the next, and the flexible form keeps the search directions conjugate
 // (about a tenth fewer iterations on the 1023^2 Fisher-KPP steps).
 //
-// On GB300 these kernels are bound by the FP64 pipe (about two FP64
-// operations per clock per SM): per unknown, w = A z takes one multiply and
-// four (3D: six) fused multiply-adds, the two dots two more, and the update
-// kernel five.  Everything else stays off that pipe: positions are walked
-// without divisions, the FP32 <-> FP64 conversions are integer bit
-// operations, both dots share one reduction tree, per-block scalars are read
+// On GB300 the FP64 pipe retires about two lane operations per clock per SM
+// (measured: 1.89 FMA lanes per clock and SM with independent chains), so
+// these kernels are bound by FP64 arithmetic and memory latency together:
+// per unknown, w = A z takes one multiply and four (3D: six) fused
+// multiply-adds, the three dots three more, and the update kernel five.
+// When every warp loads its operands, waits, then computes, the warps fall
+// into step: all of them wait on memory while the FP64 pipe idles, then all
+// compute while memory idles (ncu: FP64 pipe and DRAM each busy about half
+// the time).  So each thread keeps the operands of its next element in
+// registers: the loads of element j + stride are issued before the
+// arithmetic of element j (software pipelining, depth one), and the grid has
+// two blocks of 256 threads per SM (measured at 1023^2 with L2 flushed: the
+// pair of kernels 62.6 us in the load-then-compute form at four blocks per
+// SM, 50.7 us pipelined at two; deeper prefetch, more or fewer threads were
+// slower).  Absent stencil neighbours are loaded as a zero coefficient and a
+// zero value, so every row takes the same straight-line arithmetic (y - 0 * 0
+// is y exactly: the results equal those of skipping the term).  Positions are
+// walked without divisions, the FP32 <-> FP64 conversions are integer bit
+// operations, block sums go through shared memory, per-block scalars are read
 // once by one thread.
-//
+
+// operands of one row of w = A z and the dots (the 3D fields only with D3)
+template <typename TZ, bool D3>
+struct WzRow {
+  TZ z, zxp, zxm, zyp, zym, zzp, zzm;
+  double r, d, wxp, wxm, wyp, wym, wzp, wzm, q;
+};
+
+template <typename TZ, bool D3>
+__device__ __forceinline__ void wz_load(int j, int N, int S, int S2, const GridWalk &g, bool first,
+                                        const double *__restrict__ r, const TZ *__restrict__ z,
+                                        const double *__restrict__ q, const StencilArgs &st,
+                                        WzRow<TZ, D3> &a) {
+  if (j < N) {
+    const bool xp = g.i1 < S - 1, xm = g.i1 > 0, yp = g.i2 < S - 1, ym = g.i2 > 0;
+    a.z = z[j];
+    a.r = r[j];
+    a.d = st.diag[j];
+    a.q = first ? 0.0 : q[j];
+    a.wxp = xp ? st.wx[j] : 0.0;
+    a.zxp = xp ? z[j + 1] : TZ(0);
+    a.wxm = xm ? st.wx[j - 1] : 0.0;
+    a.zxm = xm ? z[j - 1] : TZ(0);
+    a.wyp = yp ? st.wy[j] : 0.0;
+    a.zyp = yp ? z[j + S] : TZ(0);
+    a.wym = ym ? st.wy[j - S] : 0.0;
+    a.zym = ym ? z[j - S] : TZ(0);
+    if constexpr (D3) {
+      const bool zp = g.i3 < S - 1, zm = g.i3 > 0;
+      a.wzp = zp ? st.wz[j] : 0.0;
+      a.zzp = zp ? z[j + S2] : TZ(0);
+      a.wzm = zm ? st.wz[j - S2] : 0.0;
+      a.zzm = zm ? z[j - S2] : TZ(0);
+    }
+  } else {
+    a.z = a.zxp = a.zxm = a.zyp = a.zym = TZ(0);
+    a.r = a.d = a.wxp = a.wxm = a.wyp = a.wym = a.q = 0.0;
+    if constexpr (D3) {
+      a.zzp = a.zzm = TZ(0);
+      a.wzp = a.wzm = 0.0;
+    }
+  }
+}
+
 // first kernel: w = A z, partials of r.z, w.z and q.z; the last block forms
 // beta, sigma and alpha
-template <typename TZ>
+template <typename TZ, bool D3>
 __global__ void __launch_bounds__(NT) k_cg_wz(const double *__restrict__ r, const TZ *__restrict__ z,
                                               double *__restrict__ w, const double *__restrict__ q,
                                               StencilArgs st, double *__restrict__ part,
                                               double *__restrict__ s, unsigned *__restrict__ ticket) {
-  __shared__ double sm[2 * (NT / 32)];
+  __shared__ double sm[3 * NT];
   cg_pdl_enter();
   double arz = 0.0, awz = 0.0, aqz = 0.0;
   const bool first = s[S_IT] == 0.0;  // q holds no direction yet
   const int N = (int)st.N, S = st.n - 1, S2 = S * S;
-  const int stride = gridDim.x * NT, stride2 = 2 * stride;
-  const bool d3 = st.dim == 3;
-  // two rows per pass (j and j + stride), written as straight-line code so
-  // that the loads of both are in flight together
-  auto row = [&](int j, const GridWalk &g) -> double {
-    const double zj = widen(z[j]);
-    double y = st.diag[j] * zj;
-    if (g.i1 < S - 1) y -= st.wx[j] * widen(z[j + 1]);
-    if (g.i1 > 0) y -= st.wx[j - 1] * widen(z[j - 1]);
-    if (g.i2 < S - 1) y -= st.wy[j] * widen(z[j + S]);
-    if (g.i2 > 0) y -= st.wy[j - S] * widen(z[j - S]);
-    if (d3) {
-      if (g.i3 < S - 1) y -= st.wz[j] * widen(z[j + S2]);
-      if (g.i3 > 0) y -= st.wz[j - S2] * widen(z[j - S2]);
-    }
-    return y;
-  };
+  const int stride = gridDim.x * NT;
   int j = blockIdx.x * NT + threadIdx.x;
-  GridWalk g0(j, stride2, S, d3), g1(j + stride, stride2, S, d3);
-  for (; j < N; j += stride2, g0.advance(S, d3), g1.advance(S, d3)) {
-    const int j1 = j + stride;
-    const double z0 = widen(z[j]), r0 = r[j];
-    const double y0 = row(j, g0);
-    double z1 = 0.0, r1 = 0.0, y1 = 0.0;
-    if (j1 < N) {
-      z1 = widen(z[j1]);
-      r1 = r[j1];
-      y1 = row(j1, g1);
+  GridWalk g(j, stride, S, D3);  // position of the next row to load
+  WzRow<TZ, D3> cur, nxt;
+  wz_load<TZ, D3>(j, N, S, S2, g, first, r, z, q, st, cur);
+  g.advance(S, D3);
+  for (; j < N; j += stride) {
+    wz_load<TZ, D3>(j + stride, N, S, S2, g, first, r, z, q, st, nxt);
+    g.advance(S, D3);
+    const double zj = widen(cur.z);
+    double y = cur.d * zj;
+    y -= cur.wxp * widen(cur.zxp);
+    y -= cur.wxm * widen(cur.zxm);
+    y -= cur.wyp * widen(cur.zyp);
+    y -= cur.wym * widen(cur.zym);
+    if constexpr (D3) {
+      y -= cur.wzp * widen(cur.zzp);
+      y -= cur.wzm * widen(cur.zzm);
     }
-    w[j] = y0;
-    if (j1 < N) w[j1] = y1;
-    if (!first) {
-      aqz += q[j] * z0;
-      if (j1 < N) aqz += q[j1] * z1;
-    }
-    arz += r0 * z0;
-    awz += y0 * z0;
-    arz += r1 * z1;
-    awz += y1 * z1;
+    w[j] = y;
+    aqz += cur.q * zj;
+    arz += cur.r * zj;
+    awz += y * zj;
+    cur = nxt;
   }
-  const double2 t = block_sum2<NT>(arz, awz, sm);
-  const double2 t3 = block_sum2<NT>(aqz, 0.0, sm);
-  if (threadIdx.x == 0) {
-    part[blockIdx.x] = t.x;
-    part[gridDim.x + blockIdx.x] = t.y;
-    part[2 * gridDim.x + blockIdx.x] = t3.x;
-  }
+  const double acc[3] = {arz, awz, aqz};
+  const double t = block_sum_smem<NT, 3>(acc, sm);
+  if ((threadIdx.x & 31) == 0 && threadIdx.x < 96) part[(threadIdx.x >> 5) * gridDim.x + blockIdx.x] = t;
   if (!last_block(ticket)) return;
   const double2 tot = sum_partials2<NT>(part, part + gridDim.x, gridDim.x, sm);
   const double2 tot3 = sum_partials2<NT>(part + 2 * gridDim.x, nullptr, gridDim.x, sm);
@@ -410,11 +472,36 @@ __device__ __forceinline__ void finish_iteration(double *s, double rr, double to
   if constexpr (kGraph) cudaGraphSetConditional(cond, (!conv && !failed && it < (double)maxit) ? 1u : 0u);
 }
 
+// operands of one element of the update
+template <typename TZ>
+struct UpdRow {
+  TZ z;
+  double w, r, x, p, q;
+};
+
+template <typename TZ>
+__device__ __forceinline__ void upd_load(int j, int n, bool first, const TZ *zin, const double *__restrict__ w,
+                                         const double *__restrict__ r, const double *__restrict__ x,
+                                         const double *__restrict__ p, const double *__restrict__ q,
+                                         UpdRow<TZ> &a) {
+  if (j < n) {
+    a.z = zin[j];
+    a.w = w[j];
+    a.r = r[j];
+    a.x = x[j];
+    a.p = first ? 0.0 : p[j];
+    a.q = first ? 0.0 : q[j];
+  } else {
+    a.z = TZ(0);
+    a.w = a.r = a.x = a.p = a.q = 0.0;
+  }
+}
+
 // second kernel: p = z + beta p, q = w + beta q (p = z, q = w on the first
 // iteration), x += alpha p, r -= alpha q, z-input = r, r.r; then (last block,
 // unless this iteration recomputes the true residual) the end-of-iteration
-// scalar phase.  z and zin are the same buffer: each element is read before
-// it is overwritten, by the same thread.
+// scalar phase.  z and zin are the same buffer: each element is read (one
+// element ahead, by the same thread) before it is overwritten.
 template <typename TZ, bool kGraph>
 __global__ void __launch_bounds__(NT) k_cg_update(double *__restrict__ x, double *__restrict__ r,
                                                   double *__restrict__ p, double *__restrict__ q,
@@ -423,7 +510,7 @@ __global__ void __launch_bounds__(NT) k_cg_update(double *__restrict__ x, double
                                                   double *__restrict__ part, unsigned *__restrict__ ticket,
                                                   int period, double tol2, int maxit,
                                                   cudaGraphConditionalHandle cond) {
-  __shared__ double sm[2 * (NT / 32)];
+  __shared__ double sm[NT];
   __shared__ int s_flags;  // bit 0: first iteration, bit 1: the true residual follows
   cg_pdl_enter();
   if (threadIdx.x == 0) {
@@ -438,44 +525,25 @@ __global__ void __launch_bounds__(NT) k_cg_update(double *__restrict__ x, double
   double acc = 0.0;
   const int n = (int)N;
   const int stride = gridDim.x * NT;
-  // two elements per pass (j and j + stride): all loads first, then the updates
-  for (int j = blockIdx.x * NT + threadIdx.x; j < n; j += 2 * stride) {
-    const int j1 = j + stride;
-    const bool h1 = j1 < n;
-    const double z0 = widen(zin[j]), w0 = w[j], r0 = r[j], x0 = x[j];
-    const double p0 = first ? 0.0 : p[j], q0 = first ? 0.0 : q[j];
-    double z1 = 0.0, w1 = 0.0, r1 = 0.0, x1 = 0.0, p1 = 0.0, q1 = 0.0;
-    if (h1) {
-      z1 = widen(zin[j1]);
-      w1 = w[j1];
-      r1 = r[j1];
-      x1 = x[j1];
-      if (!first) {
-        p1 = p[j1];
-        q1 = q[j1];
-      }
-    }
-    const double pj0 = first ? z0 : z0 + beta * p0, qj0 = first ? w0 : w0 + beta * q0;
-    const double rj0 = r0 - alpha * qj0;
-    p[j] = pj0;
-    q[j] = qj0;
-    x[j] = x0 + alpha * pj0;
-    r[j] = rj0;
-    zin[j] = to_z<TZ>(rj0);
-    acc += rj0 * rj0;
-    if (h1) {
-      const double pj1 = first ? z1 : z1 + beta * p1, qj1 = first ? w1 : w1 + beta * q1;
-      const double rj1 = r1 - alpha * qj1;
-      p[j1] = pj1;
-      q[j1] = qj1;
-      x[j1] = x1 + alpha * pj1;
-      r[j1] = rj1;
-      zin[j1] = to_z<TZ>(rj1);
-      acc += rj1 * rj1;
-    }
+  int j = blockIdx.x * NT + threadIdx.x;
+  UpdRow<TZ> cur, nxt;
+  upd_load<TZ>(j, n, first, zin, w, r, x, p, q, cur);
+  for (; j < n; j += stride) {
+    upd_load<TZ>(j + stride, n, first, zin, w, r, x, p, q, nxt);
+    const double zj = widen(cur.z);
+    const double pj = first ? zj : zj + beta * cur.p, qj = first ? cur.w : cur.w + beta * cur.q;
+    const double rj = cur.r - alpha * qj;
+    p[j] = pj;
+    q[j] = qj;
+    x[j] = cur.x + alpha * pj;
+    r[j] = rj;
+    zin[j] = to_z<TZ>(rj);
+    acc += rj * rj;
+    cur = nxt;
   }
-  const double2 t = block_sum2<NT>(acc, 0.0, sm);
-  if (threadIdx.x == 0) part[blockIdx.x] = t.x;
+  const double a1[1] = {acc};
+  const double t = block_sum_smem<NT, 1>(a1, sm);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
   if (flags & 2) return;  // the true-residual kernel finishes the iteration
   if (!last_block(ticket)) return;
   const double2 tot = sum_partials2<NT>(part, nullptr, gridDim.x, sm);
@@ -483,6 +551,21 @@ __global__ void __launch_bounds__(NT) k_cg_update(double *__restrict__ x, double
     *ticket = 0u;
     finish_iteration<kGraph>(s, tot.x, tol2, maxit, cond);
   }
+}
+
+// w = A z and the dots on nb blocks (the 2D or 3D form of the kernel),
+// with programmatic dependent launch when pdl is set
+template <typename TZ>
+cudaError_t launch_cg_wz(bool pdl, int nb, cudaStream_t s, const double *r, const TZ *z, double *w,
+                         const double *q, const StencilArgs &st, double *part, double *sc, unsigned *tk) {
+  if (st.dim == 3) {
+    if (pdl) return launch_cg(k_cg_wz<TZ, true>, nb, NT, s, r, z, w, q, st, part, sc, tk);
+    k_cg_wz<TZ, true><<<nb, NT, 0, s>>>(r, z, w, q, st, part, sc, tk);
+  } else {
+    if (pdl) return launch_cg(k_cg_wz<TZ, false>, nb, NT, s, r, z, w, q, st, part, sc, tk);
+    k_cg_wz<TZ, false><<<nb, NT, 0, s>>>(r, z, w, q, st, part, sc, tk);
+  }
+  return cudaGetLastError();
 }
 
 // every `period` iterations: r = b - A x, z-input = r, r.r and the
@@ -632,9 +715,9 @@ int build_pcg_graph(Handle *h, TZ *z, PcgGraph *G, bool warm) {
   if constexpr (sizeof(TZ) == 8) st_apply = apply_inplace_f64(h, (double *)z, cs);
   else st_apply = apply_inplace_f32(h, (float *)z, cs);
   unsigned *tk = h->tickets;
-  HIF_CUDA_TRY(launch_cg(k_cg_wz<TZ>, nb, NT, cs, (const double *)h->r, (const TZ *)z, h->w,
-                         (const double *)h->q, st, part, sc, tk));
-  HIF_CUDA_TRY(launch_cg(k_cg_update<TZ, true>, nb, NT, cs, h->xsol, h->r, h->p, h->q, (const double *)h->w, z,
+  const int nbc = h->nblocks_cg;
+  HIF_CUDA_TRY(launch_cg_wz<TZ>(true, nbc, cs, h->r, z, h->w, h->q, st, part, sc, tk));
+  HIF_CUDA_TRY(launch_cg(k_cg_update<TZ, true>, nbc, NT, cs, h->xsol, h->r, h->p, h->q, (const double *)h->w, z,
                          sc, N, part, tk + 2, h->opt.true_res_period, tol2, h->opt.cg_maxit, cond));
   HIF_CUDA_TRY(launch_cg(k_true_residual_cond<TZ, true>, nb, NT, cs, (const double *)h->g,
                          (const double *)h->xsol, h->r, z, st, sc, h->opt.true_res_period, part, tk + 3, tol2,
@@ -742,8 +825,8 @@ int pcg_impl(Handle *h, const double *b, double *x, TZ *z, int *iters_out, doubl
   const int period = h->opt.true_res_period;
   while (it < h->opt.cg_maxit) {
     HIF_TRY(precond(z));
-    k_cg_wz<TZ><<<nb, NT, 0, s>>>(h->r, z, h->w, h->q, st, part, sc, tk);
-    k_cg_update<TZ, false><<<nb, NT, 0, s>>>(x, h->r, h->p, h->q, h->w, z, sc, N, part, tk + 2, period,
+    HIF_CUDA_TRY(launch_cg_wz<TZ>(false, h->nblocks_cg, s, h->r, z, h->w, h->q, st, part, sc, tk));
+    k_cg_update<TZ, false><<<h->nblocks_cg, NT, 0, s>>>(x, h->r, h->p, h->q, h->w, z, sc, N, part, tk + 2, period,
                                             tol2, h->opt.cg_maxit, 0);
     k_true_residual_cond<TZ, false><<<nb, NT, 0, s>>>(b, x, h->r, z, st, sc, period, part, tk + 3, tol2,
                                                      h->opt.cg_maxit, 0);
@@ -876,8 +959,9 @@ int cn_cols(Handle *h, const double *U, const double *R, double *U1, int k, int 
       double *sct = C.scal + 16 * c, *part = C.part + 4LL * nb * c;
       unsigned *tk = C.tk + 4 * c;
       float *z = C.z + c * N;
-      k_cg_wz<float><<<nb, NT, 0, s>>>(C.r + c * N, z, C.w + c * N, C.q + c * N, st, part, sct, tk);
-      k_cg_update<float, false><<<nb, NT, 0, s>>>(C.x + c * N, C.r + c * N, C.p + c * N, C.q + c * N,
+      HIF_CUDA_TRY(launch_cg_wz<float>(false, h->nblocks_cg, s, C.r + c * N, z, C.w + c * N, C.q + c * N, st,
+                                       part, sct, tk));
+      k_cg_update<float, false><<<h->nblocks_cg, NT, 0, s>>>(C.x + c * N, C.r + c * N, C.p + c * N, C.q + c * N,
                                                   C.w + c * N, z, sct, N, part, tk + 2, period, tol2,
                                                   h->opt.cg_maxit, 0);
       k_true_residual_cond<float, false><<<nb, NT, 0, s>>>(C.g + c * N, C.x + c * N, C.r + c * N, z, st, sct,
