@@ -278,7 +278,7 @@ __device__ __forceinline__ void group_fwd_unit(const GroupDesc &g, const int *__
 constexpr int kSmallWarps = 8;
 
 // one warp: entity g with n <= 32; xs is the warp's 32-element buffer
-template <typename T, typename TV = T, bool PDL = false>
+template <typename T, typename TV = T, bool PDL = false, bool kPreload = false>
 __device__ __forceinline__ void group_fwd_small_warp(const GroupDesc &g, const int *__restrict__ idx,
                                                      const long long *__restrict__ cptr,
                                                      const long long *__restrict__ cslot,
@@ -287,19 +287,32 @@ __device__ __forceinline__ void group_fwd_small_warp(const GroupDesc &g, const i
                                                      T *__restrict__ x, T *xs) {
   const int lane = threadIdx.x & 31;
   const int *gi = idx + g.idx_off;
-  // static part: the DOF, its first contribution slots, the H row in L2
+  const int nq = (int)pad4(g.n) / 4;
+  // static part: the DOF, its first contribution slots and the H row.  With
+  // kPreload (the one-level FP32 kernels) the row itself is loaded into
+  // registers (at most 8 quads), so that after the dependency point only the
+  // gathers of x and the contributions are on the critical path; otherwise
+  // it is prefetched into L2 (in the fused sweeps, 32 more registers per
+  // thread would cost occupancy).
   constexpr int kSlots = 4;
+  constexpr bool kRegRow = kPreload && sizeof(T) == 4;
+  constexpr int kQ = kRegRow ? 8 : 1;
   int dof = 0;
   long long a = 0, b = 0, sl[kSlots];
+  T hv[kQ][4];
   if (lane < g.n) {
     dof = gi[lane];
     a = cptr[g.cptr_off + lane];
     b = cptr[g.cptr_off + lane + 1];
 #pragma unroll
     for (int k = 0; k < kSlots; ++k) sl[k] = a + k < b ? cslot[a + k] : 0;
-    if constexpr (PDL) {
-      const int np = (int)pad4(g.n);
-      prefetch_block_l2(vals + g.H_off + (long long)lane * np, np);
+    if constexpr (kRegRow) {
+      const TV *row = vals + g.H_off + (long long)lane * 4 * nq;
+#pragma unroll
+      for (int q = 0; q < kQ; ++q)
+        if (q < nq) ld4(row + 4 * q, hv[q]);
+    } else if constexpr (PDL) {
+      prefetch_block_l2(vals + g.H_off + (long long)lane * 4 * nq, 4 * nq);
     }
   }
   unit_dependency_point<PDL>();
@@ -314,38 +327,62 @@ __device__ __forceinline__ void group_fwd_small_warp(const GroupDesc &g, const i
   xs[lane] = v;
   __syncwarp();
   if (lane < g.n) {
-    const int np = (int)pad4(g.n);
-    const TV *row = vals + g.H_off + (long long)lane * np;
     T acc = T(0);
+    if constexpr (kRegRow) {
+#pragma unroll
+      for (int q = 0; q < kQ; ++q)
+        if (q < nq)
+          acc += hv[q][0] * xs[4 * q] + hv[q][1] * xs[4 * q + 1] + hv[q][2] * xs[4 * q + 2] +
+                 hv[q][3] * xs[4 * q + 3];
+    } else {
+      const TV *row = vals + g.H_off + (long long)lane * 4 * nq;
 #pragma unroll 8
-    for (int q = 0; q < np / 4; ++q) {
-      T w[4];
-      ld4(row + 4 * q, w);
-      acc += w[0] * xs[4 * q] + w[1] * xs[4 * q + 1] + w[2] * xs[4 * q + 2] + w[3] * xs[4 * q + 3];
+      for (int q = 0; q < nq; ++q) {
+        T w[4];
+        ld4(row + 4 * q, w);
+        acc += w[0] * xs[4 * q] + w[1] * xs[4 * q + 1] + w[2] * xs[4 * q + 2] + w[3] * xs[4 * q + 3];
+      }
     }
     x[gi[lane]] = acc;
   }
   __syncwarp();
 }
 
-template <typename T, typename TV = T, bool PDL = false>
+template <typename T, typename TV = T, bool PDL = false, bool kPreload = false>
 __device__ __forceinline__ void group_bwd_small_warp(const GroupDesc &g, const int *__restrict__ idx,
                                                      const TV *__restrict__ vals, T *__restrict__ x,
                                                      T *xs) {
   const int lane = threadIdx.x & 31;
   const int *gi = idx + g.idx_off;
   const int dof = lane < g.n ? gi[lane] : 0;
-  if constexpr (PDL)
-    if (lane < g.n) prefetch_block_l2(vals + g.H_off + (long long)lane * pad4(g.n), pad4(g.n));
+  const long long np = pad4(g.n);
+  const TV *H = vals + g.H_off;
+  // lane l forms column l of H^T x: with kPreload (the one-level FP32
+  // kernels) the column (at most 32 values) is loaded into registers before
+  // the dependency point, otherwise the rows are prefetched into L2
+  constexpr bool kRegCol = kPreload && sizeof(T) == 4;
+  constexpr int kR = kRegCol ? 32 : 1;
+  T hc[kR];
+  if constexpr (kRegCol) {
+#pragma unroll
+    for (int r = 0; r < kR; ++r)
+      if (lane < g.n && r < g.n) hc[r] = ldv<T>(H + (long long)r * np + lane);
+  } else if constexpr (PDL) {
+    if (lane < g.n) prefetch_block_l2(H + (long long)lane * np, np);
+  }
   unit_dependency_point<PDL>();
   xs[lane] = lane < g.n ? __ldcg(x + dof) : T(0);
   __syncwarp();
   if (lane < g.n) {
-    const long long np = pad4(g.n);
-    const TV *H = vals + g.H_off;
     T acc = T(0);
+    if constexpr (kRegCol) {
+#pragma unroll
+      for (int r = 0; r < kR; ++r)
+        if (r < g.n) acc += hc[r] * xs[r];
+    } else {
 #pragma unroll 8
-    for (int r = 0; r < g.n; ++r) acc += ldv<T>(H + (long long)r * np + lane) * xs[r];
+      for (int r = 0; r < g.n; ++r) acc += ldv<T>(H + (long long)r * np + lane) * xs[r];
+    }
     x[gi[lane]] = acc;
   }
   __syncwarp();
@@ -448,7 +485,7 @@ __global__ void __launch_bounds__(kSmallWarps * 32) k_group_fwd_level(
   const int warp = threadIdx.x >> 5;
   const int t = (u - nlarge) * kSmallWarps + warp;
   if (t < nsmall)
-    group_fwd_small_warp<T, TV, true>(groups[small[t]], idx, cptr, cslot, vals, contrib, x,
+    group_fwd_small_warp<T, TV, true, true>(groups[small[t]], idx, cptr, cslot, vals, contrib, x,
                                       sm + 32 * warp);
   else
     pdl_enter();  // a warp without an entity
@@ -469,7 +506,7 @@ __global__ void __launch_bounds__(kSmallWarps * 32) k_group_bwd_level(
   const int warp = threadIdx.x >> 5;
   const int t = (u - nlarge) * kSmallWarps + warp;
   if (t < nsmall)
-    group_bwd_small_warp<T, TV, true>(groups[small[t]], idx, vals, x, sm + 32 * warp);
+    group_bwd_small_warp<T, TV, true, true>(groups[small[t]], idx, vals, x, sm + 32 * warp);
   else
     pdl_enter();  // a warp without an entity
 }
