@@ -81,6 +81,9 @@ int alloc_work(Handle *h) {
   int cg_bps = 2;
   if (const char *e = std::getenv("HIFCN_CG_BPS")) cg_bps = std::max(1, std::min(16, std::atoi(e)));
   h->nblocks_cg = (int)std::min<long long>(nb, std::max<long long>(1, std::min<long long>((N + 255) / 256, 152LL * cg_bps)));
+  // HIFCN_CG_GRID caps that grid (tests: many elements per thread at small sizes)
+  if (const char *e = std::getenv("HIFCN_CG_GRID"))
+    if (std::atoi(e) > 0) h->nblocks_cg = std::min(h->nblocks_cg, std::atoi(e));
   HIF_TRY(dev_alloc(h, (void **)&h->r, N * sizeof(double)));
   HIF_TRY(dev_alloc(h, (void **)&h->p, N * sizeof(double)));
   HIF_TRY(dev_alloc(h, (void **)&h->q, N * sizeof(double)));
