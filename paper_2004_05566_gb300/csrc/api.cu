@@ -66,9 +66,10 @@ StatScope::~StatScope() {
 
 int alloc_work(Handle *h) {
   const long long N = h->N;
-  // blocks of the CG vector kernels: 4 per SM (measured at 1023^2: 839 us per step
-  // against 866 us with 8 per SM and 849 us with 2; fewer blocks mean shorter FP64
-  // reduction trees, too few leave memory latency uncovered)
+  // blocks of the other vector kernels (start, true residual, residual norm, RHS):
+  // 4 per SM (measured at 1023^2 with the earlier load-then-compute CG kernels: 839
+  // us per step against 866 us with 8 per SM and 849 us with 2); the per-block
+  // partial sums are sized for this grid
   int bps = 4;
   if (const char *e = std::getenv("HIFCN_VEC_BPS")) bps = std::max(1, std::min(16, std::atoi(e)));
   long long nb = (N + 255) / 256;
